@@ -1,0 +1,141 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle side.
+
+This module holds no arithmetic of the method itself: it draws the synthetic
+PDF grid (the thesis's LHAPDF sets are not available, so a grid of the same
+shape stands in for them) and names the integrand configurations.
+
+PDF grid recipe (stand-in for an LHAPDF set such as NNPDF3.1, thesis
+Sec. "LHAPDF: the Les Houches Accord PDF"): 100 x knots x_i = 10^(-7 + 7 i/99)
+with x_99 = 1, 40 Q knots Q_j = 1.65 (1e4/1.65)^(j/39) GeV, 11 flavours in
+LHAPDF order (-5..-1, 21, 1..5), values
+    x f(x, Q) = A x^-a (1 - x)^b (1 + c ln(Q^2 / Q0^2)),  Q0 = 1.65 GeV,
+with (A, a, b, c) drawn per flavour from SplitMix64(seed):
+A in [0.5, 2] (times 3 for the gluon), a in [0, 0.3], b in [2, 6], c in [0, 0.2].
+"""
+from dataclasses import dataclass, asdict
+import math
+
+import numpy as np
+
+PIDS = (-5, -4, -3, -2, -1, 21, 1, 2, 3, 4, 5)
+GEV2_TO_PB = 0.3893794e9
+
+EE_MUMU, PP_TTBAR, GG_TTBARG, GAUSS = 0, 1, 2, 3
+FP64, FP32 = 0, 1
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea, Flood 2014): seeds the synthetic inputs."""
+
+    def __init__(self, seed):
+        self.state = seed & 0xFFFFFFFFFFFFFFFF
+
+    def next_u64(self):
+        self.state = (self.state + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+        return z ^ (z >> 31)
+
+    def uniform(self, lo=0.0, hi=1.0):
+        return lo + (hi - lo) * (self.next_u64() >> 11) * 2.0 ** -53
+
+
+@dataclass
+class PdfGrid:
+    x: np.ndarray        # [nx]
+    q: np.ndarray        # [nq] (GeV)
+    pids: np.ndarray     # [nflav] int32
+    xf: np.ndarray       # [nx][nq][nflav] float64 (LHAPDF data-block order)
+    params: np.ndarray   # [nflav][4] (A, a, b, c)
+
+
+def synthetic_pdf_grid(seed=0, nx=100, nq=40, xmin=1e-7, qmin=1.65, qmax=1e4):
+    x = np.array([10.0 ** (math.log10(xmin) * (1.0 - i / (nx - 1))) for i in range(nx)])
+    x[-1] = 1.0
+    q = np.array([qmin * (qmax / qmin) ** (j / (nq - 1)) for j in range(nq)])
+    rng = SplitMix64(seed)
+    params = []
+    for pid in PIDS:
+        A = rng.uniform(0.5, 2.0) * (3.0 if pid == 21 else 1.0)
+        a = rng.uniform(0.0, 0.3)
+        b = rng.uniform(2.0, 6.0)
+        c = rng.uniform(0.0, 0.2)
+        params.append((A, a, b, c))
+    params = np.array(params)
+    xf = np.empty((nx, nq, len(PIDS)))
+    q0 = qmin
+    for fl, (A, a, b, c) in enumerate(params):
+        for i, xi in enumerate(x):
+            for j, qj in enumerate(q):
+                xf[i, j, fl] = A * xi ** (-a) * (1.0 - xi) ** b * (1.0 + c * math.log(qj * qj / (q0 * q0)))
+    return PdfGrid(x=x, q=q, pids=np.array(PIDS, dtype=np.int32), xf=xf, params=params)
+
+
+@dataclass
+class Integrand:
+    """One integrand of the cross-section family (field order = C struct order)."""
+    proc: int
+    gauss_dim: int = 0
+    sqrt_s: float = 13000.0
+    m_top: float = 173.0
+    alpha: float = 1.0 / 128.0
+    alpha_s: float = 0.118
+    mz: float = 91.1876
+    gz: float = 2.4952
+    sw2: float = 0.2312
+    mu_f: float = 173.0
+    ptcut_g: float = 20.0
+    etacut_g: float = 2.5
+    gauss_sigma: float = 0.1
+    gev2pb: float = GEV2_TO_PB
+
+    def ndim(self):
+        return {EE_MUMU: 2, PP_TTBAR: 4, GG_TTBARG: 14}.get(self.proc, self.gauss_dim)
+
+    def asdict(self):
+        return asdict(self)
+
+
+def ee_mumu(sqrt_s=91.0):
+    """e+e- -> mu+mu- via gamma + Z (2 dims: cos theta, phi)."""
+    return Integrand(proc=EE_MUMU, sqrt_s=sqrt_s)
+
+
+def pp_ttbar(sqrt_s=13000.0):
+    """pp -> t tbar at LO, gg + q qbar (4 dims: x1, x2, cos theta, phi)."""
+    return Integrand(proc=PP_TTBAR, sqrt_s=sqrt_s)
+
+
+def gg_ttbarg(sqrt_s=13000.0):
+    """gg -> t tbar g with RAMBO (2 + 12 dims), gluon pT > 20 GeV, |eta| < 2.5."""
+    return Integrand(proc=GG_TTBARG, sqrt_s=sqrt_s)
+
+
+def gauss(dim, sigma=0.1):
+    """Normalised Gaussian centred at 1/2; integral over the cube erf(1/(2 sqrt2 sigma))^d."""
+    return Integrand(proc=GAUSS, gauss_dim=dim, gauss_sigma=sigma, sqrt_s=0.0)
+
+
+def gauss_exact(dim, sigma=0.1):
+    return math.erf(0.5 / (sigma * math.sqrt(2.0))) ** dim
+
+
+def batch_configs(seed=0):
+    """Sixteen integrands of uneven dimension and size: e+e- -> mu+mu-, pp -> tt and
+    gg -> ttg at sqrt(s) = 0.5, 2, 7, 13 TeV plus Gaussians in d = 4, 8, 12, 16; event
+    counts N_i = round(10^(4 + 3 U_i)) with U_i from SplitMix64(seed)."""
+    rng = SplitMix64(seed)
+    items = []
+    for mk in (ee_mumu, pp_ttbar, gg_ttbarg):
+        for rs in (500.0, 2000.0, 7000.0, 13000.0):
+            items.append(mk(rs))
+    for d in (4, 8, 12, 16):
+        items.append(gauss(d))
+    counts = [int(round(10.0 ** (4.0 + 3.0 * rng.uniform()))) for _ in items]
+    return items, counts
+
+
+def uniform_grid(ndim, nbins):
+    """Initial VEGAS grid: nbins equal bins per dimension, [ndim][nbins+1]."""
+    return np.tile(np.linspace(0.0, 1.0, nbins + 1), (ndim, 1))

@@ -1,0 +1,24 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (B300, sm_103a)")
+
+
+@pytest.fixture(scope="session")
+def pdf_grid():
+    from paper_2302_03343_b300 import workloads
+    return workloads.synthetic_pdf_grid(seed=0)
+
+
+@pytest.fixture(scope="session")
+def oracle_pdf(pdf_grid):
+    import oracle
+    return oracle.Pdf(pdf_grid)
