@@ -1,0 +1,287 @@
+"""Benchmark of the per-event Monte Carlo cross-section path on B300.
+
+Workload (one "step" = one VEGAS iteration = the whole hot path over one batch):
+gg -> t tbar g at sqrt(s) = 13 TeV, RAMBO phase space (2 + 12 sampled
+dimensions, 7 physical), gluon pT > 20 GeV and |eta| < 2.5, synthetic
+LHAPDF-shaped PDF grid, FP32 helicity-amplitude |M|^2 with Kahan FP64
+accumulation, 1e7 events per iteration, 50 VEGAS bins per dimension, each step
+followed by the grid refinement.  Inputs are synthetic and seeded.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a
+bounded sample of events per step on the host cores).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2302_03343_b300 import workloads as W  # noqa: E402
+
+EVENTS = 10_000_000
+NBINS = 50
+ALPHA = 1.5
+WORKLOAD = ("gg->ttg 13 TeV, RAMBO 2+12 dims (7 physical), gluon pT>20 GeV |eta|<2.5, synthetic 100x40x11 "
+            "PDF grid, FP32 helicity |M|^2 + Kahan FP64 sums, VEGAS 50 bins, 1e7 events/iteration")
+METRIC = "events/sec and GPU time to 1e-3 rel. error: FP32+flow vs plain FP64 VEGAS"
+# FP32 floating-point operations per evaluated gg -> ttg event of the fused
+# kernel (|M|^2 with 32 helicity configurations, RAMBO, PDFs, map), counted by
+# ncu as fadd + fmul + 2 ffma over one launch divided by the number of
+# evaluated (in-cut) events; see profiles/.
+FLOP_PER_EVENT = float(os.environ.get("MC_FLOP_PER_EVENT", "0")) or None
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, device_index=0):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[0] == str(device_index):
+                    rows.append(f)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(seconds=15.0, iteration=3):
+    """The FP64 oracle as it stands, timed on the host cores over a bounded
+    sample of the same workload (fresh uniform grid, one iteration)."""
+    import oracle as O
+    grid = W.synthetic_pdf_grid(0)
+    pdf = O.Pdf(grid)
+    itg = W.gg_ttbarg()
+    edges = W.uniform_grid(14, NBINS)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    n0 = 200 * cores
+    O.iterate(itg, pdf, edges, 1, 0, iteration, 0, 0, n0, nthreads=cores)
+    dt = time.perf_counter() - t0
+    n = max(n0, int(n0 * seconds / max(dt, 1e-3)))
+    t0 = time.perf_counter()
+    O.iterate(itg, pdf, edges, 1, 0, iteration, 0, n0, n, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} gg->ttg events (one iteration on a uniform 50-bin grid, FP64 oracle, "
+                      f"{cores} threads, {dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    base = cpu_baseline(seconds=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
+    # each step: a bounded sample of the same workload on all host cores
+    import oracle as O
+    grid = W.synthetic_pdf_grid(0)
+    pdf = O.Pdf(grid)
+    itg = W.gg_ttbarg()
+    edges = W.uniform_grid(14, NBINS)
+    cores = os.cpu_count() or 1
+    n = max(1000, int(base["value"] * 5.0))
+    for i in range(args.warmup):
+        O.iterate(itg, pdf, edges, 1, 0, i, 0, 0, max(1000, n // 10), nthreads=cores)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.iterate(itg, pdf, edges, 1, 0, args.warmup + i, 0, 0, n, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+        edges = O.vegas_refine(edges, r["hist_w2"], ALPHA)
+    value = n * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events_per_step": n, "sample": "bounded CPU sample per step"},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} events per step, {cores} threads"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_native(args, rank, world):
+    import torch
+    from paper_2302_03343_b300 import build
+    from paper_2302_03343_b300 import mcint as M
+
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream()
+    grid = W.synthetic_pdf_grid(0)
+    pdf = M.mc_pdf_load(grid)
+    itg = W.gg_ttbarg()
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+    # weak scaling: every rank runs its own integration (its own Philox stream)
+    v = M.mc_vegas_init(14, NBINS, 1000 + rank, M.MC_FP32_KAHAN)
+    for _ in range(args.warmup):
+        M.mc_vegas_iterate(v, itg, pdf, args.events, stream)
+        M.mc_vegas_refine(v, ALPHA, stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kernel_ms, nnz, results = [], [], []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler() as clk:
+        for i in range(args.steps):
+            flush_l2(l2)
+            ev[i][0].record(stream)
+            r = M.mc_vegas_iterate(v, itg, pdf, args.events, stream)
+            M.mc_vegas_refine(v, ALPHA, stream)
+            ev[i][1].record(stream)
+            kernel_ms.append(M.mc_vegas_kernel_ms(v))
+            nnz.append(r.n_nonzero)
+            results.append(r)
+        torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+    barrier()
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    clocks = clk.summary(local)
+
+    # end to end through the public API with host buffers: upload the host
+    # grid, iterate (sums back to the host), refine, read the grid back
+    edges = M.mc_vegas_get_grid(v)
+    ve = M.mc_vegas_init(14, NBINS, 5000 + rank, M.MC_FP32_KAHAN)
+    e2e_s = []
+    for i in range(args.steps):
+        flush_l2(l2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.mc_vegas_set_grid(ve, edges)
+        M.mc_vegas_iterate(ve, itg, pdf, args.events, stream)
+        M.mc_vegas_refine(ve, ALPHA, stream)
+        edges = M.mc_vegas_get_grid(ve)
+        e2e_s.append(time.perf_counter() - t0)
+    ngrid = 14 * (NBINS + 1)
+    h2d = ngrid * 8 + ngrid * 4
+    d2h = 64 + ngrid * 8
+
+    if rank != 0:
+        return
+    value = args.events * args.steps * world / (total_ms / 1e3)
+    pk = peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = pk.get("sm_max_mhz", 2032.0)
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s
+    mean_kernel_ms = sum(kernel_ms) / len(kernel_ms)
+    mean_nnz = sum(nnz) / len(nnz)
+    if FLOP_PER_EVENT:
+        achieved = FLOP_PER_EVENT * mean_nnz / (mean_kernel_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "note": "FLOP/event not yet counted"}
+    roof["kernel_ms"] = mean_kernel_ms
+    roof["events_in_cuts_per_launch"] = mean_nnz
+    r_last = results[-1]
+    mean = r_last.sum / r_last.n
+    var = (r_last.sum2 / r_last.n - mean * mean) / (r_last.n - 1)
+    line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (|M|^2) + f64 (sums, RAMBO boosts)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events_per_step": args.events, "nbins": NBINS,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "clocks": clocks,
+            "e2e": {"value": args.events * args.steps / sum(e2e_s), "unit": "events/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 3 * args.steps,
+            "roofline": roof,
+            "last_iteration": {"mean_pb": mean, "rel_err": (var ** 0.5) / abs(mean) if mean else None,
+                               "n_nonzero": r_last.n_nonzero, "unweighting_eff": mean / r_last.wmax
+                               if r_last.wmax > 0 else None}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--events", type=int, default=EVENTS)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

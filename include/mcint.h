@@ -1,0 +1,218 @@
+/*
+ * mcint.h - C ABI of the B300 per-event Monte Carlo cross-section library.
+ *
+ * The library evaluates, one event per thread inside a single fused CUDA
+ * kernel, the leading-order collider cross-section integrand of the thesis
+ * arXiv:2302.03343 (Part II, "MadFlow" chapter, master formula
+ * eq. mc_master_formula):
+ *
+ *     sigma = sum_ab int dPhi_n(x1, x2, p) L(x1, x2) |M(ab -> X)|^2
+ *
+ * sampled with the VEGAS importance sampler (Sec. "Adaptive Monte Carlo:
+ * VEGAS algorithm"): each event draws counter-based Philox4x32-10 uniforms,
+ * maps them through the VEGAS grid, builds phase space (two-body or RAMBO,
+ * Sec. "RAMBO"), interpolates the PDFs log-bicubically (Sec. "LHAPDF"),
+ * evaluates |M|^2 from helicity amplitudes and accumulates the weighted sum,
+ * the sum of squares and the per-bin VEGAS histograms.
+ *
+ * Conventions for every entry point:
+ *  - Return value: MC_OK (0) or a negative MC_E* code; nothing throws across
+ *    the ABI.  mc_last_error() returns a message for the calling thread's
+ *    last failure (valid until the next call from that thread).
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    device memory of the current device.  Input arrays are caller-owned
+ *    and are copied (or only read) before the call returns.
+ *  - Handles (mc_pdf, mc_vegas) are library-owned; free them with the
+ *    matching *_free call.  A handle belongs to the device that was current
+ *    when it was created.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that return results to the host synchronise that stream
+ *    before returning; other calls are asynchronous on it.
+ *  - Energies in GeV, cross sections in pb.
+ */
+#ifndef MCINT_H
+#define MCINT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define MC_OK 0
+#define MC_EINVAL (-1)   /* invalid argument (shape, range, NaN input)          */
+#define MC_ENOMEM (-2)   /* device or pinned-host allocation failed             */
+#define MC_ECUDA (-3)    /* a CUDA runtime call failed                          */
+#define MC_ENAN (-4)     /* non-finite event weights were produced (counted)    */
+#define MC_ENOCONV (-5)  /* RAMBO's massive rescaling did not converge (counted) */
+#define MC_ETIMEOUT (-6) /* reserved: a bounded device wait gave up             */
+
+/* -------------------------------------------------------------- enums */
+#define MC_FP64 0        /* integrand in FP64, 52-bit uniforms                   */
+#define MC_FP32_KAHAN 1  /* integrand in FP32, 23-bit uniforms, FP64 reductions  */
+
+#define MC_EE_MUMU 0    /* e+e- -> mu+mu- (gamma + Z), 2 dims                    */
+#define MC_PP_TTBAR 1   /* p p -> t tbar (gg + q qbar), 4 dims                   */
+#define MC_GG_TTBARG 2  /* g g -> t tbar g, RAMBO, 14 dims (7 physical)          */
+#define MC_GAUSS 3      /* normalised Gaussian centred at 1/2, gauss_dim dims     */
+
+#define MC_MAX_DIM 16
+#define MC_MAX_BINS 256
+
+typedef struct mc_pdf_s* mc_pdf;
+typedef struct mc_vegas_s* mc_vegas;
+
+/* One integrand.  Field order is part of the ABI. */
+typedef struct {
+  int32_t proc;        /* MC_EE_MUMU ... MC_GAUSS                                */
+  int32_t gauss_dim;   /* dimension of MC_GAUSS (1..16), ignored otherwise       */
+  double sqrt_s;       /* collider (or e+e-) centre-of-mass energy              */
+  double m_top;        /* top-quark mass                                         */
+  double alpha;        /* QED coupling (e+e- -> mu+mu-)                          */
+  double alpha_s;      /* strong coupling, fixed                                 */
+  double mz, gz, sw2;  /* Z mass, width, sin^2(theta_W)                          */
+  double mu_f;         /* factorisation scale: PDFs are read at Q = mu_f         */
+  double ptcut_g;      /* gg -> ttg: gluon pT > ptcut_g                          */
+  double etacut_g;     /* gg -> ttg: |eta_gluon| < etacut_g (lab frame)          */
+  double gauss_sigma;  /* width of MC_GAUSS                                      */
+  double gev2pb;       /* GeV^-2 -> pb conversion (0.3893794e9)                  */
+} mc_integrand;
+
+/* Result of one VEGAS iteration (thesis eq. mc_est_is / eq. var_is inputs). */
+typedef struct {
+  double sum;          /* sum of event weights w = f * J (Kahan, FP64)           */
+  double sum2;         /* sum of w^2                                             */
+  int64_t n;           /* events evaluated                                       */
+  int64_t n_nonzero;   /* events with w != 0                                     */
+  double wmax;         /* largest weight (unweighting efficiency = mean / wmax)  */
+  int64_t n_bad;       /* events dropped as non-finite or non-converged          */
+  int32_t status;      /* MC_OK, MC_ENAN or MC_ENOCONV                           */
+  int32_t pad_;
+} mc_iter_result;
+
+/* Combined result (thesis Sec. "Adaptive Monte Carlo: VEGAS algorithm":
+ * inverse-variance mean, its error, and eq. vegas-check chi^2/dof). */
+typedef struct {
+  double mean, sigma, chi2_dof;
+  int32_t n_iter;      /* iterations actually run                                */
+  int32_t status;
+  double gpu_ms;       /* device time of all iterations (CUDA events)            */
+} mc_result;
+
+/* Thread-local message for the last failing call of this thread. */
+const char* mc_last_error(void);
+
+/* ------------------------------------------------------------------ PDF
+ * mc_pdf_load: an LHAPDF-style grid (thesis Sec. "LHAPDF: the Les Houches
+ * Accord PDF"; PDFFlow's mkPDF/Subgrid of Sec. "Software design and
+ * benchmarks").  x_knots[nx] strictly increasing in (0, 1], q_knots[nq]
+ * strictly increasing (GeV), pids[nflav] PDG codes (21 = gluon), xf
+ * [nx][nq][nflav] values x*f(x, Q) in the LHAPDF data-block order (x outer,
+ * Q, then flavour), FP64, all host.  nx, nq >= 4.  Values must be finite.
+ * The grid is copied to the device in FP64 and FP32.  EINVAL on bad shapes,
+ * non-monotone knots or non-finite values; ENOMEM / ECUDA on device failure.
+ */
+int mc_pdf_load(const double* x_knots, int nx, const double* q_knots, int nq,
+                const int32_t* pids, int nflav, const double* xf, mc_pdf* out);
+int mc_pdf_free(mc_pdf pdf);
+
+/* mc_pdf_xfxq2: PDFFlow's xfxQ2 over a batch (thesis Sec. "Software design
+ * and benchmarks"): for n query points (x[i], q2[i]) (device arrays, FP64)
+ * writes all flavours, xf_out[i][nflav] (device, FP64), by log-bicubic
+ * Hermite interpolation in (log x, log Q^2); points outside the grid give
+ * NaN.  prec selects FP64 or FP32 arithmetic.  Asynchronous on `stream`.
+ */
+int mc_pdf_xfxq2(mc_pdf pdf, int prec, int64_t n, const double* x, const double* q2,
+                 double* xf_out, void* stream);
+
+/* ---------------------------------------------------------------- VEGAS
+ * mc_vegas_init: a VEGAS grid of ndim (1..16) dimensions with nbins
+ * (2..256) equal bins each, the Philox seed, and the precision (MC_FP64 or
+ * MC_FP32_KAHAN).  The iteration counter starts at 0; it enters the Philox
+ * counter so every iteration draws fresh, reproducible uniforms.
+ */
+int mc_vegas_init(int ndim, int nbins, uint64_t seed, int prec, mc_vegas* out);
+int mc_vegas_free(mc_vegas v);
+/* Grid edges [ndim][nbins+1], host, FP64; set requires edges[d][0] = 0,
+ * edges[d][nbins] = 1 and strictly increasing edges. */
+int mc_vegas_set_grid(mc_vegas v, const double* edges);
+int mc_vegas_get_grid(mc_vegas v, double* edges);
+/* Accumulated histograms since the last refine: w2[ndim][nbins] (sum of w^2)
+ * and counts[ndim][nbins] (events), host outputs; synchronises the device. */
+int mc_vegas_get_hist(mc_vegas v, double* w2, uint32_t* counts);
+int mc_vegas_set_iteration(mc_vegas v, uint32_t iteration);
+int mc_vegas_get_iteration(mc_vegas v, uint32_t* iteration);
+/* Integrand id (0..255) mixed into the Philox counter (batched runs). */
+int mc_vegas_set_gid(mc_vegas v, uint32_t gid);
+
+/* mc_vegas_iterate: one VEGAS iteration of nevents events (eq. mc_est_is):
+ * launches the fused integrand kernel over events 0..nevents-1 of the
+ * current iteration, accumulates the histograms, advances the iteration
+ * counter and returns the sums in *out (host; the stream is synchronised).
+ * pdf may be NULL for processes without hadrons.  ndim of the grid must
+ * equal the process dimension.  Events with a non-finite weight, or whose
+ * RAMBO rescaling failed, contribute zero and are counted in out->n_bad;
+ * out->status is then MC_ENAN or MC_ENOCONV while the call itself returns
+ * MC_OK (the sums stay valid).
+ */
+int mc_vegas_iterate(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents,
+                     void* stream, mc_iter_result* out);
+
+/* mc_vegas_refine: rebins every dimension from the accumulated histograms
+ * (smoothing, damping exponent alpha, equal-importance rebinning after
+ * Lepage 1978, the reference of the thesis's VEGAS section) and clears the
+ * histograms.  Asynchronous on `stream`. */
+int mc_vegas_refine(mc_vegas v, double alpha, void* stream);
+
+/* mc_integrate: full VEGAS integration from a uniform grid: up to niter
+ * iterations of nevents events, refining with damping alpha after each, and
+ * the inverse-variance combination with chi^2/dof.  target_rel_err > 0 stops
+ * at the first iteration whose combined sigma/|mean| <= target_rel_err.
+ * per_iter (host, may be NULL) receives niter results.  gid as in
+ * mc_vegas_set_gid.  The stream is synchronised once per iteration.
+ */
+int mc_integrate(const mc_integrand* itg, mc_pdf pdf, int niter, int64_t nevents, int nbins,
+                 uint64_t seed, uint32_t gid, int prec, double alpha, double target_rel_err,
+                 void* stream, mc_result* out, mc_iter_result* per_iter);
+
+/* ------------------------------------------------------------ debugging
+ * mc_debug_events: per-event intermediates of events first..first+k-1 of
+ * the current iteration (the counter is not advanced and no sums or
+ * histograms change), written to out (device, FP64, [k][MC_REC_STRIDE]).
+ * Used by the parity tests.
+ */
+#define MC_REC_K 0        /* 16: integer uniforms (exact in FP64)               */
+#define MC_REC_X 16       /* 16: mapped point x                                 */
+#define MC_REC_BIN 32     /* 16: VEGAS bin per dimension                        */
+#define MC_REC_JAC 48     /* VEGAS Jacobian                                     */
+#define MC_REC_P 49       /* 7 x 4: incoming a, b, outgoing momenta, CM frame    */
+#define MC_REC_X1 77
+#define MC_REC_X2 78
+#define MC_REC_SHAT 79
+#define MC_REC_LUMI 80    /* f_g(x1) f_g(x2), or 1 for e+e-                      */
+#define MC_REC_LUMI_QQ 81 /* sum_q f_q f_qbar + f_qbar f_q (pp -> tt)            */
+#define MC_REC_ME2 82     /* averaged |M|^2 (gg channel for pp -> tt)            */
+#define MC_REC_ME2_QQ 83  /* averaged |M|^2 of q qbar -> tt                      */
+#define MC_REC_PSW 84     /* phase-space weight per unit hypercube               */
+#define MC_REC_F 85       /* integrand value, pb                                 */
+#define MC_REC_W 86       /* event weight f * J                                  */
+#define MC_REC_PASS 87    /* 1 inside cuts and thresholds, else 0                */
+#define MC_REC_STATUS 88  /* 0, or MC_ENAN / MC_ENOCONV                          */
+#define MC_REC_STRIDE 96
+int mc_debug_events(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t first, int64_t k,
+                    double* out, void* stream);
+
+/* Device time (ms) of the fused integrand kernel launched by the last
+ * mc_vegas_iterate on this handle, from CUDA events recorded on the caller's
+ * stream immediately around that launch (0 if no events were evaluated). */
+int mc_vegas_kernel_ms(mc_vegas v, float* ms);
+
+/* Number of SMs of the current device and the kernel launch shape the
+ * library would use for a process (blocks, threads per block). */
+int mc_launch_shape(const mc_integrand* itg, int prec, int64_t nevents, int* blocks, int* threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCINT_H */

@@ -1,0 +1,510 @@
+// C ABI of the library (declared in include/mcint.h): handles, argument
+// validation, launch shapes and the host-side VEGAS driver.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mcint.h"
+#include "launch.h"
+
+using mc::BlockPartial;
+using mc::KernelArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define MC_CUDA(call)                                                                      \
+  do {                                                                                     \
+    const cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) return fail(MC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int current_device(int* dev) {
+  const cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return fail(MC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  return MC_OK;
+}
+
+int process_ndim(const mc_integrand* itg) {
+  switch (itg->proc) {
+    case MC_EE_MUMU: return 2;
+    case MC_PP_TTBAR: return 4;
+    case MC_GG_TTBARG: return 14;
+    case MC_GAUSS: return itg->gauss_dim;
+  }
+  return -1;
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+  return n;
+}
+
+}  // namespace
+
+struct mc_pdf_s {
+  int device = 0, nx = 0, nq = 0, nflav = 0;
+  std::vector<int> pids;
+  std::vector<double> logq2;  // host copy of the Q^2 knots (log)
+  double* d_logx = nullptr;
+  double* d_logq2 = nullptr;
+  double* d_xf64 = nullptr;
+  float* d_xf32 = nullptr;
+  mc::PdfDev dev() const { return {nx, nq, nflav, d_logx, d_logq2, d_xf64, d_xf32}; }
+  int index(int pid) const {
+    for (int i = 0; i < nflav; ++i)
+      if (pids[i] == pid) return i;
+    return -1;
+  }
+};
+
+struct mc_vegas_s {
+  int device = 0, ndim = 0, nbins = 0, prec = 0;
+  uint64_t seed = 0;
+  uint32_t iteration = 0, gid = 0;
+  double* d_edges = nullptr;
+  float* d_edges32 = nullptr;
+  double* d_hist_w2 = nullptr;
+  unsigned int* d_hist_n = nullptr;
+  BlockPartial* d_partials = nullptr;
+  int max_partials = 0;
+  BlockPartial* d_total = nullptr;
+  BlockPartial* h_total = nullptr;  // pinned
+  cudaEvent_t k0 = nullptr, k1 = nullptr;  // around the last integrand launch
+  bool timed = false;
+};
+
+extern "C" {
+
+const char* mc_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ PDF
+int mc_pdf_load(const double* x, int nx, const double* q, int nq, const int32_t* pids, int nflav, const double* xf,
+                mc_pdf* out) {
+  if (!out) return fail(MC_EINVAL, "mc_pdf_load: out is NULL");
+  *out = nullptr;
+  if (!x || !q || !pids || !xf) return fail(MC_EINVAL, "mc_pdf_load: NULL array");
+  if (nx < 4 || nq < 4 || nflav < 1 || nflav > 64) return fail(MC_EINVAL, "mc_pdf_load: bad shape");
+  for (int i = 0; i < nx; ++i) {
+    if (!(x[i] > 0.0 && x[i] <= 1.0)) return fail(MC_EINVAL, "mc_pdf_load: x knot %d outside (0,1]", i);
+    if (i && !(x[i] > x[i - 1])) return fail(MC_EINVAL, "mc_pdf_load: x knots not increasing at %d", i);
+  }
+  for (int j = 0; j < nq; ++j) {
+    if (!(q[j] > 0.0 && std::isfinite(q[j]))) return fail(MC_EINVAL, "mc_pdf_load: bad Q knot %d", j);
+    if (j && !(q[j] > q[j - 1])) return fail(MC_EINVAL, "mc_pdf_load: Q knots not increasing at %d", j);
+  }
+  const size_t nval = size_t(nx) * nq * nflav;
+  for (size_t i = 0; i < nval; ++i)
+    if (!std::isfinite(xf[i])) return fail(MC_EINVAL, "mc_pdf_load: non-finite value at %zu", i);
+  auto* p = new mc_pdf_s;
+  int rc = current_device(&p->device);
+  if (rc) {
+    delete p;
+    return rc;
+  }
+  p->nx = nx;
+  p->nq = nq;
+  p->nflav = nflav;
+  p->pids.assign(pids, pids + nflav);
+  std::vector<double> lx(nx), lq(nq), v64(nval);
+  p->logq2.resize(nq);
+  std::vector<float> v32(nval);
+  for (int i = 0; i < nx; ++i) lx[i] = std::log(x[i]);
+  for (int j = 0; j < nq; ++j) lq[j] = p->logq2[j] = std::log(q[j] * q[j]);
+  // device layout [flavour][Q][x]
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < nq; ++j)
+      for (int f = 0; f < nflav; ++f) {
+        const double v = xf[(size_t(i) * nq + j) * nflav + f];
+        v64[(size_t(f) * nq + j) * nx + i] = v;
+        v32[(size_t(f) * nq + j) * nx + i] = float(v);
+      }
+  auto cleanup = [&](int code, const char* what, cudaError_t e) {
+    mc_pdf_free(p);
+    return fail(code, "mc_pdf_load: %s: %s", what, cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_logx, sizeof(double) * nx)) != cudaSuccess) return cleanup(MC_ENOMEM, "cudaMalloc", e);
+  if ((e = cudaMalloc(&p->d_logq2, sizeof(double) * nq)) != cudaSuccess) return cleanup(MC_ENOMEM, "cudaMalloc", e);
+  if ((e = cudaMalloc(&p->d_xf64, sizeof(double) * nval)) != cudaSuccess) return cleanup(MC_ENOMEM, "cudaMalloc", e);
+  if ((e = cudaMalloc(&p->d_xf32, sizeof(float) * nval)) != cudaSuccess) return cleanup(MC_ENOMEM, "cudaMalloc", e);
+  if ((e = cudaMemcpy(p->d_logx, lx.data(), sizeof(double) * nx, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cleanup(MC_ECUDA, "cudaMemcpy", e);
+  if ((e = cudaMemcpy(p->d_logq2, lq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cleanup(MC_ECUDA, "cudaMemcpy", e);
+  if ((e = cudaMemcpy(p->d_xf64, v64.data(), sizeof(double) * nval, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cleanup(MC_ECUDA, "cudaMemcpy", e);
+  if ((e = cudaMemcpy(p->d_xf32, v32.data(), sizeof(float) * nval, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cleanup(MC_ECUDA, "cudaMemcpy", e);
+  *out = p;
+  return MC_OK;
+}
+
+int mc_pdf_free(mc_pdf p) {
+  if (!p) return MC_OK;
+  cudaFree(p->d_logx);
+  cudaFree(p->d_logq2);
+  cudaFree(p->d_xf64);
+  cudaFree(p->d_xf32);
+  delete p;
+  return MC_OK;
+}
+
+int mc_pdf_xfxq2(mc_pdf p, int prec, int64_t n, const double* x, const double* q2, double* out, void* stream) {
+  if (!p) return fail(MC_EINVAL, "mc_pdf_xfxq2: pdf is NULL");
+  if (n < 0 || (n > 0 && (!x || !q2 || !out))) return fail(MC_EINVAL, "mc_pdf_xfxq2: bad arguments");
+  if (prec != MC_FP64 && prec != MC_FP32_KAHAN) return fail(MC_EINVAL, "mc_pdf_xfxq2: bad precision");
+  int dev;
+  if (int rc = current_device(&dev)) return rc;
+  if (dev != p->device) return fail(MC_EINVAL, "mc_pdf_xfxq2: pdf lives on device %d", p->device);
+  MC_CUDA(mc::launch_pdf_xfxq2(p->dev(), prec == MC_FP64, n, x, q2, out, (cudaStream_t)stream));
+  return MC_OK;
+}
+
+// ---------------------------------------------------------------- VEGAS
+int mc_vegas_free(mc_vegas v) {
+  if (!v) return MC_OK;
+  cudaFree(v->d_edges);
+  cudaFree(v->d_edges32);
+  cudaFree(v->d_hist_w2);
+  cudaFree(v->d_hist_n);
+  cudaFree(v->d_partials);
+  cudaFree(v->d_total);
+  if (v->h_total) cudaFreeHost(v->h_total);
+  if (v->k0) cudaEventDestroy(v->k0);
+  if (v->k1) cudaEventDestroy(v->k1);
+  delete v;
+  return MC_OK;
+}
+
+static int upload_grid(mc_vegas v, const double* edges) {
+  const size_t ne = size_t(v->ndim) * (v->nbins + 1);
+  std::vector<float> e32(ne);
+  for (size_t i = 0; i < ne; ++i) e32[i] = float(edges[i]);
+  MC_CUDA(cudaMemcpy(v->d_edges, edges, sizeof(double) * ne, cudaMemcpyHostToDevice));
+  MC_CUDA(cudaMemcpy(v->d_edges32, e32.data(), sizeof(float) * ne, cudaMemcpyHostToDevice));
+  return MC_OK;
+}
+
+int mc_vegas_init(int ndim, int nbins, uint64_t seed, int prec, mc_vegas* out) {
+  if (!out) return fail(MC_EINVAL, "mc_vegas_init: out is NULL");
+  *out = nullptr;
+  if (ndim < 1 || ndim > MC_MAX_DIM) return fail(MC_EINVAL, "mc_vegas_init: ndim %d outside 1..%d", ndim, MC_MAX_DIM);
+  if (nbins < 2 || nbins > MC_MAX_BINS)
+    return fail(MC_EINVAL, "mc_vegas_init: nbins %d outside 2..%d", nbins, MC_MAX_BINS);
+  if (prec != MC_FP64 && prec != MC_FP32_KAHAN) return fail(MC_EINVAL, "mc_vegas_init: bad precision %d", prec);
+  auto* v = new mc_vegas_s;
+  if (int rc = current_device(&v->device)) {
+    delete v;
+    return rc;
+  }
+  v->ndim = ndim;
+  v->nbins = nbins;
+  v->prec = prec;
+  v->seed = seed;
+  v->max_partials = num_sms() * 32;
+  const size_t ne = size_t(ndim) * (nbins + 1), nh = size_t(ndim) * nbins;
+  cudaError_t e = cudaSuccess;
+  if ((e = cudaMalloc(&v->d_edges, sizeof(double) * ne)) != cudaSuccess ||
+      (e = cudaMalloc(&v->d_edges32, sizeof(float) * ne)) != cudaSuccess ||
+      (e = cudaMalloc(&v->d_hist_w2, sizeof(double) * nh)) != cudaSuccess ||
+      (e = cudaMalloc(&v->d_hist_n, sizeof(unsigned int) * nh)) != cudaSuccess ||
+      (e = cudaMalloc(&v->d_partials, sizeof(BlockPartial) * v->max_partials)) != cudaSuccess ||
+      (e = cudaMalloc(&v->d_total, sizeof(BlockPartial))) != cudaSuccess ||
+      (e = cudaMallocHost(&v->h_total, sizeof(BlockPartial))) != cudaSuccess ||
+      (e = cudaEventCreate(&v->k0)) != cudaSuccess || (e = cudaEventCreate(&v->k1)) != cudaSuccess) {
+    mc_vegas_free(v);
+    return fail(MC_ENOMEM, "mc_vegas_init: allocation failed: %s", cudaGetErrorString(e));
+  }
+  std::vector<double> edges(ne);
+  for (int d = 0; d < ndim; ++d)
+    for (int b = 0; b <= nbins; ++b) edges[size_t(d) * (nbins + 1) + b] = b == nbins ? 1.0 : double(b) / nbins;
+  int rc = upload_grid(v, edges.data());
+  if (!rc && (e = cudaMemset(v->d_hist_w2, 0, sizeof(double) * nh)) != cudaSuccess)
+    rc = fail(MC_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  if (!rc && (e = cudaMemset(v->d_hist_n, 0, sizeof(unsigned int) * nh)) != cudaSuccess)
+    rc = fail(MC_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  if (rc) {
+    mc_vegas_free(v);
+    return rc;
+  }
+  *out = v;
+  return MC_OK;
+}
+
+int mc_vegas_set_grid(mc_vegas v, const double* edges) {
+  if (!v || !edges) return fail(MC_EINVAL, "mc_vegas_set_grid: NULL argument");
+  for (int d = 0; d < v->ndim; ++d) {
+    const double* e = edges + size_t(d) * (v->nbins + 1);
+    if (e[0] != 0.0 || e[v->nbins] != 1.0) return fail(MC_EINVAL, "mc_vegas_set_grid: dim %d not on [0,1]", d);
+    for (int b = 1; b <= v->nbins; ++b)
+      if (!(e[b] > e[b - 1])) return fail(MC_EINVAL, "mc_vegas_set_grid: dim %d edges not increasing", d);
+  }
+  MC_CUDA(cudaDeviceSynchronize());
+  return upload_grid(v, edges);
+}
+
+int mc_vegas_get_grid(mc_vegas v, double* edges) {
+  if (!v || !edges) return fail(MC_EINVAL, "mc_vegas_get_grid: NULL argument");
+  MC_CUDA(cudaDeviceSynchronize());
+  MC_CUDA(cudaMemcpy(edges, v->d_edges, sizeof(double) * v->ndim * (v->nbins + 1), cudaMemcpyDeviceToHost));
+  return MC_OK;
+}
+
+int mc_vegas_get_hist(mc_vegas v, double* w2, uint32_t* counts) {
+  if (!v) return fail(MC_EINVAL, "mc_vegas_get_hist: NULL handle");
+  MC_CUDA(cudaDeviceSynchronize());
+  const size_t nh = size_t(v->ndim) * v->nbins;
+  if (w2) MC_CUDA(cudaMemcpy(w2, v->d_hist_w2, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+  if (counts) MC_CUDA(cudaMemcpy(counts, v->d_hist_n, sizeof(uint32_t) * nh, cudaMemcpyDeviceToHost));
+  return MC_OK;
+}
+
+int mc_vegas_set_iteration(mc_vegas v, uint32_t it) {
+  if (!v) return fail(MC_EINVAL, "mc_vegas_set_iteration: NULL handle");
+  v->iteration = it;
+  return MC_OK;
+}
+int mc_vegas_get_iteration(mc_vegas v, uint32_t* it) {
+  if (!v || !it) return fail(MC_EINVAL, "mc_vegas_get_iteration: NULL argument");
+  *it = v->iteration;
+  return MC_OK;
+}
+int mc_vegas_set_gid(mc_vegas v, uint32_t gid) {
+  if (!v || gid > 255) return fail(MC_EINVAL, "mc_vegas_set_gid: bad argument");
+  v->gid = gid;
+  return MC_OK;
+}
+
+// Validates an integrand against a grid and fills the kernel arguments.
+static int prepare(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
+  if (!v || !itg) return fail(MC_EINVAL, "NULL handle or integrand");
+  int dev;
+  if (int rc = current_device(&dev)) return rc;
+  if (dev != v->device) return fail(MC_EINVAL, "grid lives on device %d, current device is %d", v->device, dev);
+  if (itg->proc < MC_EE_MUMU || itg->proc > MC_GAUSS) return fail(MC_EINVAL, "unknown process %d", itg->proc);
+  const int nd = process_ndim(itg);
+  if (nd != v->ndim) return fail(MC_EINVAL, "process needs %d dimensions, grid has %d", nd, v->ndim);
+  const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG;
+  if (!(itg->sqrt_s > 0.0) && itg->proc != MC_GAUSS) return fail(MC_EINVAL, "sqrt_s must be positive");
+  if (itg->proc == MC_GAUSS && !(itg->gauss_sigma > 0.0)) return fail(MC_EINVAL, "gauss_sigma must be positive");
+  std::memset(a, 0, sizeof(*a));
+  a->prm = {itg->proc, itg->gauss_dim, itg->sqrt_s, itg->m_top, itg->alpha, itg->alpha_s, itg->mz, itg->gz,
+            itg->sw2, itg->mu_f, itg->ptcut_g, itg->etacut_g, itg->gauss_sigma, itg->gev2pb};
+  a->ndim = v->ndim;
+  a->nbins = v->nbins;
+  a->edges64 = v->d_edges;
+  a->edges32 = v->d_edges32;
+  if (hadronic) {
+    if (!pdf) return fail(MC_EINVAL, "process %d needs a PDF", itg->proc);
+    if (pdf->device != dev) return fail(MC_EINVAL, "pdf lives on device %d", pdf->device);
+    const double q = itg->mu_f;
+    // mu_F must lie inside the Q range of the grid (no extrapolation on the hot path)
+    const double lq = std::log(q * q);
+    if (!(lq >= pdf->logq2.front() && lq <= pdf->logq2.back())) return fail(MC_EINVAL, "mu_f outside the PDF grid");
+    a->pdf = pdf->dev();
+    a->logq2_f = lq;
+    const int g = pdf->index(21);
+    if (g < 0) return fail(MC_EINVAL, "PDF has no gluon (pid 21)");
+    a->fl[0] = g;
+    if (itg->proc == MC_PP_TTBAR)
+      for (int qf = 1; qf <= 5; ++qf) {
+        a->fl[qf] = pdf->index(qf);
+        a->fl[qf + 5] = pdf->index(-qf);
+        if (a->fl[qf] < 0 || a->fl[qf + 5] < 0) return fail(MC_EINVAL, "PDF lacks quark flavour %d", qf);
+      }
+  }
+  // three-particle RAMBO coefficient (2 pi)^(4-3n) (pi/2)^(n-1) / (Gamma(n) Gamma(n-1)), n = 3
+  a->w0_coef3 = std::pow(2.0 * M_PI, -5.0) * std::pow(M_PI / 2.0, 2.0) / (std::tgamma(3.0) * std::tgamma(2.0));
+  a->e2eta = std::exp(2.0 * itg->etacut_g);
+  a->seed = v->seed;
+  a->iteration = v->iteration;
+  a->gid = v->gid;
+  a->hist_w2 = v->d_hist_w2;
+  a->hist_n = v->d_hist_n;
+  a->partials = v->d_partials;
+  return MC_OK;
+}
+
+static int launch_grid(int proc, bool fp64, int64_t n, size_t smem, int max_blocks) {
+  const int per_sm = mc::integrand_max_blocks_per_sm(proc, fp64, smem);
+  long long grid = (long long)num_sms() * per_sm;
+  const long long need = (n + mc::kBlock - 1) / mc::kBlock;
+  if (grid > need) grid = need;
+  if (grid > max_blocks) grid = max_blocks;
+  if (grid < 1) grid = 1;
+  return int(grid);
+}
+
+int mc_launch_shape(const mc_integrand* itg, int prec, int64_t nevents, int* blocks, int* threads) {
+  if (!itg || !blocks || !threads) return fail(MC_EINVAL, "mc_launch_shape: NULL argument");
+  const int nd = process_ndim(itg);
+  if (nd < 1) return fail(MC_EINVAL, "mc_launch_shape: bad process");
+  const size_t smem = mc::integrand_smem(itg->proc, prec == MC_FP64, nd, 50, 100);
+  *blocks = launch_grid(itg->proc, prec == MC_FP64, nevents, smem, num_sms() * 32);
+  *threads = mc::kBlock;
+  return MC_OK;
+}
+
+int mc_vegas_iterate(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, void* stream,
+                     mc_iter_result* out) {
+  if (!out) return fail(MC_EINVAL, "mc_vegas_iterate: out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  if (nevents < 0) return fail(MC_EINVAL, "mc_vegas_iterate: negative event count");
+  KernelArgs a;
+  if (int rc = prepare(v, itg, pdf, &a)) return rc;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const bool fp64 = v->prec == MC_FP64;
+  out->n = nevents;
+  if (nevents > 0) {
+    const size_t smem = mc::integrand_smem(itg->proc, fp64, v->ndim, v->nbins, pdf ? pdf->nx : 0);
+    const int grid = launch_grid(itg->proc, fp64, nevents, smem, v->max_partials);
+    a.first = 0;
+    a.n = nevents;
+    MC_CUDA(cudaEventRecord(v->k0, st));
+    MC_CUDA(mc::launch_integrand(itg->proc, fp64, a, grid, smem, st));
+    MC_CUDA(cudaEventRecord(v->k1, st));
+    v->timed = true;
+    MC_CUDA(mc::launch_finalize(v->d_partials, grid, v->d_total, st));
+    MC_CUDA(cudaMemcpyAsync(v->h_total, v->d_total, sizeof(BlockPartial), cudaMemcpyDeviceToHost, st));
+    MC_CUDA(cudaStreamSynchronize(st));
+    const BlockPartial& t = *v->h_total;
+    out->sum = t.sum_hi + t.sum_lo;
+    out->sum2 = t.sum2_hi + t.sum2_lo;
+    out->wmax = t.wmax;
+    out->n_nonzero = t.n_nonzero;
+    out->n_bad = t.n_bad + t.n_noconv;
+    out->status = t.n_bad ? MC_ENAN : (t.n_noconv ? MC_ENOCONV : MC_OK);
+  }
+  ++v->iteration;
+  return MC_OK;
+}
+
+int mc_vegas_kernel_ms(mc_vegas v, float* ms) {
+  if (!v || !ms) return fail(MC_EINVAL, "mc_vegas_kernel_ms: NULL argument");
+  *ms = 0.0f;
+  if (!v->timed) return MC_OK;
+  MC_CUDA(cudaEventSynchronize(v->k1));
+  MC_CUDA(cudaEventElapsedTime(ms, v->k0, v->k1));
+  return MC_OK;
+}
+
+int mc_vegas_refine(mc_vegas v, double alpha, void* stream) {
+  if (!v) return fail(MC_EINVAL, "mc_vegas_refine: NULL handle");
+  if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(MC_EINVAL, "mc_vegas_refine: bad alpha");
+  MC_CUDA(mc::launch_refine(v->d_edges, v->d_edges32, v->d_hist_w2, v->d_hist_n, v->ndim, v->nbins, alpha,
+                            (cudaStream_t)stream));
+  return MC_OK;
+}
+
+int mc_debug_events(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t first, int64_t k, double* out,
+                    void* stream) {
+  if (k < 0 || first < 0 || (k > 0 && !out)) return fail(MC_EINVAL, "mc_debug_events: bad arguments");
+  KernelArgs a;
+  if (int rc = prepare(v, itg, pdf, &a)) return rc;
+  if (k == 0) return MC_OK;
+  const bool fp64 = v->prec == MC_FP64;
+  const size_t smem = mc::integrand_smem(itg->proc, fp64, v->ndim, v->nbins, pdf ? pdf->nx : 0);
+  a.first = uint64_t(first);
+  a.n = k;
+  a.record = out;
+  const long long grid = (k + mc::kBlock - 1) / mc::kBlock;
+  MC_CUDA(mc::launch_integrand_record(itg->proc, fp64, a, int(grid), smem, (cudaStream_t)stream));
+  return MC_OK;
+}
+
+// Inverse-variance combination and chi^2/dof (thesis eq. vegas-check); an
+// iteration with zero variance is left out unless every iteration has zero
+// variance.
+static void combine(const std::vector<double>& e, const std::vector<double>& s2, mc_result* r) {
+  double inv = 0.0, acc = 0.0;
+  int used = 0;
+  for (size_t i = 0; i < e.size(); ++i)
+    if (s2[i] > 0.0) {
+      inv += 1.0 / s2[i];
+      acc += e[i] / s2[i];
+      ++used;
+    }
+  if (!used) {
+    double m = 0.0;
+    for (double x : e) m += x;
+    r->mean = e.empty() ? 0.0 : m / double(e.size());
+    r->sigma = 0.0;
+    r->chi2_dof = 0.0;
+    return;
+  }
+  r->mean = acc / inv;
+  r->sigma = std::sqrt(1.0 / inv);
+  double chi = 0.0;
+  for (size_t i = 0; i < e.size(); ++i)
+    if (s2[i] > 0.0) chi += (e[i] - r->mean) * (e[i] - r->mean) / s2[i];
+  r->chi2_dof = used > 1 ? chi / (used - 1) : 0.0;
+}
+
+int mc_integrate(const mc_integrand* itg, mc_pdf pdf, int niter, int64_t nevents, int nbins, uint64_t seed,
+                 uint32_t gid, int prec, double alpha, double target, void* stream, mc_result* out,
+                 mc_iter_result* per_iter) {
+  if (!out || !itg) return fail(MC_EINVAL, "mc_integrate: NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  if (niter < 1 || nevents < 2) return fail(MC_EINVAL, "mc_integrate: need niter >= 1 and nevents >= 2");
+  const int nd = process_ndim(itg);
+  if (nd < 1 || nd > MC_MAX_DIM) return fail(MC_EINVAL, "mc_integrate: bad process dimension");
+  mc_vegas v = nullptr;
+  if (int rc = mc_vegas_init(nd, nbins, seed, prec, &v)) return rc;
+  if (int rc = mc_vegas_set_gid(v, gid)) {
+    mc_vegas_free(v);
+    return rc;
+  }
+  const cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<double> es, s2s;
+  int rc = MC_OK;
+  float total_ms = 0.0f;
+  for (int it = 0; it < niter; ++it) {
+    mc_iter_result r;
+    cudaEventRecord(e0, st);
+    rc = mc_vegas_iterate(v, itg, pdf, nevents, stream, &r);
+    if (rc) break;
+    rc = mc_vegas_refine(v, alpha, stream);
+    if (rc) break;
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    total_ms += ms;
+    if (per_iter) per_iter[it] = r;
+    if (r.status && !out->status) out->status = r.status;
+    const double n = double(r.n);
+    const double mean = r.sum / n;
+    es.push_back(mean);
+    s2s.push_back((r.sum2 / n - mean * mean) / (n - 1.0));
+    combine(es, s2s, out);
+    out->n_iter = it + 1;
+    if (target > 0.0 && out->mean != 0.0 && out->sigma / std::fabs(out->mean) <= target) break;
+  }
+  out->gpu_ms = total_ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  mc_vegas_free(v);
+  return rc;
+}
+
+}  // extern "C"

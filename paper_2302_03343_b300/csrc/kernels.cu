@@ -1,0 +1,400 @@
+// CUDA kernels of the hot path and their launchers.
+//
+//  * integrand_kernel: one fused pass over a range of events: Philox
+//    uniforms -> VEGAS map -> phase space -> PDFs -> |M|^2 -> weight ->
+//    Kahan FP64 sums and shared-memory histograms -> per-block partials and
+//    global histogram atomics.  Nothing per event touches global memory.
+//  * finalize_kernel: fixed-order reduction of the per-block partials
+//    (deterministic sums for a given launch shape).
+//  * refine_kernel: VEGAS rebinning, one thread per dimension, FP64.
+//  * pdf_xfxq2_kernel: batched log-bicubic PDF interpolation (all flavours).
+#include <cstdio>
+#include <type_traits>
+
+#include "../../include/mcint.h"
+#include "integrand.cuh"
+#include "launch.h"
+
+namespace mc {
+
+// value = hi + lo pairs: compensated addition of two such pairs
+MC_D void pair_add(double& hi, double& lo, double h2, double l2) {
+  const double s = hi + h2;
+  const double bp = s - hi;
+  const double e = (hi - (s - bp)) + (h2 - bp);
+  hi = s;
+  lo = lo + l2 + e;
+}
+
+template <class R> MC_D const R* edges_of(const KernelArgs& a);
+template <> MC_D const double* edges_of<double>(const KernelArgs& a) { return a.edges64; }
+template <> MC_D const float* edges_of<float>(const KernelArgs& a) { return a.edges32; }
+
+template <int PROC, bool FP64, bool RECORD>
+__global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
+  using R = typename std::conditional<FP64, double, float>::type;
+  constexpr int MAXD = ProcTraits<PROC>::MAXD;
+  constexpr int NFL = ProcTraits<PROC>::NFL;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ndim = a.ndim, nb = a.nbins;
+  const int nedge = ndim * (nb + 1), nhist = ndim * nb;
+  double* sh_w2 = reinterpret_cast<double*>(smem);
+  unsigned int* sh_n = reinterpret_cast<unsigned int*>(sh_w2 + nhist);
+  R* sh_edges = reinterpret_cast<R*>(smem + ((size_t(nhist) * 12 + 15) / 16) * 16);
+  R* sh_pdf = sh_edges + nedge;
+
+  const R* g_edges = edges_of<R>(a);
+  for (int i = threadIdx.x; i < nedge; i += blockDim.x) sh_edges[i] = g_edges[i];
+  if (!RECORD)
+    for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
+      sh_w2[i] = 0.0;
+      sh_n[i] = 0u;
+    }
+  SmPdf<R> pdf;
+  if constexpr (NFL > 0) {
+    const int nx = a.pdf.nx;
+    R* t = sh_pdf;
+    R* f = t + nx;
+    R* d = f + NFL * nx;
+    build_pdf_tables<R>(a.pdf, a.logq2_f, a.fl, NFL, t, f, d);  // ends with __syncthreads
+#pragma unroll
+    for (int k = 0; k < NFL; ++k) pdf.tab[k] = {t, f + k * nx, d + k * nx, nx};
+  } else {
+    __syncthreads();
+  }
+
+  double s_hi = 0.0, s_c = 0.0, q_hi = 0.0, q_c = 0.0, wmax = 0.0;
+  long long nnz = 0, nbad = 0, nnoconv = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const uint64_t ev = a.first + uint64_t(i);
+    uint64_t k[MAXD];
+    event_uniforms<MAXD, FP64>(a.seed, a.iteration, a.gid, ev, ndim, k);
+    R x[MAXD];
+    int bin[MAXD];
+    R jac = R(1);
+#pragma unroll
+    for (int dd = 0; dd < MAXD; ++dd) {
+      if (dd < ndim) {
+        R jd;
+        x[dd] = vegas_map_1d<R, FP64>(sh_edges + dd * (nb + 1), nb, k[dd], &bin[dd], &jd);
+        jac *= jd;
+      }
+    }
+    double* rec = RECORD ? a.record + size_t(i) * MC_REC_STRIDE : nullptr;
+    const EventOut o = integrand<PROC, R>(a, pdf, x, rec);
+    double w = o.f * double(jac);
+    int status = o.status;
+    if (!isfinite(w)) {
+      status = MC_ENAN;
+      w = 0.0;
+    }
+    if (RECORD) {
+#pragma unroll
+      for (int dd = 0; dd < MAXD; ++dd) {
+        if (dd < ndim) {
+          rec[MC_REC_K + dd] = double(k[dd]);
+          rec[MC_REC_X + dd] = double(x[dd]);
+          rec[MC_REC_BIN + dd] = double(bin[dd]);
+        }
+      }
+      rec[MC_REC_JAC] = double(jac);
+      rec[MC_REC_F] = o.f;
+      rec[MC_REC_W] = w;
+      rec[MC_REC_PASS] = double(o.pass);
+      rec[MC_REC_STATUS] = double(status);
+      continue;
+    }
+    if (status != 0) {
+      if (status == -5)
+        ++nnoconv;
+      else
+        ++nbad;
+    }
+    // Kahan-compensated FP64 sums of w and w^2
+    {
+      const double y = w - s_c;
+      const double t = s_hi + y;
+      s_c = (t - s_hi) - y;
+      s_hi = t;
+      const double w2 = w * w;
+      const double y2 = w2 - q_c;
+      const double t2 = q_hi + y2;
+      q_c = (t2 - q_hi) - y2;
+      q_hi = t2;
+      if (w != 0.0) ++nnz;
+      wmax = fmax(wmax, w);
+#pragma unroll
+      for (int dd = 0; dd < MAXD; ++dd) {
+        if (dd < ndim) {
+          atomicAdd(&sh_w2[dd * nb + bin[dd]], w2);
+          atomicAdd(&sh_n[dd * nb + bin[dd]], 1u);
+        }
+      }
+    }
+  }
+  if (RECORD) return;
+
+  // block reduction: warp shuffles, then one warp over the warp results
+  double lo = -s_c, lo2 = -q_c;  // Kahan compensation -> (hi, lo) pairs
+  for (int off = 16; off > 0; off >>= 1) {
+    const double h2 = __shfl_xor_sync(0xffffffffu, s_hi, off), l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+    pair_add(s_hi, lo, h2, l2);
+    const double g2 = __shfl_xor_sync(0xffffffffu, q_hi, off), m2 = __shfl_xor_sync(0xffffffffu, lo2, off);
+    pair_add(q_hi, lo2, g2, m2);
+    wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, off));
+    nnz += __shfl_xor_sync(0xffffffffu, nnz, off);
+    nbad += __shfl_xor_sync(0xffffffffu, nbad, off);
+    nnoconv += __shfl_xor_sync(0xffffffffu, nnoconv, off);
+  }
+  __shared__ BlockPartial warp_part[kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_part[wid] = {s_hi, lo, q_hi, lo2, wmax, nnz, nbad, nnoconv};
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    BlockPartial b = warp_part[0];
+    for (int w = 1; w < int(blockDim.x / 32); ++w) {
+      const BlockPartial& o = warp_part[w];
+      pair_add(b.sum_hi, b.sum_lo, o.sum_hi, o.sum_lo);
+      pair_add(b.sum2_hi, b.sum2_lo, o.sum2_hi, o.sum2_lo);
+      b.wmax = fmax(b.wmax, o.wmax);
+      b.n_nonzero += o.n_nonzero;
+      b.n_bad += o.n_bad;
+      b.n_noconv += o.n_noconv;
+    }
+    a.partials[blockIdx.x] = b;
+  }
+  for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
+    if (sh_n[i]) {
+      atomicAdd(&a.hist_n[i], sh_n[i]);
+      atomicAdd(&a.hist_w2[i], sh_w2[i]);
+    }
+  }
+}
+
+// Fixed-order reduction of nblocks partials into out (one block of 256).
+__global__ void finalize_kernel(const BlockPartial* parts, int nblocks, BlockPartial* out) {
+  __shared__ BlockPartial sh[256];
+  BlockPartial b = {0.0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0};
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    const BlockPartial& o = parts[i];
+    pair_add(b.sum_hi, b.sum_lo, o.sum_hi, o.sum_lo);
+    pair_add(b.sum2_hi, b.sum2_lo, o.sum2_hi, o.sum2_lo);
+    b.wmax = fmax(b.wmax, o.wmax);
+    b.n_nonzero += o.n_nonzero;
+    b.n_bad += o.n_bad;
+    b.n_noconv += o.n_noconv;
+  }
+  sh[threadIdx.x] = b;
+  __syncthreads();
+  for (int width = blockDim.x / 2; width > 0; width >>= 1) {
+    if (int(threadIdx.x) < width) {
+      BlockPartial& m = sh[threadIdx.x];
+      const BlockPartial& o = sh[threadIdx.x + width];
+      pair_add(m.sum_hi, m.sum_lo, o.sum_hi, o.sum_lo);
+      pair_add(m.sum2_hi, m.sum2_lo, o.sum2_hi, o.sum2_lo);
+      m.wmax = fmax(m.wmax, o.wmax);
+      m.n_nonzero += o.n_nonzero;
+      m.n_bad += o.n_bad;
+      m.n_noconv += o.n_noconv;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// VEGAS refinement (Lepage 1978): per dimension, smooth the histogram of
+// w^2 with nearest neighbours, normalise, damp m_b = ((r_b - 1)/ln r_b)^alpha,
+// and place the new edges at equal cumulative importance by linear
+// interpolation inside the old bins; then clear the histograms.  One thread
+// per dimension; dimensions with an empty histogram keep their grid.
+__global__ void refine_kernel(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim,
+                              int nbins, double alpha) {
+  const int d = threadIdx.x;
+  if (d >= ndim) return;
+  double* e = edges + size_t(d) * (nbins + 1);
+  double* h = hist_w2 + size_t(d) * nbins;
+  double imp[MC_MAX_BINS];
+  double total = 0.0;
+  for (int b = 0; b < nbins; ++b) {
+    double sm;
+    if (b == 0)
+      sm = (h[0] + h[1]) / 2.0;
+    else if (b == nbins - 1)
+      sm = (h[nbins - 2] + h[nbins - 1]) / 2.0;
+    else
+      sm = (h[b - 1] + h[b] + h[b + 1]) / 3.0;
+    imp[b] = sm;
+    total += sm;
+  }
+  if (total > 0.0) {
+    double cum = 0.0;
+    for (int b = 0; b < nbins; ++b) {
+      const double r = imp[b] / total;
+      double m;
+      if (r <= 0.0)
+        m = 0.0;
+      else if (r == 1.0)
+        m = 1.0;
+      else
+        m = pow((r - 1.0) / log(r), alpha);
+      imp[b] = m;
+      cum += m;
+    }
+    const double per_bin = cum / nbins;
+    double old[MC_MAX_BINS + 1];
+    for (int b = 0; b <= nbins; ++b) old[b] = e[b];
+    // walk the old bins once, emitting the new edges in order
+    int b = 0;
+    double c_lo = 0.0;  // cumulative importance before old bin b
+    for (int k = 1; k < nbins; ++k) {
+      const double target = k * per_bin;
+      while (b + 1 < nbins && c_lo + imp[b] < target) {
+        c_lo += imp[b];
+        ++b;
+      }
+      e[k] = old[b] + (target - c_lo) / imp[b] * (old[b + 1] - old[b]);
+    }
+  }
+  for (int b = 0; b <= nbins; ++b) edges32[size_t(d) * (nbins + 1) + b] = float(e[b]);
+  for (int b = 0; b < nbins; ++b) {
+    h[b] = 0.0;
+    hist_n[size_t(d) * nbins + b] = 0u;
+  }
+}
+
+// Batched xf(x, Q^2) for all flavours: one thread per (point, flavour).
+template <class R>
+__global__ void pdf_xfxq2_kernel(PdfDev pdf, long long n, const double* x, const double* q2, double* out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * pdf.nflav) return;
+  const long long i = idx / pdf.nflav;
+  const int fl = int(idx % pdf.nflav);
+  const double xv = x[i], qv = q2[i];
+  const int nx = pdf.nx, nq = pdf.nq;
+  const double lx = log(xv), lq = log(qv);
+  if (!(lx >= pdf.logx[0] && lx <= pdf.logx[nx - 1] && lq >= pdf.logq2[0] && lq <= pdf.logq2[nq - 1])) {
+    out[idx] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
+  int j0;
+  double w[4];
+  q_weights(pdf.logq2, nq, lq, &j0, w);
+  const int ix = knot_cell(pdf.logx, nx, lx);
+  const R h = R(pdf.logx[ix + 1] - pdf.logx[ix]);
+  const R tau = R((lx - pdf.logx[ix]) / double(h));
+  // slope stencil in x: knots ix-1 .. ix+2
+  R tk[4];
+  for (int t = 0; t < 4; ++t) {
+    const int ii = min(max(ix - 1 + t, 0), nx - 1);
+    tk[t] = R(pdf.logx[ii]);
+  }
+  double acc = 0.0;
+  for (int t = 0; t < 4; ++t) {
+    const int j = j0 + t;
+    if (j < 0 || j >= nq || w[t] == 0.0) continue;
+    const size_t base = (size_t(fl) * nq + j) * nx;
+    R f[4];
+    for (int u = 0; u < 4; ++u) {
+      const int ii = min(max(ix - 1 + u, 0), nx - 1);
+      f[u] = sizeof(R) == 8 ? R(pdf.xf64[base + ii]) : R(pdf.xf32[base + ii]);
+    }
+    R d0, d1;
+    if (ix == 0)
+      d0 = (f[2] - f[1]) / (tk[2] - tk[1]);
+    else
+      d0 = R(0.5) * ((f[2] - f[1]) / (tk[2] - tk[1]) + (f[1] - f[0]) / (tk[1] - tk[0]));
+    if (ix + 1 == nx - 1)
+      d1 = (f[2] - f[1]) / (tk[2] - tk[1]);
+    else
+      d1 = R(0.5) * ((f[3] - f[2]) / (tk[3] - tk[2]) + (f[2] - f[1]) / (tk[2] - tk[1]));
+    acc += w[t] * double(hermite<R>(tau, h, f[1], f[2], d0, d1));
+  }
+  out[idx] = acc;
+}
+
+// ------------------------------------------------------------------ launchers
+template <int PROC, bool FP64, bool RECORD>
+static cudaError_t launch_one(const KernelArgs& a, int grid, size_t smem, cudaStream_t st) {
+  auto k = integrand_kernel<PROC, FP64, RECORD>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, kBlock, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool RECORD>
+static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem, cudaStream_t st) {
+  switch (proc) {
+    case P_EE_MUMU:
+      return fp64 ? launch_one<P_EE_MUMU, true, RECORD>(a, grid, smem, st)
+                  : launch_one<P_EE_MUMU, false, RECORD>(a, grid, smem, st);
+    case P_PP_TTBAR:
+      return fp64 ? launch_one<P_PP_TTBAR, true, RECORD>(a, grid, smem, st)
+                  : launch_one<P_PP_TTBAR, false, RECORD>(a, grid, smem, st);
+    case P_GG_TTBARG:
+      return fp64 ? launch_one<P_GG_TTBARG, true, RECORD>(a, grid, smem, st)
+                  : launch_one<P_GG_TTBARG, false, RECORD>(a, grid, smem, st);
+    case P_GAUSS:
+      return fp64 ? launch_one<P_GAUSS, true, RECORD>(a, grid, smem, st)
+                  : launch_one<P_GAUSS, false, RECORD>(a, grid, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t integrand_smem(int proc, bool fp64, int ndim, int nbins, int nx) {
+  const size_t r = fp64 ? 8 : 4;
+  const int nfl = proc == P_PP_TTBAR ? 11 : (proc == P_GG_TTBARG ? 1 : 0);
+  const size_t hist = ((size_t(ndim) * nbins * 12 + 15) / 16) * 16;
+  return hist + r * (size_t(ndim) * (nbins + 1) + (nfl > 0 ? size_t(nx) * (1 + 2 * nfl) : 0));
+}
+
+int integrand_max_blocks_per_sm(int proc, bool fp64, size_t smem) {
+  int nb = 0;
+  cudaError_t e = cudaSuccess;
+#define MC_OCC(P)                                                                                        \
+  e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, integrand_kernel<P, true, false>, kBlock, smem) \
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, integrand_kernel<P, false, false>, kBlock, smem)
+  switch (proc) {
+    case P_EE_MUMU: MC_OCC(P_EE_MUMU); break;
+    case P_PP_TTBAR: MC_OCC(P_PP_TTBAR); break;
+    case P_GG_TTBARG: MC_OCC(P_GG_TTBARG); break;
+    default: MC_OCC(P_GAUSS); break;
+  }
+#undef MC_OCC
+  if (e != cudaSuccess || nb < 1) nb = 1;
+  return nb;
+}
+
+cudaError_t launch_integrand(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem, cudaStream_t st) {
+  return dispatch<false>(proc, fp64, a, grid, smem, st);
+}
+cudaError_t launch_integrand_record(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem,
+                                    cudaStream_t st) {
+  return dispatch<true>(proc, fp64, a, grid, smem, st);
+}
+cudaError_t launch_finalize(const BlockPartial* parts, int nblocks, BlockPartial* out, cudaStream_t st) {
+  finalize_kernel<<<1, 256, 0, st>>>(parts, nblocks, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_refine(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim, int nbins,
+                          double alpha, cudaStream_t st) {
+  refine_kernel<<<1, 32, 0, st>>>(edges, edges32, hist_w2, hist_n, ndim, nbins, alpha);
+  return cudaGetLastError();
+}
+cudaError_t launch_pdf_xfxq2(const PdfDev& pdf, bool fp64, long long n, const double* x, const double* q2,
+                             double* out, cudaStream_t st) {
+  const long long total = n * pdf.nflav;
+  if (total == 0) return cudaSuccess;
+  const int block = 256;
+  const long long grid = (total + block - 1) / block;
+  if (fp64)
+    pdf_xfxq2_kernel<double><<<unsigned(grid), block, 0, st>>>(pdf, n, x, q2, out);
+  else
+    pdf_xfxq2_kernel<float><<<unsigned(grid), block, 0, st>>>(pdf, n, x, q2, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mc

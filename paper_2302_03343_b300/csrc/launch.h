@@ -1,0 +1,25 @@
+// Internal: launchers of the CUDA kernels (kernels.cu) used by the C ABI
+// (api.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "integrand.cuh"
+
+namespace mc {
+
+constexpr int kBlock = 128;  // threads per block of the fused integrand kernel
+
+size_t integrand_smem(int proc, bool fp64, int ndim, int nbins, int nx);
+int integrand_max_blocks_per_sm(int proc, bool fp64, size_t smem);
+cudaError_t launch_integrand(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_integrand_record(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem,
+                                    cudaStream_t st);
+cudaError_t launch_finalize(const BlockPartial* parts, int nblocks, BlockPartial* out, cudaStream_t st);
+cudaError_t launch_refine(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim, int nbins,
+                          double alpha, cudaStream_t st);
+cudaError_t launch_pdf_xfxq2(const PdfDev& pdf, bool fp64, long long n, const double* x, const double* q2,
+                             double* out, cudaStream_t st);
+
+}  // namespace mc

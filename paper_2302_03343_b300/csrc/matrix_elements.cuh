@@ -1,0 +1,274 @@
+// Tree-level |M|^2 from helicity amplitudes (thesis Sec. "The MadFlow event
+// generator": helicity amplitudes joined by vertex/propagator routines and
+// gathered into colour-ordered, gauge-invariant groups; fig. pp_ttx for the
+// pp -> tt diagrams).  All functions return the spin- and colour-averaged
+// |M|^2 for momenta in the partonic centre-of-mass frame.
+#pragma once
+#include "helas.cuh"
+
+namespace mc {
+
+// ------------------------------------------------------------- e+e- -> mu+mu-
+// s-channel photon and Z (fixed-width Breit-Wigner) between massless lepton
+// currents J^mu = g_L x_L^dag sigmabar^mu y_L + g_R x_R^dag sigma^mu y_R.
+template <class R>
+MC_D void lepton_current(const cx<R>* xl, const cx<R>* xr, const cx<R>* yl, const cx<R>* yr, R gl, R gr,
+                         cx<R>* j) {
+  // x^dag sigma^mu y for mu = 0..3 (sigmabar^mu = (1, -sigma^k))
+  auto sandwich = [](const cx<R>* x, const cx<R>* y, cx<R>* s) {
+    const cx<R> a = mul_conj(y[0], x[0]), b = mul_conj(y[1], x[1]);  // x0* y0, x1* y1
+    const cx<R> c = mul_conj(y[1], x[0]), d = mul_conj(y[0], x[1]);  // x0* y1, x1* y0
+    s[0] = a + b;
+    s[1] = c + d;
+    s[2] = mkc(c.im - d.im, d.re - c.re);  // -i x0* y1 + i x1* y0
+    s[3] = a - b;
+  };
+  cx<R> sl[4], sr[4];
+  sandwich(xl, yl, sl);
+  sandwich(xr, yr, sr);
+  j[0] = sl[0] * gl + sr[0] * gr;
+  for (int k = 1; k < 4; ++k) j[k] = sr[k] * gr - sl[k] * gl;
+}
+
+template <class R>
+MC_D R me2_eemumu(const v4<R>& pem, const v4<R>& pep, const v4<R>& pmm, const v4<R>& pmp, R s, R e2,
+                  R sw2, R mz, R gz) {
+  const R cw2 = R(1) - sw2;
+  const R q = R(-1), t3 = R(-0.5);
+  const R gl = t3 - q * sw2, gr = -q * sw2;
+  const R zc = R(1) / (sw2 * cw2);
+  // 1/(s - MZ^2 + i MZ GZ)
+  const R dre = s - mz * mz, dim = mz * gz, dn = R(1) / (dre * dre + dim * dim);
+  const cx<R> zprop = mkc(dre * dn, -dim * dn);
+  R total = R(0);
+  for (int h1 = -1; h1 <= 1; h1 += 2)
+    for (int h2 = -1; h2 <= 1; h2 += 2) {
+      const sp4<R> u1 = u_spinor(pem, R(0), h1);
+      const sp4<R> v2 = v_spinor(pep, R(0), h2);
+      const cx<R> v2l[2] = {v2.l0, v2.l1}, v2r[2] = {v2.r0, v2.r1};
+      const cx<R> u1l[2] = {u1.l0, u1.l1}, u1r[2] = {u1.r0, u1.r1};
+      cx<R> jev[4], jez[4];
+      lepton_current(v2l, v2r, u1l, u1r, R(1), R(1), jev);  // vbar gamma u
+      lepton_current(v2l, v2r, u1l, u1r, gl, gr, jez);
+      for (int h3 = -1; h3 <= 1; h3 += 2)
+        for (int h4 = -1; h4 <= 1; h4 += 2) {
+          const sp4<R> u3 = u_spinor(pmm, R(0), h3);
+          const sp4<R> v4s = v_spinor(pmp, R(0), h4);
+          const cx<R> u3l[2] = {u3.l0, u3.l1}, u3r[2] = {u3.r0, u3.r1};
+          const cx<R> v4l[2] = {v4s.l0, v4s.l1}, v4r[2] = {v4s.r0, v4s.r1};
+          cx<R> jmv[4], jmz[4];
+          lepton_current(u3l, u3r, v4l, v4r, R(1), R(1), jmv);  // ubar gamma v
+          lepton_current(u3l, u3r, v4l, v4r, gl, gr, jmz);
+          cx<R> dv = jev[0] * jmv[0], dz = jez[0] * jmz[0];
+          for (int k = 1; k < 4; ++k) {
+            dv = dv - jev[k] * jmv[k];
+            dz = dz - jez[k] * jmz[k];
+          }
+          const cx<R> amp = dv * (q * q / s) + dz * zprop * zc;
+          total += norm2(amp);
+        }
+    }
+  return e2 * e2 * total * R(0.25);
+}
+
+// ------------------------------------------------------------- q qbar -> t tbar
+// One s-channel gluon: |M|^2 = g^4 / s^2 |J_q . J_t|^2 summed over helicities,
+// colour sum tr(t^a t^b) tr(t^a t^b) = 2, average 1/4 x 1/9.
+template <class R>
+MC_D R me2_qqbar_ttbar(const v4<R>& pq, const v4<R>& pqb, const v4<R>& pt, const v4<R>& ptb, R m, R g2) {
+  const R s = mdot(pq + pqb, pq + pqb);
+  R total = R(0);
+  for (int h1 = -1; h1 <= 1; h1 += 2)
+    for (int h2 = -1; h2 <= 1; h2 += 2) {
+      const sp4<R> u = u_spinor(pq, R(0), h1);
+      const sp4<R> vb = vbar_spinor(pqb, R(0), h2);
+      // J_q^mu = vbar gamma^mu u for mu = 0..3 via slashing the basis vectors
+      cx<R> jq[4];
+      const v4<R> basis[4] = {{R(1), R(0), R(0), R(0)}, {R(0), R(1), R(0), R(0)},
+                              {R(0), R(0), R(1), R(0)}, {R(0), R(0), R(0), R(1)}};
+      for (int mu = 0; mu < 4; ++mu) {
+        // gamma^mu = gamma^nu (e_mu)_nu with (e_mu)_nu = g_{mu nu}: slash(a) uses a^mu,
+        // so gamma^0 = slash(1,0,0,0) and gamma^k = -slash(e_k).
+        const cx<R> val = dot(vb, slash_col(basis[mu], u));
+        jq[mu] = mu == 0 ? val : -val;
+      }
+      for (int h3 = -1; h3 <= 1; h3 += 2)
+        for (int h4 = -1; h4 <= 1; h4 += 2) {
+          const sp4<R> ub = ubar_spinor(pt, m, h3);
+          const sp4<R> v = v_spinor(ptb, m, h4);
+          cx<R> jt[4];
+          for (int mu = 0; mu < 4; ++mu) {
+            const cx<R> val = dot(ub, slash_col(basis[mu], v));
+            jt[mu] = mu == 0 ? val : -val;
+          }
+          cx<R> d = jq[0] * jt[0] - jq[1] * jt[1] - jq[2] * jt[2] - jq[3] * jt[3];
+          total += norm2(d);
+        }
+    }
+  return g2 * g2 / (s * s) * total * R(2) / R(36);
+}
+
+// ------------------------------------------------------------- g g -> t tbar
+// Two colour-ordered partial amplitudes (gluon order along the quark line)
+// A(ab) = ubar [ -epsa S(pt - qa) epsb + J(ab) ] v (common factor i g^2
+// dropped), colour matrix of the strings t^a t^b, t^b t^a:
+// [[16/3, -2/3], [-2/3, 16/3]]; average 1/4 (spins) x 1/64 (colours).
+template <class R>
+MC_D R me2_gg_ttbar(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4<R>& ptb, R m, R g2) {
+  const v4<R> q[2] = {pa, pb};
+  v4<R> eps[2][2];
+  linear_polarisations(pa, &eps[0][0], &eps[0][1]);
+  linear_polarisations(pb, &eps[1][0], &eps[1][1]);
+  const v4<R> k0 = pt - pa, k1 = pt - pb;
+  const R inv0 = R(1) / (mdot(k0, k0) - m * m), inv1 = R(1) / (mdot(k1, k1) - m * m);
+  const v4<R> qab = pa + pb;
+  const R invq = R(1) / mdot(qab, qab);
+  R total = R(0);
+  for (int ht = -1; ht <= 1; ht += 2) {
+    const sp4<R> ub = ubar_spinor(pt, m, ht);
+    for (int hb = -1; hb <= 1; hb += 2) {
+      const sp4<R> v = v_spinor(ptb, m, hb);
+      for (int h = 0; h < 4; ++h) {
+        const v4<R> e0 = eps[0][h & 1], e1 = eps[1][h >> 1];
+        const v4<R> j01 = gluon_current(e0, q[0], e1, q[1], invq);
+        const sp4<R> r0 = slash_col(e0, v), r1 = slash_col(e1, v);
+        const cx<R> cur = dot(ub, slash_col(j01, v));
+        // A(01) = -ubar e0 S0 e1 v + J01 ;  A(10) = -ubar e1 S1 e0 v - J01
+        const cx<R> a01 = cur - dot(slash_row(ub, e0), prop_col(k0, m, inv0, r1));
+        const cx<R> a10 = -cur - dot(slash_row(ub, e1), prop_col(k1, m, inv1, r0));
+        const R d = norm2(a01) + norm2(a10);
+        const R o = a01.re * a10.re + a01.im * a10.im;
+        total += (R(16) / R(3)) * d - (R(4) / R(3)) * o;
+      }
+    }
+  }
+  return g2 * g2 * total / R(256);
+}
+
+// ------------------------------------------------------------- g g -> t tbar g
+// Six colour-ordered partial amplitudes A(abc) of the strings t^a t^b t^c
+// (gluons with incoming momenta q_a; the outgoing gluon is crossed) built
+// right to left on the anti-top spinor:
+//   Gamma(abc) v = epsa S_a epsb S_ab epsc v - J(ab) S_ab epsc v
+//                - epsa S_a J(bc) v + J(abc) v,
+// S_a = S(pt - q_a), S_ab = S(pt - q_a - q_b) (its momentum depends only on
+// the remaining gluon c), J(ab) = W(eps_a, eps_b), J(abc) = W(J(ab), eps_c) +
+// W(eps_a, J(bc)) + contact term (common factor i g^3 dropped).
+// Orderings are indexed lexicographically: 012, 021, 102, 120, 201, 210.
+// Colour matrix (x 1/27) = sum over gluon colours of tr(t^{s1} t^{s2} t^{s3}
+// (t^{s'1} t^{s'2} t^{s'3})^dagger), tr(t^a t^b) = delta/2, evaluated with
+// the Fierz identity sum_a t^a_ij t^a_kl = (delta_il delta_kj - delta_ij delta_kl / 3) / 2:
+// 192 on the diagonal (C_F^3 N), 30 for the reversed string, 3 for its two
+// cyclic shifts, -24 for the two adjacent transpositions.
+__constant__ float kColour3[36] = {
+    192, -24, -24, 3,   3,   30,  -24, 192, 3,   30,  -24, 3,   -24, 3,   192, -24, 30,  3,
+    3,   30,  -24, 192, 3,   -24, 3,   -24, 30,  3,   192, -24, 30,  3,   3,   -24, -24, 192};
+
+template <class R>
+MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4<R>& ptb, const v4<R>& pg,
+                     R m, R g2) {
+  const v4<R> q[3] = {pa, pb, -pg};
+  v4<R> eps[3][2];
+  linear_polarisations(pa, &eps[0][0], &eps[0][1]);
+  linear_polarisations(pb, &eps[1][0], &eps[1][1]);
+  linear_polarisations(pg, &eps[2][0], &eps[2][1]);
+  // fermion propagators: single gluon a next to the top, and the pair
+  // complementary to gluon c
+  v4<R> ka[3], kc[3];
+  R inva[3], invc[3];
+  for (int a = 0; a < 3; ++a) {
+    ka[a] = pt - q[a];
+    inva[a] = R(1) / (mdot(ka[a], ka[a]) - m * m);
+    kc[a] = q[a] - ptb;  // pt - q_b - q_c with {b, c} the other two gluons
+    invc[a] = R(1) / (mdot(kc[a], kc[a]) - m * m);
+  }
+  // gluon propagators of the pairs (01), (02), (12) and of all three
+  const v4<R> q01 = q[0] + q[1], q02 = q[0] + q[2], q12 = q[1] + q[2];
+  const R i01 = R(1) / mdot(q01, q01), i02 = R(1) / mdot(q02, q02), i12 = R(1) / mdot(q12, q12);
+  const v4<R> qall = q01 + q[2];
+  const R iall = R(1) / mdot(qall, qall);
+
+  sp4<R> ubar[2];
+  ubar[0] = ubar_spinor(pt, m, -1);
+  ubar[1] = ubar_spinor(pt, m, +1);
+
+  R total = R(0);
+#pragma unroll 1
+  for (int h = 0; h < 8; ++h) {
+    const v4<R> e0 = eps[0][h & 1], e1 = eps[1][(h >> 1) & 1], e2 = eps[2][h >> 2];
+    const v4<R> e[3] = {e0, e1, e2};
+    // pair currents J(ab) for a < b (J(ba) = -J(ab))
+    const v4<R> j01 = gluon_current(e0, q[0], e1, q[1], i01);
+    const v4<R> j02 = gluon_current(e0, q[0], e2, q[2], i02);
+    const v4<R> j12 = gluon_current(e1, q[1], e2, q[2], i12);
+    // triple currents, J(cba) = J(abc): J012 = J210, J021 = J120, J102 = J201
+    const v4<R> j012 = gluon_current(j01, q01, e2, q[2], iall) + gluon_current(e0, q[0], j12, q12, iall) +
+                       gluon_contact(e0, e1, e2, iall);
+    const v4<R> j021 = gluon_current(j02, q02, e1, q[1], iall) + gluon_current(e0, q[0], -j12, q12, iall) +
+                       gluon_contact(e0, e2, e1, iall);
+    const v4<R> j102 = gluon_current(-j01, q01, e2, q[2], iall) + gluon_current(e1, q[1], j02, q02, iall) +
+                       gluon_contact(e1, e0, e2, iall);
+#pragma unroll 1
+    for (int hb = 0; hb < 2; ++hb) {
+      const sp4<R> v = v_spinor(ptb, m, hb ? 1 : -1);
+      // X_c = S_{pair != c} eps_c v
+      sp4<R> x[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) x[c] = prop_col(kc[c], m, invc[c], slash_col(e[c], v));
+      // column spinors Gamma(sigma) v for the six orderings
+      sp4<R> col[6];
+      // term 1: eps_a S_a eps_b X_c
+      // (a,b,c): 012 021 102 120 201 210
+      col[0] = slash_col(e0, prop_col(ka[0], m, inva[0], slash_col(e1, x[2])));
+      col[1] = slash_col(e0, prop_col(ka[0], m, inva[0], slash_col(e2, x[1])));
+      col[2] = slash_col(e1, prop_col(ka[1], m, inva[1], slash_col(e0, x[2])));
+      col[3] = slash_col(e1, prop_col(ka[1], m, inva[1], slash_col(e2, x[0])));
+      col[4] = slash_col(e2, prop_col(ka[2], m, inva[2], slash_col(e0, x[1])));
+      col[5] = slash_col(e2, prop_col(ka[2], m, inva[2], slash_col(e1, x[0])));
+      // term 2: -J(ab) X_c
+      const sp4<R> y2 = slash_col(j01, x[2]), y1 = slash_col(j02, x[1]), y0 = slash_col(j12, x[0]);
+      col[0] = col[0] - y2;
+      col[2] = col[2] + y2;
+      col[1] = col[1] - y1;
+      col[4] = col[4] + y1;
+      col[3] = col[3] - y0;
+      col[5] = col[5] + y0;
+      // term 3: -eps_a S_a J(bc) v
+      const sp4<R> z0 = slash_col(e0, prop_col(ka[0], m, inva[0], slash_col(j12, v)));
+      const sp4<R> z1 = slash_col(e1, prop_col(ka[1], m, inva[1], slash_col(j02, v)));
+      const sp4<R> z2 = slash_col(e2, prop_col(ka[2], m, inva[2], slash_col(j01, v)));
+      col[0] = col[0] - z0;
+      col[1] = col[1] + z0;
+      col[2] = col[2] - z1;
+      col[3] = col[3] + z1;
+      col[4] = col[4] - z2;
+      col[5] = col[5] + z2;
+      // term 4: J(abc) v
+      const sp4<R> w012 = slash_col(j012, v), w021 = slash_col(j021, v), w102 = slash_col(j102, v);
+      col[0] = col[0] + w012;
+      col[5] = col[5] + w012;
+      col[1] = col[1] + w021;
+      col[3] = col[3] + w021;
+      col[2] = col[2] + w102;
+      col[4] = col[4] + w102;
+#pragma unroll
+      for (int ht = 0; ht < 2; ++ht) {
+        cx<R> amp[6];
+#pragma unroll
+        for (int s = 0; s < 6; ++s) amp[s] = dot(ubar[ht], col[s]);
+        R acc = R(0);
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+          acc += R(kColour3[s * 6 + s]) * norm2(amp[s]);
+#pragma unroll
+          for (int t = s + 1; t < 6; ++t)
+            acc += R(2) * R(kColour3[s * 6 + t]) * (amp[s].re * amp[t].re + amp[s].im * amp[t].im);
+        }
+        total += acc;
+      }
+    }
+  }
+  return g2 * g2 * g2 * total / (R(27) * R(256));
+}
+
+}  // namespace mc

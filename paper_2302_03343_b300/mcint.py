@@ -1,0 +1,271 @@
+"""Thin ctypes binding of libmcint.so (C ABI in include/mcint.h).
+
+Argument marshalling only: every step of the Monte Carlo path runs in the CUDA
+library.  Device buffers are passed as raw pointers (e.g. a torch tensor's
+data_ptr()), streams as the integer handle of a cudaStream_t.  A non-zero
+status raises McError with the library's message.  The library must have been
+built (python -m paper_2302_03343_b300.build); there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmcint.so")
+
+MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ENAN, MC_ENOCONV, MC_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+MC_FP64, MC_FP32_KAHAN = 0, 1
+MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS = 0, 1, 2, 3
+MC_MAX_DIM, MC_MAX_BINS = 16, 256
+REC = dict(K=0, X=16, BIN=32, JAC=48, P=49, X1=77, X2=78, SHAT=79, LUMI=80, LUMI_QQ=81, ME2=82, ME2_QQ=83,
+           PSW=84, F=85, W=86, PASS=87, STATUS=88)
+REC_STRIDE = 96
+
+# exported symbols (each declared in include/mcint.h)
+SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_vegas_init", "mc_vegas_free",
+           "mc_vegas_set_grid", "mc_vegas_get_grid", "mc_vegas_get_hist", "mc_vegas_set_iteration",
+           "mc_vegas_get_iteration", "mc_vegas_set_gid", "mc_vegas_iterate", "mc_vegas_refine", "mc_integrate",
+           "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms")
+
+
+class McError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mcint error {code}: {msg}")
+        self.code = code
+
+
+class Integrand(ctypes.Structure):
+    _fields_ = [("proc", ctypes.c_int32), ("gauss_dim", ctypes.c_int32)] + [
+        (n, ctypes.c_double) for n in ("sqrt_s", "m_top", "alpha", "alpha_s", "mz", "gz", "sw2", "mu_f", "ptcut_g",
+                                       "etacut_g", "gauss_sigma", "gev2pb")]
+
+
+class IterResult(ctypes.Structure):
+    _fields_ = [("sum", ctypes.c_double), ("sum2", ctypes.c_double), ("n", ctypes.c_int64),
+                ("n_nonzero", ctypes.c_int64), ("wmax", ctypes.c_double), ("n_bad", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("sigma", ctypes.c_double), ("chi2_dof", ctypes.c_double),
+                ("n_iter", ctypes.c_int32), ("status", ctypes.c_int32), ("gpu_ms", ctypes.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """Load libmcint.so; raises if it is missing (no CPU fallback exists)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise McError(MC_EINVAL, f"{LIB_PATH} not built: run python -m paper_2302_03343_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        L.mc_last_error.restype = ctypes.c_char_p
+        i64, i32, u32, u64, d = ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "mc_pdf_load": [_dp, i32, _dp, i32, ctypes.POINTER(ctypes.c_int32), i32, _dp, ctypes.POINTER(_vp)],
+            "mc_pdf_free": [_vp],
+            "mc_pdf_xfxq2": [_vp, i32, i64, _vp, _vp, _vp, _vp],
+            "mc_vegas_init": [i32, i32, u64, i32, ctypes.POINTER(_vp)],
+            "mc_vegas_free": [_vp],
+            "mc_vegas_set_grid": [_vp, _dp],
+            "mc_vegas_get_grid": [_vp, _dp],
+            "mc_vegas_get_hist": [_vp, _dp, ctypes.POINTER(ctypes.c_uint32)],
+            "mc_vegas_set_iteration": [_vp, u32],
+            "mc_vegas_get_iteration": [_vp, ctypes.POINTER(ctypes.c_uint32)],
+            "mc_vegas_set_gid": [_vp, u32],
+            "mc_vegas_iterate": [_vp, ctypes.POINTER(Integrand), _vp, i64, _vp, ctypes.POINTER(IterResult)],
+            "mc_vegas_refine": [_vp, d, _vp],
+            "mc_integrate": [ctypes.POINTER(Integrand), _vp, i32, i64, i32, u64, u32, i32, d, d, _vp,
+                             ctypes.POINTER(Result), ctypes.POINTER(IterResult)],
+            "mc_debug_events": [_vp, ctypes.POINTER(Integrand), _vp, i64, i64, _vp, _vp],
+            "mc_launch_shape": [ctypes.POINTER(Integrand), i32, i64, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)],
+            "mc_vegas_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_float)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc != MC_OK:
+        raise McError(rc, lib().mc_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (or an int)."""
+    return ctypes.c_void_p(x.data_ptr() if hasattr(x, "data_ptr") else int(x))
+
+
+def _integrand(itg):
+    if isinstance(itg, Integrand):
+        return itg
+    d = itg.asdict() if hasattr(itg, "asdict") else dict(itg)
+    return Integrand(**d)
+
+
+# ------------------------------------------------------------------ PDF
+class Pdf:
+    """Owns an mc_pdf handle (device copy of an LHAPDF-style grid)."""
+
+    def __init__(self, handle, nflav, pids):
+        self.handle, self.nflav, self.pids = handle, nflav, pids
+
+    def free(self):
+        if self.handle:
+            mc_pdf_free(self)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mc_pdf_load(grid):
+    x = np.ascontiguousarray(grid.x, dtype=np.float64)
+    q = np.ascontiguousarray(grid.q, dtype=np.float64)
+    pids = np.ascontiguousarray(grid.pids, dtype=np.int32)
+    xf = np.ascontiguousarray(grid.xf, dtype=np.float64)
+    h = _vp()
+    _check(lib().mc_pdf_load(x.ctypes.data_as(_dp), len(x), q.ctypes.data_as(_dp), len(q),
+                             pids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(pids), xf.ctypes.data_as(_dp),
+                             ctypes.byref(h)))
+    return Pdf(h, len(pids), tuple(int(p) for p in pids))
+
+
+def mc_pdf_free(pdf):
+    _check(lib().mc_pdf_free(pdf.handle))
+
+
+def mc_pdf_xfxq2(pdf, prec, n, x_dev, q2_dev, out_dev, stream=None):
+    _check(lib().mc_pdf_xfxq2(pdf.handle, prec, n, _ptr(x_dev), _ptr(q2_dev), _ptr(out_dev), _stream(stream)))
+
+
+# ---------------------------------------------------------------- VEGAS
+class Vegas:
+    """Owns an mc_vegas handle."""
+
+    def __init__(self, handle, ndim, nbins, prec):
+        self.handle, self.ndim, self.nbins, self.prec = handle, ndim, nbins, prec
+
+    def free(self):
+        if self.handle:
+            _check(lib().mc_vegas_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mc_vegas_init(ndim, nbins, seed, prec):
+    h = _vp()
+    _check(lib().mc_vegas_init(ndim, nbins, seed, prec, ctypes.byref(h)))
+    return Vegas(h, ndim, nbins, prec)
+
+
+def mc_vegas_free(v):
+    v.free()
+
+
+def mc_vegas_set_grid(v, edges):
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    assert e.shape == (v.ndim, v.nbins + 1)
+    _check(lib().mc_vegas_set_grid(v.handle, e.ctypes.data_as(_dp)))
+
+
+def mc_vegas_get_grid(v):
+    e = np.zeros((v.ndim, v.nbins + 1))
+    _check(lib().mc_vegas_get_grid(v.handle, e.ctypes.data_as(_dp)))
+    return e
+
+
+def mc_vegas_get_hist(v):
+    w2 = np.zeros((v.ndim, v.nbins))
+    n = np.zeros((v.ndim, v.nbins), dtype=np.uint32)
+    _check(lib().mc_vegas_get_hist(v.handle, w2.ctypes.data_as(_dp), n.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    return w2, n
+
+
+def mc_vegas_set_iteration(v, it):
+    _check(lib().mc_vegas_set_iteration(v.handle, it))
+
+
+def mc_vegas_get_iteration(v):
+    it = ctypes.c_uint32()
+    _check(lib().mc_vegas_get_iteration(v.handle, ctypes.byref(it)))
+    return it.value
+
+
+def mc_vegas_set_gid(v, gid):
+    _check(lib().mc_vegas_set_gid(v.handle, gid))
+
+
+def mc_vegas_iterate(v, itg, pdf, nevents, stream=None):
+    r = IterResult()
+    c = _integrand(itg)
+    _check(lib().mc_vegas_iterate(v.handle, ctypes.byref(c), pdf.handle if pdf else None, nevents,
+                                  _stream(stream), ctypes.byref(r)))
+    return r
+
+
+def mc_vegas_refine(v, alpha=1.5, stream=None):
+    _check(lib().mc_vegas_refine(v.handle, alpha, _stream(stream)))
+
+
+def mc_integrate(itg, pdf, niter, nevents, nbins=50, seed=0, gid=0, prec=MC_FP64, alpha=1.5, target_rel_err=0.0,
+                 stream=None):
+    c = _integrand(itg)
+    out = Result()
+    per = (IterResult * niter)()
+    _check(lib().mc_integrate(ctypes.byref(c), pdf.handle if pdf else None, niter, nevents, nbins, seed, gid, prec,
+                              alpha, target_rel_err, _stream(stream), ctypes.byref(out), per))
+    return out, [per[i] for i in range(out.n_iter)]
+
+
+def mc_debug_events(v, itg, pdf, first, k, out_dev, stream=None):
+    c = _integrand(itg)
+    _check(lib().mc_debug_events(v.handle, ctypes.byref(c), pdf.handle if pdf else None, first, k, _ptr(out_dev),
+                                 _stream(stream)))
+
+
+def mc_vegas_kernel_ms(v):
+    ms = ctypes.c_float()
+    _check(lib().mc_vegas_kernel_ms(v.handle, ctypes.byref(ms)))
+    return ms.value
+
+
+def mc_launch_shape(itg, prec, nevents):
+    b, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib().mc_launch_shape(ctypes.byref(_integrand(itg)), prec, nevents, ctypes.byref(b), ctypes.byref(t)))
+    return b.value, t.value
+
+
+__all__ = ["McError", "Integrand", "IterResult", "Result", "Pdf", "Vegas", "workloads", *SYMBOLS]

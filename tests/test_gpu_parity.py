@@ -1,0 +1,321 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded Philox streams.
+
+Bars: integer uniforms, VEGAS bins and bin counts bit-exact; FP64 mode
+per-event weights within 1e-12 relative and integrals within 1e-10 relative;
+FP32+Kahan mode per-event errors reported (median / p99 / max) against the
+oracle evaluated at the identical 23-bit points, with loose bounds written
+below.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2302_03343_b300 import mcint as M
+from paper_2302_03343_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+R = M.REC
+PROCS = {"ee": W.ee_mumu(91.0), "pp": W.pp_ttbar(), "gg": W.gg_ttbarg(), "gauss": W.gauss(6)}
+
+
+@pytest.fixture(scope="module")
+def gpu(pdf_grid):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_03343_b300 import build
+    build.build()
+    M.lib()
+    torch.cuda.init()
+    return M.mc_pdf_load(pdf_grid)
+
+
+def random_grid(ndim, nbins, seed):
+    """A non-uniform monotone grid (refined from a random histogram)."""
+    rng = np.random.default_rng(seed)
+    e = W.uniform_grid(ndim, nbins)
+    return O.vegas_refine(e, rng.exponential(size=(ndim, nbins)) ** 2, alpha=1.0)
+
+
+def gpu_records(gpdf, itg, prec, edges, first, k, iteration=0, seed=0, gid=0):
+    ndim, nb1 = edges.shape
+    v = M.mc_vegas_init(ndim, nb1 - 1, seed, prec)
+    M.mc_vegas_set_grid(v, edges)
+    M.mc_vegas_set_iteration(v, iteration)
+    M.mc_vegas_set_gid(v, gid)
+    out = torch.full((max(k, 1), M.REC_STRIDE), float("nan"), dtype=torch.float64, device="cuda")
+    M.mc_debug_events(v, itg, gpdf, first, k, out)
+    torch.cuda.synchronize()
+    v.free()
+    return out.cpu().numpy()[:k]
+
+
+def oracle_records(opdf, itg, prec, edges, events, iteration=0, seed=0, gid=0):
+    return [O.event(itg, opdf, edges, prec, seed, iteration, gid, int(ev)) for ev in events]
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+# ------------------------------------------------------------------ uniforms
+@pytest.mark.parametrize("name", list(PROCS))
+@pytest.mark.parametrize("prec", [M.MC_FP64, M.MC_FP32_KAHAN])
+def test_uniforms_and_bins_bit_exact(gpu, oracle_pdf, name, prec):
+    itg = PROCS[name]
+    nd = itg.ndim()
+    edges = random_grid(nd, 50, 1)
+    first, k = 1000, 300
+    g = gpu_records(gpu, itg, prec, edges, first, k, iteration=3, seed=77, gid=5)
+    ref = O.uniform_ints(77, 3, 5, prec, nd, first, k)
+    np.testing.assert_array_equal(g[:, R["K"]:R["K"] + nd].astype(np.uint64), ref)
+    recs = oracle_records(oracle_pdf, itg, prec, edges, range(first, first + k), 3, 77, 5)
+    bins = np.array([list(r.bin)[:nd] for r in recs])
+    np.testing.assert_array_equal(g[:, R["BIN"]:R["BIN"] + nd].astype(np.int64), bins)
+
+
+def test_counter_high_word(gpu, oracle_pdf):
+    itg = PROCS["gauss"]
+    edges = W.uniform_grid(6, 50)
+    first = 2 ** 32 - 5
+    g = gpu_records(gpu, itg, M.MC_FP64, edges, first, 10, seed=3)
+    np.testing.assert_array_equal(g[:, :6].astype(np.uint64), O.uniform_ints(3, 0, 0, 0, 6, first, 10))
+
+
+# ------------------------------------------------------------------ per-event FP64
+@pytest.mark.parametrize("name,k", [("ee", 2000), ("pp", 2000), ("gg", 600), ("gauss", 2000)])
+def test_fp64_event_weights(gpu, oracle_pdf, name, k):
+    itg = PROCS[name]
+    nd = itg.ndim()
+    edges = random_grid(nd, 50, 2)
+    g = gpu_records(gpu, itg, M.MC_FP64, edges, 0, k, iteration=1, seed=11)
+    recs = oracle_records(oracle_pdf, itg, M.MC_FP64, edges, range(k), 1, 11)
+    w_o = np.array([r.weight for r in recs])
+    w_g = g[:, R["W"]]
+    pass_o = np.array([r.pass_ for r in recs])
+    np.testing.assert_array_equal(g[:, R["PASS"]].astype(int), pass_o)
+    nz = w_o != 0
+    assert np.all(w_g[~nz] == 0)
+    assert np.max(rel(w_g[nz], w_o[nz]), initial=0) < 1e-12
+    x_o = np.array([list(r.x)[:nd] for r in recs])
+    assert np.max(np.abs(g[:, R["X"]:R["X"] + nd] - x_o)) < 1e-15
+    if name in ("pp", "gg"):
+        ok = pass_o == 1
+        assert np.max(rel(g[ok, R["ME2"]], [r.me2 for r, o in zip(recs, ok) if o])) < 1e-12
+        # luminosities: relative 1e-12, except where the interpolant crosses
+        # zero near x = 1 (there the rounding-order difference of the two
+        # interpolations is compared with the typical luminosity instead)
+        def close(got, ref):
+            ref = np.asarray(ref, float)
+            scale = np.median(np.abs(ref))
+            return np.all(np.abs(got - ref) <= 1e-12 * np.maximum(np.abs(ref), 1e-3 * scale))
+        assert close(g[ok, R["LUMI"]], [r.lumi for r, o in zip(recs, ok) if o])
+        if name == "pp":
+            assert np.max(rel(g[ok, R["ME2_QQ"]], [r.me2_qq for r, o in zip(recs, ok) if o])) < 1e-12
+            assert close(g[ok, R["LUMI_QQ"]], [r.lumi_qq for r, o in zip(recs, ok) if o])
+        p_o = np.array([np.array(r.p) for r, o in zip(recs, ok) if o])
+        p_g = g[ok, R["P"]:R["P"] + 28].reshape(-1, 7, 4)
+        n_out = 4 if name == "pp" else 5
+        scale = np.sqrt(g[ok, R["SHAT"]])[:, None, None]
+        assert np.max(np.abs(p_g[:, :n_out] - p_o[:, :n_out]) / scale) < 1e-13
+
+
+# ------------------------------------------------------------------ per-event FP32
+@pytest.mark.parametrize("name,k", [("ee", 4000), ("pp", 4000), ("gg", 1500), ("gauss", 4000)])
+def test_fp32_event_weights_error_statistics(gpu, oracle_pdf, name, k):
+    itg = PROCS[name]
+    nd = itg.ndim()
+    edges = random_grid(nd, 50, 3)
+    g = gpu_records(gpu, itg, M.MC_FP32_KAHAN, edges, 0, k, iteration=2, seed=5)
+    recs = oracle_records(oracle_pdf, itg, M.MC_FP32_KAHAN, edges, range(k), 2, 5)
+    w_o = np.array([r.weight for r in recs])
+    w_g = g[:, R["W"]]
+    both = (w_o != 0) & (w_g != 0)
+    flips = np.count_nonzero((w_o != 0) != (w_g != 0))
+    e = rel(w_g[both], w_o[both])
+    print(f"\n{name} FP32 per-event rel. error: median {np.median(e):.2e} p99 {np.quantile(e, .99):.2e} "
+          f"max {e.max():.2e}; cut/threshold flips {flips}/{k}")
+    assert flips <= max(1, k // 1000)
+    assert np.median(e) < 1e-5
+    assert np.quantile(e, 0.99) < 1e-3
+
+
+# ------------------------------------------------------------------ one iteration
+@pytest.mark.parametrize("name,n,prec", [("ee", 100000, M.MC_FP64), ("pp", 20000, M.MC_FP64),
+                                         ("gg", 5000, M.MC_FP64), ("gauss", 50000, M.MC_FP64),
+                                         ("gg", 20000, M.MC_FP32_KAHAN), ("gauss", 50000, M.MC_FP32_KAHAN)])
+def test_iteration_sums_and_histograms(gpu, oracle_pdf, name, n, prec):
+    itg = PROCS[name]
+    nd = itg.ndim()
+    edges = random_grid(nd, 50, 4)
+    v = M.mc_vegas_init(nd, 50, 9, prec)
+    M.mc_vegas_set_grid(v, edges)
+    r = M.mc_vegas_iterate(v, itg, gpu, n)
+    w2, cnt = M.mc_vegas_get_hist(v)
+    ref = O.iterate(itg, oracle_pdf, edges, prec, 9, 0, 0, 0, n)
+    np.testing.assert_array_equal(cnt, ref["hist_n"])
+    assert r.n == n and M.mc_vegas_get_iteration(v) == 1
+    tol = 1e-10 if prec == M.MC_FP64 else 5e-5
+    assert abs(r.sum - ref["sum"]) <= tol * abs(ref["sum"])
+    assert abs(r.sum2 - ref["sum2"]) <= tol * abs(ref["sum2"]) * (1 if prec == M.MC_FP64 else 10)
+    if prec == M.MC_FP64:
+        assert r.n_nonzero == ref["n_nonzero"]
+        nzb = ref["hist_w2"] > 0
+        assert np.max(rel(w2[nzb], ref["hist_w2"][nzb])) < 1e-10
+        assert abs(r.wmax - ref["wmax"]) <= 1e-12 * ref["wmax"]
+    else:
+        assert abs(r.n_nonzero - ref["n_nonzero"]) <= max(1, n // 1000)
+    # the same iteration again gives bitwise-identical sums (fixed-order reduction)
+    M.mc_vegas_set_iteration(v, 0)
+    r2 = M.mc_vegas_iterate(v, itg, gpu, n)
+    assert r2.sum == r.sum and r2.sum2 == r.sum2 and r2.n_nonzero == r.n_nonzero
+    v.free()
+
+
+def test_refine_matches_oracle(gpu, oracle_pdf):
+    itg = PROCS["pp"]
+    edges = W.uniform_grid(4, 50)
+    v = M.mc_vegas_init(4, 50, 0, M.MC_FP64)
+    for it in range(3):
+        M.mc_vegas_iterate(v, itg, gpu, 20000)
+        w2, _ = M.mc_vegas_get_hist(v)
+        ref = O.iterate(itg, oracle_pdf, edges, 0, 0, it, 0, 0, 20000)
+        M.mc_vegas_refine(v, 1.5)
+        edges = O.vegas_refine(edges, ref["hist_w2"], 1.5)
+        g = M.mc_vegas_get_grid(v)
+        assert np.max(np.abs(g - edges)) < 1e-10
+        w2n, cn = M.mc_vegas_get_hist(v)
+        assert not w2n.any() and not cn.any()
+    v.free()
+
+
+def test_integrate_ee_mumu_config(gpu, oracle_pdf):
+    # e+e- -> mu+mu- at 91 GeV, FP64, 50 bins, 5 x 1e5 events, seed 0
+    itg = PROCS["ee"]
+    res, per = M.mc_integrate(itg, None, 5, 100000, nbins=50, seed=0, prec=M.MC_FP64)
+    ref = O.integrate(itg, None, W.uniform_grid(2, 50), 0, seed=0, gid=0, niter=5, nevents=100000)
+    assert abs(res.mean - ref["mean"]) <= 1e-10 * abs(ref["mean"])
+    assert abs(res.sigma - ref["sigma"]) <= 1e-8 * ref["sigma"]
+    assert res.n_iter == 5 and res.status == 0
+    s = 91.0 ** 2
+    from scipy import integrate as si
+    val, _ = si.quad(lambda c: O.me2_eemumu(itg.alpha, itg.mz, itg.gz, itg.sw2, s, c), -1, 1, epsrel=1e-13)
+    exact = val * 2 * math.pi / (64 * math.pi ** 2 * s) * itg.gev2pb
+    assert abs(res.mean - exact) < 3 * res.sigma
+
+
+def test_integrate_pp_ttbar_fp64(gpu, oracle_pdf):
+    itg = PROCS["pp"]
+    res, _ = M.mc_integrate(itg, gpu, 3, 30000, nbins=50, seed=0, prec=M.MC_FP64)
+    ref = O.integrate(itg, oracle_pdf, W.uniform_grid(4, 50), 0, seed=0, gid=0, niter=3, nevents=30000)
+    assert abs(res.mean - ref["mean"]) <= 1e-10 * abs(ref["mean"])
+
+
+# ------------------------------------------------------------------ PDF batch
+@pytest.mark.parametrize("prec,tol", [(M.MC_FP64, 1e-13), (M.MC_FP32_KAHAN, 1e-5)])
+def test_pdf_xfxq2(gpu, oracle_pdf, pdf_grid, prec, tol):
+    rng = np.random.default_rng(0)
+    n = 3000
+    x = 10 ** rng.uniform(-7, math.log10(0.5), n)
+    q2 = (10 ** rng.uniform(math.log10(1.7), 3.95, n)) ** 2
+    xd = torch.tensor(x, device="cuda")
+    qd = torch.tensor(q2, device="cuda")
+    out = torch.empty((n, len(pdf_grid.pids)), dtype=torch.float64, device="cuda")
+    M.mc_pdf_xfxq2(gpu, prec, n, xd, qd, out)
+    got = out.cpu().numpy()
+    worst = 0.0
+    for i in range(0, n, 7):
+        for fl, pid in enumerate(pdf_grid.pids):
+            ref = oracle_pdf.xfxq2(int(pid), x[i], q2[i])
+            worst = max(worst, abs(got[i, fl] - ref) / (abs(ref) + 1e-16))  # eq. pdfflow-diff
+    assert worst < tol, worst
+    # nodes: FP64 reproduces the stored values
+    if prec == M.MC_FP64:
+        xi = pdf_grid.x[5:90:7]
+        qj = pdf_grid.q[3:37:5]
+        X, Q = np.meshgrid(xi, qj, indexing="ij")
+        xd = torch.tensor(X.ravel(), device="cuda")
+        qd = torch.tensor((Q ** 2).ravel(), device="cuda")
+        out = torch.empty((X.size, len(pdf_grid.pids)), dtype=torch.float64, device="cuda")
+        M.mc_pdf_xfxq2(gpu, prec, X.size, xd, qd, out)
+        ref = pdf_grid.xf[5:90:7][:, 3:37:5].reshape(-1, len(pdf_grid.pids))
+        assert np.max(rel(out.cpu().numpy(), ref)) < 1e-13
+    # outside the grid: NaN
+    xd = torch.tensor([1e-9, 0.1], device="cuda")
+    qd = torch.tensor([100.0, 1e12], device="cuda")
+    out = torch.empty((2, len(pdf_grid.pids)), dtype=torch.float64, device="cuda")
+    M.mc_pdf_xfxq2(gpu, prec, 2, xd, qd, out)
+    assert torch.isnan(out).all()
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_single_and_ragged(gpu, oracle_pdf):
+    itg = PROCS["gauss"]
+    v = M.mc_vegas_init(6, 50, 0, M.MC_FP64)
+    r = M.mc_vegas_iterate(v, itg, None, 0)
+    assert r.n == 0 and r.sum == 0 and M.mc_vegas_get_iteration(v) == 1
+    for n in (1, 37, 128 * 1000 + 37):
+        M.mc_vegas_set_iteration(v, 0)
+        r = M.mc_vegas_iterate(v, itg, None, n)
+        ref = O.iterate(itg, None, W.uniform_grid(6, 50), 0, 0, 0, 0, 0, n)
+        assert abs(r.sum - ref["sum"]) <= 1e-12 * abs(ref["sum"])
+        M.mc_vegas_refine(v, 1.5)
+        M.mc_vegas_set_grid(v, W.uniform_grid(6, 50))
+    v.free()
+
+
+def test_invalid_arguments_are_rejected(gpu):
+    v = M.mc_vegas_init(4, 50, 0, M.MC_FP64)
+    with pytest.raises(M.McError):
+        M.mc_vegas_iterate(v, PROCS["ee"], None, 10)  # dimension mismatch
+    with pytest.raises(M.McError):
+        M.mc_vegas_iterate(v, PROCS["pp"], None, 10)  # PDF missing
+    with pytest.raises(M.McError):
+        M.mc_vegas_iterate(v, PROCS["pp"], gpu, -1)
+    bad = W.uniform_grid(4, 50)
+    bad[1, 10] = bad[1, 9]
+    with pytest.raises(M.McError):
+        M.mc_vegas_set_grid(v, bad)
+    v.free()
+
+
+# ------------------------------------------------------------------ benchmark size
+def test_full_size_gg_ttbarg_sampled(gpu, oracle_pdf):
+    """At the benchmark launch (gg -> ttg, FP32+Kahan, 1e7 events, 50 bins):
+    sampled events agree with the oracle, and the sums over a recorded
+    sub-range equal a separate iteration over that range."""
+    itg = PROCS["gg"]
+    v = M.mc_vegas_init(14, 50, 0, M.MC_FP32_KAHAN)
+    r = M.mc_vegas_iterate(v, itg, gpu, 10_000_000)
+    assert r.n == 10_000_000 and r.status in (0, M.MC_ENOCONV)
+    assert r.n_bad < 100
+    _, cnt = M.mc_vegas_get_hist(v)
+    assert np.all(cnt.sum(axis=1) == 10_000_000)
+    edges = W.uniform_grid(14, 50)
+    idx = np.sort(np.random.default_rng(0).choice(10_000_000, 200, replace=False))
+    out = torch.empty((200, M.REC_STRIDE), dtype=torch.float64, device="cuda")
+    ws = []
+    for j, ev in enumerate(idx):
+        M.mc_debug_events(v, itg, gpu, int(ev), 1, out[j:j + 1])  # iteration counter is now 1: use 1 below
+    torch.cuda.synchronize()
+    g = out.cpu().numpy()
+    recs = oracle_records(oracle_pdf, itg, M.MC_FP32_KAHAN, edges, idx, iteration=1)
+    for rr, gg in zip(recs, g):
+        if rr.weight != 0 and gg[R["W"]] != 0:
+            ws.append(abs(gg[R["W"]] - rr.weight) / abs(rr.weight))
+    assert np.median(ws) < 1e-5
+    # record events 0..99999 of iteration 1 and compare with an iteration over them
+    k = 100_000
+    rec = torch.empty((k, M.REC_STRIDE), dtype=torch.float64, device="cuda")
+    M.mc_debug_events(v, itg, gpu, 0, k, rec)
+    torch.cuda.synchronize()
+    wrec = rec[:, R["W"]].cpu().numpy()
+    M.mc_vegas_set_iteration(v, 1)
+    r1 = M.mc_vegas_iterate(v, itg, gpu, k)
+    assert abs(r1.sum - wrec.sum()) <= 1e-12 * abs(wrec.sum())
+    v.free()
