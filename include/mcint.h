@@ -212,6 +212,48 @@ int mc_vegas_kernel_ms(mc_vegas v, float* ms);
  * library would use for a process (blocks, threads per block). */
 int mc_launch_shape(const mc_integrand* itg, int prec, int64_t nevents, int* blocks, int* threads);
 
+/* ------------------------------------------- allocation-free iteration
+ * mc_vegas_iterate_noalloc: the same fused iteration as mc_vegas_iterate, for
+ * callers that must not allocate device memory while they run: code whose
+ * device memory is owned by another pool (an application or framework
+ * allocator that has reserved the device), and latency-critical loops where
+ * a cudaMalloc/cudaFree could synchronise the device.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  The thesis has no
+ * counterpart; this is an operational variant of the same kernel.
+ *
+ * Scratch: the per-block partial sums live in a file-scope device array of
+ * MC_NOALLOC_MAX_BLOCKS entries (64 B each, 256 KiB) that every device which
+ * loads this library holds until the process exits.  The first call on a
+ * device looks up the array's device address with that device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array: calls whose launches overlap on the GPU race
+ * (serialise them on one stream).  Each launch writes every slot it later
+ * reads, so nothing in the array needs clearing between calls.
+ *
+ * Inputs (caller-owned): itg (host), pdf (an mc_pdf loaded earlier, or NULL
+ * for processes without hadrons), the grid as device arrays edges64 (FP64)
+ * and, for MC_FP32_KAHAN, edges32 (FP32), both [ndim][nbins+1]; seed,
+ * iteration and gid form the Philox counter as in mc_vegas_iterate.
+ * blocks = 0 lets the library choose the launch (at most
+ * MC_NOALLOC_MAX_BLOCKS blocks); a larger request is rejected with EINVAL.
+ * Outputs (device, caller-owned): hist_w2[ndim][nbins] and
+ * hist_n[ndim][nbins] are accumulated into (zero them to start a fresh
+ * histogram); *sums receives the compensated sums of the launch.
+ * Asynchronous on `stream`; the outputs are valid once the stream reaches
+ * the end of the call.
+ */
+#define MC_NOALLOC_MAX_BLOCKS 4096
+typedef struct {
+  double sum_hi, sum_lo;    /* sum of w = sum_hi + sum_lo                       */
+  double sum2_hi, sum2_lo;  /* sum of w^2                                       */
+  double wmax;
+  int64_t n_nonzero, n_bad, n_noconv;
+} mc_device_sums;
+int mc_vegas_iterate_noalloc(const mc_integrand* itg, mc_pdf pdf, int ndim, int nbins, const double* edges64,
+                             const float* edges32, int prec, uint64_t seed, uint32_t iteration, uint32_t gid,
+                             int64_t nevents, int blocks, double* hist_w2, uint32_t* hist_n, mc_device_sums* sums,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,37 +58,12 @@ int num_sms() {
 
 }  // namespace
 
-struct mc_pdf_s {
-  int device = 0, nx = 0, nq = 0, nflav = 0;
-  std::vector<int> pids;
-  std::vector<double> logq2;  // host copy of the Q^2 knots (log)
-  double* d_logx = nullptr;
-  double* d_logq2 = nullptr;
-  double* d_xf64 = nullptr;
-  float* d_xf32 = nullptr;
-  mc::PdfDev dev() const { return {nx, nq, nflav, d_logx, d_logq2, d_xf64, d_xf32}; }
-  int index(int pid) const {
-    for (int i = 0; i < nflav; ++i)
-      if (pids[i] == pid) return i;
-    return -1;
-  }
-};
+#include "handles.h"
 
-struct mc_vegas_s {
-  int device = 0, ndim = 0, nbins = 0, prec = 0;
-  uint64_t seed = 0;
-  uint32_t iteration = 0, gid = 0;
-  double* d_edges = nullptr;
-  float* d_edges32 = nullptr;
-  double* d_hist_w2 = nullptr;
-  unsigned int* d_hist_n = nullptr;
-  BlockPartial* d_partials = nullptr;
-  int max_partials = 0;
-  BlockPartial* d_total = nullptr;
-  BlockPartial* h_total = nullptr;  // pinned
-  cudaEvent_t k0 = nullptr, k1 = nullptr;  // around the last integrand launch
-  bool timed = false;
-};
+namespace mc {
+// Message returned by mc_last_error() for the calling thread.
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace mc
 
 extern "C" {
 

@@ -1,0 +1,44 @@
+// Internal: definitions of the opaque handles of include/mcint.h, shared by
+// the translation units of the C ABI.
+#pragma once
+#include <vector>
+
+#include "../../include/mcint.h"
+#include "launch.h"
+
+namespace mc {
+void set_last_error(const char* msg);  // api.cu
+}
+
+struct mc_pdf_s {
+  int device = 0, nx = 0, nq = 0, nflav = 0;
+  std::vector<int> pids;
+  std::vector<double> logq2;  // host copy of the Q^2 knots (log)
+  double* d_logx = nullptr;
+  double* d_logq2 = nullptr;
+  double* d_xf64 = nullptr;
+  float* d_xf32 = nullptr;
+  mc::PdfDev dev() const { return {nx, nq, nflav, d_logx, d_logq2, d_xf64, d_xf32}; }
+  int index(int pid) const {
+    for (int i = 0; i < nflav; ++i)
+      if (pids[i] == pid) return i;
+    return -1;
+  }
+};
+
+struct mc_vegas_s {
+  int device = 0, ndim = 0, nbins = 0, prec = 0;
+  uint64_t seed = 0;
+  uint32_t iteration = 0, gid = 0;
+  double* d_edges = nullptr;
+  float* d_edges32 = nullptr;
+  double* d_hist_w2 = nullptr;
+  unsigned int* d_hist_n = nullptr;
+  mc::BlockPartial* d_partials = nullptr;
+  int max_partials = 0;
+  mc::BlockPartial* d_total = nullptr;
+  mc::BlockPartial* h_total = nullptr;  // pinned
+  cudaEvent_t k0 = nullptr, k1 = nullptr;  // around the last integrand launch
+  bool timed = false;
+};
+

@@ -27,7 +27,7 @@ REC_STRIDE = 96
 SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_vegas_init", "mc_vegas_free",
            "mc_vegas_set_grid", "mc_vegas_get_grid", "mc_vegas_get_hist", "mc_vegas_set_iteration",
            "mc_vegas_get_iteration", "mc_vegas_set_gid", "mc_vegas_iterate", "mc_vegas_refine", "mc_integrate",
-           "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms")
+           "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms", "mc_vegas_iterate_noalloc")
 
 
 class McError(RuntimeError):
@@ -93,6 +93,8 @@ def lib():
             "mc_launch_shape": [ctypes.POINTER(Integrand), i32, i64, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)],
             "mc_vegas_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_float)],
+            "mc_vegas_iterate_noalloc": [ctypes.POINTER(Integrand), _vp, i32, i32, _vp, _vp, i32, u64, u32, u32,
+                                         i64, i32, _vp, _vp, _vp, _vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -260,6 +262,21 @@ def mc_vegas_kernel_ms(v):
     ms = ctypes.c_float()
     _check(lib().mc_vegas_kernel_ms(v.handle, ctypes.byref(ms)))
     return ms.value
+
+
+MC_NOALLOC_MAX_BLOCKS = 4096
+
+
+def mc_vegas_iterate_noalloc(itg, pdf, ndim, nbins, edges64_dev, edges32_dev, prec, seed, iteration, gid, nevents,
+                             blocks, hist_w2_dev, hist_n_dev, sums_dev, stream=None):
+    """Allocation-free iteration: every buffer is the caller's (device
+    pointers); sums_dev receives mc_device_sums (8 x 8 bytes: sum_hi, sum_lo,
+    sum2_hi, sum2_lo, wmax as FP64, then n_nonzero, n_bad, n_noconv as int64)."""
+    c = _integrand(itg)
+    e32 = _ptr(edges32_dev) if edges32_dev is not None else None
+    _check(lib().mc_vegas_iterate_noalloc(ctypes.byref(c), pdf.handle if pdf else None, ndim, nbins,
+                                          _ptr(edges64_dev), e32, prec, seed, iteration, gid, nevents, blocks,
+                                          _ptr(hist_w2_dev), _ptr(hist_n_dev), _ptr(sums_dev), _stream(stream)))
 
 
 def mc_launch_shape(itg, prec, nevents):
