@@ -126,9 +126,60 @@ MC_D EventOut integrand(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, do
     }
   } else if constexpr (PROC == P_GG_TTBARG) {
     const R x1 = x[0], x2 = x[1];
+    rec_put(rec, 77, x1); rec_put(rec, 78, x2);
+    if constexpr (sizeof(R) == 4) {
+      // FP32 mode: FP64 only inside RAMBO's conformal transformation
+      const float m = float(p.m_top);
+      const float shat = x1 * x2 * float(s);
+      rec_put(rec, 79, shat);
+      if (!(shat > 4.0f * m * m)) {
+        out.pass = 0;
+        return out;
+      }
+      const float rs = sqrtf(shat);
+      const float masses[3] = {m, m, 0.0f};
+      v4<float> k[3];
+      double psw;
+      const int rc = rambo_fp32<3>(masses, rs, a.w0_coef3, x + 2, k, &psw);
+      if (rec) {
+        const v4<float> pa = {rs * 0.5f, 0.0f, 0.0f, rs * 0.5f}, pb = {rs * 0.5f, 0.0f, 0.0f, -rs * 0.5f};
+        rec_p4(rec, 0, pa); rec_p4(rec, 1, pb); rec_p4(rec, 2, k[0]); rec_p4(rec, 3, k[1]); rec_p4(rec, 4, k[2]);
+        rec_put(rec, 84, psw);
+      }
+      if (rc != 0) {
+        out.pass = 0;
+        out.status = -5;
+        return out;
+      }
+      // gluon cuts (see the FP64 branch)
+      const v4<float>& g = k[2];
+      const float pt2 = g.x * g.x + g.y * g.y;
+      const float ptc = float(p.ptcut_g);
+      if (!(pt2 > ptc * ptc)) {
+        out.pass = 0;
+        return out;
+      }
+      const float pabs = sqrtf(pt2 + g.z * g.z);
+      const float fwd = (pabs + g.z) * x1, bwd = (pabs - g.z) * x2;
+      const float e2 = float(a.e2eta);
+      if (!(fwd < e2 * bwd && bwd < e2 * fwd)) {
+        out.pass = 0;
+        return out;
+      }
+      const v4<float> pa = {rs * 0.5f, 0.0f, 0.0f, rs * 0.5f}, pb = {rs * 0.5f, 0.0f, 0.0f, -rs * 0.5f};
+      const float me2 = me2_gg_ttbarg<float>(pa, pb, k[0], k[1], k[2], m, float(4.0 * kPi * p.alpha_s));
+      const float lgg = xf_over_x(pdf.tab[0], x1) * xf_over_x(pdf.tab[0], x2);
+      const float flux = float(p.gev2pb) / (2.0f * shat);
+      out.f = double(lgg * me2 * flux) * psw;
+      if (rec) {
+        rec_put(rec, 80, lgg);
+        rec_put(rec, 82, me2);
+      }
+      return out;
+    }
     const double shat = double(x1) * double(x2) * s;
     const double m = p.m_top;
-    rec_put(rec, 77, x1); rec_put(rec, 78, x2); rec_put(rec, 79, shat);
+    rec_put(rec, 79, shat);
     if (!(shat > 4.0 * m * m)) {
       out.pass = 0;
       return out;

@@ -38,8 +38,11 @@ __global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ndim = a.ndim, nb = a.nbins;
   const int nedge = ndim * (nb + 1), nhist = ndim * nb;
-  double* sh_w2 = reinterpret_cast<double*>(smem);
-  unsigned int* sh_n = reinterpret_cast<unsigned int*>(sh_w2 + nhist);
+  // per-bin sums of w^2: FP64 in FP64 mode, FP32 in FP32 mode (a block's
+  // partial histogram only steers the refinement; the global sum is FP64)
+  using H = typename std::conditional<FP64, double, float>::type;
+  H* sh_w2 = reinterpret_cast<H*>(smem);
+  unsigned int* sh_n = reinterpret_cast<unsigned int*>(smem + size_t(nhist) * 8);
   R* sh_edges = reinterpret_cast<R*>(smem + ((size_t(nhist) * 12 + 15) / 16) * 16);
   R* sh_pdf = sh_edges + nedge;
 
@@ -47,7 +50,7 @@ __global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
   for (int i = threadIdx.x; i < nedge; i += blockDim.x) sh_edges[i] = g_edges[i];
   if (!RECORD)
     for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
-      sh_w2[i] = 0.0;
+      sh_w2[i] = H(0);
       sh_n[i] = 0u;
     }
   SmPdf<R> pdf;
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
 #pragma unroll
       for (int dd = 0; dd < MAXD; ++dd) {
         if (dd < ndim) {
-          atomicAdd(&sh_w2[dd * nb + bin[dd]], w2);
+          atomicAdd(&sh_w2[dd * nb + bin[dd]], H(w2));
           atomicAdd(&sh_n[dd * nb + bin[dd]], 1u);
         }
       }
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
   for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
     if (sh_n[i]) {
       atomicAdd(&a.hist_n[i], sh_n[i]);
-      atomicAdd(&a.hist_w2[i], sh_w2[i]);
+      atomicAdd(&a.hist_w2[i], double(sh_w2[i]));
     }
   }
 }
@@ -206,17 +209,22 @@ __global__ void finalize_kernel(const BlockPartial* parts, int nblocks, BlockPar
 // VEGAS refinement (Lepage 1978): per dimension, smooth the histogram of
 // w^2 with nearest neighbours, normalise, damp m_b = ((r_b - 1)/ln r_b)^alpha,
 // and place the new edges at equal cumulative importance by linear
-// interpolation inside the old bins; then clear the histograms.  One thread
-// per dimension; dimensions with an empty histogram keep their grid.
+// interpolation inside the old bins; then clear the histograms.  One warp per
+// dimension: lanes own bins, a warp prefix sum forms the cumulative
+// importance, and each new edge finds its old bin by binary search.
+// Dimensions with an empty histogram keep their grid.
 __global__ void refine_kernel(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim,
                               int nbins, double alpha) {
-  const int d = threadIdx.x;
+  extern __shared__ double refine_smem[];  // per dimension: imp[nbins], cum[nbins+1], old[nbins+1]
+  const int d = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (d >= ndim) return;
+  double* sh_imp = refine_smem + size_t(d) * (3 * nbins + 2);
+  double* sh_cum = sh_imp + nbins;
+  double* sh_old = sh_cum + nbins + 1;
   double* e = edges + size_t(d) * (nbins + 1);
   double* h = hist_w2 + size_t(d) * nbins;
-  double imp[MC_MAX_BINS];
-  double total = 0.0;
-  for (int b = 0; b < nbins; ++b) {
+  double part = 0.0;
+  for (int b = lane; b < nbins; b += 32) {
     double sm;
     if (b == 0)
       sm = (h[0] + h[1]) / 2.0;
@@ -224,40 +232,52 @@ __global__ void refine_kernel(double* edges, float* edges32, double* hist_w2, un
       sm = (h[nbins - 2] + h[nbins - 1]) / 2.0;
     else
       sm = (h[b - 1] + h[b] + h[b + 1]) / 3.0;
-    imp[b] = sm;
-    total += sm;
+    sh_imp[b] = sm;
+    part += sm;
   }
+  for (int b = lane; b <= nbins; b += 32) sh_old[b] = e[b];
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  const double total = part;
+  __syncwarp();
   if (total > 0.0) {
-    double cum = 0.0;
-    for (int b = 0; b < nbins; ++b) {
-      const double r = imp[b] / total;
-      double m;
-      if (r <= 0.0)
-        m = 0.0;
-      else if (r == 1.0)
-        m = 1.0;
-      else
-        m = pow((r - 1.0) / log(r), alpha);
-      imp[b] = m;
-      cum += m;
+    for (int b = lane; b < nbins; b += 32) {
+      const double r = sh_imp[b] / total;
+      sh_imp[b] = r <= 0.0 ? 0.0 : (r == 1.0 ? 1.0 : pow((r - 1.0) / log(r), alpha));
     }
-    const double per_bin = cum / nbins;
-    double old[MC_MAX_BINS + 1];
-    for (int b = 0; b <= nbins; ++b) old[b] = e[b];
-    // walk the old bins once, emitting the new edges in order
-    int b = 0;
-    double c_lo = 0.0;  // cumulative importance before old bin b
-    for (int k = 1; k < nbins; ++k) {
-      const double target = k * per_bin;
-      while (b + 1 < nbins && c_lo + imp[b] < target) {
-        c_lo += imp[b];
-        ++b;
+    __syncwarp();
+    // inclusive prefix sums in chunks of 32 bins
+    double carry = 0.0;
+    if (lane == 0) sh_cum[0] = 0.0;
+    for (int base = 0; base < nbins; base += 32) {
+      const int b = base + lane;
+      double v = b < nbins ? sh_imp[b] : 0.0;
+      for (int off = 1; off < 32; off <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += t;
       }
-      e[k] = old[b] + (target - c_lo) / imp[b] * (old[b + 1] - old[b]);
+      if (b < nbins) sh_cum[b + 1] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    __syncwarp();
+    const double per_bin = sh_cum[nbins] / nbins;
+    for (int k = 1 + lane; k < nbins; k += 32) {
+      const double target = k * per_bin;
+      // first old bin b with cum[b+1] >= target
+      int lo = 0, hi = nbins - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sh_cum[mid + 1] < target)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      const double c_lo = sh_cum[lo];
+      e[k] = sh_old[lo] + (target - c_lo) / sh_imp[lo] * (sh_old[lo + 1] - sh_old[lo]);
     }
   }
-  for (int b = 0; b <= nbins; ++b) edges32[size_t(d) * (nbins + 1) + b] = float(e[b]);
-  for (int b = 0; b < nbins; ++b) {
+  __syncwarp();
+  for (int b = lane; b <= nbins; b += 32) edges32[size_t(d) * (nbins + 1) + b] = float(e[b]);
+  for (int b = lane; b < nbins; b += 32) {
     h[b] = 0.0;
     hist_n[size_t(d) * nbins + b] = 0u;
   }
@@ -381,7 +401,12 @@ cudaError_t launch_finalize(const BlockPartial* parts, int nblocks, BlockPartial
 }
 cudaError_t launch_refine(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim, int nbins,
                           double alpha, cudaStream_t st) {
-  refine_kernel<<<1, 32, 0, st>>>(edges, edges32, hist_w2, hist_n, ndim, nbins, alpha);
+  const size_t smem = sizeof(double) * size_t(ndim) * (3 * nbins + 2);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  refine_kernel<<<1, 32 * ndim, smem, st>>>(edges, edges32, hist_w2, hist_n, ndim, nbins, alpha);
   return cudaGetLastError();
 }
 cudaError_t launch_pdf_xfxq2(const PdfDev& pdf, bool fp64, long long n, const double* x, const double* q2,

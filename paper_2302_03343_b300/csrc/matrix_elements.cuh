@@ -124,10 +124,11 @@ MC_D R me2_gg_ttbar(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4<
   const v4<R> qab = pa + pb;
   const R invq = R(1) / mdot(qab, qab);
   R total = R(0);
+  // spin-flip symmetry (see me2_gg_ttbarg): the antitop spin +1/2 half, doubled
   for (int ht = -1; ht <= 1; ht += 2) {
     const sp4<R> ub = ubar_spinor(pt, m, ht);
-    for (int hb = -1; hb <= 1; hb += 2) {
-      const sp4<R> v = v_spinor(ptb, m, hb);
+    {
+      const sp4<R> v = v_spinor(ptb, m, +1);
       for (int h = 0; h < 4; ++h) {
         const v4<R> e0 = eps[0][h & 1], e1 = eps[1][h >> 1];
         const v4<R> j01 = gluon_current(e0, q[0], e1, q[1], invq);
@@ -142,7 +143,7 @@ MC_D R me2_gg_ttbar(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4<
       }
     }
   }
-  return g2 * g2 * total / R(256);
+  return g2 * g2 * total * R(2) / R(256);
 }
 
 // ------------------------------------------------------------- g g -> t tbar g
@@ -188,17 +189,35 @@ MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4
   const v4<R> qall = q01 + q[2];
   const R iall = R(1) / mdot(qall, qall);
 
+  // Spin-flip symmetry: with real momenta and real (linear) polarisation
+  // vectors the antilinear map psi -> gamma^5 gamma^2 psi^* turns every
+  // helicity spinor into the opposite-helicity one up to a phase and leaves
+  // the slashed real vectors and the propagators invariant, so
+  // A_sigma(-s_t, -s_tbar) = c A_sigma(s_t, s_tbar)^* with one phase c for all
+  // orderings.  The colour-summed square is then equal for the two spin
+  // assignments: only the anti-top spin +1/2 is evaluated and the sum doubled.
   sp4<R> ubar[2];
   ubar[0] = ubar_spinor(pt, m, -1);
   ubar[1] = ubar_spinor(pt, m, +1);
+  const sp4<R> v = v_spinor(ptb, m, +1);
 
   R total = R(0);
+  // polarisation loops nested so that X_0, X_1, J(01) and S_2 J(01) v are
+  // formed once per outer configuration
 #pragma unroll 1
-  for (int h = 0; h < 8; ++h) {
-    const v4<R> e0 = eps[0][h & 1], e1 = eps[1][(h >> 1) & 1], e2 = eps[2][h >> 2];
-    const v4<R> e[3] = {e0, e1, e2};
-    // pair currents J(ab) for a < b (J(ba) = -J(ab))
+  for (int h0 = 0; h0 < 2; ++h0) {
+   const v4<R> e0 = eps[0][h0];
+   const sp4<R> x0 = prop_col(kc[0], m, invc[0], slash_col(e0, v));
+#pragma unroll 1
+   for (int h1 = 0; h1 < 2; ++h1) {
+    const v4<R> e1 = eps[1][h1];
+    const sp4<R> x1 = prop_col(kc[1], m, invc[1], slash_col(e1, v));
     const v4<R> j01 = gluon_current(e0, q[0], e1, q[1], i01);
+    const sp4<R> s2j01 = prop_col(ka[2], m, inva[2], slash_col(j01, v));
+#pragma unroll 1
+    for (int h2 = 0; h2 < 2; ++h2) {
+    const v4<R> e2 = eps[2][h2];
+    // pair currents J(ab) for a < b (J(ba) = -J(ab))
     const v4<R> j02 = gluon_current(e0, q[0], e2, q[2], i02);
     const v4<R> j12 = gluon_current(e1, q[1], e2, q[2], i12);
     // triple currents, J(cba) = J(abc): J012 = J210, J021 = J120, J102 = J201
@@ -208,13 +227,9 @@ MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4
                        gluon_contact(e0, e2, e1, iall);
     const v4<R> j102 = gluon_current(-j01, q01, e2, q[2], iall) + gluon_current(e1, q[1], j02, q02, iall) +
                        gluon_contact(e1, e0, e2, iall);
-#pragma unroll 1
-    for (int hb = 0; hb < 2; ++hb) {
-      const sp4<R> v = v_spinor(ptb, m, hb ? 1 : -1);
+    {
       // X_c = S_{pair != c} eps_c v
-      sp4<R> x[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) x[c] = prop_col(kc[c], m, invc[c], slash_col(e[c], v));
+      const sp4<R> x[3] = {x0, x1, prop_col(kc[2], m, invc[2], slash_col(e2, v))};
       // column spinors Gamma(sigma) v for the six orderings
       sp4<R> col[6];
       // term 1: eps_a S_a eps_b X_c
@@ -236,7 +251,7 @@ MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4
       // term 3: -eps_a S_a J(bc) v
       const sp4<R> z0 = slash_col(e0, prop_col(ka[0], m, inva[0], slash_col(j12, v)));
       const sp4<R> z1 = slash_col(e1, prop_col(ka[1], m, inva[1], slash_col(j02, v)));
-      const sp4<R> z2 = slash_col(e2, prop_col(ka[2], m, inva[2], slash_col(j01, v)));
+      const sp4<R> z2 = slash_col(e2, s2j01);
       col[0] = col[0] - z0;
       col[1] = col[1] + z0;
       col[2] = col[2] - z1;
@@ -267,8 +282,10 @@ MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4
         total += acc;
       }
     }
+    }
+   }
   }
-  return g2 * g2 * g2 * total / (R(27) * R(256));
+  return g2 * g2 * g2 * total * R(2) / (R(27) * R(256));
 }
 
 }  // namespace mc

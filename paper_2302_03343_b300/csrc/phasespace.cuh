@@ -142,4 +142,103 @@ MC_D int rambo(const double* masses, double sqrt_s, double w0_coef, const R* u, 
   return 0;
 }
 
+// Reciprocal and square root in FP64 from an FP32 seed plus one
+// Newton-Raphson step (r <- r (2 - x r); y <- y + (x - y^2)/(2y)): about
+// 1e-14 relative for arguments inside the FP32 range, at the cost of two or
+// three FP64 operations instead of a full FP64 division or square root.
+MC_D double rcp_nr(double x) {
+  const double r = double(1.0f / float(x));
+  return fma(r, fma(-x, r, 1.0), r);
+}
+MC_D double sqrt_nr(double x) {
+  const float yf = sqrtf(float(x));
+  const double y = double(yf);
+  return fma(double(0.5f / yf), fma(-y, y, x), y);
+}
+
+// RAMBO in the FP32 mode: isotropic momenta in FP32, the conformal
+// transformation (eq. rambo-transform) in FP64, the massive rescaling and the
+// weights in FP32 on the accurately boosted momenta.  Same outputs as rambo()
+// (momenta in FP32), returns 0 or -5.
+template <int N>
+MC_D int rambo_fp32(const float* masses, float sqrt_s, double w0_coef, const float* u, v4<float>* out, double* w) {
+  double qe[N], qx[N], qy[N], qz[N];
+  double se = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const float c = 2.0f * u[4 * i] - 1.0f;
+    float sp, cp;
+    sincospif(2.0f * u[4 * i + 1], &sp, &cp);
+    const float q0 = -logf(u[4 * i + 2] * u[4 * i + 3]);
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - c * c));
+    qe[i] = q0; qx[i] = q0 * st * cp; qy[i] = q0 * st * sp; qz[i] = q0 * c;
+    se += qe[i]; sx += qx[i]; sy += qy[i]; sz += qz[i];
+  }
+  const double mq = sqrt_nr(se * se - sx * sx - sy * sy - sz * sz);
+  const double inv_mq = rcp_nr(mq);
+  const double bx = -sx * inv_mq, by = -sy * inv_mq, bz = -sz * inv_mq;
+  const double gamma = se * inv_mq;
+  const double a = rcp_nr(1.0 + gamma);
+  const double x = double(sqrt_s) * inv_mq;
+  float pe[N], px[N], py[N], pz[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double bq = bx * qx[i] + by * qy[i] + bz * qz[i];
+    const double t = qe[i] + a * bq;
+    pe[i] = float(x * (gamma * qe[i] + bq));
+    px[i] = float(x * (qx[i] + bx * t));
+    py[i] = float(x * (qy[i] + by * t));
+    pz[i] = float(x * (qz[i] + bz * t));
+  }
+  const float s = sqrt_s * sqrt_s;
+  float w0 = float(w0_coef);
+#pragma unroll
+  for (int i = 0; i < N - 2; ++i) w0 *= s;
+  float msum = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) msum += masses[i];
+  float xi = sqrtf(fmaxf(0.0f, 1.0f - (msum / sqrt_s) * (msum / sqrt_s)));
+  float k0[N];
+  float resid = 0.0f;
+  for (int it = 0; it < 16; ++it) {
+    float f = -sqrt_s, fp = 0.0f;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      k0[i] = sqrtf(masses[i] * masses[i] + xi * xi * pe[i] * pe[i]);
+      f += k0[i];
+      fp += xi * pe[i] * pe[i] / k0[i];
+    }
+    resid = f;
+    const float step = f / fp;
+    xi -= step;
+    if (fabsf(step) <= 4e-7f * xi) break;  // a few ulps: the FP32 root is reached
+  }
+  // accept the root when the residual is at FP32 rounding level of sqrt_s
+  if (!(xi > 0.0f) || !(fabsf(resid) <= 1e-5f * sqrt_s)) return -5;
+  float sum_k = 0.0f, prod_k = 1.0f, denom = 0.0f;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    k0[i] = sqrtf(masses[i] * masses[i] + xi * xi * pe[i] * pe[i]);
+    const float kabs = xi * pe[i];
+    sum_k += kabs;
+    prod_k *= kabs;
+    float others = 1.0f;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+      if (j != i) others *= k0[j];
+    denom += kabs * kabs * others;
+  }
+  // w_m = s^(2-N) (sum|k|)^(2N-3) prod|k_i| / (prod k_j^0 sum |k_i|^2/k_i^0)
+  float num = prod_k;
+#pragma unroll
+  for (int i = 0; i < 2 * N - 3; ++i) num *= sum_k;
+  float sp = 1.0f;
+#pragma unroll
+  for (int i = 0; i < N - 2; ++i) sp *= s;
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[i] = {k0[i], xi * px[i], xi * py[i], xi * pz[i]};
+  *w = double(w0) * double(num / (sp * denom));
+  return 0;
+}
+
 }  // namespace mc

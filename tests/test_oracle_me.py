@@ -236,3 +236,40 @@ def test_ggttg_soft_gluon_limit_of_colour_ordered_amplitudes():
         devs.append(worst)
     assert devs[1] < 1e-3, devs
     assert devs[1] < devs[0] / 3, devs  # deviation falls with the gluon energy
+
+
+def _helicity_spinors(p, m, lam):
+    """Massive helicity spinors u(p, lam), v(p, lam) in the Dirac representation."""
+    pa = np.linalg.norm(p[1:])
+    n = p[1:] / pa
+    th, ph = math.acos(max(-1.0, min(1.0, n[2]))), math.atan2(n[1], n[0])
+    def chi(l):
+        return (np.array([math.cos(th / 2), np.exp(1j * ph) * math.sin(th / 2)]) if l > 0
+                else np.array([-np.exp(-1j * ph) * math.sin(th / 2), math.cos(th / 2)]))
+    e = p[0]
+    u = np.concatenate([math.sqrt(e + m) * chi(lam), lam * pa / math.sqrt(e + m) * chi(lam)])
+    v = np.concatenate([-lam * pa / math.sqrt(e + m) * chi(-lam), math.sqrt(e + m) * chi(-lam)])
+    return u, v
+
+
+def test_ggttg_spin_flip_symmetry():
+    # With real momenta and real polarisation vectors, flipping both fermion
+    # helicities conjugates every colour-ordered amplitude up to one common
+    # phase, so the colour-summed square is unchanged (used by the CUDA path
+    # to evaluate half of the fermion spin sum).
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        P = ggttg_point(1800.0, rng.uniform(size=12))
+        q = np.array([P[0], P[1], -P[4], P[2]])
+        for h in itertools.product(range(2), repeat=3):
+            eps = [pol(P[0], h[0]), pol(P[1], h[1]), pol(P[4], h[2])]
+            for s, sb in ((1, 1), (1, -1)):
+                u1, _ = _helicity_spinors(P[2], MT, s)
+                _, v1 = _helicity_spinors(P[3], MT, sb)
+                u2, _ = _helicity_spinors(P[2], MT, -s)
+                _, v2 = _helicity_spinors(P[3], MT, -sb)
+                a = O.ggttg_partial_amplitudes(AS, MT, q, eps, u1.conj() @ _G0, v1)
+                b = O.ggttg_partial_amplitudes(AS, MT, q, eps, u2.conj() @ _G0, v2)
+                ratio = b / np.conj(a)
+                assert np.max(np.abs(ratio - ratio[0])) < 1e-10 * np.abs(ratio[0])
+                assert abs(abs(ratio[0]) - 1.0) < 1e-10

@@ -9,7 +9,7 @@ it through the C ABI twice in a row (two iterations, so the second call runs
 over the scratch the first one left behind) and checks each call against the
 ordinary mc_vegas_iterate on the same iteration: identical bin counts, sums
 within the FP64 tolerance of the other tests (1e-12 relative), histograms
-within 1e-10.  The file is collected last so a failure here cannot hide
+within 1e-10 (FP64 mode) or 1e-5 (FP32 mode, FP32 per-block histograms).  The file is collected last so a failure here cannot hide
 failures elsewhere.
 """
 import numpy as np
@@ -65,7 +65,9 @@ def test_noalloc_matches_iterate_on_two_calls(gpdf, itg, prec, n):
         assert counts[0] == r.n_nonzero and counts[1] + counts[2] == r.n_bad
         np.testing.assert_array_equal(hn.cpu().numpy().astype(np.uint32), n_ref)
         nz = w2_ref > 0
-        assert np.max(np.abs(hw2.cpu().numpy()[nz] - w2_ref[nz]) / w2_ref[nz]) < 1e-10
+        # FP32 mode sums w^2 per block in FP32 shared-memory atomics (order-dependent rounding)
+        htol = 1e-10 if prec == M.MC_FP64 else 1e-5
+        assert np.max(np.abs(hw2.cpu().numpy()[nz] - w2_ref[nz]) / w2_ref[nz]) < htol
         M.mc_vegas_refine(ref, 1.5)  # clears the reference histograms; keep its grid fixed
         M.mc_vegas_set_grid(ref, edges)
     ref.free()
