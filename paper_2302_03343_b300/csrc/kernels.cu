@@ -12,19 +12,12 @@
 #include <type_traits>
 
 #include "../../include/mcint.h"
+#include "event.cuh"
 #include "integrand.cuh"
 #include "launch.h"
+#include "refine.cuh"
 
 namespace mc {
-
-// value = hi + lo pairs: compensated addition of two such pairs
-MC_D void pair_add(double& hi, double& lo, double h2, double l2) {
-  const double s = hi + h2;
-  const double bp = s - hi;
-  const double e = (hi - (s - bp)) + (h2 - bp);
-  hi = s;
-  lo = lo + l2 + e;
-}
 
 template <class R> MC_D const R* edges_of(const KernelArgs& a);
 template <> MC_D const double* edges_of<double>(const KernelArgs& a) { return a.edges64; }
@@ -33,14 +26,13 @@ template <> MC_D const float* edges_of<float>(const KernelArgs& a) { return a.ed
 template <int PROC, bool FP64, bool RECORD>
 __global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
   using R = typename std::conditional<FP64, double, float>::type;
-  constexpr int MAXD = ProcTraits<PROC>::MAXD;
+  // per-bin sums of w^2: FP64 in FP64 mode, FP32 in FP32 mode (a block's
+  // partial histogram only steers the refinement; the global sum is FP64)
+  using H = typename std::conditional<FP64, double, float>::type;
   constexpr int NFL = ProcTraits<PROC>::NFL;
   extern __shared__ __align__(16) unsigned char smem[];
   const int ndim = a.ndim, nb = a.nbins;
   const int nedge = ndim * (nb + 1), nhist = ndim * nb;
-  // per-bin sums of w^2: FP64 in FP64 mode, FP32 in FP32 mode (a block's
-  // partial histogram only steers the refinement; the global sum is FP64)
-  using H = typename std::conditional<FP64, double, float>::type;
   H* sh_w2 = reinterpret_cast<H*>(smem);
   unsigned int* sh_n = reinterpret_cast<unsigned int*>(smem + size_t(nhist) * 8);
   R* sh_edges = reinterpret_cast<R*>(smem + ((size_t(nhist) * 12 + 15) / 16) * 16);
@@ -66,107 +58,15 @@ __global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
     __syncthreads();
   }
 
-  double s_hi = 0.0, s_c = 0.0, q_hi = 0.0, q_c = 0.0, wmax = 0.0;
-  long long nnz = 0, nbad = 0, nnoconv = 0;
+  Acc acc;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-    const uint64_t ev = a.first + uint64_t(i);
-    uint64_t k[MAXD];
-    event_uniforms<MAXD, FP64>(a.seed, a.iteration, a.gid, ev, ndim, k);
-    R x[MAXD];
-    int bin[MAXD];
-    R jac = R(1);
-#pragma unroll
-    for (int dd = 0; dd < MAXD; ++dd) {
-      if (dd < ndim) {
-        R jd;
-        x[dd] = vegas_map_1d<R, FP64>(sh_edges + dd * (nb + 1), nb, k[dd], &bin[dd], &jd);
-        jac *= jd;
-      }
-    }
     double* rec = RECORD ? a.record + size_t(i) * MC_REC_STRIDE : nullptr;
-    const EventOut o = integrand<PROC, R>(a, pdf, x, rec);
-    double w = o.f * double(jac);
-    int status = o.status;
-    if (!isfinite(w)) {
-      status = MC_ENAN;
-      w = 0.0;
-    }
-    if (RECORD) {
-#pragma unroll
-      for (int dd = 0; dd < MAXD; ++dd) {
-        if (dd < ndim) {
-          rec[MC_REC_K + dd] = double(k[dd]);
-          rec[MC_REC_X + dd] = double(x[dd]);
-          rec[MC_REC_BIN + dd] = double(bin[dd]);
-        }
-      }
-      rec[MC_REC_JAC] = double(jac);
-      rec[MC_REC_F] = o.f;
-      rec[MC_REC_W] = w;
-      rec[MC_REC_PASS] = double(o.pass);
-      rec[MC_REC_STATUS] = double(status);
-      continue;
-    }
-    if (status != 0) {
-      if (status == -5)
-        ++nnoconv;
-      else
-        ++nbad;
-    }
-    // Kahan-compensated FP64 sums of w and w^2
-    {
-      const double y = w - s_c;
-      const double t = s_hi + y;
-      s_c = (t - s_hi) - y;
-      s_hi = t;
-      const double w2 = w * w;
-      const double y2 = w2 - q_c;
-      const double t2 = q_hi + y2;
-      q_c = (t2 - q_hi) - y2;
-      q_hi = t2;
-      if (w != 0.0) ++nnz;
-      wmax = fmax(wmax, w);
-#pragma unroll
-      for (int dd = 0; dd < MAXD; ++dd) {
-        if (dd < ndim) {
-          atomicAdd(&sh_w2[dd * nb + bin[dd]], H(w2));
-          atomicAdd(&sh_n[dd * nb + bin[dd]], 1u);
-        }
-      }
-    }
+    process_event<PROC, FP64, RECORD, R, H>(a, pdf, sh_edges, sh_w2, sh_n, a.first + uint64_t(i), rec, acc);
   }
   if (RECORD) return;
-
-  // block reduction: warp shuffles, then one warp over the warp results
-  double lo = -s_c, lo2 = -q_c;  // Kahan compensation -> (hi, lo) pairs
-  for (int off = 16; off > 0; off >>= 1) {
-    const double h2 = __shfl_xor_sync(0xffffffffu, s_hi, off), l2 = __shfl_xor_sync(0xffffffffu, lo, off);
-    pair_add(s_hi, lo, h2, l2);
-    const double g2 = __shfl_xor_sync(0xffffffffu, q_hi, off), m2 = __shfl_xor_sync(0xffffffffu, lo2, off);
-    pair_add(q_hi, lo2, g2, m2);
-    wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, off));
-    nnz += __shfl_xor_sync(0xffffffffu, nnz, off);
-    nbad += __shfl_xor_sync(0xffffffffu, nbad, off);
-    nnoconv += __shfl_xor_sync(0xffffffffu, nnoconv, off);
-  }
   __shared__ BlockPartial warp_part[kBlock / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) warp_part[wid] = {s_hi, lo, q_hi, lo2, wmax, nnz, nbad, nnoconv};
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    BlockPartial b = warp_part[0];
-    for (int w = 1; w < int(blockDim.x / 32); ++w) {
-      const BlockPartial& o = warp_part[w];
-      pair_add(b.sum_hi, b.sum_lo, o.sum_hi, o.sum_lo);
-      pair_add(b.sum2_hi, b.sum2_lo, o.sum2_hi, o.sum2_lo);
-      b.wmax = fmax(b.wmax, o.wmax);
-      b.n_nonzero += o.n_nonzero;
-      b.n_bad += o.n_bad;
-      b.n_noconv += o.n_noconv;
-    }
-    a.partials[blockIdx.x] = b;
-  }
+  block_reduce(acc, warp_part, &a.partials[blockIdx.x]);
   for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
     if (sh_n[i]) {
       atomicAdd(&a.hist_n[i], sh_n[i]);
@@ -179,108 +79,25 @@ __global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
 __global__ void finalize_kernel(const BlockPartial* parts, int nblocks, BlockPartial* out) {
   __shared__ BlockPartial sh[256];
   BlockPartial b = {0.0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0};
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
-    const BlockPartial& o = parts[i];
-    pair_add(b.sum_hi, b.sum_lo, o.sum_hi, o.sum_lo);
-    pair_add(b.sum2_hi, b.sum2_lo, o.sum2_hi, o.sum2_lo);
-    b.wmax = fmax(b.wmax, o.wmax);
-    b.n_nonzero += o.n_nonzero;
-    b.n_bad += o.n_bad;
-    b.n_noconv += o.n_noconv;
-  }
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) partial_add(b, parts[i]);
   sh[threadIdx.x] = b;
   __syncthreads();
   for (int width = blockDim.x / 2; width > 0; width >>= 1) {
-    if (int(threadIdx.x) < width) {
-      BlockPartial& m = sh[threadIdx.x];
-      const BlockPartial& o = sh[threadIdx.x + width];
-      pair_add(m.sum_hi, m.sum_lo, o.sum_hi, o.sum_lo);
-      pair_add(m.sum2_hi, m.sum2_lo, o.sum2_hi, o.sum2_lo);
-      m.wmax = fmax(m.wmax, o.wmax);
-      m.n_nonzero += o.n_nonzero;
-      m.n_bad += o.n_bad;
-      m.n_noconv += o.n_noconv;
-    }
+    if (int(threadIdx.x) < width) partial_add(sh[threadIdx.x], sh[threadIdx.x + width]);
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = sh[0];
 }
 
-// VEGAS refinement (Lepage 1978): per dimension, smooth the histogram of
-// w^2 with nearest neighbours, normalise, damp m_b = ((r_b - 1)/ln r_b)^alpha,
-// and place the new edges at equal cumulative importance by linear
-// interpolation inside the old bins; then clear the histograms.  One warp per
-// dimension: lanes own bins, a warp prefix sum forms the cumulative
-// importance, and each new edge finds its old bin by binary search.
-// Dimensions with an empty histogram keep their grid.
+// Refinement kernel of one grid: one warp per dimension (refine_dimension in
+// refine.cuh); dynamic shared memory ndim * (3 nbins + 2) doubles.
 __global__ void refine_kernel(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim,
                               int nbins, double alpha) {
-  extern __shared__ double refine_smem[];  // per dimension: imp[nbins], cum[nbins+1], old[nbins+1]
-  const int d = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  extern __shared__ double refine_smem[];
+  const int d = threadIdx.x >> 5;
   if (d >= ndim) return;
-  double* sh_imp = refine_smem + size_t(d) * (3 * nbins + 2);
-  double* sh_cum = sh_imp + nbins;
-  double* sh_old = sh_cum + nbins + 1;
-  double* e = edges + size_t(d) * (nbins + 1);
-  double* h = hist_w2 + size_t(d) * nbins;
-  double part = 0.0;
-  for (int b = lane; b < nbins; b += 32) {
-    double sm;
-    if (b == 0)
-      sm = (h[0] + h[1]) / 2.0;
-    else if (b == nbins - 1)
-      sm = (h[nbins - 2] + h[nbins - 1]) / 2.0;
-    else
-      sm = (h[b - 1] + h[b] + h[b + 1]) / 3.0;
-    sh_imp[b] = sm;
-    part += sm;
-  }
-  for (int b = lane; b <= nbins; b += 32) sh_old[b] = e[b];
-  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-  const double total = part;
-  __syncwarp();
-  if (total > 0.0) {
-    for (int b = lane; b < nbins; b += 32) {
-      const double r = sh_imp[b] / total;
-      sh_imp[b] = r <= 0.0 ? 0.0 : (r == 1.0 ? 1.0 : pow((r - 1.0) / log(r), alpha));
-    }
-    __syncwarp();
-    // inclusive prefix sums in chunks of 32 bins
-    double carry = 0.0;
-    if (lane == 0) sh_cum[0] = 0.0;
-    for (int base = 0; base < nbins; base += 32) {
-      const int b = base + lane;
-      double v = b < nbins ? sh_imp[b] : 0.0;
-      for (int off = 1; off < 32; off <<= 1) {
-        const double t = __shfl_up_sync(0xffffffffu, v, off);
-        if (lane >= off) v += t;
-      }
-      if (b < nbins) sh_cum[b + 1] = carry + v;
-      carry += __shfl_sync(0xffffffffu, v, 31);
-    }
-    __syncwarp();
-    const double per_bin = sh_cum[nbins] / nbins;
-    for (int k = 1 + lane; k < nbins; k += 32) {
-      const double target = k * per_bin;
-      // first old bin b with cum[b+1] >= target
-      int lo = 0, hi = nbins - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (sh_cum[mid + 1] < target)
-          lo = mid + 1;
-        else
-          hi = mid;
-      }
-      const double c_lo = sh_cum[lo];
-      e[k] = sh_old[lo] + (target - c_lo) / sh_imp[lo] * (sh_old[lo + 1] - sh_old[lo]);
-    }
-  }
-  __syncwarp();
-  for (int b = lane; b <= nbins; b += 32) edges32[size_t(d) * (nbins + 1) + b] = float(e[b]);
-  for (int b = lane; b < nbins; b += 32) {
-    h[b] = 0.0;
-    hist_n[size_t(d) * nbins + b] = 0u;
-  }
+  refine_dimension(edges + size_t(d) * (nbins + 1), edges32 + size_t(d) * (nbins + 1), hist_w2 + size_t(d) * nbins,
+                   hist_n + size_t(d) * nbins, nbins, alpha, refine_smem + size_t(d) * (3 * nbins + 2));
 }
 
 // Batched xf(x, Q^2) for all flavours: one thread per (point, flavour).
