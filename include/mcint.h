@@ -212,6 +212,39 @@ int mc_vegas_kernel_ms(mc_vegas v, float* ms);
  * library would use for a process (blocks, threads per block). */
 int mc_launch_shape(const mc_integrand* itg, int prec, int64_t nevents, int* blocks, int* threads);
 
+/* ---------------------------------------------------------------- batches
+ * Many integrands of uneven dimension and event count in one persistent
+ * launch per iteration.  The thesis evaluates one integrand at a time over
+ * vectors of events (Sec. "Software design and benchmarks"); here every
+ * integrand keeps its own VEGAS grid, Philox stream (gid = its index) and
+ * histograms, and one iteration of all of them is: the persistent kernel
+ * (blocks pull (integrand, event range) tiles from an atomic counter,
+ * heaviest integrands first), a fixed-order reduction per integrand, the
+ * refinement of every grid, and the advance of the iteration counter, all
+ * captured once in a CUDA graph and replayed.  The first mc_batch_iterate
+ * autotunes the launch: it times one pass for each block size in {64, 128,
+ * 256} and events per thread in {2, 8, 32} (results discarded) and keeps the
+ * fastest.
+ *
+ * mc_batch_create: n (1..256) integrands itgs[n] and event counts nevents[n]
+ * (host), the PDF (needed if any integrand is hadronic; all hadronic
+ * integrands must share mu_f), nbins, seed, precision.  Grids start uniform.
+ * mc_batch_iterate: one iteration of all integrands with damping alpha;
+ * out[n] (host) receives the sums; synchronises `stream`.  Do not call it
+ * while `stream` is being captured.
+ * mc_batch_get_grid: the current grid of integrand i, [ndim_i][nbins+1] host.
+ * mc_batch_shape: the launch shape chosen by the autotuner.
+ * mc_batch_kernel_ms: device time of the last persistent launch.
+ */
+typedef struct mc_batch_s* mc_batch;
+int mc_batch_create(int n, const mc_integrand* itgs, const int64_t* nevents, mc_pdf pdf, int nbins, uint64_t seed,
+                    int prec, mc_batch* out);
+int mc_batch_iterate(mc_batch b, double alpha, void* stream, mc_iter_result* out);
+int mc_batch_get_grid(mc_batch b, int i, double* edges);
+int mc_batch_shape(mc_batch b, int* block, int* events_per_thread, int* grid, int* ntiles);
+int mc_batch_kernel_ms(mc_batch b, float* ms);
+int mc_batch_free(mc_batch b);
+
 /* ------------------------------------------- allocation-free iteration
  * mc_vegas_iterate_noalloc: the same fused iteration as mc_vegas_iterate, for
  * callers that must not allocate device memory while they run: code whose

@@ -154,6 +154,7 @@ __global__ void pdf_xfxq2_kernel(PdfDev pdf, long long n, const double* x, const
 template <int PROC, bool FP64, bool RECORD>
 static cudaError_t launch_one(const KernelArgs& a, int grid, size_t smem, cudaStream_t st) {
   auto k = integrand_kernel<PROC, FP64, RECORD>;
+  (void)cudaGetLastError();  // report only this launch's error below
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -213,12 +214,14 @@ cudaError_t launch_integrand_record(int proc, bool fp64, const KernelArgs& a, in
   return dispatch<true>(proc, fp64, a, grid, smem, st);
 }
 cudaError_t launch_finalize(const BlockPartial* parts, int nblocks, BlockPartial* out, cudaStream_t st) {
+  (void)cudaGetLastError();
   finalize_kernel<<<1, 256, 0, st>>>(parts, nblocks, out);
   return cudaGetLastError();
 }
 cudaError_t launch_refine(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim, int nbins,
                           double alpha, cudaStream_t st) {
   const size_t smem = sizeof(double) * size_t(ndim) * (3 * nbins + 2);
+  (void)cudaGetLastError();
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -230,6 +233,7 @@ cudaError_t launch_pdf_xfxq2(const PdfDev& pdf, bool fp64, long long n, const do
                              double* out, cudaStream_t st) {
   const long long total = n * pdf.nflav;
   if (total == 0) return cudaSuccess;
+  (void)cudaGetLastError();
   const int block = 256;
   const long long grid = (total + block - 1) / block;
   if (fp64)

@@ -27,7 +27,9 @@ REC_STRIDE = 96
 SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_vegas_init", "mc_vegas_free",
            "mc_vegas_set_grid", "mc_vegas_get_grid", "mc_vegas_get_hist", "mc_vegas_set_iteration",
            "mc_vegas_get_iteration", "mc_vegas_set_gid", "mc_vegas_iterate", "mc_vegas_refine", "mc_integrate",
-           "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms", "mc_vegas_iterate_noalloc")
+           "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms", "mc_vegas_iterate_noalloc",
+           "mc_batch_create", "mc_batch_iterate", "mc_batch_get_grid", "mc_batch_shape", "mc_batch_kernel_ms",
+           "mc_batch_free")
 
 
 class McError(RuntimeError):
@@ -93,6 +95,13 @@ def lib():
             "mc_launch_shape": [ctypes.POINTER(Integrand), i32, i64, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)],
             "mc_vegas_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_float)],
+            "mc_batch_create": [i32, ctypes.POINTER(Integrand), ctypes.POINTER(ctypes.c_int64), _vp, i32, u64, i32,
+                                ctypes.POINTER(_vp)],
+            "mc_batch_iterate": [_vp, d, _vp, ctypes.POINTER(IterResult)],
+            "mc_batch_get_grid": [_vp, i32, _dp],
+            "mc_batch_shape": [_vp] + [ctypes.POINTER(ctypes.c_int)] * 4,
+            "mc_batch_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_float)],
+            "mc_batch_free": [_vp],
             "mc_vegas_iterate_noalloc": [ctypes.POINTER(Integrand), _vp, i32, i32, _vp, _vp, i32, u64, u32, u32,
                                          i64, i32, _vp, _vp, _vp, _vp],
         }
@@ -262,6 +271,61 @@ def mc_vegas_kernel_ms(v):
     ms = ctypes.c_float()
     _check(lib().mc_vegas_kernel_ms(v.handle, ctypes.byref(ms)))
     return ms.value
+
+
+class Batch:
+    """Owns an mc_batch handle (many integrands, one persistent launch per iteration)."""
+
+    def __init__(self, handle, ndims, nbins):
+        self.handle, self.ndims, self.nbins = handle, ndims, nbins
+
+    def free(self):
+        if self.handle:
+            _check(lib().mc_batch_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mc_batch_create(itgs, nevents, pdf, nbins=50, seed=0, prec=MC_FP32_KAHAN):
+    n = len(itgs)
+    arr = (Integrand * n)(*[_integrand(t) for t in itgs])
+    ev = (ctypes.c_int64 * n)(*[int(x) for x in nevents])
+    h = _vp()
+    _check(lib().mc_batch_create(n, arr, ev, pdf.handle if pdf else None, nbins, seed, prec, ctypes.byref(h)))
+    return Batch(h, [t.ndim() for t in itgs], nbins)
+
+
+def mc_batch_iterate(b, alpha=1.5, stream=None):
+    out = (IterResult * len(b.ndims))()
+    _check(lib().mc_batch_iterate(b.handle, alpha, _stream(stream), out))
+    return [out[i] for i in range(len(b.ndims))]
+
+
+def mc_batch_get_grid(b, i):
+    e = np.zeros((b.ndims[i], b.nbins + 1))
+    _check(lib().mc_batch_get_grid(b.handle, i, e.ctypes.data_as(_dp)))
+    return e
+
+
+def mc_batch_shape(b):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().mc_batch_shape(b.handle, *[ctypes.byref(x) for x in v]))
+    return dict(block=v[0].value, events_per_thread=v[1].value, grid=v[2].value, ntiles=v[3].value)
+
+
+def mc_batch_kernel_ms(b):
+    ms = ctypes.c_float()
+    _check(lib().mc_batch_kernel_ms(b.handle, ctypes.byref(ms)))
+    return ms.value
+
+
+def mc_batch_free(b):
+    b.free()
 
 
 MC_NOALLOC_MAX_BLOCKS = 4096
