@@ -56,6 +56,7 @@ extern "C" {
 #define MC_PP_TTBAR 1   /* p p -> t tbar (gg + q qbar), 4 dims                   */
 #define MC_GG_TTBARG 2  /* g g -> t tbar g, RAMBO, 14 dims (7 physical)          */
 #define MC_GAUSS 3      /* normalised Gaussian centred at 1/2, gauss_dim dims     */
+#define MC_GG_TTBARG_7D 4 /* g g -> t tbar g, hierarchical 2->3 generator, 7 dims */
 
 #define MC_MAX_DIM 16
 #define MC_MAX_BINS 256
@@ -65,7 +66,7 @@ typedef struct mc_vegas_s* mc_vegas;
 
 /* One integrand.  Field order is part of the ABI. */
 typedef struct {
-  int32_t proc;        /* MC_EE_MUMU ... MC_GAUSS                                */
+  int32_t proc;        /* MC_EE_MUMU ... MC_GG_TTBARG_7D                         */
   int32_t gauss_dim;   /* dimension of MC_GAUSS (1..16), ignored otherwise       */
   double sqrt_s;       /* collider (or e+e-) centre-of-mass energy              */
   double m_top;        /* top-quark mass                                         */

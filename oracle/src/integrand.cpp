@@ -41,6 +41,7 @@ int process_ndim(const orc_integrand& in) {
     case PP_TTBAR: return 4;
     case GG_TTBARG: return 14;
     case GAUSS: return in.gauss_dim;
+    case GG_TTBARG_7D: return 7;
   }
   return -1;
 }
@@ -106,7 +107,8 @@ static double integrand_value(const orc_integrand& in, const Pdf* pdf, const dou
       rec->ps_weight = w;
       return (rec->lumi * rec->me2 + lqq * rec->me2_qq) / (2.0 * shat) * w * in.gev2pb;
     }
-    case GG_TTBARG: {
+    case GG_TTBARG:
+    case GG_TTBARG_7D: {
       const double x1 = x[0], x2 = x[1], shat = x1 * x2 * s, m = in.m_top;
       rec->x1 = x1;
       rec->x2 = x2;
@@ -121,7 +123,9 @@ static double integrand_value(const orc_integrand& in, const Pdf* pdf, const dou
       p[0] = {rs / 2.0, 0.0, 0.0, rs / 2.0};
       p[1] = {rs / 2.0, 0.0, 0.0, -rs / 2.0};
       double w;
-      const int rc = rambo(3, masses, rs, x + 2, p + 2, &w);
+      // RAMBO (Sec. "RAMBO") or sequential branchings (table tab:hierarchical)
+      const int rc = in.proc == GG_TTBARG ? rambo(3, masses, rs, x + 2, p + 2, &w)
+                                          : hierarchical(3, masses, rs, x + 2, p + 2, &w);
       for (int i = 0; i < 5; ++i) put(rec->p, i, p[i]);
       rec->ps_weight = w;
       if (rc != 0) {

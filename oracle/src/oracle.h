@@ -84,7 +84,7 @@ void ggttg_partial_amplitudes(double alpha_s, double mt, const P4* q_in, const c
                               int ngluon, const cplx* ubar, const cplx* v, cplx* amps);
 
 // ---------------------------------------------------------------- integrand
-enum Process { EE_MUMU = 0, PP_TTBAR = 1, GG_TTBARG = 2, GAUSS = 3 };
+enum Process { EE_MUMU = 0, PP_TTBAR = 1, GG_TTBARG = 2, GAUSS = 3, GG_TTBARG_7D = 4 };
 
 }  // namespace orc
 

@@ -45,6 +45,7 @@ int process_ndim(const mc_integrand* itg) {
     case MC_PP_TTBAR: return 4;
     case MC_GG_TTBARG: return 14;
     case MC_GAUSS: return itg->gauss_dim;
+    case MC_GG_TTBARG_7D: return 7;
   }
   return -1;
 }
@@ -273,10 +274,10 @@ static int prepare(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, KernelArgs* 
   int dev;
   if (int rc = current_device(&dev)) return rc;
   if (dev != v->device) return fail(MC_EINVAL, "grid lives on device %d, current device is %d", v->device, dev);
-  if (itg->proc < MC_EE_MUMU || itg->proc > MC_GAUSS) return fail(MC_EINVAL, "unknown process %d", itg->proc);
+  if (itg->proc < MC_EE_MUMU || itg->proc > MC_GG_TTBARG_7D) return fail(MC_EINVAL, "unknown process %d", itg->proc);
   const int nd = process_ndim(itg);
   if (nd != v->ndim) return fail(MC_EINVAL, "process needs %d dimensions, grid has %d", nd, v->ndim);
-  const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG;
+  const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG || itg->proc == MC_GG_TTBARG_7D;
   if (!(itg->sqrt_s > 0.0) && itg->proc != MC_GAUSS) return fail(MC_EINVAL, "sqrt_s must be positive");
   if (itg->proc == MC_GAUSS && !(itg->gauss_sigma > 0.0)) return fail(MC_EINVAL, "gauss_sigma must be positive");
   std::memset(a, 0, sizeof(*a));

@@ -126,6 +126,11 @@ __global__ void __launch_bounds__(BLOCK) batch_kernel(BatchArgs b) {
         for (long long i = start + threadIdx.x; i < end; i += BLOCK)
           process_event<P_GG_TTBARG, FP64, false, R, H>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i), nullptr, acc);
         break;
+      case P_GG_TTBARG_7D:
+        for (long long i = start + threadIdx.x; i < end; i += BLOCK)
+          process_event<P_GG_TTBARG_7D, FP64, false, R, H>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i), nullptr,
+                                                           acc);
+        break;
       default:
         for (long long i = start + threadIdx.x; i < end; i += BLOCK)
           process_event<P_GAUSS, FP64, false, R, H>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i), nullptr, acc);
@@ -212,7 +217,8 @@ int batch_blocks_per_sm(bool fp64, int block, size_t smem) {
 // (heaviest integrands first) so the launch ends with cheap tiles.
 double event_cost(int proc) {
   switch (proc) {
-    case P_GG_TTBARG: return 100.0;
+    case P_GG_TTBARG:
+    case P_GG_TTBARG_7D: return 100.0;
     case P_PP_TTBAR: return 10.0;
     case P_EE_MUMU: return 2.0;
   }
@@ -439,12 +445,13 @@ int mc_batch_create(int n, const mc_integrand* itgs, const int64_t* nevents, mc_
       case MC_PP_TTBAR: nd = 4; break;
       case MC_GG_TTBARG: nd = 14; break;
       case MC_GAUSS: nd = t.gauss_dim; break;
+      case MC_GG_TTBARG_7D: nd = 7; break;
     }
     if (nd < 1 || nd > MC_MAX_DIM || nevents[i] < 0) {
       mc_batch_free(b);
       return bfail(MC_EINVAL, "mc_batch_create: bad integrand or event count");
     }
-    if (t.proc == MC_PP_TTBAR || t.proc == MC_GG_TTBARG) {
+    if (t.proc == MC_PP_TTBAR || t.proc == MC_GG_TTBARG || t.proc == MC_GG_TTBARG_7D) {
       if (!pdf || pdf->device != dev) {
         mc_batch_free(b);
         return bfail(MC_EINVAL, "mc_batch_create: hadronic integrands need a PDF on this device");

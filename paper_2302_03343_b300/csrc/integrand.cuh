@@ -11,13 +11,14 @@
 
 namespace mc {
 
-enum : int { P_EE_MUMU = 0, P_PP_TTBAR = 1, P_GG_TTBARG = 2, P_GAUSS = 3 };
+enum : int { P_EE_MUMU = 0, P_PP_TTBAR = 1, P_GG_TTBARG = 2, P_GAUSS = 3, P_GG_TTBARG_7D = 4 };
 
 template <int PROC> struct ProcTraits;
 template <> struct ProcTraits<P_EE_MUMU> { static constexpr int MAXD = 2, NFL = 0; };
 template <> struct ProcTraits<P_PP_TTBAR> { static constexpr int MAXD = 4, NFL = 11; };
 template <> struct ProcTraits<P_GG_TTBARG> { static constexpr int MAXD = 14, NFL = 1; };
 template <> struct ProcTraits<P_GAUSS> { static constexpr int MAXD = 16, NFL = 0; };
+template <> struct ProcTraits<P_GG_TTBARG_7D> { static constexpr int MAXD = 7, NFL = 1; };
 
 // Arguments of one launch of the fused kernel (passed by value).
 struct BlockPartial {
@@ -124,73 +125,37 @@ MC_D EventOut integrand(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, do
       rec_put(rec, 80, lgg); rec_put(rec, 81, lqq); rec_put(rec, 82, megg); rec_put(rec, 83, meqq);
       rec_put(rec, 84, psw);
     }
-  } else if constexpr (PROC == P_GG_TTBARG) {
+  } else if constexpr (PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D) {
+    // gg -> t tbar g: RAMBO (14 dims) or the hierarchical generator (7 dims)
     const R x1 = x[0], x2 = x[1];
     rec_put(rec, 77, x1); rec_put(rec, 78, x2);
-    if constexpr (sizeof(R) == 4) {
-      // FP32 mode: FP64 only inside RAMBO's conformal transformation
-      const float m = float(p.m_top);
-      const float shat = x1 * x2 * float(s);
-      rec_put(rec, 79, shat);
-      if (!(shat > 4.0f * m * m)) {
-        out.pass = 0;
-        return out;
-      }
-      const float rs = sqrtf(shat);
-      const float masses[3] = {m, m, 0.0f};
-      v4<float> k[3];
-      double psw;
-      const int rc = rambo_fp32<3>(masses, rs, a.w0_coef3, x + 2, k, &psw);
-      if (rec) {
-        const v4<float> pa = {rs * 0.5f, 0.0f, 0.0f, rs * 0.5f}, pb = {rs * 0.5f, 0.0f, 0.0f, -rs * 0.5f};
-        rec_p4(rec, 0, pa); rec_p4(rec, 1, pb); rec_p4(rec, 2, k[0]); rec_p4(rec, 3, k[1]); rec_p4(rec, 4, k[2]);
-        rec_put(rec, 84, psw);
-      }
-      if (rc != 0) {
-        out.pass = 0;
-        out.status = -5;
-        return out;
-      }
-      // gluon cuts (see the FP64 branch)
-      const v4<float>& g = k[2];
-      const float pt2 = g.x * g.x + g.y * g.y;
-      const float ptc = float(p.ptcut_g);
-      if (!(pt2 > ptc * ptc)) {
-        out.pass = 0;
-        return out;
-      }
-      const float pabs = sqrtf(pt2 + g.z * g.z);
-      const float fwd = (pabs + g.z) * x1, bwd = (pabs - g.z) * x2;
-      const float e2 = float(a.e2eta);
-      if (!(fwd < e2 * bwd && bwd < e2 * fwd)) {
-        out.pass = 0;
-        return out;
-      }
-      const v4<float> pa = {rs * 0.5f, 0.0f, 0.0f, rs * 0.5f}, pb = {rs * 0.5f, 0.0f, 0.0f, -rs * 0.5f};
-      const float me2 = me2_gg_ttbarg<float>(pa, pb, k[0], k[1], k[2], m, float(4.0 * kPi * p.alpha_s));
-      const float lgg = xf_over_x(pdf.tab[0], x1) * xf_over_x(pdf.tab[0], x2);
-      const float flux = float(p.gev2pb) / (2.0f * shat);
-      out.f = double(lgg * me2 * flux) * psw;
-      if (rec) {
-        rec_put(rec, 80, lgg);
-        rec_put(rec, 82, me2);
-      }
-      return out;
-    }
-    const double shat = double(x1) * double(x2) * s;
-    const double m = p.m_top;
+    const R m = R(p.m_top);
+    const R shat = sizeof(R) == 4 ? R(x1 * x2 * R(s)) : R(double(x1) * double(x2) * s);
     rec_put(rec, 79, shat);
-    if (!(shat > 4.0 * m * m)) {
+    if (!(shat > R(4) * m * m)) {
       out.pass = 0;
       return out;
     }
-    const double rs = sqrt(shat);
-    const double masses[3] = {m, m, 0.0};
-    v4<double> k[3];
+    const R rs = m_sqrt(shat);
+    v4<R> k[3];
     double psw;
-    const int rc = rambo<R, 3>(masses, rs, a.w0_coef3, x + 2, k, &psw);
+    int rc = 0;
+    if constexpr (PROC == P_GG_TTBARG_7D) {
+      v4<double> kd[3];
+      hierarchical3<R>(double(m), double(rs), x + 2, kd, &psw);
+      for (int i = 0; i < 3; ++i) k[i] = vcast<R>(kd[i]);
+    } else if constexpr (sizeof(R) == 4) {
+      // FP32 mode: FP64 only inside RAMBO's conformal transformation
+      const float masses[3] = {m, m, 0.0f};
+      rc = rambo_fp32<3>(masses, rs, a.w0_coef3, x + 2, k, &psw);
+    } else {
+      const double masses[3] = {double(m), double(m), 0.0};
+      v4<double> kd[3];
+      rc = rambo<R, 3>(masses, double(rs), a.w0_coef3, x + 2, kd, &psw);
+      for (int i = 0; i < 3; ++i) k[i] = vcast<R>(kd[i]);
+    }
+    const v4<R> pa = {rs * R(0.5), R(0), R(0), rs * R(0.5)}, pb = {rs * R(0.5), R(0), R(0), -rs * R(0.5)};
     if (rec) {
-      const v4<double> pa = {rs * 0.5, 0.0, 0.0, rs * 0.5}, pb = {rs * 0.5, 0.0, 0.0, -rs * 0.5};
       rec_p4(rec, 0, pa); rec_p4(rec, 1, pb); rec_p4(rec, 2, k[0]); rec_p4(rec, 3, k[1]); rec_p4(rec, 4, k[2]);
       rec_put(rec, 84, psw);
     }
@@ -199,27 +164,29 @@ MC_D EventOut integrand(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, do
       out.status = -5;
       return out;
     }
-    // gluon cuts in the lab frame (FP64): pT > cut and |eta_cm + y| < cut with
+    // gluon cuts in the lab frame: pT > cut and |eta_cm + y| < cut with
     // y = ln(x1/x2)/2, written without logarithms:
     // e^{-2c} (|p| - pz) x2 < (|p| + pz) x1 < e^{2c} (|p| - pz) x2.
-    const v4<double>& g = k[2];
-    const double pt2 = g.x * g.x + g.y * g.y;
-    if (!(pt2 > p.ptcut_g * p.ptcut_g)) {
+    const v4<R>& g = k[2];
+    const R pt2 = g.x * g.x + g.y * g.y;
+    const R ptc = R(p.ptcut_g);
+    if (!(pt2 > ptc * ptc)) {
       out.pass = 0;
       return out;
     }
-    const double pabs = sqrt(pt2 + g.z * g.z);
-    const double fwd = (pabs + g.z) * double(x1), bwd = (pabs - g.z) * double(x2);
-    if (!(fwd < a.e2eta * bwd && bwd < a.e2eta * fwd)) {
+    const R pabs = m_sqrt(pt2 + g.z * g.z);
+    const R fwd = (pabs + g.z) * x1, bwd = (pabs - g.z) * x2;
+    const R e2 = R(a.e2eta);
+    if (!(fwd < e2 * bwd && bwd < e2 * fwd)) {
       out.pass = 0;
       return out;
     }
-    const R rsr = R(rs);
-    const v4<R> pa = {rsr * R(0.5), R(0), R(0), rsr * R(0.5)}, pb = {rsr * R(0.5), R(0), R(0), -rsr * R(0.5)};
-    const R me2 = me2_gg_ttbarg<R>(pa, pb, vcast<R>(k[0]), vcast<R>(k[1]), vcast<R>(k[2]), R(m),
-                                   R(4.0 * kPi * p.alpha_s));
+    const R me2 = me2_gg_ttbarg<R>(pa, pb, k[0], k[1], k[2], m, R(4.0 * kPi * p.alpha_s));
     const R lgg = xf_over_x(pdf.tab[0], x1) * xf_over_x(pdf.tab[0], x2);
-    out.f = double(lgg) * double(me2) / (2.0 * shat) * psw * p.gev2pb;
+    if (sizeof(R) == 4)
+      out.f = double(lgg * me2 * (R(p.gev2pb) / (R(2) * shat))) * psw;
+    else
+      out.f = double(lgg) * double(me2) / (2.0 * double(shat)) * psw * p.gev2pb;
     if (rec) {
       rec_put(rec, 80, lgg);
       rec_put(rec, 82, me2);

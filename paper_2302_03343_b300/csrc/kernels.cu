@@ -178,13 +178,16 @@ static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, 
     case P_GAUSS:
       return fp64 ? launch_one<P_GAUSS, true, RECORD>(a, grid, smem, st)
                   : launch_one<P_GAUSS, false, RECORD>(a, grid, smem, st);
+    case P_GG_TTBARG_7D:
+      return fp64 ? launch_one<P_GG_TTBARG_7D, true, RECORD>(a, grid, smem, st)
+                  : launch_one<P_GG_TTBARG_7D, false, RECORD>(a, grid, smem, st);
   }
   return cudaErrorInvalidValue;
 }
 
 size_t integrand_smem(int proc, bool fp64, int ndim, int nbins, int nx) {
   const size_t r = fp64 ? 8 : 4;
-  const int nfl = proc == P_PP_TTBAR ? 11 : (proc == P_GG_TTBARG ? 1 : 0);
+  const int nfl = proc == P_PP_TTBAR ? 11 : ((proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D) ? 1 : 0);
   const size_t hist = ((size_t(ndim) * nbins * 12 + 15) / 16) * 16;
   return hist + r * (size_t(ndim) * (nbins + 1) + (nfl > 0 ? size_t(nx) * (1 + 2 * nfl) : 0));
 }
@@ -199,6 +202,7 @@ int integrand_max_blocks_per_sm(int proc, bool fp64, size_t smem) {
     case P_EE_MUMU: MC_OCC(P_EE_MUMU); break;
     case P_PP_TTBAR: MC_OCC(P_PP_TTBAR); break;
     case P_GG_TTBARG: MC_OCC(P_GG_TTBARG); break;
+    case P_GG_TTBARG_7D: MC_OCC(P_GG_TTBARG_7D); break;
     default: MC_OCC(P_GAUSS); break;
   }
 #undef MC_OCC

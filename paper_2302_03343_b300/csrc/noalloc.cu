@@ -40,6 +40,7 @@ int ndim_of(const mc_integrand* itg) {
     case MC_PP_TTBAR: return 4;
     case MC_GG_TTBARG: return 14;
     case MC_GAUSS: return itg->gauss_dim;
+    case MC_GG_TTBARG_7D: return 7;
   }
   return -1;
 }
@@ -64,7 +65,7 @@ extern "C" int mc_vegas_iterate_noalloc(const mc_integrand* itg, mc_pdf pdf, int
   if (blocks < 0 || blocks > MC_NOALLOC_MAX_BLOCKS)
     return reject(MC_EINVAL, "blocks exceeds MC_NOALLOC_MAX_BLOCKS (the size of the static scratch)");
   if (gid > 255) return reject(MC_EINVAL, "gid outside 0..255");
-  const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG;
+  const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG || itg->proc == MC_GG_TTBARG_7D;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return reject(MC_ECUDA, "no device");
   mc::BlockPartial* scratch = nullptr;

@@ -241,4 +241,39 @@ MC_D int rambo_fp32(const float* masses, float sqrt_s, double w0_coef, const flo
   return 0;
 }
 
+// Three-body phase space by sequential two-body branchings (thesis table
+// tab:hierarchical, n = 3): P -> p3 (massless gluon) + q2 (mass M2), then
+// q2 -> p2 + p1 (top pair of mass m each) in the rest frame of q2, boosted
+// back.  Uniforms: u0 -> phi_3, u1 -> cos theta_3, u2 -> M2 in [2m, sqrt_s],
+// u3 -> phi_2, u4 -> cos theta_2.  Weight per unit hypercube (re-derived from
+// eq. 2bodyps and eq. sequential-splitting, the printed eq. sequential-weight
+// not being dimensionless):
+//   w = pi^-3 4^-2 / sqrt_s * (sqrt_s - 2m) * |p*_2| |p*_3|.
+// p[0] = top, p[1] = anti-top, p[2] = gluon, FP64.
+template <class R>
+MC_D void hierarchical3(double m, double sqrt_s, const R* u, v4<double>* p, double* w) {
+  R s3, c3p, s2, c2p;
+  m_sincos2pi(u[0], &s3, &c3p);
+  m_sincos2pi(u[3], &s2, &c2p);
+  const double c3 = 2.0 * double(u[1]) - 1.0, c2 = 2.0 * double(u[4]) - 1.0;
+  const double st3 = sqrt(fmax(0.0, 1.0 - c3 * c3)), st2 = sqrt(fmax(0.0, 1.0 - c2 * c2));
+  const double s = sqrt_s * sqrt_s;
+  const double m2 = 2.0 * m + double(u[2]) * (sqrt_s - 2.0 * m);
+  const double p3 = (s - m2 * m2) / (2.0 * sqrt_s);
+  const double n3x = st3 * double(c3p), n3y = st3 * double(s3), n3z = c3;
+  p[2] = {p3, p3 * n3x, p3 * n3y, p3 * n3z};
+  const v4<double> q = {sqrt(p3 * p3 + m2 * m2), -p3 * n3x, -p3 * n3y, -p3 * n3z};
+  const double p2 = 0.5 * m2 * sqrt(fmax(0.0, 1.0 - 4.0 * m * m / (m2 * m2)));
+  const double e2 = sqrt(p2 * p2 + m * m);
+  const double n2x = st2 * double(c2p), n2y = st2 * double(s2), n2z = c2;
+  // boost (e, +-p2 n2) from the rest frame of q (mass m2) to the lab
+  const double qn = q.x * n2x + q.y * n2y + q.z * n2z;
+  const double inv_m2 = 1.0 / m2;
+  const double ea = (q.e * e2 + p2 * qn) * inv_m2, eb = (q.e * e2 - p2 * qn) * inv_m2;
+  const double fa = (e2 + ea) / (q.e + m2), fb = (e2 + eb) / (q.e + m2);
+  p[1] = {ea, p2 * n2x + fa * q.x, p2 * n2y + fa * q.y, p2 * n2z + fa * q.z};
+  p[0] = {eb, -p2 * n2x + fb * q.x, -p2 * n2y + fb * q.y, -p2 * n2z + fb * q.z};
+  *w = (sqrt_s - 2.0 * m) * p2 * p3 / (kPi * kPi * kPi * 16.0 * sqrt_s);
+}
+
 }  // namespace mc

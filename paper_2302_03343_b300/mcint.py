@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmcint.so
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ENAN, MC_ENOCONV, MC_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 MC_FP64, MC_FP32_KAHAN = 0, 1
-MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS = 0, 1, 2, 3
+MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS, MC_GG_TTBARG_7D = 0, 1, 2, 3, 4
 MC_MAX_DIM, MC_MAX_BINS = 16, 256
 REC = dict(K=0, X=16, BIN=32, JAC=48, P=49, X1=77, X2=78, SHAT=79, LUMI=80, LUMI_QQ=81, ME2=82, ME2_QQ=83,
            PSW=84, F=85, W=86, PASS=87, STATUS=88)

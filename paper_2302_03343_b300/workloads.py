@@ -20,7 +20,7 @@ import numpy as np
 PIDS = (-5, -4, -3, -2, -1, 21, 1, 2, 3, 4, 5)
 GEV2_TO_PB = 0.3893794e9
 
-EE_MUMU, PP_TTBAR, GG_TTBARG, GAUSS = 0, 1, 2, 3
+EE_MUMU, PP_TTBAR, GG_TTBARG, GAUSS, GG_TTBARG_7D = 0, 1, 2, 3, 4
 FP64, FP32 = 0, 1
 
 
@@ -91,7 +91,7 @@ class Integrand:
     gev2pb: float = GEV2_TO_PB
 
     def ndim(self):
-        return {EE_MUMU: 2, PP_TTBAR: 4, GG_TTBARG: 14}.get(self.proc, self.gauss_dim)
+        return {EE_MUMU: 2, PP_TTBAR: 4, GG_TTBARG: 14, GG_TTBARG_7D: 7}.get(self.proc, self.gauss_dim)
 
     def asdict(self):
         return asdict(self)
@@ -110,6 +110,11 @@ def pp_ttbar(sqrt_s=13000.0):
 def gg_ttbarg(sqrt_s=13000.0):
     """gg -> t tbar g with RAMBO (2 + 12 dims), gluon pT > 20 GeV, |eta| < 2.5."""
     return Integrand(proc=GG_TTBARG, sqrt_s=sqrt_s)
+
+
+def gg_ttbarg_7d(sqrt_s=13000.0):
+    """gg -> t tbar g with the hierarchical three-body generator (2 + 5 = 7 dims), same cuts."""
+    return Integrand(proc=GG_TTBARG_7D, sqrt_s=sqrt_s)
 
 
 def gauss(dim, sigma=0.1):

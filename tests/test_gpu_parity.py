@@ -20,7 +20,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 R = M.REC
-PROCS = {"ee": W.ee_mumu(91.0), "pp": W.pp_ttbar(), "gg": W.gg_ttbarg(), "gauss": W.gauss(6)}
+PROCS = {"ee": W.ee_mumu(91.0), "pp": W.pp_ttbar(), "gg": W.gg_ttbarg(), "gg7": W.gg_ttbarg_7d(),
+         "gauss": W.gauss(6)}
 
 
 @pytest.fixture(scope="module")
@@ -88,7 +89,7 @@ def test_counter_high_word(gpu, oracle_pdf):
 
 
 # ------------------------------------------------------------------ per-event FP64
-@pytest.mark.parametrize("name,k", [("ee", 2000), ("pp", 2000), ("gg", 600), ("gauss", 2000)])
+@pytest.mark.parametrize("name,k", [("ee", 2000), ("pp", 2000), ("gg", 600), ("gg7", 600), ("gauss", 2000)])
 def test_fp64_event_weights(gpu, oracle_pdf, name, k):
     itg = PROCS[name]
     nd = itg.ndim()
@@ -104,7 +105,7 @@ def test_fp64_event_weights(gpu, oracle_pdf, name, k):
     assert np.max(rel(w_g[nz], w_o[nz]), initial=0) < 1e-12
     x_o = np.array([list(r.x)[:nd] for r in recs])
     assert np.max(np.abs(g[:, R["X"]:R["X"] + nd] - x_o)) < 1e-15
-    if name in ("pp", "gg"):
+    if name in ("pp", "gg", "gg7"):
         ok = pass_o == 1
         assert np.max(rel(g[ok, R["ME2"]], [r.me2 for r, o in zip(recs, ok) if o])) < 1e-12
         # luminosities: relative 1e-12, except where the interpolant crosses
@@ -126,7 +127,7 @@ def test_fp64_event_weights(gpu, oracle_pdf, name, k):
 
 
 # ------------------------------------------------------------------ per-event FP32
-@pytest.mark.parametrize("name,k", [("ee", 4000), ("pp", 4000), ("gg", 1500), ("gauss", 4000)])
+@pytest.mark.parametrize("name,k", [("ee", 4000), ("pp", 4000), ("gg", 1500), ("gg7", 1500), ("gauss", 4000)])
 def test_fp32_event_weights_error_statistics(gpu, oracle_pdf, name, k):
     itg = PROCS[name]
     nd = itg.ndim()
@@ -147,7 +148,8 @@ def test_fp32_event_weights_error_statistics(gpu, oracle_pdf, name, k):
 
 # ------------------------------------------------------------------ one iteration
 @pytest.mark.parametrize("name,n,prec", [("ee", 100000, M.MC_FP64), ("pp", 20000, M.MC_FP64),
-                                         ("gg", 5000, M.MC_FP64), ("gauss", 50000, M.MC_FP64),
+                                         ("gg", 5000, M.MC_FP64), ("gg7", 5000, M.MC_FP64),
+                                         ("gauss", 50000, M.MC_FP64), ("gg7", 20000, M.MC_FP32_KAHAN),
                                          ("gg", 20000, M.MC_FP32_KAHAN), ("gauss", 50000, M.MC_FP32_KAHAN)])
 def test_iteration_sums_and_histograms(gpu, oracle_pdf, name, n, prec):
     itg = PROCS[name]
@@ -322,3 +324,16 @@ def test_full_size_gg_ttbarg_sampled(gpu, oracle_pdf):
     r1 = M.mc_vegas_iterate(v, itg, gpu, k)
     assert abs(r1.sum - wrec.sum()) <= 1e-12 * abs(wrec.sum())
     v.free()
+
+
+def test_ggttg_rambo_and_hierarchical_agree(gpu):
+    """The same cross section through two phase-space generators (RAMBO in 14
+    dimensions, sequential branchings in 7): VEGAS integrals agree within 4
+    combined standard deviations."""
+    res = {}
+    for name in ("gg", "gg7"):
+        r, _ = M.mc_integrate(PROCS[name], gpu, 8, 2_000_000, nbins=50, seed=0, prec=M.MC_FP32_KAHAN)
+        res[name] = r
+    a, b = res["gg"], res["gg7"]
+    assert abs(a.mean - b.mean) < 4 * math.hypot(a.sigma, b.sigma), (a.mean, a.sigma, b.mean, b.sigma)
+    assert a.sigma / a.mean < 5e-3 and b.sigma / b.mean < 5e-3

@@ -89,3 +89,11 @@ def test_iterate_threads_do_not_change_the_result(oracle_pdf):
     assert a["n_nonzero"] == b["n_nonzero"] and a["wmax"] == b["wmax"]
     assert abs(a["sum"] - b["sum"]) < 1e-13 * abs(a["sum"])
     np.testing.assert_array_equal(a["hist_n"], b["hist_n"])
+
+
+def test_gg_ttbarg_rambo_and_hierarchical_integrate_alike(oracle_pdf):
+    # one cross section, two phase-space parametrisations (Sec. "RAMBO" and
+    # table tab:hierarchical): the VEGAS estimates agree within errors
+    r14 = O.integrate(W.gg_ttbarg(), oracle_pdf, W.uniform_grid(14, 20), 0, seed=1, gid=0, niter=3, nevents=12000)
+    r7 = O.integrate(W.gg_ttbarg_7d(), oracle_pdf, W.uniform_grid(7, 20), 0, seed=1, gid=0, niter=3, nevents=12000)
+    assert abs(r14["mean"] - r7["mean"]) < 4 * math.hypot(r14["sigma"], r7["sigma"]), (r14, r7)
