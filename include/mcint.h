@@ -246,6 +246,22 @@ int mc_batch_shape(mc_batch b, int* block, int* events_per_thread, int* grid, in
 int mc_batch_kernel_ms(mc_batch b, float* ms);
 int mc_batch_free(mc_batch b);
 
+/* ------------------------------------------------ tensor-core dense layer
+ * mc_gemm_bf16: the dense-layer contraction of the flow sampler's
+ * conditioner (thesis Sec. "Deep learning": dense layer y = phi(W x + b)) on
+ * the tcgen05 tensor cores: C[M x N] (+)= A[M x K] . B[N x K]^T with A and B
+ * BF16 row-major (device; leading dimensions lda, ldb multiples of 8,
+ * 16-byte aligned), FP32 accumulation, and the epilogue:
+ *   0: C (BF16) = relu(acc + bias)      1: C (FP32) = acc + bias (bias may be NULL)
+ *   2: C (BF16) = acc * [mask > 0]       3: C (FP32) += acc (split-K over `splits`)
+ * M % 128 == 0, K % 64 == 0, bn (the N tile) a multiple of 16 <= 256 that
+ * divides N.  err: device int set non-zero if a bounded wait inside the kernel
+ * timed out (the result is then invalid).  Asynchronous on `stream`.
+ */
+int mc_gemm_bf16(int M, int N, int K, int bn, int epilogue, const void* a, int lda, const void* b, int ldb,
+                 const float* bias, void* c, int ldc, const void* mask, int ld_mask, int splits, int* err,
+                 void* stream);
+
 /* ------------------------------------------- allocation-free iteration
  * mc_vegas_iterate_noalloc: the same fused iteration as mc_vegas_iterate, for
  * callers that must not allocate device memory while they run: code whose

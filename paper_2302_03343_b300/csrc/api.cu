@@ -60,6 +60,7 @@ int num_sms() {
 }  // namespace
 
 #include "handles.h"
+#include "tc_gemm.h"
 
 namespace mc {
 // Message returned by mc_last_error() for the calling thread.
@@ -481,6 +482,34 @@ int mc_integrate(const mc_integrand* itg, mc_pdf pdf, int niter, int64_t nevents
   cudaEventDestroy(e1);
   mc_vegas_free(v);
   return rc;
+}
+
+int mc_gemm_bf16(int M, int N, int K, int bn, int epilogue, const void* a, int lda, const void* b, int ldb,
+                 const float* bias, void* c, int ldc, const void* mask, int ld_mask, int splits, int* err,
+                 void* stream) {
+  if (!a || !b || !c || !err || epilogue < 0 || epilogue > 3 || (epilogue == 2 && !mask))
+    return fail(MC_EINVAL, "mc_gemm_bf16: bad arguments");
+  mc::TcGemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.bn = bn;
+  g.epilogue = epilogue;
+  g.bias = bias;
+  g.ldc = ldc;
+  if (epilogue == 1 || epilogue == 3)
+    g.c_f32 = static_cast<float*>(c);
+  else
+    g.c_bf16 = static_cast<__nv_bfloat16*>(c);
+  g.mask = static_cast<const __nv_bfloat16*>(mask);
+  g.ld_mask = ld_mask;
+  g.error = err;
+  const cudaError_t e = mc::tc_gemm(g, static_cast<const __nv_bfloat16*>(a), lda, static_cast<const __nv_bfloat16*>(b),
+                                    ldb, splits, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return fail(MC_EINVAL, "mc_gemm_bf16: unsupported shape or alignment");
+  if (e != cudaSuccess) return fail(MC_ECUDA, "mc_gemm_bf16: %s", cudaGetErrorString(e));
+  return MC_OK;
 }
 
 }  // extern "C"

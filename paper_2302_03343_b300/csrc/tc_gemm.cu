@@ -1,0 +1,294 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05) for the dense layers
+// of the normalizing-flow sampler:
+//     C[M x N] (+)= A[M x K] . B[N x K]^T,   A, B in BF16, K-major (row-major);
+// FP32 accumulation in tensor memory, with fused epilogues.
+//
+// One CTA (4 warps) computes one 128 x BN tile (BN <= 256, a multiple of 16)
+// over its K range (split-K over gridDim.z).  One elected thread streams the
+// K blocks (64 BF16 = 128 B per row, 128-byte swizzle) into a ring of shared-
+// memory stages with TMA (cp.async.bulk.tensor, completion on an mbarrier)
+// and issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a
+// TMEM accumulator; tcgen05.commit on a per-stage mbarrier returns the stage
+// to the loader.  After the last MMA all four warps read the accumulator with
+// tcgen05.ld (warp w owns rows 32w..32w+31, one row per thread) and apply the
+// epilogue.  Every mbarrier wait is bounded: on timeout the kernel records an
+// error code, waits (bounded) for its TMA copies, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "tc_gemm.h"
+
+namespace mc {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;          // K elements per stage (one 128-byte swizzle atom)
+constexpr int kStages = 4;
+constexpr uint32_t kSpinLimit = 1u << 20;  // about a second of try_wait polling
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte
+// swizzle, 8-row groups 1024 bytes apart (stride byte offset), descriptor
+// version 1, leading byte offset unused for this layout.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return uint64_t((addr & 0x3FFFF) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46) |
+         (uint64_t(2) << 61);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                   TcGemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned stages
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int bn = g.bn;
+  const uint32_t a_bytes = kBM * kBK * 2, b_bytes = uint32_t(bn) * kBK * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int failed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile_m = blockIdx.x, tile_n = blockIdx.y;
+  const int kblocks_total = g.K / kBK;
+  const int kb_per_split = (kblocks_total + gridDim.z - 1) / gridDim.z;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int nkb = max(0, min(kblocks_total, kb0 + kb_per_split) - kb0);
+  uint32_t ncols = 32;
+  while (ncols < uint32_t(bn)) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  if (threadIdx.x == 0 && nkb > 0) {
+    // idesc: D = F32, A = B = BF16, both K-major, N = bn, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(bn >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
+    int issued = 0;
+    auto load = [&](int i) {  // K block i of this split into stage i % kStages
+      const int s = i % kStages;
+      unsigned char* st = smem + size_t(s) * stage_bytes;
+      mbar_expect_tx(&full_bar[s], stage_bytes);
+      tma_load_2d(st, &map_a, (kb0 + i) * kBK, tile_m * kBM, &full_bar[s]);
+      tma_load_2d(st + a_bytes, &map_b, (kb0 + i) * kBK, tile_n * bn, &full_bar[s]);
+    };
+    for (; issued < min(nkb, kStages); ++issued) load(issued);
+    bool ok = true;
+    for (int i = 0; i < nkb && ok; ++i) {
+      const int s = i % kStages;
+      const uint32_t ph = uint32_t(i / kStages) & 1u;
+      if (!mbar_wait(&full_bar[s], ph)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a_addr = smem_u32(smem + size_t(s) * stage_bytes);
+      const uint32_t b_addr = a_addr + a_bytes;
+      const uint64_t ad = smem_desc(a_addr), bd = smem_desc(b_addr);
+#pragma unroll
+      for (int k = 0; k < kBK / 16; ++k)  // advance 16 BF16 = 32 bytes along K inside the swizzle atom
+        mma_bf16(tmem, ad + uint64_t(k * 2), bd + uint64_t(k * 2), idesc, (i > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&empty_bar[s]);
+      if (issued < nkb) {  // refill this stage once the MMAs reading it are done
+        if (!mbar_wait(&empty_bar[s], ph)) {
+          ok = false;
+          break;
+        }
+        load(issued);
+        ++issued;
+      }
+    }
+    if (ok) {
+      mma_commit(&done_bar);
+    } else {
+      failed = 1;
+      atomicExch(g.error, 1);
+      // let the copies already issued land before the CTA exits
+      for (int i = 0; i < min(issued, nkb); ++i) mbar_wait(&full_bar[i % kStages], uint32_t(i / kStages) & 1u);
+      mbar_expect_tx(&done_bar, 0);  // release the other threads
+    }
+  }
+  if (nkb > 0) {
+    // every thread waits for the accumulator (or the failure release)
+    if (!mbar_wait(&done_bar, 0)) {
+      if (lane == 0) atomicExch(g.error, 2);
+      failed = 1;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  if (!failed && nkb > 0) {
+    const int row = tile_m * kBM + warp * 32 + lane;
+    const uint32_t lane_base = uint32_t(warp * 32) << 16;
+    for (int c0 = 0; c0 < bn; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + uint32_t(c0), v);
+      const int col0 = tile_n * bn + c0;
+      if (row >= g.M) continue;
+      switch (g.epilogue) {
+        case kEpiBiasReluBf16: {
+          __nv_bfloat16* out = g.c_bf16 + size_t(row) * g.ldc + col0;
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const float a = fmaxf(v[j] + (g.bias ? g.bias[col0 + j] : 0.0f), 0.0f);
+            const float b = fmaxf(v[j + 1] + (g.bias ? g.bias[col0 + j + 1] : 0.0f), 0.0f);
+            *reinterpret_cast<__nv_bfloat162*>(out + j) = __floats2bfloat162_rn(a, b);
+          }
+          break;
+        }
+        case kEpiBiasF32: {
+          float* out = g.c_f32 + size_t(row) * g.ldc + col0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) out[j] = v[j] + (g.bias ? g.bias[col0 + j] : 0.0f);
+          break;
+        }
+        case kEpiReluMaskBf16: {
+          // gradient through ReLU: keep where the layer's activation is positive
+          __nv_bfloat16* out = g.c_bf16 + size_t(row) * g.ldc + col0;
+          const __nv_bfloat16* act = g.mask + size_t(row) * g.ld_mask + col0;
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const float a = __bfloat162float(act[j]) > 0.0f ? v[j] : 0.0f;
+            const float b = __bfloat162float(act[j + 1]) > 0.0f ? v[j + 1] : 0.0f;
+            *reinterpret_cast<__nv_bfloat162*>(out + j) = __floats2bfloat162_rn(a, b);
+          }
+          break;
+        }
+        default: {  // kEpiAtomicF32: split-K accumulation
+          float* out = g.c_f32 + size_t(row) * g.ldc + col0;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) atomicAdd(out + j, v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2D BF16 tensor map of a row-major [rows x K] matrix, box [box_rows x 64].
+bool make_map(CUtensorMap* m, const void* base, int rows, int k, int ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(k), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(ld) * 2};
+  const cuuint32_t box[2] = {cuuint32_t(kBK), cuuint32_t(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t tc_gemm_smem(int bn) { return size_t(kStages) * (kBM * kBK * 2 + size_t(bn) * kBK * 2) + 1024; }
+
+cudaError_t tc_gemm(const TcGemmArgs& g_in, const __nv_bfloat16* a, int lda, const __nv_bfloat16* b, int ldb,
+                    int splits, cudaStream_t st) {
+  TcGemmArgs g = g_in;
+  if (g.M % kBM || g.K % kBK || g.bn % 16 || g.bn < 16 || g.bn > 256 || g.N % g.bn || splits < 1 || !g.error ||
+      (reinterpret_cast<uintptr_t>(a) & 15) || (reinterpret_cast<uintptr_t>(b) & 15) || (lda % 8) || (ldb % 8))
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a, g.M, g.K, lda, kBM) || !make_map(&mb, b, g.N, g.K, ldb, g.bn)) return cudaErrorInvalidValue;
+  const size_t smem = tc_gemm_smem(g.bn);
+  (void)cudaGetLastError();
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const dim3 grid(g.M / kBM, g.N / g.bn, splits);
+  tc_gemm_kernel<<<grid, 128, smem, st>>>(ma, mb, g);
+  return cudaGetLastError();
+}
+
+}  // namespace mc

@@ -1,0 +1,35 @@
+// Internal: tcgen05 BF16 GEMM C[M x N] (+)= A[M x K] . B[N x K]^T (tc_gemm.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace mc {
+
+enum TcEpilogue : int {
+  kEpiBiasReluBf16 = 0,  // c_bf16 = bf16(relu(acc + bias))
+  kEpiBiasF32 = 1,       // c_f32 = acc + bias (bias may be null)
+  kEpiReluMaskBf16 = 2,  // c_bf16 = bf16(acc * [mask > 0]) (gradient through ReLU)
+  kEpiAtomicF32 = 3,     // c_f32 += acc (split-K)
+};
+
+struct TcGemmArgs {
+  int M, N, K;  // M % 128 == 0, K % 64 == 0, N % bn == 0
+  int bn;       // N tile: multiple of 16, <= 256
+  int epilogue;
+  const float* bias;           // [N] or null
+  float* c_f32;                // row-major, leading dimension ldc
+  __nv_bfloat16* c_bf16;       // row-major, leading dimension ldc
+  int ldc;
+  const __nv_bfloat16* mask;   // kEpiReluMaskBf16: activation of the layer, leading dimension ld_mask
+  int ld_mask;
+  int* error;                  // device flag: set non-zero when a bounded wait timed out
+};
+
+size_t tc_gemm_smem(int bn);
+// a: [M x K] row-major (leading dimension lda), b: [N x K] row-major (ldb);
+// 16-byte aligned, lda and ldb multiples of 8.  splits > 1 divides K across
+// gridDim.z (use kEpiAtomicF32).  Returns cudaErrorInvalidValue on bad shapes.
+cudaError_t tc_gemm(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, const __nv_bfloat16* b, int ldb,
+                    int splits, cudaStream_t st);
+
+}  // namespace mc

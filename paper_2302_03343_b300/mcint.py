@@ -29,7 +29,7 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_vegas_get_iteration", "mc_vegas_set_gid", "mc_vegas_iterate", "mc_vegas_refine", "mc_integrate",
            "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms", "mc_vegas_iterate_noalloc",
            "mc_batch_create", "mc_batch_iterate", "mc_batch_get_grid", "mc_batch_shape", "mc_batch_kernel_ms",
-           "mc_batch_free")
+           "mc_batch_free", "mc_gemm_bf16")
 
 
 class McError(RuntimeError):
@@ -102,6 +102,7 @@ def lib():
             "mc_batch_shape": [_vp] + [ctypes.POINTER(ctypes.c_int)] * 4,
             "mc_batch_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_float)],
             "mc_batch_free": [_vp],
+            "mc_gemm_bf16": [i32, i32, i32, i32, i32, _vp, i32, _vp, i32, _vp, _vp, i32, _vp, i32, i32, _vp, _vp],
             "mc_vegas_iterate_noalloc": [ctypes.POINTER(Integrand), _vp, i32, i32, _vp, _vp, i32, u64, u32, u32,
                                          i64, i32, _vp, _vp, _vp, _vp],
         }
@@ -326,6 +327,18 @@ def mc_batch_kernel_ms(b):
 
 def mc_batch_free(b):
     b.free()
+
+
+EPI_BIAS_RELU_BF16, EPI_BIAS_F32, EPI_RELU_MASK_BF16, EPI_ATOMIC_F32 = 0, 1, 2, 3
+
+
+def mc_gemm_bf16(M, N, K, bn, epilogue, a, b, c, bias=None, mask=None, splits=1, err=None, stream=None):
+    """C[M x N] (+)= A[M x K] . B[N x K]^T on the tcgen05 tensor cores (torch tensors on the device)."""
+    null = ctypes.c_void_p(0)
+    _check(lib().mc_gemm_bf16(M, N, K, bn, epilogue, _ptr(a), a.stride(0), _ptr(b), b.stride(0),
+                              _ptr(bias) if bias is not None else null, _ptr(c), c.stride(0),
+                              _ptr(mask) if mask is not None else null, mask.stride(0) if mask is not None else 0,
+                              splits, _ptr(err), _stream(stream)))
 
 
 MC_NOALLOC_MAX_BLOCKS = 4096

@@ -1,0 +1,80 @@
+"""tcgen05 BF16 GEMM (mc_gemm_bf16) against a plain PyTorch FP32 reference of
+the same op: C = A . B^T (+ bias, ReLU, ReLU mask, split-K)."""
+import pytest
+
+from paper_2302_03343_b300 import mcint as M
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_03343_b300 import build
+    build.build()
+    return torch.device("cuda")
+
+
+def operands(M_, N, K, dev, seed=0):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    a = torch.randn(M_, K, generator=g).to(torch.bfloat16).to(dev)
+    b = torch.randn(N, K, generator=g).to(torch.bfloat16).to(dev)
+    bias = torch.randn(N, generator=g).to(dev)
+    return a, b, bias
+
+
+def rel_err(x, ref):
+    return ((x.float() - ref).abs().max() / ref.abs().max().clamp_min(1e-30)).item()
+
+
+@pytest.mark.parametrize("M_,N,K,bn", [(128, 256, 256, 256), (256, 320, 256, 160), (384, 208, 64, 208),
+                                       (128, 16, 128, 16), (640, 256, 512, 128)])
+def test_gemm_bias_fp32(dev, M_, N, K, bn):
+    a, b, bias = operands(M_, N, K, dev)
+    c = torch.full((M_, N), float("nan"), device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    M.mc_gemm_bf16(M_, N, K, bn, M.EPI_BIAS_F32, a, b, c, bias=bias, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = a.float() @ b.float().T + bias
+    assert rel_err(c, ref) < 1e-5
+
+
+def test_gemm_split_k_atomic(dev):
+    M_, N, K = 256, 256, 4096
+    a, b, _ = operands(M_, N, K, dev, seed=1)
+    c = torch.zeros((M_, N), device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    M.mc_gemm_bf16(M_, N, K, 256, M.EPI_ATOMIC_F32, a, b, c, splits=8, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert rel_err(c, a.float() @ b.float().T) < 1e-5
+
+
+def test_gemm_relu_bf16_and_mask(dev):
+    M_, N, K = 256, 256, 256
+    a, b, bias = operands(M_, N, K, dev, seed=2)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    c = torch.empty((M_, N), dtype=torch.bfloat16, device=dev)
+    M.mc_gemm_bf16(M_, N, K, 256, M.EPI_BIAS_RELU_BF16, a, b, c, bias=bias, err=err)
+    ref = torch.relu(a.float() @ b.float().T + bias)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert ((c.float() - ref).abs() <= 2 ** -7 * ref.abs() + 1e-6).all()
+    mask = torch.randn(M_, N, device=dev).to(torch.bfloat16)
+    g = torch.empty((M_, N), dtype=torch.bfloat16, device=dev)
+    M.mc_gemm_bf16(M_, N, K, 256, M.EPI_RELU_MASK_BF16, a, b, g, mask=mask, err=err)
+    ref = (a.float() @ b.float().T) * (mask.float() > 0)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert ((g.float() - ref).abs() <= 2 ** -7 * ref.abs() + 1e-6).all()
+
+
+def test_gemm_rejects_bad_shapes(dev):
+    a, b, bias = operands(100, 256, 256, dev)
+    c = torch.empty((100, 256), device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    with pytest.raises(M.McError):
+        M.mc_gemm_bf16(100, 256, 256, 256, M.EPI_BIAS_F32, a, b, c, err=err)
