@@ -144,3 +144,45 @@ def batch_configs(seed=0):
 def uniform_grid(ndim, nbins):
     """Initial VEGAS grid: nbins equal bins per dimension, [ndim][nbins+1]."""
     return np.tile(np.linspace(0.0, 1.0, nbins + 1), (ndim, 1))
+
+
+def splitmix64_uniform(seed, n, offset=0):
+    """n uniforms in [0, 1) from the SplitMix64 sequence of `seed` (vectorised)."""
+    with np.errstate(over="ignore"):
+        i = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed) + i * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+def flow_layer_masks(D, L):
+    """(conditioning dims, transformed dims) of each coupling layer: layer l
+    transforms the dimensions d with d % 2 == l % 2."""
+    return [([d for d in range(D) if d % 2 != l % 2], [d for d in range(D) if d % 2 == l % 2]) for l in range(L)]
+
+
+def flow_init_params(D, L=6, K=32, hidden=256, seed=0, last_scale=0.0):
+    """Initial flow parameters (FP32), one dict per coupling layer:
+    W1 [hidden, d_A], b1, W2 [hidden, hidden], b2, W3, b3, W4 [d_B (2K+1), hidden], b4.
+    Glorot-uniform weights from SplitMix64(seed), zero biases; the last layer is
+    scaled by last_scale (0: the initial flow is the identity map)."""
+    out = []
+    off = 0
+    for a, b in flow_layer_masks(D, L):
+        shapes = [("W1", (hidden, len(a))), ("W2", (hidden, hidden)), ("W3", (hidden, hidden)),
+                  ("W4", (len(b) * (2 * K + 1), hidden))]
+        layer = {}
+        for name, (fo, fi) in shapes:
+            lim = math.sqrt(6.0 / (fo + fi))
+            u = splitmix64_uniform(seed, fo * fi, off)
+            off += fo * fi
+            w = (2.0 * u - 1.0) * lim
+            if name == "W4":
+                w = w * last_scale
+            layer[name] = w.reshape(fo, fi).astype(np.float32)
+        for name, n in (("b1", hidden), ("b2", hidden), ("b3", hidden), ("b4", len(b) * (2 * K + 1))):
+            layer[name] = np.zeros(n, dtype=np.float32)
+        out.append(layer)
+    return out
