@@ -46,7 +46,7 @@ extern "C" {
 #define MC_ECUDA (-3)    /* a CUDA runtime call failed                          */
 #define MC_ENAN (-4)     /* non-finite event weights were produced (counted)    */
 #define MC_ENOCONV (-5)  /* RAMBO's massive rescaling did not converge (counted) */
-#define MC_ETIMEOUT (-6) /* reserved: a bounded device wait gave up             */
+#define MC_ETIMEOUT (-6) /* a bounded device wait gave up (result invalid)      */
 
 /* -------------------------------------------------------------- enums */
 #define MC_FP64 0        /* integrand in FP64, 52-bit uniforms                   */
@@ -303,6 +303,75 @@ int mc_vegas_iterate_noalloc(const mc_integrand* itg, mc_pdf pdf, int ndim, int 
                              const float* edges32, int prec, uint64_t seed, uint32_t iteration, uint32_t gid,
                              int64_t nevents, int blocks, double* hist_w2, uint32_t* hist_n, mc_device_sums* sums,
                              void* stream);
+
+/* ------------------------------------------------ normalizing-flow sampler
+ * Importance sampling with a trained density q (thesis Sec. "Importance
+ * sampling": E = (1/N) sum f(x_i)/q(x_i), variance minimal for q ~ |f|), the
+ * density being a normalizing flow built from dense layers y = phi(W x + b)
+ * (Sec. "Deep learning") and trained with Adam (Sec. "Optimizers").  The
+ * flow is a stack of piecewise-quadratic coupling layers on the unit cube:
+ * layer l transforms the coordinates d with d % 2 == l % 2; its conditioner
+ * maps u = 2 x_A - 1 through dense layers of `hidden` units with ReLU to
+ * 2 * bins + 1 logits per transformed coordinate (bins width logits ->
+ * softmax; bins + 1 vertex-height logits -> exp, normalised to unit area).
+ * The first dense layer runs in FP32; the three hidden-width layers run on
+ * the tcgen05 tensor cores with BF16 weights and activations and FP32
+ * accumulation; the splines and log-determinants are FP32.
+ *
+ * Parameters (host, packed FP32): for each layer in order, W1 [hidden x n_A],
+ * b1 [hidden], W2 [hidden x hidden], b2, W3 [hidden x hidden], b3,
+ * W4 [n_B (2 bins + 1) x hidden], b4 [n_B (2 bins + 1)], matrices row-major
+ * [out x in]; n_B = number of transformed coordinates, n_A = ndim - n_B.
+ * mc_flow_param_count gives the total.
+ */
+typedef struct mc_flow_s* mc_flow;
+typedef struct {
+  int ndim;    /* 2..16 */
+  int layers;  /* 1..16 coupling layers */
+  int bins;    /* 2..32 spline bins */
+  int hidden;  /* must be 256 */
+} mc_flow_cfg;
+
+/* Number of FP32 parameters of a flow of configuration cfg. */
+int mc_flow_param_count(const mc_flow_cfg* cfg, int64_t* n);
+/* Creates a flow on the current device with parameters `init` (host, packed,
+ * copied), workspace for batches of up to max_batch events, and `seed` as
+ * the Philox key of its uniforms; 1 <= max_batch <= 2^21.  Device memory: about
+ * max_batch * layers * (6 hidden + 4 * 2 * ndim * (2 bins + 1)) bytes. */
+int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch, uint64_t seed, mc_flow* out);
+int mc_flow_free(mc_flow f);
+/* Replace / read the parameters (host, packed).  Set resets nothing else
+ * (Adam moments and the step counter are kept).  Both synchronise. */
+int mc_flow_set_params(mc_flow f, const float* host);
+int mc_flow_get_params(mc_flow f, float* host);
+/* Sampling direction: z [n x ndim] (device, uniform in the unit cube) ->
+ * x [n x ndim] (device) and log q(x) [n] (device); n <= max_batch.
+ * Synchronises (to read the tensor-core error flag). */
+int mc_flow_forward(mc_flow f, int64_t n, const float* z, float* x, float* log_q, void* stream);
+/* Loss L = -sum w_i log q(x_i) / sum w_i at fixed points x [n x ndim] and
+ * weights w [n] (device), q evaluated through the inverse pass; *loss
+ * (host, may be NULL) receives L and grads (host, packed like the
+ * parameters, may be NULL) dL/dtheta.  Leaves the gradients in place for
+ * mc_flow_adam_step.  Synchronises. */
+int mc_flow_loss_grad(mc_flow f, int64_t n, const float* x, const float* w, double* loss, float* grads,
+                      void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the
+ * gradients of the last loss evaluation, then refreshes the BF16 weights. */
+int mc_flow_adam_step(mc_flow f, double lr, void* stream);
+/* `steps` online training steps on the integrand: each samples `batch`
+ * events from the current flow (Philox counter iteration 0x10000 + step),
+ * evaluates f in FP32 at them, forms w = |f| / q, and takes one loss
+ * gradient and Adam step.  losses (host, may be NULL) receives each step's
+ * loss; without it the call is asynchronous except for a final error-flag
+ * check.  The flow's ndim must equal the process's. */
+int mc_flow_train(mc_flow f, const mc_integrand* itg, mc_pdf pdf, int steps, int64_t batch, double lr,
+                  void* stream, double* losses);
+/* One sampling pass of nevents events from the flow (Philox counter
+ * iteration 0x20000 + iteration), in chunks of max_batch: weights
+ * w = f(x)/q(x) accumulated in compensated FP64 into *out (host); events
+ * whose integrand failed or is non-finite count in n_bad with w = 0. */
+int mc_flow_iterate(mc_flow f, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, uint32_t iteration,
+                    void* stream, mc_iter_result* out);
 
 #ifdef __cplusplus
 }

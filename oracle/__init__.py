@@ -85,6 +85,8 @@ def lib():
         L.orc_integrate.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
                                     ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int64, _d,
                                     ctypes.c_int, _dp, _dp, _dp, _dp]
+        L.orc_integrand_at.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int64, _dp, _dp,
+                                       ctypes.POINTER(ctypes.c_int32)]
         _LIB = L
     return _LIB
 
@@ -258,6 +260,18 @@ def event(itg, pdf, edges, prec, seed, iteration, gid, ev):
     lib().orc_event(ctypes.byref(c), pdf.handle if pdf is not None else None, edges.shape[1] - 1,
                     _ptr(edges), prec, seed, iteration, gid, ev, ctypes.byref(rec))
     return rec
+
+
+def integrand_at(itg, pdf, x):
+    """Integrand f at the points x [n, ndim] of the unit hypercube; returns (f, status)."""
+    c = _integrand_c(itg)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    f = np.zeros(n)
+    st = np.zeros(n, dtype=np.int32)
+    lib().orc_integrand_at(ctypes.byref(c), pdf.handle if pdf is not None else None, n, _ptr(x), _ptr(f),
+                           st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return f, st
 
 
 def iterate(itg, pdf, edges, prec, seed, iteration, gid, first, n, nthreads=0):

@@ -195,6 +195,19 @@ void orc_event(const orc_integrand* in, const void* pdf, int nbins, const double
                   ev, rec);
 }
 
+// Integrand at n given points x [n][ndim] of the unit hypercube (no VEGAS
+// map): f[i] and the status of each evaluation (0, or negative on failure).
+void orc_integrand_at(const orc_integrand* in, const void* pdf, int64_t n, const double* x, double* f,
+                      int32_t* status) {
+  const int ndim = orc::process_ndim(*in);
+  for (int64_t i = 0; i < n; ++i) {
+    orc_event_record rec;
+    std::memset(&rec, 0, sizeof(rec));
+    f[i] = orc::integrand_value(*in, static_cast<const orc::Pdf*>(pdf), x + i * ndim, &rec);
+    status[i] = rec.status;
+  }
+}
+
 // One VEGAS iteration over events [first, first + n): sums of w and w^2,
 // the count of non-zero weights, the largest weight, and the per-dimension
 // histograms of w^2 and of event counts (both accumulated into the outputs).

@@ -269,25 +269,22 @@ int mc_vegas_set_gid(mc_vegas v, uint32_t gid) {
   return MC_OK;
 }
 
-// Validates an integrand against a grid and fills the kernel arguments.
-static int prepare(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
-  if (!v || !itg) return fail(MC_EINVAL, "NULL handle or integrand");
+}  // extern "C"
+
+// Validates an integrand and fills the process part of the kernel arguments
+// (parameters, PDF tables and flavours, constants); shared with the flow
+// sampler (flow.cu).
+int mc::fill_process_args(const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
+  if (!itg) return fail(MC_EINVAL, "NULL integrand");
   int dev;
   if (int rc = current_device(&dev)) return rc;
-  if (dev != v->device) return fail(MC_EINVAL, "grid lives on device %d, current device is %d", v->device, dev);
   if (itg->proc < MC_EE_MUMU || itg->proc > MC_GG_TTBARG_7D) return fail(MC_EINVAL, "unknown process %d", itg->proc);
-  const int nd = process_ndim(itg);
-  if (nd != v->ndim) return fail(MC_EINVAL, "process needs %d dimensions, grid has %d", nd, v->ndim);
   const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG || itg->proc == MC_GG_TTBARG_7D;
   if (!(itg->sqrt_s > 0.0) && itg->proc != MC_GAUSS) return fail(MC_EINVAL, "sqrt_s must be positive");
   if (itg->proc == MC_GAUSS && !(itg->gauss_sigma > 0.0)) return fail(MC_EINVAL, "gauss_sigma must be positive");
   std::memset(a, 0, sizeof(*a));
   a->prm = {itg->proc, itg->gauss_dim, itg->sqrt_s, itg->m_top, itg->alpha, itg->alpha_s, itg->mz, itg->gz,
             itg->sw2, itg->mu_f, itg->ptcut_g, itg->etacut_g, itg->gauss_sigma, itg->gev2pb};
-  a->ndim = v->ndim;
-  a->nbins = v->nbins;
-  a->edges64 = v->d_edges;
-  a->edges32 = v->d_edges32;
   if (hadronic) {
     if (!pdf) return fail(MC_EINVAL, "process %d needs a PDF", itg->proc);
     if (pdf->device != dev) return fail(MC_EINVAL, "pdf lives on device %d", pdf->device);
@@ -310,6 +307,26 @@ static int prepare(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, KernelArgs* 
   // three-particle RAMBO coefficient (2 pi)^(4-3n) (pi/2)^(n-1) / (Gamma(n) Gamma(n-1)), n = 3
   a->w0_coef3 = std::pow(2.0 * M_PI, -5.0) * std::pow(M_PI / 2.0, 2.0) / (std::tgamma(3.0) * std::tgamma(2.0));
   a->e2eta = std::exp(2.0 * itg->etacut_g);
+  return MC_OK;
+}
+
+int mc::process_dim(const mc_integrand* itg) { return process_ndim(itg); }
+
+extern "C" {
+
+// Validates an integrand against a grid and fills the kernel arguments.
+static int prepare(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
+  if (!v || !itg) return fail(MC_EINVAL, "NULL handle or integrand");
+  int dev;
+  if (int rc = current_device(&dev)) return rc;
+  if (dev != v->device) return fail(MC_EINVAL, "grid lives on device %d, current device is %d", v->device, dev);
+  const int nd = process_ndim(itg);
+  if (nd != v->ndim) return fail(MC_EINVAL, "process needs %d dimensions, grid has %d", nd, v->ndim);
+  if (int rc = mc::fill_process_args(itg, pdf, a)) return rc;
+  a->ndim = v->ndim;
+  a->nbins = v->nbins;
+  a->edges64 = v->d_edges;
+  a->edges32 = v->d_edges32;
   a->seed = v->seed;
   a->iteration = v->iteration;
   a->gid = v->gid;

@@ -16,7 +16,7 @@ struct Acc {
 };
 
 // value = hi + lo pairs: compensated addition of two such pairs
-MC_D void pair_add(double& hi, double& lo, double h2, double l2) {
+MC_HD void pair_add(double& hi, double& lo, double h2, double l2) {
   const double s = hi + h2;
   const double bp = s - hi;
   const double e = (hi - (s - bp)) + (h2 - bp);
@@ -24,7 +24,7 @@ MC_D void pair_add(double& hi, double& lo, double h2, double l2) {
   lo = lo + l2 + e;
 }
 
-MC_D void partial_add(BlockPartial& b, const BlockPartial& o) {
+MC_HD void partial_add(BlockPartial& b, const BlockPartial& o) {
   pair_add(b.sum_hi, b.sum_lo, o.sum_hi, o.sum_lo);
   pair_add(b.sum2_hi, b.sum2_lo, o.sum2_hi, o.sum2_lo);
   b.wmax = fmax(b.wmax, o.wmax);

@@ -8,6 +8,11 @@
 
 namespace mc {
 void set_last_error(const char* msg);  // api.cu
+// Validates a process description and fills KernelArgs::prm, pdf, fl,
+// logq2_f, w0_coef3 and e2eta (the rest zeroed); MC_OK or an MC_E* code with
+// the message set (api.cu).
+int fill_process_args(const mc_integrand* itg, mc_pdf pdf, KernelArgs* a);
+int process_dim(const mc_integrand* itg);  // sampled dimensions of the process, -1 if unknown
 }
 
 struct mc_pdf_s {

@@ -29,7 +29,9 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_vegas_get_iteration", "mc_vegas_set_gid", "mc_vegas_iterate", "mc_vegas_refine", "mc_integrate",
            "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms", "mc_vegas_iterate_noalloc",
            "mc_batch_create", "mc_batch_iterate", "mc_batch_get_grid", "mc_batch_shape", "mc_batch_kernel_ms",
-           "mc_batch_free", "mc_gemm_bf16")
+           "mc_batch_free", "mc_gemm_bf16", "mc_flow_param_count", "mc_flow_create", "mc_flow_free",
+           "mc_flow_set_params", "mc_flow_get_params", "mc_flow_forward", "mc_flow_loss_grad", "mc_flow_adam_step",
+           "mc_flow_train", "mc_flow_iterate")
 
 
 class McError(RuntimeError):
@@ -53,6 +55,11 @@ class IterResult(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
+class FlowCfg(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("layers", ctypes.c_int32), ("bins", ctypes.c_int32),
+                ("hidden", ctypes.c_int32)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("mean", ctypes.c_double), ("sigma", ctypes.c_double), ("chi2_dof", ctypes.c_double),
                 ("n_iter", ctypes.c_int32), ("status", ctypes.c_int32), ("gpu_ms", ctypes.c_double)]
@@ -64,6 +71,7 @@ class Result(ctypes.Structure):
 _LIB = None
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 
 
 def lib():
@@ -105,6 +113,16 @@ def lib():
             "mc_gemm_bf16": [i32, i32, i32, i32, i32, _vp, i32, _vp, i32, _vp, _vp, i32, _vp, i32, i32, _vp, _vp],
             "mc_vegas_iterate_noalloc": [ctypes.POINTER(Integrand), _vp, i32, i32, _vp, _vp, i32, u64, u32, u32,
                                          i64, i32, _vp, _vp, _vp, _vp],
+            "mc_flow_param_count": [ctypes.POINTER(FlowCfg), ctypes.POINTER(ctypes.c_int64)],
+            "mc_flow_create": [ctypes.POINTER(FlowCfg), _fp, i64, u64, ctypes.POINTER(_vp)],
+            "mc_flow_free": [_vp],
+            "mc_flow_set_params": [_vp, _fp],
+            "mc_flow_get_params": [_vp, _fp],
+            "mc_flow_forward": [_vp, i64, _vp, _vp, _vp, _vp],
+            "mc_flow_loss_grad": [_vp, i64, _vp, _vp, _dp, _fp, _vp],
+            "mc_flow_adam_step": [_vp, d, _vp],
+            "mc_flow_train": [_vp, ctypes.POINTER(Integrand), _vp, i32, i64, d, _vp, _dp],
+            "mc_flow_iterate": [_vp, ctypes.POINTER(Integrand), _vp, i64, u32, _vp, ctypes.POINTER(IterResult)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -362,4 +380,114 @@ def mc_launch_shape(itg, prec, nevents):
     return b.value, t.value
 
 
-__all__ = ["McError", "Integrand", "IterResult", "Result", "Pdf", "Vegas", "workloads", *SYMBOLS]
+FLOW_KEYS = ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4")
+
+
+def pack_flow_params(layers):
+    """Packed FP32 parameter vector (the mc_flow layout) from per-layer dicts of arrays."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float32).ravel() for p in layers for k in FLOW_KEYS])
+
+
+def unpack_flow_params(flat, ndim, nlayers, bins, hidden=256):
+    """Per-layer dicts of arrays from a packed parameter vector."""
+    out, o = [], 0
+    for l in range(nlayers):
+        nb = (ndim + 1 - (l % 2)) // 2
+        na, nout = ndim - nb, nb * (2 * bins + 1)
+        shapes = dict(W1=(hidden, na), b1=(hidden,), W2=(hidden, hidden), b2=(hidden,), W3=(hidden, hidden),
+                      b3=(hidden,), W4=(nout, hidden), b4=(nout,))
+        d = {}
+        for k in FLOW_KEYS:
+            n = int(np.prod(shapes[k]))
+            d[k] = np.asarray(flat[o:o + n]).reshape(shapes[k])
+            o += n
+        out.append(d)
+    assert o == len(flat)
+    return out
+
+
+class Flow:
+    """Owns an mc_flow handle (normalizing-flow sampler on the device)."""
+
+    def __init__(self, handle, cfg, nparam, max_batch):
+        self.handle, self.cfg, self.nparam, self.max_batch = handle, cfg, nparam, max_batch
+
+    def free(self):
+        if self.handle:
+            _check(lib().mc_flow_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mc_flow_param_count(ndim, layers, bins, hidden=256):
+    n = ctypes.c_int64()
+    _check(lib().mc_flow_param_count(ctypes.byref(FlowCfg(ndim, layers, bins, hidden)), ctypes.byref(n)))
+    return n.value
+
+
+def mc_flow_create(ndim, layers, bins, init_layers, max_batch, seed=0, hidden=256):
+    cfg = FlowCfg(ndim, layers, bins, hidden)
+    flat = np.ascontiguousarray(pack_flow_params(init_layers), dtype=np.float32)
+    n = mc_flow_param_count(ndim, layers, bins, hidden)
+    if flat.size != n:
+        raise McError(MC_EINVAL, f"flow needs {n} parameters, got {flat.size}")
+    h = _vp()
+    _check(lib().mc_flow_create(ctypes.byref(cfg), flat.ctypes.data_as(_fp), max_batch, seed, ctypes.byref(h)))
+    return Flow(h, cfg, n, max_batch)
+
+
+def mc_flow_free(f):
+    f.free()
+
+
+def mc_flow_set_params(f, layers):
+    flat = np.ascontiguousarray(pack_flow_params(layers), dtype=np.float32)
+    _check(lib().mc_flow_set_params(f.handle, flat.ctypes.data_as(_fp)))
+
+
+def mc_flow_get_params(f):
+    flat = np.zeros(f.nparam, dtype=np.float32)
+    _check(lib().mc_flow_get_params(f.handle, flat.ctypes.data_as(_fp)))
+    return unpack_flow_params(flat, f.cfg.ndim, f.cfg.layers, f.cfg.bins, f.cfg.hidden)
+
+
+def mc_flow_forward(f, z_dev, x_dev, logq_dev, stream=None):
+    """z [n x ndim] -> x, log q (float32 device tensors)."""
+    _check(lib().mc_flow_forward(f.handle, z_dev.shape[0], _ptr(z_dev), _ptr(x_dev), _ptr(logq_dev),
+                                 _stream(stream)))
+
+
+def mc_flow_loss_grad(f, x_dev, w_dev, grads=True, stream=None):
+    """Loss at fixed points and weights; returns (loss, per-layer gradient dicts or None)."""
+    loss = ctypes.c_double()
+    g = np.zeros(f.nparam, dtype=np.float32) if grads else None
+    _check(lib().mc_flow_loss_grad(f.handle, x_dev.shape[0], _ptr(x_dev), _ptr(w_dev), ctypes.byref(loss),
+                                   g.ctypes.data_as(_fp) if grads else None, _stream(stream)))
+    return loss.value, (unpack_flow_params(g, f.cfg.ndim, f.cfg.layers, f.cfg.bins, f.cfg.hidden) if grads else None)
+
+
+def mc_flow_adam_step(f, lr=1e-3, stream=None):
+    _check(lib().mc_flow_adam_step(f.handle, lr, _stream(stream)))
+
+
+def mc_flow_train(f, itg, pdf, steps, batch, lr=1e-3, stream=None, losses=True):
+    out = (ctypes.c_double * max(steps, 1))() if losses else None
+    _check(lib().mc_flow_train(f.handle, ctypes.byref(_integrand(itg)), pdf.handle if pdf else None, steps, batch, lr,
+                               _stream(stream), out))
+    return list(out)[:steps] if losses else None
+
+
+def mc_flow_iterate(f, itg, pdf, nevents, iteration=0, stream=None):
+    r = IterResult()
+    _check(lib().mc_flow_iterate(f.handle, ctypes.byref(_integrand(itg)), pdf.handle if pdf else None, nevents,
+                                 iteration, _stream(stream), ctypes.byref(r)))
+    return r
+
+
+__all__ = ["McError", "Integrand", "IterResult", "Result", "Pdf", "Vegas", "Flow", "FlowCfg", "workloads",
+           "pack_flow_params", "unpack_flow_params", *SYMBOLS]

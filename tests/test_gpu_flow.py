@@ -1,0 +1,213 @@
+"""GPU parity of the normalizing-flow sampler (csrc/flow.cu) against the FP64
+flow oracle (oracle/flow.py) with the same BF16 roundings emulated.
+
+Why the bars are not bit-level: the GPU accumulates the dense layers in FP32
+(tensor cores, in an order the oracle does not reproduce) before rounding the
+activations to BF16, so an activation that sits within ~1e-7 relative of a
+BF16 rounding boundary can round the other way (one BF16 ulp, 2^-8 relative);
+the splines and log-determinants run in FP32.  The per-event bars are
+therefore on the median (which no such flip reaches) and a loose maximum;
+gradients, which the BF16 backward products round again, are compared by
+cosine similarity; integrals by their statistical errors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import flow as OF
+from paper_2302_03343_b300 import mcint as M
+from paper_2302_03343_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K, L, H = 32, 6, 256
+
+
+@pytest.fixture(scope="module")
+def gpu(pdf_grid):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_03343_b300 import build
+    build.build()
+    M.lib()
+    torch.cuda.init()
+    return M.mc_pdf_load(pdf_grid)
+
+
+def stats(a):
+    a = np.abs(np.asarray(a, dtype=np.float64)).ravel()
+    return dict(median=float(np.median(a)), p99=float(np.quantile(a, 0.99)), max=float(a.max()))
+
+
+def make_flow(D, seed, last_scale, max_batch, flow_seed=0):
+    arrays = W.flow_init_params(D, L=L, K=K, hidden=H, seed=seed, last_scale=last_scale)
+    f = M.mc_flow_create(D, L, K, arrays, max_batch, seed=flow_seed)
+    return f, arrays
+
+
+@pytest.mark.parametrize("D,n", [(7, 1000), (4, 128), (14, 300)])
+def test_forward_matches_oracle(gpu, D, n):
+    f, arrays = make_flow(D, seed=11, last_scale=2.0, max_batch=n)
+    rng = np.random.default_rng(5)
+    z = rng.random((n, D)).astype(np.float32)
+    zd = torch.tensor(z, device="cuda")
+    x = torch.empty_like(zd)
+    lq = torch.empty(n, dtype=torch.float32, device="cuda")
+    M.mc_flow_forward(f, zd, x, lq)
+    torch.cuda.synchronize()
+    xo, lqo = OF.flow_forward(OF.params_from_arrays(arrays), torch.tensor(z, dtype=OF.DT), K, bf16=True)
+    dx = stats(x.cpu().double().numpy() - xo.numpy())
+    dl = stats(lq.cpu().double().numpy() - lqo.numpy())
+    print(f"\nD={D} n={n} |dx| {dx}  |dlogq| {dl}  logq range [{lqo.min():.3f}, {lqo.max():.3f}]")
+    assert float(lqo.abs().max()) > 0.3  # the flow is far from the identity
+    assert dx["median"] < 1e-6 and dx["max"] < 5e-4
+    assert dl["median"] < 1e-5 and dl["max"] < 5e-3
+    f.free()
+
+
+def test_identity_flow_is_exact(gpu):
+    """Zero last-layer weights: every spline is the identity; x = z, log q = 0."""
+    D, n = 7, 777
+    f, _ = make_flow(D, seed=3, last_scale=0.0, max_batch=1024)
+    z = torch.rand(n, D, generator=torch.Generator().manual_seed(4)).cuda()
+    x = torch.empty_like(z)
+    lq = torch.empty(n, device="cuda")
+    M.mc_flow_forward(f, z, x, lq)
+    torch.cuda.synchronize()
+    assert torch.max(torch.abs(x - z)).item() < 1e-6
+    assert torch.max(torch.abs(lq)).item() < 1e-5
+    f.free()
+
+
+def cosine(a, b):
+    a, b = np.ravel(a).astype(np.float64), np.ravel(b).astype(np.float64)
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
+
+
+@pytest.mark.parametrize("D,n", [(7, 2000), (4, 333)])
+def test_loss_and_gradients_match_oracle(gpu, D, n):
+    f, arrays = make_flow(D, seed=21, last_scale=0.5, max_batch=2048)
+    rng = np.random.default_rng(8)
+    x = rng.random((n, D)).astype(np.float32)
+    w = rng.exponential(size=n).astype(np.float32)
+    loss, grads = M.mc_flow_loss_grad(f, torch.tensor(x, device="cuda"), torch.tensor(w, device="cuda"))
+    lo, go = OF.loss_and_grads(OF.params_from_arrays(arrays), torch.tensor(x, dtype=OF.DT),
+                               torch.tensor(w, dtype=OF.DT), K, bf16=True)
+    print(f"\nD={D} loss gpu {loss:.8f} oracle {lo:.8f}")
+    assert abs(loss - lo) < 1e-4 * max(1.0, abs(lo))
+    allg, allo = [], []
+    for l in range(L):
+        for k in M.FLOW_KEYS:
+            c = cosine(grads[l][k], go[l][k].numpy())
+            nr = np.linalg.norm(grads[l][k]) / (np.linalg.norm(go[l][k].numpy()) + 1e-300)
+            print(f"  layer {l} {k}: cos {c:.6f} norm ratio {nr:.5f}")
+            assert c > 0.9995 and abs(nr - 1.0) < 0.005, (l, k, c, nr)
+            allg.append(np.ravel(grads[l][k]))
+            allo.append(go[l][k].numpy().ravel())
+    assert cosine(np.concatenate(allg), np.concatenate(allo)) > 0.99995
+    f.free()
+
+
+def test_adam_first_step_moves_by_lr(gpu):
+    """First Adam step: m_hat = g and v_hat = g^2, so every parameter moves
+    by -lr g / (|g| + eps) (Sec. "Optimizers"), i.e. by lr against the sign of
+    a gradient much larger than eps; the FP32 parameter rounding bounds the
+    absolute error."""
+    D, n, lr = 7, 1024, 1e-3
+    f, arrays = make_flow(D, seed=5, last_scale=0.5, max_batch=n)
+    rng = np.random.default_rng(9)
+    x = torch.tensor(rng.random((n, D)).astype(np.float32), device="cuda")
+    w = torch.tensor(rng.exponential(size=n).astype(np.float32), device="cuda")
+    _, grads = M.mc_flow_loss_grad(f, x, w)
+    M.mc_flow_adam_step(f, lr)
+    after = M.mc_flow_get_params(f)
+    for l in range(L):
+        for k in M.FLOW_KEYS:
+            g = grads[l][k].astype(np.float64)
+            d = after[l][k].astype(np.float64) - arrays[l][k].astype(np.float64)
+            assert np.all(np.abs(d) <= lr * (1 + 1e-3) + 1e-7)
+            np.testing.assert_allclose(d, -lr * g / (np.abs(g) + 1e-8), rtol=1e-3, atol=2e-7)
+    f.free()
+
+
+def test_params_round_trip(gpu):
+    f, arrays = make_flow(7, seed=2, last_scale=0.7, max_batch=128)
+    back = M.mc_flow_get_params(f)
+    for l in range(L):
+        for k in M.FLOW_KEYS:
+            assert np.array_equal(back[l][k], arrays[l][k])
+    f.free()
+
+
+def oracle_flow_sums(itg, pdf, arrays, D, seed, iteration, n):
+    """The sampling pass written out on the oracle side: Philox uniforms of
+    the FP32 mode, flow forward (FP64 with the BF16 roundings), integrand,
+    weights f / q."""
+    k = O.uniform_ints(seed, 0x20000 + iteration, 0, M.MC_FP32_KAHAN, D, 0, n).astype(np.float64)
+    z = (2.0 * k + 1.0) / 2.0 ** 24
+    x, lq = OF.flow_forward(OF.params_from_arrays(arrays), torch.tensor(z, dtype=OF.DT), K, bf16=True)
+    fv, st = O.integrand_at(itg, pdf, x.numpy())
+    w = np.where(st == 0, fv * np.exp(-lq.numpy()), 0.0)
+    return w
+
+
+@pytest.mark.parametrize("name", ["gg7", "gauss"])
+def test_sampling_pass_matches_oracle(gpu, oracle_pdf, name):
+    itg = {"gg7": W.gg_ttbarg_7d(), "gauss": W.gauss(6, sigma=0.2)}[name]
+    D = itg.ndim()
+    n = 3000
+    f, arrays = make_flow(D, seed=17, last_scale=0.5, max_batch=1024, flow_seed=123)
+    r = M.mc_flow_iterate(f, itg, gpu if name == "gg7" else None, n, iteration=2)
+    w = oracle_flow_sums(itg, oracle_pdf if name == "gg7" else None, arrays, D, 123, 2, n)
+    print(f"\n{name}: gpu sum {r.sum:.10e} oracle {w.sum():.10e} nnz {r.n_nonzero} vs {np.count_nonzero(w)} "
+          f"bad {r.n_bad}")
+    assert r.n == n and r.n_bad == 0
+    assert abs(r.n_nonzero - np.count_nonzero(w)) <= 2
+    assert abs(r.sum - w.sum()) <= 2e-3 * abs(w.sum())
+    assert abs(r.sum2 - (w * w).sum()) <= 5e-3 * (w * w).sum()
+    f.free()
+
+
+def test_training_reduces_variance_and_keeps_the_integral(gpu):
+    """Gaussian of width 0.1 in 4 dimensions (exact integral known): online
+    training lowers the per-event variance many-fold; the estimate stays
+    unbiased within its error."""
+    itg = W.gauss(4, sigma=0.1)
+    exact = W.gauss_exact(4, sigma=0.1)
+    f, _ = make_flow(4, seed=1, last_scale=0.0, max_batch=8192, flow_seed=7)
+    n = 1 << 20
+
+    def estimate(it):
+        r = M.mc_flow_iterate(f, itg, None, n, iteration=it)
+        mean = r.sum / n
+        var = (r.sum2 / n - mean * mean)
+        return mean, var
+
+    m0, v0 = estimate(0)
+    losses = M.mc_flow_train(f, itg, None, steps=300, batch=8192, lr=1e-3)
+    m1, v1 = estimate(1)
+    print(f"\nvariance per event before {v0:.4e} after {v1:.4e} ratio {v0 / v1:.1f}; "
+          f"loss {losses[0]:.4f} -> {losses[-1]:.4f}; estimate {m1:.6f} exact {exact:.6f}")
+    assert v1 < v0 / 10
+    assert abs(m1 - exact) < 4 * math.sqrt(v1 / n)
+    assert abs(m0 - exact) < 4 * math.sqrt(v0 / n)
+    assert losses[-1] < losses[0]
+    f.free()
+
+
+def test_flow_on_gg_ttbarg_agrees_with_fp64_vegas(gpu):
+    itg = W.gg_ttbarg_7d()
+    ref, _ = M.mc_integrate(itg, gpu, niter=10, nevents=1 << 21, nbins=50, seed=3, prec=M.MC_FP64)
+    f, _ = make_flow(7, seed=4, last_scale=0.0, max_batch=1 << 16, flow_seed=9)
+    M.mc_flow_train(f, itg, gpu, steps=100, batch=1 << 14, lr=1e-3, losses=False)
+    n = 1 << 22
+    r = M.mc_flow_iterate(f, itg, gpu, n, iteration=0)
+    mean = r.sum / n
+    sig = math.sqrt(max(r.sum2 / n - mean * mean, 0.0) / n)
+    print(f"\nflow {mean:.6e} +- {sig:.2e}   vegas fp64 {ref.mean:.6e} +- {ref.sigma:.2e}")
+    assert r.n_bad == 0
+    assert abs(mean - ref.mean) < 4 * math.hypot(sig, ref.sigma)
+    f.free()
