@@ -254,6 +254,7 @@ int mc_batch_free(mc_batch b);
  * 16-byte aligned), FP32 accumulation, and the epilogue:
  *   0: C (BF16) = relu(acc + bias)      1: C (FP32) = acc + bias (bias may be NULL)
  *   2: C (BF16) = acc * [mask > 0]       3: C (FP32) += acc (split-K over `splits`)
+ *   4: C (FP32) [splits][M][ldc]: the partial product of each K split
  * M % 128 == 0, K % 64 == 0, bn (the N tile) a multiple of 16 <= 256 that
  * divides N.  err: device int set non-zero if a bounded wait inside the kernel
  * timed out (the result is then invalid).  Asynchronous on `stream`.
@@ -261,6 +262,15 @@ int mc_batch_free(mc_batch b);
 int mc_gemm_bf16(int M, int N, int K, int bn, int epilogue, const void* a, int lda, const void* b, int ldb,
                  const float* bias, void* c, int ldc, const void* mask, int ld_mask, int splits, int* err,
                  void* stream);
+/* mc_gemm_bf16_rs: the same product for a long A and a short B (a dense
+ * layer applied to a batch): a persistent kernel keeps B in shared memory
+ * (bn * K * 2 bytes, K <= 320) and streams the 128-row tiles of A, with the
+ * epilogue of one tile overlapping the MMAs of the next.  Epilogues 0-2 as
+ * above.  c (row-major, ldc) and/or c_t (the transpose, c_t[col * ldt + row],
+ * ldt >= M) receive the result; either may be NULL, not both.  Asynchronous. */
+int mc_gemm_bf16_rs(int M, int N, int K, int bn, int epilogue, const void* a, int lda, const void* b, int ldb,
+                    const float* bias, void* c, int ldc, void* c_t, int ldt, const void* mask, int ld_mask, int* err,
+                    void* stream);
 
 /* ------------------------------------------- allocation-free iteration
  * mc_vegas_iterate_noalloc: the same fused iteration as mc_vegas_iterate, for

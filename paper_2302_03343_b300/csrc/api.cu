@@ -504,7 +504,7 @@ int mc_integrate(const mc_integrand* itg, mc_pdf pdf, int niter, int64_t nevents
 int mc_gemm_bf16(int M, int N, int K, int bn, int epilogue, const void* a, int lda, const void* b, int ldb,
                  const float* bias, void* c, int ldc, const void* mask, int ld_mask, int splits, int* err,
                  void* stream) {
-  if (!a || !b || !c || !err || epilogue < 0 || epilogue > 3 || (epilogue == 2 && !mask))
+  if (!a || !b || !c || !err || epilogue < 0 || epilogue > 4 || (epilogue == 2 && !mask))
     return fail(MC_EINVAL, "mc_gemm_bf16: bad arguments");
   mc::TcGemmArgs g;
   std::memset(&g, 0, sizeof(g));
@@ -515,7 +515,7 @@ int mc_gemm_bf16(int M, int N, int K, int bn, int epilogue, const void* a, int l
   g.epilogue = epilogue;
   g.bias = bias;
   g.ldc = ldc;
-  if (epilogue == 1 || epilogue == 3)
+  if (epilogue == 1 || epilogue >= 3)
     g.c_f32 = static_cast<float*>(c);
   else
     g.c_bf16 = static_cast<__nv_bfloat16*>(c);
@@ -526,6 +526,38 @@ int mc_gemm_bf16(int M, int N, int K, int bn, int epilogue, const void* a, int l
                                     ldb, splits, static_cast<cudaStream_t>(stream));
   if (e == cudaErrorInvalidValue) return fail(MC_EINVAL, "mc_gemm_bf16: unsupported shape or alignment");
   if (e != cudaSuccess) return fail(MC_ECUDA, "mc_gemm_bf16: %s", cudaGetErrorString(e));
+  return MC_OK;
+}
+
+int mc_gemm_bf16_rs(int M, int N, int K, int bn, int epilogue, const void* a, int lda, const void* b, int ldb,
+                    const float* bias, void* c, int ldc, void* c_t, int ldt, const void* mask, int ld_mask, int* err,
+                    void* stream) {
+  if (!a || !b || (!c && !c_t) || !err || epilogue < 0 || epilogue > 2 || (epilogue == 2 && !mask))
+    return fail(MC_EINVAL, "mc_gemm_bf16_rs: bad arguments");
+  mc::TcGemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.bn = bn;
+  g.epilogue = epilogue;
+  g.bias = bias;
+  g.ldc = ldc;
+  g.ldt = ldt;
+  if (epilogue == 1) {
+    g.c_f32 = static_cast<float*>(c);
+    g.c_t_f32 = static_cast<float*>(c_t);
+  } else {
+    g.c_bf16 = static_cast<__nv_bfloat16*>(c);
+    g.c_t_bf16 = static_cast<__nv_bfloat16*>(c_t);
+  }
+  g.mask = static_cast<const __nv_bfloat16*>(mask);
+  g.ld_mask = ld_mask;
+  g.error = err;
+  const cudaError_t e = mc::tc_gemm_rs(g, static_cast<const __nv_bfloat16*>(a), lda,
+                                       static_cast<const __nv_bfloat16*>(b), ldb, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return fail(MC_EINVAL, "mc_gemm_bf16_rs: unsupported shape or alignment");
+  if (e != cudaSuccess) return fail(MC_ECUDA, "mc_gemm_bf16_rs: %s", cudaGetErrorString(e));
   return MC_OK;
 }
 

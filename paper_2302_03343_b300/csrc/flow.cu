@@ -4,18 +4,29 @@
 // Flow: L piecewise-quadratic coupling layers (flow_spline.cuh) over the unit
 // cube; layer l transforms the coordinates d with d % 2 == l % 2 and
 // conditions on the others through a dense network u = 2 x_A - 1 -> 256 ->
-// 256 -> 256 -> d_B (2K + 1) with ReLU.  The first dense layer (K = d_A) runs
-// on the CUDA cores in FP32; the three 256-wide layers run on the tcgen05
-// tensor cores (tc_gemm.cu) with BF16 operands and FP32 accumulation.
+// 256 -> 256 -> (2K + 1) logits per transformed coordinate, with ReLU.  The
+// first dense layer (K = d_A) runs on the CUDA cores in FP32; the three
+// 256-wide layers run on the tcgen05 tensor cores (tc_gemm.cu, persistent
+// B-resident kernel) with BF16 operands and FP32 accumulation.
 //
-// Sampling: Philox uniforms z -> flow forward -> x, log q(x) -> integrand at
-// x -> weight w = f(x) / q(x) -> Kahan FP64 sums (thesis Sec. "Importance
-// sampling", eq. mc_est_is).  Training (online, on events the method itself
-// generates): sample a batch, evaluate f, weights w = |f| / q held fixed, then
-// L = -sum w log q(x) / sum w through the inverse pass (x -> z) with its
-// activations kept, backward through the splines and the dense layers (BF16
-// tensor-core GEMMs for the activation gradients and, split-K over the batch,
-// for the weight gradients), and one Adam step (thesis Sec. "Optimizers").
+// Sampling (thesis Sec. "Importance sampling", eq. mc_est_is): Philox
+// uniforms z -> flow forward -> x, log q(x) -> integrand at x -> w = f / q ->
+// Kahan FP64 sums.  Training (online, on events the method generates itself):
+// sample a batch with the forward pass keeping every layer's activations,
+// evaluate f, hold the weights w = |f| / q fixed, and minimise
+// L = -sum w log q(x) / sum w; since a coupling layer passes its conditioning
+// coordinates through unchanged, the forward activations are exactly those of
+// the density (inverse) pass at x, so the backward runs on them directly:
+// spline backward, activation gradients on the tensor cores (B-resident
+// kernel), weight gradients as split-K products over the batch with a
+// fixed-order reduction, then Adam (thesis Sec. "Optimizers").
+//
+// Layouts (n = padded batch rows, H = 256): points P [n][D]; activations h
+// [n][H] BF16 row-major (A operands) plus their transposes [H][n] (operands of
+// the weight-gradient products, written by the producing epilogue); logits
+// transposed [row][n] FP32 with coordinate j's 2K+1 logits at rows
+// j * ls .. j * ls + 2K (ls = 2K+1 rounded up to 8, so that each coordinate
+// starts on a 16-byte boundary in the row-major gradient).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -33,72 +44,108 @@ namespace mc {
 namespace {
 
 constexpr int kMaxFlowDim = 16;
+constexpr int kMaxA = kMaxFlowDim / 2;
 constexpr int kMaxLayers = 16;
+constexpr int kH = 256;  // hidden width
 
 struct LayerDev {
-  int na, nb, nout, nout_pad;
+  int na, nb, ls, nout_pad;  // conditioning / transformed coordinates, logit stride, padded rows
   int a_idx[kMaxFlowDim], b_idx[kMaxFlowDim];
   // master parameters (FP32) and their gradients / Adam moments share one
   // layout: W1 [H x na], b1 [H], W2 [H x H], b2, W3 [H x H], b3,
   // W4 [nout_pad x H], b4 [nout_pad]; gradients of W2..W4 are kept transposed
-  // (gW^T [in x out]) as the split-K GEMMs produce them.
+  // (gW^T [in x out]) as the weight-gradient products produce them.
   size_t off_W1, off_b1, off_W2, off_b2, off_W3, off_b3, off_W4, off_b4;
-  // BF16 copies for the GEMMs: W2, W3, W4 (row-major [out x in]) and their
-  // transposes [in x out] for the backward activation products
+  // BF16 copies for the tensor cores: W2, W3, W4 (row-major [out x in]) and
+  // their transposes [in x out] for the activation gradients
   __nv_bfloat16 *W2h, *W3h, *W4h, *W2t, *W3t, *W4t;
 };
 
+unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
+
 // ------------------------------------------------------------------ kernels
-__global__ void flow_uniforms_kernel(float* z, long long n, int D, uint64_t seed, uint32_t iteration, uint32_t gid,
-                                     long long first) {
+// z: FP32-mode Philox uniforms (2k + 1) / 2^24 of events first + i.
+__global__ void flow_uniforms_kernel(float* z, long long n, int D, uint64_t seed, uint32_t iteration, long long first) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint64_t k[kMaxFlowDim];
-  event_uniforms<kMaxFlowDim, false>(seed, iteration, gid, uint64_t(first + i), D, k);
+  event_uniforms<kMaxFlowDim, false>(seed, iteration, 0u, uint64_t(first + i), D, k);
   for (int d = 0; d < D; ++d) z[i * D + d] = float(uint32_t(2 * k[d] + 1)) * 0x1p-24f;
 }
 
-// h1 = bf16(relu(W1 (2 x_A - 1) + b1)), one thread per (event, hidden unit).
-__global__ void dense1_kernel(const float* P, int D, const LayerDev L, const float* params, __nv_bfloat16* h1, int H,
-                              long long n) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * H) return;
-  const long long i = idx / H;
-  const int j = int(idx % H);
-  const float* W1 = params + L.off_W1 + size_t(j) * L.na;
-  float acc = params[L.off_b1 + j];
-  for (int a = 0; a < L.na; ++a) acc += W1[a] * (2.0f * P[i * D + L.a_idx[a]] - 1.0f);
-  h1[idx] = __float2bfloat16_rn(fmaxf(acc, 0.0f));
-}
-
-// Forward spline of one layer, in place on P; logq -= sum log c.
-__global__ void spline_fwd_kernel(float* P, int D, const LayerDev L, const float* logits, int K, float* logq,
-                                  long long n) {
+// h1 = bf16(relu(W1 (2 x_A - 1) + b1)) for one event per thread: row-major
+// h1 [n][H] (16-byte stores) and, if hT, its transpose [H][n] (coalesced).
+__global__ void __launch_bounds__(128) dense1_kernel(const float* P, int D, const LayerDev L, const float* params,
+                                                     __nv_bfloat16* h1, __nv_bfloat16* hT, long long n) {
+  __shared__ float w1[kH * kMaxA], b1[kH];
+  const int na = L.na;
+  for (int t = threadIdx.x; t < kH * na; t += blockDim.x) w1[t] = params[L.off_W1 + t];
+  for (int t = threadIdx.x; t < kH; t += blockDim.x) b1[t] = params[L.off_b1 + t];
+  __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  SplineCoef s;
+  float u[kMaxA];
+#pragma unroll
+  for (int a = 0; a < kMaxA; ++a) u[a] = a < na ? 2.0f * P[i * D + L.a_idx[a]] - 1.0f : 0.0f;
+  uint4* row = reinterpret_cast<uint4*>(h1 + size_t(i) * kH);
+  for (int j8 = 0; j8 < kH / 8; ++j8) {
+    uint4 pk;
+    uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float o[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int j = j8 * 8 + 2 * q + e;
+        float acc = b1[j];
+#pragma unroll
+        for (int a = 0; a < kMaxA; ++a)
+          if (a < na) acc += w1[j * na + a] * u[a];
+        o[e] = fmaxf(acc, 0.0f);
+      }
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(o[0], o[1]);
+      pw[q] = *reinterpret_cast<const uint32_t*>(&hh);
+      if (hT) {
+        hT[size_t(j8 * 8 + 2 * q) * n + i] = hh.x;
+        hT[size_t(j8 * 8 + 2 * q + 1) * n + i] = hh.y;
+      }
+    }
+    row[j8] = pk;
+  }
+}
+
+// Forward spline of one layer for one event per thread: Pout = Pin with the
+// transformed coordinates mapped (Pout may equal Pin); logq -= sum log c.
+// Logits transposed: LT[(j * ls + k) * ldn + i].
+__global__ void __launch_bounds__(128) spline_fwd_kernel(const float* Pin, float* Pout, int D, const LayerDev L,
+                                                         const float* LT, size_t ldn, int K, float* logq, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (Pout != Pin)
+    for (int a = 0; a < L.na; ++a) Pout[i * D + L.a_idx[a]] = Pin[i * D + L.a_idx[a]];
+  Spline s;
   float ld = 0.0f;
   for (int j = 0; j < L.nb; ++j) {
-    spline_coef(logits + i * L.nout_pad + j * (2 * K + 1), K, s);
+    spline_load(LT + size_t(j) * L.ls * ldn + i, ldn, K, s);
     float lc;
     const int d = L.b_idx[j];
-    P[i * D + d] = spline_fwd(s, K, P[i * D + d], &lc);
+    Pout[i * D + d] = spline_fwd(s, K, Pin[i * D + d], &lc);
     ld += lc;
   }
   logq[i] -= ld;
 }
 
-// Inverse spline of one layer: Pout = Pin with the B coordinates inverted;
-// logq -= sum log c.
-__global__ void spline_inv_kernel(const float* Pin, float* Pout, int D, const LayerDev L, const float* logits, int K,
-                                  float* logq, long long n) {
+// Inverse spline of one layer: Pout = Pin with the transformed coordinates
+// inverted; logq -= sum log c.
+__global__ void __launch_bounds__(128) spline_inv_kernel(const float* Pin, float* Pout, int D, const LayerDev L,
+                                                         const float* LT, size_t ldn, int K, float* logq, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  for (int d = 0; d < D; ++d) Pout[i * D + d] = Pin[i * D + d];
-  SplineCoef s;
+  for (int a = 0; a < L.na; ++a) Pout[i * D + L.a_idx[a]] = Pin[i * D + L.a_idx[a]];
+  Spline s;
   float ld = 0.0f;
   for (int j = 0; j < L.nb; ++j) {
-    spline_coef(logits + i * L.nout_pad + j * (2 * K + 1), K, s);
+    spline_load(LT + size_t(j) * L.ls * ldn + i, ldn, K, s);
     float lc;
     const int d = L.b_idx[j];
     Pout[i * D + d] = spline_inv(s, K, Pin[i * D + d], &lc);
@@ -108,132 +155,149 @@ __global__ void spline_inv_kernel(const float* Pin, float* Pout, int D, const La
 }
 
 // Backward of one inverse layer.  dP holds dL/d(layer output) on entry and
-// dL/d(layer input) for the B coordinates on exit (the A coordinates receive
-// the conditioner's contribution later); gl_i = dL/d(log q_i) = -w_i / sum w.
-__global__ void spline_inv_bwd_kernel(const float* Pin, float* dP, int D, const LayerDev L, const float* logits, int K,
-                                      const float* w, const double* wsum, float* glog32, __nv_bfloat16* glog16,
-                                      long long n, long long n_real) {
+// dL/d(layer input) for the transformed coordinates on exit (the conditioning
+// coordinates receive the conditioner's contribution later);
+// gl_i = dL/d(log q_i) = -w_i / sum w.  The logit gradients go out in BF16
+// row-major G [n][nout_pad] (operand of the activation gradient) and
+// transposed GT [nout_pad][n] (operand of the weight gradient).
+__global__ void __launch_bounds__(128) spline_inv_bwd_kernel(const float* Pin, float* dP, int D, const LayerDev L,
+                                                             const float* LT, int K, const float* w,
+                                                             const double* wsum, __nv_bfloat16* G,
+                                                             __nv_bfloat16* GT, long long n, long long n_real) {
+  constexpr int kRow = 2 * kFlowMaxBins + 9;  // odd stride >= 2K+1: conflict-free rows
+  __shared__ float gsh[128][kRow];
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float gl = i < n_real ? float(-double(w[i]) / *wsum) : 0.0f;
-  SplineCoef s;
-  float g[2 * kFlowMaxBins + 1];
+  if (i >= n) return;  // no block-wide barrier below
+  float* gs = gsh[threadIdx.x];
+  const bool real = i < n_real;
+  const float gl = real ? float(-double(w[i]) / *wsum) : 0.0f;
+  const size_t ldn = size_t(n);
+  const int K2 = 2 * K + 1;
+  Spline s;
+  float gw[kFlowMaxBins], gv[kFlowMaxBins + 1];
   for (int j = 0; j < L.nb; ++j) {
     const int d = L.b_idx[j];
-    const size_t row = size_t(i) * L.nout_pad + j * (2 * K + 1);
-    if (i < n_real) {
-      spline_coef(logits + row, K, s);
-      dP[i * D + d] = spline_inv_bwd(s, K, Pin[i * D + d], dP[i * D + d], gl, g);
+    if (real) {
+      spline_load(LT + size_t(j) * L.ls * ldn + i, ldn, K, s);
+      dP[i * D + d] = spline_inv_bwd(s, K, Pin[i * D + d], dP[i * D + d], gl, gw, gv);
+#pragma unroll
+      for (int k = 0; k < kFlowMaxBins; ++k)
+        if (k < K) gs[k] = gw[k];
+#pragma unroll
+      for (int k = 0; k <= kFlowMaxBins; ++k)
+        if (k <= K) gs[K + k] = gv[k];
     } else {
       dP[i * D + d] = 0.0f;
-      for (int k = 0; k < 2 * K + 1; ++k) g[k] = 0.0f;
+      for (int k = 0; k < K2; ++k) gs[k] = 0.0f;
     }
-    for (int k = 0; k < 2 * K + 1; ++k) {
-      glog32[row + k] = g[k];
-      glog16[row + k] = __float2bfloat16_rn(g[k]);
+    for (int k = K2; k < L.ls; ++k) gs[k] = 0.0f;
+    // transposed rows (coalesced over events)
+    __nv_bfloat16* gt = GT + size_t(j) * L.ls * ldn + i;
+    for (int k = 0; k < K2; ++k) gt[size_t(k) * ldn] = __float2bfloat16_rn(gs[k]);
+    // row-major block of ls entries (zero padded), 16-byte stores
+    uint4* gr = reinterpret_cast<uint4*>(G + size_t(i) * L.nout_pad + size_t(j) * L.ls);
+    for (int c8 = 0; c8 < L.ls / 8; ++c8) {
+      uint4 pk;
+      uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(gs[c8 * 8 + 2 * e], gs[c8 * 8 + 2 * e + 1]);
+        pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+      }
+      gr[c8] = pk;
     }
-  }
-  for (int c = L.nb * (2 * K + 1); c < L.nout_pad; ++c) {  // padding columns
-    glog32[size_t(i) * L.nout_pad + c] = 0.0f;
-    glog16[size_t(i) * L.nout_pad + c] = __float2bfloat16_rn(0.0f);
   }
 }
 
-// First dense layer backward, input side: dL/dx_A += 2 W1^T dA1 (u = 2 x_A - 1);
-// one thread per event, W1 [H x na] staged in shared memory.
-constexpr int kMaxA = kMaxFlowDim / 2;
-__global__ void dense1_bwd_input_kernel(float* dP, int D, const LayerDev L, const float* params,
-                                        const __nv_bfloat16* dA1, int H, long long n) {
-  extern __shared__ float w1[];  // [H * na]
+// First dense layer backward, input side: dL/dx_A += 2 W1^T dA1 (u = 2 x_A - 1),
+// one event per thread reading the transposed gradient dA1T [H][n].
+__global__ void __launch_bounds__(128) dense1_bwd_input_kernel(float* dP, int D, const LayerDev L,
+                                                               const float* params, const __nv_bfloat16* dA1T,
+                                                               long long n) {
+  __shared__ float w1[kH * kMaxA];
   const int na = L.na;
-  for (int t = threadIdx.x; t < H * na; t += blockDim.x) w1[t] = params[L.off_W1 + t];
+  for (int t = threadIdx.x; t < kH * na; t += blockDim.x) w1[t] = params[L.off_W1 + t];
   __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float gu[kMaxA];
 #pragma unroll
   for (int a = 0; a < kMaxA; ++a) gu[a] = 0.0f;
-  const uint4* row = reinterpret_cast<const uint4*>(dA1 + size_t(i) * H);
-  for (int j8 = 0; j8 < H / 8; ++j8) {
-    const uint4 v = row[j8];
-    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+  for (int j = 0; j < kH; ++j) {
+    const float g = __bfloat162float(dA1T[size_t(j) * n + i]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float2 g = __bfloat1622float2(h2[q]);
-      const float* wa = w1 + (j8 * 8 + 2 * q) * na;
-#pragma unroll
-      for (int a = 0; a < kMaxA; ++a)
-        if (a < na) gu[a] += g.x * wa[a] + g.y * wa[na + a];
-    }
+    for (int a = 0; a < kMaxA; ++a)
+      if (a < na) gu[a] += g * w1[j * na + a];
   }
 #pragma unroll
   for (int a = 0; a < kMaxA; ++a)
     if (a < na) dP[i * D + L.a_idx[a]] += 2.0f * gu[a];
 }
 
-// First dense layer backward, weight side: dL/dW1[j][a] = sum_i dA1[i][j] u[i][a]
-// and dL/db1[j] = sum_i dA1[i][j]; a block of H threads (one per hidden unit)
-// over `rows` events staged in shared memory, then one atomic per entry.
-__global__ void dense1_bwd_weight_kernel(const float* Pin, int D, const LayerDev L, const __nv_bfloat16* dA1, int H,
-                                         long long n, int rows, float* grads) {
-  extern __shared__ float u[];  // [rows * na]
-  const int na = L.na;
-  const long long r0 = (long long)blockIdx.x * rows;
-  const int nr = int(min((long long)rows, n - r0));
-  for (int t = threadIdx.x; t < nr * na; t += blockDim.x) {
-    const int r = t / na, a = t % na;
-    u[t] = 2.0f * Pin[(r0 + r) * D + L.a_idx[a]] - 1.0f;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < H; j += blockDim.x) {
-    float acc[kMaxA], accb = 0.0f;
+// First dense layer backward, weight side: one block per hidden unit j,
+// dL/dW1[j][a] += sum_i dA1[i][j] u_i[a] and dL/db1[j] += sum_i dA1[i][j]
+// (block reduction in a fixed order: deterministic).
+__global__ void __launch_bounds__(256) dense1_bwd_weight_kernel(const float* Pin, int D, const LayerDev L,
+                                                                const __nv_bfloat16* dA1T, long long n,
+                                                                float* grads) {
+  __shared__ float red[kMaxA + 1][8];
+  const int j = blockIdx.x, na = L.na;
+  float acc[kMaxA + 1];
 #pragma unroll
-    for (int a = 0; a < kMaxA; ++a) acc[a] = 0.0f;
-    for (int r = 0; r < nr; ++r) {
-      const float g = __bfloat162float(dA1[size_t(r0 + r) * H + j]);
-      accb += g;
-#pragma unroll
-      for (int a = 0; a < kMaxA; ++a)
-        if (a < na) acc[a] += g * u[r * na + a];
-    }
+  for (int a = 0; a <= kMaxA; ++a) acc[a] = 0.0f;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const float g = __bfloat162float(dA1T[size_t(j) * n + i]);
+    if (g == 0.0f) continue;
+    acc[kMaxA] += g;
 #pragma unroll
     for (int a = 0; a < kMaxA; ++a)
-      if (a < na) atomicAdd(&grads[L.off_W1 + size_t(j) * na + a], acc[a]);
-    atomicAdd(&grads[L.off_b1 + j], accb);
+      if (a < na) acc[a] += g * (2.0f * Pin[i * D + L.a_idx[a]] - 1.0f);
   }
-}
-
-// out[c] += sum over rows of m[r][c] (bias gradients); one thread per column
-// and block-row chunk.
-template <class T>
-__global__ void colsum_kernel(const T* m, long long rows, int cols, int ld, float* out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  const long long r0 = (long long)blockIdx.y * 1024, r1 = min(rows, r0 + 1024);
-  float acc = 0.0f;
-  for (long long r = r0; r < r1; ++r) acc += float(m[r * ld + c]);
-  atomicAdd(&out[c], acc);
-}
-
-// dst[c][r] = src[r][c] for a BF16 [rows x cols] matrix (32 x 32 tiles).
-__global__ void transpose_bf16_kernel(const __nv_bfloat16* src, long long rows, int cols, __nv_bfloat16* dst) {
-  __shared__ __nv_bfloat16 tile[32][33];
-  const long long r0 = (long long)blockIdx.y * 32;
-  const int c0 = blockIdx.x * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const long long r = r0 + k;
-    const int c = c0 + threadIdx.x;
-    if (r < rows && c < cols) tile[k][threadIdx.x] = src[r * cols + c];
+#pragma unroll
+  for (int a = 0; a <= kMaxA; ++a) {
+    float v = acc[a];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
   }
   __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int c = c0 + k;
-    const long long r = r0 + threadIdx.x;
-    if (r < rows && c < cols) dst[size_t(c) * rows + r] = tile[threadIdx.x][k];
+  if (threadIdx.x <= kMaxA) {
+    const int a = threadIdx.x;
+    float v = 0.0f;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[a][w];
+    if (a == kMaxA)
+      grads[L.off_b1 + j] += v;
+    else if (a < na)
+      grads[L.off_W1 + size_t(j) * na + a] += v;
   }
 }
 
-// Integrand at given points (no VEGAS map): f[i] = f(x_i), FP32 path.
+// out[r] += sum_i XT[r][i] over a BF16 matrix XT [rows][n]: one block per
+// row, fixed-order reduction (bias gradients from transposed gradients).
+__global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* XT, long long n, float* out) {
+  __shared__ float red[8];
+  const uint4* row = reinterpret_cast<const uint4*>(XT + size_t(blockIdx.x) * n);
+  float acc = 0.0f;
+  for (long long c = threadIdx.x; c < n / 8; c += blockDim.x) {
+    const uint4 v = row[c];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = __bfloat1622float2(h[q]);
+      acc += f.x + f.y;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.0f;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[w];
+    out[blockIdx.x] += v;
+  }
+}
+
+// Integrand at given points (no VEGAS map): f[i] = f(x_i) in FP32; a failed
+// event (non-finite, or unconverged phase space) is marked NaN.
 template <int PROC>
 __global__ void __launch_bounds__(128) points_kernel(KernelArgs a, const float* X, int D, float* f, long long n) {
   constexpr int NFL = ProcTraits<PROC>::NFL;
@@ -255,9 +319,56 @@ __global__ void __launch_bounds__(128) points_kernel(KernelArgs a, const float* 
 #pragma unroll
     for (int d = 0; d < MAXD; ++d) x[d] = d < D ? X[i * D + d] : 0.5f;
     const EventOut o = integrand<PROC, float>(a, pdf, x, nullptr);
-    // a failed event (non-finite or unconverged phase space) is marked NaN
     f[i] = (o.status == 0 && isfinite(o.f)) ? float(o.f) : __int_as_float(0x7fc00000);
   }
+}
+
+// The sampling pass's integrand fused with its sums: w = f(x) / q(x) =
+// f exp(-log q), Kahan FP64 per thread, block partials (BlockPartial).
+template <int PROC>
+__global__ void __launch_bounds__(128) points_sums_kernel(KernelArgs a, const float* X, const float* logq, int D,
+                                                          long long n, BlockPartial* parts) {
+  constexpr int NFL = ProcTraits<PROC>::NFL;
+  constexpr int MAXD = ProcTraits<PROC>::MAXD;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* sh_pdf = reinterpret_cast<float*>(smem);
+  __shared__ BlockPartial warp_part[4];
+  SmPdf<float> pdf;
+  if constexpr (NFL > 0) {
+    const int nx = a.pdf.nx;
+    float* t = sh_pdf;
+    float* fv = t + nx;
+    float* d = fv + NFL * nx;
+    build_pdf_tables<float>(a.pdf, a.logq2_f, a.fl, NFL, t, fv, d);
+#pragma unroll
+    for (int k = 0; k < NFL; ++k) pdf.tab[k] = {t, fv + k * nx, d + k * nx, nx};
+  }
+  Acc acc;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float x[MAXD];
+#pragma unroll
+    for (int d = 0; d < MAXD; ++d) x[d] = d < D ? X[i * D + d] : 0.5f;
+    const EventOut o = integrand<PROC, float>(a, pdf, x, nullptr);
+    double w = o.f * exp(-double(logq[i]));
+    if (o.status != 0 || !isfinite(w)) {
+      if (o.status == MC_ENOCONV)
+        ++acc.nnoconv;
+      else
+        ++acc.nbad;
+      w = 0.0;
+    }
+    const double y = w - acc.s_c;
+    const double t = acc.s_hi + y;
+    acc.s_c = (t - acc.s_hi) - y;
+    acc.s_hi = t;
+    const double y2 = w * w - acc.q_c;
+    const double t2 = acc.q_hi + y2;
+    acc.q_c = (t2 - acc.q_hi) - y2;
+    acc.q_hi = t2;
+    if (w != 0.0) ++acc.nnz;
+    acc.wmax = fmax(acc.wmax, w);
+  }
+  block_reduce(acc, warp_part, &parts[blockIdx.x]);
 }
 
 // Training weights w = |f| / q = |f| exp(-log q) (0 for a failed event).
@@ -296,55 +407,27 @@ __global__ void loss_sums_kernel(const float* w, const float* logq, long long n,
   }
 }
 
-// Sampling sums over a chunk: w = f exp(-log q) accumulated with Kahan FP64
-// per thread into per-block partials (BlockPartial, fixed-order reduced).
-__global__ void flow_sums_kernel(const float* f, const float* logq, long long n, BlockPartial* parts) {
-  Acc acc;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double w = double(f[i]) * exp(-double(logq[i]));
-    if (!isfinite(w)) {
-      ++acc.nbad;
-      w = 0.0;
-    }
-    const double y = w - acc.s_c;
-    const double t = acc.s_hi + y;
-    acc.s_c = (t - acc.s_hi) - y;
-    acc.s_hi = t;
-    const double y2 = w * w - acc.q_c;
-    const double t2 = acc.q_hi + y2;
-    acc.q_c = (t2 - acc.q_hi) - y2;
-    acc.q_hi = t2;
-    if (w != 0.0) ++acc.nnz;
-    acc.wmax = fmax(acc.wmax, w);
-  }
-  __shared__ BlockPartial warp_part[8];
-  block_reduce(acc, warp_part, &parts[blockIdx.x]);
-}
-
 // Adam (thesis Sec. "Optimizers") on every master parameter; gradients of the
-// 256-wide weights are read from their transposed layout.  Then the BF16
-// copies (and transposes) are refreshed and the gradients cleared.
+// 256-wide weights are read from their transposed layout.
 struct AdamArgs {
   float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1 - b1^t), c2 = 1/(1 - b2^t)
 };
-__global__ void adam_kernel(float* params, float* grads, float* m, float* v, size_t n, const LayerDev* layers, int nl,
-                            int H, AdamArgs A) {
+__global__ void adam_kernel(float* params, const float* grads, float* m, float* v, size_t n, const LayerDev* layers,
+                            int nl, AdamArgs A) {
   const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= n) return;
-  // locate the tensor: transposed-gradient mapping for W2, W3, W4
   size_t gidx = idx;
   for (int l = 0; l < nl; ++l) {
     const LayerDev& L = layers[l];
     auto tr = [&](size_t off, int rows, int cols) {  // W [rows x cols], gradient stored [cols x rows]
       if (idx >= off && idx < off + size_t(rows) * cols) {
         const size_t e = idx - off;
-        const size_t r = e / cols, c = e % cols;
-        gidx = off + c * rows + r;
+        gidx = off + (e % cols) * rows + e / cols;
       }
     };
-    tr(L.off_W2, H, H);
-    tr(L.off_W3, H, H);
-    tr(L.off_W4, L.nout_pad, H);
+    tr(L.off_W2, kH, kH);
+    tr(L.off_W3, kH, kH);
+    tr(L.off_W4, L.nout_pad, kH);
   }
   const float g = grads[gidx];
   const float mi = A.b1 * m[idx] + (1.0f - A.b1) * g;
@@ -369,32 +452,33 @@ __global__ void to_bf16_kernel(const float* W, int rows, int cols, __nv_bfloat16
   out_t[size_t(c) * rows + r] = h;
 }
 
-unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
-
 }  // namespace
 }  // namespace mc
 
 using mc::BlockPartial;
 using mc::LayerDev;
+using mc::kH;
 
 struct mc_flow_s {
-  int device = 0, D = 0, L = 0, K = 0, H = 256;
+  int device = 0, D = 0, L = 0, K = 0;
   long long max_batch = 0, bp = 0;  // capacity (rows, padded to 128)
   uint64_t seed = 0;
   int step = 0;
   std::vector<LayerDev> layers;
-  size_t nparam = 0;                // device master-parameter count (padded layout)
-  std::vector<size_t> host_map;     // packed host index -> device index
+  size_t nparam = 0;             // device master-parameter count (padded layout)
+  std::vector<size_t> host_map;  // packed host index -> device index
   float *d_params = nullptr, *d_grads = nullptr, *d_m = nullptr, *d_v = nullptr;
-  __nv_bfloat16* d_wbf = nullptr;   // BF16 weights and transposes of all layers
+  __nv_bfloat16* d_wbf = nullptr;  // BF16 weights and transposes of all layers
   LayerDev* d_layers = nullptr;
   // workspace
-  float *P = nullptr, *logq = nullptr, *f = nullptr, *w = nullptr, *dP = nullptr;
-  float *logits = nullptr, *glog32 = nullptr;
-  __nv_bfloat16 *h = nullptr, *glog16 = nullptr, *dA = nullptr, *tA = nullptr, *tB = nullptr;
+  float *P = nullptr, *logq = nullptr, *f = nullptr, *w = nullptr, *dP = nullptr, *LT = nullptr;
+  __nv_bfloat16 *h = nullptr, *hT = nullptr, *G = nullptr, *GT = nullptr, *dA = nullptr, *dAT = nullptr;
+  float* part = nullptr;  // split-K partial products of the weight gradients
+  int max_splits = 0;
   double* sums = nullptr;
   double* h_sums = nullptr;  // pinned
-  BlockPartial *parts = nullptr, *total = nullptr, *h_total = nullptr;
+  BlockPartial *parts = nullptr, *chunk_totals = nullptr, *total = nullptr, *h_total = nullptr;
+  long long max_chunks = 0;
   int* err = nullptr;
   int nout_pad_max = 0;
 };
@@ -412,161 +496,167 @@ int ffail(int code, const std::string& msg) {
     if (e_ != cudaSuccess) return ffail(MC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+constexpr int kPartsGrid = 148 * 8;  // blocks of the fused sampling integrand
+
 long long pad128(long long n) { return (n + 127) / 128 * 128; }
 
 float* P_of(mc_flow F, int l) { return F->P + size_t(l) * F->bp * F->D; }
-__nv_bfloat16* h_of(mc_flow F, int l, int k) { return F->h + (size_t(l) * 3 + k) * F->bp * F->H; }
-float* logits_of(mc_flow F, int l) { return F->logits + size_t(l) * F->bp * F->nout_pad_max; }
+__nv_bfloat16* h_of(mc_flow F, int l, int k) { return F->h + (size_t(l) * 3 + k) * F->bp * kH; }
+__nv_bfloat16* hT_of(mc_flow F, int l, int k) { return F->hT + (size_t(l) * 3 + k) * F->bp * kH; }
+float* LT_of(mc_flow F, int l) { return F->LT + size_t(l) * F->bp * F->nout_pad_max; }
 
-// N tile: the largest multiple of 16 up to 256 that divides N (N % 64 == 0).
+// N tile: the largest multiple of 16 up to 256 that divides N.
 int pick_bn(int N) {
   for (int bn = std::min(256, N) / 16 * 16; bn >= 16; bn -= 16)
     if (N % bn == 0) return bn;
   return 16;
 }
 
-// split-K factor for a weight-gradient product (K = batch): about two CTAs
-// per SM, at least four 64-deep k-blocks per split.
-int pick_splits(int M, int N, long long K) {
-  const int tiles = (M / 128) * (N / pick_bn(N));
-  const long long kb = K / 64;
-  return int(std::max<long long>(1, std::min<long long>(kb / 4, (2 * 148 + tiles - 1) / tiles)));
-}
-
-int gemm(mc_flow F, int M, int N, int K, int epi, const __nv_bfloat16* a, int lda, const __nv_bfloat16* b, int ldb,
-         const float* bias, void* c, int ldc, const __nv_bfloat16* mask, int splits, cudaStream_t st) {
+// Persistent B-resident product out = epilogue(A [n x K] . B^T), B [N x K].
+int gemm_rs(mc_flow F, long long n, int N, int K, int epi, const __nv_bfloat16* a, const __nv_bfloat16* b,
+            const float* bias, void* c, void* c_t, const __nv_bfloat16* mask, cudaStream_t st) {
   FLOW_CUDA(cudaGetLastError());  // launches queued before this product
   mc::TcGemmArgs g;
   std::memset(&g, 0, sizeof(g));
-  g.M = M;
+  g.M = int(n);
   g.N = N;
   g.K = K;
   g.bn = pick_bn(N);
   g.epilogue = epi;
   g.bias = bias;
-  g.ldc = ldc;
-  if (epi == mc::kEpiBiasF32 || epi == mc::kEpiAtomicF32)
+  g.ldc = N;
+  g.ldt = int(n);
+  if (epi == mc::kEpiBiasF32) {
     g.c_f32 = static_cast<float*>(c);
-  else
+    g.c_t_f32 = static_cast<float*>(c_t);
+  } else {
     g.c_bf16 = static_cast<__nv_bfloat16*>(c);
+    g.c_t_bf16 = static_cast<__nv_bfloat16*>(c_t);
+  }
   g.mask = mask;
-  g.ld_mask = ldc;
+  g.ld_mask = N;
   g.error = F->err;
-  FLOW_CUDA(mc::tc_gemm(g, a, lda, b, ldb, splits, st));
+  FLOW_CUDA(mc::tc_gemm_rs(g, a, K, b, K, st));
   return MC_OK;
 }
 
-// Conditioner of layer l on the points P (rows n padded to F->bp granularity):
-// h1..h3 into the layer's activation slots, logits into logits_of(l).
-int conditioner(mc_flow F, int l, const float* P, long long n, bool keep, cudaStream_t st) {
-  const LayerDev& L = F->layers[l];
-  const int H = F->H;
-  const int slot = keep ? l : 0;
-  __nv_bfloat16 *h1 = h_of(F, slot, 0), *h2 = h_of(F, slot, 1), *h3 = h_of(F, slot, 2);
-  mc::dense1_kernel<<<mc::blocks_for(n * H, 256), 256, 0, st>>>(P, F->D, L, F->d_params, h1, H, n);
-  if (int rc = gemm(F, int(n), H, H, mc::kEpiBiasReluBf16, h1, H, L.W2h, H, F->d_params + L.off_b2, h2, H, nullptr, 1,
-                    st))
-    return rc;
-  if (int rc = gemm(F, int(n), H, H, mc::kEpiBiasReluBf16, h2, H, L.W3h, H, F->d_params + L.off_b3, h3, H, nullptr, 1,
-                    st))
-    return rc;
-  return gemm(F, int(n), L.nout_pad, H, mc::kEpiBiasF32, h3, H, L.W4h, H, F->d_params + L.off_b4,
-              logits_of(F, keep ? l : 0), L.nout_pad, nullptr, 1, st);
+// Weight gradient gW^T [H x N] += XT [H x n] . YT [N x n]^T (both transposed
+// activations / gradients, K = n): split-K partial tiles, then a fixed-order
+// sum into the gradient.
+int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* XT, const __nv_bfloat16* YT, float* gWt,
+               cudaStream_t st) {
+  FLOW_CUDA(cudaGetLastError());
+  const int bn = pick_bn(N);
+  const int tiles = (kH / 128) * (N / bn);
+  const int kb = int(n / 64);
+  int splits = std::max(1, std::min({F->max_splits, (148 + tiles - 1) / tiles, kb}));
+  const int per = (kb + splits - 1) / splits;  // k blocks per split: no split left empty
+  splits = (kb + per - 1) / per;
+  mc::TcGemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.M = kH;
+  g.N = N;
+  g.K = int(n);
+  g.bn = bn;
+  g.epilogue = mc::kEpiPartialF32;
+  g.c_f32 = F->part;
+  g.ldc = N;
+  g.error = F->err;
+  FLOW_CUDA(mc::tc_gemm(g, XT, int(n), YT, int(n), splits, st));
+  FLOW_CUDA(mc::tc_reduce_splits(F->part, splits, size_t(kH) * N, gWt, st));
+  return MC_OK;
 }
 
-// Forward (sampling) pass over n (multiple of 128) rows of P[0] -> P[0] in
-// place; logq initialised to 0 and accumulated.
-int forward_pass(mc_flow F, long long n, cudaStream_t st) {
-  float* P = P_of(F, 0);
+// Conditioner of layer l on the points P (n rows): activations into slot
+// `slot` (with their transposes when `keep`), transposed logits into LT_of(slot).
+int conditioner(mc_flow F, int l, int slot, const float* P, long long n, bool keep, cudaStream_t st) {
+  const LayerDev& L = F->layers[l];
+  const float* prm = F->d_params;
+  __nv_bfloat16 *h1 = h_of(F, slot, 0), *h2 = h_of(F, slot, 1), *h3 = h_of(F, slot, 2);
+  mc::dense1_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P, F->D, L, prm, h1, keep ? hT_of(F, slot, 0) : nullptr,
+                                                             n);
+  if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiBiasReluBf16, h1, L.W2h, prm + L.off_b2, h2,
+                       keep ? hT_of(F, slot, 1) : nullptr, nullptr, st))
+    return rc;
+  if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiBiasReluBf16, h2, L.W3h, prm + L.off_b3, h3,
+                       keep ? hT_of(F, slot, 2) : nullptr, nullptr, st))
+    return rc;
+  return gemm_rs(F, n, L.nout_pad, kH, mc::kEpiBiasF32, h3, L.W4h, prm + L.off_b4, nullptr, LT_of(F, slot), nullptr,
+                 st);
+}
+
+// Forward (sampling direction) from P[0] = z over n (multiple of 128) rows;
+// logq initialised to 0.  keep: layer l writes P[l+1] and keeps its
+// activations (training); otherwise P[0] is mapped in place (sampling).
+int forward_pass(mc_flow F, long long n, bool keep, cudaStream_t st) {
   FLOW_CUDA(cudaMemsetAsync(F->logq, 0, sizeof(float) * n, st));
   for (int l = 0; l < F->L; ++l) {
-    if (int rc = conditioner(F, l, P, n, false, st)) return rc;
-    mc::spline_fwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P, F->D, F->layers[l], logits_of(F, 0), F->K,
-                                                                   F->logq, n);
+    const int slot = keep ? l : 0;
+    const float* Pin = keep ? P_of(F, l) : P_of(F, 0);
+    float* Pout = keep ? P_of(F, l + 1) : P_of(F, 0);
+    if (int rc = conditioner(F, l, slot, Pin, n, keep, st)) return rc;
+    mc::spline_fwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(Pin, Pout, F->D, F->layers[l], LT_of(F, slot),
+                                                                   size_t(n), F->K, F->logq, n);
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
 
 // Inverse (density) pass from P[L] (the points x) down to P[0] = z, keeping
-// every layer's activations and logits; logq accumulated.
+// every layer's activations; logq accumulated from 0.
 int inverse_pass(mc_flow F, long long n, cudaStream_t st) {
   FLOW_CUDA(cudaMemsetAsync(F->logq, 0, sizeof(float) * n, st));
   for (int l = F->L - 1; l >= 0; --l) {
-    if (int rc = conditioner(F, l, P_of(F, l + 1), n, true, st)) return rc;
+    if (int rc = conditioner(F, l, l, P_of(F, l + 1), n, true, st)) return rc;
     mc::spline_inv_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P_of(F, l + 1), P_of(F, l), F->D, F->layers[l],
-                                                                   logits_of(F, l), F->K, F->logq, n);
+                                                                   LT_of(F, l), size_t(n), F->K, F->logq, n);
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
 
-void transpose(const __nv_bfloat16* src, long long rows, int cols, __nv_bfloat16* dst, cudaStream_t st) {
-  const dim3 grid(unsigned((cols + 31) / 32), unsigned((rows + 31) / 32));
-  mc::transpose_bf16_kernel<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, dst);
-}
-
-// Backward of the inverse pass (weights F->w and sums F->sums[0] = sum w):
-// accumulates all parameter gradients into F->d_grads (zeroed beforehand).
+// Backward of the density pass (weights F->w, sum w in F->sums[0]) over the
+// kept activations: accumulates every parameter gradient into F->d_grads
+// (zeroed beforehand).
 int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
-  const int H = F->H, D = F->D;
+  const int D = F->D;
+  float* g = F->d_grads;
   FLOW_CUDA(cudaMemsetAsync(F->dP, 0, sizeof(float) * n * D, st));
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& L = F->layers[l];
-    float* g = F->d_grads;
-    mc::spline_inv_bwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P_of(F, l + 1), F->dP, D, L, logits_of(F, l),
-                                                                       F->K, F->w, F->sums, F->glog32, F->glog16, n,
-                                                                       n_real);
-    // last dense layer: dW4^T = H3^T . dY (split-K over the batch), db4, dH3
-    const __nv_bfloat16 *h1 = h_of(F, l, 0), *h2 = h_of(F, l, 1), *h3 = h_of(F, l, 2);
     __nv_bfloat16* dA = F->dA;
-    __nv_bfloat16* dA_b = F->dA + size_t(F->bp) * H;
-    transpose(h3, n, H, F->tA, st);
-    transpose(F->glog16, n, L.nout_pad, F->tB, st);
-    if (int rc = gemm(F, H, L.nout_pad, int(n), mc::kEpiAtomicF32, F->tA, int(n), F->tB, int(n), nullptr,
-                      g + L.off_W4, L.nout_pad, nullptr, pick_splits(H, L.nout_pad, n), st))
-      return rc;
-    mc::colsum_kernel<float><<<dim3(mc::blocks_for(L.nout_pad, 128), unsigned((n + 1023) / 1024)), 128, 0, st>>>(
-        F->glog32, n, L.nout_pad, L.nout_pad, g + L.off_b4);
-    if (int rc = gemm(F, int(n), H, L.nout_pad, mc::kEpiReluMaskBf16, F->glog16, L.nout_pad, L.W4t, L.nout_pad,
-                      nullptr, dA, H, h3, 1, st))
+    __nv_bfloat16* dA_b = F->dA + size_t(F->bp) * kH;
+    mc::spline_inv_bwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P_of(F, l + 1), F->dP, D, L, LT_of(F, l), F->K,
+                                                                       F->w, F->sums, F->G, F->GT, n, n_real);
+    // last dense layer: W4, b4, and the gradient of h3 (through its ReLU)
+    if (int rc = gemm_wgrad(F, n, L.nout_pad, hT_of(F, l, 2), F->GT, g + L.off_W4, st)) return rc;
+    mc::rowsum_bf16_kernel<<<L.nout_pad, 256, 0, st>>>(F->GT, n, g + L.off_b4);
+    if (int rc = gemm_rs(F, n, kH, L.nout_pad, mc::kEpiReluMaskBf16, F->G, L.W4t, nullptr, dA, F->dAT,
+                         h_of(F, l, 2), st))
       return rc;
     // third dense layer
-    transpose(h2, n, H, F->tA, st);
-    transpose(dA, n, H, F->tB, st);
-    if (int rc = gemm(F, H, H, int(n), mc::kEpiAtomicF32, F->tA, int(n), F->tB, int(n), nullptr, g + L.off_W3, H,
-                      nullptr, pick_splits(H, H, n), st))
+    if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 1), F->dAT, g + L.off_W3, st)) return rc;
+    mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b3);
+    if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA, L.W3t, nullptr, dA_b, F->dAT, h_of(F, l, 1), st))
       return rc;
-    mc::colsum_kernel<__nv_bfloat16><<<dim3(mc::blocks_for(H, 128), unsigned((n + 1023) / 1024)), 128, 0, st>>>(
-        dA, n, H, H, g + L.off_b3);
-    if (int rc = gemm(F, int(n), H, H, mc::kEpiReluMaskBf16, dA, H, L.W3t, H, nullptr, dA_b, H, h2, 1, st)) return rc;
     // second dense layer
-    transpose(h1, n, H, F->tA, st);
-    transpose(dA_b, n, H, F->tB, st);
-    if (int rc = gemm(F, H, H, int(n), mc::kEpiAtomicF32, F->tA, int(n), F->tB, int(n), nullptr, g + L.off_W2, H,
-                      nullptr, pick_splits(H, H, n), st))
+    if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 0), F->dAT, g + L.off_W2, st)) return rc;
+    mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b2);
+    if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA_b, L.W2t, nullptr, nullptr, F->dAT, h_of(F, l, 0), st))
       return rc;
-    mc::colsum_kernel<__nv_bfloat16><<<dim3(mc::blocks_for(H, 128), unsigned((n + 1023) / 1024)), 128, 0, st>>>(
-        dA_b, n, H, H, g + L.off_b2);
-    if (int rc = gemm(F, int(n), H, H, mc::kEpiReluMaskBf16, dA_b, H, L.W2t, H, nullptr, dA, H, h1, 1, st)) return rc;
-    // first dense layer (CUDA cores): adds 2 W1^T dA1 to the A coordinates of dP; W1, b1 gradients
-    mc::dense1_bwd_input_kernel<<<mc::blocks_for(n, 128), 128, sizeof(float) * H * L.na, st>>>(
-        F->dP, D, L, F->d_params, dA, H, n);
-    constexpr int kRows = 256;
-    mc::dense1_bwd_weight_kernel<<<mc::blocks_for(n, kRows), H, sizeof(float) * kRows * L.na, st>>>(
-        P_of(F, l + 1), D, L, dA, H, n, kRows, g);
+    // first dense layer (CUDA cores): 2 W1^T dA1 into the conditioning coordinates of dP; W1, b1
+    mc::dense1_bwd_input_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(F->dP, D, L, F->d_params, F->dAT, n);
+    mc::dense1_bwd_weight_kernel<<<kH, 256, 0, st>>>(P_of(F, l + 1), D, L, F->dAT, n, g);
     FLOW_CUDA(cudaGetLastError());
   }
-  FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
 
 int refresh_bf16(mc_flow F, cudaStream_t st) {
-  const int H = F->H;
   for (const LayerDev& L : F->layers) {
-    mc::to_bf16_kernel<<<mc::blocks_for(H * H, 256), 256, 0, st>>>(F->d_params + L.off_W2, H, H, L.W2h, L.W2t);
-    mc::to_bf16_kernel<<<mc::blocks_for(H * H, 256), 256, 0, st>>>(F->d_params + L.off_W3, H, H, L.W3h, L.W3t);
-    mc::to_bf16_kernel<<<mc::blocks_for(L.nout_pad * H, 256), 256, 0, st>>>(F->d_params + L.off_W4, L.nout_pad, H,
+    mc::to_bf16_kernel<<<mc::blocks_for(kH * kH, 256), 256, 0, st>>>(F->d_params + L.off_W2, kH, kH, L.W2h, L.W2t);
+    mc::to_bf16_kernel<<<mc::blocks_for(kH * kH, 256), 256, 0, st>>>(F->d_params + L.off_W3, kH, kH, L.W3h, L.W3t);
+    mc::to_bf16_kernel<<<mc::blocks_for(L.nout_pad * kH, 256), 256, 0, st>>>(F->d_params + L.off_W4, L.nout_pad, kH,
                                                                              L.W4h, L.W4t);
   }
   FLOW_CUDA(cudaGetLastError());
@@ -581,11 +671,15 @@ int check_err(mc_flow F, cudaStream_t st) {
   return MC_OK;
 }
 
+size_t pdf_smem(const mc_integrand* itg, const mc::KernelArgs& a) {
+  const int nfl = itg->proc == MC_PP_TTBAR ? 11 : (a.pdf.nx ? 1 : 0);
+  return sizeof(float) * size_t(a.pdf.nx) * (1 + 2 * nfl);
+}
+
 int eval_points(mc_flow F, const mc_integrand* itg, mc_pdf pdf, const float* X, long long n, float* f, cudaStream_t st) {
   mc::KernelArgs a;
   if (int rc = mc::fill_process_args(itg, pdf, &a)) return rc;
-  const int nfl = itg->proc == MC_PP_TTBAR ? 11 : (a.pdf.nx ? 1 : 0);
-  const size_t smem = sizeof(float) * size_t(a.pdf.nx) * (1 + 2 * nfl);
+  const size_t smem = pdf_smem(itg, a);
   const unsigned grid = std::min<unsigned>(mc::blocks_for(n, 128), 148u * 16u);
   switch (itg->proc) {
     case MC_EE_MUMU: mc::points_kernel<mc::P_EE_MUMU><<<grid, 128, smem, st>>>(a, X, F->D, f, n); break;
@@ -596,6 +690,52 @@ int eval_points(mc_flow F, const mc_integrand* itg, mc_pdf pdf, const float* X, 
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
+}
+
+int eval_points_sums(mc_flow F, const mc_integrand* itg, const mc::KernelArgs& a, const float* X, const float* logq,
+                     long long n, cudaStream_t st) {
+  const size_t smem = pdf_smem(itg, a);
+  const int grid = kPartsGrid;
+  BlockPartial* parts = F->parts;
+  switch (itg->proc) {
+    case MC_EE_MUMU:
+      mc::points_sums_kernel<mc::P_EE_MUMU><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
+      break;
+    case MC_PP_TTBAR:
+      mc::points_sums_kernel<mc::P_PP_TTBAR><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
+      break;
+    case MC_GG_TTBARG:
+      mc::points_sums_kernel<mc::P_GG_TTBARG><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
+      break;
+    case MC_GG_TTBARG_7D:
+      mc::points_sums_kernel<mc::P_GG_TTBARG_7D><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
+      break;
+    default: mc::points_sums_kernel<mc::P_GAUSS><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
+  }
+  FLOW_CUDA(cudaGetLastError());
+  return MC_OK;
+}
+
+// Packed host parameter layout -> padded device layout: W4 row j (2K+1) + k
+// of the packed matrix is device row j ls + k (and likewise for b4).
+void build_host_map(mc_flow F) {
+  F->host_map.clear();
+  const int K2 = 2 * F->K + 1;
+  for (const LayerDev& L : F->layers) {
+    auto span = [&](size_t dev_off, size_t n) {
+      for (size_t i = 0; i < n; ++i) F->host_map.push_back(dev_off + i);
+    };
+    span(L.off_W1, size_t(kH) * L.na);
+    span(L.off_b1, kH);
+    span(L.off_W2, size_t(kH) * kH);
+    span(L.off_b2, kH);
+    span(L.off_W3, size_t(kH) * kH);
+    span(L.off_b3, kH);
+    for (int j = 0; j < L.nb; ++j)
+      for (int k = 0; k < K2; ++k) span(L.off_W4 + size_t(j * L.ls + k) * kH, kH);
+    for (int j = 0; j < L.nb; ++j)
+      for (int k = 0; k < K2; ++k) span(L.off_b4 + size_t(j * L.ls + k), 1);
+  }
 }
 
 }  // namespace
@@ -619,8 +759,9 @@ int mc_flow_free(mc_flow F) {
   if (!F) return MC_OK;
   for (void* p : {(void*)F->d_params, (void*)F->d_grads, (void*)F->d_m, (void*)F->d_v, (void*)F->d_wbf,
                   (void*)F->d_layers, (void*)F->P, (void*)F->logq, (void*)F->f, (void*)F->w, (void*)F->dP,
-                  (void*)F->logits, (void*)F->glog32, (void*)F->h, (void*)F->glog16, (void*)F->dA, (void*)F->tA,
-                  (void*)F->tB, (void*)F->sums, (void*)F->parts, (void*)F->total, (void*)F->err})
+                  (void*)F->LT, (void*)F->h, (void*)F->hT, (void*)F->G, (void*)F->GT, (void*)F->dA, (void*)F->dAT,
+                  (void*)F->part, (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
+                  (void*)F->err})
     cudaFree(p);
   if (F->h_sums) cudaFreeHost(F->h_sums);
   if (F->h_total) cudaFreeHost(F->h_total);
@@ -632,7 +773,8 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   if (!out || !cfg || !init) return ffail(MC_EINVAL, "mc_flow_create: NULL argument");
   *out = nullptr;
   if (cfg->ndim < 2 || cfg->ndim > mc::kMaxFlowDim || cfg->layers < 1 || cfg->layers > mc::kMaxLayers ||
-      cfg->bins < 2 || cfg->bins > mc::kFlowMaxBins || cfg->hidden != 256 || max_batch < 1 || max_batch > (int64_t(1) << 21))
+      cfg->bins < 2 || cfg->bins > mc::kFlowMaxBins || cfg->hidden != kH || max_batch < 1 ||
+      max_batch > (int64_t(1) << 21))
     return ffail(MC_EINVAL,
                  "mc_flow_create: need 2 <= ndim <= 16, 1..16 layers, 2..32 bins, hidden 256, 1 <= max_batch <= 2^21");
   auto* F = new mc_flow_s;
@@ -640,11 +782,10 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   F->D = cfg->ndim;
   F->L = cfg->layers;
   F->K = cfg->bins;
-  F->H = cfg->hidden;
   F->max_batch = max_batch;
   F->bp = pad128(max_batch);
   F->seed = seed;
-  const int H = F->H;
+  const int ls = (2 * F->K + 1 + 7) / 8 * 8;
   size_t off = 0, woff = 0;
   for (int l = 0; l < F->L; ++l) {
     LayerDev L;
@@ -655,22 +796,24 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
       else
         L.a_idx[L.na++] = d;
     }
-    L.nout = L.nb * (2 * F->K + 1);
-    L.nout_pad = (L.nout + 63) / 64 * 64;
+    L.ls = ls;
+    L.nout_pad = (L.nb * ls + 63) / 64 * 64;
     F->nout_pad_max = std::max(F->nout_pad_max, L.nout_pad);
-    L.off_W1 = off; off += size_t(H) * L.na;
-    L.off_b1 = off; off += H;
-    L.off_W2 = off; off += size_t(H) * H;
-    L.off_b2 = off; off += H;
-    L.off_W3 = off; off += size_t(H) * H;
-    L.off_b3 = off; off += H;
-    L.off_W4 = off; off += size_t(L.nout_pad) * H;
+    L.off_W1 = off; off += size_t(kH) * L.na;
+    off = (off + 3) / 4 * 4;  // 16-byte aligned biases and matrices
+    L.off_b1 = off; off += kH;
+    L.off_W2 = off; off += size_t(kH) * kH;
+    L.off_b2 = off; off += kH;
+    L.off_W3 = off; off += size_t(kH) * kH;
+    L.off_b3 = off; off += kH;
+    L.off_W4 = off; off += size_t(L.nout_pad) * kH;
     L.off_b4 = off; off += L.nout_pad;
     F->layers.push_back(L);
-    woff += 2 * (2 * size_t(H) * H + size_t(L.nout_pad) * H);
+    woff += 2 * (2 * size_t(kH) * kH + size_t(L.nout_pad) * kH);
   }
   F->nparam = off;
-  const size_t bp = size_t(F->bp), D = size_t(F->D), np = size_t(F->nout_pad_max);
+  const size_t bp = size_t(F->bp), D = size_t(F->D), np = size_t(F->nout_pad_max), L = size_t(F->L);
+  F->max_splits = 148;
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** p, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(p, bytes);
@@ -680,21 +823,22 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->d_m, sizeof(float) * off);
   alloc((void**)&F->d_v, sizeof(float) * off);
   alloc((void**)&F->d_wbf, sizeof(__nv_bfloat16) * woff);
-  alloc((void**)&F->d_layers, sizeof(LayerDev) * F->L);
-  alloc((void**)&F->P, sizeof(float) * (F->L + 1) * bp * D);
+  alloc((void**)&F->d_layers, sizeof(LayerDev) * L);
+  alloc((void**)&F->P, sizeof(float) * (L + 1) * bp * D);
   alloc((void**)&F->logq, sizeof(float) * bp);
   alloc((void**)&F->f, sizeof(float) * bp);
   alloc((void**)&F->w, sizeof(float) * bp);
   alloc((void**)&F->dP, sizeof(float) * bp * D);
-  alloc((void**)&F->logits, sizeof(float) * F->L * bp * np);
-  alloc((void**)&F->glog32, sizeof(float) * bp * np);
-  alloc((void**)&F->h, sizeof(__nv_bfloat16) * F->L * 3 * bp * H);
-  alloc((void**)&F->glog16, sizeof(__nv_bfloat16) * bp * np);
-  alloc((void**)&F->dA, sizeof(__nv_bfloat16) * 2 * bp * H);
-  alloc((void**)&F->tA, sizeof(__nv_bfloat16) * bp * std::max<size_t>(H, np));
-  alloc((void**)&F->tB, sizeof(__nv_bfloat16) * bp * std::max<size_t>(H, np));
+  alloc((void**)&F->LT, sizeof(float) * L * np * bp);
+  alloc((void**)&F->h, sizeof(__nv_bfloat16) * L * 3 * bp * kH);
+  alloc((void**)&F->hT, sizeof(__nv_bfloat16) * L * 3 * bp * kH);
+  alloc((void**)&F->G, sizeof(__nv_bfloat16) * bp * np);
+  alloc((void**)&F->GT, sizeof(__nv_bfloat16) * bp * np);
+  alloc((void**)&F->dA, sizeof(__nv_bfloat16) * 2 * bp * kH);
+  alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * bp * kH);
+  alloc((void**)&F->part, sizeof(float) * size_t(F->max_splits) * kH * np);
   alloc((void**)&F->sums, sizeof(double) * 2);
-  alloc((void**)&F->parts, sizeof(BlockPartial) * 148 * 32);
+  alloc((void**)&F->parts, sizeof(BlockPartial) * kPartsGrid);
   alloc((void**)&F->total, sizeof(BlockPartial));
   alloc((void**)&F->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_sums, sizeof(double) * 2);
@@ -704,32 +848,22 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
     return ffail(MC_ENOMEM, std::string("mc_flow_create: allocation failed: ") + cudaGetErrorString(e));
   }
   woff = 0;
-  for (LayerDev& L : F->layers) {
-    L.W2h = F->d_wbf + woff; woff += size_t(H) * H;
-    L.W2t = F->d_wbf + woff; woff += size_t(H) * H;
-    L.W3h = F->d_wbf + woff; woff += size_t(H) * H;
-    L.W3t = F->d_wbf + woff; woff += size_t(H) * H;
-    L.W4h = F->d_wbf + woff; woff += size_t(L.nout_pad) * H;
-    L.W4t = F->d_wbf + woff; woff += size_t(L.nout_pad) * H;
+  for (LayerDev& Ld : F->layers) {
+    Ld.W2h = F->d_wbf + woff; woff += size_t(kH) * kH;
+    Ld.W2t = F->d_wbf + woff; woff += size_t(kH) * kH;
+    Ld.W3h = F->d_wbf + woff; woff += size_t(kH) * kH;
+    Ld.W3t = F->d_wbf + woff; woff += size_t(kH) * kH;
+    Ld.W4h = F->d_wbf + woff; woff += size_t(Ld.nout_pad) * kH;
+    Ld.W4t = F->d_wbf + woff; woff += size_t(Ld.nout_pad) * kH;
   }
-  // packed host layout -> padded device layout
-  for (const LayerDev& L : F->layers) {
-    auto span = [&](size_t dev_off, size_t n) {
-      for (size_t i = 0; i < n; ++i) F->host_map.push_back(dev_off + i);
-    };
-    span(L.off_W1, size_t(H) * L.na);
-    span(L.off_b1, H);
-    span(L.off_W2, size_t(H) * H);
-    span(L.off_b2, H);
-    span(L.off_W3, size_t(H) * H);
-    span(L.off_b3, H);
-    span(L.off_W4, size_t(L.nout) * H);
-    span(L.off_b4, L.nout);
-  }
-  if (cudaMemcpy(F->d_layers, F->layers.data(), sizeof(LayerDev) * F->L, cudaMemcpyHostToDevice) != cudaSuccess ||
+  build_host_map(F);
+  // the padding rows of the logit gradients are never written: zero them once
+  if (cudaMemcpy(F->d_layers, F->layers.data(), sizeof(LayerDev) * L, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(F->d_m, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(F->d_v, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(F->d_grads, 0, sizeof(float) * off) != cudaSuccess ||
+      cudaMemset(F->GT, 0, sizeof(__nv_bfloat16) * bp * np) != cudaSuccess ||
+      cudaMemset(F->G, 0, sizeof(__nv_bfloat16) * bp * np) != cudaSuccess ||
       cudaMemset(F->err, 0, sizeof(int)) != cudaSuccess) {
     mc_flow_free(F);
     return ffail(MC_ECUDA, "mc_flow_create: initialisation failed");
@@ -762,13 +896,14 @@ int mc_flow_get_params(mc_flow F, float* host) {
 }
 
 int mc_flow_forward(mc_flow F, int64_t n, const float* z, float* x, float* logq, void* stream) {
-  if (!F || n < 0 || n > F->max_batch || (n && (!z || !x || !logq))) return ffail(MC_EINVAL, "mc_flow_forward: bad arguments");
+  if (!F || n < 0 || n > F->max_batch || (n && (!z || !x || !logq)))
+    return ffail(MC_EINVAL, "mc_flow_forward: bad arguments");
   if (n == 0) return MC_OK;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long np = pad128(n);
   FLOW_CUDA(cudaMemsetAsync(P_of(F, 0), 0, sizeof(float) * np * F->D, st));
   FLOW_CUDA(cudaMemcpyAsync(P_of(F, 0), z, sizeof(float) * n * F->D, cudaMemcpyDeviceToDevice, st));
-  if (int rc = forward_pass(F, np, st)) return rc;
+  if (int rc = forward_pass(F, np, false, st)) return rc;
   FLOW_CUDA(cudaMemcpyAsync(x, P_of(F, 0), sizeof(float) * n * F->D, cudaMemcpyDeviceToDevice, st));
   FLOW_CUDA(cudaMemcpyAsync(logq, F->logq, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
   return check_err(F, st);
@@ -794,21 +929,23 @@ int mc_flow_loss_grad(mc_flow F, int64_t n, const float* x, const float* w, doub
   if (grads) {
     std::vector<float> dev(F->nparam);
     FLOW_CUDA(cudaMemcpy(dev.data(), F->d_grads, sizeof(float) * F->nparam, cudaMemcpyDeviceToHost));
-    // gradients of W2..W4 are stored transposed
+    // gradients of W2..W4 are stored transposed; W4 rows sit at j ls + k
     size_t k = 0;
-    const int H = F->H;
+    const int K2 = 2 * F->K + 1;
     for (const LayerDev& L : F->layers) {
-      for (size_t i = 0; i < size_t(H) * L.na; ++i) grads[k++] = dev[L.off_W1 + i];
-      for (int i = 0; i < H; ++i) grads[k++] = dev[L.off_b1 + i];
-      for (int r = 0; r < H; ++r)
-        for (int c = 0; c < H; ++c) grads[k++] = dev[L.off_W2 + size_t(c) * H + r];
-      for (int i = 0; i < H; ++i) grads[k++] = dev[L.off_b2 + i];
-      for (int r = 0; r < H; ++r)
-        for (int c = 0; c < H; ++c) grads[k++] = dev[L.off_W3 + size_t(c) * H + r];
-      for (int i = 0; i < H; ++i) grads[k++] = dev[L.off_b3 + i];
-      for (int r = 0; r < L.nout; ++r)
-        for (int c = 0; c < H; ++c) grads[k++] = dev[L.off_W4 + size_t(c) * L.nout_pad + r];
-      for (int i = 0; i < L.nout; ++i) grads[k++] = dev[L.off_b4 + i];
+      for (size_t i = 0; i < size_t(kH) * L.na; ++i) grads[k++] = dev[L.off_W1 + i];
+      for (int i = 0; i < kH; ++i) grads[k++] = dev[L.off_b1 + i];
+      for (int r = 0; r < kH; ++r)
+        for (int c = 0; c < kH; ++c) grads[k++] = dev[L.off_W2 + size_t(c) * kH + r];
+      for (int i = 0; i < kH; ++i) grads[k++] = dev[L.off_b2 + i];
+      for (int r = 0; r < kH; ++r)
+        for (int c = 0; c < kH; ++c) grads[k++] = dev[L.off_W3 + size_t(c) * kH + r];
+      for (int i = 0; i < kH; ++i) grads[k++] = dev[L.off_b3 + i];
+      for (int j = 0; j < L.nb; ++j)
+        for (int q = 0; q < K2; ++q)
+          for (int c = 0; c < kH; ++c) grads[k++] = dev[L.off_W4 + size_t(c) * L.nout_pad + j * L.ls + q];
+      for (int j = 0; j < L.nb; ++j)
+        for (int q = 0; q < K2; ++q) grads[k++] = dev[L.off_b4 + j * L.ls + q];
     }
   }
   return MC_OK;
@@ -822,7 +959,7 @@ int mc_flow_adam_step(mc_flow F, double lr, void* stream) {
   mc::AdamArgs A{float(lr), float(b1), float(b2), 1e-8f, float(1.0 / (1.0 - std::pow(b1, F->step))),
                  float(1.0 / (1.0 - std::pow(b2, F->step)))};
   mc::adam_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_params, F->d_grads, F->d_m, F->d_v, F->nparam,
-                                                                   F->d_layers, F->L, F->H, A);
+                                                                   F->d_layers, F->L, A);
   FLOW_CUDA(cudaGetLastError());
   return refresh_bf16(F, st);
 }
@@ -835,22 +972,19 @@ int mc_flow_train(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int steps, int
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long n = batch, np = pad128(n);
   for (int s = 0; s < steps; ++s) {
-    // sample a batch from the current flow: z -> x (into P[L]), log q
-    float* Z = P_of(F, 0);
-    FLOW_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * np * F->D, st));
-    mc::flow_uniforms_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(Z, n, F->D, F->seed, 0x10000u + uint32_t(F->step),
-                                                                      0u, 0);
-    if (int rc = forward_pass(F, np, st)) return rc;
-    FLOW_CUDA(cudaMemcpyAsync(P_of(F, F->L), Z, sizeof(float) * np * F->D, cudaMemcpyDeviceToDevice, st));
+    // sample a batch from the current flow, keeping every layer's activations
+    FLOW_CUDA(cudaMemsetAsync(P_of(F, 0), 0, sizeof(float) * np * F->D, st));
+    mc::flow_uniforms_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(P_of(F, 0), n, F->D, F->seed,
+                                                                      0x10000u + uint32_t(F->step), 0);
+    if (int rc = forward_pass(F, np, true, st)) return rc;
     if (int rc = eval_points(F, itg, pdf, P_of(F, F->L), n, F->f, st)) return rc;
     FLOW_CUDA(cudaMemsetAsync(F->w, 0, sizeof(float) * np, st));
     mc::flow_weights_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->f, F->logq, F->w, n);
-    // density pass with activations, loss sums, backward, Adam
-    mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
-    if (int rc = inverse_pass(F, np, st)) return rc;
     FLOW_CUDA(cudaMemsetAsync(F->sums, 0, sizeof(double) * 2, st));
     mc::loss_sums_kernel<<<std::min<unsigned>(mc::blocks_for(n, 256), 1184u), 256, 0, st>>>(F->w, F->logq, n,
                                                                                             F->sums);
+    // the forward activations are those of the density pass at x: backward, Adam
+    mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
     if (int rc = backward_pass(F, np, n, st)) return rc;
     if (int rc = mc_flow_adam_step(F, lr, stream)) return rc;
     if (losses) {
@@ -868,32 +1002,43 @@ int mc_flow_iterate(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int64_t neve
   if (mc::process_dim(itg) != F->D) return ffail(MC_EINVAL, "mc_flow_iterate: flow dimension differs from the process");
   std::memset(out, 0, sizeof(*out));
   out->n = nevents;
+  if (nevents == 0) return MC_OK;
+  mc::KernelArgs a;
+  if (int rc = mc::fill_process_args(itg, pdf, &a)) return rc;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long chunk = (F->max_batch / 128) * 128;
   if (chunk < 128) return ffail(MC_EINVAL, "mc_flow_iterate: max_batch below 128");
-  BlockPartial tot = {0.0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0};
-  for (long long first = 0; first < nevents; first += chunk) {
-    const long long n = std::min<long long>(chunk, nevents - first), np = pad128(n);
-    float* Z = P_of(F, 0);
-    FLOW_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * np * F->D, st));
-    mc::flow_uniforms_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(Z, n, F->D, F->seed, 0x20000u + iteration, 0u,
-                                                                      first);
-    if (int rc = forward_pass(F, np, st)) return rc;
-    if (int rc = eval_points(F, itg, pdf, Z, n, F->f, st)) return rc;
-    const int grid = 148 * 8;
-    mc::flow_sums_kernel<<<grid, 256, 0, st>>>(F->f, F->logq, n, F->parts);
-    FLOW_CUDA(mc::launch_finalize(F->parts, grid, F->total, st));
-    FLOW_CUDA(cudaMemcpyAsync(F->h_total, F->total, sizeof(BlockPartial), cudaMemcpyDeviceToHost, st));
+  const long long nchunks = (nevents + chunk - 1) / chunk;
+  if (nchunks > F->max_chunks) {  // grow-only per-chunk totals
     FLOW_CUDA(cudaStreamSynchronize(st));
-    mc::partial_add(tot, *F->h_total);
+    cudaFree(F->chunk_totals);
+    F->chunk_totals = nullptr;
+    F->max_chunks = 0;
+    FLOW_CUDA(cudaMalloc((void**)&F->chunk_totals, sizeof(BlockPartial) * nchunks));
+    F->max_chunks = nchunks;
   }
+  float* Z = P_of(F, 0);
+  for (long long c = 0; c < nchunks; ++c) {
+    const long long first = c * chunk;
+    const long long n = std::min<long long>(chunk, nevents - first), np = pad128(n);
+    if (np != n) FLOW_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * np * F->D, st));
+    mc::flow_uniforms_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(Z, n, F->D, F->seed, 0x20000u + iteration,
+                                                                      first);
+    if (int rc = forward_pass(F, np, false, st)) return rc;
+    if (int rc = eval_points_sums(F, itg, a, Z, F->logq, n, st)) return rc;
+    FLOW_CUDA(mc::launch_finalize(F->parts, kPartsGrid, F->chunk_totals + c, st));
+  }
+  FLOW_CUDA(mc::launch_finalize(F->chunk_totals, int(nchunks), F->total, st));
+  FLOW_CUDA(cudaMemcpyAsync(F->h_total, F->total, sizeof(BlockPartial), cudaMemcpyDeviceToHost, st));
+  if (int rc = check_err(F, st)) return rc;
+  const BlockPartial& tot = *F->h_total;
   out->sum = tot.sum_hi + tot.sum_lo;
   out->sum2 = tot.sum2_hi + tot.sum2_lo;
   out->wmax = tot.wmax;
   out->n_nonzero = tot.n_nonzero;
-  out->n_bad = tot.n_bad;
-  out->status = tot.n_bad ? MC_ENAN : MC_OK;
-  return check_err(F, st);
+  out->n_bad = tot.n_bad + tot.n_noconv;
+  out->status = tot.n_bad ? MC_ENAN : (tot.n_noconv ? MC_ENOCONV : MC_OK);
+  return MC_OK;
 }
 
 }  // extern "C"

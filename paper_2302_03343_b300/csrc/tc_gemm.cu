@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -77,6 +78,9 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
           tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -93,6 +97,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// 16 columns of this warp's 32 TMEM lanes into v (no wait: call tmem_wait_ld
+// before using v).
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
@@ -230,6 +246,12 @@ __global__ void __launch_bounds__(128, 1)
           }
           break;
         }
+        case kEpiPartialF32: {  // this split's partial tile, summed later in a fixed order
+          float4* out = reinterpret_cast<float4*>(g.c_f32 + size_t(blockIdx.z) * g.M * g.ldc + size_t(row) * g.ldc + col0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) out[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          break;
+        }
         default: {  // kEpiAtomicF32: split-K accumulation
           float* out = g.c_f32 + size_t(row) * g.ldc + col0;
 #pragma unroll
@@ -238,9 +260,261 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   }
+  if (!failed && nkb == 0 && g.epilogue == kEpiPartialF32) {  // an empty split contributes zeros
+    const int row = tile_m * kBM + warp * 32 + lane;
+    float4* out = reinterpret_cast<float4*>(g.c_f32 + size_t(blockIdx.z) * g.M * g.ldc + size_t(row) * g.ldc +
+                                            tile_n * bn);
+    for (int j = 0; j < bn / 4; ++j) out[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
+
+// ---------------------------------------------------------------------------
+// Persistent B-resident GEMM (tc_gemm_rs).  Warp roles: warp 0 loads B once
+// and then streams the A tiles of this CTA's M tiles through the ring; warp 1
+// owns the TMEM allocation and issues the MMAs (tile i into accumulator
+// i % 2); warps 2-9 read accumulator i % 2 back and run the epilogue (warp w
+// may only access TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31, i.e. one quarter
+// of the tile's rows; the two warps of a quarter take alternate 16-column
+// chunks), then hand the accumulator back.
+constexpr int kRsThreads = 320;
+constexpr int kRsEpiThreads = 256;
+constexpr int kRsMaxStages = 6;
+constexpr uint32_t kAStage = kBM * kBK * 2;  // 16 KiB
+
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float* o) {
+  uint4 w[2];
+  uint32_t* u = reinterpret_cast<uint32_t*>(w);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+    u[j] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  reinterpret_cast<uint4*>(dst)[0] = w[0];
+  reinterpret_cast<uint4*>(dst)[1] = w[1];
+}
+
+__device__ __forceinline__ void rs_epilogue16(const TcGemmArgs& g, int row, int col0, const float* v) {
+  float o[16];
+  if (g.epilogue == kEpiReluMaskBf16) {
+    uint4 mw[2];
+    const uint4* mp = reinterpret_cast<const uint4*>(g.mask + size_t(row) * g.ld_mask + col0);
+    mw[0] = mp[0];
+    mw[1] = mp[1];
+    const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(mw);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = __bfloat162float(m[j]) > 0.0f ? v[j] : 0.0f;
+  } else {
+    if (g.bias) {
+      const float4* bp = reinterpret_cast<const float4*>(g.bias + col0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 b4 = __ldg(bp + j);
+        o[4 * j] = v[4 * j] + b4.x;
+        o[4 * j + 1] = v[4 * j + 1] + b4.y;
+        o[4 * j + 2] = v[4 * j + 2] + b4.z;
+        o[4 * j + 3] = v[4 * j + 3] + b4.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) o[j] = v[j];
+    }
+    if (g.epilogue == kEpiBiasReluBf16) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) o[j] = fmaxf(o[j], 0.0f);
+    }
+  }
+  if (g.epilogue == kEpiBiasF32) {
+    if (g.c_f32) {
+      float4* out = reinterpret_cast<float4*>(g.c_f32 + size_t(row) * g.ldc + col0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[j] = make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
+    }
+    if (g.c_t_f32) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g.c_t_f32[size_t(col0 + j) * g.ldt + row] = o[j];
+    }
+  } else {
+    if (g.c_bf16) store_bf16x16(g.c_bf16 + size_t(row) * g.ldc + col0, o);
+    if (g.c_t_bf16) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g.c_t_bf16[size_t(col0 + j) * g.ldt + row] = __float2bfloat16_rn(o[j]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRsThreads, 1)
+    tc_gemm_rs_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                      TcGemmArgs g, int stages) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t b_full;
+  __shared__ __align__(8) uint64_t a_full[kRsMaxStages];
+  __shared__ __align__(8) uint64_t a_empty[kRsMaxStages];
+  __shared__ __align__(8) uint64_t acc_full[2];
+  __shared__ __align__(8) uint64_t acc_empty[2];
+  __shared__ __align__(8) uint64_t fin_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int failed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bn = g.bn, nkb = g.K / kBK;
+  const uint32_t b_chunk = uint32_t(bn) * kBK * 2;  // one 64-wide K chunk of B (bn rows x 128 bytes)
+  unsigned char* smem_b = smem;
+  unsigned char* smem_a = smem + size_t(nkb) * b_chunk;
+  const int n_tile = blockIdx.y;
+  const int m_tiles = g.M / kBM;
+  const int my_tiles = int(blockIdx.x) < m_tiles ? (m_tiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  uint32_t acc_cols = 32;
+  while (acc_cols < uint32_t(bn)) acc_cols <<= 1;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&b_full, 1);
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&a_full[s], 1);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], kRsEpiThreads);
+    }
+    mbar_init(&fin_bar, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(2 * acc_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0 && my_tiles > 0) {
+      mbar_expect_tx(&b_full, uint32_t(nkb) * b_chunk);
+      for (int kb = 0; kb < nkb; ++kb) tma_load_2d(smem_b + size_t(kb) * b_chunk, &map_b, kb * kBK, n_tile * bn, &b_full);
+      int it = 0;
+      for (int i = 0; i < my_tiles && !failed; ++i) {
+        const int m = int(blockIdx.x) + i * int(gridDim.x);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int s = it % stages;
+          const uint32_t use = uint32_t(it / stages);
+          if (use > 0 && !mbar_wait(&a_empty[s], (use - 1) & 1u)) {
+            failed = 1;
+            atomicExch(g.error, 11);
+            break;
+          }
+          mbar_expect_tx(&a_full[s], kAStage);
+          tma_load_2d(smem_a + size_t(s) * kAStage, &map_a, kb * kBK, m * kBM, &a_full[s]);
+          ++it;
+        }
+      }
+      // every copy issued must land before the CTA may exit
+      mbar_wait(&b_full, 0);
+      for (int s = 0; s < stages && s < it; ++s) {
+        const int uses = (it - 1 - s) / stages + 1;  // loads issued into stage s
+        mbar_wait(&a_full[s], uint32_t(uses - 1) & 1u);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && my_tiles > 0) {
+      // idesc: D = F32, A = B = BF16, both K-major, N = bn, M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(bn >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
+      bool ok = mbar_wait(&b_full, 0);
+      if (!ok) {
+        failed = 1;
+        atomicExch(g.error, 12);
+      }
+      int it = 0;
+      for (int i = 0; i < my_tiles && ok && !failed; ++i) {
+        const int acc = i & 1;
+        const uint32_t use = uint32_t(i >> 1);
+        if (use > 0 && !mbar_wait(&acc_empty[acc], (use - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t d = tmem + uint32_t(acc) * acc_cols;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % stages;
+          if (!mbar_wait(&a_full[s], uint32_t(it / stages) & 1u)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint64_t ad = smem_desc(smem_u32(smem_a + size_t(s) * kAStage));
+          const uint64_t bd = smem_desc(smem_u32(smem_b + size_t(kb) * b_chunk));
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            mma_bf16(d, ad + uint64_t(k * 2), bd + uint64_t(k * 2), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          mma_commit(&a_empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&acc_full[acc]);
+      }
+      if (!ok) {
+        failed = 1;
+        atomicExch(g.error, 13);
+      }
+      // all MMAs issued by this thread complete before the accumulators are released
+      mma_commit(&fin_bar);
+      mbar_wait(&fin_bar, 0);
+    }
+  } else {
+    const int q = warp & 3;          // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;  // which alternate 16-column chunks
+    const int rl = q * 32 + lane;
+    const int nchunks = bn / 16;
+    for (int i = 0; i < my_tiles; ++i) {
+      const int acc = i & 1;
+      // warp-uniform decisions: the tcgen05.ld below needs the whole warp
+      if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[acc], uint32_t(i >> 1) & 1u))) {
+        failed = 1;
+        if (lane == 0) atomicExch(g.error, 14);
+        break;
+      }
+      if (__any_sync(0xffffffffu, failed != 0)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int row = (int(blockIdx.x) + i * int(gridDim.x)) * kBM + rl;
+      const uint32_t base = tmem + (uint32_t(q * 32) << 16) + uint32_t(acc) * acc_cols;
+      // four chunks in flight per wait
+      for (int c = half; c < nchunks; c += 8) {
+        uint32_t r[4][16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (c + 2 * u < nchunks) tmem_ld16_nw(base + uint32_t((c + 2 * u) * 16), r[u]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (c + 2 * u < nchunks) {
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[u][j]);
+            rs_epilogue16(g, row, n_tile * bn + (c + 2 * u) * 16, v);
+          }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mbar_arrive(&acc_empty[acc]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * acc_cols));
+}
+
+__global__ void reduce_splits_kernel(const float* part, int splits, size_t n, float* out) {
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    float acc = out[i];
+    for (int s = 0; s < splits; ++s) acc += part[size_t(s) * n + i];
+    out[i] = acc;
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -270,6 +544,19 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int k, int ld, int box
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+int num_sms_cached() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      n = v;
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 }  // namespace
 
 size_t tc_gemm_smem(int bn) { return size_t(kStages) * (kBM * kBK * 2 + size_t(bn) * kBK * 2) + 1024; }
@@ -288,6 +575,43 @@ cudaError_t tc_gemm(const TcGemmArgs& g_in, const __nv_bfloat16* a, int lda, con
   if (e != cudaSuccess) return e;
   const dim3 grid(g.M / kBM, g.N / g.bn, splits);
   tc_gemm_kernel<<<grid, 128, smem, st>>>(ma, mb, g);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_rs(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, const __nv_bfloat16* b, int ldb,
+                       cudaStream_t st) {
+  constexpr size_t kMaxSmem = 232448 - 1024;  // 227 KiB opt-in limit per block, less the static barriers
+  if (g.M % kBM || g.K % kBK || g.K > 5 * kBK || g.bn % 16 || g.bn < 16 || g.bn > 256 || g.N % g.bn || !g.error ||
+      g.epilogue < kEpiBiasReluBf16 || g.epilogue > kEpiReluMaskBf16 || !aligned16(a) || !aligned16(b) || (lda % 8) ||
+      (ldb % 8))
+    return cudaErrorInvalidValue;
+  if (g.epilogue == kEpiBiasF32 ? (!g.c_f32 && !g.c_t_f32) : (!g.c_bf16 && !g.c_t_bf16)) return cudaErrorInvalidValue;
+  if ((g.c_f32 && !aligned16(g.c_f32)) || (g.c_bf16 && !aligned16(g.c_bf16)) || (g.ldc % 8) ||
+      ((g.c_t_bf16 || g.c_t_f32) && g.ldt < g.M))
+    return cudaErrorInvalidValue;
+  if (g.epilogue == kEpiReluMaskBf16 && (!g.mask || !aligned16(g.mask) || (g.ld_mask % 8))) return cudaErrorInvalidValue;
+  if (g.bias && !aligned16(g.bias)) return cudaErrorInvalidValue;
+  const size_t b_bytes = size_t(g.bn) * g.K * 2;
+  const size_t room = kMaxSmem - 1024 - b_bytes;
+  const int stages = int(std::min<size_t>(kRsMaxStages, room / kAStage));
+  if (b_bytes + 1024 > kMaxSmem || stages < 2) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a, g.M, g.K, lda, kBM) || !make_map(&mb, b, g.N, g.K, ldb, g.bn)) return cudaErrorInvalidValue;
+  const size_t smem = b_bytes + size_t(stages) * kAStage + 1024;
+  (void)cudaGetLastError();
+  cudaError_t e = cudaFuncSetAttribute(tc_gemm_rs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int n_tiles = g.N / g.bn, m_tiles = g.M / kBM;
+  const int per_n = std::max(1, std::min(m_tiles, num_sms_cached() / n_tiles));
+  tc_gemm_rs_kernel<<<dim3(per_n, n_tiles), kRsThreads, smem, st>>>(ma, mb, g, stages);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_reduce_splits(const float* part, int splits, size_t n, float* out, cudaStream_t st) {
+  if (splits < 1 || !part || !out) return cudaErrorInvalidValue;
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = unsigned(std::min<size_t>((n + 255) / 256, size_t(num_sms_cached()) * 8));
+  reduce_splits_kernel<<<grid, 256, 0, st>>>(part, splits, n, out);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@ enum TcEpilogue : int {
   kEpiBiasF32 = 1,       // c_f32 = acc + bias (bias may be null)
   kEpiReluMaskBf16 = 2,  // c_bf16 = bf16(acc * [mask > 0]) (gradient through ReLU)
   kEpiAtomicF32 = 3,     // c_f32 += acc (split-K)
+  kEpiPartialF32 = 4,    // c_f32[split] = acc: per-split partial tiles, summed by tc_reduce_splits
 };
 
 struct TcGemmArgs {
@@ -23,6 +24,11 @@ struct TcGemmArgs {
   const __nv_bfloat16* mask;   // kEpiReluMaskBf16: activation of the layer, leading dimension ld_mask
   int ld_mask;
   int* error;                  // device flag: set non-zero when a bounded wait timed out
+  // optional transposed copies written by the persistent kernel (tc_gemm_rs):
+  // c_t_bf16[col * ldt + row] (epilogues 0 and 2), c_t_f32[col * ldt + row] (epilogue 1)
+  __nv_bfloat16* c_t_bf16;
+  float* c_t_f32;
+  int ldt;
 };
 
 size_t tc_gemm_smem(int bn);
@@ -31,5 +37,17 @@ size_t tc_gemm_smem(int bn);
 // gridDim.z (use kEpiAtomicF32).  Returns cudaErrorInvalidValue on bad shapes.
 cudaError_t tc_gemm(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, const __nv_bfloat16* b, int ldb,
                     int splits, cudaStream_t st);
+
+// Persistent variant for a long A and a short B (the dense layers applied to
+// a batch): B [N x K] stays resident in shared memory (bn * K * 2 bytes <=
+// 160 KiB, K <= 320), A tiles stream through a TMA ring, two TMEM
+// accumulators let the epilogue of one tile overlap the MMAs of the next.
+// Epilogues 0-2; row-major output optional when a transposed copy is asked
+// for (c_bf16 / c_f32 may be null).  Same alignment rules as tc_gemm.
+cudaError_t tc_gemm_rs(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, const __nv_bfloat16* b, int ldb,
+                       cudaStream_t st);
+
+// out[i] += sum over s < splits of part[s * n + i] (fixed order), n floats.
+cudaError_t tc_reduce_splits(const float* part, int splits, size_t n, float* out, cudaStream_t st);
 
 }  // namespace mc

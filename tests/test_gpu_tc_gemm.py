@@ -78,3 +78,65 @@ def test_gemm_rejects_bad_shapes(dev):
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     with pytest.raises(M.McError):
         M.mc_gemm_bf16(100, 256, 256, 256, M.EPI_BIAS_F32, a, b, c, err=err)
+
+
+def test_gemm_split_k_partials(dev):
+    M_, N, K, S = 256, 320, 2048, 4
+    a, b, _ = operands(M_, N, K, dev, seed=3)
+    c = torch.full((S, M_, N), float("nan"), device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    M.mc_gemm_bf16(M_, N, K, 160, M.EPI_PARTIAL_F32, a, b, c, splits=S, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    for s in range(S):  # split s covers K blocks [s K/S, (s+1) K/S)
+        k0, k1 = s * K // S, (s + 1) * K // S
+        assert rel_err(c[s], a[:, k0:k1].float() @ b[:, k0:k1].float().T) < 1e-5
+
+
+# the persistent B-resident kernel: every M tile count (fewer tiles than SMs,
+# several per CTA, an odd remainder), N split into two tiles, K up to 320
+@pytest.mark.parametrize("M_,N,K,bn", [(128, 256, 256, 256), (65536, 256, 256, 256), (40960 + 128, 320, 256, 160),
+                                       (1024, 256, 320, 256), (384, 64, 64, 64), (19072, 288, 256, 144)])
+def test_gemm_rs_bias_fp32_and_transposed(dev, M_, N, K, bn):
+    a, b, bias = operands(M_, N, K, dev, seed=4)
+    c = torch.full((M_, N), float("nan"), device=dev)
+    ct = torch.full((N, M_), float("nan"), device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    M.mc_gemm_bf16_rs(M_, N, K, bn, M.EPI_BIAS_F32, a, b, c=c, c_t=ct, bias=bias, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = a.float() @ b.float().T + bias
+    assert rel_err(c, ref) < 1e-5
+    assert torch.equal(ct, c.T)
+
+
+def test_gemm_rs_relu_and_mask_bf16(dev):
+    # absolute slack 1e-4: sums of 256 products of N(0, 1) values are ~16, so
+    # FP32 accumulation in another order moves them by ~1e-5, which decides
+    # the ReLU differently for pre-activations that close to zero
+    M_, N, K = 8192 + 256, 256, 256
+    a, b, bias = operands(M_, N, K, dev, seed=5)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    c = torch.empty((M_, N), dtype=torch.bfloat16, device=dev)
+    ct = torch.empty((N, M_), dtype=torch.bfloat16, device=dev)
+    M.mc_gemm_bf16_rs(M_, N, K, 256, M.EPI_BIAS_RELU_BF16, a, b, c=c, c_t=ct, bias=bias, err=err)
+    ref = torch.relu(a.float() @ b.float().T + bias)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert ((c.float() - ref).abs() <= 2 ** -7 * ref.abs() + 1e-4).all()
+    assert torch.equal(ct, c.T)
+    mask = torch.randn(M_, N, device=dev).to(torch.bfloat16)
+    g = torch.empty((M_, N), dtype=torch.bfloat16, device=dev)
+    M.mc_gemm_bf16_rs(M_, N, K, 256, M.EPI_RELU_MASK_BF16, a, b, c=g, mask=mask, err=err)
+    ref = (a.float() @ b.float().T) * (mask.float() > 0)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert ((g.float() - ref).abs() <= 2 ** -7 * ref.abs() + 1e-4).all()
+
+
+def test_gemm_rs_rejects_oversized_b(dev):
+    a, b, _ = operands(128, 256, 384, dev)
+    c = torch.empty((128, 256), device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    with pytest.raises(M.McError):
+        M.mc_gemm_bf16_rs(128, 256, 384, 256, M.EPI_BIAS_F32, a, b, c=c, err=err)
