@@ -25,8 +25,9 @@
 // [n][H] BF16 row-major (A operands) plus their transposes [H][n] (operands of
 // the weight-gradient products, written by the producing epilogue); logits
 // transposed [row][n] FP32 with coordinate j's 2K+1 logits at rows
-// j * ls .. j * ls + 2K (ls = 2K+1 rounded up to 8, so that each coordinate
-// starts on a 16-byte boundary in the row-major gradient).
+// j * ls .. j * ls + 2K (ls = 2K+1 rounded up to 16, so that each coordinate
+// starts on a 16-byte boundary in the row-major gradient and on a 16-column
+// group of the tensor-memory accumulator).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,6 +40,7 @@
 #include "flow_spline.cuh"
 #include "handles.h"
 #include "tc_gemm.h"
+#include "tcgen05.cuh"
 
 namespace mc {
 namespace {
@@ -57,9 +59,11 @@ struct LayerDev {
   // (gW^T [in x out]) as the weight-gradient products produce them.
   size_t off_W1, off_b1, off_W2, off_b2, off_W3, off_b3, off_W4, off_b4;
   // BF16 copies for the tensor cores: W2, W3, W4 (row-major [out x in]) and
-  // their transposes [in x out] for the activation gradients
-  __nv_bfloat16 *W2h, *W3h, *W4h, *W2t, *W3t, *W4t;
+  // their transposes [in x out] for the activation gradients; W1 transposed
+  // and zero-padded to [16 x H] for the input gradient of the first layer
+  __nv_bfloat16 *W2h, *W3h, *W4h, *W2t, *W3t, *W4t, *W1t;
 };
+constexpr int kUPad = 16;  // rows of U^T: u_0 .. u_{na-1}, a row of ones (bias), zeros
 
 unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
 
@@ -74,9 +78,12 @@ __global__ void flow_uniforms_kernel(float* z, long long n, int D, uint64_t seed
 }
 
 // h1 = bf16(relu(W1 (2 x_A - 1) + b1)) for one event per thread: row-major
-// h1 [n][H] (16-byte stores) and, if hT, its transpose [H][n] (coalesced).
+// h1 [n][H] (16-byte stores) and, if hT, its transpose [H][n] (coalesced) and
+// the layer input U^T [16][n] (u_a, then a row of ones) for the weight
+// gradient of W1 and b1.
 __global__ void __launch_bounds__(128) dense1_kernel(const float* P, int D, const LayerDev L, const float* params,
-                                                     __nv_bfloat16* h1, __nv_bfloat16* hT, long long n) {
+                                                     __nv_bfloat16* h1, __nv_bfloat16* hT, __nv_bfloat16* UT,
+                                                     long long n) {
   __shared__ float w1[kH * kMaxA], b1[kH];
   const int na = L.na;
   for (int t = threadIdx.x; t < kH * na; t += blockDim.x) w1[t] = params[L.off_W1 + t];
@@ -87,6 +94,10 @@ __global__ void __launch_bounds__(128) dense1_kernel(const float* P, int D, cons
   float u[kMaxA];
 #pragma unroll
   for (int a = 0; a < kMaxA; ++a) u[a] = a < na ? 2.0f * P[i * D + L.a_idx[a]] - 1.0f : 0.0f;
+  if (UT) {
+    for (int a = 0; a < na; ++a) UT[size_t(a) * n + i] = __float2bfloat16_rn(u[a]);
+    UT[size_t(na) * n + i] = __float2bfloat16_rn(1.0f);
+  }
   uint4* row = reinterpret_cast<uint4*>(h1 + size_t(i) * kH);
   for (int j8 = 0; j8 < kH / 8; ++j8) {
     uint4 pk;
@@ -124,15 +135,15 @@ __global__ void __launch_bounds__(128) spline_fwd_kernel(const float* Pin, float
   if (Pout != Pin)
     for (int a = 0; a < L.na; ++a) Pout[i * D + L.a_idx[a]] = Pin[i * D + L.a_idx[a]];
   Spline s;
-  float ld = 0.0f;
+  float ld[2] = {0.0f, 0.0f};  // even and odd coordinates summed apart, as in the fused layer
   for (int j = 0; j < L.nb; ++j) {
     spline_load(LT + size_t(j) * L.ls * ldn + i, ldn, K, s);
     float lc;
     const int d = L.b_idx[j];
     Pout[i * D + d] = spline_fwd(s, K, Pin[i * D + d], &lc);
-    ld += lc;
+    ld[j & 1] += lc;
   }
-  logq[i] -= ld;
+  logq[i] -= ld[0] + ld[1];
 }
 
 // Inverse spline of one layer: Pout = Pin with the transformed coordinates
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(128) spline_inv_bwd_kernel(const float* Pin, f
                                                              const float* LT, int K, const float* w,
                                                              const double* wsum, __nv_bfloat16* G,
                                                              __nv_bfloat16* GT, long long n, long long n_real) {
-  constexpr int kRow = 2 * kFlowMaxBins + 9;  // odd stride >= 2K+1: conflict-free rows
+  constexpr int kRow = 2 * kFlowMaxBins + 17;  // odd stride >= ls (2K+1 rounded up to 16): conflict-free rows
   __shared__ float gsh[128][kRow];
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;  // no block-wide barrier below
@@ -209,66 +220,28 @@ __global__ void __launch_bounds__(128) spline_inv_bwd_kernel(const float* Pin, f
   }
 }
 
-// First dense layer backward, input side: dL/dx_A += 2 W1^T dA1 (u = 2 x_A - 1),
-// one event per thread reading the transposed gradient dA1T [H][n].
-__global__ void __launch_bounds__(128) dense1_bwd_input_kernel(float* dP, int D, const LayerDev L,
-                                                               const float* params, const __nv_bfloat16* dA1T,
-                                                               long long n) {
-  __shared__ float w1[kH * kMaxA];
-  const int na = L.na;
-  for (int t = threadIdx.x; t < kH * na; t += blockDim.x) w1[t] = params[L.off_W1 + t];
-  __syncthreads();
+// First dense layer backward, input side: dL/dx_A += 2 dU with dU = dA1 W1
+// computed on the tensor cores as [n][16] (u = 2 x_A - 1).
+__global__ void add_input_grad_kernel(float* dP, int D, const LayerDev L, const float* dU, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float gu[kMaxA];
-#pragma unroll
-  for (int a = 0; a < kMaxA; ++a) gu[a] = 0.0f;
-  for (int j = 0; j < kH; ++j) {
-    const float g = __bfloat162float(dA1T[size_t(j) * n + i]);
-#pragma unroll
-    for (int a = 0; a < kMaxA; ++a)
-      if (a < na) gu[a] += g * w1[j * na + a];
-  }
-#pragma unroll
-  for (int a = 0; a < kMaxA; ++a)
-    if (a < na) dP[i * D + L.a_idx[a]] += 2.0f * gu[a];
+  for (int a = 0; a < L.na; ++a) dP[i * D + L.a_idx[a]] += 2.0f * dU[i * kUPad + a];
 }
 
-// First dense layer backward, weight side: one block per hidden unit j,
-// dL/dW1[j][a] += sum_i dA1[i][j] u_i[a] and dL/db1[j] += sum_i dA1[i][j]
-// (block reduction in a fixed order: deterministic).
-__global__ void __launch_bounds__(256) dense1_bwd_weight_kernel(const float* Pin, int D, const LayerDev L,
-                                                                const __nv_bfloat16* dA1T, long long n,
-                                                                float* grads) {
-  __shared__ float red[kMaxA + 1][8];
-  const int j = blockIdx.x, na = L.na;
-  float acc[kMaxA + 1];
-#pragma unroll
-  for (int a = 0; a <= kMaxA; ++a) acc[a] = 0.0f;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const float g = __bfloat162float(dA1T[size_t(j) * n + i]);
-    if (g == 0.0f) continue;
-    acc[kMaxA] += g;
-#pragma unroll
-    for (int a = 0; a < kMaxA; ++a)
-      if (a < na) acc[a] += g * (2.0f * Pin[i * D + L.a_idx[a]] - 1.0f);
-  }
-#pragma unroll
-  for (int a = 0; a <= kMaxA; ++a) {
-    float v = acc[a];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x <= kMaxA) {
-    const int a = threadIdx.x;
-    float v = 0.0f;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[a][w];
-    if (a == kMaxA)
-      grads[L.off_b1 + j] += v;
-    else if (a < na)
-      grads[L.off_W1 + size_t(j) * na + a] += v;
-  }
+// First dense layer backward, weight side: the split-K partial products
+// part[s][j][c] of dA1^T U (c < na: W1 column, c = na: the bias row of ones)
+// summed in a fixed order into the gradients of W1 [H x na] and b1.
+__global__ void w1_grad_kernel(const float* part, int splits, const LayerDev L, float* grads) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kH * kUPad) return;
+  const int j = idx / kUPad, c = idx % kUPad;
+  if (c > L.na) return;
+  float acc = 0.0f;
+  for (int s = 0; s < splits; ++s) acc += part[size_t(s) * kH * kUPad + idx];
+  if (c == L.na)
+    grads[L.off_b1 + j] += acc;
+  else
+    grads[L.off_W1 + size_t(j) * L.na + c] += acc;
 }
 
 // out[r] += sum_i XT[r][i] over a BF16 matrix XT [rows][n]: one block per
@@ -437,6 +410,14 @@ __global__ void adam_kernel(float* params, const float* grads, float* m, float* 
   params[idx] -= A.lr * (mi * A.c1) / (sqrtf(vi * A.c2) + A.eps);
 }
 
+// W1t [16][H] = W1^T zero-padded (W1 [H x na], FP32).
+__global__ void w1t_bf16_kernel(const float* W1, int na, __nv_bfloat16* W1t) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kUPad * kH) return;
+  const int a = idx / kH, j = idx % kH;
+  W1t[idx] = __float2bfloat16_rn(a < na ? W1[size_t(j) * na + a] : 0.0f);
+}
+
 __global__ void zero_kernel(float* p, size_t n) {
   const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) p[i] = 0.0f;
@@ -450,6 +431,285 @@ __global__ void to_bf16_kernel(const float* W, int rows, int cols, __nv_bfloat16
   const __nv_bfloat16 h = __float2bfloat16_rn(W[idx]);
   out[idx] = h;
   out_t[size_t(c) * rows + r] = h;
+}
+
+
+// ---------------------------------------------------------------------------
+// Fused coupling layer (sampling direction, K = 32 bins): one persistent
+// kernel per layer.  For each tile of 128 events the conditioner runs without
+// leaving the SM: dense1 on the CUDA cores writes h1 (BF16) into a shared-
+// memory operand buffer in the 128-byte-swizzled K-major layout the tensor
+// cores read; three tcgen05 products (W2, W3, W4 streamed from L2 through a
+// TMA ring) each land in TMEM, and the compute warps turn the accumulator
+// into the next operand (bias, ReLU, BF16) in the same buffer; the logits of
+// the last product are read straight from TMEM by the spline.  Warp 0 streams
+// the weights, warp 1 issues the MMAs, warps 2-9 compute (warp w owns TMEM
+// lanes 32 (w % 4).., i.e. a quarter of the tile's events, and half of the
+// columns or of the transformed coordinates).
+constexpr int kFusedK = 32;                       // bins
+constexpr int kFusedLs = 80;                      // logit stride: 2K+1 rounded up to 16 columns
+constexpr int kFusedThreads = 320;
+constexpr int kFusedCompute = 256;
+constexpr uint32_t kFusedABytes = 128 * kH * 2;   // one 128 x 256 BF16 operand (4 swizzled chunks)
+
+struct FusedLayerArgs {
+  float* P;        // [n][D], updated in place
+  float* logq;     // [n], log q -= sum log c
+  const float* params;
+  LayerDev L;
+  int D;
+  long long n;     // multiple of 128
+  int n_sub4;      // W4 products per K step (N split into n_sub4 MMAs of nout_pad / n_sub4)
+  int* error;
+};
+
+// Byte offset of row r, 16-byte unit u (0..31 along K) in the swizzled operand.
+__device__ __forceinline__ uint32_t swz_off(int r, int u) {
+  return uint32_t(u >> 3) * 16384u + uint32_t(r >> 3) * 1024u + uint32_t(r & 7) * 128u +
+         uint32_t(((u & 7) ^ (r & 7)) << 4);
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    flow_layer_fused_kernel(const __grid_constant__ CUtensorMap map_w2, const __grid_constant__ CUtensorMap map_w3,
+                            const __grid_constant__ CUtensorMap map_w4, FusedLayerArgs g, int stages) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int kMaxStages = 4;
+  __shared__ __align__(8) uint64_t w_full[kMaxStages];
+  __shared__ __align__(8) uint64_t w_empty[kMaxStages];
+  __shared__ __align__(8) uint64_t a_ready, acc_full, fin_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int failed;
+  __shared__ float s_w1[kH * kMaxA], s_b1[kH], s_b2[kH], s_b3[kH], s_b4[512];
+  __shared__ float s_ld[2][128];
+
+  const LayerDev& L = g.L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nout = L.nout_pad;
+  const uint32_t stage_bytes = uint32_t(max(kH, nout)) * 128u;
+  unsigned char* abuf = smem;
+  unsigned char* ring = smem + kFusedABytes;
+  const int m_tiles = int(g.n / 128);
+  const int my_tiles = int(blockIdx.x) < m_tiles ? (m_tiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+
+  for (int t = threadIdx.x; t < kH * L.na; t += blockDim.x) s_w1[t] = g.params[L.off_W1 + t];
+  for (int t = threadIdx.x; t < kH; t += blockDim.x) {
+    s_b1[t] = g.params[L.off_b1 + t];
+    s_b2[t] = g.params[L.off_b2 + t];
+    s_b3[t] = g.params[L.off_b3 + t];
+  }
+  for (int t = threadIdx.x; t < nout; t += blockDim.x) s_b4[t] = g.params[L.off_b4 + t];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&w_full[s], 1);
+      mbar_init(&w_empty[s], 1);
+    }
+    mbar_init(&a_ready, kFusedCompute);
+    mbar_init(&acc_full, 1);
+    mbar_init(&fin_bar, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    // weight stream: per tile W2, W3, W4, four 64-wide K chunks each
+    if (lane == 0 && my_tiles > 0) {
+      const int sub4 = nout / g.n_sub4;
+      int it = 0;
+      for (int i = 0; i < my_tiles && !failed; ++i) {
+        for (int q = 0; q < 12 && !failed; ++q, ++it) {
+          const int s = it % stages;
+          const uint32_t use = uint32_t(it / stages);
+          if (use > 0 && !mbar_wait(&w_empty[s], (use - 1) & 1u)) {
+            failed = 1;
+            atomicExch(g.error, 21);
+            break;
+          }
+          const int m = q >> 2, c = q & 3;
+          unsigned char* dst = ring + size_t(s) * stage_bytes;
+          if (m < 2) {
+            mbar_expect_tx(&w_full[s], uint32_t(kH) * 128u);
+            tma_load_2d(dst, m == 0 ? &map_w2 : &map_w3, c * 64, 0, &w_full[s]);
+          } else {
+            mbar_expect_tx(&w_full[s], uint32_t(nout) * 128u);
+            for (int sb = 0; sb < g.n_sub4; ++sb)
+              tma_load_2d(dst + size_t(sb) * sub4 * 128, &map_w4, c * 64, sb * sub4, &w_full[s]);
+          }
+        }
+      }
+      // every copy issued lands before the CTA may exit
+      for (int s = 0; s < stages && s < it; ++s) mbar_wait(&w_full[s], uint32_t((it - 1 - s) / stages) & 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && my_tiles > 0) {
+      const uint32_t idesc_h = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kH >> 3) << 17) | (8u << 24);
+      const int sub4 = nout / g.n_sub4;
+      const uint32_t idesc_o = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(sub4 >> 3) << 17) | (8u << 24);
+      int it = 0, use_a = 0;
+      bool ok = true;
+      for (int i = 0; i < my_tiles && ok; ++i) {
+        for (int m = 0; m < 3 && ok; ++m, ++use_a) {
+          if (!mbar_wait(&a_ready, uint32_t(use_a) & 1u) || failed) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          for (int c = 0; c < 4; ++c, ++it) {
+            const int s = it % stages;
+            if (!mbar_wait(&w_full[s], uint32_t(it / stages) & 1u)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint64_t ad = smem_desc(smem_u32(abuf + c * 16384));
+            const uint32_t bbase = smem_u32(ring + size_t(s) * stage_bytes);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
+              if (m < 2) {
+                mma_bf16(tmem, ad + uint64_t(k * 2), smem_desc(bbase) + uint64_t(k * 2), idesc_h, acc);
+              } else {
+                for (int sb = 0; sb < g.n_sub4; ++sb)
+                  mma_bf16(tmem + uint32_t(sb * sub4), ad + uint64_t(k * 2),
+                           smem_desc(bbase + uint32_t(sb * sub4 * 128)) + uint64_t(k * 2), idesc_o, acc);
+              }
+            }
+            mma_commit(&w_empty[s]);
+          }
+          if (!ok) break;
+          mma_commit(&acc_full);
+        }
+      }
+      if (!ok) {
+        failed = 1;
+        atomicExch(g.error, 22);
+      }
+      mma_commit(&fin_bar);  // every MMA issued here completes before the TMEM is released
+      mbar_wait(&fin_bar, 0);
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const int r = q * 32 + lane;  // event row in the tile (= TMEM lane)
+    const uint32_t trow = tmem + (uint32_t(q * 32) << 16);
+    int use_acc = 0;
+    // Every compute thread passes the two named barriers of every tile, also
+    // after a failure (the work is then skipped), so none can wait forever.
+    for (int i = 0; i < my_tiles; ++i) {
+      const long long ev = (long long)(int(blockIdx.x) + i * int(gridDim.x)) * 128 + r;
+      float* Pe = g.P + ev * g.D;
+      bool ok = !__any_sync(0xffffffffu, failed != 0);
+      if (ok) {
+        // dense1: h1 for units [128 half, 128 half + 128) of this event
+        float u[kMaxA];
+#pragma unroll
+        for (int a = 0; a < kMaxA; ++a) u[a] = a < L.na ? 2.0f * Pe[L.a_idx[a]] - 1.0f : 0.0f;
+        for (int u16 = half * 16; u16 < half * 16 + 16; ++u16) {
+          uint4 pk;
+          uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float o[2];
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int j = u16 * 8 + 2 * e + h2;
+              float acc = s_b1[j];
+#pragma unroll
+              for (int a = 0; a < kMaxA; ++a)
+                if (a < L.na) acc += s_w1[j * L.na + a] * u[a];
+              o[h2] = fmaxf(acc, 0.0f);
+            }
+            const __nv_bfloat162 hh = __floats2bfloat162_rn(o[0], o[1]);
+            pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+          }
+          *reinterpret_cast<uint4*>(abuf + swz_off(r, u16)) = pk;
+        }
+        fence_async_smem();
+        mbar_arrive(&a_ready);
+        // two hidden products: accumulator -> bias, ReLU, BF16 -> operand buffer
+        for (int m = 0; m < 2 && ok; ++m, ++use_acc) {
+          if (!__all_sync(0xffffffffu, mbar_wait(&acc_full, uint32_t(use_acc) & 1u))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const float* bias = m == 0 ? s_b2 : s_b3;
+          for (int cg = 0; cg < 2; ++cg) {  // 2 groups of 4 x 16 columns
+            uint32_t v[4][16];
+            const int col0 = half * 128 + cg * 64;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) tmem_ld16_nw(trow + uint32_t(col0 + 16 * x), v[x]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+#pragma unroll
+              for (int hlf = 0; hlf < 2; ++hlf) {
+                uint4 pk;
+                uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const int cc = col0 + 16 * x + 8 * hlf + 2 * e;
+                  const float o0 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e]) + bias[cc], 0.0f);
+                  const float o1 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e + 1]) + bias[cc + 1], 0.0f);
+                  const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
+                  pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                }
+                *reinterpret_cast<uint4*>(abuf + swz_off(r, (col0 + 16 * x + 8 * hlf) >> 3)) = pk;
+              }
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          fence_async_smem();
+          mbar_arrive(&a_ready);
+        }
+        if (ok && !__all_sync(0xffffffffu, mbar_wait(&acc_full, uint32_t(use_acc) & 1u))) ok = false;
+        ++use_acc;
+      }
+      float ld = 0.0f;
+      if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // splines of this half's transformed coordinates from the logits in TMEM
+        for (int j = half; j < L.nb; j += 2) {
+          float lg[kFusedLs];
+#pragma unroll
+          for (int x = 0; x < kFusedLs / 16; ++x)
+            tmem_ld16_nw(trow + uint32_t(j * kFusedLs + 16 * x), reinterpret_cast<uint32_t*>(lg + 16 * x));
+          tmem_wait_ld();
+#pragma unroll
+          for (int k = 0; k < kFusedLs; ++k) lg[k] += s_b4[j * kFusedLs + k];
+          Spline sp;
+          spline_load_regs<kFusedK>(lg, sp);
+          float lc;
+          const int d = L.b_idx[j];
+          Pe[d] = spline_fwd(sp, kFusedK, Pe[d], &lc);
+          ld += lc;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+      } else {
+        failed = 1;
+        if (lane == 0) atomicExch(g.error, 23);
+      }
+      s_ld[half][r] = ld;
+      compute_bar();
+      if (half == 0 && ok) g.logq[ev] -= s_ld[0][r] + s_ld[1][r];
+      compute_bar();
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 }  // namespace
@@ -473,6 +733,8 @@ struct mc_flow_s {
   // workspace
   float *P = nullptr, *logq = nullptr, *f = nullptr, *w = nullptr, *dP = nullptr, *LT = nullptr;
   __nv_bfloat16 *h = nullptr, *hT = nullptr, *G = nullptr, *GT = nullptr, *dA = nullptr, *dAT = nullptr;
+  __nv_bfloat16* UT = nullptr;  // per layer: first-layer inputs, transposed [16][n]
+  float* dU = nullptr;          // [n][16] input gradient of the first layer
   float* part = nullptr;  // split-K partial products of the weight gradients
   int max_splits = 0;
   double* sums = nullptr;
@@ -481,6 +743,11 @@ struct mc_flow_s {
   long long max_chunks = 0;
   int* err = nullptr;
   int nout_pad_max = 0;
+  // fused sampling layers (K = 32, nout_pad <= 512): tensor maps of W2, W3, W4 per layer
+  bool use_fused = true;
+  std::vector<bool> fused_ok;
+  std::vector<int> n_sub4;
+  std::vector<CUtensorMap> maps;
 };
 
 namespace {
@@ -504,6 +771,7 @@ float* P_of(mc_flow F, int l) { return F->P + size_t(l) * F->bp * F->D; }
 __nv_bfloat16* h_of(mc_flow F, int l, int k) { return F->h + (size_t(l) * 3 + k) * F->bp * kH; }
 __nv_bfloat16* hT_of(mc_flow F, int l, int k) { return F->hT + (size_t(l) * 3 + k) * F->bp * kH; }
 float* LT_of(mc_flow F, int l) { return F->LT + size_t(l) * F->bp * F->nout_pad_max; }
+__nv_bfloat16* UT_of(mc_flow F, int l) { return F->UT + size_t(l) * F->bp * mc::kUPad; }
 
 // N tile: the largest multiple of 16 up to 256 that divides N.
 int pick_bn(int N) {
@@ -544,7 +812,7 @@ int gemm_rs(mc_flow F, long long n, int N, int K, int epi, const __nv_bfloat16* 
 // activations / gradients, K = n): split-K partial tiles, then a fixed-order
 // sum into the gradient.
 int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* XT, const __nv_bfloat16* YT, float* gWt,
-               cudaStream_t st) {
+               cudaStream_t st, int* splits_out = nullptr) {
   FLOW_CUDA(cudaGetLastError());
   const int bn = pick_bn(N);
   const int tiles = (kH / 128) * (N / bn);
@@ -563,7 +831,10 @@ int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* XT, const __n
   g.ldc = N;
   g.error = F->err;
   FLOW_CUDA(mc::tc_gemm(g, XT, int(n), YT, int(n), splits, st));
-  FLOW_CUDA(mc::tc_reduce_splits(F->part, splits, size_t(kH) * N, gWt, st));
+  if (splits_out)
+    *splits_out = splits;  // the caller sums the partials itself
+  else
+    FLOW_CUDA(mc::tc_reduce_splits(F->part, splits, size_t(kH) * N, gWt, st));
   return MC_OK;
 }
 
@@ -574,7 +845,7 @@ int conditioner(mc_flow F, int l, int slot, const float* P, long long n, bool ke
   const float* prm = F->d_params;
   __nv_bfloat16 *h1 = h_of(F, slot, 0), *h2 = h_of(F, slot, 1), *h3 = h_of(F, slot, 2);
   mc::dense1_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P, F->D, L, prm, h1, keep ? hT_of(F, slot, 0) : nullptr,
-                                                             n);
+                                                             keep ? UT_of(F, slot) : nullptr, n);
   if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiBiasReluBf16, h1, L.W2h, prm + L.off_b2, h2,
                        keep ? hT_of(F, slot, 1) : nullptr, nullptr, st))
     return rc;
@@ -585,12 +856,50 @@ int conditioner(mc_flow F, int l, int slot, const float* P, long long n, bool ke
                  st);
 }
 
+// One fused sampling layer (flow_layer_fused_kernel) over n rows of P[0].
+int fused_layer(mc_flow F, int l, long long n, cudaStream_t st) {
+  FLOW_CUDA(cudaGetLastError());  // launches queued before this one
+  static int num_sms = 0;
+  if (num_sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms < 1)
+      num_sms = 1;
+  }
+  const LayerDev& L = F->layers[l];
+  mc::FusedLayerArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.P = P_of(F, 0);
+  a.logq = F->logq;
+  a.params = F->d_params;
+  a.L = L;
+  a.D = F->D;
+  a.n = n;
+  a.n_sub4 = F->n_sub4[l];
+  a.error = F->err;
+  constexpr size_t kMaxDyn = 232448 - 16384;  // opt-in limit less the kernel's static shared memory
+  const size_t stage = size_t(std::max(kH, L.nout_pad)) * 128;
+  const int stages = int(std::min<size_t>(4, (kMaxDyn - 1024 - mc::kFusedABytes) / stage));
+  if (stages < 2) return ffail(MC_EINVAL, "mc_flow: fused layer does not fit in shared memory");
+  const size_t smem = 1024 + mc::kFusedABytes + stages * stage;
+  FLOW_CUDA(cudaFuncSetAttribute(mc::flow_layer_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const int grid = int(std::min<long long>(n / 128, num_sms));
+  mc::flow_layer_fused_kernel<<<grid, mc::kFusedThreads, smem, st>>>(F->maps[3 * l], F->maps[3 * l + 1],
+                                                                     F->maps[3 * l + 2], a, stages);
+  FLOW_CUDA(cudaGetLastError());
+  return MC_OK;
+}
+
 // Forward (sampling direction) from P[0] = z over n (multiple of 128) rows;
 // logq initialised to 0.  keep: layer l writes P[l+1] and keeps its
 // activations (training); otherwise P[0] is mapped in place (sampling).
 int forward_pass(mc_flow F, long long n, bool keep, cudaStream_t st) {
   FLOW_CUDA(cudaMemsetAsync(F->logq, 0, sizeof(float) * n, st));
   for (int l = 0; l < F->L; ++l) {
+    if (!keep && F->use_fused && F->fused_ok[l]) {
+      if (int rc = fused_layer(F, l, n, st)) return rc;
+      continue;
+    }
     const int slot = keep ? l : 0;
     const float* Pin = keep ? P_of(F, l) : P_of(F, 0);
     float* Pout = keep ? P_of(F, l + 1) : P_of(F, 0);
@@ -642,11 +951,17 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
     // second dense layer
     if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 0), F->dAT, g + L.off_W2, st)) return rc;
     mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b2);
-    if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA_b, L.W2t, nullptr, nullptr, F->dAT, h_of(F, l, 0), st))
+    if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA_b, L.W2t, nullptr, dA, F->dAT, h_of(F, l, 0), st))
       return rc;
-    // first dense layer (CUDA cores): 2 W1^T dA1 into the conditioning coordinates of dP; W1, b1
-    mc::dense1_bwd_input_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(F->dP, D, L, F->d_params, F->dAT, n);
-    mc::dense1_bwd_weight_kernel<<<kH, 256, 0, st>>>(P_of(F, l + 1), D, L, F->dAT, n, g);
+    // first dense layer: dU = dA1 W1 (tensor cores, W1 zero-padded to 16
+    // columns) into the conditioning coordinates of dP; W1 and b1 from the
+    // split-K product dA1^T [u | 1]
+    if (int rc = gemm_rs(F, n, mc::kUPad, kH, mc::kEpiBiasF32, dA, L.W1t, nullptr, F->dU, nullptr, nullptr, st))
+      return rc;
+    mc::add_input_grad_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->dP, D, L, F->dU, n);
+    int splits = 0;
+    if (int rc = gemm_wgrad(F, n, mc::kUPad, F->dAT, UT_of(F, l), nullptr, st, &splits)) return rc;
+    mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
     FLOW_CUDA(cudaGetLastError());
   }
   return MC_OK;
@@ -658,6 +973,7 @@ int refresh_bf16(mc_flow F, cudaStream_t st) {
     mc::to_bf16_kernel<<<mc::blocks_for(kH * kH, 256), 256, 0, st>>>(F->d_params + L.off_W3, kH, kH, L.W3h, L.W3t);
     mc::to_bf16_kernel<<<mc::blocks_for(L.nout_pad * kH, 256), 256, 0, st>>>(F->d_params + L.off_W4, L.nout_pad, kH,
                                                                              L.W4h, L.W4t);
+    mc::w1t_bf16_kernel<<<mc::blocks_for(mc::kUPad * kH, 256), 256, 0, st>>>(F->d_params + L.off_W1, L.na, L.W1t);
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
@@ -760,7 +1076,7 @@ int mc_flow_free(mc_flow F) {
   for (void* p : {(void*)F->d_params, (void*)F->d_grads, (void*)F->d_m, (void*)F->d_v, (void*)F->d_wbf,
                   (void*)F->d_layers, (void*)F->P, (void*)F->logq, (void*)F->f, (void*)F->w, (void*)F->dP,
                   (void*)F->LT, (void*)F->h, (void*)F->hT, (void*)F->G, (void*)F->GT, (void*)F->dA, (void*)F->dAT,
-                  (void*)F->part, (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
+                  (void*)F->part, (void*)F->UT, (void*)F->dU, (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
                   (void*)F->err})
     cudaFree(p);
   if (F->h_sums) cudaFreeHost(F->h_sums);
@@ -785,7 +1101,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   F->max_batch = max_batch;
   F->bp = pad128(max_batch);
   F->seed = seed;
-  const int ls = (2 * F->K + 1 + 7) / 8 * 8;
+  const int ls = (2 * F->K + 1 + 15) / 16 * 16;
   size_t off = 0, woff = 0;
   for (int l = 0; l < F->L; ++l) {
     LayerDev L;
@@ -809,7 +1125,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
     L.off_W4 = off; off += size_t(L.nout_pad) * kH;
     L.off_b4 = off; off += L.nout_pad;
     F->layers.push_back(L);
-    woff += 2 * (2 * size_t(kH) * kH + size_t(L.nout_pad) * kH);
+    woff += 2 * (2 * size_t(kH) * kH + size_t(L.nout_pad) * kH) + size_t(mc::kUPad) * kH;
   }
   F->nparam = off;
   const size_t bp = size_t(F->bp), D = size_t(F->D), np = size_t(F->nout_pad_max), L = size_t(F->L);
@@ -837,6 +1153,8 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->dA, sizeof(__nv_bfloat16) * 2 * bp * kH);
   alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * bp * kH);
   alloc((void**)&F->part, sizeof(float) * size_t(F->max_splits) * kH * np);
+  alloc((void**)&F->UT, sizeof(__nv_bfloat16) * L * mc::kUPad * bp);
+  alloc((void**)&F->dU, sizeof(float) * bp * mc::kUPad);
   alloc((void**)&F->sums, sizeof(double) * 2);
   alloc((void**)&F->parts, sizeof(BlockPartial) * kPartsGrid);
   alloc((void**)&F->total, sizeof(BlockPartial));
@@ -855,15 +1173,31 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
     Ld.W3t = F->d_wbf + woff; woff += size_t(kH) * kH;
     Ld.W4h = F->d_wbf + woff; woff += size_t(Ld.nout_pad) * kH;
     Ld.W4t = F->d_wbf + woff; woff += size_t(Ld.nout_pad) * kH;
+    Ld.W1t = F->d_wbf + woff; woff += size_t(mc::kUPad) * kH;
   }
   build_host_map(F);
-  // the padding rows of the logit gradients are never written: zero them once
+  // tensor maps of the fused sampling layers
+  F->maps.resize(3 * L);
+  for (int l = 0; l < F->L; ++l) {
+    const LayerDev& Ld = F->layers[l];
+    const int n_sub4 = (Ld.nout_pad + 255) / 256;
+    const int sub4 = Ld.nout_pad / n_sub4;
+    bool ok = F->K == mc::kFusedK && ls == mc::kFusedLs && Ld.nout_pad <= 512 && Ld.nout_pad % n_sub4 == 0 &&
+              sub4 % 16 == 0;
+    ok = ok && mc::tc_make_map(&F->maps[3 * l], Ld.W2h, kH, kH, kH, kH) &&
+         mc::tc_make_map(&F->maps[3 * l + 1], Ld.W3h, kH, kH, kH, kH) &&
+         mc::tc_make_map(&F->maps[3 * l + 2], Ld.W4h, Ld.nout_pad, kH, kH, sub4);
+    F->fused_ok.push_back(ok);
+    F->n_sub4.push_back(n_sub4);
+  }
+  // the padding rows of the logit gradients and of U^T are never written: zero them once
   if (cudaMemcpy(F->d_layers, F->layers.data(), sizeof(LayerDev) * L, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(F->d_m, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(F->d_v, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(F->d_grads, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(F->GT, 0, sizeof(__nv_bfloat16) * bp * np) != cudaSuccess ||
       cudaMemset(F->G, 0, sizeof(__nv_bfloat16) * bp * np) != cudaSuccess ||
+      cudaMemset(F->UT, 0, sizeof(__nv_bfloat16) * L * mc::kUPad * bp) != cudaSuccess ||
       cudaMemset(F->err, 0, sizeof(int)) != cudaSuccess) {
     mc_flow_free(F);
     return ffail(MC_ECUDA, "mc_flow_create: initialisation failed");
@@ -892,6 +1226,12 @@ int mc_flow_get_params(mc_flow F, float* host) {
   FLOW_CUDA(cudaDeviceSynchronize());
   FLOW_CUDA(cudaMemcpy(dev.data(), F->d_params, sizeof(float) * F->nparam, cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < F->host_map.size(); ++i) host[i] = dev[F->host_map[i]];
+  return MC_OK;
+}
+
+int mc_flow_set_fused(mc_flow F, int enable) {
+  if (!F) return ffail(MC_EINVAL, "mc_flow_set_fused: NULL handle");
+  F->use_fused = enable != 0;
   return MC_OK;
 }
 

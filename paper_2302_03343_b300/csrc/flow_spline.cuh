@@ -51,6 +51,34 @@ MC_D void spline_load(const float* lg, size_t ld, int K, Spline& s) {
   for (int k = 0; k <= kFlowMaxBins; ++k) s.V[k] *= ia;
 }
 
+// The same from logits held in registers (lg[0 .. 2K]), K fixed at compile
+// time so that every index is static.
+template <int K, int NL>
+MC_D void spline_load_regs(const float (&lg)[NL], Spline& s) {
+  static_assert(K <= kFlowMaxBins && 2 * K + 1 <= NL, "logit count");
+  float mx = lg[0];
+#pragma unroll
+  for (int k = 1; k < K; ++k) mx = fmaxf(mx, lg[k]);
+  float sw = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kFlowMaxBins; ++k) {
+    s.W[k] = k < K ? expf(lg[k < K ? k : 0] - mx) : 0.0f;
+    sw += s.W[k];
+  }
+  const float isw = 1.0f / sw;
+#pragma unroll
+  for (int k = 0; k < kFlowMaxBins; ++k) s.W[k] *= isw;
+#pragma unroll
+  for (int k = 0; k <= kFlowMaxBins; ++k) s.V[k] = k <= K ? expf(lg[k <= K ? K + k : 0]) : 0.0f;
+  float area = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kFlowMaxBins; ++k)
+    if (k < K) area += 0.5f * (s.V[k] + s.V[k + 1]) * s.W[k];
+  const float ia = 1.0f / area;
+#pragma unroll
+  for (int k = 0; k <= kFlowMaxBins; ++k) s.V[k] *= ia;
+}
+
 // The bin of a point: Xb, Cb (left edge and CDF there), Wb, Vb, Vb1.  With
 // by_cdf the point is a CDF value y (inverse), otherwise a coordinate x.
 struct SplineBin {

@@ -4,14 +4,14 @@
 // FP32 accumulation in tensor memory, with fused epilogues.
 //
 // One CTA (4 warps) computes one 128 x BN tile (BN <= 256, a multiple of 16)
-// over its K range (split-K over gridDim.z).  One elected thread streams the
+// over its K range (split-K over gridDim.z).  One thread of warp 0 streams the
 // K blocks (64 BF16 = 128 B per row, 128-byte swizzle) into a ring of shared-
-// memory stages with TMA (cp.async.bulk.tensor, completion on an mbarrier)
-// and issues tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a
-// TMEM accumulator; tcgen05.commit on a per-stage mbarrier returns the stage
-// to the loader.  After the last MMA all four warps read the accumulator with
-// tcgen05.ld (warp w owns rows 32w..32w+31, one row per thread) and apply the
-// epilogue.  Every mbarrier wait is bounded: on timeout the kernel records an
+// memory stages with TMA (cp.async.bulk.tensor, completion on an mbarrier);
+// one thread of warp 1 issues tcgen05.mma (M = 128, N = BN, K = 16 per
+// instruction) into a TMEM accumulator, and tcgen05.commit on a per-stage
+// mbarrier returns the stage to the loader.  After the last MMA all four
+// warps read the accumulator with tcgen05.ld (warp w owns rows 32w..32w+31,
+// one row per thread) and apply the epilogue.  Every mbarrier wait is bounded: on timeout the kernel records an
 // error code, waits (bounded) for its TMA copies, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "tc_gemm.h"
+#include "tcgen05.cuh"
 
 namespace mc {
 namespace {
@@ -30,85 +31,6 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kBK = 64;          // K elements per stage (one 128-byte swizzle atom)
 constexpr int kStages = 4;
-constexpr uint32_t kSpinLimit = 1u << 20;  // about a second of try_wait polling
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false when the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte
-// swizzle, 8-row groups 1024 bytes apart (stride byte offset), descriptor
-// version 1, leading byte offset unused for this layout.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return uint64_t((addr & 0x3FFFF) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46) |
-         (uint64_t(2) << 61);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 16 columns of this warp's 32 TMEM lanes into v (no wait: call tmem_wait_ld
-// before using v).
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
@@ -123,7 +45,7 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ __align__(8) uint64_t empty_bar[kStages];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ int failed;
+  __shared__ volatile int failed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile_m = blockIdx.x, tile_n = blockIdx.y;
@@ -153,57 +75,49 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
 
-  if (threadIdx.x == 0 && nkb > 0) {
-    // idesc: D = F32, A = B = BF16, both K-major, N = bn, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(bn >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
+  if (warp == 0 && lane == 0 && nkb > 0) {
+    // producer: the K blocks of this split through the ring of stages
     int issued = 0;
-    auto load = [&](int i) {  // K block i of this split into stage i % kStages
+    for (int i = 0; i < nkb && !failed; ++i) {
       const int s = i % kStages;
+      if (i >= kStages && !mbar_wait(&empty_bar[s], uint32_t(i / kStages - 1) & 1u)) {
+        failed = 1;
+        atomicExch(g.error, 1);
+        break;
+      }
       unsigned char* st = smem + size_t(s) * stage_bytes;
       mbar_expect_tx(&full_bar[s], stage_bytes);
       tma_load_2d(st, &map_a, (kb0 + i) * kBK, tile_m * kBM, &full_bar[s]);
       tma_load_2d(st + a_bytes, &map_b, (kb0 + i) * kBK, tile_n * bn, &full_bar[s]);
-    };
-    for (; issued < min(nkb, kStages); ++issued) load(issued);
-    bool ok = true;
-    for (int i = 0; i < nkb && ok; ++i) {
+      ++issued;
+    }
+    // every copy issued lands before the CTA may exit
+    for (int s = 0; s < kStages && s < issued; ++s)
+      mbar_wait(&full_bar[s], uint32_t((issued - 1 - s) / kStages) & 1u);
+  } else if (warp == 1 && lane == 0 && nkb > 0) {
+    // MMA issuer: D = F32, A = B = BF16, both K-major, N = bn, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(bn >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
+    for (int i = 0; i < nkb; ++i) {
       const int s = i % kStages;
-      const uint32_t ph = uint32_t(i / kStages) & 1u;
-      if (!mbar_wait(&full_bar[s], ph)) {
-        ok = false;
+      if (!mbar_wait(&full_bar[s], uint32_t(i / kStages) & 1u)) {
+        failed = 1;
+        atomicExch(g.error, 2);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t a_addr = smem_u32(smem + size_t(s) * stage_bytes);
-      const uint32_t b_addr = a_addr + a_bytes;
-      const uint64_t ad = smem_desc(a_addr), bd = smem_desc(b_addr);
+      const uint64_t ad = smem_desc(a_addr), bd = smem_desc(a_addr + a_bytes);
 #pragma unroll
       for (int k = 0; k < kBK / 16; ++k)  // advance 16 BF16 = 32 bytes along K inside the swizzle atom
         mma_bf16(tmem, ad + uint64_t(k * 2), bd + uint64_t(k * 2), idesc, (i > 0 || k > 0) ? 1u : 0u);
       mma_commit(&empty_bar[s]);
-      if (issued < nkb) {  // refill this stage once the MMAs reading it are done
-        if (!mbar_wait(&empty_bar[s], ph)) {
-          ok = false;
-          break;
-        }
-        load(issued);
-        ++issued;
-      }
     }
-    if (ok) {
-      mma_commit(&done_bar);
-    } else {
-      failed = 1;
-      atomicExch(g.error, 1);
-      // let the copies already issued land before the CTA exits
-      for (int i = 0; i < min(issued, nkb); ++i) mbar_wait(&full_bar[i % kStages], uint32_t(i / kStages) & 1u);
-      mbar_expect_tx(&done_bar, 0);  // release the other threads
-    }
+    mma_commit(&done_bar);  // completes once every MMA issued above has
   }
   if (nkb > 0) {
     // every thread waits for the accumulator (or the failure release)
     if (!mbar_wait(&done_bar, 0)) {
-      if (lane == 0) atomicExch(g.error, 2);
+      if (lane == 0) atomicExch(g.error, 3);
       failed = 1;
     }
   }
@@ -531,8 +445,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+}  // namespace
+
 // 2D BF16 tensor map of a row-major [rows x K] matrix, box [box_rows x 64].
-bool make_map(CUtensorMap* m, const void* base, int rows, int k, int ld, int box_rows) {
+bool tc_make_map(CUtensorMap* m, const void* base, int rows, int k, int ld, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {cuuint64_t(k), cuuint64_t(rows)};
@@ -542,6 +458,11 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int k, int ld, int box
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+bool make_map(CUtensorMap* m, const void* base, int rows, int k, int ld, int box_rows) {
+  return tc_make_map(m, base, rows, k, ld, box_rows);
 }
 
 int num_sms_cached() {

@@ -1,5 +1,6 @@
 // Internal: tcgen05 BF16 GEMM C[M x N] (+)= A[M x K] . B[N x K]^T (tc_gemm.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -32,6 +33,9 @@ struct TcGemmArgs {
 };
 
 size_t tc_gemm_smem(int bn);
+// 2D BF16 tensor map (128-byte swizzle) of a row-major [rows x k] matrix
+// with leading dimension ld elements, box [box_rows x 64]; false on failure.
+bool tc_make_map(CUtensorMap* m, const void* base, int rows, int k, int ld, int box_rows);
 // a: [M x K] row-major (leading dimension lda), b: [N x K] row-major (ldb);
 // 16-byte aligned, lda and ldb multiples of 8.  splits > 1 divides K across
 // gridDim.z (use kEpiAtomicF32).  Returns cudaErrorInvalidValue on bad shapes.

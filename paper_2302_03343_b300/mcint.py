@@ -31,7 +31,7 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_batch_create", "mc_batch_iterate", "mc_batch_get_grid", "mc_batch_shape", "mc_batch_kernel_ms",
            "mc_batch_free", "mc_gemm_bf16", "mc_gemm_bf16_rs", "mc_flow_param_count", "mc_flow_create", "mc_flow_free",
            "mc_flow_set_params", "mc_flow_get_params", "mc_flow_forward", "mc_flow_loss_grad", "mc_flow_adam_step",
-           "mc_flow_train", "mc_flow_iterate")
+           "mc_flow_train", "mc_flow_iterate", "mc_flow_set_fused")
 
 
 class McError(RuntimeError):
@@ -123,6 +123,7 @@ def lib():
             "mc_flow_forward": [_vp, i64, _vp, _vp, _vp, _vp],
             "mc_flow_loss_grad": [_vp, i64, _vp, _vp, _dp, _fp, _vp],
             "mc_flow_adam_step": [_vp, d, _vp],
+            "mc_flow_set_fused": [_vp, i32],
             "mc_flow_train": [_vp, ctypes.POINTER(Integrand), _vp, i32, i64, d, _vp, _dp],
             "mc_flow_iterate": [_vp, ctypes.POINTER(Integrand), _vp, i64, u32, _vp, ctypes.POINTER(IterResult)],
         }
@@ -466,6 +467,10 @@ def mc_flow_get_params(f):
     flat = np.zeros(f.nparam, dtype=np.float32)
     _check(lib().mc_flow_get_params(f.handle, flat.ctypes.data_as(_fp)))
     return unpack_flow_params(flat, f.cfg.ndim, f.cfg.layers, f.cfg.bins, f.cfg.hidden)
+
+
+def mc_flow_set_fused(f, enable):
+    _check(lib().mc_flow_set_fused(f.handle, 1 if enable else 0))
 
 
 def mc_flow_forward(f, z_dev, x_dev, logq_dev, stream=None):
