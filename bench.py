@@ -7,6 +7,12 @@ LHAPDF-shaped PDF grid, FP32 helicity-amplitude |M|^2 with Kahan FP64
 accumulation, 1e7 events per iteration, 50 VEGAS bins per dimension, each step
 followed by the grid refinement.  Inputs are synthetic and seeded.
 
+The line also carries "time_to_target": the GPU time to a 1e-3 relative
+error on gg -> t tbar g in 7 sampled dimensions for plain FP64 VEGAS, FP32
+VEGAS and FP32 + normalizing-flow sampling (200 online training steps
+included), each run from scratch, with the variance per event and the
+unweighting efficiency of each.
+
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a
 bounded sample of events per step on the host cores).
 """
@@ -36,8 +42,16 @@ METRIC = "events/sec and GPU time to 1e-3 rel. error: FP32+flow vs plain FP64 VE
 # kernel (|M|^2 with 32 helicity configurations, RAMBO, PDFs, map), counted by
 # ncu as fadd + fmul + 2 ffma over one launch divided by the number of
 # evaluated (in-cut) events; see profiles/.
-FLOP_PER_EVENT = float(os.environ.get("MC_FLOP_PER_EVENT", "0")) or None
+FLOP_PER_EVENT = 24978.0
 FP32_LANES_PER_SM = 128
+# time to a target relative error (gg -> t tbar g, 7 sampled dimensions):
+# FP32 + normalizing flow (6 coupling layers, 32 bins, 3 x 256 BF16 hidden
+# units, Adam lr 1e-3, 200 training steps of 65536 events, then 1e7 events per
+# iteration) against plain FP64 VEGAS (1e7 events per iteration, 50 bins)
+TTT_TARGET = 1e-3
+TTT_EVENTS = 10_000_000
+TTT_MAX_ITER = 15
+FLOW_LAYERS, FLOW_BINS, FLOW_STEPS, FLOW_BATCH, FLOW_LR = 6, 32, 200, 65536, 1e-3
 
 
 def peaks():
@@ -153,6 +167,91 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+def _combine(res):
+    """Inverse-variance combination of per-iteration (mean, variance of the mean)."""
+    w = [1.0 / v for _, v in res if v > 0]
+    if not w:
+        return 0.0, float("inf")
+    mean = sum(m / v for m, v in res if v > 0) / sum(w)
+    return mean, (1.0 / sum(w)) ** 0.5
+
+
+def _iter_stats(r):
+    mean = r.sum / r.n
+    var = max(r.sum2 / r.n - mean * mean, 0.0) / (r.n - 1)
+    return mean, var
+
+
+def time_to_target(M, pdf, stream, seed=0):
+    """GPU time (CUDA events around every launch of the arm) from the first
+    launch to the end of the first iteration whose combined relative error is
+    at most TTT_TARGET, for plain FP64 VEGAS, FP32 VEGAS and FP32 + flow on
+    gg -> t tbar g (7 dims), each from scratch (uniform grid / identity flow)."""
+    import torch
+    itg = W.gg_ttbarg_7d()
+    out = {"target_rel_err": TTT_TARGET, "events_per_iteration": TTT_EVENTS, "workload":
+           "gg->ttg 13 TeV, hierarchical 2->3 phase space (7 dims), same cuts and PDF grid"}
+
+    def vegas(prec, name):
+        v = M.mc_vegas_init(7, NBINS, seed, prec)
+        res, per_event, eff = [], None, None
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for it in range(TTT_MAX_ITER):
+            r = M.mc_vegas_iterate(v, itg, pdf, TTT_EVENTS, stream)
+            M.mc_vegas_refine(v, ALPHA, stream)
+            res.append(_iter_stats(r))
+            mean, sig = _combine(res)
+            if sig <= TTT_TARGET * abs(mean):
+                break
+        t1.record(stream)
+        torch.cuda.synchronize()
+        m_it, v_it = res[-1]
+        per_event = v_it * r.n / (m_it * m_it)
+        eff = m_it / r.wmax if r.wmax > 0 else None
+        v.free()
+        return {"ms": t0.elapsed_time(t1), "iterations": len(res), "mean_pb": mean, "rel_err": sig / abs(mean),
+                "rel_var_per_event_last": per_event, "unweighting_eff_last": eff}
+
+    out["vegas_fp64"] = vegas(M.MC_FP64, "fp64")
+    out["vegas_fp32"] = vegas(M.MC_FP32_KAHAN, "fp32")
+    # flow arm: training included in the timed region
+    init = W.flow_init_params(7, L=FLOW_LAYERS, K=FLOW_BINS, seed=seed)
+    f = M.mc_flow_create(7, FLOW_LAYERS, FLOW_BINS, init, FLOW_BATCH, seed=seed + 1)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    tt = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    M.mc_flow_train(f, itg, pdf, FLOW_STEPS, FLOW_BATCH, FLOW_LR, stream=stream, losses=False)
+    tt.record(stream)
+    res = []
+    for it in range(TTT_MAX_ITER):
+        r = M.mc_flow_iterate(f, itg, pdf, TTT_EVENTS, iteration=it, stream=stream)
+        res.append(_iter_stats(r))
+        mean, sig = _combine(res)
+        if sig <= TTT_TARGET * abs(mean):
+            break
+    t1.record(stream)
+    torch.cuda.synchronize()
+    m_it, v_it = res[-1]
+    flow = {"ms": t0.elapsed_time(t1), "train_ms": t0.elapsed_time(tt), "sample_ms": tt.elapsed_time(t1),
+            "train_steps": FLOW_STEPS, "train_batch": FLOW_BATCH, "iterations": len(res), "mean_pb": mean,
+            "rel_err": sig / abs(mean), "rel_var_per_event_last": v_it * r.n / (m_it * m_it),
+            "unweighting_eff_last": m_it / r.wmax if r.wmax > 0 else None,
+            "sample_events_per_s": TTT_EVENTS * len(res) / (tt.elapsed_time(t1) / 1e3)}
+    f.free()
+    out["flow_fp32"] = flow
+    out["ratio_vegas_fp64_over_flow"] = out["vegas_fp64"]["ms"] / flow["ms"]
+    comb = (out["vegas_fp64"]["mean_pb"] - flow["mean_pb"]) / (
+        (out["vegas_fp64"]["rel_err"] * out["vegas_fp64"]["mean_pb"]) ** 2 +
+        (flow["rel_err"] * flow["mean_pb"]) ** 2) ** 0.5
+    out["flow_vs_vegas_fp64_pulls"] = comb
+    return out
+
+
 def run_native(args, rank, world):
     import torch
     from paper_2302_03343_b300 import build
@@ -261,6 +360,8 @@ def run_native(args, rank, world):
             "last_iteration": {"mean_pb": mean, "rel_err": (var ** 0.5) / abs(mean) if mean else None,
                                "n_nonzero": r_last.n_nonzero, "unweighting_eff": mean / r_last.wmax
                                if r_last.wmax > 0 else None}}
+    if not args.no_time_to_target:
+        line["time_to_target"] = time_to_target(M, pdf, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -274,6 +375,7 @@ def main():
     ap.add_argument("--events", type=int, default=EVENTS)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-target", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -354,13 +354,17 @@ int mc_flow_free(mc_flow f);
  * (Adam moments and the step counter are kept).  Both synchronise. */
 int mc_flow_set_params(mc_flow f, const float* host);
 int mc_flow_get_params(mc_flow f, float* host);
-/* Choose between the two implementations of the sampling direction (used
- * by mc_flow_forward and mc_flow_iterate): enable != 0 (the default) runs
- * each coupling layer as one fused kernel (dense layers on the tensor cores
- * with activations kept in shared and tensor memory, spline in the epilogue)
- * wherever it applies (bins == 32 and at most 6 transformed coordinates per
- * layer); 0 runs the layer-by-layer kernels.  Both give the same numbers. */
-int mc_flow_set_fused(mc_flow f, int enable);
+/* Choose between the fused and the layer-by-layer kernels of the flow.
+ * mask bit 0: the forward direction (mc_flow_forward, mc_flow_iterate and
+ * the sampling half of mc_flow_train) runs each coupling layer as one fused
+ * kernel (dense layers on the tensor cores with the activations kept in
+ * shared and tensor memory, spline in the epilogue); bit 1: the backward
+ * (mc_flow_loss_grad, mc_flow_train) runs the spline and activation
+ * gradients of each layer as one fused kernel.  Both apply where bins == 32
+ * and a layer transforms at most 6 coordinates; elsewhere, or with the bit
+ * clear, the layer-by-layer kernels run.  Default 3.  Both implementations
+ * compute the same numbers. */
+int mc_flow_set_fused(mc_flow f, int mask);
 /* Sampling direction: z [n x ndim] (device, uniform in the unit cube) ->
  * x [n x ndim] (device) and log q(x) [n] (device); n <= max_batch.
  * Synchronises (to read the tensor-core error flag). */

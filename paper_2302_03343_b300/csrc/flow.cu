@@ -218,6 +218,13 @@ __global__ void __launch_bounds__(128) spline_inv_bwd_kernel(const float* Pin, f
       gr[c8] = pk;
     }
   }
+  // the rows past the last coordinate: the buffers are shared by layers with
+  // more transformed coordinates, so clear what such a layer left there
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+  for (int c = L.nb * L.ls; c < L.nout_pad; ++c) {
+    GT[size_t(c) * ldn + i] = z;
+    G[size_t(i) * L.nout_pad + c] = z;
+  }
 }
 
 // First dense layer backward, input side: dL/dx_A += 2 dU with dU = dA1 W1
@@ -242,6 +249,20 @@ __global__ void w1_grad_kernel(const float* part, int splits, const LayerDev L, 
     grads[L.off_b1 + j] += acc;
   else
     grads[L.off_W1 + size_t(j) * L.na + c] += acc;
+}
+
+// ReLU activity bits of the three hidden activations of a layer from their
+// transposes hT [3][H][n] (layer slot): bits [3][n][8], bit c % 32 of word
+// c / 32 set where h[c] > 0 (the fused backward's masks).
+__global__ void mask_bits_kernel(const __nv_bfloat16* hT, size_t slot_stride, long long n, uint32_t* bits) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * 8 * n) return;
+  const long long ev = t % n;
+  const int w = int((t / n) % 8), act = int(t / (8 * n));
+  const __nv_bfloat16* h = hT + size_t(act) * slot_stride;
+  uint32_t word = 0u;
+  for (int b = 0; b < 32; ++b) word |= uint32_t(__bfloat162float(h[size_t(w * 32 + b) * n + ev]) > 0.0f) << b;
+  bits[(size_t(act) * n + ev) * 8 + w] = word;
 }
 
 // out[r] += sum_i XT[r][i] over a BF16 matrix XT [rows][n]: one block per
@@ -352,11 +373,13 @@ __global__ void flow_weights_kernel(const float* f, const float* logq, float* w,
   w[i] = isfinite(wi) ? wi : 0.0f;
 }
 
-// Loss sums in FP64: sums[0] += sum w, sums[1] += sum w log q.
-__global__ void loss_sums_kernel(const float* w, const float* logq, long long n, double* sums) {
+// Loss sums in FP64: sums[0] = sum w, sums[1] = sum w log q; one block, fixed
+// reduction order (deterministic).
+__global__ void __launch_bounds__(1024) loss_sums_kernel(const float* w, const float* logq, long long n,
+                                                         double* sums) {
   __shared__ double sh[2][32];
   double a = 0.0, b = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
     a += w[i];
     b += double(w[i]) * logq[i];
   }
@@ -375,8 +398,8 @@ __global__ void loss_sums_kernel(const float* w, const float* logq, long long n,
       sa += sh[0][k];
       sb += sh[1][k];
     }
-    atomicAdd(&sums[0], sa);
-    atomicAdd(&sums[1], sb);
+    sums[0] = sa;
+    sums[1] = sb;
   }
 }
 
@@ -453,7 +476,8 @@ constexpr int kFusedCompute = 256;
 constexpr uint32_t kFusedABytes = 128 * kH * 2;   // one 128 x 256 BF16 operand (4 swizzled chunks)
 
 struct FusedLayerArgs {
-  float* P;        // [n][D], updated in place
+  const float* P;  // [n][D] layer input
+  float* Pout;     // [n][D] layer output (may equal P)
   float* logq;     // [n], log q -= sum log c
   const float* params;
   LayerDev L;
@@ -461,6 +485,12 @@ struct FusedLayerArgs {
   long long n;     // multiple of 128
   int n_sub4;      // W4 products per K step (N split into n_sub4 MMAs of nout_pad / n_sub4)
   int* error;
+  // training: the activations the backward needs, transposed [feature][n]
+  // (all null when sampling): h1, h2, h3 (BF16), the first-layer inputs
+  // U^T (BF16, rows u_a then a row of ones) and the logits (FP32, with bias)
+  __nv_bfloat16 *hT1, *hT2, *hT3, *UT;
+  float* LT;
+  uint32_t* bits;  // ReLU activity of h1, h2, h3: [3][n][8] words (bit c % 32 of word c / 32)
 };
 
 // Byte offset of row r, 16-byte unit u (0..31 along K) in the swizzled operand.
@@ -472,6 +502,8 @@ __device__ __forceinline__ uint32_t swz_off(int r, int u) {
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// KEEP: training (writes the activations for the backward); otherwise sampling.
+template <bool KEEP>
 __global__ void __launch_bounds__(kFusedThreads, 1)
     flow_layer_fused_kernel(const __grid_constant__ CUtensorMap map_w2, const __grid_constant__ CUtensorMap map_w3,
                             const __grid_constant__ CUtensorMap map_w4, FusedLayerArgs g, int stages) {
@@ -608,13 +640,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     // after a failure (the work is then skipped), so none can wait forever.
     for (int i = 0; i < my_tiles; ++i) {
       const long long ev = (long long)(int(blockIdx.x) + i * int(gridDim.x)) * 128 + r;
-      float* Pe = g.P + ev * g.D;
+      const float* Pe = g.P + ev * g.D;
+      float* Po = g.Pout + ev * g.D;
       bool ok = !__any_sync(0xffffffffu, failed != 0);
       if (ok) {
         // dense1: h1 for units [128 half, 128 half + 128) of this event
         float u[kMaxA];
 #pragma unroll
         for (int a = 0; a < kMaxA; ++a) u[a] = a < L.na ? 2.0f * Pe[L.a_idx[a]] - 1.0f : 0.0f;
+        uint32_t wb[4] = {0u, 0u, 0u, 0u};  // ReLU activity of this thread's 128 units
+        if (KEEP && half == 0) {
+          for (int a = 0; a < L.na; ++a) {
+            g.UT[size_t(a) * g.n + ev] = __float2bfloat16_rn(u[a]);
+            if (Po != Pe) Po[L.a_idx[a]] = Pe[L.a_idx[a]];
+          }
+          g.UT[size_t(L.na) * g.n + ev] = __float2bfloat16_rn(1.0f);
+        }
         for (int u16 = half * 16; u16 < half * 16 + 16; ++u16) {
           uint4 pk;
           uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
@@ -632,9 +673,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             }
             const __nv_bfloat162 hh = __floats2bfloat162_rn(o[0], o[1]);
             pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+            if (KEEP) {
+              const int jl = (u16 - half * 16) * 8 + 2 * e;  // unit within this thread's 128
+              wb[jl >> 5] |= (uint32_t(__bfloat162float(hh.x) > 0.0f) << (jl & 31)) |
+                             (uint32_t(__bfloat162float(hh.y) > 0.0f) << ((jl + 1) & 31));
+              g.hT1[size_t(u16 * 8 + 2 * e) * g.n + ev] = hh.x;
+              g.hT1[size_t(u16 * 8 + 2 * e + 1) * g.n + ev] = hh.y;
+            }
           }
           *reinterpret_cast<uint4*>(abuf + swz_off(r, u16)) = pk;
         }
+        if (KEEP) reinterpret_cast<uint4*>(g.bits + size_t(ev) * 8)[half] = make_uint4(wb[0], wb[1], wb[2], wb[3]);
         fence_async_smem();
         mbar_arrive(&a_ready);
         // two hidden products: accumulator -> bias, ReLU, BF16 -> operand buffer
@@ -645,6 +694,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const float* bias = m == 0 ? s_b2 : s_b3;
+          __nv_bfloat16* hT = m == 0 ? g.hT2 : g.hT3;
+          uint32_t mb[4] = {0u, 0u, 0u, 0u};
           for (int cg = 0; cg < 2; ++cg) {  // 2 groups of 4 x 16 columns
             uint32_t v[4][16];
             const int col0 = half * 128 + cg * 64;
@@ -664,11 +715,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                   const float o1 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e + 1]) + bias[cc + 1], 0.0f);
                   const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
                   pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                  if (KEEP) {
+                    const int jl = cc - half * 128;
+                    mb[jl >> 5] |= (uint32_t(__bfloat162float(hh.x) > 0.0f) << (jl & 31)) |
+                                   (uint32_t(__bfloat162float(hh.y) > 0.0f) << ((jl + 1) & 31));
+                    hT[size_t(cc) * g.n + ev] = hh.x;
+                    hT[size_t(cc + 1) * g.n + ev] = hh.y;
+                  }
                 }
                 *reinterpret_cast<uint4*>(abuf + swz_off(r, (col0 + 16 * x + 8 * hlf) >> 3)) = pk;
               }
             }
           }
+          if (KEEP)
+            reinterpret_cast<uint4*>(g.bits + (size_t(m + 1) * g.n + ev) * 8)[half] =
+                make_uint4(mb[0], mb[1], mb[2], mb[3]);
           asm volatile("tcgen05.fence::before_thread_sync;");
           fence_async_smem();
           mbar_arrive(&a_ready);
@@ -688,11 +749,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           tmem_wait_ld();
 #pragma unroll
           for (int k = 0; k < kFusedLs; ++k) lg[k] += s_b4[j * kFusedLs + k];
+          if (KEEP) {
+#pragma unroll
+            for (int k = 0; k < 2 * kFusedK + 1; ++k) g.LT[size_t(j * kFusedLs + k) * g.n + ev] = lg[k];
+          }
           Spline sp;
           spline_load_regs<kFusedK>(lg, sp);
           float lc;
           const int d = L.b_idx[j];
-          Pe[d] = spline_fwd(sp, kFusedK, Pe[d], &lc);
+          Po[d] = spline_fwd(sp, kFusedK, Pe[d], &lc);
           ld += lc;
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
@@ -710,6 +775,273 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// ---------------------------------------------------------------------------
+// Fused coupling-layer backward (K = 32 bins): the mirror of the fused layer.
+// Per tile of 128 events the compute warps run the spline backward and write
+// the logit gradients G (BF16) into the swizzled operand buffer; then four
+// tcgen05 products follow the chain dA3 = (G W4) * [h3 > 0], dA2 = (dA3 W3) *
+// [h2 > 0], dA1 = (dA2 W2) * [h1 > 0], dU = dA1 W1, each accumulator turned
+// into the next operand by the compute warps (masks from the transposed
+// activations); the transposed gradients G^T, dA3^T, dA2^T, dA1^T go to
+// global memory for the weight-gradient products, dU into the conditioning
+// coordinates of dP.  Weights (transposed, BF16) stream through a TMA ring.
+struct FusedBwdArgs {
+  const float* Y;   // [n][D] input of the inverse layer (= output of the forward layer)
+  float* dP;        // [n][D] dL/d(inverse-layer output) in, dL/d(input) out
+  const float* LT;  // logits transposed [nout_pad][n] (with bias)
+  const float* w;
+  const double* wsum;
+  const uint32_t* bits;  // ReLU activity of h1, h2, h3: [3][n][8] words
+  __nv_bfloat16 *GT, *dA3T, *dA2T, *dA1T;  // outputs, transposed
+  LayerDev L;
+  int D;
+  long long n, n_real;
+  int* error;
+};
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    flow_layer_bwd_kernel(const __grid_constant__ CUtensorMap map_w4t, const __grid_constant__ CUtensorMap map_w3t,
+                          const __grid_constant__ CUtensorMap map_w2t, const __grid_constant__ CUtensorMap map_w1t,
+                          FusedBwdArgs g, int stages) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int kMaxStages = 4;
+  __shared__ __align__(8) uint64_t w_full[kMaxStages];
+  __shared__ __align__(8) uint64_t w_empty[kMaxStages];
+  __shared__ __align__(8) uint64_t a_ready, acc_full, fin_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int failed;
+
+  const LayerDev& L = g.L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nout = L.nout_pad, kc0 = nout / 64;  // K chunks of the first product
+  const uint32_t stage_bytes = uint32_t(kH) * 128u;
+  unsigned char* abuf = smem;
+  unsigned char* ring = smem + size_t(max(kH, nout)) * 256;
+  const int m_tiles = int(g.n / 128);
+  const int my_tiles = int(blockIdx.x) < m_tiles ? (m_tiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  const int per_tile = kc0 + 12;  // weight chunks per tile: W4^T, W3^T, W2^T, W1^T
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&w_full[s], 1);
+      mbar_init(&w_empty[s], 1);
+    }
+    mbar_init(&a_ready, kFusedCompute);
+    mbar_init(&acc_full, 1);
+    mbar_init(&fin_bar, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0 && my_tiles > 0) {
+      int it = 0;
+      for (int i = 0; i < my_tiles && !failed; ++i) {
+        for (int q = 0; q < per_tile && !failed; ++q, ++it) {
+          const int s = it % stages;
+          const uint32_t use = uint32_t(it / stages);
+          if (use > 0 && !mbar_wait(&w_empty[s], (use - 1) & 1u)) {
+            failed = 1;
+            atomicExch(g.error, 31);
+            break;
+          }
+          unsigned char* dst = ring + size_t(s) * stage_bytes;
+          if (q < kc0) {
+            mbar_expect_tx(&w_full[s], stage_bytes);
+            tma_load_2d(dst, &map_w4t, q * 64, 0, &w_full[s]);
+          } else if (q < kc0 + 8) {
+            const int c = (q - kc0) & 3;
+            mbar_expect_tx(&w_full[s], stage_bytes);
+            tma_load_2d(dst, q < kc0 + 4 ? &map_w3t : &map_w2t, c * 64, 0, &w_full[s]);
+          } else {
+            mbar_expect_tx(&w_full[s], uint32_t(kUPad) * 128u);
+            tma_load_2d(dst, &map_w1t, (q - kc0 - 8) * 64, 0, &w_full[s]);
+          }
+        }
+      }
+      for (int s = 0; s < stages && s < it; ++s) mbar_wait(&w_full[s], uint32_t((it - 1 - s) / stages) & 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && my_tiles > 0) {
+      const uint32_t idesc_h = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kH >> 3) << 17) | (8u << 24);
+      const uint32_t idesc_u = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kUPad >> 3) << 17) | (8u << 24);
+      int it = 0, use_a = 0;
+      bool ok = true;
+      for (int i = 0; i < my_tiles && ok; ++i) {
+        for (int m = 0; m < 4 && ok; ++m, ++use_a) {
+          if (!mbar_wait(&a_ready, uint32_t(use_a) & 1u) || failed) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const int nk = m == 0 ? kc0 : 4;
+          for (int c = 0; c < nk; ++c, ++it) {
+            const int s = it % stages;
+            if (!mbar_wait(&w_full[s], uint32_t(it / stages) & 1u)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint64_t ad = smem_desc(smem_u32(abuf + c * 16384));
+            const uint64_t bd = smem_desc(smem_u32(ring + size_t(s) * stage_bytes));
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              mma_bf16(tmem, ad + uint64_t(k * 2), bd + uint64_t(k * 2), m == 3 ? idesc_u : idesc_h,
+                       (c > 0 || k > 0) ? 1u : 0u);
+            mma_commit(&w_empty[s]);
+          }
+          if (!ok) break;
+          mma_commit(&acc_full);
+        }
+      }
+      if (!ok) {
+        failed = 1;
+        atomicExch(g.error, 32);
+      }
+      mma_commit(&fin_bar);
+      mbar_wait(&fin_bar, 0);
+    }
+  } else {
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    const int r = q * 32 + lane;
+    const uint32_t trow = tmem + (uint32_t(q * 32) << 16);
+    const double wsum = *g.wsum;
+    const size_t n = size_t(g.n);
+    int use_acc = 0;
+    for (int i = 0; i < my_tiles; ++i) {
+      const long long ev = (long long)(int(blockIdx.x) + i * int(gridDim.x)) * 128 + r;
+      const bool real = ev < g.n_real;
+      float* dPe = g.dP + ev * g.D;
+      const float* Ye = g.Y + ev * g.D;
+      if (__any_sync(0xffffffffu, failed != 0)) break;
+      // spline backward of this half's coordinates -> G (operand buffer, G^T)
+      {
+        const float gl = real ? float(-double(g.w[ev]) / wsum) : 0.0f;
+        for (int j = half; j < L.nb; j += 2) {
+          float gw[kFlowMaxBins], gv[kFlowMaxBins + 1];
+          const int d = L.b_idx[j];
+          if (real) {
+            Spline sp;
+            spline_load(g.LT + size_t(j) * kFusedLs * n + ev, n, kFusedK, sp);
+            dPe[d] = spline_inv_bwd(sp, kFusedK, Ye[d], dPe[d], gl, gw, gv);
+          } else {
+            dPe[d] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kFlowMaxBins; ++k) gw[k] = gv[k] = 0.0f;
+            gv[kFlowMaxBins] = 0.0f;
+          }
+          __nv_bfloat16* gt = g.GT + size_t(j) * kFusedLs * n + ev;
+#pragma unroll
+          for (int c8 = 0; c8 < kFusedLs / 8; ++c8) {
+            uint4 pk;
+            uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              float v2[2];
+#pragma unroll
+              for (int h2 = 0; h2 < 2; ++h2) {
+                const int k = c8 * 8 + 2 * e + h2;
+                v2[h2] = k < kFusedK ? gw[k < kFusedK ? k : 0]
+                                     : (k <= 2 * kFusedK ? gv[k <= 2 * kFusedK && k >= kFusedK ? k - kFusedK : 0]
+                                                         : 0.0f);
+              }
+              const __nv_bfloat162 hh = __floats2bfloat162_rn(v2[0], v2[1]);
+              pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+              if (c8 * 8 + 2 * e <= 2 * kFusedK) gt[size_t(c8 * 8 + 2 * e) * n] = hh.x;
+              if (c8 * 8 + 2 * e + 1 <= 2 * kFusedK) gt[size_t(c8 * 8 + 2 * e + 1) * n] = hh.y;
+            }
+            *reinterpret_cast<uint4*>(abuf + swz_off(r, j * (kFusedLs / 8) + c8)) = pk;
+          }
+        }
+        // zero the operand columns of the padding coordinates, and the rows of
+        // G^T past the last coordinate (the buffer is shared by layers with
+        // more transformed coordinates)
+        if (half == 0) {
+          for (int u = L.nb * (kFusedLs / 8); u < nout / 8; ++u)
+            *reinterpret_cast<uint4*>(abuf + swz_off(r, u)) = make_uint4(0u, 0u, 0u, 0u);
+          for (int c = L.nb * kFusedLs; c < nout; ++c) g.GT[size_t(c) * n + ev] = __float2bfloat16_rn(0.0f);
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(&a_ready);
+      // three masked products: accumulator * [h > 0] -> BF16 operand, transposed copy
+      bool ok = true;
+      for (int m = 0; m < 3 && ok; ++m, ++use_acc) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full, uint32_t(use_acc) & 1u))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // the activity bits of this thread's 128 columns of h3, h2, h1
+        const uint4 mbv = reinterpret_cast<const uint4*>(g.bits + (size_t(2 - m) * n + ev) * 8)[half];
+        const uint32_t mbw[4] = {mbv.x, mbv.y, mbv.z, mbv.w};
+        __nv_bfloat16* outT = m == 0 ? g.dA3T : (m == 1 ? g.dA2T : g.dA1T);
+        for (int cg = 0; cg < 2; ++cg) {
+          uint32_t v[4][16];
+          const int col0 = half * 128 + cg * 64;
+#pragma unroll
+          for (int x = 0; x < 4; ++x) tmem_ld16_nw(trow + uint32_t(col0 + 16 * x), v[x]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+#pragma unroll
+            for (int hlf = 0; hlf < 2; ++hlf) {
+              uint4 pk;
+              uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int cc = col0 + 16 * x + 8 * hlf + 2 * e;
+                const int jl = cc - half * 128;
+                const uint32_t word = mbw[cg * 2 + (x >> 1)];  // jl >> 5 = 2 cg + x / 2
+                const float o0 = (word >> (jl & 31)) & 1u ? __uint_as_float(v[x][8 * hlf + 2 * e]) : 0.0f;
+                const float o1 = (word >> ((jl + 1) & 31)) & 1u ? __uint_as_float(v[x][8 * hlf + 2 * e + 1]) : 0.0f;
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
+                pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                outT[size_t(cc) * n + ev] = hh.x;
+                outT[size_t(cc + 1) * n + ev] = hh.y;
+              }
+              *reinterpret_cast<uint4*>(abuf + swz_off(r, (col0 + 16 * x + 8 * hlf) >> 3)) = pk;
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        fence_async_smem();
+        mbar_arrive(&a_ready);
+      }
+      if (ok && !__all_sync(0xffffffffu, mbar_wait(&acc_full, uint32_t(use_acc) & 1u))) ok = false;
+      ++use_acc;
+      if (!ok) {
+        failed = 1;
+        if (lane == 0) atomicExch(g.error, 33);
+        break;
+      }
+      // dU = dA1 W1 into the conditioning coordinates: dL/dx_A += 2 dU
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (half == 0) {
+        uint32_t v[16];
+        tmem_ld16_nw(trow, v);
+        tmem_wait_ld();
+        for (int a = 0; a < L.na; ++a) dPe[L.a_idx[a]] += 2.0f * __uint_as_float(v[a < 16 ? a : 0]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
 }  // namespace
@@ -734,6 +1066,7 @@ struct mc_flow_s {
   float *P = nullptr, *logq = nullptr, *f = nullptr, *w = nullptr, *dP = nullptr, *LT = nullptr;
   __nv_bfloat16 *h = nullptr, *hT = nullptr, *G = nullptr, *GT = nullptr, *dA = nullptr, *dAT = nullptr;
   __nv_bfloat16* UT = nullptr;  // per layer: first-layer inputs, transposed [16][n]
+  uint32_t* MB = nullptr;       // per layer: ReLU activity bits of h1, h2, h3 [3][n][8]
   float* dU = nullptr;          // [n][16] input gradient of the first layer
   float* part = nullptr;  // split-K partial products of the weight gradients
   int max_splits = 0;
@@ -744,10 +1077,12 @@ struct mc_flow_s {
   int* err = nullptr;
   int nout_pad_max = 0;
   // fused sampling layers (K = 32, nout_pad <= 512): tensor maps of W2, W3, W4 per layer
-  bool use_fused = true;
+  bool use_fused = true;      // fused forward layers
+  bool use_fused_bwd = true;  // fused backward layers
   std::vector<bool> fused_ok;
   std::vector<int> n_sub4;
   std::vector<CUtensorMap> maps;
+  std::vector<CUtensorMap> bwd_maps;  // W4^T, W3^T, W2^T, W1^T per layer (fused backward)
 };
 
 namespace {
@@ -772,6 +1107,12 @@ __nv_bfloat16* h_of(mc_flow F, int l, int k) { return F->h + (size_t(l) * 3 + k)
 __nv_bfloat16* hT_of(mc_flow F, int l, int k) { return F->hT + (size_t(l) * 3 + k) * F->bp * kH; }
 float* LT_of(mc_flow F, int l) { return F->LT + size_t(l) * F->bp * F->nout_pad_max; }
 __nv_bfloat16* UT_of(mc_flow F, int l) { return F->UT + size_t(l) * F->bp * mc::kUPad; }
+uint32_t* MB_of(mc_flow F, int l) { return F->MB + size_t(l) * 3 * F->bp * 8; }
+
+// ReLU activity bits of layer slot l from its transposed activations (n rows).
+void make_mask_bits(mc_flow F, int l, long long n, cudaStream_t st) {
+  mc::mask_bits_kernel<<<mc::blocks_for(24 * n, 256), 256, 0, st>>>(hT_of(F, l, 0), size_t(F->bp) * kH, n, MB_of(F, l));
+}
 
 // N tile: the largest multiple of 16 up to 256 that divides N.
 int pick_bn(int N) {
@@ -780,7 +1121,8 @@ int pick_bn(int N) {
   return 16;
 }
 
-// Persistent B-resident product out = epilogue(A [n x K] . B^T), B [N x K].
+// Persistent B-resident product out = epilogue(A [n x K] . B^T), B [N x K];
+// for the ReLU-mask epilogue, mask is the activation transposed [N][n].
 int gemm_rs(mc_flow F, long long n, int N, int K, int epi, const __nv_bfloat16* a, const __nv_bfloat16* b,
             const float* bias, void* c, void* c_t, const __nv_bfloat16* mask, cudaStream_t st) {
   FLOW_CUDA(cudaGetLastError());  // launches queued before this product
@@ -801,8 +1143,8 @@ int gemm_rs(mc_flow F, long long n, int N, int K, int epi, const __nv_bfloat16* 
     g.c_bf16 = static_cast<__nv_bfloat16*>(c);
     g.c_t_bf16 = static_cast<__nv_bfloat16*>(c_t);
   }
-  g.mask = mask;
-  g.ld_mask = N;
+  g.mask_t = mask;  // the layer's activation transposed [N][n]
+  g.ld_mask_t = int(n);
   g.error = F->err;
   FLOW_CUDA(mc::tc_gemm_rs(g, a, K, b, K, st));
   return MC_OK;
@@ -856,8 +1198,10 @@ int conditioner(mc_flow F, int l, int slot, const float* P, long long n, bool ke
                  st);
 }
 
-// One fused sampling layer (flow_layer_fused_kernel) over n rows of P[0].
-int fused_layer(mc_flow F, int l, long long n, cudaStream_t st) {
+// One fused layer (flow_layer_fused_kernel) over n rows: sampling maps P[0]
+// in place; keep (training) maps P[l] to P[l+1] and writes the transposed
+// activations, first-layer inputs and logits of slot l.
+int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st) {
   FLOW_CUDA(cudaGetLastError());  // launches queued before this one
   static int num_sms = 0;
   if (num_sms == 0) {
@@ -869,8 +1213,17 @@ int fused_layer(mc_flow F, int l, long long n, cudaStream_t st) {
   const LayerDev& L = F->layers[l];
   mc::FusedLayerArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.P = P_of(F, 0);
+  a.P = keep ? P_of(F, l) : P_of(F, 0);
+  a.Pout = keep ? P_of(F, l + 1) : P_of(F, 0);
   a.logq = F->logq;
+  if (keep) {
+    a.hT1 = hT_of(F, l, 0);
+    a.hT2 = hT_of(F, l, 1);
+    a.hT3 = hT_of(F, l, 2);
+    a.UT = UT_of(F, l);
+    a.LT = LT_of(F, l);
+    a.bits = MB_of(F, l);
+  }
   a.params = F->d_params;
   a.L = L;
   a.D = F->D;
@@ -882,10 +1235,10 @@ int fused_layer(mc_flow F, int l, long long n, cudaStream_t st) {
   const int stages = int(std::min<size_t>(4, (kMaxDyn - 1024 - mc::kFusedABytes) / stage));
   if (stages < 2) return ffail(MC_EINVAL, "mc_flow: fused layer does not fit in shared memory");
   const size_t smem = 1024 + mc::kFusedABytes + stages * stage;
-  FLOW_CUDA(cudaFuncSetAttribute(mc::flow_layer_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  auto kern = keep ? mc::flow_layer_fused_kernel<true> : mc::flow_layer_fused_kernel<false>;
+  FLOW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const int grid = int(std::min<long long>(n / 128, num_sms));
-  mc::flow_layer_fused_kernel<<<grid, mc::kFusedThreads, smem, st>>>(F->maps[3 * l], F->maps[3 * l + 1],
-                                                                     F->maps[3 * l + 2], a, stages);
+  kern<<<grid, mc::kFusedThreads, smem, st>>>(F->maps[3 * l], F->maps[3 * l + 1], F->maps[3 * l + 2], a, stages);
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
@@ -896,14 +1249,15 @@ int fused_layer(mc_flow F, int l, long long n, cudaStream_t st) {
 int forward_pass(mc_flow F, long long n, bool keep, cudaStream_t st) {
   FLOW_CUDA(cudaMemsetAsync(F->logq, 0, sizeof(float) * n, st));
   for (int l = 0; l < F->L; ++l) {
-    if (!keep && F->use_fused && F->fused_ok[l]) {
-      if (int rc = fused_layer(F, l, n, st)) return rc;
+    if (F->use_fused && F->fused_ok[l]) {
+      if (int rc = fused_layer(F, l, n, keep, st)) return rc;
       continue;
     }
     const int slot = keep ? l : 0;
     const float* Pin = keep ? P_of(F, l) : P_of(F, 0);
     float* Pout = keep ? P_of(F, l + 1) : P_of(F, 0);
     if (int rc = conditioner(F, l, slot, Pin, n, keep, st)) return rc;
+    if (keep) make_mask_bits(F, l, n, st);
     mc::spline_fwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(Pin, Pout, F->D, F->layers[l], LT_of(F, slot),
                                                                    size_t(n), F->K, F->logq, n);
   }
@@ -917,9 +1271,54 @@ int inverse_pass(mc_flow F, long long n, cudaStream_t st) {
   FLOW_CUDA(cudaMemsetAsync(F->logq, 0, sizeof(float) * n, st));
   for (int l = F->L - 1; l >= 0; --l) {
     if (int rc = conditioner(F, l, l, P_of(F, l + 1), n, true, st)) return rc;
+    make_mask_bits(F, l, n, st);
     mc::spline_inv_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P_of(F, l + 1), P_of(F, l), F->D, F->layers[l],
                                                                    LT_of(F, l), size_t(n), F->K, F->logq, n);
   }
+  FLOW_CUDA(cudaGetLastError());
+  return MC_OK;
+}
+
+// Fused backward of layer l (flow_layer_bwd_kernel): dP updated, the
+// transposed gradients G^T and dA3^T, dA2^T, dA1^T (three slices of F->dAT)
+// written for the weight-gradient products.
+int fused_bwd_layer(mc_flow F, int l, long long n, long long n_real, cudaStream_t st) {
+  FLOW_CUDA(cudaGetLastError());
+  static int num_sms = 0;
+  if (num_sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms < 1)
+      num_sms = 1;
+  }
+  const LayerDev& L = F->layers[l];
+  mc::FusedBwdArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.Y = P_of(F, l + 1);
+  a.dP = F->dP;
+  a.LT = LT_of(F, l);
+  a.w = F->w;
+  a.wsum = F->sums;
+  a.bits = MB_of(F, l);
+  a.GT = F->GT;
+  a.dA3T = F->dAT;
+  a.dA2T = F->dAT + size_t(F->bp) * kH;
+  a.dA1T = F->dAT + 2 * size_t(F->bp) * kH;
+  a.L = L;
+  a.D = F->D;
+  a.n = n;
+  a.n_real = n_real;
+  a.error = F->err;
+  constexpr size_t kMaxDyn = 232448 - 2048;  // opt-in limit less the kernel's static shared memory
+  const size_t abytes = size_t(std::max(kH, L.nout_pad)) * 256, stage = size_t(kH) * 128;
+  const int stages = int(std::min<size_t>(4, (kMaxDyn - 1024 - abytes) / stage));
+  if (stages < 2) return ffail(MC_EINVAL, "mc_flow: fused backward does not fit in shared memory");
+  const size_t smem = 1024 + abytes + stages * stage;
+  FLOW_CUDA(cudaFuncSetAttribute(mc::flow_layer_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const int grid = int(std::min<long long>(n / 128, num_sms));
+  mc::flow_layer_bwd_kernel<<<grid, mc::kFusedThreads, smem, st>>>(F->bwd_maps[4 * l], F->bwd_maps[4 * l + 1],
+                                                                   F->bwd_maps[4 * l + 2], F->bwd_maps[4 * l + 3], a,
+                                                                   stages);
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
@@ -933,6 +1332,24 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
   FLOW_CUDA(cudaMemsetAsync(F->dP, 0, sizeof(float) * n * D, st));
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& L = F->layers[l];
+    if (F->use_fused_bwd && F->fused_ok[l]) {
+      // spline and activation gradients in one kernel, then the weight gradients
+      __nv_bfloat16* dA3T = F->dAT;
+      __nv_bfloat16* dA2T = F->dAT + size_t(F->bp) * kH;
+      __nv_bfloat16* dA1T = F->dAT + 2 * size_t(F->bp) * kH;
+      if (int rc = fused_bwd_layer(F, l, n, n_real, st)) return rc;
+      if (int rc = gemm_wgrad(F, n, L.nout_pad, hT_of(F, l, 2), F->GT, g + L.off_W4, st)) return rc;
+      mc::rowsum_bf16_kernel<<<L.nout_pad, 256, 0, st>>>(F->GT, n, g + L.off_b4);
+      if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 1), dA3T, g + L.off_W3, st)) return rc;
+      mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(dA3T, n, g + L.off_b3);
+      if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 0), dA2T, g + L.off_W2, st)) return rc;
+      mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(dA2T, n, g + L.off_b2);
+      int splits = 0;
+      if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, UT_of(F, l), nullptr, st, &splits)) return rc;
+      mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
+      FLOW_CUDA(cudaGetLastError());
+      continue;
+    }
     __nv_bfloat16* dA = F->dA;
     __nv_bfloat16* dA_b = F->dA + size_t(F->bp) * kH;
     mc::spline_inv_bwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P_of(F, l + 1), F->dP, D, L, LT_of(F, l), F->K,
@@ -941,17 +1358,17 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
     if (int rc = gemm_wgrad(F, n, L.nout_pad, hT_of(F, l, 2), F->GT, g + L.off_W4, st)) return rc;
     mc::rowsum_bf16_kernel<<<L.nout_pad, 256, 0, st>>>(F->GT, n, g + L.off_b4);
     if (int rc = gemm_rs(F, n, kH, L.nout_pad, mc::kEpiReluMaskBf16, F->G, L.W4t, nullptr, dA, F->dAT,
-                         h_of(F, l, 2), st))
+                         hT_of(F, l, 2), st))
       return rc;
     // third dense layer
     if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 1), F->dAT, g + L.off_W3, st)) return rc;
     mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b3);
-    if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA, L.W3t, nullptr, dA_b, F->dAT, h_of(F, l, 1), st))
+    if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA, L.W3t, nullptr, dA_b, F->dAT, hT_of(F, l, 1), st))
       return rc;
     // second dense layer
     if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 0), F->dAT, g + L.off_W2, st)) return rc;
     mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b2);
-    if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA_b, L.W2t, nullptr, dA, F->dAT, h_of(F, l, 0), st))
+    if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA_b, L.W2t, nullptr, dA, F->dAT, hT_of(F, l, 0), st))
       return rc;
     // first dense layer: dU = dA1 W1 (tensor cores, W1 zero-padded to 16
     // columns) into the conditioning coordinates of dP; W1 and b1 from the
@@ -1076,7 +1493,7 @@ int mc_flow_free(mc_flow F) {
   for (void* p : {(void*)F->d_params, (void*)F->d_grads, (void*)F->d_m, (void*)F->d_v, (void*)F->d_wbf,
                   (void*)F->d_layers, (void*)F->P, (void*)F->logq, (void*)F->f, (void*)F->w, (void*)F->dP,
                   (void*)F->LT, (void*)F->h, (void*)F->hT, (void*)F->G, (void*)F->GT, (void*)F->dA, (void*)F->dAT,
-                  (void*)F->part, (void*)F->UT, (void*)F->dU, (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
+                  (void*)F->part, (void*)F->UT, (void*)F->MB, (void*)F->dU, (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
                   (void*)F->err})
     cudaFree(p);
   if (F->h_sums) cudaFreeHost(F->h_sums);
@@ -1151,9 +1568,10 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->G, sizeof(__nv_bfloat16) * bp * np);
   alloc((void**)&F->GT, sizeof(__nv_bfloat16) * bp * np);
   alloc((void**)&F->dA, sizeof(__nv_bfloat16) * 2 * bp * kH);
-  alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * bp * kH);
+  alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * 3 * bp * kH);
   alloc((void**)&F->part, sizeof(float) * size_t(F->max_splits) * kH * np);
   alloc((void**)&F->UT, sizeof(__nv_bfloat16) * L * mc::kUPad * bp);
+  alloc((void**)&F->MB, sizeof(uint32_t) * L * 3 * bp * 8);
   alloc((void**)&F->dU, sizeof(float) * bp * mc::kUPad);
   alloc((void**)&F->sums, sizeof(double) * 2);
   alloc((void**)&F->parts, sizeof(BlockPartial) * kPartsGrid);
@@ -1178,6 +1596,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   build_host_map(F);
   // tensor maps of the fused sampling layers
   F->maps.resize(3 * L);
+  F->bwd_maps.resize(4 * L);
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& Ld = F->layers[l];
     const int n_sub4 = (Ld.nout_pad + 255) / 256;
@@ -1186,7 +1605,11 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
               sub4 % 16 == 0;
     ok = ok && mc::tc_make_map(&F->maps[3 * l], Ld.W2h, kH, kH, kH, kH) &&
          mc::tc_make_map(&F->maps[3 * l + 1], Ld.W3h, kH, kH, kH, kH) &&
-         mc::tc_make_map(&F->maps[3 * l + 2], Ld.W4h, Ld.nout_pad, kH, kH, sub4);
+         mc::tc_make_map(&F->maps[3 * l + 2], Ld.W4h, Ld.nout_pad, kH, kH, sub4) &&
+         mc::tc_make_map(&F->bwd_maps[4 * l], Ld.W4t, kH, Ld.nout_pad, Ld.nout_pad, kH) &&
+         mc::tc_make_map(&F->bwd_maps[4 * l + 1], Ld.W3t, kH, kH, kH, kH) &&
+         mc::tc_make_map(&F->bwd_maps[4 * l + 2], Ld.W2t, kH, kH, kH, kH) &&
+         mc::tc_make_map(&F->bwd_maps[4 * l + 3], Ld.W1t, mc::kUPad, kH, kH, mc::kUPad);
     F->fused_ok.push_back(ok);
     F->n_sub4.push_back(n_sub4);
   }
@@ -1229,9 +1652,10 @@ int mc_flow_get_params(mc_flow F, float* host) {
   return MC_OK;
 }
 
-int mc_flow_set_fused(mc_flow F, int enable) {
-  if (!F) return ffail(MC_EINVAL, "mc_flow_set_fused: NULL handle");
-  F->use_fused = enable != 0;
+int mc_flow_set_fused(mc_flow F, int mask) {
+  if (!F || mask < 0 || mask > 3) return ffail(MC_EINVAL, "mc_flow_set_fused: bad arguments");
+  F->use_fused = (mask & 1) != 0;
+  F->use_fused_bwd = (mask & 2) != 0;
   return MC_OK;
 }
 
@@ -1260,8 +1684,7 @@ int mc_flow_loss_grad(mc_flow F, int64_t n, const float* x, const float* w, doub
   FLOW_CUDA(cudaMemcpyAsync(F->w, w, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
   mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
   if (int rc = inverse_pass(F, np, st)) return rc;
-  FLOW_CUDA(cudaMemsetAsync(F->sums, 0, sizeof(double) * 2, st));
-  mc::loss_sums_kernel<<<std::min<unsigned>(mc::blocks_for(n, 256), 1184u), 256, 0, st>>>(F->w, F->logq, n, F->sums);
+  mc::loss_sums_kernel<<<1, 1024, 0, st>>>(F->w, F->logq, n, F->sums);
   if (int rc = backward_pass(F, np, n, st)) return rc;
   FLOW_CUDA(cudaMemcpyAsync(F->h_sums, F->sums, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
   if (int rc = check_err(F, st)) return rc;
@@ -1320,9 +1743,7 @@ int mc_flow_train(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int steps, int
     if (int rc = eval_points(F, itg, pdf, P_of(F, F->L), n, F->f, st)) return rc;
     FLOW_CUDA(cudaMemsetAsync(F->w, 0, sizeof(float) * np, st));
     mc::flow_weights_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->f, F->logq, F->w, n);
-    FLOW_CUDA(cudaMemsetAsync(F->sums, 0, sizeof(double) * 2, st));
-    mc::loss_sums_kernel<<<std::min<unsigned>(mc::blocks_for(n, 256), 1184u), 256, 0, st>>>(F->w, F->logq, n,
-                                                                                            F->sums);
+    mc::loss_sums_kernel<<<1, 1024, 0, st>>>(F->w, F->logq, n, F->sums);
     // the forward activations are those of the density pass at x: backward, Adam
     mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
     if (int rc = backward_pass(F, np, n, st)) return rc;

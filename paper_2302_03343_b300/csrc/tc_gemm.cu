@@ -214,13 +214,19 @@ __device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float* o
 __device__ __forceinline__ void rs_epilogue16(const TcGemmArgs& g, int row, int col0, const float* v) {
   float o[16];
   if (g.epilogue == kEpiReluMaskBf16) {
-    uint4 mw[2];
-    const uint4* mp = reinterpret_cast<const uint4*>(g.mask + size_t(row) * g.ld_mask + col0);
-    mw[0] = mp[0];
-    mw[1] = mp[1];
-    const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(mw);
+    if (g.mask) {
+      uint4 mw[2];
+      const uint4* mp = reinterpret_cast<const uint4*>(g.mask + size_t(row) * g.ld_mask + col0);
+      mw[0] = mp[0];
+      mw[1] = mp[1];
+      const __nv_bfloat16* m = reinterpret_cast<const __nv_bfloat16*>(mw);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) o[j] = __bfloat162float(m[j]) > 0.0f ? v[j] : 0.0f;
+      for (int j = 0; j < 16; ++j) o[j] = __bfloat162float(m[j]) > 0.0f ? v[j] : 0.0f;
+    } else {  // transposed activation: coalesced over the warp's rows
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        o[j] = __bfloat162float(g.mask_t[size_t(col0 + j) * g.ld_mask_t + row]) > 0.0f ? v[j] : 0.0f;
+    }
   } else {
     if (g.bias) {
       const float4* bp = reinterpret_cast<const float4*>(g.bias + col0);
@@ -510,7 +516,9 @@ cudaError_t tc_gemm_rs(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, con
   if ((g.c_f32 && !aligned16(g.c_f32)) || (g.c_bf16 && !aligned16(g.c_bf16)) || (g.ldc % 8) ||
       ((g.c_t_bf16 || g.c_t_f32) && g.ldt < g.M))
     return cudaErrorInvalidValue;
-  if (g.epilogue == kEpiReluMaskBf16 && (!g.mask || !aligned16(g.mask) || (g.ld_mask % 8))) return cudaErrorInvalidValue;
+  if (g.epilogue == kEpiReluMaskBf16 &&
+      (g.mask ? (!aligned16(g.mask) || (g.ld_mask % 8)) : (!g.mask_t || g.ld_mask_t < g.M)))
+    return cudaErrorInvalidValue;
   if (g.bias && !aligned16(g.bias)) return cudaErrorInvalidValue;
   const size_t b_bytes = size_t(g.bn) * g.K * 2;
   const size_t room = kMaxSmem - 1024 - b_bytes;

@@ -23,7 +23,9 @@ struct TcGemmArgs {
   __nv_bfloat16* c_bf16;       // row-major, leading dimension ldc
   int ldc;
   const __nv_bfloat16* mask;   // kEpiReluMaskBf16: activation of the layer, leading dimension ld_mask
-  int ld_mask;
+  int ld_mask;                 // (or, in tc_gemm_rs, mask == null and mask_t: the activation transposed,
+  const __nv_bfloat16* mask_t; //  mask_t[col * ld_mask_t + row])
+  int ld_mask_t;
   int* error;                  // device flag: set non-zero when a bounded wait timed out
   // optional transposed copies written by the persistent kernel (tc_gemm_rs):
   // c_t_bf16[col * ldt + row] (epilogues 0 and 2), c_t_f32[col * ldt + row] (epilogue 1)

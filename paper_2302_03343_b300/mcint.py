@@ -470,7 +470,9 @@ def mc_flow_get_params(f):
 
 
 def mc_flow_set_fused(f, enable):
-    _check(lib().mc_flow_set_fused(f.handle, 1 if enable else 0))
+    """enable: bool (both directions) or a mask (bit 0 forward, bit 1 backward)."""
+    mask = (3 if enable else 0) if isinstance(enable, bool) else int(enable)
+    _check(lib().mc_flow_set_fused(f.handle, mask))
 
 
 def mc_flow_forward(f, z_dev, x_dev, logq_dev, stream=None):

@@ -234,3 +234,20 @@ def test_fused_layer_matches_layer_by_layer(gpu, D, n):
     assert torch.equal(out[0][1], out[1][1])
     assert out[0][1].abs().max().item() > 0.3
     f.free()
+
+
+def test_fused_training_matches_layer_by_layer(gpu):
+    """Training steps with the fused forward (activations written from the
+    fused layer) and with the layer-by-layer kernels give bit-identical
+    parameters: every reduction on the training path has a fixed order."""
+    itg = W.gauss(7, sigma=0.2)
+    params = []
+    for fused in (True, False):
+        f, _ = make_flow(7, seed=8, last_scale=0.5, max_batch=4096, flow_seed=5)
+        M.mc_flow_set_fused(f, fused)
+        M.mc_flow_train(f, itg, None, steps=3, batch=4000, lr=1e-3, losses=False)
+        params.append(M.mc_flow_get_params(f))
+        f.free()
+    for l in range(L):
+        for k in M.FLOW_KEYS:
+            assert np.array_equal(params[0][l][k], params[1][l][k]), (l, k)
