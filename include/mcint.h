@@ -262,6 +262,15 @@ int mc_batch_free(mc_batch b);
 int mc_gemm_bf16(int M, int N, int K, int bn, int epilogue, const void* a, int lda, const void* b, int ldb,
                  const float* bias, void* c, int ldc, const void* mask, int ld_mask, int splits, int* err,
                  void* stream);
+/* mc_gemm_bf16_tn: C[M x N] (+)= X^T Y with X [K x M] and Y [K x N]
+ * row-major BF16 (device; leading dimensions ldx >= M, ldy >= N, multiples
+ * of 8): the weight gradient of a dense layer from row-major activations and
+ * gradients, both operands read MN-major by the tensor cores.  Epilogue 1
+ * (C = acc), 3 (C += acc, split-K) or 4 (per-split partials as above);
+ * M % 128 == 0, K % 64 == 0, bn a multiple of 64 <= 256 dividing N.
+ * Asynchronous on `stream`. */
+int mc_gemm_bf16_tn(int M, int N, int K, int bn, int epilogue, const void* x, int ldx, const void* y, int ldy,
+                    float* c, int ldc, int splits, int* err, void* stream);
 /* mc_gemm_bf16_rs: the same product for a long A and a short B (a dense
  * layer applied to a batch): a persistent kernel keeps B in shared memory
  * (bn * K * 2 bytes, K <= 320) and streams the 128-row tiles of A, with the

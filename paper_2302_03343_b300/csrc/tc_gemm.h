@@ -44,6 +44,13 @@ bool tc_make_map(CUtensorMap* m, const void* base, int rows, int k, int ld, int 
 cudaError_t tc_gemm(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, const __nv_bfloat16* b, int ldb,
                     int splits, cudaStream_t st);
 
+// Both operands MN-major: C[M x N] (+)= X^T Y with X [K x M] (leading
+// dimension ldx >= M) and Y [K x N] (ldy >= N) row-major, split-K over
+// `splits`; bn a multiple of 64, epilogues 1, 3 or 4.  The weight gradient
+// of a dense layer straight from row-major activations and gradients.
+cudaError_t tc_gemm_tn(const TcGemmArgs& g, const __nv_bfloat16* x, int ldx, const __nv_bfloat16* y, int ldy,
+                       int splits, cudaStream_t st);
+
 // Persistent variant for a long A and a short B (the dense layers applied to
 // a batch): B [N x K] stays resident in shared memory (bn * K * 2 bytes <=
 // 160 KiB, K <= 320), A tiles stream through a TMA ring, two TMEM

@@ -140,3 +140,19 @@ def test_gemm_rs_rejects_oversized_b(dev):
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     with pytest.raises(M.McError):
         M.mc_gemm_bf16_rs(128, 256, 384, 256, M.EPI_BIAS_F32, a, b, c=c, err=err)
+
+
+# both operands MN-major: C = X^T Y from row-major X [K x M], Y [K x N]
+@pytest.mark.parametrize("M_,N,K,bn,splits", [(128, 64, 64, 64, 1), (256, 256, 4096, 256, 4), (256, 320, 8192, 64, 8),
+                                              (128, 128, 65536, 128, 37)])
+def test_gemm_tn_weight_gradient(dev, M_, N, K, bn, splits):
+    g = torch.Generator(device="cpu").manual_seed(7)
+    x = torch.randn(K, M_, generator=g).to(torch.bfloat16).to(dev)
+    y = torch.randn(K, N, generator=g).to(torch.bfloat16).to(dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    c = torch.zeros((M_, N), device=dev)
+    M.mc_gemm_bf16_tn(M_, N, K, bn, M.EPI_ATOMIC_F32, x, y, c, splits=splits, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = x.double().T @ y.double()
+    assert ((c.double() - ref).abs().max() / ref.abs().max()).item() < 1e-5
