@@ -373,13 +373,14 @@ __global__ void flow_weights_kernel(const float* f, const float* logq, float* w,
   w[i] = isfinite(wi) ? wi : 0.0f;
 }
 
-// Loss sums in FP64: sums[0] = sum w, sums[1] = sum w log q; one block, fixed
-// reduction order (deterministic).
-__global__ void __launch_bounds__(1024) loss_sums_kernel(const float* w, const float* logq, long long n,
-                                                         double* sums) {
-  __shared__ double sh[2][32];
+// Loss sums in FP64: sums[0] = sum w, sums[1] = sum w log q, in a fixed
+// order (deterministic): per-block partials, then one block sums them.
+constexpr int kLossBlocks = 148;
+__global__ void __launch_bounds__(256) loss_partials_kernel(const float* w, const float* logq, long long n,
+                                                            double* part) {
+  __shared__ double sh[2][8];
   double a = 0.0, b = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     a += w[i];
     b += double(w[i]) * logq[i];
   }
@@ -398,9 +399,19 @@ __global__ void __launch_bounds__(1024) loss_sums_kernel(const float* w, const f
       sa += sh[0][k];
       sb += sh[1][k];
     }
-    sums[0] = sa;
-    sums[1] = sb;
+    part[2 * blockIdx.x] = sa;
+    part[2 * blockIdx.x + 1] = sb;
   }
+}
+__global__ void loss_final_kernel(const double* part, int nblocks, double* sums) {
+  if (threadIdx.x != 0) return;
+  double sa = 0.0, sb = 0.0;
+  for (int k = 0; k < nblocks; ++k) {
+    sa += part[2 * k];
+    sb += part[2 * k + 1];
+  }
+  sums[0] = sa;
+  sums[1] = sb;
 }
 
 // Adam (thesis Sec. "Optimizers") on every master parameter; gradients of the
@@ -413,24 +424,41 @@ __global__ void adam_kernel(float* params, const float* grads, float* m, float* 
   const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= n) return;
   size_t gidx = idx;
+  // the BF16 copies the tensor cores read: W2, W3, W4 and their transposes, W1^T
+  __nv_bfloat16 *dst = nullptr, *dst_t = nullptr;
+  size_t di = 0, dti = 0;
   for (int l = 0; l < nl; ++l) {
     const LayerDev& L = layers[l];
-    auto tr = [&](size_t off, int rows, int cols) {  // W [rows x cols], gradient stored [cols x rows]
+    auto tr = [&](size_t off, int rows, int cols, __nv_bfloat16* h, __nv_bfloat16* ht) {
+      // W [rows x cols], gradient stored [cols x rows]
       if (idx >= off && idx < off + size_t(rows) * cols) {
-        const size_t e = idx - off;
-        gidx = off + (e % cols) * rows + e / cols;
+        const size_t e = idx - off, r = e / cols, c = e % cols;
+        gidx = off + c * rows + r;
+        dst = h;
+        di = e;
+        dst_t = ht;
+        dti = c * rows + r;
       }
     };
-    tr(L.off_W2, kH, kH);
-    tr(L.off_W3, kH, kH);
-    tr(L.off_W4, L.nout_pad, kH);
+    tr(L.off_W2, kH, kH, L.W2h, L.W2t);
+    tr(L.off_W3, kH, kH, L.W3h, L.W3t);
+    tr(L.off_W4, L.nout_pad, kH, L.W4h, L.W4t);
+    if (idx >= L.off_W1 && idx < L.off_W1 + size_t(kH) * L.na) {
+      const size_t e = idx - L.off_W1;
+      dst_t = L.W1t;
+      dti = (e % L.na) * kH + e / L.na;
+    }
   }
   const float g = grads[gidx];
   const float mi = A.b1 * m[idx] + (1.0f - A.b1) * g;
   const float vi = A.b2 * v[idx] + (1.0f - A.b2) * g * g;
   m[idx] = mi;
   v[idx] = vi;
-  params[idx] -= A.lr * (mi * A.c1) / (sqrtf(vi * A.c2) + A.eps);
+  const float p = params[idx] - A.lr * (mi * A.c1) / (sqrtf(vi * A.c2) + A.eps);
+  params[idx] = p;
+  const __nv_bfloat16 h = __float2bfloat16_rn(p);
+  if (dst) dst[di] = h;
+  if (dst_t) dst_t[dti] = h;
 }
 
 // W1t [16][H] = W1^T zero-padded (W1 [H x na], FP32).
@@ -1074,6 +1102,9 @@ struct mc_flow_s {
   double* h_sums = nullptr;  // pinned
   BlockPartial *parts = nullptr, *chunk_totals = nullptr, *total = nullptr, *h_total = nullptr;
   long long max_chunks = 0;
+  // sampling chunks of the fused path (which needs only the points and log q)
+  long long sbp = 0;
+  float *Ps = nullptr, *lqs = nullptr;
   int* err = nullptr;
   int nout_pad_max = 0;
   // fused sampling layers (K = 32, nout_pad <= 512): tensor maps of W2, W3, W4 per layer
@@ -1201,7 +1232,7 @@ int conditioner(mc_flow F, int l, int slot, const float* P, long long n, bool ke
 // One fused layer (flow_layer_fused_kernel) over n rows: sampling maps P[0]
 // in place; keep (training) maps P[l] to P[l+1] and writes the transposed
 // activations, first-layer inputs and logits of slot l.
-int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st) {
+int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st, float* P0 = nullptr, float* lq = nullptr) {
   FLOW_CUDA(cudaGetLastError());  // launches queued before this one
   static int num_sms = 0;
   if (num_sms == 0) {
@@ -1213,9 +1244,9 @@ int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st) {
   const LayerDev& L = F->layers[l];
   mc::FusedLayerArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.P = keep ? P_of(F, l) : P_of(F, 0);
-  a.Pout = keep ? P_of(F, l + 1) : P_of(F, 0);
-  a.logq = F->logq;
+  a.P = keep ? P_of(F, l) : (P0 ? P0 : P_of(F, 0));
+  a.Pout = keep ? P_of(F, l + 1) : (P0 ? P0 : P_of(F, 0));
+  a.logq = lq ? lq : F->logq;
   if (keep) {
     a.hT1 = hT_of(F, l, 0);
     a.hT2 = hT_of(F, l, 1);
@@ -1243,14 +1274,12 @@ int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st) {
   return MC_OK;
 }
 
-// Forward (sampling direction) from P[0] = z over n (multiple of 128) rows;
-// logq initialised to 0.  keep: layer l writes P[l+1] and keeps its
-// activations (training); otherwise P[0] is mapped in place (sampling).
-int forward_pass(mc_flow F, long long n, bool keep, cudaStream_t st) {
-  FLOW_CUDA(cudaMemsetAsync(F->logq, 0, sizeof(float) * n, st));
+// The L layers of the forward direction (see forward_pass); P0 / logq
+// override the points and log q of the sampling path (fused layers only).
+int forward_layers(mc_flow F, long long n, bool keep, cudaStream_t st, float* P0 = nullptr, float* lq = nullptr) {
   for (int l = 0; l < F->L; ++l) {
     if (F->use_fused && F->fused_ok[l]) {
-      if (int rc = fused_layer(F, l, n, keep, st)) return rc;
+      if (int rc = fused_layer(F, l, n, keep, st, P0, lq)) return rc;
       continue;
     }
     const int slot = keep ? l : 0;
@@ -1263,6 +1292,14 @@ int forward_pass(mc_flow F, long long n, bool keep, cudaStream_t st) {
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
+}
+
+// Forward (sampling direction) from P[0] = z over n (multiple of 128) rows;
+// logq initialised to 0.  keep: layer l writes P[l+1] and keeps its
+// activations (training); otherwise P[0] is mapped in place (sampling).
+int forward_pass(mc_flow F, long long n, bool keep, cudaStream_t st) {
+  FLOW_CUDA(cudaMemsetAsync(F->logq, 0, sizeof(float) * n, st));
+  return forward_layers(F, n, keep, st);
 }
 
 // Inverse (density) pass from P[L] (the points x) down to P[0] = z, keeping
@@ -1396,6 +1433,11 @@ int refresh_bf16(mc_flow F, cudaStream_t st) {
   return MC_OK;
 }
 
+void loss_sums(mc_flow F, long long n, cudaStream_t st) {
+  mc::loss_partials_kernel<<<mc::kLossBlocks, 256, 0, st>>>(F->w, F->logq, n, F->sums + 2);
+  mc::loss_final_kernel<<<1, 32, 0, st>>>(F->sums + 2, mc::kLossBlocks, F->sums);
+}
+
 int check_err(mc_flow F, cudaStream_t st) {
   int e = 0;
   FLOW_CUDA(cudaMemcpyAsync(&e, F->err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1493,7 +1535,8 @@ int mc_flow_free(mc_flow F) {
   for (void* p : {(void*)F->d_params, (void*)F->d_grads, (void*)F->d_m, (void*)F->d_v, (void*)F->d_wbf,
                   (void*)F->d_layers, (void*)F->P, (void*)F->logq, (void*)F->f, (void*)F->w, (void*)F->dP,
                   (void*)F->LT, (void*)F->h, (void*)F->hT, (void*)F->G, (void*)F->GT, (void*)F->dA, (void*)F->dAT,
-                  (void*)F->part, (void*)F->UT, (void*)F->MB, (void*)F->dU, (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
+                  (void*)F->part, (void*)F->UT, (void*)F->MB, (void*)F->dU, (void*)F->Ps, (void*)F->lqs,
+                  (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
                   (void*)F->err})
     cudaFree(p);
   if (F->h_sums) cudaFreeHost(F->h_sums);
@@ -1573,10 +1616,13 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->UT, sizeof(__nv_bfloat16) * L * mc::kUPad * bp);
   alloc((void**)&F->MB, sizeof(uint32_t) * L * 3 * bp * 8);
   alloc((void**)&F->dU, sizeof(float) * bp * mc::kUPad);
-  alloc((void**)&F->sums, sizeof(double) * 2);
+  alloc((void**)&F->sums, sizeof(double) * (2 + 2 * mc::kLossBlocks));
   alloc((void**)&F->parts, sizeof(BlockPartial) * kPartsGrid);
   alloc((void**)&F->total, sizeof(BlockPartial));
   alloc((void**)&F->err, sizeof(int));
+  F->sbp = std::max<long long>(F->bp, 1 << 20);
+  alloc((void**)&F->Ps, sizeof(float) * size_t(F->sbp) * D);
+  alloc((void**)&F->lqs, sizeof(float) * size_t(F->sbp));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_sums, sizeof(double) * 2);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_total, sizeof(BlockPartial));
   if (e != cudaSuccess) {
@@ -1684,7 +1730,7 @@ int mc_flow_loss_grad(mc_flow F, int64_t n, const float* x, const float* w, doub
   FLOW_CUDA(cudaMemcpyAsync(F->w, w, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
   mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
   if (int rc = inverse_pass(F, np, st)) return rc;
-  mc::loss_sums_kernel<<<1, 1024, 0, st>>>(F->w, F->logq, n, F->sums);
+  loss_sums(F, n, st);
   if (int rc = backward_pass(F, np, n, st)) return rc;
   FLOW_CUDA(cudaMemcpyAsync(F->h_sums, F->sums, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
   if (int rc = check_err(F, st)) return rc;
@@ -1722,9 +1768,9 @@ int mc_flow_adam_step(mc_flow F, double lr, void* stream) {
   mc::AdamArgs A{float(lr), float(b1), float(b2), 1e-8f, float(1.0 / (1.0 - std::pow(b1, F->step))),
                  float(1.0 / (1.0 - std::pow(b2, F->step)))};
   mc::adam_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_params, F->d_grads, F->d_m, F->d_v, F->nparam,
-                                                                   F->d_layers, F->L, A);
+                                                                   F->d_layers, F->L, A);  // refreshes the BF16 copies
   FLOW_CUDA(cudaGetLastError());
-  return refresh_bf16(F, st);
+  return MC_OK;
 }
 
 int mc_flow_train(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int steps, int64_t batch, double lr, void* stream,
@@ -1743,7 +1789,7 @@ int mc_flow_train(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int steps, int
     if (int rc = eval_points(F, itg, pdf, P_of(F, F->L), n, F->f, st)) return rc;
     FLOW_CUDA(cudaMemsetAsync(F->w, 0, sizeof(float) * np, st));
     mc::flow_weights_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->f, F->logq, F->w, n);
-    mc::loss_sums_kernel<<<1, 1024, 0, st>>>(F->w, F->logq, n, F->sums);
+    loss_sums(F, n, st);
     // the forward activations are those of the density pass at x: backward, Adam
     mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
     if (int rc = backward_pass(F, np, n, st)) return rc;
@@ -1767,8 +1813,13 @@ int mc_flow_iterate(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int64_t neve
   mc::KernelArgs a;
   if (int rc = mc::fill_process_args(itg, pdf, &a)) return rc;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const long long chunk = (F->max_batch / 128) * 128;
+  bool all_fused = F->use_fused && F->sbp > 0;
+  for (int l = 0; l < F->L; ++l) all_fused = all_fused && F->fused_ok[l];
+  // the fused layers need only the points and log q: sample in large chunks
+  const long long chunk = all_fused ? F->sbp : (F->max_batch / 128) * 128;
   if (chunk < 128) return ffail(MC_EINVAL, "mc_flow_iterate: max_batch below 128");
+  float* Z = all_fused ? F->Ps : P_of(F, 0);
+  float* LQ = all_fused ? F->lqs : F->logq;
   const long long nchunks = (nevents + chunk - 1) / chunk;
   if (nchunks > F->max_chunks) {  // grow-only per-chunk totals
     FLOW_CUDA(cudaStreamSynchronize(st));
@@ -1778,15 +1829,15 @@ int mc_flow_iterate(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int64_t neve
     FLOW_CUDA(cudaMalloc((void**)&F->chunk_totals, sizeof(BlockPartial) * nchunks));
     F->max_chunks = nchunks;
   }
-  float* Z = P_of(F, 0);
   for (long long c = 0; c < nchunks; ++c) {
     const long long first = c * chunk;
     const long long n = std::min<long long>(chunk, nevents - first), np = pad128(n);
     if (np != n) FLOW_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * np * F->D, st));
     mc::flow_uniforms_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(Z, n, F->D, F->seed, 0x20000u + iteration,
                                                                       first);
-    if (int rc = forward_pass(F, np, false, st)) return rc;
-    if (int rc = eval_points_sums(F, itg, a, Z, F->logq, n, st)) return rc;
+    FLOW_CUDA(cudaMemsetAsync(LQ, 0, sizeof(float) * np, st));
+    if (int rc = all_fused ? forward_layers(F, np, false, st, Z, LQ) : forward_layers(F, np, false, st)) return rc;
+    if (int rc = eval_points_sums(F, itg, a, Z, LQ, n, st)) return rc;
     FLOW_CUDA(mc::launch_finalize(F->parts, kPartsGrid, F->chunk_totals + c, st));
   }
   FLOW_CUDA(mc::launch_finalize(F->chunk_totals, int(nchunks), F->total, st));
