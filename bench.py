@@ -11,7 +11,9 @@ The line also carries "time_to_target": the GPU time to a 1e-3 relative
 error on gg -> t tbar g in 7 sampled dimensions for plain FP64 VEGAS, FP32
 VEGAS and FP32 + normalizing-flow sampling (200 online training steps
 included), each run from scratch, with the variance per event and the
-unweighting efficiency of each.
+unweighting efficiency of each; and "batch16": sixteen integrands of uneven
+dimension and event count in one persistent launch per iteration (CUDA
+graph, autotuned shape) against the sum of their single launches.
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a
 bounded sample of events per step on the host cores).
@@ -180,6 +182,70 @@ def _iter_stats(r):
     mean = r.sum / r.n
     var = max(r.sum2 / r.n - mean * mean, 0.0) / (r.n - 1)
     return mean, var
+
+
+def batch16(M, pdf, stream, iterations=10):
+    """Sixteen integrands of uneven dimension and event count in one
+    persistent launch per iteration, captured in a CUDA graph (autotuned
+    block size and events per thread), against the sum of the sixteen
+    single-integrand launches of the same events."""
+    import torch
+    itgs, counts = W.batch_configs(seed=0)
+    b = M.mc_batch_create(itgs, counts, pdf, NBINS, seed=0, prec=M.MC_FP32_KAHAN)
+    M.mc_batch_iterate(b, ALPHA, stream)  # first iteration builds the graph
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(iterations):
+        M.mc_batch_iterate(b, ALPHA, stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = t0.elapsed_time(t1) / iterations
+    shape = M.mc_batch_shape(b)
+    b.free()
+    single_ms = 0.0
+    for i, (itg, n) in enumerate(zip(itgs, counts)):
+        v = M.mc_vegas_init(itg.ndim(), NBINS, 0, M.MC_FP32_KAHAN)
+        M.mc_vegas_set_gid(v, i)
+        M.mc_vegas_iterate(v, itg, pdf, n, stream)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(iterations):
+            M.mc_vegas_iterate(v, itg, pdf, n, stream)
+            M.mc_vegas_refine(v, ALPHA, stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        single_ms += s0.elapsed_time(s1) / iterations
+        v.free()
+    total = int(sum(counts))
+    return {"integrands": len(itgs), "events_per_iteration": total, "ms_per_iteration": batch_ms,
+            "events_per_s": total / (batch_ms / 1e3), "single_launches_ms_per_iteration": single_ms,
+            "speedup_vs_single_launches": single_ms / batch_ms, "autotuned": shape}
+
+
+def profile_case(case):
+    """A small fixed workload for ncu captures (no timing output)."""
+    import torch
+    from paper_2302_03343_b300 import build
+    from paper_2302_03343_b300 import mcint as M
+    build.build()
+    pdf = M.mc_pdf_load(W.synthetic_pdf_grid(0))
+    if case == "integrand":
+        v = M.mc_vegas_init(14, NBINS, 0, M.MC_FP32_KAHAN)
+        for _ in range(3):
+            M.mc_vegas_iterate(v, W.gg_ttbarg(), pdf, 1 << 20)
+            M.mc_vegas_refine(v, ALPHA)
+    else:  # flow: two training steps of 65536 events, one sampling pass of 2^20 events
+        itg = W.gg_ttbarg_7d()
+        f = M.mc_flow_create(7, FLOW_LAYERS, FLOW_BINS, W.flow_init_params(7, FLOW_LAYERS, FLOW_BINS, seed=0),
+                             FLOW_BATCH, seed=1)
+        M.mc_flow_train(f, itg, pdf, 2, FLOW_BATCH, FLOW_LR, losses=False)
+        M.mc_flow_iterate(f, itg, pdf, 1 << 20, iteration=0)
+    torch.cuda.synchronize()
+    print("profile case done:", case)
 
 
 def time_to_target(M, pdf, stream, seed=0):
@@ -362,6 +428,7 @@ def run_native(args, rank, world):
                                if r_last.wmax > 0 else None}}
     if not args.no_time_to_target:
         line["time_to_target"] = time_to_target(M, pdf, stream)
+        line["batch16"] = batch16(M, pdf, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -376,7 +443,12 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-target", action="store_true")
+    ap.add_argument("--profile-case", choices=["integrand", "flow"], default=None,
+                    help="run a small fixed workload for profiling and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
