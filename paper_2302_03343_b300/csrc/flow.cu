@@ -135,15 +135,15 @@ __global__ void __launch_bounds__(128) spline_fwd_kernel(const float* Pin, float
   if (Pout != Pin)
     for (int a = 0; a < L.na; ++a) Pout[i * D + L.a_idx[a]] = Pin[i * D + L.a_idx[a]];
   Spline s;
-  float ld[2] = {0.0f, 0.0f};  // even and odd coordinates summed apart, as in the fused layer
+  float ld = 0.0f;  // summed over the coordinates in order, as in the fused layer
   for (int j = 0; j < L.nb; ++j) {
     spline_load(LT + size_t(j) * L.ls * ldn + i, ldn, K, s);
     float lc;
     const int d = L.b_idx[j];
     Pout[i * D + d] = spline_fwd(s, K, Pin[i * D + d], &lc);
-    ld[j & 1] += lc;
+    ld += lc;
   }
-  logq[i] -= ld[0] + ld[1];
+  logq[i] -= ld;
 }
 
 // Inverse spline of one layer: Pout = Pin with the transformed coordinates
@@ -486,17 +486,20 @@ __global__ void to_bf16_kernel(const float* W, int rows, int cols, __nv_bfloat16
 
 
 // ---------------------------------------------------------------------------
-// Fused coupling layer (sampling direction, K = 32 bins): one persistent
-// kernel per layer.  For each tile of 128 events the conditioner runs without
-// leaving the SM: dense1 on the CUDA cores writes h1 (BF16) into a shared-
-// memory operand buffer in the 128-byte-swizzled K-major layout the tensor
-// cores read; three tcgen05 products (W2, W3, W4 streamed from L2 through a
-// TMA ring) each land in TMEM, and the compute warps turn the accumulator
-// into the next operand (bias, ReLU, BF16) in the same buffer; the logits of
-// the last product are read straight from TMEM by the spline.  Warp 0 streams
-// the weights, warp 1 issues the MMAs, warps 2-9 compute (warp w owns TMEM
-// lanes 32 (w % 4).., i.e. a quarter of the tile's events, and half of the
-// columns or of the transformed coordinates).
+// Fused coupling layer (K = 32 bins): one persistent kernel per layer with
+// two 128-event tiles in flight per SM.  For each tile the conditioner runs
+// without leaving the SM: dense1 on the CUDA cores writes h1 (BF16) into the
+// tile's shared-memory operand buffer in the 128-byte-swizzled K-major layout
+// the tensor cores read; three tcgen05 products (W2, W3, then W4 in
+// two-coordinate sub-blocks) stream the weights from L2 through a TMA ring
+// into the tile's 256 TMEM columns, and the tile's compute warps turn each
+// accumulator into the next operand (bias, ReLU, BF16) in the same buffer or
+// feed the logits straight from TMEM to the spline.  Warp 0 streams the
+// weights, warp 1 issues the MMAs, alternating between the two tiles so that
+// one tile's products overlap the other's CUDA-core phases; warps 2-5 and
+// 6-9 are the two tiles' compute groups (warp w owns TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31: one event per thread, all of its columns).
+// KEEP (training) also writes the activations the backward needs.
 constexpr int kFusedK = 32;                       // bins
 constexpr int kFusedLs = 80;                      // logit stride: 2K+1 rounded up to 16 columns
 constexpr int kFusedThreads = 320;
@@ -511,7 +514,6 @@ struct FusedLayerArgs {
   LayerDev L;
   int D;
   long long n;     // multiple of 128
-  int n_sub4;      // W4 products per K step (N split into n_sub4 MMAs of nout_pad / n_sub4)
   int* error;
   // training: the activations the backward needs, transposed [feature][n]
   // (all null when sampling): h1, h2, h3 (BF16), the first-layer inputs
@@ -528,9 +530,10 @@ __device__ __forceinline__ uint32_t swz_off(int r, int u) {
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // KEEP: training (writes the activations for the backward); otherwise sampling.
+constexpr int kFusedSubRows = 2 * kFusedLs;  // W4 rows of one two-coordinate sub-product
+
 template <bool KEEP>
 __global__ void __launch_bounds__(kFusedThreads, 1)
     flow_layer_fused_kernel(const __grid_constant__ CUtensorMap map_w2, const __grid_constant__ CUtensorMap map_w3,
@@ -540,35 +543,30 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   constexpr int kMaxStages = 4;
   __shared__ __align__(8) uint64_t w_full[kMaxStages];
   __shared__ __align__(8) uint64_t w_empty[kMaxStages];
-  __shared__ __align__(8) uint64_t a_ready, acc_full, fin_bar;
+  __shared__ __align__(8) uint64_t a_ready[2], acc_full[2], fin_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int failed;
-  __shared__ float s_w1[kH * kMaxA], s_b1[kH], s_b2[kH], s_b3[kH], s_b4[512];
-  __shared__ float s_ld[2][128];
 
   const LayerDev& L = g.L;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nout = L.nout_pad;
-  const uint32_t stage_bytes = uint32_t(max(kH, nout)) * 128u;
-  unsigned char* abuf = smem;
-  unsigned char* ring = smem + kFusedABytes;
+  const int nsub = (L.nb + 1) / 2;  // W4 sub-products, two coordinates each
+  const int nphase = 2 + nsub;
+  const uint32_t stage_bytes = uint32_t(kH) * 128u;
+  unsigned char* ring = smem + 2 * kFusedABytes;
   const int m_tiles = int(g.n / 128);
   const int my_tiles = int(blockIdx.x) < m_tiles ? (m_tiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  auto sub_rows = [&](int k) { return k == nsub - 1 ? nout - kFusedSubRows * k : kFusedSubRows; };
 
-  for (int t = threadIdx.x; t < kH * L.na; t += blockDim.x) s_w1[t] = g.params[L.off_W1 + t];
-  for (int t = threadIdx.x; t < kH; t += blockDim.x) {
-    s_b1[t] = g.params[L.off_b1 + t];
-    s_b2[t] = g.params[L.off_b2 + t];
-    s_b3[t] = g.params[L.off_b3 + t];
-  }
-  for (int t = threadIdx.x; t < nout; t += blockDim.x) s_b4[t] = g.params[L.off_b4 + t];
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(&w_full[s], 1);
       mbar_init(&w_empty[s], 1);
     }
-    mbar_init(&a_ready, kFusedCompute);
-    mbar_init(&acc_full, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&a_ready[s], kFusedCompute / 2);
+      mbar_init(&acc_full[s], 1);
+    }
     mbar_init(&fin_bar, 1);
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -584,74 +582,69 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0) {
-    // weight stream: per tile W2, W3, W4, four 64-wide K chunks each
+    // weight stream, in the MMA order: per pair of tiles, phase by phase,
+    // tile 0 then tile 1; four 64-wide K chunks per product
     if (lane == 0 && my_tiles > 0) {
-      const int sub4 = nout / g.n_sub4;
       int it = 0;
-      for (int i = 0; i < my_tiles && !failed; ++i) {
-        for (int q = 0; q < 12 && !failed; ++q, ++it) {
-          const int s = it % stages;
-          const uint32_t use = uint32_t(it / stages);
-          if (use > 0 && !mbar_wait(&w_empty[s], (use - 1) & 1u)) {
-            failed = 1;
-            atomicExch(g.error, 21);
-            break;
+      for (int j = 0; 2 * j < my_tiles && !failed; ++j)
+        for (int p = 0; p < nphase && !failed; ++p)
+          for (int s = 0; s < 2 && !failed; ++s) {
+            if (2 * j + s >= my_tiles) continue;
+            for (int c = 0; c < 4; ++c, ++it) {
+              const int st = it % stages;
+              const uint32_t use = uint32_t(it / stages);
+              if (use > 0 && !mbar_wait(&w_empty[st], (use - 1) & 1u)) {
+                failed = 1;
+                atomicExch(g.error, 21);
+                break;
+              }
+              unsigned char* dst = ring + size_t(st) * stage_bytes;
+              if (p < 2) {
+                mbar_expect_tx(&w_full[st], stage_bytes);
+                tma_load_2d(dst, p == 0 ? &map_w2 : &map_w3, c * 64, 0, &w_full[st]);
+              } else {
+                const int k = p - 2, rows = sub_rows(k);
+                mbar_expect_tx(&w_full[st], uint32_t(rows) * 128u);
+                for (int b = 0; b < rows / 32; ++b)
+                  tma_load_2d(dst + size_t(b) * 32 * 128, &map_w4, c * 64, kFusedSubRows * k + 32 * b, &w_full[st]);
+              }
+            }
           }
-          const int m = q >> 2, c = q & 3;
-          unsigned char* dst = ring + size_t(s) * stage_bytes;
-          if (m < 2) {
-            mbar_expect_tx(&w_full[s], uint32_t(kH) * 128u);
-            tma_load_2d(dst, m == 0 ? &map_w2 : &map_w3, c * 64, 0, &w_full[s]);
-          } else {
-            mbar_expect_tx(&w_full[s], uint32_t(nout) * 128u);
-            for (int sb = 0; sb < g.n_sub4; ++sb)
-              tma_load_2d(dst + size_t(sb) * sub4 * 128, &map_w4, c * 64, sb * sub4, &w_full[s]);
-          }
-        }
-      }
-      // every copy issued lands before the CTA may exit
-      for (int s = 0; s < stages && s < it; ++s) mbar_wait(&w_full[s], uint32_t((it - 1 - s) / stages) & 1u);
+      for (int st = 0; st < stages && st < it; ++st) mbar_wait(&w_full[st], uint32_t((it - 1 - st) / stages) & 1u);
     }
   } else if (warp == 1) {
     if (lane == 0 && my_tiles > 0) {
-      const uint32_t idesc_h = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kH >> 3) << 17) | (8u << 24);
-      const int sub4 = nout / g.n_sub4;
-      const uint32_t idesc_o = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(sub4 >> 3) << 17) | (8u << 24);
-      int it = 0, use_a = 0;
+      int it = 0, use_a[2] = {0, 0};
       bool ok = true;
-      for (int i = 0; i < my_tiles && ok; ++i) {
-        for (int m = 0; m < 3 && ok; ++m, ++use_a) {
-          if (!mbar_wait(&a_ready, uint32_t(use_a) & 1u) || failed) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          for (int c = 0; c < 4; ++c, ++it) {
-            const int s = it % stages;
-            if (!mbar_wait(&w_full[s], uint32_t(it / stages) & 1u)) {
+      for (int j = 0; 2 * j < my_tiles && ok; ++j)
+        for (int p = 0; p < nphase && ok; ++p)
+          for (int s = 0; s < 2 && ok; ++s) {
+            if (2 * j + s >= my_tiles) continue;
+            if (!mbar_wait(&a_ready[s], uint32_t(use_a[s]++) & 1u) || failed) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint64_t ad = smem_desc(smem_u32(abuf + c * 16384));
-            const uint32_t bbase = smem_u32(ring + size_t(s) * stage_bytes);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const uint32_t acc = (c > 0 || k > 0) ? 1u : 0u;
-              if (m < 2) {
-                mma_bf16(tmem, ad + uint64_t(k * 2), smem_desc(bbase) + uint64_t(k * 2), idesc_h, acc);
-              } else {
-                for (int sb = 0; sb < g.n_sub4; ++sb)
-                  mma_bf16(tmem + uint32_t(sb * sub4), ad + uint64_t(k * 2),
-                           smem_desc(bbase + uint32_t(sb * sub4 * 128)) + uint64_t(k * 2), idesc_o, acc);
+            const int nn = p < 2 ? kH : sub_rows(p - 2);
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(nn >> 3) << 17) | (8u << 24);
+            const uint32_t d = tmem + uint32_t(s) * kH;
+            for (int c = 0; c < 4; ++c, ++it) {
+              const int st = it % stages;
+              if (!mbar_wait(&w_full[st], uint32_t(it / stages) & 1u)) {
+                ok = false;
+                break;
               }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              const uint64_t ad = smem_desc(smem_u32(smem + size_t(s) * kFusedABytes + c * 16384));
+              const uint64_t bd = smem_desc(smem_u32(ring + size_t(st) * stage_bytes));
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                mma_bf16(d, ad + uint64_t(k * 2), bd + uint64_t(k * 2), idesc, (c > 0 || k > 0) ? 1u : 0u);
+              mma_commit(&w_empty[st]);
             }
-            mma_commit(&w_empty[s]);
+            if (!ok) break;
+            mma_commit(&acc_full[s]);
           }
-          if (!ok) break;
-          mma_commit(&acc_full);
-        }
-      }
       if (!ok) {
         failed = 1;
         atomicExch(g.error, 22);
@@ -660,31 +653,33 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
       mbar_wait(&fin_bar, 0);
     }
   } else {
-    const int q = warp & 3, half = (warp - 2) >> 2;
+    const int slot = (warp - 2) >> 2, q = warp & 3;
     const int r = q * 32 + lane;  // event row in the tile (= TMEM lane)
-    const uint32_t trow = tmem + (uint32_t(q * 32) << 16);
+    const uint32_t trow = tmem + (uint32_t(q * 32) << 16) + uint32_t(slot) * kH;
+    unsigned char* abuf = smem + size_t(slot) * kFusedABytes;
+    const float* prm = g.params;
     int use_acc = 0;
-    // Every compute thread passes the two named barriers of every tile, also
-    // after a failure (the work is then skipped), so none can wait forever.
-    for (int i = 0; i < my_tiles; ++i) {
+    for (int i = slot; i < my_tiles; i += 2) {
       const long long ev = (long long)(int(blockIdx.x) + i * int(gridDim.x)) * 128 + r;
       const float* Pe = g.P + ev * g.D;
       float* Po = g.Pout + ev * g.D;
-      bool ok = !__any_sync(0xffffffffu, failed != 0);
-      if (ok) {
-        // dense1: h1 for units [128 half, 128 half + 128) of this event
+      if (__any_sync(0xffffffffu, failed != 0)) break;
+      // dense1: h1 = relu(W1 u + b1) for the 256 units of this event
+      {
         float u[kMaxA];
 #pragma unroll
         for (int a = 0; a < kMaxA; ++a) u[a] = a < L.na ? 2.0f * Pe[L.a_idx[a]] - 1.0f : 0.0f;
-        uint32_t wb[4] = {0u, 0u, 0u, 0u};  // ReLU activity of this thread's 128 units
-        if (KEEP && half == 0) {
+        if (KEEP) {
           for (int a = 0; a < L.na; ++a) {
             g.UT[size_t(a) * g.n + ev] = __float2bfloat16_rn(u[a]);
-            if (Po != Pe) Po[L.a_idx[a]] = Pe[L.a_idx[a]];
+            Po[L.a_idx[a]] = Pe[L.a_idx[a]];
           }
           g.UT[size_t(L.na) * g.n + ev] = __float2bfloat16_rn(1.0f);
         }
-        for (int u16 = half * 16; u16 < half * 16 + 16; ++u16) {
+        uint32_t wb[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};  // ReLU activity of the 256 units
+        const float* W1 = prm + L.off_W1;
+        const float* b1 = prm + L.off_b1;
+        for (int u16 = 0; u16 < 32; ++u16) {
           uint4 pk;
           uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
 #pragma unroll
@@ -693,93 +688,105 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
               const int j = u16 * 8 + 2 * e + h2;
-              float acc = s_b1[j];
+              float acc = __ldg(b1 + j);
 #pragma unroll
               for (int a = 0; a < kMaxA; ++a)
-                if (a < L.na) acc += s_w1[j * L.na + a] * u[a];
+                if (a < L.na) acc += __ldg(W1 + j * L.na + a) * u[a];
               o[h2] = fmaxf(acc, 0.0f);
             }
             const __nv_bfloat162 hh = __floats2bfloat162_rn(o[0], o[1]);
             pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
             if (KEEP) {
-              const int jl = (u16 - half * 16) * 8 + 2 * e;  // unit within this thread's 128
+              const int jl = u16 * 8 + 2 * e;
               wb[jl >> 5] |= (uint32_t(__bfloat162float(hh.x) > 0.0f) << (jl & 31)) |
                              (uint32_t(__bfloat162float(hh.y) > 0.0f) << ((jl + 1) & 31));
-              g.hT1[size_t(u16 * 8 + 2 * e) * g.n + ev] = hh.x;
-              g.hT1[size_t(u16 * 8 + 2 * e + 1) * g.n + ev] = hh.y;
+              g.hT1[size_t(jl) * g.n + ev] = hh.x;
+              g.hT1[size_t(jl + 1) * g.n + ev] = hh.y;
             }
           }
           *reinterpret_cast<uint4*>(abuf + swz_off(r, u16)) = pk;
         }
-        if (KEEP) reinterpret_cast<uint4*>(g.bits + size_t(ev) * 8)[half] = make_uint4(wb[0], wb[1], wb[2], wb[3]);
-        fence_async_smem();
-        mbar_arrive(&a_ready);
-        // two hidden products: accumulator -> bias, ReLU, BF16 -> operand buffer
-        for (int m = 0; m < 2 && ok; ++m, ++use_acc) {
-          if (!__all_sync(0xffffffffu, mbar_wait(&acc_full, uint32_t(use_acc) & 1u))) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const float* bias = m == 0 ? s_b2 : s_b3;
-          __nv_bfloat16* hT = m == 0 ? g.hT2 : g.hT3;
-          uint32_t mb[4] = {0u, 0u, 0u, 0u};
-          for (int cg = 0; cg < 2; ++cg) {  // 2 groups of 4 x 16 columns
-            uint32_t v[4][16];
-            const int col0 = half * 128 + cg * 64;
+        if (KEEP) {
+          uint4* bp = reinterpret_cast<uint4*>(g.bits + size_t(ev) * 8);
+          bp[0] = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+          bp[1] = make_uint4(wb[4], wb[5], wb[6], wb[7]);
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(&a_ready[slot]);
+      // two hidden products: accumulator -> bias, ReLU, BF16 -> operand buffer
+      bool ok = true;
+      for (int m = 0; m < 2 && ok; ++m, ++use_acc) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[slot], uint32_t(use_acc) & 1u))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const float* bias = prm + (m == 0 ? L.off_b2 : L.off_b3);
+        __nv_bfloat16* hT = m == 0 ? g.hT2 : g.hT3;
+        uint32_t mb[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        for (int cg = 0; cg < 4; ++cg) {  // 4 groups of 4 x 16 columns
+          uint32_t v[4][16];
+          const int col0 = cg * 64;
 #pragma unroll
-            for (int x = 0; x < 4; ++x) tmem_ld16_nw(trow + uint32_t(col0 + 16 * x), v[x]);
-            tmem_wait_ld();
+          for (int x = 0; x < 4; ++x) tmem_ld16_nw(trow + uint32_t(col0 + 16 * x), v[x]);
+          tmem_wait_ld();
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
+          for (int x = 0; x < 4; ++x) {
 #pragma unroll
-              for (int hlf = 0; hlf < 2; ++hlf) {
-                uint4 pk;
-                uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+            for (int hlf = 0; hlf < 2; ++hlf) {
+              uint4 pk;
+              uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  const int cc = col0 + 16 * x + 8 * hlf + 2 * e;
-                  const float o0 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e]) + bias[cc], 0.0f);
-                  const float o1 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e + 1]) + bias[cc + 1], 0.0f);
-                  const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
-                  pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
-                  if (KEEP) {
-                    const int jl = cc - half * 128;
-                    mb[jl >> 5] |= (uint32_t(__bfloat162float(hh.x) > 0.0f) << (jl & 31)) |
-                                   (uint32_t(__bfloat162float(hh.y) > 0.0f) << ((jl + 1) & 31));
-                    hT[size_t(cc) * g.n + ev] = hh.x;
-                    hT[size_t(cc + 1) * g.n + ev] = hh.y;
-                  }
+              for (int e = 0; e < 4; ++e) {
+                const int cc = col0 + 16 * x + 8 * hlf + 2 * e;
+                const float o0 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e]) + __ldg(bias + cc), 0.0f);
+                const float o1 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e + 1]) + __ldg(bias + cc + 1), 0.0f);
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
+                pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                if (KEEP) {
+                  mb[cc >> 5] |= (uint32_t(__bfloat162float(hh.x) > 0.0f) << (cc & 31)) |
+                                 (uint32_t(__bfloat162float(hh.y) > 0.0f) << ((cc + 1) & 31));
+                  hT[size_t(cc) * g.n + ev] = hh.x;
+                  hT[size_t(cc + 1) * g.n + ev] = hh.y;
                 }
-                *reinterpret_cast<uint4*>(abuf + swz_off(r, (col0 + 16 * x + 8 * hlf) >> 3)) = pk;
               }
+              *reinterpret_cast<uint4*>(abuf + swz_off(r, (col0 + 16 * x + 8 * hlf) >> 3)) = pk;
             }
           }
-          if (KEEP)
-            reinterpret_cast<uint4*>(g.bits + (size_t(m + 1) * g.n + ev) * 8)[half] =
-                make_uint4(mb[0], mb[1], mb[2], mb[3]);
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          fence_async_smem();
-          mbar_arrive(&a_ready);
         }
-        if (ok && !__all_sync(0xffffffffu, mbar_wait(&acc_full, uint32_t(use_acc) & 1u))) ok = false;
-        ++use_acc;
+        if (KEEP) {
+          uint4* bp = reinterpret_cast<uint4*>(g.bits + (size_t(m + 1) * g.n + ev) * 8);
+          bp[0] = make_uint4(mb[0], mb[1], mb[2], mb[3]);
+          bp[1] = make_uint4(mb[4], mb[5], mb[6], mb[7]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        fence_async_smem();
+        mbar_arrive(&a_ready[slot]);
       }
+      // W4 sub-products: the logits of two coordinates at a time, straight
+      // from TMEM into the spline (coordinates in order, log c summed in order)
       float ld = 0.0f;
-      if (ok) {
+      for (int k = 0; k < nsub && ok; ++k, ++use_acc) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[slot], uint32_t(use_acc) & 1u))) {
+          ok = false;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // splines of this half's transformed coordinates from the logits in TMEM
-        for (int j = half; j < L.nb; j += 2) {
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = 2 * k + jj;
+          if (j >= L.nb) break;
           float lg[kFusedLs];
 #pragma unroll
           for (int x = 0; x < kFusedLs / 16; ++x)
-            tmem_ld16_nw(trow + uint32_t(j * kFusedLs + 16 * x), reinterpret_cast<uint32_t*>(lg + 16 * x));
+            tmem_ld16_nw(trow + uint32_t(jj * kFusedLs + 16 * x), reinterpret_cast<uint32_t*>(lg + 16 * x));
           tmem_wait_ld();
+          const float* b4 = prm + L.off_b4 + j * kFusedLs;
 #pragma unroll
-          for (int k = 0; k < kFusedLs; ++k) lg[k] += s_b4[j * kFusedLs + k];
+          for (int kk = 0; kk < kFusedLs; ++kk) lg[kk] += __ldg(b4 + kk);
           if (KEEP) {
 #pragma unroll
-            for (int k = 0; k < 2 * kFusedK + 1; ++k) g.LT[size_t(j * kFusedLs + k) * g.n + ev] = lg[k];
+            for (int kk = 0; kk < 2 * kFusedK + 1; ++kk) g.LT[size_t(j * kFusedLs + kk) * g.n + ev] = lg[kk];
           }
           Spline sp;
           spline_load_regs<kFusedK>(lg, sp);
@@ -789,14 +796,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           ld += lc;
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
-      } else {
+        if (k + 1 < nsub) mbar_arrive(&a_ready[slot]);  // the accumulator is free for the next sub-product
+      }
+      if (!ok) {
         failed = 1;
         if (lane == 0) atomicExch(g.error, 23);
+        break;
       }
-      s_ld[half][r] = ld;
-      compute_bar();
-      if (half == 0 && ok) g.logq[ev] -= s_ld[0][r] + s_ld[1][r];
-      compute_bar();
+      g.logq[ev] -= ld;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1111,7 +1118,6 @@ struct mc_flow_s {
   bool use_fused = true;      // fused forward layers
   bool use_fused_bwd = true;  // fused backward layers
   std::vector<bool> fused_ok;
-  std::vector<int> n_sub4;
   std::vector<CUtensorMap> maps;
   std::vector<CUtensorMap> bwd_maps;  // W4^T, W3^T, W2^T, W1^T per layer (fused backward)
 };
@@ -1259,13 +1265,12 @@ int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st, float
   a.L = L;
   a.D = F->D;
   a.n = n;
-  a.n_sub4 = F->n_sub4[l];
   a.error = F->err;
-  constexpr size_t kMaxDyn = 232448 - 16384;  // opt-in limit less the kernel's static shared memory
-  const size_t stage = size_t(std::max(kH, L.nout_pad)) * 128;
-  const int stages = int(std::min<size_t>(4, (kMaxDyn - 1024 - mc::kFusedABytes) / stage));
+  constexpr size_t kMaxDyn = 232448 - 1024;  // opt-in limit less the kernel's static shared memory
+  const size_t stage = size_t(kH) * 128;
+  const int stages = int(std::min<size_t>(4, (kMaxDyn - 1024 - 2 * mc::kFusedABytes) / stage));
   if (stages < 2) return ffail(MC_EINVAL, "mc_flow: fused layer does not fit in shared memory");
-  const size_t smem = 1024 + mc::kFusedABytes + stages * stage;
+  const size_t smem = 1024 + 2 * mc::kFusedABytes + stages * stage;
   auto kern = keep ? mc::flow_layer_fused_kernel<true> : mc::flow_layer_fused_kernel<false>;
   FLOW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const int grid = int(std::min<long long>(n / 128, num_sms));
@@ -1645,19 +1650,17 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   F->bwd_maps.resize(4 * L);
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& Ld = F->layers[l];
-    const int n_sub4 = (Ld.nout_pad + 255) / 256;
-    const int sub4 = Ld.nout_pad / n_sub4;
-    bool ok = F->K == mc::kFusedK && ls == mc::kFusedLs && Ld.nout_pad <= 512 && Ld.nout_pad % n_sub4 == 0 &&
-              sub4 % 16 == 0;
+    // fused layers: 32 bins (logit stride 80), at most 6 transformed
+    // coordinates (W4 sub-products of at most 256 rows)
+    bool ok = F->K == mc::kFusedK && ls == mc::kFusedLs && Ld.nb <= 6 && Ld.nout_pad <= 512;
     ok = ok && mc::tc_make_map(&F->maps[3 * l], Ld.W2h, kH, kH, kH, kH) &&
          mc::tc_make_map(&F->maps[3 * l + 1], Ld.W3h, kH, kH, kH, kH) &&
-         mc::tc_make_map(&F->maps[3 * l + 2], Ld.W4h, Ld.nout_pad, kH, kH, sub4) &&
+         mc::tc_make_map(&F->maps[3 * l + 2], Ld.W4h, Ld.nout_pad, kH, kH, 32) &&
          mc::tc_make_map(&F->bwd_maps[4 * l], Ld.W4t, kH, Ld.nout_pad, Ld.nout_pad, kH) &&
          mc::tc_make_map(&F->bwd_maps[4 * l + 1], Ld.W3t, kH, kH, kH, kH) &&
          mc::tc_make_map(&F->bwd_maps[4 * l + 2], Ld.W2t, kH, kH, kH, kH) &&
          mc::tc_make_map(&F->bwd_maps[4 * l + 3], Ld.W1t, mc::kUPad, kH, kH, mc::kUPad);
     F->fused_ok.push_back(ok);
-    F->n_sub4.push_back(n_sub4);
   }
   // the padding rows of the logit gradients and of U^T are never written: zero them once
   if (cudaMemcpy(F->d_layers, F->layers.data(), sizeof(LayerDev) * L, cudaMemcpyHostToDevice) != cudaSuccess ||
