@@ -25,9 +25,10 @@ Sampling", 2019), readings listed in the design doc:
 * Loss (forward KL with importance weights, x sampled from the flow and held
   fixed): L = -sum_i w_i log q(x_i) / sum_i w_i, w_i = |f(x_i)| / q(x_i).
 
-`bf16=True` rounds what the CUDA path holds in BF16 (the weights of the
-second to fourth dense layers and the hidden activations after each ReLU) so
-the GPU can be compared with the same rounding.
+`bf16=True` rounds what the CUDA path holds in BF16 (the inputs u, the
+weights and the first layer's bias of the dense layers, and the hidden
+activations after each ReLU) so the GPU can be compared with the same
+rounding.
 """
 import math
 
@@ -104,8 +105,10 @@ def conditioner(p, xa, K, nb, bf16=False):
     """Logits [B, nb, 2K+1] of one layer from its conditioning coordinates."""
     u = 2 * xa - 1
     if bf16:
-        u = _r32(u)
-        h = _r16(torch.relu(u @ _r32(p["W1"]).T + _r32(p["b1"])))
+        # every dense layer on BF16 operands (the first layer's bias enters
+        # as a BF16 weight on a constant input 1), FP32 accumulation
+        u = _r16(_r32(u))
+        h = _r16(torch.relu(u @ _r16(p["W1"]).T + _r16(p["b1"])))
         h = _r16(torch.relu(h @ _r16(p["W2"]).T + _r32(p["b2"])))
         h = _r16(torch.relu(h @ _r16(p["W3"]).T + _r32(p["b3"])))
         out = h @ _r16(p["W4"]).T + _r32(p["b4"])

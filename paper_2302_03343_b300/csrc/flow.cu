@@ -62,7 +62,11 @@ struct LayerDev {
   // their transposes [in x out] for the activation gradients; W1 transposed
   // and zero-padded to [16 x H] for the input gradient of the first layer
   __nv_bfloat16 *W2h, *W3h, *W4h, *W2t, *W3t, *W4t, *W1t;
+  // first layer as a tensor-core product: W1e [H x 64] = (W1 | b1 | 0), so
+  // that h1 = relu(W1e . (u, 1, 0, ..)) with the bias on a constant input
+  __nv_bfloat16* W1e;
 };
+constexpr int kUK = 64;  // K of the first-layer product (u, 1, zero padding)
 constexpr int kUPad = 16;  // rows of U^T: u_0 .. u_{na-1}, a row of ones (bias), zeros
 
 unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
@@ -77,52 +81,25 @@ __global__ void flow_uniforms_kernel(float* z, long long n, int D, uint64_t seed
   for (int d = 0; d < D; ++d) z[i * D + d] = float(uint32_t(2 * k[d] + 1)) * 0x1p-24f;
 }
 
-// h1 = bf16(relu(W1 (2 x_A - 1) + b1)) for one event per thread: row-major
-// h1 [n][H] (16-byte stores) and, if hT, its transpose [H][n] (coalesced) and
-// the layer input U^T [16][n] (u_a, then a row of ones) for the weight
-// gradient of W1 and b1.
-__global__ void __launch_bounds__(128) dense1_kernel(const float* P, int D, const LayerDev L, const float* params,
-                                                     __nv_bfloat16* h1, __nv_bfloat16* hT, __nv_bfloat16* UT,
-                                                     long long n) {
-  __shared__ float w1[kH * kMaxA], b1[kH];
-  const int na = L.na;
-  for (int t = threadIdx.x; t < kH * na; t += blockDim.x) w1[t] = params[L.off_W1 + t];
-  for (int t = threadIdx.x; t < kH; t += blockDim.x) b1[t] = params[L.off_b1 + t];
-  __syncthreads();
+// The first-layer input of one event per thread: U [n][64] BF16 row-major
+// (u_a = 2 x_A - 1, then 1 for the bias, then zeros; the A operand of the
+// first-layer product) and, if UT, its transpose [16][n] (u_a, then the row
+// of ones: the operand of the W1 and b1 gradient).
+__global__ void __launch_bounds__(128) dense1_input_kernel(const float* P, int D, const LayerDev L, __nv_bfloat16* U,
+                                                           __nv_bfloat16* UT, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float u[kMaxA];
+  __nv_bfloat16 v[16];
 #pragma unroll
-  for (int a = 0; a < kMaxA; ++a) u[a] = a < na ? 2.0f * P[i * D + L.a_idx[a]] - 1.0f : 0.0f;
-  if (UT) {
-    for (int a = 0; a < na; ++a) UT[size_t(a) * n + i] = __float2bfloat16_rn(u[a]);
-    UT[size_t(na) * n + i] = __float2bfloat16_rn(1.0f);
+  for (int a = 0; a < 16; ++a) {
+    const float x = a < L.na ? 2.0f * P[i * D + L.a_idx[a < L.na ? a : 0]] - 1.0f : (a == L.na ? 1.0f : 0.0f);
+    v[a] = __float2bfloat16_rn(x);
+    if (UT && a <= L.na) UT[size_t(a) * n + i] = v[a];
   }
-  uint4* row = reinterpret_cast<uint4*>(h1 + size_t(i) * kH);
-  for (int j8 = 0; j8 < kH / 8; ++j8) {
-    uint4 pk;
-    uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float o[2];
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int j = j8 * 8 + 2 * q + e;
-        float acc = b1[j];
-#pragma unroll
-        for (int a = 0; a < kMaxA; ++a)
-          if (a < na) acc += w1[j * na + a] * u[a];
-        o[e] = fmaxf(acc, 0.0f);
-      }
-      const __nv_bfloat162 hh = __floats2bfloat162_rn(o[0], o[1]);
-      pw[q] = *reinterpret_cast<const uint32_t*>(&hh);
-      if (hT) {
-        hT[size_t(j8 * 8 + 2 * q) * n + i] = hh.x;
-        hT[size_t(j8 * 8 + 2 * q + 1) * n + i] = hh.y;
-      }
-    }
-    row[j8] = pk;
-  }
+  uint4* row = reinterpret_cast<uint4*>(U + size_t(i) * kUK);
+  row[0] = *reinterpret_cast<const uint4*>(v);
+  row[1] = *reinterpret_cast<const uint4*>(v + 8);
+  for (int c = 2; c < kUK / 8; ++c) row[c] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // Forward spline of one layer for one event per thread: Pout = Pin with the
@@ -447,6 +424,12 @@ __global__ void adam_kernel(float* params, const float* grads, float* m, float* 
       const size_t e = idx - L.off_W1;
       dst_t = L.W1t;
       dti = (e % L.na) * kH + e / L.na;
+      dst = L.W1e;
+      di = (e / L.na) * kUK + e % L.na;
+    }
+    if (idx >= L.off_b1 && idx < L.off_b1 + kH) {
+      dst = L.W1e;
+      di = (idx - L.off_b1) * kUK + L.na;
     }
   }
   const float g = grads[gidx];
@@ -459,6 +442,14 @@ __global__ void adam_kernel(float* params, const float* grads, float* m, float* 
   const __nv_bfloat16 h = __float2bfloat16_rn(p);
   if (dst) dst[di] = h;
   if (dst_t) dst_t[dti] = h;
+}
+
+// W1e [H][64] = (W1 | b1 | 0) in BF16 (W1 [H x na], b1 [H], FP32).
+__global__ void w1e_bf16_kernel(const float* W1, const float* b1, int na, __nv_bfloat16* W1e) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kH * kUK) return;
+  const int j = idx / kUK, c = idx % kUK;
+  W1e[idx] = __float2bfloat16_rn(c < na ? W1[size_t(j) * na + c] : (c == na ? b1[j] : 0.0f));
 }
 
 // W1t [16][H] = W1^T zero-padded (W1 [H x na], FP32).
@@ -536,8 +527,9 @@ constexpr int kFusedSubRows = 2 * kFusedLs;  // W4 rows of one two-coordinate su
 
 template <bool KEEP>
 __global__ void __launch_bounds__(kFusedThreads, 1)
-    flow_layer_fused_kernel(const __grid_constant__ CUtensorMap map_w2, const __grid_constant__ CUtensorMap map_w3,
-                            const __grid_constant__ CUtensorMap map_w4, FusedLayerArgs g, int stages) {
+    flow_layer_fused_kernel(const __grid_constant__ CUtensorMap map_w1, const __grid_constant__ CUtensorMap map_w2,
+                            const __grid_constant__ CUtensorMap map_w3, const __grid_constant__ CUtensorMap map_w4,
+                            FusedLayerArgs g, int stages) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int kMaxStages = 4;
@@ -551,7 +543,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nout = L.nout_pad;
   const int nsub = (L.nb + 1) / 2;  // W4 sub-products, two coordinates each
-  const int nphase = 2 + nsub;
+  const int nphase = 3 + nsub;  // W1e, W2, W3, then the W4 sub-products
   const uint32_t stage_bytes = uint32_t(kH) * 128u;
   unsigned char* ring = smem + 2 * kFusedABytes;
   const int m_tiles = int(g.n / 128);
@@ -590,7 +582,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         for (int p = 0; p < nphase && !failed; ++p)
           for (int s = 0; s < 2 && !failed; ++s) {
             if (2 * j + s >= my_tiles) continue;
-            for (int c = 0; c < 4; ++c, ++it) {
+            for (int c = 0; c < (p == 0 ? 1 : 4); ++c, ++it) {
               const int st = it % stages;
               const uint32_t use = uint32_t(it / stages);
               if (use > 0 && !mbar_wait(&w_empty[st], (use - 1) & 1u)) {
@@ -599,11 +591,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 break;
               }
               unsigned char* dst = ring + size_t(st) * stage_bytes;
-              if (p < 2) {
+              if (p < 3) {
                 mbar_expect_tx(&w_full[st], stage_bytes);
-                tma_load_2d(dst, p == 0 ? &map_w2 : &map_w3, c * 64, 0, &w_full[st]);
+                tma_load_2d(dst, p == 0 ? &map_w1 : (p == 1 ? &map_w2 : &map_w3), c * 64, 0, &w_full[st]);
               } else {
-                const int k = p - 2, rows = sub_rows(k);
+                const int k = p - 3, rows = sub_rows(k);
                 mbar_expect_tx(&w_full[st], uint32_t(rows) * 128u);
                 for (int b = 0; b < rows / 32; ++b)
                   tma_load_2d(dst + size_t(b) * 32 * 128, &map_w4, c * 64, kFusedSubRows * k + 32 * b, &w_full[st]);
@@ -625,10 +617,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int nn = p < 2 ? kH : sub_rows(p - 2);
+            const int nn = p < 3 ? kH : sub_rows(p - 3);
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(nn >> 3) << 17) | (8u << 24);
             const uint32_t d = tmem + uint32_t(s) * kH;
-            for (int c = 0; c < 4; ++c, ++it) {
+            for (int c = 0; c < (p == 0 ? 1 : 4); ++c, ++it) {
               const int st = it % stages;
               if (!mbar_wait(&w_full[st], uint32_t(it / stages) & 1u)) {
                 ok = false;
@@ -664,66 +656,37 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
       const float* Pe = g.P + ev * g.D;
       float* Po = g.Pout + ev * g.D;
       if (__any_sync(0xffffffffu, failed != 0)) break;
-      // dense1: h1 = relu(W1 u + b1) for the 256 units of this event
+      // the first-layer input (u_a, 1, zeros) as the A operand of the W1e product
       {
-        float u[kMaxA];
+        __nv_bfloat16 v[16];
 #pragma unroll
-        for (int a = 0; a < kMaxA; ++a) u[a] = a < L.na ? 2.0f * Pe[L.a_idx[a]] - 1.0f : 0.0f;
-        if (KEEP) {
-          for (int a = 0; a < L.na; ++a) {
-            g.UT[size_t(a) * g.n + ev] = __float2bfloat16_rn(u[a]);
-            Po[L.a_idx[a]] = Pe[L.a_idx[a]];
-          }
-          g.UT[size_t(L.na) * g.n + ev] = __float2bfloat16_rn(1.0f);
-        }
-        uint32_t wb[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};  // ReLU activity of the 256 units
-        const float* W1 = prm + L.off_W1;
-        const float* b1 = prm + L.off_b1;
-        for (int u16 = 0; u16 < 32; ++u16) {
-          uint4 pk;
-          uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float o[2];
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-              const int j = u16 * 8 + 2 * e + h2;
-              float acc = __ldg(b1 + j);
-#pragma unroll
-              for (int a = 0; a < kMaxA; ++a)
-                if (a < L.na) acc += __ldg(W1 + j * L.na + a) * u[a];
-              o[h2] = fmaxf(acc, 0.0f);
-            }
-            const __nv_bfloat162 hh = __floats2bfloat162_rn(o[0], o[1]);
-            pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
-            if (KEEP) {
-              const int jl = u16 * 8 + 2 * e;
-              wb[jl >> 5] |= (uint32_t(__bfloat162float(hh.x) > 0.0f) << (jl & 31)) |
-                             (uint32_t(__bfloat162float(hh.y) > 0.0f) << ((jl + 1) & 31));
-              g.hT1[size_t(jl) * g.n + ev] = hh.x;
-              g.hT1[size_t(jl + 1) * g.n + ev] = hh.y;
-            }
-          }
-          *reinterpret_cast<uint4*>(abuf + swz_off(r, u16)) = pk;
+        for (int a = 0; a < 16; ++a) {
+          const float x = a < L.na ? 2.0f * Pe[L.a_idx[a < L.na ? a : 0]] - 1.0f : (a == L.na ? 1.0f : 0.0f);
+          v[a] = __float2bfloat16_rn(x);
         }
         if (KEEP) {
-          uint4* bp = reinterpret_cast<uint4*>(g.bits + size_t(ev) * 8);
-          bp[0] = make_uint4(wb[0], wb[1], wb[2], wb[3]);
-          bp[1] = make_uint4(wb[4], wb[5], wb[6], wb[7]);
+          for (int a = 0; a < L.na; ++a) Po[L.a_idx[a]] = Pe[L.a_idx[a]];
+#pragma unroll
+          for (int a = 0; a < 16; ++a)
+            if (a <= L.na) g.UT[size_t(a) * g.n + ev] = v[a];
         }
+        *reinterpret_cast<uint4*>(abuf + swz_off(r, 0)) = *reinterpret_cast<const uint4*>(v);
+        *reinterpret_cast<uint4*>(abuf + swz_off(r, 1)) = *reinterpret_cast<const uint4*>(v + 8);
+#pragma unroll
+        for (int u16 = 2; u16 < kUK / 8; ++u16) *reinterpret_cast<uint4*>(abuf + swz_off(r, u16)) = make_uint4(0u, 0u, 0u, 0u);
       }
       fence_async_smem();
       mbar_arrive(&a_ready[slot]);
-      // two hidden products: accumulator -> bias, ReLU, BF16 -> operand buffer
+      // three hidden products: accumulator -> (bias), ReLU, BF16 -> operand buffer
       bool ok = true;
-      for (int m = 0; m < 2 && ok; ++m, ++use_acc) {
+      for (int m = 0; m < 3 && ok; ++m, ++use_acc) {
         if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[slot], uint32_t(use_acc) & 1u))) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const float* bias = prm + (m == 0 ? L.off_b2 : L.off_b3);
-        __nv_bfloat16* hT = m == 0 ? g.hT2 : g.hT3;
+        const float* bias = m == 0 ? nullptr : prm + (m == 1 ? L.off_b2 : L.off_b3);  // b1 is inside W1e
+        __nv_bfloat16* hT = m == 0 ? g.hT1 : (m == 1 ? g.hT2 : g.hT3);
         uint32_t mb[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
         for (int cg = 0; cg < 4; ++cg) {  // 4 groups of 4 x 16 columns
           uint32_t v[4][16];
@@ -737,11 +700,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             for (int hlf = 0; hlf < 2; ++hlf) {
               uint4 pk;
               uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+              float bv[8];
+              if (bias) {
+                const float4 b0 = __ldg(reinterpret_cast<const float4*>(bias + col0 + 16 * x + 8 * hlf));
+                const float4 b1v = __ldg(reinterpret_cast<const float4*>(bias + col0 + 16 * x + 8 * hlf + 4));
+                bv[0] = b0.x; bv[1] = b0.y; bv[2] = b0.z; bv[3] = b0.w;
+                bv[4] = b1v.x; bv[5] = b1v.y; bv[6] = b1v.z; bv[7] = b1v.w;
+              } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) bv[e] = 0.0f;
+              }
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int cc = col0 + 16 * x + 8 * hlf + 2 * e;
-                const float o0 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e]) + __ldg(bias + cc), 0.0f);
-                const float o1 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e + 1]) + __ldg(bias + cc + 1), 0.0f);
+                const float o0 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e]) + bv[2 * e], 0.0f);
+                const float o1 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e + 1]) + bv[2 * e + 1], 0.0f);
                 const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
                 pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
                 if (KEEP) {
@@ -756,7 +729,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           }
         }
         if (KEEP) {
-          uint4* bp = reinterpret_cast<uint4*>(g.bits + (size_t(m + 1) * g.n + ev) * 8);
+          uint4* bp = reinterpret_cast<uint4*>(g.bits + (size_t(m) * g.n + ev) * 8);
           bp[0] = make_uint4(mb[0], mb[1], mb[2], mb[3]);
           bp[1] = make_uint4(mb[4], mb[5], mb[6], mb[7]);
         }
@@ -781,9 +754,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           for (int x = 0; x < kFusedLs / 16; ++x)
             tmem_ld16_nw(trow + uint32_t(jj * kFusedLs + 16 * x), reinterpret_cast<uint32_t*>(lg + 16 * x));
           tmem_wait_ld();
-          const float* b4 = prm + L.off_b4 + j * kFusedLs;
+          const float4* b4 = reinterpret_cast<const float4*>(prm + L.off_b4 + j * kFusedLs);
 #pragma unroll
-          for (int kk = 0; kk < kFusedLs; ++kk) lg[kk] += __ldg(b4 + kk);
+          for (int kk = 0; kk < kFusedLs / 4; ++kk) {
+            const float4 bb = __ldg(b4 + kk);
+            lg[4 * kk] += bb.x;
+            lg[4 * kk + 1] += bb.y;
+            lg[4 * kk + 2] += bb.z;
+            lg[4 * kk + 3] += bb.w;
+          }
           if (KEEP) {
 #pragma unroll
             for (int kk = 0; kk < 2 * kFusedK + 1; ++kk) g.LT[size_t(j * kFusedLs + kk) * g.n + ev] = lg[kk];
@@ -1103,6 +1082,7 @@ struct mc_flow_s {
   __nv_bfloat16* UT = nullptr;  // per layer: first-layer inputs, transposed [16][n]
   uint32_t* MB = nullptr;       // per layer: ReLU activity bits of h1, h2, h3 [3][n][8]
   float* dU = nullptr;          // [n][16] input gradient of the first layer
+  __nv_bfloat16* U = nullptr;   // [n][64] first-layer inputs of the layer-by-layer path
   float* part = nullptr;  // split-K partial products of the weight gradients
   int max_splits = 0;
   double* sums = nullptr;
@@ -1114,7 +1094,7 @@ struct mc_flow_s {
   float *Ps = nullptr, *lqs = nullptr;
   int* err = nullptr;
   int nout_pad_max = 0;
-  // fused sampling layers (K = 32, nout_pad <= 512): tensor maps of W2, W3, W4 per layer
+  // fused layers (K = 32, nout_pad <= 512): tensor maps of W2, W3, W4, W1e per layer
   bool use_fused = true;      // fused forward layers
   bool use_fused_bwd = true;  // fused backward layers
   std::vector<bool> fused_ok;
@@ -1223,8 +1203,11 @@ int conditioner(mc_flow F, int l, int slot, const float* P, long long n, bool ke
   const LayerDev& L = F->layers[l];
   const float* prm = F->d_params;
   __nv_bfloat16 *h1 = h_of(F, slot, 0), *h2 = h_of(F, slot, 1), *h3 = h_of(F, slot, 2);
-  mc::dense1_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P, F->D, L, prm, h1, keep ? hT_of(F, slot, 0) : nullptr,
-                                                             keep ? UT_of(F, slot) : nullptr, n);
+  mc::dense1_input_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P, F->D, L, F->U, keep ? UT_of(F, slot) : nullptr,
+                                                                   n);
+  if (int rc = gemm_rs(F, n, kH, mc::kUK, mc::kEpiBiasReluBf16, F->U, L.W1e, nullptr, h1,
+                       keep ? hT_of(F, slot, 0) : nullptr, nullptr, st))
+    return rc;
   if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiBiasReluBf16, h1, L.W2h, prm + L.off_b2, h2,
                        keep ? hT_of(F, slot, 1) : nullptr, nullptr, st))
     return rc;
@@ -1274,7 +1257,8 @@ int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st, float
   auto kern = keep ? mc::flow_layer_fused_kernel<true> : mc::flow_layer_fused_kernel<false>;
   FLOW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const int grid = int(std::min<long long>(n / 128, num_sms));
-  kern<<<grid, mc::kFusedThreads, smem, st>>>(F->maps[3 * l], F->maps[3 * l + 1], F->maps[3 * l + 2], a, stages);
+  kern<<<grid, mc::kFusedThreads, smem, st>>>(F->maps[4 * l + 3], F->maps[4 * l], F->maps[4 * l + 1],
+                                              F->maps[4 * l + 2], a, stages);
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
@@ -1433,6 +1417,8 @@ int refresh_bf16(mc_flow F, cudaStream_t st) {
     mc::to_bf16_kernel<<<mc::blocks_for(L.nout_pad * kH, 256), 256, 0, st>>>(F->d_params + L.off_W4, L.nout_pad, kH,
                                                                              L.W4h, L.W4t);
     mc::w1t_bf16_kernel<<<mc::blocks_for(mc::kUPad * kH, 256), 256, 0, st>>>(F->d_params + L.off_W1, L.na, L.W1t);
+    mc::w1e_bf16_kernel<<<mc::blocks_for(kH * mc::kUK, 256), 256, 0, st>>>(F->d_params + L.off_W1,
+                                                                          F->d_params + L.off_b1, L.na, L.W1e);
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
@@ -1540,7 +1526,7 @@ int mc_flow_free(mc_flow F) {
   for (void* p : {(void*)F->d_params, (void*)F->d_grads, (void*)F->d_m, (void*)F->d_v, (void*)F->d_wbf,
                   (void*)F->d_layers, (void*)F->P, (void*)F->logq, (void*)F->f, (void*)F->w, (void*)F->dP,
                   (void*)F->LT, (void*)F->h, (void*)F->hT, (void*)F->G, (void*)F->GT, (void*)F->dA, (void*)F->dAT,
-                  (void*)F->part, (void*)F->UT, (void*)F->MB, (void*)F->dU, (void*)F->Ps, (void*)F->lqs,
+                  (void*)F->part, (void*)F->UT, (void*)F->MB, (void*)F->dU, (void*)F->U, (void*)F->Ps, (void*)F->lqs,
                   (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
                   (void*)F->err})
     cudaFree(p);
@@ -1590,7 +1576,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
     L.off_W4 = off; off += size_t(L.nout_pad) * kH;
     L.off_b4 = off; off += L.nout_pad;
     F->layers.push_back(L);
-    woff += 2 * (2 * size_t(kH) * kH + size_t(L.nout_pad) * kH) + size_t(mc::kUPad) * kH;
+    woff += 2 * (2 * size_t(kH) * kH + size_t(L.nout_pad) * kH) + size_t(mc::kUPad) * kH + size_t(kH) * mc::kUK;
   }
   F->nparam = off;
   const size_t bp = size_t(F->bp), D = size_t(F->D), np = size_t(F->nout_pad_max), L = size_t(F->L);
@@ -1621,6 +1607,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->UT, sizeof(__nv_bfloat16) * L * mc::kUPad * bp);
   alloc((void**)&F->MB, sizeof(uint32_t) * L * 3 * bp * 8);
   alloc((void**)&F->dU, sizeof(float) * bp * mc::kUPad);
+  alloc((void**)&F->U, sizeof(__nv_bfloat16) * bp * mc::kUK);
   alloc((void**)&F->sums, sizeof(double) * (2 + 2 * mc::kLossBlocks));
   alloc((void**)&F->parts, sizeof(BlockPartial) * kPartsGrid);
   alloc((void**)&F->total, sizeof(BlockPartial));
@@ -1643,19 +1630,21 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
     Ld.W4h = F->d_wbf + woff; woff += size_t(Ld.nout_pad) * kH;
     Ld.W4t = F->d_wbf + woff; woff += size_t(Ld.nout_pad) * kH;
     Ld.W1t = F->d_wbf + woff; woff += size_t(mc::kUPad) * kH;
+    Ld.W1e = F->d_wbf + woff; woff += size_t(kH) * mc::kUK;
   }
   build_host_map(F);
-  // tensor maps of the fused sampling layers
-  F->maps.resize(3 * L);
+  // tensor maps of the fused layers
+  F->maps.resize(4 * L);
   F->bwd_maps.resize(4 * L);
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& Ld = F->layers[l];
     // fused layers: 32 bins (logit stride 80), at most 6 transformed
     // coordinates (W4 sub-products of at most 256 rows)
     bool ok = F->K == mc::kFusedK && ls == mc::kFusedLs && Ld.nb <= 6 && Ld.nout_pad <= 512;
-    ok = ok && mc::tc_make_map(&F->maps[3 * l], Ld.W2h, kH, kH, kH, kH) &&
-         mc::tc_make_map(&F->maps[3 * l + 1], Ld.W3h, kH, kH, kH, kH) &&
-         mc::tc_make_map(&F->maps[3 * l + 2], Ld.W4h, Ld.nout_pad, kH, kH, 32) &&
+    ok = ok && mc::tc_make_map(&F->maps[4 * l], Ld.W2h, kH, kH, kH, kH) &&
+         mc::tc_make_map(&F->maps[4 * l + 1], Ld.W3h, kH, kH, kH, kH) &&
+         mc::tc_make_map(&F->maps[4 * l + 2], Ld.W4h, Ld.nout_pad, kH, kH, 32) &&
+         mc::tc_make_map(&F->maps[4 * l + 3], Ld.W1e, kH, mc::kUK, mc::kUK, kH) &&
          mc::tc_make_map(&F->bwd_maps[4 * l], Ld.W4t, kH, Ld.nout_pad, Ld.nout_pad, kH) &&
          mc::tc_make_map(&F->bwd_maps[4 * l + 1], Ld.W3t, kH, kH, kH, kH) &&
          mc::tc_make_map(&F->bwd_maps[4 * l + 2], Ld.W2t, kH, kH, kH, kH) &&
