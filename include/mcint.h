@@ -403,6 +403,23 @@ int mc_flow_train(mc_flow f, const mc_integrand* itg, mc_pdf pdf, int steps, int
 int mc_flow_iterate(mc_flow f, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, uint32_t iteration,
                     void* stream, mc_iter_result* out);
 
+/* mc_integrate_flow: the integral with the flow as importance sampler and
+ * plain VEGAS as its judge and fallback.  One FP32 VEGAS iteration of
+ * nevents on a fresh nbins grid (then refined) measures VEGAS's variance per
+ * event; the flow (configuration cfg, parameters init) is trained online
+ * (train_steps Adam steps of train_batch events, learning rate lr) and runs
+ * one iteration of nevents.  The flow is used (*sampler = 1) when its
+ * training loss and its iteration are finite and its relative variance per
+ * event does not exceed VEGAS's; otherwise VEGAS continues (*sampler = 0).
+ * Iterations of the chosen sampler follow until the combined relative error
+ * is at most target (0: no target) or niter of them have run; every
+ * iteration, the judge's included, enters the inverse-variance combination
+ * (each is unbiased).  out->gpu_ms covers everything from the first launch.
+ * Synchronises. */
+int mc_integrate_flow(const mc_integrand* itg, mc_pdf pdf, const mc_flow_cfg* cfg, const float* init,
+                      int train_steps, int64_t train_batch, double lr, int niter, int64_t nevents, int nbins,
+                      uint64_t seed, double target_rel_err, void* stream, mc_result* out, int* sampler);
+
 #ifdef __cplusplus
 }
 #endif

@@ -426,7 +426,9 @@ int mc_debug_events(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t fir
 // Inverse-variance combination and chi^2/dof (thesis eq. vegas-check); an
 // iteration with zero variance is left out unless every iteration has zero
 // variance.
-static void combine(const std::vector<double>& e, const std::vector<double>& s2, mc_result* r) {
+}  // extern "C"
+
+void mc::combine_iterations(const std::vector<double>& e, const std::vector<double>& s2, mc_result* r) {
   double inv = 0.0, acc = 0.0;
   int used = 0;
   for (size_t i = 0; i < e.size(); ++i)
@@ -449,6 +451,12 @@ static void combine(const std::vector<double>& e, const std::vector<double>& s2,
   for (size_t i = 0; i < e.size(); ++i)
     if (s2[i] > 0.0) chi += (e[i] - r->mean) * (e[i] - r->mean) / s2[i];
   r->chi2_dof = used > 1 ? chi / (used - 1) : 0.0;
+}
+
+extern "C" {
+
+static void combine(const std::vector<double>& e, const std::vector<double>& s2, mc_result* r) {
+  mc::combine_iterations(e, s2, r);
 }
 
 int mc_integrate(const mc_integrand* itg, mc_pdf pdf, int niter, int64_t nevents, int nbins, uint64_t seed,

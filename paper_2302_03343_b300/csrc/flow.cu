@@ -1845,4 +1845,93 @@ int mc_flow_iterate(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int64_t neve
   return MC_OK;
 }
 
+int mc_integrate_flow(const mc_integrand* itg, mc_pdf pdf, const mc_flow_cfg* cfg, const float* init,
+                      int train_steps, int64_t train_batch, double lr, int niter, int64_t nevents, int nbins,
+                      uint64_t seed, double target, void* stream, mc_result* out, int* sampler) {
+  if (!itg || !cfg || !init || !out || !sampler || niter < 1 || nevents < 2 || train_steps < 0 || train_batch < 2)
+    return ffail(MC_EINVAL, "mc_integrate_flow: bad arguments");
+  std::memset(out, 0, sizeof(*out));
+  *sampler = 0;
+  const int nd = mc::process_dim(itg);
+  if (nd != cfg->ndim) return ffail(MC_EINVAL, "mc_integrate_flow: flow dimension differs from the process");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  FLOW_CUDA(cudaEventCreate(&e0));
+  FLOW_CUDA(cudaEventCreate(&e1));
+  FLOW_CUDA(cudaEventRecord(e0, st));
+  std::vector<double> es, s2s;
+  auto add = [&](const mc_iter_result& r) {  // one iteration's estimate and the variance of its mean
+    const double n = double(r.n), mean = r.sum / n;
+    es.push_back(mean);
+    s2s.push_back((r.sum2 / n - mean * mean) / (n - 1.0));
+    return s2s.back() * n / (mean * mean);  // relative variance per event
+  };
+  auto done = [&]() {
+    mc::combine_iterations(es, s2s, out);
+    out->n_iter = int(es.size());
+    return target > 0.0 && out->mean != 0.0 && out->sigma / std::fabs(out->mean) <= target;
+  };
+  // the judge: one FP32 VEGAS iteration on a fresh grid (then refined)
+  mc_vegas v = nullptr;
+  mc_flow f = nullptr;
+  int rc = mc_vegas_init(nd, nbins, seed, MC_FP32_KAHAN, &v);
+  mc_iter_result r;
+  double relvar_v = 0.0, relvar_f = 0.0;
+  bool flow_ok = false;
+  if (!rc) rc = mc_vegas_iterate(v, itg, pdf, nevents, stream, &r);
+  if (!rc) rc = mc_vegas_refine(v, 1.5, stream);
+  if (!rc) relvar_v = add(r);
+  // the flow: online training, then its first iteration
+  if (!rc) rc = mc_flow_create(cfg, init, train_batch, seed + 1, &f);
+  if (!rc && train_steps > 0) {
+    // asynchronous steps, then the last one with its loss read back
+    double last_loss = 0.0;
+    if (train_steps > 1) rc = mc_flow_train(f, itg, pdf, train_steps - 1, train_batch, lr, stream, nullptr);
+    if (!rc) rc = mc_flow_train(f, itg, pdf, 1, train_batch, lr, stream, &last_loss);
+    flow_ok = !rc && std::isfinite(last_loss);
+  } else {
+    flow_ok = !rc;
+  }
+  mc_iter_result rf;
+  std::memset(&rf, 0, sizeof(rf));
+  uint32_t flow_it = 0;
+  if (!rc && flow_ok) {
+    rc = mc_flow_iterate(f, itg, pdf, nevents, flow_it++, stream, &rf);
+    flow_ok = !rc && rf.status == MC_OK && std::isfinite(rf.sum) && std::isfinite(rf.sum2) && rf.sum != 0.0;
+    if (rc == MC_ENAN || rc == MC_ENOCONV) rc = MC_OK;
+  }
+  if (flow_ok) {
+    const double n = double(rf.n), mean = rf.sum / n;
+    relvar_f = (rf.sum2 / n - mean * mean) / (mean * mean);
+    flow_ok = std::isfinite(relvar_f) && relvar_f <= relvar_v;  // VEGAS judges the flow
+  }
+  *sampler = flow_ok ? 1 : 0;
+  if (!rc) {
+    if (flow_ok) add(rf);
+    bool reached = done();
+    while (!rc && !reached && out->n_iter < niter + 1) {
+      if (flow_ok) {
+        rc = mc_flow_iterate(f, itg, pdf, nevents, flow_it++, stream, &r);
+      } else {
+        rc = mc_vegas_iterate(v, itg, pdf, nevents, stream, &r);
+        if (!rc) rc = mc_vegas_refine(v, 1.5, stream);
+      }
+      if (!rc) {
+        add(r);
+        reached = done();
+      }
+    }
+  }
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  out->gpu_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (f) mc_flow_free(f);
+  if (v) mc_vegas_free(v);
+  return rc;
+}
+
 }  // extern "C"

@@ -13,6 +13,9 @@ void set_last_error(const char* msg);  // api.cu
 // the message set (api.cu).
 int fill_process_args(const mc_integrand* itg, mc_pdf pdf, KernelArgs* a);
 int process_dim(const mc_integrand* itg);  // sampled dimensions of the process, -1 if unknown
+// Inverse-variance combination of per-iteration estimates e[i] with
+// variances s2[i] (thesis Sec. VEGAS, eq. vegas-check): mean, sigma, chi2/dof.
+void combine_iterations(const std::vector<double>& e, const std::vector<double>& s2, mc_result* r);
 }
 
 struct mc_pdf_s {

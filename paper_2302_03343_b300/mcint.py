@@ -31,7 +31,7 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_batch_create", "mc_batch_iterate", "mc_batch_get_grid", "mc_batch_shape", "mc_batch_kernel_ms",
            "mc_batch_free", "mc_gemm_bf16", "mc_gemm_bf16_rs", "mc_gemm_bf16_tn", "mc_flow_param_count", "mc_flow_create", "mc_flow_free",
            "mc_flow_set_params", "mc_flow_get_params", "mc_flow_forward", "mc_flow_loss_grad", "mc_flow_adam_step",
-           "mc_flow_train", "mc_flow_iterate", "mc_flow_set_fused")
+           "mc_flow_train", "mc_flow_iterate", "mc_flow_set_fused", "mc_integrate_flow")
 
 
 class McError(RuntimeError):
@@ -125,6 +125,8 @@ def lib():
             "mc_flow_loss_grad": [_vp, i64, _vp, _vp, _dp, _fp, _vp],
             "mc_flow_adam_step": [_vp, d, _vp],
             "mc_flow_set_fused": [_vp, i32],
+            "mc_integrate_flow": [ctypes.POINTER(Integrand), _vp, ctypes.POINTER(FlowCfg), _fp, i32, i64, d, i32, i64,
+                                  i32, u64, d, _vp, ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_int)],
             "mc_flow_train": [_vp, ctypes.POINTER(Integrand), _vp, i32, i64, d, _vp, _dp],
             "mc_flow_iterate": [_vp, ctypes.POINTER(Integrand), _vp, i64, u32, _vp, ctypes.POINTER(IterResult)],
         }
@@ -513,6 +515,19 @@ def mc_flow_iterate(f, itg, pdf, nevents, iteration=0, stream=None):
     _check(lib().mc_flow_iterate(f.handle, ctypes.byref(_integrand(itg)), pdf.handle if pdf else None, nevents,
                                  iteration, _stream(stream), ctypes.byref(r)))
     return r
+
+
+def mc_integrate_flow(itg, pdf, ndim, layers, bins, init_layers, train_steps, train_batch, lr=1e-3, niter=15,
+                      nevents=10_000_000, nbins=50, seed=0, target_rel_err=0.0, stream=None, hidden=256):
+    """Flow importance sampling with plain VEGAS as judge and fallback; returns (Result, used_flow)."""
+    cfg = FlowCfg(ndim, layers, bins, hidden)
+    flat = np.ascontiguousarray(pack_flow_params(init_layers), dtype=np.float32)
+    out = Result()
+    used = ctypes.c_int()
+    _check(lib().mc_integrate_flow(ctypes.byref(_integrand(itg)), pdf.handle if pdf else None, ctypes.byref(cfg),
+                                   flat.ctypes.data_as(_fp), train_steps, train_batch, lr, niter, nevents, nbins, seed,
+                                   target_rel_err, _stream(stream), ctypes.byref(out), ctypes.byref(used)))
+    return out, bool(used.value)
 
 
 __all__ = ["McError", "Integrand", "IterResult", "Result", "Pdf", "Vegas", "Flow", "FlowCfg", "workloads",
