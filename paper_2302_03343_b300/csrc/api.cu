@@ -14,6 +14,8 @@ using mc::BlockPartial;
 using mc::KernelArgs;
 
 namespace {
+// the reduced sums of a launch followed by its status word (MC_ETIMEOUT or 0)
+constexpr size_t kTotalBytes = sizeof(BlockPartial) + 16;
 
 thread_local std::string g_err;
 
@@ -203,8 +205,8 @@ int mc_vegas_init(int ndim, int nbins, uint64_t seed, int prec, mc_vegas* out) {
       (e = cudaMalloc(&v->d_hist_w2, sizeof(double) * nh)) != cudaSuccess ||
       (e = cudaMalloc(&v->d_hist_n, sizeof(unsigned int) * nh)) != cudaSuccess ||
       (e = cudaMalloc(&v->d_partials, sizeof(BlockPartial) * v->max_partials)) != cudaSuccess ||
-      (e = cudaMalloc(&v->d_total, sizeof(BlockPartial))) != cudaSuccess ||
-      (e = cudaMallocHost(&v->h_total, sizeof(BlockPartial))) != cudaSuccess ||
+      (e = cudaMalloc(&v->d_total, kTotalBytes)) != cudaSuccess ||
+      (e = cudaMallocHost(&v->h_total, kTotalBytes)) != cudaSuccess ||
       (e = cudaEventCreate(&v->k0)) != cudaSuccess || (e = cudaEventCreate(&v->k1)) != cudaSuccess) {
     mc_vegas_free(v);
     return fail(MC_ENOMEM, "mc_vegas_init: allocation failed: %s", cudaGetErrorString(e));
@@ -339,7 +341,8 @@ static int prepare(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, KernelArgs* 
 static int launch_grid(int proc, bool fp64, int64_t n, size_t smem, int max_blocks) {
   const int per_sm = mc::integrand_max_blocks_per_sm(proc, fp64, smem);
   long long grid = (long long)num_sms() * per_sm;
-  const long long need = (n + mc::kBlock - 1) / mc::kBlock;
+  const int per_block = mc::integrand_block_events(proc, fp64);
+  const long long need = (n + per_block - 1) / per_block;
   if (grid > need) grid = need;
   if (grid > max_blocks) grid = max_blocks;
   if (grid < 1) grid = 1;
@@ -352,7 +355,7 @@ int mc_launch_shape(const mc_integrand* itg, int prec, int64_t nevents, int* blo
   if (nd < 1) return fail(MC_EINVAL, "mc_launch_shape: bad process");
   const size_t smem = mc::integrand_smem(itg->proc, prec == MC_FP64, nd, 50, 100);
   *blocks = launch_grid(itg->proc, prec == MC_FP64, nevents, smem, num_sms() * 32);
-  *threads = mc::kBlock;
+  *threads = mc::integrand_threads(itg->proc, prec == MC_FP64);
   return MC_OK;
 }
 
@@ -371,13 +374,18 @@ int mc_vegas_iterate(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t ne
     const int grid = launch_grid(itg->proc, fp64, nevents, smem, v->max_partials);
     a.first = 0;
     a.n = nevents;
+    int* d_status = reinterpret_cast<int*>(v->d_total + 1);
+    a.status = d_status;
+    MC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
     MC_CUDA(cudaEventRecord(v->k0, st));
     MC_CUDA(mc::launch_integrand(itg->proc, fp64, a, grid, smem, st));
     MC_CUDA(cudaEventRecord(v->k1, st));
     v->timed = true;
     MC_CUDA(mc::launch_finalize(v->d_partials, grid, v->d_total, st));
-    MC_CUDA(cudaMemcpyAsync(v->h_total, v->d_total, sizeof(BlockPartial), cudaMemcpyDeviceToHost, st));
+    MC_CUDA(cudaMemcpyAsync(v->h_total, v->d_total, kTotalBytes, cudaMemcpyDeviceToHost, st));
     MC_CUDA(cudaStreamSynchronize(st));
+    if (*reinterpret_cast<const int*>(v->h_total + 1) != 0)
+      return fail(MC_ETIMEOUT, "mc_vegas_iterate: a bounded wait inside the integrand kernel gave up");
     const BlockPartial& t = *v->h_total;
     out->sum = t.sum_hi + t.sum_lo;
     out->sum2 = t.sum2_hi + t.sum2_lo;

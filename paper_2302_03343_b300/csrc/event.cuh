@@ -12,7 +12,7 @@ namespace mc {
 // Per-thread accumulators: Kahan-compensated FP64 sums of w and w^2.
 struct Acc {
   double s_hi = 0.0, s_c = 0.0, q_hi = 0.0, q_c = 0.0, wmax = 0.0;
-  long long nnz = 0, nbad = 0, nnoconv = 0;
+  unsigned int nnz = 0, nbad = 0, nnoconv = 0;  // per thread: below 2^32 events
 };
 
 // value = hi + lo pairs: compensated addition of two such pairs
@@ -45,12 +45,17 @@ MC_D void process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_ed
   event_uniforms<MAXD, FP64>(a.seed, a.iteration, a.gid, ev, ndim, k);
   R x[MAXD];
   int bin[MAXD];
+  // bin indices (< 256) packed four to a word while the integrand runs
+  uint32_t binw[(MAXD + 3) / 4];
+#pragma unroll
+  for (int j = 0; j < (MAXD + 3) / 4; ++j) binw[j] = 0u;
   R jac = R(1);
 #pragma unroll
   for (int dd = 0; dd < MAXD; ++dd) {
     if (dd < ndim) {
       R jd;
       x[dd] = vegas_map_1d<R, FP64>(sh_edges + dd * (nb + 1), nb, k[dd], &bin[dd], &jd);
+      binw[dd / 4] |= uint32_t(bin[dd]) << (8 * (dd % 4));
       jac *= jd;
     }
   }
@@ -97,8 +102,9 @@ MC_D void process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_ed
 #pragma unroll
   for (int dd = 0; dd < MAXD; ++dd) {
     if (dd < ndim) {
-      atomicAdd(&sh_w2[dd * nb + bin[dd]], H(w2));
-      atomicAdd(&sh_n[dd * nb + bin[dd]], 1u);
+      const int b = int((binw[dd / 4] >> (8 * (dd % 4))) & 0xffu);
+      atomicAdd(&sh_w2[dd * nb + b], H(w2));
+      atomicAdd(&sh_n[dd * nb + b], 1u);
     }
   }
 }

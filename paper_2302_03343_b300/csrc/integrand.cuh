@@ -44,6 +44,7 @@ struct KernelArgs {
   double* hist_w2;         // [ndim][nbins]
   unsigned int* hist_n;    // [ndim][nbins]
   double* record;          // [n][MC_REC_STRIDE] (debug launches only)
+  int* status;             // optional: MC_ETIMEOUT when a bounded wait of the launch gave up
 };
 
 // Shared-memory PDF tables of a launch.
@@ -70,6 +71,96 @@ template <class T> MC_D void rec_p4(double* rec, int slot, const v4<T>& p) {
     rec[49 + 4 * slot + 2] = double(p.y);
     rec[49 + 4 * slot + 3] = double(p.z);
   }
+}
+
+// gg -> t tbar g, split into the kinematic part (phase space, cuts, gluon
+// luminosity) and the |M|^2 part so that the warp-specialised kernel can run
+// them in different warps; the fused path calls the same three functions.
+template <class R>
+struct GgKin {
+  v4<R> k[3];  // top, anti-top, gluon in the partonic frame
+  R shat, rs;  // partonic s and its square root
+  R lgg;       // g(x1) g(x2) / (x1 x2)
+  R flux;      // gev2pb / (2 shat)
+  double psw;  // phase-space weight
+};
+
+// Returns 1 when the event passes the cuts (kin filled), 0 when it fails
+// them, -5 when RAMBO's rescaling did not converge.
+template <int PROC, class R>
+MC_D int gg_kinematics(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, GgKin<R>* kin, double* rec) {
+  const Params& p = a.prm;
+  const double s = p.sqrt_s * p.sqrt_s;
+  const R x1 = x[0], x2 = x[1];
+  rec_put(rec, 77, x1); rec_put(rec, 78, x2);
+  const R m = R(p.m_top);
+  const R shat = sizeof(R) == 4 ? R(x1 * x2 * R(s)) : R(double(x1) * double(x2) * s);
+  rec_put(rec, 79, shat);
+  if (!(shat > R(4) * m * m)) return 0;
+  const R rs = m_sqrt(shat);
+  v4<R>* k = kin->k;
+  double psw;
+  int rc = 0;
+  if constexpr (PROC == P_GG_TTBARG_7D) {
+    v4<double> kd[3];
+    hierarchical3<R>(double(m), double(rs), x + 2, kd, &psw);
+    for (int i = 0; i < 3; ++i) k[i] = vcast<R>(kd[i]);
+  } else if constexpr (sizeof(R) == 4) {
+    // FP32 mode: FP64 only inside RAMBO's conformal transformation
+    const float masses[3] = {m, m, 0.0f};
+    rc = rambo_fp32<3>(masses, rs, a.w0_coef3, x + 2, k, &psw);
+  } else {
+    const double masses[3] = {double(m), double(m), 0.0};
+    v4<double> kd[3];
+    rc = rambo<R, 3>(masses, double(rs), a.w0_coef3, x + 2, kd, &psw);
+    for (int i = 0; i < 3; ++i) k[i] = vcast<R>(kd[i]);
+  }
+  if (rec) {
+    const v4<R> pa = {rs * R(0.5), R(0), R(0), rs * R(0.5)}, pb = {rs * R(0.5), R(0), R(0), -rs * R(0.5)};
+    rec_p4(rec, 0, pa); rec_p4(rec, 1, pb); rec_p4(rec, 2, k[0]); rec_p4(rec, 3, k[1]); rec_p4(rec, 4, k[2]);
+    rec_put(rec, 84, psw);
+  }
+  if (rc != 0) return -5;
+  // gluon cuts in the lab frame: pT > cut and |eta_cm + y| < cut with
+  // y = ln(x1/x2)/2, written without logarithms:
+  // e^{-2c} (|p| - pz) x2 < (|p| + pz) x1 < e^{2c} (|p| - pz) x2.
+  const v4<R>& g = k[2];
+  const R pt2 = g.x * g.x + g.y * g.y;
+  const R ptc = R(p.ptcut_g);
+  if (!(pt2 > ptc * ptc)) return 0;
+  const R pabs = m_sqrt(pt2 + g.z * g.z);
+  const R fwd = (pabs + g.z) * x1, bwd = (pabs - g.z) * x2;
+  const R e2 = R(a.e2eta);
+  if (!(fwd < e2 * bwd && bwd < e2 * fwd)) return 0;
+  kin->shat = shat;
+  kin->rs = rs;
+  kin->lgg = xf_over_x(pdf.tab[0], x1) * xf_over_x(pdf.tab[0], x2);
+  kin->flux = sizeof(R) == 4 ? R(p.gev2pb) / (R(2) * shat) : R(0);
+  kin->psw = psw;
+  return 1;
+}
+
+// |M|^2 of an event that passed the cuts: packed FP32x2 arithmetic in FP32
+// mode, the precision-generic routine in FP64 mode.
+template <class R>
+MC_D R gg_me2(const KernelArgs& a, const GgKin<R>& kin) {
+  const R h = kin.rs * R(0.5);
+  const v4<R> pa = {h, R(0), R(0), h}, pb = {h, R(0), R(0), -h};
+  const R m = R(a.prm.m_top), g2 = R(4.0 * kPi * a.prm.alpha_s);
+  if constexpr (sizeof(R) == 4)
+    return me2_gg_ttbarg_p(pa, pb, kin.k[0], kin.k[1], kin.k[2], m, g2);
+  else
+    return me2_gg_ttbarg<R>(pa, pb, kin.k[0], kin.k[1], kin.k[2], m, g2);
+}
+
+// f = L_gg <|M|^2> / (2 shat) * w_PS * gev2pb (the VEGAS Jacobian is applied
+// by the caller).
+template <class R>
+MC_D double gg_weight(const KernelArgs& a, const GgKin<R>& kin, R me2) {
+  if constexpr (sizeof(R) == 4)
+    return double(kin.lgg * me2 * kin.flux) * kin.psw;
+  else
+    return double(kin.lgg) * double(me2) / (2.0 * double(kin.shat)) * kin.psw * a.prm.gev2pb;
 }
 
 // Integrand at the point x of the unit hypercube; rec (may be null) receives
@@ -126,69 +217,17 @@ MC_D EventOut integrand(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, do
       rec_put(rec, 84, psw);
     }
   } else if constexpr (PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D) {
-    // gg -> t tbar g: RAMBO (14 dims) or the hierarchical generator (7 dims)
-    const R x1 = x[0], x2 = x[1];
-    rec_put(rec, 77, x1); rec_put(rec, 78, x2);
-    const R m = R(p.m_top);
-    const R shat = sizeof(R) == 4 ? R(x1 * x2 * R(s)) : R(double(x1) * double(x2) * s);
-    rec_put(rec, 79, shat);
-    if (!(shat > R(4) * m * m)) {
+    GgKin<R> kin;
+    const int st = gg_kinematics<PROC, R>(a, pdf, x, &kin, rec);
+    if (st != 1) {
       out.pass = 0;
+      out.status = st;
       return out;
     }
-    const R rs = m_sqrt(shat);
-    v4<R> k[3];
-    double psw;
-    int rc = 0;
-    if constexpr (PROC == P_GG_TTBARG_7D) {
-      v4<double> kd[3];
-      hierarchical3<R>(double(m), double(rs), x + 2, kd, &psw);
-      for (int i = 0; i < 3; ++i) k[i] = vcast<R>(kd[i]);
-    } else if constexpr (sizeof(R) == 4) {
-      // FP32 mode: FP64 only inside RAMBO's conformal transformation
-      const float masses[3] = {m, m, 0.0f};
-      rc = rambo_fp32<3>(masses, rs, a.w0_coef3, x + 2, k, &psw);
-    } else {
-      const double masses[3] = {double(m), double(m), 0.0};
-      v4<double> kd[3];
-      rc = rambo<R, 3>(masses, double(rs), a.w0_coef3, x + 2, kd, &psw);
-      for (int i = 0; i < 3; ++i) k[i] = vcast<R>(kd[i]);
-    }
-    const v4<R> pa = {rs * R(0.5), R(0), R(0), rs * R(0.5)}, pb = {rs * R(0.5), R(0), R(0), -rs * R(0.5)};
+    const R me2 = gg_me2<R>(a, kin);
+    out.f = gg_weight<R>(a, kin, me2);
     if (rec) {
-      rec_p4(rec, 0, pa); rec_p4(rec, 1, pb); rec_p4(rec, 2, k[0]); rec_p4(rec, 3, k[1]); rec_p4(rec, 4, k[2]);
-      rec_put(rec, 84, psw);
-    }
-    if (rc != 0) {
-      out.pass = 0;
-      out.status = -5;
-      return out;
-    }
-    // gluon cuts in the lab frame: pT > cut and |eta_cm + y| < cut with
-    // y = ln(x1/x2)/2, written without logarithms:
-    // e^{-2c} (|p| - pz) x2 < (|p| + pz) x1 < e^{2c} (|p| - pz) x2.
-    const v4<R>& g = k[2];
-    const R pt2 = g.x * g.x + g.y * g.y;
-    const R ptc = R(p.ptcut_g);
-    if (!(pt2 > ptc * ptc)) {
-      out.pass = 0;
-      return out;
-    }
-    const R pabs = m_sqrt(pt2 + g.z * g.z);
-    const R fwd = (pabs + g.z) * x1, bwd = (pabs - g.z) * x2;
-    const R e2 = R(a.e2eta);
-    if (!(fwd < e2 * bwd && bwd < e2 * fwd)) {
-      out.pass = 0;
-      return out;
-    }
-    const R me2 = me2_gg_ttbarg<R>(pa, pb, k[0], k[1], k[2], m, R(4.0 * kPi * p.alpha_s));
-    const R lgg = xf_over_x(pdf.tab[0], x1) * xf_over_x(pdf.tab[0], x2);
-    if (sizeof(R) == 4)
-      out.f = double(lgg * me2 * (R(p.gev2pb) / (R(2) * shat))) * psw;
-    else
-      out.f = double(lgg) * double(me2) / (2.0 * double(shat)) * psw * p.gev2pb;
-    if (rec) {
-      rec_put(rec, 80, lgg);
+      rec_put(rec, 80, kin.lgg);
       rec_put(rec, 82, me2);
     }
   } else {  // Gaussian

@@ -4,6 +4,8 @@
 //    uniforms -> VEGAS map -> phase space -> PDFs -> |M|^2 -> weight ->
 //    Kahan FP64 sums and shared-memory histograms -> per-block partials and
 //    global histogram atomics.  Nothing per event touches global memory.
+//  * ws_integrand_kernel (ws_integrand.cuh): the same pass for gg -> t tbar g
+//    in FP32 mode with producer (kinematics) and consumer (|M|^2) warps.
 //  * finalize_kernel: fixed-order reduction of the per-block partials
 //    (deterministic sums for a given launch shape).
 //  * refine_kernel: VEGAS rebinning, one thread per dimension, FP64.
@@ -16,6 +18,7 @@
 #include "integrand.cuh"
 #include "launch.h"
 #include "refine.cuh"
+#include "ws_integrand.cuh"
 
 namespace mc {
 
@@ -163,8 +166,26 @@ static cudaError_t launch_one(const KernelArgs& a, int grid, size_t smem, cudaSt
   return cudaGetLastError();
 }
 
+template <int PROC>
+static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
+  auto k = ws_integrand_kernel<PROC>;
+  const size_t smem = ws_smem_bytes(a.ndim, a.nbins, a.pdf.nx);
+  (void)cudaGetLastError();
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  k<<<grid, kWsThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+bool integrand_ws(int proc, bool fp64) { return !fp64 && (proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D); }
+int integrand_threads(int proc, bool fp64) { return integrand_ws(proc, fp64) ? kWsThreads : kBlock; }
+// events one block takes per round of its grid-stride loop
+int integrand_block_events(int proc, bool fp64) { return integrand_ws(proc, fp64) ? 32 * kWsProducerWarps : kBlock; }
+
 template <bool RECORD>
 static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem, cudaStream_t st) {
+  if (!RECORD && integrand_ws(proc, fp64))
+    return proc == P_GG_TTBARG ? launch_ws<P_GG_TTBARG>(a, grid, st) : launch_ws<P_GG_TTBARG_7D>(a, grid, st);
   switch (proc) {
     case P_EE_MUMU:
       return fp64 ? launch_one<P_EE_MUMU, true, RECORD>(a, grid, smem, st)
@@ -186,6 +207,7 @@ static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, 
 }
 
 size_t integrand_smem(int proc, bool fp64, int ndim, int nbins, int nx) {
+  if (integrand_ws(proc, fp64)) return ws_smem_bytes(ndim, nbins, nx);
   const size_t r = fp64 ? 8 : 4;
   const int nfl = proc == P_PP_TTBAR ? 11 : ((proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D) ? 1 : 0);
   const size_t hist = ((size_t(ndim) * nbins * 12 + 15) / 16) * 16;
@@ -193,6 +215,7 @@ size_t integrand_smem(int proc, bool fp64, int ndim, int nbins, int nx) {
 }
 
 int integrand_max_blocks_per_sm(int proc, bool fp64, size_t smem) {
+  if (integrand_ws(proc, fp64)) return 1;
   int nb = 0;
   cudaError_t e = cudaSuccess;
 #define MC_OCC(P)                                                                                        \

@@ -11,6 +11,13 @@ namespace mc {
 
 constexpr int kBlock = 128;  // threads per block of the fused integrand kernel
 
+// The fused integrand launch: gg -> t tbar g in FP32 mode runs the
+// warp-specialised kernel (integrand_threads() threads, one block per SM,
+// integrand_block_events() events per block and round); everything else the
+// per-thread kernel of kBlock threads.
+bool integrand_ws(int proc, bool fp64);
+int integrand_threads(int proc, bool fp64);
+int integrand_block_events(int proc, bool fp64);
 size_t integrand_smem(int proc, bool fp64, int ndim, int nbins, int nx);
 int integrand_max_blocks_per_sm(int proc, bool fp64, size_t smem);
 cudaError_t launch_integrand(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem, cudaStream_t st);

@@ -5,6 +5,7 @@
 // |M|^2 for momenta in the partonic centre-of-mass frame.
 #pragma once
 #include "helas.cuh"
+#include "packed.cuh"
 
 namespace mc {
 
@@ -286,6 +287,147 @@ MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4
    }
   }
   return g2 * g2 * g2 * total * R(2) / (R(27) * R(256));
+}
+
+// FP32 gg -> t tbar g with packed (re, im) complex arithmetic: the same
+// colour-ordered amplitudes as me2_gg_ttbarg, regrouped per ordering (abc):
+//   Gamma(abc) v = eps_a S_a [eps_b X_c - J(bc) v] - J(ab) X_c + J(abc) v,
+// with ubar J(abc)-slash v = J(abc) . T, T^mu = ubar gamma^mu v; each column
+// spinor is contracted with both top spinors as soon as it is formed.
+MC_D float me2_gg_ttbarg_p(const v4<float>& pa, const v4<float>& pb, const v4<float>& pt, const v4<float>& ptb,
+                           const v4<float>& pg, float m, float g2) {
+  const v4<float> q[3] = {pa, pb, -pg};
+  v4<float> eps[3][2];
+  linear_polarisations(pa, &eps[0][0], &eps[0][1]);
+  linear_polarisations(pb, &eps[1][0], &eps[1][1]);
+  linear_polarisations(pg, &eps[2][0], &eps[2][1]);
+  sv ka[3], kc[3];
+  float ma[3], mc_[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const v4<float> k1 = pt - q[a];
+    const float i1 = 1.0f / (mdot(k1, k1) - m * m);
+    ka[a] = make_sv(k1, i1);
+    ma[a] = m * i1;
+    const v4<float> k2 = q[a] - ptb;
+    const float i2 = 1.0f / (mdot(k2, k2) - m * m);
+    kc[a] = make_sv(k2, i2);
+    mc_[a] = m * i2;
+  }
+  const v4<float> q01 = q[0] + q[1], q02 = q[0] + q[2], q12 = q[1] + q[2];
+  const float i01 = 1.0f / mdot(q01, q01), i02 = 1.0f / mdot(q02, q02), i12 = 1.0f / mdot(q12, q12);
+  const v4<float> qall = q01 + q[2];
+  const float iall = 1.0f / mdot(qall, qall);
+  const sp4<float> ub[2] = {ubar_spinor(pt, m, -1), ubar_spinor(pt, m, +1)};
+  const sp4p v = to_p(v_spinor(ptb, m, +1));
+  // T[ht][mu] = ubar gamma^mu v, gamma^0 = slash(1,0,0,0), gamma^k = slash(-e_k)
+  f2 T[2][4];
+  {
+    const sp4p g0 = slash_colp(make_sv(v4<float>{1.0f, 0.0f, 0.0f, 0.0f}), v);
+    const sp4p g1 = slash_colp(make_sv(v4<float>{0.0f, -1.0f, 0.0f, 0.0f}), v);
+    const sp4p g2v = slash_colp(make_sv(v4<float>{0.0f, 0.0f, -1.0f, 0.0f}), v);
+    const sp4p g3 = slash_colp(make_sv(v4<float>{0.0f, 0.0f, 0.0f, -1.0f}), v);
+#pragma unroll
+    for (int ht = 0; ht < 2; ++ht) {
+      T[ht][0] = dotp(ub[ht], g0);
+      T[ht][1] = dotp(ub[ht], g1);
+      T[ht][2] = dotp(ub[ht], g2v);
+      T[ht][3] = dotp(ub[ht], g3);
+    }
+  }
+  f2 total0 = bc2(0.0f), total1 = bc2(0.0f);
+#pragma unroll 1
+  for (int h0 = 0; h0 < 2; ++h0) {
+    const v4<float> e0 = eps[0][h0];
+    const sp4p x0 = prop_colp(kc[0], mc_[0], slash_colp(make_sv(e0), v));
+#pragma unroll 1
+    for (int h1 = 0; h1 < 2; ++h1) {
+      const v4<float> e1 = eps[1][h1];
+      const sp4p x1 = prop_colp(kc[1], mc_[1], slash_colp(make_sv(e1), v));
+      const v4<float> j01 = gluon_current(e0, q[0], e1, q[1], i01);
+      const sp4p u01 = slash_colp(make_sv(j01), v);
+#pragma unroll 1
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const v4<float> e2 = eps[2][h2];
+        const v4<float> j02 = gluon_current(e0, q[0], e2, q[2], i02);
+        const v4<float> j12 = gluon_current(e1, q[1], e2, q[2], i12);
+        const sp4p x2 = prop_colp(kc[2], mc_[2], slash_colp(make_sv(e2), v));
+        f2 amp[2][6];
+        // orderings 012 021 102 120 201 210
+#define MC_PUT(S, EA, A, B)                                                  \
+  {                                                                          \
+    const sp4p c_ = slash_colp(make_sv(EA), prop_colp(ka[A], ma[A], B));     \
+    amp[0][S] = dotp(ub[0], c_);                                             \
+    amp[1][S] = dotp(ub[1], c_);                                             \
+  }
+        {
+          const sp4p u12 = slash_colp(make_sv(j12), v);
+          MC_PUT(0, e0, 0, slash_colp(make_sv(e1), x2) - u12)
+          MC_PUT(1, e0, 0, slash_colp(make_sv(e2), x1) + u12)
+        }
+        {
+          const sp4p u02 = slash_colp(make_sv(j02), v);
+          MC_PUT(2, e1, 1, slash_colp(make_sv(e0), x2) - u02)
+          MC_PUT(3, e1, 1, slash_colp(make_sv(e2), x0) + u02)
+        }
+        MC_PUT(4, e2, 2, slash_colp(make_sv(e0), x1) - u01)
+        MC_PUT(5, e2, 2, slash_colp(make_sv(e1), x0) + u01)
+#undef MC_PUT
+        // -J(ab) X_c, with J(ba) = -J(ab)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const sp4p y = c == 2 ? slash_colp(make_sv(j01), x2) : (c == 1 ? slash_colp(make_sv(j02), x1)
+                                                                         : slash_colp(make_sv(j12), x0));
+          const int sm = c == 2 ? 0 : (c == 1 ? 1 : 3), sp = c == 2 ? 2 : (c == 1 ? 4 : 5);
+#pragma unroll
+          for (int ht = 0; ht < 2; ++ht) {
+            const f2 d = dotp(ub[ht], y);
+            amp[ht][sm] = sub2(amp[ht][sm], d);
+            amp[ht][sp] = add2(amp[ht][sp], d);
+          }
+        }
+        // J(abc) v contracted with ubar: J . T ; J(012) = J(210), J(021) = J(120), J(102) = J(201)
+        {
+          const v4<float> j012 = gluon_current(j01, q01, e2, q[2], iall) + gluon_current(e0, q[0], j12, q12, iall) +
+                                 gluon_contact(e0, e1, e2, iall);
+          const v4<float> j021 = gluon_current(j02, q02, e1, q[1], iall) + gluon_current(e0, q[0], -j12, q12, iall) +
+                                 gluon_contact(e0, e2, e1, iall);
+          const v4<float> j102 = gluon_current(-j01, q01, e2, q[2], iall) + gluon_current(e1, q[1], j02, q02, iall) +
+                                 gluon_contact(e1, e0, e2, iall);
+#pragma unroll
+          for (int ht = 0; ht < 2; ++ht) {
+            const f2 wa = fma2(bc2(j012.e), T[ht][0], fma2(bc2(-j012.x), T[ht][1],
+                          fma2(bc2(-j012.y), T[ht][2], mul2(bc2(-j012.z), T[ht][3]))));
+            const f2 wb = fma2(bc2(j021.e), T[ht][0], fma2(bc2(-j021.x), T[ht][1],
+                          fma2(bc2(-j021.y), T[ht][2], mul2(bc2(-j021.z), T[ht][3]))));
+            const f2 wc = fma2(bc2(j102.e), T[ht][0], fma2(bc2(-j102.x), T[ht][1],
+                          fma2(bc2(-j102.y), T[ht][2], mul2(bc2(-j102.z), T[ht][3]))));
+            amp[ht][0] = add2(amp[ht][0], wa);
+            amp[ht][5] = add2(amp[ht][5], wa);
+            amp[ht][1] = add2(amp[ht][1], wb);
+            amp[ht][3] = add2(amp[ht][3], wb);
+            amp[ht][2] = add2(amp[ht][2], wc);
+            amp[ht][4] = add2(amp[ht][4], wc);
+          }
+        }
+#pragma unroll
+        for (int ht = 0; ht < 2; ++ht) {
+#pragma unroll
+          for (int s = 0; s < 6; ++s) {
+            f2 c = mul2(bc2(kColour3[s * 6 + s]), amp[ht][s]);
+#pragma unroll
+            for (int t = s + 1; t < 6; ++t) c = fma2(bc2(2.0f * kColour3[s * 6 + t]), amp[ht][t], c);
+            if (ht == 0)
+              total0 = fma2(amp[ht][s], c, total0);
+            else
+              total1 = fma2(amp[ht][s], c, total1);
+          }
+        }
+      }
+    }
+  }
+  const f2 total = add2(total0, total1);
+  return g2 * g2 * g2 * (lo2(total) + hi2(total)) * 2.0f / (27.0f * 256.0f);
 }
 
 }  // namespace mc

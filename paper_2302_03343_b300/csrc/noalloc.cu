@@ -112,7 +112,8 @@ extern "C" int mc_vegas_iterate_noalloc(const mc_integrand* itg, mc_pdf pdf, int
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long g = (long long)sms * mc::integrand_max_blocks_per_sm(itg->proc, fp64, smem);
-    const long long need = (nevents + mc::kBlock - 1) / mc::kBlock;
+    const int per_block = mc::integrand_block_events(itg->proc, fp64);
+    const long long need = (nevents + per_block - 1) / per_block;
     if (g > need) g = need;
     if (g > MC_NOALLOC_MAX_BLOCKS) g = MC_NOALLOC_MAX_BLOCKS;
     grid = int(g < 1 ? 1 : g);

@@ -162,8 +162,7 @@ MC_D double sqrt_nr(double x) {
 // (momenta in FP32), returns 0 or -5.
 template <int N>
 MC_D int rambo_fp32(const float* masses, float sqrt_s, double w0_coef, const float* u, v4<float>* out, double* w) {
-  double qe[N], qx[N], qy[N], qz[N];
-  double se = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+  float fe[N], fx[N], fy[N], fz[N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const float c = 2.0f * u[4 * i] - 1.0f;
@@ -171,25 +170,35 @@ MC_D int rambo_fp32(const float* masses, float sqrt_s, double w0_coef, const flo
     sincospif(2.0f * u[4 * i + 1], &sp, &cp);
     const float q0 = -logf(u[4 * i + 2] * u[4 * i + 3]);
     const float st = sqrtf(fmaxf(0.0f, 1.0f - c * c));
-    qe[i] = q0; qx[i] = q0 * st * cp; qy[i] = q0 * st * sp; qz[i] = q0 * c;
-    se += qe[i]; sx += qx[i]; sy += qy[i]; sz += qz[i];
+    fe[i] = q0; fx[i] = q0 * st * cp; fy[i] = q0 * st * sp; fz[i] = q0 * c;
   }
-  const double mq = sqrt_nr(se * se - sx * sx - sy * sy - sz * sz);
-  const double inv_mq = rcp_nr(mq);
+  double qe[N], qx[N], qy[N], qz[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) { qe[i] = fe[i]; qx[i] = fx[i]; qy[i] = fy[i]; qz[i] = fz[i]; }
+  double se = qe[0], sx = qx[0], sy = qy[0], sz = qz[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i) { se += qe[i]; sx += qx[i]; sy += qy[i]; sz += qz[i]; }
+  // 1/M by one FP64 Newton step on the FP32 rsqrt seed: r (3 - M^2 r^2) / 2
+  const double m2q = se * se - sx * sx - sy * sy - sz * sz;
+  const double r0 = double(rsqrtf(float(m2q)));
+  const double inv_mq = r0 * fma(-0.5 * m2q, r0 * r0, 1.5);
   const double bx = -sx * inv_mq, by = -sy * inv_mq, bz = -sz * inv_mq;
   const double gamma = se * inv_mq;
   const double a = rcp_nr(1.0 + gamma);
   const double x = double(sqrt_s) * inv_mq;
   float pe[N], px[N], py[N], pz[N];
+  double de = double(sqrt_s), dx = 0.0, dy = 0.0, dz = 0.0;
 #pragma unroll
-  for (int i = 0; i < N; ++i) {
+  for (int i = 0; i < N - 1; ++i) {
     const double bq = bx * qx[i] + by * qy[i] + bz * qz[i];
     const double t = qe[i] + a * bq;
-    pe[i] = float(x * (gamma * qe[i] + bq));
-    px[i] = float(x * (qx[i] + bx * t));
-    py[i] = float(x * (qy[i] + by * t));
-    pz[i] = float(x * (qz[i] + bz * t));
+    const double e = x * (gamma * qe[i] + bq), vx = x * (qx[i] + bx * t), vy = x * (qy[i] + by * t),
+                 vz = x * (qz[i] + bz * t);
+    pe[i] = float(e); px[i] = float(vx); py[i] = float(vy); pz[i] = float(vz);
+    de -= e; dx -= vx; dy -= vy; dz -= vz;
   }
+  // the last momentum by conservation: P - sum of the others
+  pe[N - 1] = float(de); px[N - 1] = float(dx); py[N - 1] = float(dy); pz[N - 1] = float(dz);
   const float s = sqrt_s * sqrt_s;
   float w0 = float(w0_coef);
 #pragma unroll

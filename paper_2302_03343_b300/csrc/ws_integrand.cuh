@@ -1,0 +1,280 @@
+// Warp-specialised fused integrand kernel for gg -> t tbar g in FP32 mode.
+//
+// The fused path of one event has two parts with very different hardware
+// profiles: the kinematics (Philox, VEGAS map, RAMBO with its FP64 conformal
+// boost, cuts, gluon luminosity) is bound by the FP64 pipe, whose B300
+// throughput is about 1/64 of the FP32 rate, and about a fifth of the events
+// fail the cuts; the |M|^2 (colour-ordered helicity amplitudes in packed
+// FP32x2 arithmetic) is bound by the FMA pipe.  Run one after the other in
+// every thread, a warp stalls for thousands of cycles in its FP64 section
+// and carries idle lanes through the |M|^2 for the events that were cut.
+//
+// Here each block (one per SM) splits its warps into two roles:
+//  * 4 producer warps (one per SM sub-partition) walk the event range in
+//    chunks of 32, evaluate the kinematics, add every event to the bin-count
+//    histogram, and append the events that pass the cuts, compacted with a
+//    warp ballot, to a shared-memory ring of slots of 32 event records;
+//  * 8 consumer warps take full slots, evaluate |M|^2 on all 32 lanes, form
+//    the weights w = f J, and keep the Kahan FP64 sums, w_max and the
+//    shared-memory histogram of w^2.
+// Slots pass between the roles through mbarriers (full: 32 producer-lane
+// arrivals; empty: 32 consumer-lane arrivals).  Producer warp p owns the
+// slots p, p+4, p+8, p+12 in that order; consumer warp c takes producer
+// (c mod 4)'s slots of sequence parity c / 4, i.e. slots c and c + 8.  The
+// assignment of events to lanes is fixed by the launch shape, so the sums
+// are deterministic for a given grid.  A producer ends its stream with a
+// partial slot and one end marker (count -1) for each of its two consumers.
+//
+// Every wait is bounded (kWsWaitNs of %globaltimer); a warp that gives up
+// stops, the block poisons its partial sums with NaN and, when the launch
+// carries a status word, sets it to MC_ETIMEOUT.
+#pragma once
+#include "event.cuh"
+#include "tcgen05.cuh"
+
+namespace mc {
+
+constexpr int kWsProducerWarps = 4;
+constexpr int kWsConsumerWarps = 8;
+constexpr int kWsThreads = 32 * (kWsProducerWarps + kWsConsumerWarps);
+constexpr int kWsSlots = 4 * kWsProducerWarps;
+// record words of one event (structure of arrays inside a slot: word j of
+// lane e at [j][e]): k[3] (12), rs, lgg, flux, jac, psw (2 words), bins (4)
+enum : int { kWK = 0, kWRs = 12, kWLgg = 13, kWFlux = 14, kWJac = 15, kWPsw = 16, kWBin = 18, kWsWords = 22 };
+constexpr unsigned long long kWsWaitNs = 2000000000ull;
+// Registers per thread: the launch gets kWsRegs (65536 / 384, rounded down
+// to a multiple of 8); producers give up to kWsProducerRegs, consumers take
+// kWsConsumerRegs, and 128 kWsProducerRegs + 256 kWsConsumerRegs stays within
+// 384 kWsRegs, so the increase never waits on registers that are not there.
+constexpr int kWsRegs = 168, kWsProducerRegs = 104, kWsConsumerRegs = 192;
+static_assert(32 * kWsProducerWarps * kWsProducerRegs + 32 * kWsConsumerWarps * kWsConsumerRegs <=
+                  kWsThreads * kWsRegs,
+              "register split exceeds the launch's registers");
+
+MC_D unsigned long long ws_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the completion of the mbarrier phase of the given parity; false
+// after kWsWaitNs.
+MC_D bool ws_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = ws_clock_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (ws_clock_ns() - t0 > kWsWaitNs) return false;
+  return true;
+}
+
+// Dynamic shared memory of one block: the ring, then the histograms, the
+// grid edges and the PDF tables (as in the per-thread fused kernel).
+inline size_t ws_smem_bytes(int ndim, int nbins, int nx) {
+  const size_t ring = size_t(kWsSlots) * kWsWords * 32 * 4;
+  const size_t hist = ((size_t(ndim) * nbins * 8 + 15) / 16) * 16;
+  return ring + hist + 4 * (size_t(ndim) * (nbins + 1) + size_t(nx) * 3);
+}
+
+template <int PROC>
+__global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs a) {
+  static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D, "gg -> t tbar g only");
+  constexpr int MAXD = ProcTraits<PROC>::MAXD;
+  constexpr int NW = (MAXD + 3) / 4;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kWsSlots], empty[kWsSlots];
+  __shared__ int count[kWsSlots];
+  __shared__ int failed;
+  __shared__ BlockPartial warp_part[kWsThreads / 32];
+  const int ndim = a.ndim, nb = a.nbins;
+  const int nedge = ndim * (nb + 1), nhist = ndim * nb;
+  uint32_t* ring = reinterpret_cast<uint32_t*>(smem);
+  unsigned char* rest = smem + size_t(kWsSlots) * kWsWords * 32 * 4;
+  float* sh_w2 = reinterpret_cast<float*>(rest);
+  unsigned int* sh_n = reinterpret_cast<unsigned int*>(rest + size_t(nhist) * 4);
+  float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
+  float* sh_pdf = sh_edges + nedge;
+
+  for (int i = threadIdx.x; i < nedge; i += blockDim.x) sh_edges[i] = a.edges32[i];
+  for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
+    sh_w2[i] = 0.0f;
+    sh_n[i] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWsSlots; ++s) {
+      mbar_init(&full[s], 32);
+      mbar_init(&empty[s], 32);
+    }
+    failed = 0;
+  }
+  SmPdf<float> pdf;
+  {
+    const int nx = a.pdf.nx;
+    float* t = sh_pdf;
+    float* f = t + nx;
+    float* d = f + nx;
+    build_pdf_tables<float>(a.pdf, a.logq2_f, a.fl, 1, t, f, d);  // ends with __syncthreads
+    pdf.tab[0] = {t, f, d, nx};
+  }
+
+  Acc acc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool ok = true;
+  if (warp < kWsProducerWarps) {
+    // ------------------------------------------------------------- producer
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
+    const int p = warp;
+    auto slot_of = [&](int q) { return p + kWsProducerWarps * (q & 3); };
+    auto acquire = [&](int q) -> bool {
+      const int u = q >> 2;  // earlier uses of this slot
+      return u == 0 || ws_wait(&empty[slot_of(q)], uint32_t(u - 1) & 1u);
+    };
+    auto publish = [&](int q, int cnt) {
+      if (lane == 0) count[slot_of(q)] = cnt;
+      mbar_arrive(&full[slot_of(q)]);
+    };
+    const long long nchunks = (a.n + 31) / 32;
+    const long long G = (long long)gridDim.x * kWsProducerWarps;
+    int seq = 0, fill = 0;
+    bool next_held = false;
+    ok = acquire(0);
+    for (long long chunk = (long long)blockIdx.x * kWsProducerWarps + p; ok && chunk < nchunks; chunk += G) {
+      const long long i = chunk * 32 + lane;
+      GgKin<float> kin;
+      uint32_t binw[NW];
+#pragma unroll
+      for (int j = 0; j < NW; ++j) binw[j] = 0u;
+      float jac = 1.0f;
+      int st = 0;
+      if (i < a.n) {
+        uint64_t k[MAXD];
+        event_uniforms<MAXD, false>(a.seed, a.iteration, a.gid, a.first + uint64_t(i), ndim, k);
+        float x[MAXD];
+#pragma unroll
+        for (int dd = 0; dd < MAXD; ++dd) {
+          if (dd < ndim) {
+            int b;
+            float jd;
+            x[dd] = vegas_map_1d<float, false>(sh_edges + dd * (nb + 1), nb, k[dd], &b, &jd);
+            binw[dd / 4] |= uint32_t(b) << (8 * (dd % 4));
+            jac *= jd;
+            atomicAdd(&sh_n[dd * nb + b], 1u);
+          }
+        }
+        st = gg_kinematics<PROC, float>(a, pdf, x, &kin, nullptr);
+        if (st == -5) ++acc.nnoconv;
+      }
+      const bool pass = st == 1;
+      const unsigned m = __ballot_sync(0xffffffffu, pass);
+      const int tot = __popc(m);
+      if (fill + tot > 32 && !next_held) {
+        ok = acquire(seq + 1);
+        next_held = true;
+        if (!ok) break;
+      }
+      if (pass) {
+        const int pos = fill + __popc(m & ((1u << lane) - 1u));
+        uint32_t* r = ring + size_t(slot_of(pos < 32 ? seq : seq + 1)) * kWsWords * 32 + (pos & 31);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          r[(kWK + 4 * j + 0) * 32] = __float_as_uint(kin.k[j].e);
+          r[(kWK + 4 * j + 1) * 32] = __float_as_uint(kin.k[j].x);
+          r[(kWK + 4 * j + 2) * 32] = __float_as_uint(kin.k[j].y);
+          r[(kWK + 4 * j + 3) * 32] = __float_as_uint(kin.k[j].z);
+        }
+        r[kWRs * 32] = __float_as_uint(kin.rs);
+        r[kWLgg * 32] = __float_as_uint(kin.lgg);
+        r[kWFlux * 32] = __float_as_uint(kin.flux);
+        r[kWJac * 32] = __float_as_uint(jac);
+        r[kWPsw * 32] = __double2loint(kin.psw);
+        r[(kWPsw + 1) * 32] = __double2hiint(kin.psw);
+#pragma unroll
+        for (int j = 0; j < NW; ++j) r[(kWBin + j) * 32] = binw[j];
+      }
+      fill += tot;
+      if (fill >= 32) {
+        publish(seq, 32);
+        ++seq;
+        fill -= 32;
+        if (!next_held) ok = acquire(seq);
+        next_held = false;
+      }
+    }
+    if (ok) {
+      publish(seq, fill);  // the last, partial slot (possibly empty)
+      for (int e = 1; e <= 2 && ok; ++e) {
+        ok = acquire(seq + e);
+        if (ok) publish(seq + e, -1);
+      }
+    }
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsRegs));
+  } else {
+    // ------------------------------------------------------------- consumer
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
+    const int c = warp - kWsProducerWarps;
+    const int p = c % kWsProducerWarps, cls = c / kWsProducerWarps;
+    for (int q = cls;; q += 2) {
+      const int s = p + kWsProducerWarps * (q & 3);
+      if (!ws_wait(&full[s], uint32_t(q >> 2) & 1u)) {
+        ok = false;
+        break;
+      }
+      const int cnt = count[s];
+      if (cnt < 0) break;
+      if (lane < cnt) {
+        const uint32_t* r = ring + size_t(s) * kWsWords * 32 + lane;
+        GgKin<float> kin;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          kin.k[j] = {__uint_as_float(r[(kWK + 4 * j + 0) * 32]), __uint_as_float(r[(kWK + 4 * j + 1) * 32]),
+                      __uint_as_float(r[(kWK + 4 * j + 2) * 32]), __uint_as_float(r[(kWK + 4 * j + 3) * 32])};
+        kin.rs = __uint_as_float(r[kWRs * 32]);
+        kin.lgg = __uint_as_float(r[kWLgg * 32]);
+        kin.flux = __uint_as_float(r[kWFlux * 32]);
+        const float jac = __uint_as_float(r[kWJac * 32]);
+        kin.psw = __hiloint2double(int(r[(kWPsw + 1) * 32]), int(r[kWPsw * 32]));
+        uint32_t binw[NW];
+#pragma unroll
+        for (int j = 0; j < NW; ++j) binw[j] = r[(kWBin + j) * 32];
+        const float me2 = gg_me2<float>(a, kin);
+        double w = gg_weight<float>(a, kin, me2) * double(jac);
+        if (!isfinite(w)) {
+          ++acc.nbad;
+          w = 0.0;
+        }
+        const double y = w - acc.s_c;
+        const double t = acc.s_hi + y;
+        acc.s_c = (t - acc.s_hi) - y;
+        acc.s_hi = t;
+        const double w2 = w * w;
+        const double y2 = w2 - acc.q_c;
+        const double t2 = acc.q_hi + y2;
+        acc.q_c = (t2 - acc.q_hi) - y2;
+        acc.q_hi = t2;
+        if (w != 0.0) ++acc.nnz;
+        acc.wmax = fmax(acc.wmax, w);
+#pragma unroll
+        for (int dd = 0; dd < MAXD; ++dd)
+          if (dd < ndim) atomicAdd(&sh_w2[dd * nb + int((binw[dd / 4] >> (8 * (dd % 4))) & 0xffu)], float(w2));
+      }
+      mbar_arrive(&empty[s]);
+    }
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
+  }
+  if (!ok) atomicExch(&failed, 1);
+  __syncthreads();
+  block_reduce(acc, warp_part, &a.partials[blockIdx.x]);
+  if (threadIdx.x == 0 && failed) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    a.partials[blockIdx.x].sum_hi = nan;
+    a.partials[blockIdx.x].sum2_hi = nan;
+    a.partials[blockIdx.x].n_bad += 1;
+    if (a.status) atomicExch(a.status, MC_ETIMEOUT);
+  }
+  for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
+    if (sh_n[i]) {
+      atomicAdd(&a.hist_n[i], sh_n[i]);
+      atomicAdd(&a.hist_w2[i], double(sh_w2[i]));
+    }
+  }
+}
+
+}  // namespace mc
