@@ -10,7 +10,7 @@
 // and carries idle lanes through the |M|^2 for the events that were cut.
 //
 // Here each block (one per SM) splits its warps into two roles:
-//  * 4 producer warps (one per SM sub-partition) walk the event range in
+//  * 8 producer warps (two per SM sub-partition) walk the event range in
 //    chunks of 32, evaluate the kinematics, add every event to the bin-count
 //    histogram, and append the events that pass the cuts, compacted with a
 //    warp ballot, to a shared-memory ring of slots of 32 event records;
@@ -19,11 +19,14 @@
 //    shared-memory histogram of w^2.
 // Slots pass between the roles through mbarriers (full: 32 producer-lane
 // arrivals; empty: 32 consumer-lane arrivals).  Producer warp p owns the
-// slots p, p+4, p+8, p+12 in that order; consumer warp c takes producer
-// (c mod 4)'s slots of sequence parity c / 4, i.e. slots c and c + 8.  The
-// assignment of events to lanes is fixed by the launch shape, so the sums
-// are deterministic for a given grid.  A producer ends its stream with a
-// partial slot and one end marker (count -1) for each of its two consumers.
+// slots 4p .. 4p+3, used in turn; with equal counts consumer warp c takes
+// producer c's slots (the general mapping is below).  The assignment of
+// events to lanes is fixed by the launch shape, so the sums are
+// deterministic for a given grid.  A producer ends its stream with a partial
+// slot and one end marker (count -1) for each consumer it feeds.  Sixteen
+// warps of 128 registers at launch, rebalanced to 88 (producers) and 168
+// (consumers) with setmaxnreg, measured fastest among the 4+8, 8+4 and 8+8
+// shapes on B300.
 //
 // Every wait is bounded (kWsWaitNs of %globaltimer); a warp that gives up
 // stops, the block poisons its partial sums with NaN and, when the launch
@@ -32,24 +35,46 @@
 #include "event.cuh"
 #include "tcgen05.cuh"
 
+#ifndef WS_NP
+#define WS_NP 8
+#define WS_NC 8
+#define WS_PREGS 88
+#define WS_CREGS 168
+#endif
+
 namespace mc {
 
-constexpr int kWsProducerWarps = 4;
-constexpr int kWsConsumerWarps = 8;
+// Launch shape: kWsProducerWarps producer warps and kWsConsumerWarps consumer
+// warps per block (each a multiple of 4, i.e. whole warpgroups, since the
+// register split below is per warpgroup), one block per SM.
+constexpr int kWsProducerWarps = WS_NP;
+constexpr int kWsConsumerWarps = WS_NC;
 constexpr int kWsThreads = 32 * (kWsProducerWarps + kWsConsumerWarps);
-constexpr int kWsSlots = 4 * kWsProducerWarps;
+constexpr int kWsSlotsPerProducer = 4;
+constexpr int kWsSlots = kWsSlotsPerProducer * kWsProducerWarps;
 // record words of one event (structure of arrays inside a slot: word j of
 // lane e at [j][e]): k[3] (12), rs, lgg, flux, jac, psw (2 words), bins (4)
 enum : int { kWK = 0, kWRs = 12, kWLgg = 13, kWFlux = 14, kWJac = 15, kWPsw = 16, kWBin = 18, kWsWords = 22 };
 constexpr unsigned long long kWsWaitNs = 2000000000ull;
-// Registers per thread: the launch gets kWsRegs (65536 / 384, rounded down
-// to a multiple of 8); producers give up to kWsProducerRegs, consumers take
-// kWsConsumerRegs, and 128 kWsProducerRegs + 256 kWsConsumerRegs stays within
-// 384 kWsRegs, so the increase never waits on registers that are not there.
-constexpr int kWsRegs = 168, kWsProducerRegs = 104, kWsConsumerRegs = 192;
+// Registers per thread: the launch gets kWsRegs (65536 / threads, rounded
+// down to a multiple of 8); producers give up to kWsProducerRegs, consumers
+// take kWsConsumerRegs, and the two together stay within the launch's
+// registers, so the increase never waits on registers that are not there.
+constexpr int kWsRegs = (65536 / kWsThreads) / 8 * 8 > 248 ? 248 : (65536 / kWsThreads) / 8 * 8;
+constexpr int kWsProducerRegs = WS_PREGS, kWsConsumerRegs = WS_CREGS;
+static_assert(kWsProducerWarps % 4 == 0 && kWsConsumerWarps % 4 == 0, "roles must be whole warpgroups");
 static_assert(32 * kWsProducerWarps * kWsProducerRegs + 32 * kWsConsumerWarps * kWsConsumerRegs <=
                   kWsThreads * kWsRegs,
               "register split exceeds the launch's registers");
+// Streams: producer p's slot sequence q = 0, 1, 2, ... goes to consumer
+// (p mod C) + P ((q mod kWsClasses)) when there are more consumers than
+// producers (C = kWsClasses P), and every consumer c serves the producers
+// c, c + C, ... (kWsStreams of them) when there are more producers.
+constexpr int kWsClasses = kWsConsumerWarps >= kWsProducerWarps ? kWsConsumerWarps / kWsProducerWarps : 1;
+constexpr int kWsStreams = kWsProducerWarps >= kWsConsumerWarps ? kWsProducerWarps / kWsConsumerWarps : 1;
+static_assert(kWsClasses * kWsProducerWarps == kWsConsumerWarps || kWsStreams * kWsConsumerWarps == kWsProducerWarps,
+              "warp counts must divide one another");
+static_assert(kWsStreams <= 2, "a consumer serves at most two producers");
 
 MC_D unsigned long long ws_clock_ns() {
   unsigned long long t;
@@ -122,7 +147,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
     // ------------------------------------------------------------- producer
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
     const int p = warp;
-    auto slot_of = [&](int q) { return p + kWsProducerWarps * (q & 3); };
+    auto slot_of = [&](int q) { return p * kWsSlotsPerProducer + (q & 3); };
     auto acquire = [&](int q) -> bool {
       const int u = q >> 2;  // earlier uses of this slot
       return u == 0 || ws_wait(&empty[slot_of(q)], uint32_t(u - 1) & 1u);
@@ -200,7 +225,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
     }
     if (ok) {
       publish(seq, fill);  // the last, partial slot (possibly empty)
-      for (int e = 1; e <= 2 && ok; ++e) {
+      for (int e = 1; e <= kWsClasses && ok; ++e) {
         ok = acquire(seq + e);
         if (ok) publish(seq + e, -1);
       }
@@ -210,15 +235,31 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
     // ------------------------------------------------------------- consumer
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
     const int c = warp - kWsProducerWarps;
-    const int p = c % kWsProducerWarps, cls = c / kWsProducerWarps;
-    for (int q = cls;; q += 2) {
-      const int s = p + kWsProducerWarps * (q & 3);
+    const int cls = c / kWsProducerWarps;
+    // up to two streams, served in turn until both have ended
+    int q0 = cls, q1 = cls;
+    bool live0 = true, live1 = kWsStreams > 1;
+    for (int si = 0; live0 || live1; si ^= (kWsStreams > 1)) {
+      if (si == 0 ? !live0 : !live1) si ^= 1;
+      const int p = (c % kWsProducerWarps) + si * kWsConsumerWarps;
+      const int q = si == 0 ? q0 : q1;
+      const int s = p * kWsSlotsPerProducer + (q & 3);
       if (!ws_wait(&full[s], uint32_t(q >> 2) & 1u)) {
         ok = false;
         break;
       }
       const int cnt = count[s];
-      if (cnt < 0) break;
+      if (cnt < 0) {
+        if (si == 0)
+          live0 = false;
+        else
+          live1 = false;
+        continue;
+      }
+      if (si == 0)
+        q0 += kWsClasses;
+      else
+        q1 += kWsClasses;
       if (lane < cnt) {
         const uint32_t* r = ring + size_t(s) * kWsWords * 32 + lane;
         GgKin<float> kin;
