@@ -42,11 +42,18 @@ ALPHA = 1.5
 WORKLOAD = ("gg->ttg 13 TeV, RAMBO 2+12 dims (7 physical), gluon pT>20 GeV |eta|<2.5, synthetic 100x40x11 "
             "PDF grid, FP32 helicity |M|^2 + Kahan FP64 sums, VEGAS 50 bins, 1e7 events/iteration")
 METRIC = "events/sec and GPU time to 1e-3 rel. error: FP32+flow vs plain FP64 VEGAS"
-# FP32 floating-point operations per evaluated gg -> ttg event of the fused
-# kernel (|M|^2 with 32 helicity configurations, RAMBO, PDFs, map), counted by
-# ncu as fadd + fmul + 2 ffma over one launch divided by the number of
-# evaluated (in-cut) events; see profiles/.
-FLOP_PER_EVENT = 24978.0
+# FP32 floating-point operations per in-cut gg -> ttg event of the
+# warp-specialised fused kernel (packed |M|^2 over 16 polarisation
+# configurations, RAMBO, PDFs and the map of every event, in-cut or not),
+# counted by ncu over one full-size launch of this workload as
+# 2 ffma + fmul + fadd + 4 ffma2 + 2 fmul2 + 2 fadd2 (1.806e11 FLOP) divided by
+# the launch's 8 049 119 in-cut events; see profiles/.
+FLOP_PER_EVENT = 22434.0
+# DRAM bytes (read + write) of one launch of that kernel, from an ncu capture
+# of this workload (0.46 MB read + 2.18 MB written; see profiles/).  Nothing
+# per event reaches DRAM: the kernel reads the grid and the PDF grid and
+# writes histograms and per-block partials.
+TRAFFIC_BYTES = 2643712
 FP32_LANES_PER_SM = 128
 # time to a target relative error (gg -> t tbar g, 7 sampled dimensions):
 # FP32 + normalizing flow (6 coupling layers, 32 bins, 3 x 256 BF16 hidden
@@ -122,10 +129,16 @@ def cpu_baseline(seconds=15.0, iteration=3):
     itg = W.gg_ttbarg()
     edges = W.uniform_grid(14, NBINS)
     cores = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    n0 = 200 * cores
-    O.iterate(itg, pdf, edges, 1, 0, iteration, 0, 0, n0, nthreads=cores)
-    dt = time.perf_counter() - t0
+    # calibrate on samples of at least a second (thread start-up dominates
+    # smaller ones), then time a sample of about `seconds`
+    n0, dt = 200 * cores, 0.0
+    while True:
+        t0 = time.perf_counter()
+        O.iterate(itg, pdf, edges, 1, 0, iteration, 0, 0, n0, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt >= 1.0 or n0 >= 1 << 30:
+            break
+        n0 *= 4
     n = max(n0, int(n0 * seconds / max(dt, 1e-3)))
     t0 = time.perf_counter()
     O.iterate(itg, pdf, edges, 1, 0, iteration, 0, n0, n, nthreads=cores)
@@ -413,7 +426,7 @@ def run_native(args, rank, world):
     if FLOP_PER_EVENT:
         achieved = FLOP_PER_EVENT * mean_nnz / (mean_kernel_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+                "frac": achieved / fp32_peak, "traffic": TRAFFIC_BYTES,
                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
