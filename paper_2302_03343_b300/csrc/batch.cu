@@ -11,6 +11,12 @@
 // sequence of launches that is captured once in a CUDA graph and replayed.
 // Block size and events per thread are chosen by timing candidate launch
 // shapes on the batch itself (autotune()).
+//
+// In FP32 mode the batch runs batch_ws_kernel instead: one block of
+// kWsThreads per SM; a tile of gg -> t tbar g events goes through the
+// warp-specialised producer/consumer path of ws_integrand.cuh (each tile
+// ends every producer stream with end markers, so the ring is empty between
+// tiles), any other tile through all threads of the block one event each.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -21,6 +27,7 @@
 #include "event.cuh"
 #include "handles.h"
 #include "refine.cuh"
+#include "ws_integrand.cuh"
 
 namespace mc {
 
@@ -45,6 +52,7 @@ struct BatchArgs {
   double logq2_f;
   int fl[11];
   BlockPartial* tile_partials;
+  int* status;  // MC_ETIMEOUT when a bounded wait of the launch gave up (warp-specialised kernel)
 };
 
 template <bool FP64, int BLOCK>
@@ -138,6 +146,143 @@ __global__ void __launch_bounds__(BLOCK) batch_kernel(BatchArgs b) {
     block_reduce(acc, warp_part, &b.tile_partials[tile]);  // ends with __syncthreads
   }
   if (cur >= 0) flush(cur);
+}
+
+// FP32 batch kernel with the warp-specialised path for gg -> t tbar g tiles.
+__global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kWsSlots], empty[kWsSlots];
+  __shared__ int count[kWsSlots];
+  __shared__ int failed;
+  __shared__ KernelArgs ka;
+  __shared__ int sh_tile;
+  __shared__ BlockPartial warp_part[kWsThreads / 32];
+  const int nb = b.nbins;
+  const int nhist = MC_MAX_DIM * nb, nedge = MC_MAX_DIM * (nb + 1);
+  const WsRing ring = {reinterpret_cast<uint32_t*>(smem), full, empty, count};
+  unsigned char* rest = smem + size_t(kWsSlots) * kWsWords * 32 * 4;
+  float* sh_w2 = reinterpret_cast<float*>(rest);
+  unsigned int* sh_n = reinterpret_cast<unsigned int*>(rest + size_t(nhist) * 4);
+  float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
+  float* sh_pdf = sh_edges + nedge;
+
+  for (int i = threadIdx.x; i < nhist; i += kWsThreads) {
+    sh_w2[i] = 0.0f;
+    sh_n[i] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWsSlots; ++s) {
+      mbar_init(&full[s], 32);
+      mbar_init(&empty[s], 32);
+    }
+    failed = 0;
+  }
+  SmPdf<float> pdf;
+  if (b.has_pdf) {
+    const int nx = b.pdf.nx;
+    float* t = sh_pdf;
+    float* f = t + nx;
+    float* d = f + 11 * nx;
+    build_pdf_tables<float>(b.pdf, b.logq2_f, b.fl, 11, t, f, d);  // ends with __syncthreads
+#pragma unroll
+    for (int k = 0; k < 11; ++k) pdf.tab[k] = {t, f + k * nx, d + k * nx, nx};
+  } else {
+    __syncthreads();
+  }
+  const unsigned int iteration = *b.iteration;
+  const int warp = threadIdx.x >> 5;
+  int cur = -1;
+  auto flush = [&](int item) {
+    const BatchItem& it = b.items[item];
+    const int n = it.args.ndim * nb;
+    for (int i = threadIdx.x; i < n; i += kWsThreads) {
+      if (sh_n[i]) {
+        atomicAdd(&it.args.hist_n[i], sh_n[i]);
+        atomicAdd(&it.args.hist_w2[i], double(sh_w2[i]));
+      }
+      sh_w2[i] = 0.0f;
+      sh_n[i] = 0u;
+    }
+  };
+  // slot sequence numbers, carried over from tile to tile
+  int seq = 0;
+  int q0 = (warp - kWsProducerWarps) / kWsProducerWarps, q1 = q0;
+  for (;;) {
+    if (threadIdx.x == 0) sh_tile = int(atomicAdd(b.counter, 1u));
+    __syncthreads();
+    const int tile = sh_tile;
+    if (tile >= b.ntiles) break;
+    const int item = b.tile_item[tile];
+    if (item != cur) {
+      if (cur >= 0) flush(cur);
+      const BatchItem& it = b.items[item];
+      if (threadIdx.x == 0) {
+        ka = it.args;
+        ka.iteration = iteration;
+      }
+      const int ne = it.args.ndim * (nb + 1);
+      for (int i = threadIdx.x; i < ne; i += kWsThreads) sh_edges[i] = it.args.edges32[i];
+      cur = item;
+    }
+    __syncthreads();
+    const BatchItem& it = b.items[item];
+    const long long start = (long long)(tile - it.first_tile) * b.tile_events;
+    const long long end = min(start + (long long)b.tile_events, it.nevents);
+    Acc acc;
+    bool ok = true;
+    if (it.proc == P_GG_TTBARG || it.proc == P_GG_TTBARG_7D) {
+      if (warp < kWsProducerWarps) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
+        ok = it.proc == P_GG_TTBARG
+                 ? ws_produce<P_GG_TTBARG>(ka, pdf, sh_edges, sh_n, ring, warp, start, end, warp, kWsProducerWarps,
+                                           seq, acc)
+                 : ws_produce<P_GG_TTBARG_7D>(ka, pdf, sh_edges, sh_n, ring, warp, start, end, warp,
+                                              kWsProducerWarps, seq, acc);
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsRegs));
+      } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
+        const int c = warp - kWsProducerWarps;
+        ok = it.proc == P_GG_TTBARG ? ws_consume<P_GG_TTBARG>(ka, sh_w2, ring, c, q0, q1, acc)
+                                    : ws_consume<P_GG_TTBARG_7D>(ka, sh_w2, ring, c, q0, q1, acc);
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
+      }
+    } else {
+      switch (it.proc) {
+        case P_EE_MUMU:
+          for (long long i = start + threadIdx.x; i < end; i += kWsThreads)
+            process_event<P_EE_MUMU, false, false, float, float>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i), nullptr,
+                                                                 acc);
+          break;
+        case P_PP_TTBAR:
+          for (long long i = start + threadIdx.x; i < end; i += kWsThreads)
+            process_event<P_PP_TTBAR, false, false, float, float>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i),
+                                                                  nullptr, acc);
+          break;
+        default:
+          for (long long i = start + threadIdx.x; i < end; i += kWsThreads)
+            process_event<P_GAUSS, false, false, float, float>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i), nullptr,
+                                                               acc);
+      }
+    }
+    if (!ok) atomicExch(&failed, 1);
+    block_reduce(acc, warp_part, &b.tile_partials[tile]);  // ends with __syncthreads
+    if (failed) {
+      if (threadIdx.x == 0) {
+        b.tile_partials[tile].sum_hi = __longlong_as_double(0x7ff8000000000000LL);
+        if (b.status) atomicExch(b.status, MC_ETIMEOUT);
+      }
+      break;  // the ring is no longer consistent: stop this block
+    }
+  }
+  if (cur >= 0) flush(cur);
+}
+
+cudaError_t launch_batch_ws(const BatchArgs& b, int grid, size_t smem, cudaStream_t st) {
+  (void)cudaGetLastError();
+  const cudaError_t e = cudaFuncSetAttribute(batch_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  batch_ws_kernel<<<grid, kWsThreads, smem, st>>>(b);
+  return cudaGetLastError();
 }
 
 // One block per integrand: fixed-order reduction of its tile partials.
@@ -256,6 +401,7 @@ struct mc_batch_s {
   int max_tiles = 0;
   // launch shape (autotuned)
   int block = 128, events_per_thread = 8, ntiles = 0, grid = 0;
+  bool ws = false;  // FP32: the warp-specialised batch kernel
   size_t smem = 0;
   BatchArgs args{};
   std::vector<BatchItem> h_items;
@@ -302,9 +448,12 @@ int build_tiles(mc_batch b) {
   const size_t nhist = size_t(MC_MAX_DIM) * b->nbins;
   b->smem = ((nhist * 12 + 15) / 16) * 16 + r * (size_t(MC_MAX_DIM) * (b->nbins + 1)) +
             (b->pdf ? r * size_t(b->pdf->nx) * 23 : 0);
+  if (b->ws)
+    b->smem = size_t(mc::kWsSlots) * mc::kWsWords * 32 * 4 + ((nhist * 8 + 15) / 16) * 16 +
+              4 * (size_t(MC_MAX_DIM) * (b->nbins + 1)) + (b->pdf ? 4 * size_t(b->pdf->nx) * 23 : 0);
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  const int per_sm = mc::batch_blocks_per_sm(fp64, b->block, b->smem);
+  const int per_sm = b->ws ? 1 : mc::batch_blocks_per_sm(fp64, b->block, b->smem);
   b->grid = std::max(1, std::min(sms * per_sm, b->ntiles));
   BatchArgs& a = b->args;
   a.items = b->d_items;
@@ -315,6 +464,7 @@ int build_tiles(mc_batch b) {
   a.iteration = b->d_iteration;
   a.nbins = b->nbins;
   a.tile_partials = b->d_tile_partials;
+  a.status = reinterpret_cast<int*>(b->d_results + b->n);
   return MC_OK;
 }
 
@@ -330,10 +480,13 @@ void drop_graph(mc_batch b) {
 int enqueue_iteration(mc_batch b, cudaStream_t st, bool with_refine, bool captured) {
   const bool fp64 = b->prec == MC_FP64;
   const unsigned int flags = captured ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (cudaMemsetAsync(b->args.status, 0, sizeof(int), st) != cudaSuccess)
+    return bfail(MC_ECUDA, "mc_batch: status reset failed");
   if (cudaEventRecordWithFlags(b->k0, st, flags) != cudaSuccess)
     return bfail(MC_ECUDA, "mc_batch: event record failed");
-  if (mc::launch_batch(fp64, b->block, b->args, b->grid, b->smem, st) != cudaSuccess)
-    return bfail(MC_ECUDA, "mc_batch: batch kernel launch failed");
+  const cudaError_t le = b->ws ? mc::launch_batch_ws(b->args, b->grid, b->smem, st)
+                               : mc::launch_batch(fp64, b->block, b->args, b->grid, b->smem, st);
+  if (le != cudaSuccess) return bfail(MC_ECUDA, "mc_batch: batch kernel launch failed");
   if (cudaEventRecordWithFlags(b->k1, st, flags) != cudaSuccess)
     return bfail(MC_ECUDA, "mc_batch: event record failed");
   mc::batch_finalize_kernel<<<b->n, 256, 0, st>>>(b->d_items, b->d_tile_partials, b->d_results);
@@ -342,7 +495,7 @@ int enqueue_iteration(mc_batch b, cudaStream_t st, bool with_refine, bool captur
     mc::batch_refine_kernel<<<b->n, 32 * MC_MAX_DIM, smem, st>>>(b->d_items, b->d_alpha, b->nbins);
   }
   mc::batch_advance_kernel<<<1, 1, 0, st>>>(b->d_counter, b->d_iteration);
-  if (cudaMemcpyAsync(b->h_results, b->d_results, sizeof(BlockPartial) * b->n, cudaMemcpyDeviceToHost, st) !=
+  if (cudaMemcpyAsync(b->h_results, b->d_results, sizeof(BlockPartial) * (b->n + 1), cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)
     return bfail(MC_ECUDA, "mc_batch: result copy failed");
   if (cudaGetLastError() != cudaSuccess) return bfail(MC_ECUDA, "mc_batch: launch failed");
@@ -356,7 +509,7 @@ int autotune(mc_batch b, cudaStream_t st) {
   static const int kBlocks[] = {64, 128, 256};
   static const int kEpt[] = {2, 8, 32};
   float best = 1e30f;
-  int best_b = 128, best_e = 8;
+  int best_b = b->ws ? mc::kWsThreads : 128, best_e = b->ws ? 16 : 8;
   unsigned int it0 = 0;
   cudaMemcpy(&it0, b->d_iteration, sizeof(unsigned int), cudaMemcpyDeviceToHost);
   const size_t smem_r = sizeof(double) * MC_MAX_DIM * (3 * b->nbins + 2);
@@ -364,10 +517,17 @@ int autotune(mc_batch b, cudaStream_t st) {
       cudaFuncSetAttribute(mc::batch_refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_r)) !=
           cudaSuccess)
     return bfail(MC_ECUDA, "mc_batch: refine kernel attribute");
+  // warp-specialised kernel: one block shape, tiles of 4, 16 or 64 events per thread
+  static const int kBlocksWs[] = {mc::kWsThreads};
+  static const int kEptWs[] = {4, 16, 64};
+  const int nbl = b->ws ? 1 : 3, nep = 3;
+  const int* blocks = b->ws ? kBlocksWs : kBlocks;
+  const int* epts = b->ws ? kEptWs : kEpt;
   for (int pass = 0; pass < 2; ++pass) {  // pass 0 warms up the first shape
-    for (int bl : kBlocks)
-      for (int ep : kEpt) {
-        if (pass == 0 && !(bl == 128 && ep == 8)) continue;
+    for (int ib = 0; ib < nbl; ++ib)
+      for (int ie = 0; ie < nep; ++ie) {
+        const int bl = blocks[ib], ep = epts[ie];
+        if (pass == 0 && !(ib == nbl / 2 && ie == 1)) continue;
         b->block = bl;
         b->events_per_thread = ep;
         if (int rc = build_tiles(b)) return rc;
@@ -434,6 +594,11 @@ int mc_batch_create(int n, const mc_integrand* itgs, const int64_t* nevents, mc_
   b->prec = prec;
   b->seed = seed;
   b->pdf = pdf;
+  b->ws = prec == MC_FP32_KAHAN;
+  if (b->ws) {
+    b->block = mc::kWsThreads;
+    b->events_per_thread = 16;
+  }
   b->itg.assign(itgs, itgs + n);
   double logq2 = 0.0;
   bool have_mu = false;
@@ -480,11 +645,11 @@ int mc_batch_create(int n, const mc_integrand* itgs, const int64_t* nevents, mc_
       (e = cudaMalloc(&b->d_items, sizeof(BatchItem) * n)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_tile_item, sizeof(int) * b->max_tiles)) != cudaSuccess ||
       (e = cudaMalloc(&b->d_tile_partials, sizeof(BlockPartial) * b->max_tiles)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_results, sizeof(BlockPartial) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_results, sizeof(BlockPartial) * (n + 1))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_counter, sizeof(unsigned int))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_iteration, sizeof(unsigned int))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_alpha, sizeof(double))) != cudaSuccess ||
-      (e = cudaMallocHost(&b->h_results, sizeof(BlockPartial) * n)) != cudaSuccess ||
+      (e = cudaMallocHost(&b->h_results, sizeof(BlockPartial) * (n + 1))) != cudaSuccess ||
       (e = cudaMallocHost(&b->h_alpha, sizeof(double))) != cudaSuccess ||
       (e = cudaEventCreate(&b->k0)) != cudaSuccess || (e = cudaEventCreate(&b->k1)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -598,6 +763,8 @@ int mc_batch_iterate(mc_batch b, double alpha, void* stream, mc_iter_result* out
     return bfail(MC_ECUDA, "mc_batch_iterate: alpha upload failed");
   if (cudaGraphLaunch(b->exec, st) != cudaSuccess) return bfail(MC_ECUDA, "mc_batch_iterate: graph launch failed");
   if (cudaStreamSynchronize(st) != cudaSuccess) return bfail(MC_ECUDA, "mc_batch_iterate: iteration failed");
+  if (*reinterpret_cast<const int*>(b->h_results + b->n) != 0)
+    return bfail(MC_ETIMEOUT, "mc_batch_iterate: a bounded wait inside the batch kernel gave up");
   for (int i = 0; i < b->n; ++i) {
     const BlockPartial& t = b->h_results[i];
     mc_iter_result& r = out[i];

@@ -99,11 +99,192 @@ inline size_t ws_smem_bytes(int ndim, int nbins, int nx) {
   return ring + hist + 4 * (size_t(ndim) * (nbins + 1) + size_t(nx) * 3);
 }
 
+// Shared-memory ring of one block: kWsSlots slots of 32 event records, their
+// full/empty mbarriers and counts (-1 = end marker).
+struct WsRing {
+  uint32_t* rec;   // [kWsSlots][kWsWords][32]
+  uint64_t* full;  // [kWsSlots], arrival count 32 (the producer's lanes)
+  uint64_t* empty;  // [kWsSlots], arrival count 32 (the consumer's lanes)
+  int* count;      // [kWsSlots]
+};
+
+// Producer warp p (0 <= p < kWsProducerWarps): evaluates the kinematics of the
+// events [lo, hi) of the integrand in chunks of 32 (chunk k = events
+// lo + 32 k .. lo + 32 k + 31; this warp takes chunks k0, k0 + dk, ...), adds
+// every event to the bin counts, appends the events that pass the cuts to its
+// slots, and ends the stream with a partial slot and one end marker per
+// consumer it feeds.  seq is the warp's slot sequence number and carries
+// over between calls (the slot of seq is p * 4 + seq % 4, used for the
+// (seq / 4)-th time).  The Philox event index is a.first + i.  Returns false
+// when a wait gave up.
+template <int PROC>
+MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* sh_edges, unsigned int* sh_n,
+                     const WsRing& ring, int p, long long lo, long long hi, long long k0, long long dk, int& seq,
+                     Acc& acc) {
+  constexpr int MAXD = ProcTraits<PROC>::MAXD;
+  constexpr int NW = (MAXD + 3) / 4;
+  const int lane = threadIdx.x & 31;
+  const int ndim = a.ndim, nb = a.nbins;
+  auto slot_of = [&](int q) { return p * kWsSlotsPerProducer + (q & 3); };
+  auto acquire = [&](int q) -> bool {
+    const int u = q >> 2;  // earlier uses of this slot
+    return u == 0 || ws_wait(&ring.empty[slot_of(q)], uint32_t(u - 1) & 1u);
+  };
+  auto publish = [&](int q, int cnt) {
+    if (lane == 0) ring.count[slot_of(q)] = cnt;
+    mbar_arrive(&ring.full[slot_of(q)]);
+  };
+  const long long nchunks = (hi - lo + 31) / 32;
+  int fill = 0;
+  bool next_held = false;
+  bool ok = acquire(seq);
+  for (long long chunk = k0; ok && chunk < nchunks; chunk += dk) {
+    const long long i = lo + chunk * 32 + lane;
+    GgKin<float> kin;
+    uint32_t binw[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) binw[j] = 0u;
+    float jac = 1.0f;
+    int st = 0;
+    if (i < hi) {
+      uint64_t k[MAXD];
+      event_uniforms<MAXD, false>(a.seed, a.iteration, a.gid, a.first + uint64_t(i), ndim, k);
+      float x[MAXD];
+#pragma unroll
+      for (int dd = 0; dd < MAXD; ++dd) {
+        if (dd < ndim) {
+          int b;
+          float jd;
+          x[dd] = vegas_map_1d<float, false>(sh_edges + dd * (nb + 1), nb, k[dd], &b, &jd);
+          binw[dd / 4] |= uint32_t(b) << (8 * (dd % 4));
+          jac *= jd;
+          atomicAdd(&sh_n[dd * nb + b], 1u);
+        }
+      }
+      st = gg_kinematics<PROC, float>(a, pdf, x, &kin, nullptr);
+      if (st == -5) ++acc.nnoconv;
+    }
+    const bool pass = st == 1;
+    const unsigned m = __ballot_sync(0xffffffffu, pass);
+    const int tot = __popc(m);
+    if (fill + tot > 32 && !next_held) {
+      ok = acquire(seq + 1);
+      next_held = true;
+      if (!ok) break;
+    }
+    if (pass) {
+      const int pos = fill + __popc(m & ((1u << lane) - 1u));
+      uint32_t* r = ring.rec + size_t(slot_of(pos < 32 ? seq : seq + 1)) * kWsWords * 32 + (pos & 31);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        r[(kWK + 4 * j + 0) * 32] = __float_as_uint(kin.k[j].e);
+        r[(kWK + 4 * j + 1) * 32] = __float_as_uint(kin.k[j].x);
+        r[(kWK + 4 * j + 2) * 32] = __float_as_uint(kin.k[j].y);
+        r[(kWK + 4 * j + 3) * 32] = __float_as_uint(kin.k[j].z);
+      }
+      r[kWRs * 32] = __float_as_uint(kin.rs);
+      r[kWLgg * 32] = __float_as_uint(kin.lgg);
+      r[kWFlux * 32] = __float_as_uint(kin.flux);
+      r[kWJac * 32] = __float_as_uint(jac);
+      r[kWPsw * 32] = __double2loint(kin.psw);
+      r[(kWPsw + 1) * 32] = __double2hiint(kin.psw);
+#pragma unroll
+      for (int j = 0; j < NW; ++j) r[(kWBin + j) * 32] = binw[j];
+    }
+    fill += tot;
+    if (fill >= 32) {
+      publish(seq, 32);
+      ++seq;
+      fill -= 32;
+      if (!next_held) ok = acquire(seq);
+      next_held = false;
+    }
+  }
+  if (ok) {
+    publish(seq, fill);  // the last, partial slot (possibly empty)
+    for (int e = 1; e <= kWsClasses && ok; ++e) {
+      ok = acquire(seq + e);
+      if (ok) publish(seq + e, -1);
+    }
+    seq += kWsClasses + 1;
+  }
+  return ok;
+}
+
+// Consumer warp c (0 <= c < kWsConsumerWarps): evaluates |M|^2 for the events
+// of its producers' slots until every stream it serves has delivered an end
+// marker, and adds the weights w = f J to the Kahan sums, w_max and the
+// histogram of w^2.  q0, q1: the next slot sequence numbers of its (up to two)
+// streams, carried over between calls.  Returns false when a wait gave up.
+template <int PROC>
+MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int c, int& q0, int& q1, Acc& acc) {
+  constexpr int MAXD = ProcTraits<PROC>::MAXD;
+  constexpr int NW = (MAXD + 3) / 4;
+  const int lane = threadIdx.x & 31;
+  const int ndim = a.ndim, nb = a.nbins;
+  bool live0 = true, live1 = kWsStreams > 1;
+  for (int si = 0; live0 || live1; si ^= (kWsStreams > 1)) {
+    if (si == 0 ? !live0 : !live1) si ^= 1;
+    const int p = (c % kWsProducerWarps) + si * kWsConsumerWarps;
+    int& q = si == 0 ? q0 : q1;
+    const int s = p * kWsSlotsPerProducer + (q & 3);
+    if (!ws_wait(&ring.full[s], uint32_t(q >> 2) & 1u)) return false;
+    const int cnt = ring.count[s];
+    q += kWsClasses;
+    if (cnt < 0) {
+      // release the marker's slot too: a later call (the next tile of a
+      // batch) reuses it
+      mbar_arrive(&ring.empty[s]);
+      if (si == 0)
+        live0 = false;
+      else
+        live1 = false;
+      continue;
+    }
+    if (lane < cnt) {
+      const uint32_t* r = ring.rec + size_t(s) * kWsWords * 32 + lane;
+      GgKin<float> kin;
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        kin.k[j] = {__uint_as_float(r[(kWK + 4 * j + 0) * 32]), __uint_as_float(r[(kWK + 4 * j + 1) * 32]),
+                    __uint_as_float(r[(kWK + 4 * j + 2) * 32]), __uint_as_float(r[(kWK + 4 * j + 3) * 32])};
+      kin.rs = __uint_as_float(r[kWRs * 32]);
+      kin.lgg = __uint_as_float(r[kWLgg * 32]);
+      kin.flux = __uint_as_float(r[kWFlux * 32]);
+      const float jac = __uint_as_float(r[kWJac * 32]);
+      kin.psw = __hiloint2double(int(r[(kWPsw + 1) * 32]), int(r[kWPsw * 32]));
+      uint32_t binw[NW];
+#pragma unroll
+      for (int j = 0; j < NW; ++j) binw[j] = r[(kWBin + j) * 32];
+      const float me2 = gg_me2<float>(a, kin);
+      double w = gg_weight<float>(a, kin, me2) * double(jac);
+      if (!isfinite(w)) {
+        ++acc.nbad;
+        w = 0.0;
+      }
+      const double y = w - acc.s_c;
+      const double t = acc.s_hi + y;
+      acc.s_c = (t - acc.s_hi) - y;
+      acc.s_hi = t;
+      const double w2 = w * w;
+      const double y2 = w2 - acc.q_c;
+      const double t2 = acc.q_hi + y2;
+      acc.q_c = (t2 - acc.q_hi) - y2;
+      acc.q_hi = t2;
+      if (w != 0.0) ++acc.nnz;
+      acc.wmax = fmax(acc.wmax, w);
+#pragma unroll
+      for (int dd = 0; dd < MAXD; ++dd)
+        if (dd < ndim) atomicAdd(&sh_w2[dd * nb + int((binw[dd / 4] >> (8 * (dd % 4))) & 0xffu)], float(w2));
+    }
+    mbar_arrive(&ring.empty[s]);
+  }
+  return true;
+}
+
 template <int PROC>
 __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs a) {
   static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D, "gg -> t tbar g only");
-  constexpr int MAXD = ProcTraits<PROC>::MAXD;
-  constexpr int NW = (MAXD + 3) / 4;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kWsSlots], empty[kWsSlots];
   __shared__ int count[kWsSlots];
@@ -111,7 +292,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
   __shared__ BlockPartial warp_part[kWsThreads / 32];
   const int ndim = a.ndim, nb = a.nbins;
   const int nedge = ndim * (nb + 1), nhist = ndim * nb;
-  uint32_t* ring = reinterpret_cast<uint32_t*>(smem);
+  const WsRing ring = {reinterpret_cast<uint32_t*>(smem), full, empty, count};
   unsigned char* rest = smem + size_t(kWsSlots) * kWsWords * 32 * 4;
   float* sh_w2 = reinterpret_cast<float*>(rest);
   unsigned int* sh_n = reinterpret_cast<unsigned int*>(rest + size_t(nhist) * 4);
@@ -141,163 +322,19 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
   }
 
   Acc acc;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   bool ok = true;
   if (warp < kWsProducerWarps) {
-    // ------------------------------------------------------------- producer
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
-    const int p = warp;
-    auto slot_of = [&](int q) { return p * kWsSlotsPerProducer + (q & 3); };
-    auto acquire = [&](int q) -> bool {
-      const int u = q >> 2;  // earlier uses of this slot
-      return u == 0 || ws_wait(&empty[slot_of(q)], uint32_t(u - 1) & 1u);
-    };
-    auto publish = [&](int q, int cnt) {
-      if (lane == 0) count[slot_of(q)] = cnt;
-      mbar_arrive(&full[slot_of(q)]);
-    };
-    const long long nchunks = (a.n + 31) / 32;
-    const long long G = (long long)gridDim.x * kWsProducerWarps;
-    int seq = 0, fill = 0;
-    bool next_held = false;
-    ok = acquire(0);
-    for (long long chunk = (long long)blockIdx.x * kWsProducerWarps + p; ok && chunk < nchunks; chunk += G) {
-      const long long i = chunk * 32 + lane;
-      GgKin<float> kin;
-      uint32_t binw[NW];
-#pragma unroll
-      for (int j = 0; j < NW; ++j) binw[j] = 0u;
-      float jac = 1.0f;
-      int st = 0;
-      if (i < a.n) {
-        uint64_t k[MAXD];
-        event_uniforms<MAXD, false>(a.seed, a.iteration, a.gid, a.first + uint64_t(i), ndim, k);
-        float x[MAXD];
-#pragma unroll
-        for (int dd = 0; dd < MAXD; ++dd) {
-          if (dd < ndim) {
-            int b;
-            float jd;
-            x[dd] = vegas_map_1d<float, false>(sh_edges + dd * (nb + 1), nb, k[dd], &b, &jd);
-            binw[dd / 4] |= uint32_t(b) << (8 * (dd % 4));
-            jac *= jd;
-            atomicAdd(&sh_n[dd * nb + b], 1u);
-          }
-        }
-        st = gg_kinematics<PROC, float>(a, pdf, x, &kin, nullptr);
-        if (st == -5) ++acc.nnoconv;
-      }
-      const bool pass = st == 1;
-      const unsigned m = __ballot_sync(0xffffffffu, pass);
-      const int tot = __popc(m);
-      if (fill + tot > 32 && !next_held) {
-        ok = acquire(seq + 1);
-        next_held = true;
-        if (!ok) break;
-      }
-      if (pass) {
-        const int pos = fill + __popc(m & ((1u << lane) - 1u));
-        uint32_t* r = ring + size_t(slot_of(pos < 32 ? seq : seq + 1)) * kWsWords * 32 + (pos & 31);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          r[(kWK + 4 * j + 0) * 32] = __float_as_uint(kin.k[j].e);
-          r[(kWK + 4 * j + 1) * 32] = __float_as_uint(kin.k[j].x);
-          r[(kWK + 4 * j + 2) * 32] = __float_as_uint(kin.k[j].y);
-          r[(kWK + 4 * j + 3) * 32] = __float_as_uint(kin.k[j].z);
-        }
-        r[kWRs * 32] = __float_as_uint(kin.rs);
-        r[kWLgg * 32] = __float_as_uint(kin.lgg);
-        r[kWFlux * 32] = __float_as_uint(kin.flux);
-        r[kWJac * 32] = __float_as_uint(jac);
-        r[kWPsw * 32] = __double2loint(kin.psw);
-        r[(kWPsw + 1) * 32] = __double2hiint(kin.psw);
-#pragma unroll
-        for (int j = 0; j < NW; ++j) r[(kWBin + j) * 32] = binw[j];
-      }
-      fill += tot;
-      if (fill >= 32) {
-        publish(seq, 32);
-        ++seq;
-        fill -= 32;
-        if (!next_held) ok = acquire(seq);
-        next_held = false;
-      }
-    }
-    if (ok) {
-      publish(seq, fill);  // the last, partial slot (possibly empty)
-      for (int e = 1; e <= kWsClasses && ok; ++e) {
-        ok = acquire(seq + e);
-        if (ok) publish(seq + e, -1);
-      }
-    }
+    int seq = 0;
+    ok = ws_produce<PROC>(a, pdf, sh_edges, sh_n, ring, warp, 0, a.n, (long long)blockIdx.x * kWsProducerWarps + warp,
+                          (long long)gridDim.x * kWsProducerWarps, seq, acc);
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsRegs));
   } else {
-    // ------------------------------------------------------------- consumer
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
     const int c = warp - kWsProducerWarps;
-    const int cls = c / kWsProducerWarps;
-    // up to two streams, served in turn until both have ended
-    int q0 = cls, q1 = cls;
-    bool live0 = true, live1 = kWsStreams > 1;
-    for (int si = 0; live0 || live1; si ^= (kWsStreams > 1)) {
-      if (si == 0 ? !live0 : !live1) si ^= 1;
-      const int p = (c % kWsProducerWarps) + si * kWsConsumerWarps;
-      const int q = si == 0 ? q0 : q1;
-      const int s = p * kWsSlotsPerProducer + (q & 3);
-      if (!ws_wait(&full[s], uint32_t(q >> 2) & 1u)) {
-        ok = false;
-        break;
-      }
-      const int cnt = count[s];
-      if (cnt < 0) {
-        if (si == 0)
-          live0 = false;
-        else
-          live1 = false;
-        continue;
-      }
-      if (si == 0)
-        q0 += kWsClasses;
-      else
-        q1 += kWsClasses;
-      if (lane < cnt) {
-        const uint32_t* r = ring + size_t(s) * kWsWords * 32 + lane;
-        GgKin<float> kin;
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          kin.k[j] = {__uint_as_float(r[(kWK + 4 * j + 0) * 32]), __uint_as_float(r[(kWK + 4 * j + 1) * 32]),
-                      __uint_as_float(r[(kWK + 4 * j + 2) * 32]), __uint_as_float(r[(kWK + 4 * j + 3) * 32])};
-        kin.rs = __uint_as_float(r[kWRs * 32]);
-        kin.lgg = __uint_as_float(r[kWLgg * 32]);
-        kin.flux = __uint_as_float(r[kWFlux * 32]);
-        const float jac = __uint_as_float(r[kWJac * 32]);
-        kin.psw = __hiloint2double(int(r[(kWPsw + 1) * 32]), int(r[kWPsw * 32]));
-        uint32_t binw[NW];
-#pragma unroll
-        for (int j = 0; j < NW; ++j) binw[j] = r[(kWBin + j) * 32];
-        const float me2 = gg_me2<float>(a, kin);
-        double w = gg_weight<float>(a, kin, me2) * double(jac);
-        if (!isfinite(w)) {
-          ++acc.nbad;
-          w = 0.0;
-        }
-        const double y = w - acc.s_c;
-        const double t = acc.s_hi + y;
-        acc.s_c = (t - acc.s_hi) - y;
-        acc.s_hi = t;
-        const double w2 = w * w;
-        const double y2 = w2 - acc.q_c;
-        const double t2 = acc.q_hi + y2;
-        acc.q_c = (t2 - acc.q_hi) - y2;
-        acc.q_hi = t2;
-        if (w != 0.0) ++acc.nnz;
-        acc.wmax = fmax(acc.wmax, w);
-#pragma unroll
-        for (int dd = 0; dd < MAXD; ++dd)
-          if (dd < ndim) atomicAdd(&sh_w2[dd * nb + int((binw[dd / 4] >> (8 * (dd % 4))) & 0xffu)], float(w2));
-      }
-      mbar_arrive(&empty[s]);
-    }
+    int q0 = c / kWsProducerWarps, q1 = q0;
+    ok = ws_consume<PROC>(a, sh_w2, ring, c, q0, q1, acc);
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
   }
   if (!ok) atomicExch(&failed, 1);

@@ -69,8 +69,43 @@ def test_batch_matches_single_path(gpdf, prec):
             M.mc_vegas_set_grid(singles[i], g_b)  # continue both from the same grid
             assert hist_ref.sum() == itg.ndim() * counts[i]
     shape = M.mc_batch_shape(b)
-    assert shape["block"] in (64, 128, 256) and shape["events_per_thread"] in (2, 8, 32)
+    if prec == M.MC_FP64:
+        assert shape["block"] in (64, 128, 256) and shape["events_per_thread"] in (2, 8, 32)
+    else:  # warp-specialised batch kernel: 16 warps, tiles of 4, 16 or 64 events per thread
+        assert shape["block"] == 512 and shape["events_per_thread"] in (4, 16, 64)
     assert shape["ntiles"] >= len(itgs)
+    b.free()
+    for v in singles:
+        v.free()
+
+
+def test_batch_many_gg_tiles_per_block(gpdf):
+    """FP32 batch with enough gg -> t tbar g events that every block of the
+    warp-specialised batch kernel runs several gg tiles in a row, whatever
+    tile size the autotuner picks (at most 64 x 512 events): the ring of each
+    block then reuses slots across tiles, end-marker slots included.  Every
+    integrand matches the single-integrand path, as in the test above."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n_gg = 4 * sms * 64 * 512  # four of the largest tiles per block
+    itgs = [W.gg_ttbarg(sqrt_s=13000.0), W.gg_ttbarg_7d(sqrt_s=13000.0), W.gauss(8), W.gg_ttbarg(sqrt_s=7000.0)]
+    counts = [n_gg // 2, n_gg // 4, 100000, n_gg // 4]
+    b = M.mc_batch_create(itgs, counts, gpdf, nbins=50, seed=11, prec=M.MC_FP32_KAHAN)
+    singles = []
+    for i, itg in enumerate(itgs):
+        v = M.mc_vegas_init(itg.ndim(), 50, 11, M.MC_FP32_KAHAN)
+        M.mc_vegas_set_gid(v, i)
+        singles.append(v)
+    for it in range(2):
+        res = M.mc_batch_iterate(b, 1.5)
+        for i, itg in enumerate(itgs):
+            r = M.mc_vegas_iterate(singles[i], itg, gpdf, counts[i])
+            M.mc_vegas_refine(singles[i], 1.5)
+            assert res[i].status == M.MC_OK and res[i].n == r.n and res[i].n_nonzero == r.n_nonzero, (i, it)
+            scale = math.sqrt(r.n * r.sum2)
+            assert abs(res[i].sum - r.sum) <= 1e-4 * scale, (i, it, res[i].sum, r.sum)
+            M.mc_vegas_set_grid(singles[i], M.mc_batch_get_grid(b, i))
+    shape = M.mc_batch_shape(b)
+    assert shape["ntiles"] >= 4 * sms
     b.free()
     for v in singles:
         v.free()
