@@ -67,6 +67,16 @@ def lib():
         L.orc_pdf_free.argtypes = [ctypes.c_void_p]
         L.orc_pdf_xfxq2.argtypes = [ctypes.c_void_p, ctypes.c_int, _d, _d]
         L.orc_pdf_xfxq2.restype = _d
+        L.orc_pdfset_new.argtypes = [ctypes.c_int, _i32p, _i32p, _dp, _dp, ctypes.c_int, _i32p, ctypes.c_int, _dp]
+        L.orc_pdfset_new.restype = ctypes.c_void_p
+        L.orc_pdfset_free.argtypes = [ctypes.c_void_p]
+        L.orc_pdfset_xfxq2.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _d, _d]
+        L.orc_pdfset_xfxq2.restype = _d
+        L.orc_alphas_new.argtypes = [ctypes.c_int, _dp, _dp]
+        L.orc_alphas_new.restype = ctypes.c_void_p
+        L.orc_alphas_free.argtypes = [ctypes.c_void_p]
+        L.orc_alphas_q2.argtypes = [ctypes.c_void_p, _d]
+        L.orc_alphas_q2.restype = _d
         for name, args in [("orc_me2_eemumu", [_d] * 6), ("orc_me2_eemumu_trace", [_d] * 4 + [_dp]),
                            ("orc_me2_qqbar_ttbar", [_d] * 4), ("orc_me2_qqbar_ttbar_trace", [_d, _d, _dp]),
                            ("orc_me2_gg_ttbar", [_d] * 4), ("orc_me2_gg_ttbar_colour_ordered", [_d, _d, _dp]),
@@ -191,6 +201,47 @@ class Pdf:
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.orc_pdf_free(self.handle)
+            self.handle = None
+
+
+class PdfSet:
+    """A PDF set of sub-grids and members (workloads.PdfSet) with LHAPDF's
+    interpolation and extrapolation (oracle/src/pdfset.cpp)."""
+
+    def __init__(self, pset):
+        self.pset = pset
+        nx = np.array([len(x) for x in pset.x], dtype=np.int32)
+        nq = np.array([len(q) for q in pset.q], dtype=np.int32)
+        x = np.ascontiguousarray(np.concatenate(pset.x), dtype=np.float64)
+        q = np.ascontiguousarray(np.concatenate(pset.q), dtype=np.float64)
+        pids = np.ascontiguousarray(pset.pids, dtype=np.int32)
+        xf = np.ascontiguousarray(pset.xf, dtype=np.float64)
+        self.handle = lib().orc_pdfset_new(len(nx), _ptr(nx, _i32p), _ptr(nq, _i32p), _ptr(x), _ptr(q), len(pids),
+                                           _ptr(pids, _i32p), xf.shape[0], _ptr(xf))
+
+    def xfxq2(self, member, pid, x, q2):
+        return lib().orc_pdfset_xfxq2(self.handle, member, pid, x, q2)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.orc_pdfset_free(self.handle)
+            self.handle = None
+
+
+class AlphaS:
+    """alpha_s(Q^2) interpolation on LHAPDF-style knots (oracle/src/pdfset.cpp)."""
+
+    def __init__(self, q, a):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self.handle = lib().orc_alphas_new(len(q), _ptr(q), _ptr(a))
+
+    def __call__(self, q2):
+        return lib().orc_alphas_q2(self.handle, q2)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.orc_alphas_free(self.handle)
             self.handle = None
 
 

@@ -11,6 +11,8 @@ LHAPDF order (-5..-1, 21, 1..5), values
     x f(x, Q) = A x^-a (1 - x)^b (1 + c ln(Q^2 / Q0^2)),  Q0 = 1.65 GeV,
 with (A, a, b, c) drawn per flavour from SplitMix64(seed):
 A in [0.5, 2] (times 3 for the gluon), a in [0, 0.3], b in [2, 6], c in [0, 0.2].
+synthetic_pdf_set adds sub-grids (a b-quark threshold) and members, and
+synthetic_alphas_knots the alpha_s(Q) knots of such a set.
 """
 from dataclasses import dataclass, asdict
 import math
@@ -70,6 +72,97 @@ def synthetic_pdf_grid(seed=0, nx=100, nq=40, xmin=1e-7, qmin=1.65, qmax=1e4):
             for j, qj in enumerate(q):
                 xf[i, j, fl] = A * xi ** (-a) * (1.0 - xi) ** b * (1.0 + c * math.log(qj * qj / (q0 * q0)))
     return PdfGrid(x=x, q=q, pids=np.array(PIDS, dtype=np.int32), xf=xf, params=params)
+
+
+@dataclass
+class PdfSet:
+    """A PDF set of several sub-grids and members (LHAPDF layout)."""
+    x: list              # per sub-grid: x knots
+    q: list              # per sub-grid: Q knots (GeV); adjacent sub-grids share the threshold knot
+    pids: np.ndarray     # [nflav] int32
+    xf: np.ndarray       # [nmem][sum over sub-grids of nx*nq*nflav]: per sub-grid [x][q][flav]
+    params: np.ndarray   # [nmem][nflav][4]
+
+    def member_subgrid(self, m, s):
+        """Values of member m on sub-grid s as [nx][nq][nflav]."""
+        off = 0
+        for t in range(s):
+            off += len(self.x[t]) * len(self.q[t]) * len(self.pids)
+        nx, nq = len(self.x[s]), len(self.q[s])
+        return self.xf[m, off:off + nx * nq * len(self.pids)].reshape(nx, nq, len(self.pids))
+
+
+MB_THRESHOLD = 4.92   # GeV, the sub-grid boundary (b-quark mass, as in NNPDF3.1)
+
+
+def synthetic_pdf_set(nmem=1, seed=0, nx=100, nq_low=8, nq_high=32, xmin=1e-7, qmin=1.65, qmax=1e4,
+                      spread=0.05):
+    """A multi-member, two-sub-grid stand-in for an LHAPDF set with a b-quark
+    threshold: the x knots of synthetic_pdf_grid; Q knots log-spaced on
+    [qmin, m_b] (nq_low) and [m_b, qmax] (nq_high), the threshold knot in both;
+    member m draws its flavour parameters as synthetic_pdf_grid(seed) does and
+    multiplies A, a, b, c by 1 + spread u, u uniform in [-1, 1] from
+    SplitMix64(seed + 1000 + m) (member 0 is the central set, unperturbed);
+    the b and b-bar densities vanish below the threshold."""
+    x = np.array([10.0 ** (math.log10(xmin) * (1.0 - i / (nx - 1))) for i in range(nx)])
+    x[-1] = 1.0
+    q_lo = np.array([qmin * (MB_THRESHOLD / qmin) ** (j / (nq_low - 1)) for j in range(nq_low)])
+    q_hi = np.array([MB_THRESHOLD * (qmax / MB_THRESHOLD) ** (j / (nq_high - 1)) for j in range(nq_high)])
+    q_lo[-1] = q_hi[0] = MB_THRESHOLD
+    base = synthetic_pdf_grid(seed).params
+    nfl = len(PIDS)
+    size = nx * (nq_low + nq_high) * nfl
+    xf = np.empty((nmem, size))
+    params = np.empty((nmem, nfl, 4))
+    for m in range(nmem):
+        rng = SplitMix64(seed + 1000 + m)
+        pm = base.copy()
+        if m > 0:
+            for fl in range(nfl):
+                for k in range(4):
+                    pm[fl, k] *= 1.0 + spread * rng.uniform(-1.0, 1.0)
+        params[m] = pm
+        blocks = []
+        for s, qk in enumerate((q_lo, q_hi)):
+            v = np.empty((nx, len(qk), nfl))
+            for fl, (A, a, b, c) in enumerate(pm):
+                heavy_b = abs(PIDS[fl]) == 5
+                for j, qj in enumerate(qk):
+                    if heavy_b and s == 0:
+                        v[:, j, fl] = 0.0
+                        continue
+                    lq = math.log(qj * qj / (qmin * qmin))
+                    v[:, j, fl] = A * x ** (-a) * (1.0 - x) ** b * (1.0 + c * lq)
+            blocks.append(v.reshape(-1))
+        xf[m] = np.concatenate(blocks)
+    return PdfSet(x=[x, x.copy()], q=[q_lo, q_hi], pids=np.array(PIDS, dtype=np.int32), xf=xf, params=params)
+
+
+ALPHAS_MZ, MZ, MC_THRESHOLD = 0.118, 91.1876, 1.51
+
+
+def synthetic_alphas_knots(qmin=1.0, qmax=1e4, per_segment=(6, 10, 40)):
+    """alpha_s knots shaped like an LHAPDF set's: one-loop running
+    alpha_s(Q) = 1 / (b0(nf) ln(Q^2 / Lambda_nf^2)), b0 = (33 - 2 nf) / (12 pi),
+    with nf = 3 below m_c = 1.51 GeV, 4 up to m_b = 4.92 GeV and 5 above,
+    Lambda_5 fixed by alpha_s(M_Z) = 0.118 and Lambda_4, Lambda_3 by continuity
+    at the thresholds; Q knots log-spaced per segment, each threshold knot
+    repeated (the end of one segment, the start of the next).  Returns (q, a)."""
+    def b0(nf):
+        return (33.0 - 2.0 * nf) / (12.0 * math.pi)
+    lam2 = {5: MZ * MZ * math.exp(-1.0 / (b0(5) * ALPHAS_MZ))}
+    a_b = 1.0 / (b0(5) * math.log(MB_THRESHOLD ** 2 / lam2[5]))
+    lam2[4] = MB_THRESHOLD ** 2 * math.exp(-1.0 / (b0(4) * a_b))
+    a_c = 1.0 / (b0(4) * math.log(MC_THRESHOLD ** 2 / lam2[4]))
+    lam2[3] = MC_THRESHOLD ** 2 * math.exp(-1.0 / (b0(3) * a_c))
+    edges = [(qmin, MC_THRESHOLD, 3), (MC_THRESHOLD, MB_THRESHOLD, 4), (MB_THRESHOLD, qmax, 5)]
+    qs, als = [], []
+    for (lo, hi, nf), n in zip(edges, per_segment):
+        for j in range(n):
+            qj = lo * (hi / lo) ** (j / (n - 1))
+            qs.append(qj)
+            als.append(1.0 / (b0(nf) * math.log(qj * qj / lam2[nf])))
+    return np.array(qs), np.array(als)
 
 
 @dataclass
