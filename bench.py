@@ -13,9 +13,11 @@ VEGAS and FP32 + normalizing-flow sampling with VEGAS as its judge and
 fallback (200 online training steps and the judge's VEGAS iteration
 included; mc_integrate_flow), each run from scratch, with the variance per
 event and the unweighting efficiency of each (the flow's from a separately
-timed train-then-sample breakdown); and "batch16": sixteen integrands of uneven
+timed train-then-sample breakdown); "batch16": sixteen integrands of uneven
 dimension and event count in one persistent launch per iteration (CUDA
-graph, autotuned shape) against the sum of their single launches.
+graph, autotuned shape) against the sum of their single launches; and
+"pdf_members": the multi-member PDF evaluation of the thesis's Table
+tab:fktable (400 members, 11 flavours, 2415 x points) against HBM.
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a
 bounded sample of events per step on the host cores).
@@ -241,6 +243,53 @@ def batch16(M, pdf, stream, iterations=10):
             "speedup_vs_single_launches": single_ms / batch_ms, "autotuned": shape}
 
 
+PDF_MEMBERS, PDF_POINTS, PDF_Q = 400, 2415, 100.0
+
+
+def pdf_members(M, stream, reps=20):
+    """Multi-member PDF evaluation (thesis Table tab:fktable): all 11 flavours
+    of 400 members at 2415 x points (log-spaced on [1e-7, 1], Q = 100 GeV) of
+    a two-sub-grid synthetic set, FP32 and FP64, each launch timed alone with
+    CUDA events after an L2 flush.  Roofline: HBM, algorithmic bytes = output
+    + the four Q rows of every flavour and member the points touch + inputs."""
+    import torch
+    pset = W.synthetic_pdf_set(nmem=PDF_MEMBERS, seed=0)
+    ps = M.mc_pdfset_load(pset)
+    x = np.array([10.0 ** (-7.0 * (1.0 - i / (PDF_POINTS - 1))) for i in range(PDF_POINTS)])
+    x[-1] = 1.0
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    qd = torch.full_like(xd, PDF_Q * PDF_Q)
+    nfl = len(pset.pids)
+    nx = len(pset.x[1])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    hbm = peaks().get("hbm_gbs", 6400.0)
+    out = {"workload": f"{PDF_MEMBERS} members x {nfl} flavours x {PDF_POINTS} x points at Q = {PDF_Q:g} GeV, "
+                       "2 sub-grids (b threshold), 100 x knots", "hbm_peak_gbs": hbm,
+           "thesis_context": "PDFFlow on an Nvidia Titan V: 1.69 s for 400 members (LHAPDF CPU 3.63 s), "
+                             "thesis Table tab:fktable"}
+    for name, prec, dt, size in (("fp32", M.MC_FP32_KAHAN, torch.float32, 4), ("fp64", M.MC_FP64, torch.float64, 8)):
+        res = torch.empty((PDF_MEMBERS, PDF_POINTS, nfl), dtype=dt, device="cuda")
+        for _ in range(3):
+            M.mc_pdfset_xfxq2(ps, prec, 0, PDF_MEMBERS, PDF_POINTS, xd, qd, res, stream)
+        times = []
+        for _ in range(reps):
+            flush_l2(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.mc_pdfset_xfxq2(ps, prec, 0, PDF_MEMBERS, PDF_POINTS, xd, qd, res, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        nbytes = PDF_MEMBERS * PDF_POINTS * nfl * size + 4 * nx * nfl * PDF_MEMBERS * size + 2 * PDF_POINTS * 8
+        out[name] = {"ms": ms, "values_per_s": PDF_MEMBERS * PDF_POINTS * nfl / (ms / 1e3),
+                     "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (ms / 1e3) / 1e9,
+                     "hbm_frac": nbytes / (ms / 1e3) / 1e9 / hbm}
+    ps.free()
+    return out
+
+
 def profile_case(case):
     """A small fixed workload for ncu captures (no timing output)."""
     import torch
@@ -253,6 +302,17 @@ def profile_case(case):
         for _ in range(3):
             M.mc_vegas_iterate(v, W.gg_ttbarg(), pdf, 1 << 20)
             M.mc_vegas_refine(v, ALPHA)
+    elif case == "pdfset":  # the multi-member PDF evaluation, FP32 then FP64
+        import numpy as _np
+        pset = W.synthetic_pdf_set(nmem=PDF_MEMBERS, seed=0)
+        ps = M.mc_pdfset_load(pset)
+        x = _np.array([10.0 ** (-7.0 * (1.0 - i / (PDF_POINTS - 1))) for i in range(PDF_POINTS)])
+        xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+        qd = torch.full_like(xd, PDF_Q * PDF_Q)
+        for prec, dt in ((M.MC_FP32_KAHAN, torch.float32), (M.MC_FP64, torch.float64)):
+            res = torch.empty((PDF_MEMBERS, PDF_POINTS, len(pset.pids)), dtype=dt, device="cuda")
+            M.mc_pdfset_xfxq2(ps, prec, 0, PDF_MEMBERS, PDF_POINTS, xd, qd, res)
+        ps.free()
     else:  # flow: two training steps of 65536 events, one sampling pass of 2^20 events
         itg = W.gg_ttbarg_7d()
         f = M.mc_flow_create(7, FLOW_LAYERS, FLOW_BINS, W.flow_init_params(7, FLOW_LAYERS, FLOW_BINS, seed=0),
@@ -453,6 +513,7 @@ def run_native(args, rank, world):
     if not args.no_time_to_target:
         line["time_to_target"] = time_to_target(M, pdf, stream)
         line["batch16"] = batch16(M, pdf, stream)
+        line["pdf_members"] = pdf_members(M, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -467,7 +528,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-target", action="store_true")
-    ap.add_argument("--profile-case", choices=["integrand", "flow"], default=None,
+    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdfset"], default=None,
                     help="run a small fixed workload for profiling and exit")
     args = ap.parse_args()
     if args.profile_case:

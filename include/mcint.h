@@ -127,6 +127,60 @@ int mc_pdf_free(mc_pdf pdf);
 int mc_pdf_xfxq2(mc_pdf pdf, int prec, int64_t n, const double* x, const double* q2,
                  double* xf_out, void* stream);
 
+/* ---------------------------------------------------------- PDF sets
+ * A PDF set of several sub-grids and members with LHAPDF's interpolation and
+ * extrapolation rules (thesis Sec. "LHAPDF: the Les Houches Accord PDF";
+ * multi-member evaluation: Sec. "PDFFlow: interpolating PDFs on GPUs",
+ * Table tab:fktable).  Sub-grids cover adjacent Q ranges split at quark-mass
+ * thresholds; the threshold knot is the last Q knot of one sub-grid and the
+ * first of the next, and a query exactly on it uses the upper sub-grid.
+ * Inside a sub-grid: cubic Hermite splines in log x, then in log Q^2, knot
+ * slopes the mean of the adjacent divided differences (one-sided at the
+ * sub-grid's ends); bilinear in (log x, log Q^2) where the sub-grid has
+ * fewer than 4 knots in a direction.  Below x_min and above Q_max: linear
+ * continuation in log x (log Q^2) from the two edge knots, of log(x f) when
+ * both values exceed 1e-3 and of x f otherwise.  Below Q_min:
+ * x f(Q^2_min) (Q^2/Q^2_min)^(gamma r + 1 - r), r = Q^2/Q^2_min, gamma =
+ * d ln(x f)/d ln Q^2 from the two lowest Q knots (1 when either value is not
+ * positive).  When x and Q are both outside, the x rule runs first.
+ *
+ * mc_pdfset_load: nsub (1..8) sub-grids with nx[s], nq[s] (>= 2) knots;
+ * x: the x knots of all sub-grids concatenated (positive, increasing within
+ * a sub-grid); q: the Q knots (GeV) concatenated, adjacent sub-grids sharing
+ * the threshold knot; nflav (1..16) flavours with PDG ids pids[] (the output
+ * follows this order); nmem (>= 1) members; xf: for each member, for each
+ * sub-grid, nx[s] x nq[s] x nflav values in [x][q][flavour] order (LHAPDF's
+ * data blocks).  All host arrays are caller-owned, FP64, copied; the set is
+ * held on the current device in FP64 and FP32 until mc_pdfset_free.
+ * EINVAL on bad shapes or knots, ENOMEM when the device allocation fails.
+ */
+typedef struct mc_pdfset_s* mc_pdfset;
+int mc_pdfset_load(int nsub, const int* nx, const int* nq, const double* x, const double* q, int nflav,
+                   const int* pids, int nmem, const double* xf, mc_pdfset* out);
+int mc_pdfset_free(mc_pdfset set);
+/* mc_pdfset_xfxq2: x f of every flavour of members member0 .. member0+nmem-1
+ * at n points (x[i], q2[i]) (device arrays, FP64): out[m][i][flavour]
+ * (device, caller-owned), double for prec = MC_FP64, float for
+ * MC_FP32_KAHAN (FP32 arithmetic on the FP32 copy of the set).  x > x_max,
+ * x <= 0 and q2 <= 0 give NaN.  Asynchronous on `stream`; EINVAL on a bad
+ * member range or arguments, or when the set lives on another device. */
+int mc_pdfset_xfxq2(mc_pdfset set, int prec, int member0, int nmem, int64_t n, const double* x, const double* q2,
+                    void* out, void* stream);
+
+/* alpha_s(Q) on LHAPDF-style knots (thesis Sec. "LHAPDF: the Les Houches
+ * Accord PDF"): cubic Hermite in log Q^2 on the segments between repeated
+ * (threshold) knots, alpha_s(Q_max) above the knots, and below them
+ * ln alpha_s continued linearly in ln Q^2 from the two lowest knots.
+ * mc_alphas_load: n (>= 2) knots q[] (GeV, non-decreasing; a value repeated
+ * twice marks a threshold; the first and last segments need two distinct
+ * knots) and alphas[] (> 0), host, FP64, copied to the current device.
+ * mc_alphas_q2: alpha_s at n values q2[] (device, FP64) into out[] (device,
+ * FP64); q2 <= 0 gives NaN; asynchronous on `stream`. */
+typedef struct mc_alphas_s* mc_alphas;
+int mc_alphas_load(int n, const double* q, const double* alphas, mc_alphas* out);
+int mc_alphas_free(mc_alphas a);
+int mc_alphas_q2(mc_alphas a, int64_t n, const double* q2, double* out, void* stream);
+
 /* ---------------------------------------------------------------- VEGAS
  * mc_vegas_init: a VEGAS grid of ndim (1..16) dimensions with nbins
  * (2..256) equal bins each, the Philox seed, and the precision (MC_FP64 or

@@ -19,7 +19,8 @@
 //    r = Q^2 / Q^2_min, gamma the anomalous dimension d ln(x f) / d ln Q^2 at
 //    Q^2_min from the two lowest Q knots (1 when either value is not
 //    positive); where x and Q are both outside, the x rule runs first and its
-//    values enter the Q rule;
+//    values enter the Q rule; the continuation knots are evaluated in their
+//    own sub-grid (the first one below Q_min, the last one above Q_max);
 //  * alpha_s: cubic Hermite in log Q^2 on segments between repeated
 //    (threshold) knots, alpha_s(Q_max) above the grid, and below it ln alpha_s
 //    continued linearly in ln Q^2 from the two lowest knots.
@@ -121,13 +122,16 @@ int subgrid_of(const PdfSet& p, double lq) {
   return ns - 1;
 }
 
-// x f at (lx, lq) with lq inside the Q range: the x rule below x_min.
-double at_q_inside(const PdfSet& p, int m, int fl, double lx, double lq) {
-  const int s = subgrid_of(p, lq);
+// x f at (lx, lq) in sub-grid s (lq inside it): the x rule below x_min.
+double at_q_in(const PdfSet& p, int m, int fl, double lx, double lq, int s) {
   const SubGrid& g = p.sub[s];
   if (lx >= g.logx[0]) return interp(p, m, s, fl, lx, lq);
   const double f0 = interp(p, m, s, fl, g.logx[0], lq), f1 = interp(p, m, s, fl, g.logx[1], lq);
   return continue_linear(lx, g.logx[0], g.logx[1], f0, f1);
+}
+
+double at_q_inside(const PdfSet& p, int m, int fl, double lx, double lq) {
+  return at_q_in(p, m, fl, lx, lq, subgrid_of(p, lq));
 }
 
 double xfxq2(const PdfSet& p, int m, int pid, double x, double q2) {
@@ -139,13 +143,16 @@ double xfxq2(const PdfSet& p, int m, int pid, double x, double q2) {
   const SubGrid& first = p.sub.front();
   const SubGrid& last = p.sub.back();
   if (lq >= first.logq2.front() && lq <= last.logq2.back()) return at_q_inside(p, m, fl, lx, lq);
+  // the continuation knots are the last sub-grid's two highest (above Q_max)
+  // and the first sub-grid's two lowest (below Q_min), each in its sub-grid
+  const int sl = int(p.sub.size()) - 1;
   if (lq > last.logq2.back()) {
     const double t0 = last.logq2[last.nq - 2], t1 = last.logq2[last.nq - 1];
-    return continue_linear(lq, t0, t1, at_q_inside(p, m, fl, lx, t0), at_q_inside(p, m, fl, lx, t1));
+    return continue_linear(lq, t0, t1, at_q_in(p, m, fl, lx, t0, sl), at_q_in(p, m, fl, lx, t1, sl));
   }
   // low Q: anomalous-dimension continuation
   const double t0 = first.logq2[0], t1 = first.logq2[1];
-  const double f0 = at_q_inside(p, m, fl, lx, t0), f1 = at_q_inside(p, m, fl, lx, t1);
+  const double f0 = at_q_in(p, m, fl, lx, t0, 0), f1 = at_q_in(p, m, fl, lx, t1, 0);
   const double gamma = (f0 > 0.0 && f1 > 0.0) ? std::log(f1 / f0) / (t1 - t0) : 1.0;
   const double r = std::exp(lq - t0);
   return f0 * std::pow(r, gamma * r + 1.0 - r);

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmcint.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "tc_gemm.cu", "flow.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "tc_gemm.cu", "flow.cu", "pdfset.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

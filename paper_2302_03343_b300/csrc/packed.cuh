@@ -17,15 +17,13 @@ MC_D f2 pk2(float lo, float hi) {
 }
 MC_D f2 bc2(float s) { return pk2(s, s); }
 MC_D float lo2(f2 a) {
-  float l, h;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
-  (void)h;
+  float l;
+  asm("mov.b64 {%0, _}, %1;" : "=f"(l) : "l"(a.v));
   return l;
 }
 MC_D float hi2(f2 a) {
-  float l, h;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
-  (void)l;
+  float h;
+  asm("mov.b64 {_, %0}, %1;" : "=f"(h) : "l"(a.v));
   return h;
 }
 MC_D f2 swp2(f2 a) {

@@ -31,7 +31,8 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_batch_create", "mc_batch_iterate", "mc_batch_get_grid", "mc_batch_shape", "mc_batch_kernel_ms",
            "mc_batch_free", "mc_gemm_bf16", "mc_gemm_bf16_rs", "mc_gemm_bf16_tn", "mc_flow_param_count", "mc_flow_create", "mc_flow_free",
            "mc_flow_set_params", "mc_flow_get_params", "mc_flow_forward", "mc_flow_loss_grad", "mc_flow_adam_step",
-           "mc_flow_train", "mc_flow_iterate", "mc_flow_set_fused", "mc_integrate_flow")
+           "mc_flow_train", "mc_flow_iterate", "mc_flow_set_fused", "mc_integrate_flow", "mc_pdfset_load",
+           "mc_pdfset_free", "mc_pdfset_xfxq2", "mc_alphas_load", "mc_alphas_free", "mc_alphas_q2")
 
 
 class McError(RuntimeError):
@@ -129,6 +130,13 @@ def lib():
                                   i32, u64, d, _vp, ctypes.POINTER(Result), ctypes.POINTER(ctypes.c_int)],
             "mc_flow_train": [_vp, ctypes.POINTER(Integrand), _vp, i32, i64, d, _vp, _dp],
             "mc_flow_iterate": [_vp, ctypes.POINTER(Integrand), _vp, i64, u32, _vp, ctypes.POINTER(IterResult)],
+            "mc_pdfset_load": [i32, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp, _dp, i32,
+                               ctypes.POINTER(ctypes.c_int), i32, _dp, ctypes.POINTER(_vp)],
+            "mc_pdfset_free": [_vp],
+            "mc_pdfset_xfxq2": [_vp, i32, i32, i32, i64, _vp, _vp, _vp, _vp],
+            "mc_alphas_load": [i32, _dp, _dp, ctypes.POINTER(_vp)],
+            "mc_alphas_free": [_vp],
+            "mc_alphas_q2": [_vp, i64, _vp, _vp, _vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -200,6 +208,84 @@ def mc_pdf_free(pdf):
 
 def mc_pdf_xfxq2(pdf, prec, n, x_dev, q2_dev, out_dev, stream=None):
     _check(lib().mc_pdf_xfxq2(pdf.handle, prec, n, _ptr(x_dev), _ptr(q2_dev), _ptr(out_dev), _stream(stream)))
+
+
+# ---------------------------------------------------------------- PDF sets
+class PdfSet:
+    """Owns an mc_pdfset handle (sub-grids and members on the device)."""
+
+    def __init__(self, handle, nflav, nmem, pids):
+        self.handle, self.nflav, self.nmem, self.pids = handle, nflav, nmem, pids
+
+    def free(self):
+        if self.handle:
+            mc_pdfset_free(self)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mc_pdfset_load(pset):
+    """Load a workloads.PdfSet (x, q per sub-grid; xf [member][...])."""
+    nx = np.array([len(x) for x in pset.x], dtype=np.int32)
+    nq = np.array([len(q) for q in pset.q], dtype=np.int32)
+    x = np.ascontiguousarray(np.concatenate(pset.x), dtype=np.float64)
+    q = np.ascontiguousarray(np.concatenate(pset.q), dtype=np.float64)
+    pids = np.ascontiguousarray(pset.pids, dtype=np.int32)
+    xf = np.ascontiguousarray(pset.xf, dtype=np.float64)
+    ip = ctypes.POINTER(ctypes.c_int)
+    h = _vp()
+    _check(lib().mc_pdfset_load(len(nx), nx.ctypes.data_as(ip), nq.ctypes.data_as(ip), x.ctypes.data_as(_dp),
+                                q.ctypes.data_as(_dp), len(pids), pids.ctypes.data_as(ip), xf.shape[0],
+                                xf.ctypes.data_as(_dp), ctypes.byref(h)))
+    return PdfSet(h, len(pids), xf.shape[0], tuple(int(p) for p in pids))
+
+
+def mc_pdfset_free(pset):
+    _check(lib().mc_pdfset_free(pset.handle))
+
+
+def mc_pdfset_xfxq2(pset, prec, member0, nmem, n, x_dev, q2_dev, out_dev, stream=None):
+    _check(lib().mc_pdfset_xfxq2(pset.handle, prec, member0, nmem, n, _ptr(x_dev), _ptr(q2_dev), _ptr(out_dev),
+                                 _stream(stream)))
+
+
+class AlphaS:
+    """Owns an mc_alphas handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def free(self):
+        if self.handle:
+            _check(lib().mc_alphas_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mc_alphas_load(q, alphas):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    a = np.ascontiguousarray(alphas, dtype=np.float64)
+    h = _vp()
+    _check(lib().mc_alphas_load(len(q), q.ctypes.data_as(_dp), a.ctypes.data_as(_dp), ctypes.byref(h)))
+    return AlphaS(h)
+
+
+def mc_alphas_free(a):
+    a.free()
+
+
+def mc_alphas_q2(a, n, q2_dev, out_dev, stream=None):
+    _check(lib().mc_alphas_q2(a.handle, n, _ptr(q2_dev), _ptr(out_dev), _stream(stream)))
 
 
 # ---------------------------------------------------------------- VEGAS
