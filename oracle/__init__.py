@@ -77,6 +77,10 @@ def lib():
         L.orc_alphas_free.argtypes = [ctypes.c_void_p]
         L.orc_alphas_q2.argtypes = [ctypes.c_void_p, _d]
         L.orc_alphas_q2.restype = _d
+        L.orc_acceptance_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
+                                              ctypes.c_int64, _dp]
+        L.orc_unweight_accept.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
+                                          ctypes.c_int64, _dp, _d, ctypes.POINTER(ctypes.c_uint8)]
         for name, args in [("orc_me2_eemumu", [_d] * 6), ("orc_me2_eemumu_trace", [_d] * 4 + [_dp]),
                            ("orc_me2_qqbar_ttbar", [_d] * 4), ("orc_me2_qqbar_ttbar_trace", [_d, _d, _dp]),
                            ("orc_me2_gg_ttbar", [_d] * 4), ("orc_me2_gg_ttbar_colour_ordered", [_d, _d, _dp]),
@@ -243,6 +247,23 @@ class AlphaS:
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.orc_alphas_free(self.handle)
             self.handle = None
+
+
+# ----------------------------------------------------------------- unweighting
+def acceptance_uniforms(seed, iteration, gid, first, n):
+    """The acceptance-rejection uniforms r_i of events first .. first+n-1."""
+    r = np.empty(n)
+    lib().orc_acceptance_uniforms(seed, iteration, gid, first, n, _ptr(r))
+    return r
+
+
+def unweight_accept(seed, iteration, gid, first, weights, wmax):
+    """Boolean mask of the events accepted by w_i > r_i w_max."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    acc = np.zeros(len(w), dtype=np.uint8)
+    lib().orc_unweight_accept(seed, iteration, gid, first, len(w), _ptr(w), wmax,
+                              acc.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return acc.astype(bool)
 
 
 # ----------------------------------------------------------------- |M|^2
