@@ -29,6 +29,12 @@ class EventRecord(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class LabEvent(ctypes.Structure):
+    _fields_ = [("event", ctypes.c_int64), ("weight", ctypes.c_double), ("x1", ctypes.c_double),
+                ("x2", ctypes.c_double), ("p", (ctypes.c_double * 4) * 5), ("proc", ctypes.c_int32),
+                ("nout", ctypes.c_int32)]
+
+
 class IterResult(ctypes.Structure):
     _fields_ = [("sum", ctypes.c_double), ("sum2", ctypes.c_double), ("n", ctypes.c_int64),
                 ("n_nonzero", ctypes.c_int64), ("wmax", ctypes.c_double)]
@@ -81,6 +87,11 @@ def lib():
                                               ctypes.c_int64, _dp]
         L.orc_unweight_accept.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
                                           ctypes.c_int64, _dp, _d, ctypes.POINTER(ctypes.c_uint8)]
+        L.orc_unweight_events.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp,
+                                          ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_int64, ctypes.c_int64, _d, _dp, ctypes.POINTER(LabEvent),
+                                          ctypes.c_int64, _dp]
+        L.orc_unweight_events.restype = ctypes.c_int64
         for name, args in [("orc_me2_eemumu", [_d] * 6), ("orc_me2_eemumu_trace", [_d] * 4 + [_dp]),
                            ("orc_me2_qqbar_ttbar", [_d] * 4), ("orc_me2_qqbar_ttbar_trace", [_d, _d, _dp]),
                            ("orc_me2_gg_ttbar", [_d] * 4), ("orc_me2_gg_ttbar_colour_ordered", [_d, _d, _dp]),
@@ -264,6 +275,24 @@ def unweight_accept(seed, iteration, gid, first, weights, wmax):
     lib().orc_unweight_accept(seed, iteration, gid, first, len(w), _ptr(w), wmax,
                               acc.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     return acc.astype(bool)
+
+
+def unweight_events(itg, pdf, edges, prec, seed, iteration, gid, first, n, wmax=0.0, cap=None):
+    """Unweighted sample of events first .. first+n-1 of one iteration:
+    returns (weights [n], w_max used, list of accepted LabEvent in event
+    order, number accepted).  wmax <= 0: the largest weight of the sample."""
+    c = _integrand_c(itg)
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    cap = n if cap is None else cap
+    w = np.zeros(n)
+    out = (LabEvent * max(cap, 1))()
+    wm = ctypes.c_double()
+    nacc = lib().orc_unweight_events(ctypes.byref(c), pdf.handle if pdf is not None else None, edges.shape[1] - 1,
+                                     _ptr(edges), prec, seed, iteration, gid, first, n, wmax, _ptr(w), out, cap,
+                                     ctypes.byref(wm))
+    if nacc < 0:
+        raise ValueError("process has no event record")
+    return w, wm.value, list(out[:min(nacc, cap)]), nacc
 
 
 # ----------------------------------------------------------------- |M|^2

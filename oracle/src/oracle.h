@@ -122,4 +122,20 @@ typedef struct {
 void* orc_pdf_new(int nx, const double* x, int nq, const double* q, int nflav, const int* pids,
                   const double* xf);
 void orc_pdf_free(void* pdf);
+
+// An accepted event of the unweighted sample in the laboratory frame.
+typedef struct {
+  int64_t event;    // Philox event index
+  double weight;    // its weight in the weighted sample
+  double x1, x2;    // momentum fractions (1, 1 for e+e-)
+  double p[5][4];   // incoming a, b, outgoing 1..nout: (E, px, py, pz)
+  int32_t proc, nout;
+} orc_lab_event;
 }
+
+namespace orc {
+// Uniforms -> VEGAS map -> integrand of one event (integrand.cpp).
+void eval_event(const orc_integrand& in, const Pdf* pdf, int nbins, const double* edges, int prec, uint64_t seed,
+                uint32_t iteration, uint32_t gid, int64_t ev, orc_event_record* rec);
+double acceptance_uniform(uint64_t seed, uint32_t iteration, uint32_t gid, int64_t ev);
+}  // namespace orc
