@@ -17,7 +17,10 @@ timed train-then-sample breakdown); "batch16": sixteen integrands of uneven
 dimension and event count in one persistent launch per iteration (CUDA
 graph, autotuned shape) against the sum of their single launches; and
 "pdf_members": the multi-member PDF evaluation of the thesis's Table
-tab:fktable (400 members, 11 flavours, 2415 x points) against HBM.
+tab:fktable (400 members, 11 flavours, 2415 x points) against HBM; and
+"unweighting": unweighted event generation on the benchmark workload (weights
+pass, device-side acceptance-rejection and export of the accepted events,
+and the native LHE writer's throughput on them).
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a
 bounded sample of events per step on the host cores).
@@ -290,6 +293,56 @@ def pdf_members(M, stream, reps=20):
     return out
 
 
+def unweighting(M, pdf, stream, edges, plain_ms, reps=3):
+    """Unweighted events on the benchmark workload (gg -> ttg, FP32, 1e7
+    events) on the grid the timed steps adapted: the weights pass (the fused
+    kernel writing every weight), the acceptance-rejection with the
+    iteration's own w_max and the export of the accepted events in the
+    laboratory frame (CUDA events around each), then the LHE writer on one
+    iteration's accepted events (device batch, written to a temporary file by
+    the native writer thread with min(16, cores) formatting threads)."""
+    import torch
+    itg = W.gg_ttbarg()
+    n = EVENTS
+    cap = n // 4
+    v = M.mc_vegas_init(14, NBINS, 7000, M.MC_FP32_KAHAN)
+    M.mc_vegas_set_grid(v, edges)
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    ev = torch.empty((cap, M.EVENT_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+    wp_ms, uw_ms, eff, nacc = [], [], [], 0
+    for i in range(reps + 1):
+        r = M.mc_vegas_iterate_weights(v, itg, pdf, n, w, stream)
+        nacc = M.mc_unweight(v, itg, pdf, w, n, r.wmax, ev, cap, stream)
+        if i == 0:
+            continue  # warm-up
+        wp_ms.append(M.mc_vegas_kernel_ms(v))
+        uw_ms.append(M.mc_unweight_ms(v))
+        eff.append(nacc / n)
+    threads = max(1, min(16, os.cpu_count() or 1))
+    fd, path = tempfile.mkstemp(suffix=".lhe")
+    os.close(fd)
+    try:
+        t0 = time.perf_counter()
+        lhe = M.mc_lhe_open(path, itg, threads)
+        M.mc_lhe_write_device(lhe, ev, min(nacc, cap), stream)
+        written = lhe.close(r.sum / r.n, 0.0, r.wmax)
+        t_lhe = time.perf_counter() - t0
+        size = os.path.getsize(path)
+    finally:
+        os.unlink(path)
+    v.free()
+    wpm, uwm = statistics.median(wp_ms), statistics.median(uw_ms)
+    return {"workload": "gg->ttg FP32, 1e7 events per iteration on the adapted grid, w_max = the iteration's "
+                        "largest weight", "efficiency": statistics.mean(eff), "accepted_per_iteration": nacc,
+            "weights_pass_ms": wpm, "plain_pass_ms": plain_ms, "unweight_ms": uwm,
+            "unweight_frac_of_weights_pass": uwm / wpm,
+            "accepted_events_per_s_device": nacc / ((wpm + uwm) / 1e3),
+            "lhe_writer": {"threads": threads, "events": written, "bytes": size, "s": t_lhe,
+                           "events_per_s": written / t_lhe, "MB_per_s": size / t_lhe / 1e6},
+            "thesis_context": "MadFlow's RAMBO sampling: unweighting efficiency about 5% (thesis Sec. "
+                              "\"Unweighted event exporter\")"}
+
+
 def profile_case(case):
     """A small fixed workload for ncu captures (no timing output)."""
     import torch
@@ -302,6 +355,15 @@ def profile_case(case):
         for _ in range(3):
             M.mc_vegas_iterate(v, W.gg_ttbarg(), pdf, 1 << 20)
             M.mc_vegas_refine(v, ALPHA)
+    elif case == "unweight":  # weights pass and unweighting of 2^20 events
+        n = 1 << 20
+        itg = W.gg_ttbarg()
+        v = M.mc_vegas_init(14, NBINS, 0, M.MC_FP32_KAHAN)
+        w = torch.empty(n, dtype=torch.float64, device="cuda")
+        ev = torch.empty((n, M.EVENT_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            r = M.mc_vegas_iterate_weights(v, itg, pdf, n, w)
+            M.mc_unweight(v, itg, pdf, w, n, r.wmax, ev, n)
     elif case == "pdfset":  # the multi-member PDF evaluation, FP32 then FP64
         import numpy as _np
         pset = W.synthetic_pdf_set(nmem=PDF_MEMBERS, seed=0)
@@ -514,6 +576,7 @@ def run_native(args, rank, world):
         line["time_to_target"] = time_to_target(M, pdf, stream)
         line["batch16"] = batch16(M, pdf, stream)
         line["pdf_members"] = pdf_members(M, stream)
+        line["unweighting"] = unweighting(M, pdf, stream, M.mc_vegas_get_grid(v), mean_kernel_ms)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -528,7 +591,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-target", action="store_true")
-    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdfset"], default=None,
+    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdfset", "unweight"], default=None,
                     help="run a small fixed workload for profiling and exit")
     args = ap.parse_args()
     if args.profile_case:

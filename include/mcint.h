@@ -47,6 +47,7 @@ extern "C" {
 #define MC_ENAN (-4)     /* non-finite event weights were produced (counted)    */
 #define MC_ENOCONV (-5)  /* RAMBO's massive rescaling did not converge (counted) */
 #define MC_ETIMEOUT (-6) /* a bounded device wait gave up (result invalid)      */
+#define MC_EIO (-7)      /* a file could not be created or written              */
 
 /* -------------------------------------------------------------- enums */
 #define MC_FP64 0        /* integrand in FP64, 52-bit uniforms                   */
@@ -230,6 +231,103 @@ int mc_vegas_refine(mc_vegas v, double alpha, void* stream);
 int mc_integrate(const mc_integrand* itg, mc_pdf pdf, int niter, int64_t nevents, int nbins,
                  uint64_t seed, uint32_t gid, int prec, double alpha, double target_rel_err,
                  void* stream, mc_result* out, mc_iter_result* per_iter);
+
+/* ------------------------------------------------- unweighted events
+ * Thesis Sec. "Unweighted event exporter" (acceptance-rejection as in
+ * Sec. "Monte Carlo integration"): from a weighted sample with largest
+ * weight w_max, event i is kept when w_i > r_i w_max, i.e. with probability
+ * w_i / w_max; the kept events follow the integrand's distribution with unit
+ * weight, and the efficiency is N_accepted / N_total.  r_i is Philox call 255
+ * of the event's counter (ev lo, ev hi, iteration, gid | 255 << 8):
+ * r = (2k + 1) / 2^53, k the top 52 bits of words 0:1.
+ *
+ * mc_event: one accepted event in the laboratory frame, the content of an
+ * LHE <event> record.  Incoming a (+z) and b (-z) carry x1 sqrt(s)/2 and
+ * x2 sqrt(s)/2; the outgoing momenta are the partonic-frame momenta boosted
+ * along z by the rapidity ln(x1/x2)/2.  e+e- -> mu+mu-: a = e-, b = e+,
+ * outgoing mu-, mu+, x1 = x2 = 1.  gg -> t tbar g: a = b = g, outgoing
+ * t, tbar, g.  200 bytes, field order part of the ABI.
+ */
+typedef struct {
+  int64_t event;     /* Philox event index within its iteration                */
+  double weight;     /* its weight w = f J in the weighted sample (pb)         */
+  double x1, x2;     /* momentum fractions of the incoming partons             */
+  double p[5][4];    /* (E, px, py, pz) in GeV: a, b, outgoing 1..nout; rest 0 */
+  int32_t proc;      /* MC_EE_MUMU, MC_GG_TTBARG or MC_GG_TTBARG_7D            */
+  int32_t nout;      /* outgoing particles: 2 or 3                             */
+} mc_event;
+
+/* mc_vegas_iterate_weights: mc_vegas_iterate that also writes the weight of
+ * every event to weights[0 .. nevents-1] (device, FP64; 0 for events outside
+ * the cuts or with non-finite weight).  nevents < 2^32.  The sums, histograms
+ * and iteration counter behave as in mc_vegas_iterate. */
+int mc_vegas_iterate_weights(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, double* weights,
+                             void* stream, mc_iter_result* out);
+
+/* mc_unweight: the unweighted sample of the last iteration of v, which must
+ * have been made by mc_vegas_iterate_weights with the same integrand and
+ * nevents, and the grid unchanged since (no refine or set_grid in between;
+ * EINVAL otherwise).  weights: that call's output (device).  wmax > 0: the
+ * normalisation (normally out->wmax of that call; a smaller value keeps
+ * every event above it, with its weight truncated).  The accepted events are
+ * written in event order to events[0 .. capacity-1] (device); *n_accepted
+ * (host) receives their number, which may exceed capacity (the surplus is
+ * not written).  Supported: MC_EE_MUMU, MC_GG_TTBARG, MC_GG_TTBARG_7D (EINVAL
+ * for other processes).  Device scratch: 8 KB + 4 bytes per event, kept in
+ * the handle.  Synchronises `stream` to read the count. */
+int mc_unweight(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, const double* weights, int64_t nevents, double wmax,
+                mc_event* events, int64_t capacity, int64_t* n_accepted, void* stream);
+/* Device time (ms) of the last mc_unweight's passes (CUDA events around them
+ * on its stream). */
+int mc_unweight_ms(mc_vegas v, float* ms);
+
+/* Les Houches Event files (LHE 3.0: <LesHouchesEvents version="3.0">, an
+ * <init> block and one <event> block per event), written by a native writer
+ * thread so that the caller (and the GPU) never wait on text formatting or
+ * the disk, as the thesis's LheWriter gathers events in a separate CPU
+ * thread.  Events carry unit weight (IDWTUP = 3, XWGTUP = 1); the colour flow
+ * of gg -> t tbar g is the leading-colour line g1(501,502) g2(503,504) ->
+ * t(501,0) tbar(0,504) g(503,502); particle masses are the nominal ones
+ * (m_top, 0).  Each event ends with a comment line "# mcint <event index>
+ * <weight>".
+ *
+ * mc_lhe_open: creates the file (header and a placeholder <init> block) and
+ * starts the writer with `threads` (1..64) formatting threads.
+ * mc_lhe_write: queues n host events (copied before return).
+ * mc_lhe_write_device: queues n device events: an asynchronous copy on
+ * `stream` into a pinned buffer of the writer, formatted once the copy has
+ * completed; returns without waiting for it.  Later work on `stream` is
+ * ordered after the copy, so the device buffer may be reused by it.
+ * Both block only while 4 batches are already queued.
+ * mc_lhe_close: drains the queue, writes the closing tag, fills the <init>
+ * block with the cross-section, its error and the largest weight (pb), and
+ * closes the file; *n_written (may be NULL) receives the number of events.
+ * The handle is freed even on error.
+ */
+typedef struct mc_lhe_s* mc_lhe;
+int mc_lhe_open(const char* path, const mc_integrand* itg, int threads, mc_lhe* out);
+int mc_lhe_write(mc_lhe w, const mc_event* events, int64_t n);
+int mc_lhe_write_device(mc_lhe w, const mc_event* events, int64_t n, void* stream);
+int mc_lhe_close(mc_lhe w, double xsec, double xerr, double wmax, int64_t* n_written);
+
+/* mc_generate_lhe: event generation as the thesis's MadFlow run: ntrain
+ * VEGAS iterations of nevents that adapt the grid (refinement with damping
+ * alpha), then niter iterations of nevents on the frozen grid, each one a
+ * weights pass, its unweighting with that iteration's w_max, and the export
+ * of the accepted events to the LHE file `path` while the next iteration
+ * runs.  out: the inverse-variance combination of the niter frozen
+ * iterations (the cross-section written to <init>).  stats (may be NULL):
+ * events evaluated and written, device times, host wall time. */
+typedef struct {
+  int64_t n_weighted;   /* events evaluated in the export iterations           */
+  int64_t n_accepted;   /* unweighted events written                           */
+  double iterate_ms;    /* device time of the weights passes                   */
+  double unweight_ms;   /* device time of the unweighting passes               */
+  double wall_ms;       /* host time of the export iterations until closed     */
+} mc_gen_stats;
+int mc_generate_lhe(const mc_integrand* itg, mc_pdf pdf, int ntrain, int niter, int64_t nevents, int nbins,
+                    uint64_t seed, int prec, double alpha, const char* path, int threads, void* stream,
+                    mc_result* out, mc_gen_stats* stats);
 
 /* ------------------------------------------------------------ debugging
  * mc_debug_events: per-event intermediates of events first..first+k-1 of

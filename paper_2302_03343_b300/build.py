@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmcint.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "tc_gemm.cu", "flow.cu", "pdfset.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "tc_gemm.cu", "flow.cu", "pdfset.cu", "unweight.cu",
+           "lhe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,17 +31,21 @@ def _stale(target, deps):
 
 
 def build(force=False, verbose=False, extra=()):
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "mcint.h")]
-    if not force and not _stale(LIB, deps):
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    headers.append(os.path.join(ROOT, "include", "mcint.h"))
+    srcs = [os.path.join(CSRC, f) for f in SOURCES]
+    if not force and not _stale(LIB, headers + srcs):
         return LIB
     objs = []
-    for src in SOURCES:
-        obj = os.path.join(CSRC, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-               "-c", os.path.join(CSRC, src), "-o", obj, *extra]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        subprocess.run(cmd, check=True)
+    for src in srcs:
+        obj = os.path.splitext(src)[0] + ".o"
+        # an object is rebuilt when its source or any header changed
+        if force or extra or verbose or _stale(obj, headers + [src]):
+            cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I",
+                   os.path.join(ROOT, "include"), "-c", src, "-o", obj, *extra]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+            subprocess.run(cmd, check=True)
         objs.append(obj)
     subprocess.run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs], check=True)
     return LIB

@@ -168,6 +168,10 @@ int mc_vegas_free(mc_vegas v) {
   if (v->h_total) cudaFreeHost(v->h_total);
   if (v->k0) cudaEventDestroy(v->k0);
   if (v->k1) cudaEventDestroy(v->k1);
+  if (v->d_uw) cudaFree(v->d_uw);
+  if (v->h_count) cudaFreeHost(v->h_count);
+  if (v->u0) cudaEventDestroy(v->u0);
+  if (v->u1) cudaEventDestroy(v->u1);
   delete v;
   return MC_OK;
 }
@@ -236,6 +240,7 @@ int mc_vegas_set_grid(mc_vegas v, const double* edges) {
       if (!(e[b] > e[b - 1])) return fail(MC_EINVAL, "mc_vegas_set_grid: dim %d edges not increasing", d);
   }
   MC_CUDA(cudaDeviceSynchronize());
+  v->last_valid = false;
   return upload_grid(v, edges);
 }
 
@@ -359,13 +364,16 @@ int mc_launch_shape(const mc_integrand* itg, int prec, int64_t nevents, int* blo
   return MC_OK;
 }
 
-int mc_vegas_iterate(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, void* stream,
-                     mc_iter_result* out) {
+// One iteration (weights: optional per-event weight output, device).
+static int iterate_impl(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, double* weights,
+                        void* stream, mc_iter_result* out) {
   if (!out) return fail(MC_EINVAL, "mc_vegas_iterate: out is NULL");
   std::memset(out, 0, sizeof(*out));
   if (nevents < 0) return fail(MC_EINVAL, "mc_vegas_iterate: negative event count");
   KernelArgs a;
   if (int rc = prepare(v, itg, pdf, &a)) return rc;
+  a.wout = weights;
+  v->last_valid = false;
   const cudaStream_t st = (cudaStream_t)stream;
   const bool fp64 = v->prec == MC_FP64;
   out->n = nevents;
@@ -394,7 +402,81 @@ int mc_vegas_iterate(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t ne
     out->n_bad = t.n_bad + t.n_noconv;
     out->status = t.n_bad ? MC_ENAN : (t.n_noconv ? MC_ENOCONV : MC_OK);
   }
+  v->last_iteration = v->iteration;
+  v->last_n = nevents;
+  v->last_valid = true;
   ++v->iteration;
+  return MC_OK;
+}
+
+int mc_vegas_iterate(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, void* stream,
+                     mc_iter_result* out) {
+  return iterate_impl(v, itg, pdf, nevents, nullptr, stream, out);
+}
+
+int mc_vegas_iterate_weights(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, double* weights,
+                             void* stream, mc_iter_result* out) {
+  if (out) std::memset(out, 0, sizeof(*out));
+  if (nevents > 0 && !weights) return fail(MC_EINVAL, "mc_vegas_iterate_weights: weights is NULL");
+  if (nevents >= (int64_t(1) << 32)) return fail(MC_EINVAL, "mc_vegas_iterate_weights: nevents >= 2^32");
+  return iterate_impl(v, itg, pdf, nevents, weights, stream, out);
+}
+
+int mc_unweight(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, const double* weights, int64_t nevents, double wmax,
+                mc_event* events, int64_t capacity, int64_t* n_accepted, void* stream) {
+  if (!n_accepted) return fail(MC_EINVAL, "mc_unweight: n_accepted is NULL");
+  *n_accepted = 0;
+  if (!v || !itg) return fail(MC_EINVAL, "mc_unweight: NULL handle or integrand");
+  if (itg->proc != MC_EE_MUMU && itg->proc != MC_GG_TTBARG && itg->proc != MC_GG_TTBARG_7D)
+    return fail(MC_EINVAL, "mc_unweight: process %d has no event record", itg->proc);
+  if (!v->last_valid) return fail(MC_EINVAL, "mc_unweight: no iteration on the current grid");
+  if (nevents != v->last_n) return fail(MC_EINVAL, "mc_unweight: nevents differs from the last iteration's");
+  if (capacity < 0 || (capacity > 0 && !events) || (nevents > 0 && !weights) || !std::isfinite(wmax))
+    return fail(MC_EINVAL, "mc_unweight: bad arguments");
+  if (nevents == 0 || !(wmax > 0.0)) return MC_OK;
+  KernelArgs a;
+  if (int rc = prepare(v, itg, pdf, &a)) return rc;
+  a.iteration = v->last_iteration;
+  a.first = 0;
+  a.n = nevents;
+  const cudaStream_t st = (cudaStream_t)stream;
+  const size_t need = mc::unweight_scratch_bytes(nevents, capacity);
+  if (need > v->uw_bytes) {
+    if (v->d_uw) {
+      MC_CUDA(cudaStreamSynchronize(st));
+      cudaFree(v->d_uw);
+      v->d_uw = nullptr;
+      v->uw_bytes = 0;
+    }
+    if (cudaMalloc(&v->d_uw, need) != cudaSuccess) return fail(MC_ENOMEM, "mc_unweight: scratch of %zu bytes", need);
+    v->uw_bytes = need;
+  }
+  if (!v->h_count && cudaMallocHost(&v->h_count, sizeof(unsigned long long)) != cudaSuccess)
+    return fail(MC_ENOMEM, "mc_unweight: pinned count");
+  if (!v->u0) {
+    MC_CUDA(cudaEventCreate(&v->u0));
+    MC_CUDA(cudaEventCreate(&v->u1));
+  }
+  auto* counts = static_cast<unsigned long long*>(v->d_uw);
+  auto* idx = reinterpret_cast<uint32_t*>(counts + mc::kUwMaxChunks + 1);
+  MC_CUDA(cudaEventRecord(v->u0, st));
+  MC_CUDA(mc::unweight_launch(itg->proc, v->prec == MC_FP64, a, weights, wmax, counts, idx, events, capacity,
+                              num_sms(), st));
+  MC_CUDA(cudaEventRecord(v->u1, st));
+  v->uw_timed = true;
+  MC_CUDA(cudaMemcpyAsync(v->h_count, counts + mc::kUwMaxChunks, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                          st));
+  MC_CUDA(cudaStreamSynchronize(st));
+  *n_accepted = int64_t(*v->h_count);
+  return MC_OK;
+}
+
+int mc_unweight_ms(mc_vegas v, float* ms) {
+  if (!v || !ms) return fail(MC_EINVAL, "mc_unweight_ms: NULL argument");
+  *ms = 0.0f;
+  if (!v->uw_timed) return MC_OK;
+  MC_CUDA(cudaEventSynchronize(v->u1));
+  MC_CUDA(cudaEventElapsedTime(ms, v->u0, v->u1));
   return MC_OK;
 }
 
@@ -410,6 +492,7 @@ int mc_vegas_kernel_ms(mc_vegas v, float* ms) {
 int mc_vegas_refine(mc_vegas v, double alpha, void* stream) {
   if (!v) return fail(MC_EINVAL, "mc_vegas_refine: NULL handle");
   if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(MC_EINVAL, "mc_vegas_refine: bad alpha");
+  v->last_valid = false;
   MC_CUDA(mc::launch_refine(v->d_edges, v->d_edges32, v->d_hist_w2, v->d_hist_n, v->ndim, v->nbins, alpha,
                             (cudaStream_t)stream));
   return MC_OK;

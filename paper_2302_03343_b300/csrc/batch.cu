@@ -234,16 +234,16 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
       if (warp < kWsProducerWarps) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
         ok = it.proc == P_GG_TTBARG
-                 ? ws_produce<P_GG_TTBARG>(ka, pdf, sh_edges, sh_n, ring, warp, start, end, warp, kWsProducerWarps,
-                                           seq, acc)
-                 : ws_produce<P_GG_TTBARG_7D>(ka, pdf, sh_edges, sh_n, ring, warp, start, end, warp,
-                                              kWsProducerWarps, seq, acc);
+                 ? ws_produce<P_GG_TTBARG, false>(ka, pdf, sh_edges, sh_n, ring, warp, start, end, warp,
+                                                  kWsProducerWarps, seq, acc)
+                 : ws_produce<P_GG_TTBARG_7D, false>(ka, pdf, sh_edges, sh_n, ring, warp, start, end, warp,
+                                                     kWsProducerWarps, seq, acc);
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsRegs));
       } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
         const int c = warp - kWsProducerWarps;
-        ok = it.proc == P_GG_TTBARG ? ws_consume<P_GG_TTBARG>(ka, sh_w2, ring, c, q0, q1, acc)
-                                    : ws_consume<P_GG_TTBARG_7D>(ka, sh_w2, ring, c, q0, q1, acc);
+        ok = it.proc == P_GG_TTBARG ? ws_consume<P_GG_TTBARG, false>(ka, sh_w2, ring, c, q0, q1, acc)
+                                    : ws_consume<P_GG_TTBARG_7D, false>(ka, sh_w2, ring, c, q0, q1, acc);
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
       }
     } else {

@@ -35,10 +35,11 @@ MC_HD void partial_add(BlockPartial& b, const BlockPartial& o) {
 
 // Uniforms -> VEGAS map (grid in shared memory) -> integrand -> weight, then
 // the Kahan sums and the shared-memory histograms (or, with RECORD, the
-// per-event record `rec`).  H is the histogram accumulation type.
+// per-event record `rec`).  H is the histogram accumulation type.  Returns
+// the event's weight (0 when it is cut or its weight is not finite).
 template <int PROC, bool FP64, bool RECORD, class R, class H>
-MC_D void process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, H* sh_w2, unsigned int* sh_n,
-                        uint64_t ev, double* rec, Acc& acc) {
+MC_D double process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, H* sh_w2, unsigned int* sh_n,
+                          uint64_t ev, double* rec, Acc& acc) {
   constexpr int MAXD = ProcTraits<PROC>::MAXD;
   const int ndim = a.ndim, nb = a.nbins;
   uint64_t k[MAXD];
@@ -80,7 +81,7 @@ MC_D void process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_ed
     rec[MC_REC_W] = w;
     rec[MC_REC_PASS] = double(o.pass);
     rec[MC_REC_STATUS] = double(status);
-    return;
+    return w;
   }
   if (status != 0) {
     if (status == -5)
@@ -107,6 +108,7 @@ MC_D void process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_ed
       atomicAdd(&sh_n[dd * nb + b], 1u);
     }
   }
+  return w;
 }
 
 // Block reduction of the accumulators (warp shuffles, then thread 0 over the

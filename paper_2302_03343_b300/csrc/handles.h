@@ -48,5 +48,16 @@ struct mc_vegas_s {
   mc::BlockPartial* h_total = nullptr;  // pinned
   cudaEvent_t k0 = nullptr, k1 = nullptr;  // around the last integrand launch
   bool timed = false;
+  // the last iteration's events (what mc_unweight selects from): its
+  // iteration counter and size; false once the grid has changed since
+  bool last_valid = false;
+  uint32_t last_iteration = 0;
+  int64_t last_n = 0;
+  // unweighting: device scratch (grow-only), pinned count, timing events
+  void* d_uw = nullptr;
+  size_t uw_bytes = 0;
+  unsigned long long* h_count = nullptr;
+  cudaEvent_t u0 = nullptr, u1 = nullptr;
+  bool uw_timed = false;
 };
 

@@ -45,6 +45,7 @@ struct KernelArgs {
   unsigned int* hist_n;    // [ndim][nbins]
   double* record;          // [n][MC_REC_STRIDE] (debug launches only)
   int* status;             // optional: MC_ETIMEOUT when a bounded wait of the launch gave up
+  double* wout;            // optional, [n]: weight of every event (0 outside the cuts), weights pass
 };
 
 // Shared-memory PDF tables of a launch.

@@ -65,7 +65,9 @@ __global__ void __launch_bounds__(kBlock) integrand_kernel(KernelArgs a) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
     double* rec = RECORD ? a.record + size_t(i) * MC_REC_STRIDE : nullptr;
-    process_event<PROC, FP64, RECORD, R, H>(a, pdf, sh_edges, sh_w2, sh_n, a.first + uint64_t(i), rec, acc);
+    const double w = process_event<PROC, FP64, RECORD, R, H>(a, pdf, sh_edges, sh_w2, sh_n, a.first + uint64_t(i),
+                                                             rec, acc);
+    if (!RECORD && a.wout) a.wout[i] = w;
   }
   if (RECORD) return;
   __shared__ BlockPartial warp_part[kBlock / 32];
@@ -168,7 +170,7 @@ static cudaError_t launch_one(const KernelArgs& a, int grid, size_t smem, cudaSt
 
 template <int PROC>
 static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
-  auto k = ws_integrand_kernel<PROC>;
+  auto k = a.wout ? ws_integrand_kernel<PROC, true> : ws_integrand_kernel<PROC, false>;
   const size_t smem = ws_smem_bytes(a.ndim, a.nbins, a.pdf.nx);
   (void)cudaGetLastError();
   const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

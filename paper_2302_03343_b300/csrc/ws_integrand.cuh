@@ -53,8 +53,11 @@ constexpr int kWsThreads = 32 * (kWsProducerWarps + kWsConsumerWarps);
 constexpr int kWsSlotsPerProducer = 4;
 constexpr int kWsSlots = kWsSlotsPerProducer * kWsProducerWarps;
 // record words of one event (structure of arrays inside a slot: word j of
-// lane e at [j][e]): k[3] (12), rs, lgg, flux, jac, psw (2 words), bins (4)
-enum : int { kWK = 0, kWRs = 12, kWLgg = 13, kWFlux = 14, kWJac = 15, kWPsw = 16, kWBin = 18, kWsWords = 22 };
+// lane e at [j][e]): k[3] (12), rs, lgg, flux, jac, psw (2 words), bins (4),
+// and the event's index in the launch (weights pass only)
+enum : int {
+  kWK = 0, kWRs = 12, kWLgg = 13, kWFlux = 14, kWJac = 15, kWPsw = 16, kWBin = 18, kWIdx = 22, kWsWords = 23
+};
 constexpr unsigned long long kWsWaitNs = 2000000000ull;
 // Registers per thread: the launch gets kWsRegs (65536 / threads, rounded
 // down to a multiple of 8); producers give up to kWsProducerRegs, consumers
@@ -115,9 +118,10 @@ struct WsRing {
 // slots, and ends the stream with a partial slot and one end marker per
 // consumer it feeds.  seq is the warp's slot sequence number and carries
 // over between calls (the slot of seq is p * 4 + seq % 4, used for the
-// (seq / 4)-th time).  The Philox event index is a.first + i.  Returns false
-// when a wait gave up.
-template <int PROC>
+// (seq / 4)-th time).  The Philox event index is a.first + i.  With WOUT the
+// weights pass writes a.wout[i] = 0 for the events that are cut and passes i
+// on in the record.  Returns false when a wait gave up.
+template <int PROC, bool WOUT>
 MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* sh_edges, unsigned int* sh_n,
                      const WsRing& ring, int p, long long lo, long long hi, long long k0, long long dk, int& seq,
                      Acc& acc) {
@@ -163,6 +167,7 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
       }
       st = gg_kinematics<PROC, float>(a, pdf, x, &kin, nullptr);
       if (st == -5) ++acc.nnoconv;
+      if (WOUT && st != 1) a.wout[i] = 0.0;
     }
     const bool pass = st == 1;
     const unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -190,6 +195,7 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
       r[(kWPsw + 1) * 32] = __double2hiint(kin.psw);
 #pragma unroll
       for (int j = 0; j < NW; ++j) r[(kWBin + j) * 32] = binw[j];
+      if (WOUT) r[kWIdx * 32] = uint32_t(i);
     }
     fill += tot;
     if (fill >= 32) {
@@ -215,8 +221,9 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
 // of its producers' slots until every stream it serves has delivered an end
 // marker, and adds the weights w = f J to the Kahan sums, w_max and the
 // histogram of w^2.  q0, q1: the next slot sequence numbers of its (up to two)
-// streams, carried over between calls.  Returns false when a wait gave up.
-template <int PROC>
+// streams, carried over between calls.  With WOUT the weights pass writes
+// a.wout[i] = w.  Returns false when a wait gave up.
+template <int PROC, bool WOUT>
 MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int c, int& q0, int& q1, Acc& acc) {
   constexpr int MAXD = ProcTraits<PROC>::MAXD;
   constexpr int NW = (MAXD + 3) / 4;
@@ -262,6 +269,7 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int 
         ++acc.nbad;
         w = 0.0;
       }
+      if (WOUT) a.wout[r[kWIdx * 32]] = w;
       const double y = w - acc.s_c;
       const double t = acc.s_hi + y;
       acc.s_c = (t - acc.s_hi) - y;
@@ -282,7 +290,9 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int 
   return true;
 }
 
-template <int PROC>
+// WOUT: the weights pass (a.wout receives every event's weight; launches of
+// at most 2^32 - 1 events).
+template <int PROC, bool WOUT>
 __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs a) {
   static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D, "gg -> t tbar g only");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -327,14 +337,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
   if (warp < kWsProducerWarps) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
     int seq = 0;
-    ok = ws_produce<PROC>(a, pdf, sh_edges, sh_n, ring, warp, 0, a.n, (long long)blockIdx.x * kWsProducerWarps + warp,
+    ok = ws_produce<PROC, WOUT>(a, pdf, sh_edges, sh_n, ring, warp, 0, a.n, (long long)blockIdx.x * kWsProducerWarps + warp,
                           (long long)gridDim.x * kWsProducerWarps, seq, acc);
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsRegs));
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
     const int c = warp - kWsProducerWarps;
     int q0 = c / kWsProducerWarps, q1 = q0;
-    ok = ws_consume<PROC>(a, sh_w2, ring, c, q0, q1, acc);
+    ok = ws_consume<PROC, WOUT>(a, sh_w2, ring, c, q0, q1, acc);
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
   }
   if (!ok) atomicExch(&failed, 1);

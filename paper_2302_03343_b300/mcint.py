@@ -15,7 +15,7 @@ from . import workloads
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmcint.so")
 
-MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ENAN, MC_ENOCONV, MC_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ENAN, MC_ENOCONV, MC_ETIMEOUT, MC_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 MC_FP64, MC_FP32_KAHAN = 0, 1
 MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS, MC_GG_TTBARG_7D = 0, 1, 2, 3, 4
 MC_MAX_DIM, MC_MAX_BINS = 16, 256
@@ -32,7 +32,14 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_batch_free", "mc_gemm_bf16", "mc_gemm_bf16_rs", "mc_gemm_bf16_tn", "mc_flow_param_count", "mc_flow_create", "mc_flow_free",
            "mc_flow_set_params", "mc_flow_get_params", "mc_flow_forward", "mc_flow_loss_grad", "mc_flow_adam_step",
            "mc_flow_train", "mc_flow_iterate", "mc_flow_set_fused", "mc_integrate_flow", "mc_pdfset_load",
-           "mc_pdfset_free", "mc_pdfset_xfxq2", "mc_alphas_load", "mc_alphas_free", "mc_alphas_q2")
+           "mc_pdfset_free", "mc_pdfset_xfxq2", "mc_alphas_load", "mc_alphas_free", "mc_alphas_q2",
+           "mc_vegas_iterate_weights", "mc_unweight", "mc_unweight_ms", "mc_lhe_open", "mc_lhe_write",
+           "mc_lhe_write_device", "mc_lhe_close", "mc_generate_lhe")
+
+# mc_event (include/mcint.h): one accepted event in the laboratory frame, 200 bytes
+EVENT_DTYPE = np.dtype([("event", "<i8"), ("weight", "<f8"), ("x1", "<f8"), ("x2", "<f8"), ("p", "<f8", (5, 4)),
+                        ("proc", "<i4"), ("nout", "<i4")])
+assert EVENT_DTYPE.itemsize == 200
 
 
 class McError(RuntimeError):
@@ -59,6 +66,14 @@ class IterResult(ctypes.Structure):
 class FlowCfg(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int32), ("layers", ctypes.c_int32), ("bins", ctypes.c_int32),
                 ("hidden", ctypes.c_int32)]
+
+
+class GenStats(ctypes.Structure):
+    _fields_ = [("n_weighted", ctypes.c_int64), ("n_accepted", ctypes.c_int64), ("iterate_ms", ctypes.c_double),
+                ("unweight_ms", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Result(ctypes.Structure):
@@ -137,6 +152,17 @@ def lib():
             "mc_alphas_load": [i32, _dp, _dp, ctypes.POINTER(_vp)],
             "mc_alphas_free": [_vp],
             "mc_alphas_q2": [_vp, i64, _vp, _vp, _vp],
+            "mc_vegas_iterate_weights": [_vp, ctypes.POINTER(Integrand), _vp, i64, _vp, _vp,
+                                         ctypes.POINTER(IterResult)],
+            "mc_unweight": [_vp, ctypes.POINTER(Integrand), _vp, _vp, i64, d, _vp, i64, ctypes.POINTER(ctypes.c_int64),
+                            _vp],
+            "mc_unweight_ms": [_vp, ctypes.POINTER(ctypes.c_float)],
+            "mc_lhe_open": [ctypes.c_char_p, ctypes.POINTER(Integrand), i32, ctypes.POINTER(_vp)],
+            "mc_lhe_write": [_vp, _vp, i64],
+            "mc_lhe_write_device": [_vp, _vp, i64, _vp],
+            "mc_lhe_close": [_vp, d, d, d, ctypes.POINTER(ctypes.c_int64)],
+            "mc_generate_lhe": [ctypes.POINTER(Integrand), _vp, i32, i32, i64, i32, u64, i32, d, ctypes.c_char_p, i32,
+                                _vp, ctypes.POINTER(Result), ctypes.POINTER(GenStats)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -356,6 +382,92 @@ def mc_vegas_iterate(v, itg, pdf, nevents, stream=None):
     _check(lib().mc_vegas_iterate(v.handle, ctypes.byref(c), pdf.handle if pdf else None, nevents,
                                   _stream(stream), ctypes.byref(r)))
     return r
+
+
+def mc_vegas_iterate_weights(v, itg, pdf, nevents, weights_dev, stream=None):
+    """mc_vegas_iterate that also writes every event's weight to weights_dev
+    (device FP64 [nevents])."""
+    r = IterResult()
+    c = _integrand(itg)
+    _check(lib().mc_vegas_iterate_weights(v.handle, ctypes.byref(c), pdf.handle if pdf else None, nevents,
+                                          _ptr(weights_dev), _stream(stream), ctypes.byref(r)))
+    return r
+
+
+def mc_unweight(v, itg, pdf, weights_dev, nevents, wmax, events_dev, capacity, stream=None):
+    """Unweighted sample of the last iteration: writes up to `capacity` mc_event
+    records (device buffer of capacity * 200 bytes) and returns the number
+    accepted."""
+    c = _integrand(itg)
+    n = ctypes.c_int64()
+    _check(lib().mc_unweight(v.handle, ctypes.byref(c), pdf.handle if pdf else None, _ptr(weights_dev), nevents,
+                             wmax, _ptr(events_dev) if capacity else None, capacity, ctypes.byref(n),
+                             _stream(stream)))
+    return n.value
+
+
+def mc_unweight_ms(v):
+    ms = ctypes.c_float()
+    _check(lib().mc_unweight_ms(v.handle, ctypes.byref(ms)))
+    return ms.value
+
+
+class Lhe:
+    """Owns an mc_lhe writer; close() returns the number of events written."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self, xsec=0.0, xerr=0.0, wmax=0.0):
+        n = ctypes.c_int64()
+        h, self.handle = self.handle, None
+        _check(lib().mc_lhe_close(h, xsec, xerr, wmax, ctypes.byref(n)))
+        return n.value
+
+    def __del__(self):
+        if self.handle:
+            try:
+                self.close()
+            except Exception:
+                pass
+
+
+def mc_lhe_open(path, itg, threads=4):
+    h = _vp()
+    c = _integrand(itg)
+    _check(lib().mc_lhe_open(os.fsencode(path), ctypes.byref(c), threads, ctypes.byref(h)))
+    return Lhe(h)
+
+
+def mc_lhe_write(lhe, events):
+    """Queue host events (a numpy array of EVENT_DTYPE)."""
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    _check(lib().mc_lhe_write(lhe.handle, ev.ctypes.data_as(_vp), len(ev)))
+
+
+def mc_lhe_write_device(lhe, events_dev, n, stream=None):
+    _check(lib().mc_lhe_write_device(lhe.handle, _ptr(events_dev), n, _stream(stream)))
+
+
+def mc_lhe_close(lhe, xsec=0.0, xerr=0.0, wmax=0.0):
+    return lhe.close(xsec, xerr, wmax)
+
+
+def mc_generate_lhe(itg, pdf, path, ntrain, niter, nevents, nbins=50, seed=0, prec=MC_FP64, alpha=1.5, threads=4,
+                    stream=None):
+    """Train the grid, then generate unweighted events to an LHE file; returns
+    (Result, GenStats)."""
+    c = _integrand(itg)
+    out, st = Result(), GenStats()
+    _check(lib().mc_generate_lhe(ctypes.byref(c), pdf.handle if pdf else None, ntrain, niter, nevents, nbins, seed,
+                                 prec, alpha, os.fsencode(path), threads, _stream(stream), ctypes.byref(out),
+                                 ctypes.byref(st)))
+    return out, st
+
+
+def events_from_bytes(buf):
+    """View raw mc_event bytes (e.g. a uint8 tensor copied to the host) as records."""
+    return np.frombuffer(memoryview(buf), dtype=EVENT_DTYPE)
 
 
 def mc_vegas_refine(v, alpha=1.5, stream=None):
@@ -616,5 +728,6 @@ def mc_integrate_flow(itg, pdf, ndim, layers, bins, init_layers, train_steps, tr
     return out, bool(used.value)
 
 
-__all__ = ["McError", "Integrand", "IterResult", "Result", "Pdf", "Vegas", "Flow", "FlowCfg", "workloads",
+__all__ = ["McError", "Integrand", "IterResult", "Result", "GenStats", "Lhe", "EVENT_DTYPE", "Pdf", "Vegas", "Flow",
+           "FlowCfg", "workloads", "events_from_bytes",
            "pack_flow_params", "unpack_flow_params", *SYMBOLS]
