@@ -295,12 +295,15 @@ def pdf_members(M, stream, reps=20):
 
 def unweighting(M, pdf, stream, edges, plain_ms, reps=3):
     """Unweighted events on the benchmark workload (gg -> ttg, FP32, 1e7
-    events) on the grid the timed steps adapted: the weights pass (the fused
-    kernel writing every weight), the acceptance-rejection with the
-    iteration's own w_max and the export of the accepted events in the
-    laboratory frame (CUDA events around each), then the LHE writer on one
-    iteration's accepted events (device batch, written to a temporary file by
-    the native writer thread with min(16, cores) formatting threads)."""
+    events per iteration).  (1) On the grid the timed steps adapted: the
+    weights pass (the fused kernel writing every weight), the
+    acceptance-rejection with the iteration's own w_max and the export of the
+    accepted events in the laboratory frame, each timed with CUDA events.
+    (2) The native LHE writer alone on 2^19 exported events (w_max lowered
+    to the weight quantile that accepts them), device batch to a temporary
+    file, min(16, cores) formatting threads.  (3) mc_generate_lhe end to end
+    from a uniform grid: 5 adapting iterations, then 3 iterations whose
+    accepted events are written while the next one runs (host wall time)."""
     import torch
     itg = W.gg_ttbarg()
     n = EVENTS
@@ -318,29 +321,46 @@ def unweighting(M, pdf, stream, edges, plain_ms, reps=3):
         wp_ms.append(M.mc_vegas_kernel_ms(v))
         uw_ms.append(M.mc_unweight_ms(v))
         eff.append(nacc / n)
+    wpm, uwm = statistics.median(wp_ms), statistics.median(uw_ms)
+    out = {"workload": "gg->ttg FP32, 1e7 events per iteration on the adapted grid, w_max = the iteration's "
+                       "largest weight", "efficiency": statistics.mean(eff), "accepted_per_iteration": nacc,
+           "weights_pass_ms": wpm, "plain_pass_ms": plain_ms, "unweight_ms": uwm,
+           "unweight_frac_of_weights_pass": uwm / wpm,
+           "weighted_events_per_s_device": n / ((wpm + uwm) / 1e3),
+           "accepted_events_per_s_device": nacc / ((wpm + uwm) / 1e3),
+           "thesis_context": "MadFlow's RAMBO sampling: unweighting efficiency about 5% (thesis Sec. "
+                             "\"Unweighted event exporter\")"}
+    # (2) the writer on 2^19 events
+    k = 1 << 19
+    wq = torch.sort(w[w > 0]).values
+    wlow = float(wq[max(0, wq.numel() - 2 * k)].item())
+    nk = min(M.mc_unweight(v, itg, pdf, w, n, wlow, ev, cap, stream), k)
     threads = max(1, min(16, os.cpu_count() or 1))
     fd, path = tempfile.mkstemp(suffix=".lhe")
     os.close(fd)
     try:
         t0 = time.perf_counter()
         lhe = M.mc_lhe_open(path, itg, threads)
-        M.mc_lhe_write_device(lhe, ev, min(nacc, cap), stream)
+        M.mc_lhe_write_device(lhe, ev, nk, stream)
         written = lhe.close(r.sum / r.n, 0.0, r.wmax)
         t_lhe = time.perf_counter() - t0
         size = os.path.getsize(path)
+        out["lhe_writer"] = {"threads": threads, "events": written, "bytes": size, "s": t_lhe,
+                             "events_per_s": written / t_lhe, "MB_per_s": size / t_lhe / 1e6}
+        # (3) end to end
+        res, st = M.mc_generate_lhe(itg, pdf, path, ntrain=5, niter=3, nevents=n, nbins=NBINS, seed=11,
+                                    prec=M.MC_FP32_KAHAN, alpha=ALPHA, threads=threads, stream=stream)
+        out["generate_lhe"] = {"train_iterations": 5, "export_iterations": 3, "events_per_iteration": n,
+                               "written": st.n_accepted, "efficiency": st.n_accepted / st.n_weighted,
+                               "xsec_pb": res.mean, "xsec_rel_err": res.sigma / res.mean,
+                               "device_ms": st.iterate_ms + st.unweight_ms, "wall_ms": st.wall_ms,
+                               "weighted_events_per_s_wall": st.n_weighted / (st.wall_ms / 1e3),
+                               "unweighted_events_per_s_wall": st.n_accepted / (st.wall_ms / 1e3),
+                               "file_bytes": os.path.getsize(path)}
     finally:
         os.unlink(path)
     v.free()
-    wpm, uwm = statistics.median(wp_ms), statistics.median(uw_ms)
-    return {"workload": "gg->ttg FP32, 1e7 events per iteration on the adapted grid, w_max = the iteration's "
-                        "largest weight", "efficiency": statistics.mean(eff), "accepted_per_iteration": nacc,
-            "weights_pass_ms": wpm, "plain_pass_ms": plain_ms, "unweight_ms": uwm,
-            "unweight_frac_of_weights_pass": uwm / wpm,
-            "accepted_events_per_s_device": nacc / ((wpm + uwm) / 1e3),
-            "lhe_writer": {"threads": threads, "events": written, "bytes": size, "s": t_lhe,
-                           "events_per_s": written / t_lhe, "MB_per_s": size / t_lhe / 1e6},
-            "thesis_context": "MadFlow's RAMBO sampling: unweighting efficiency about 5% (thesis Sec. "
-                              "\"Unweighted event exporter\")"}
+    return out
 
 
 def profile_case(case):
@@ -355,15 +375,15 @@ def profile_case(case):
         for _ in range(3):
             M.mc_vegas_iterate(v, W.gg_ttbarg(), pdf, 1 << 20)
             M.mc_vegas_refine(v, ALPHA)
-    elif case == "unweight":  # weights pass and unweighting of 2^20 events
-        n = 1 << 20
+    elif case == "unweight":  # weights pass and unweighting of 2^24 events (134 MB of weights > L2)
+        n = 1 << 24
         itg = W.gg_ttbarg()
         v = M.mc_vegas_init(14, NBINS, 0, M.MC_FP32_KAHAN)
         w = torch.empty(n, dtype=torch.float64, device="cuda")
-        ev = torch.empty((n, M.EVENT_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
+        ev = torch.empty((n // 8, M.EVENT_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
         for _ in range(2):
             r = M.mc_vegas_iterate_weights(v, itg, pdf, n, w)
-            M.mc_unweight(v, itg, pdf, w, n, r.wmax, ev, n)
+            M.mc_unweight(v, itg, pdf, w, n, r.wmax, ev, n // 8)
     elif case == "pdfset":  # the multi-member PDF evaluation, FP32 then FP64
         import numpy as _np
         pset = W.synthetic_pdf_set(nmem=PDF_MEMBERS, seed=0)

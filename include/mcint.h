@@ -273,8 +273,9 @@ int mc_vegas_iterate_weights(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, in
  * written in event order to events[0 .. capacity-1] (device); *n_accepted
  * (host) receives their number, which may exceed capacity (the surplus is
  * not written).  Supported: MC_EE_MUMU, MC_GG_TTBARG, MC_GG_TTBARG_7D (EINVAL
- * for other processes).  Device scratch: 8 KB + 4 bytes per event, kept in
- * the handle.  Synchronises `stream` to read the count. */
+ * for other processes).  Device scratch, kept in the handle: 8 KB, one bit
+ * per event and 4 bytes per event up to capacity.  Synchronises `stream` to
+ * read the count. */
 int mc_unweight(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, const double* weights, int64_t nevents, double wmax,
                 mc_event* events, int64_t capacity, int64_t* n_accepted, void* stream);
 /* Device time (ms) of the last mc_unweight's passes (CUDA events around them

@@ -457,11 +457,10 @@ int mc_unweight(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, const double* w
     MC_CUDA(cudaEventCreate(&v->u0));
     MC_CUDA(cudaEventCreate(&v->u1));
   }
-  auto* counts = static_cast<unsigned long long*>(v->d_uw);
-  auto* idx = reinterpret_cast<uint32_t*>(counts + mc::kUwMaxChunks + 1);
+  const auto* counts = static_cast<const unsigned long long*>(v->d_uw);
   MC_CUDA(cudaEventRecord(v->u0, st));
-  MC_CUDA(mc::unweight_launch(itg->proc, v->prec == MC_FP64, a, weights, wmax, counts, idx, events, capacity,
-                              num_sms(), st));
+  MC_CUDA(mc::unweight_launch(itg->proc, v->prec == MC_FP64, a, weights, wmax, v->d_uw, events, capacity, num_sms(),
+                              st));
   MC_CUDA(cudaEventRecord(v->u1, st));
   v->uw_timed = true;
   MC_CUDA(cudaMemcpyAsync(v->h_count, counts + mc::kUwMaxChunks, sizeof(unsigned long long), cudaMemcpyDeviceToHost,

@@ -76,10 +76,14 @@ template <class R> MC_D sp4<R> prop_row(const sp4<R>& s, const v4<R>& p, R m, R 
 }
 
 // Two-component helicity eigenstates chi_+, chi_- along the direction of p.
+// a = |p| + p_z is formed as p_T^2 / (|p| - p_z) when p_z < 0, so that it
+// keeps full relative precision for momenta close to the -z axis (the direct
+// sum cancels there).
 template <class R> MC_D void helicity_states(const v4<R>& p, cx<R>* chip, cx<R>* chim) {
-  const R pabs = m_sqrt(p.x * p.x + p.y * p.y + p.z * p.z);
-  const R a = pabs + p.z;
-  if (a <= pabs * R(1e-6) || a <= R(0)) {  // along -z
+  const R pt2 = p.x * p.x + p.y * p.y;
+  const R pabs = m_sqrt(pt2 + p.z * p.z);
+  const R a = p.z >= R(0) ? pabs + p.z : pt2 / (pabs - p.z);
+  if (!(a > R(0))) {  // along -z (or p = 0)
     chip[0] = mkc(R(0), R(0)); chip[1] = mkc(R(1), R(0));
     chim[0] = mkc(R(-1), R(0)); chim[1] = mkc(R(0), R(0));
     return;

@@ -27,14 +27,13 @@ cudaError_t launch_integrand_record(int proc, bool fp64, const KernelArgs& a, in
 cudaError_t launch_finalize(const BlockPartial* parts, int nblocks, BlockPartial* out, cudaStream_t st);
 cudaError_t launch_refine(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim, int nbins,
                           double alpha, cudaStream_t st);
-// Unweighting of the events of a weights pass (unweight.cu): count, scan,
-// ordered compaction and export of the accepted events.  Scratch of
-// unweight_scratch_bytes(n, cap) bytes: counts [kUwMaxChunks + 1] (the last
-// entry receives the number accepted), then idx [min(n, cap)].
+// Unweighting of the events of a weights pass (unweight.cu): decision,
+// scan, ordered compaction and export of the accepted events.  Scratch of
+// unweight_scratch_bytes(n, cap) bytes, starting with counts
+// [kUwMaxChunks + 1] whose last entry receives the number accepted.
 constexpr int kUwMaxChunks = 1024;
-cudaError_t unweight_launch(int proc, bool fp64, const KernelArgs& a, const double* w, double wmax,
-                            unsigned long long* counts, uint32_t* idx, mc_event* out, long long cap, int nsm,
-                            cudaStream_t st);
+cudaError_t unweight_launch(int proc, bool fp64, const KernelArgs& a, const double* w, double wmax, void* scratch,
+                            mc_event* out, long long cap, int nsm, cudaStream_t st);
 size_t unweight_scratch_bytes(long long n, long long cap);
 cudaError_t launch_pdf_xfxq2(const PdfDev& pdf, bool fp64, long long n, const double* x, const double* q2,
                              double* out, cudaStream_t st);

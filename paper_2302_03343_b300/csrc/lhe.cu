@@ -55,12 +55,90 @@ struct Staging {
   cudaEvent_t ready = nullptr;
 };
 
-// One particle line: IDUP ISTUP MOTHUP(1,2) ICOLUP(1,2) PUP(1..5) VTIMUP SPINUP.
-void put_particle(std::string& s, int id, int status, int m1, int m2, int c1, int c2, const double* p, double mass) {
-  char line[256];
-  const int k = snprintf(line, sizeof(line), " %8d %2d %4d %4d %4d %4d %+.10e %+.10e %+.10e %+.10e %+.10e 0. 9.\n", id,
-                         status, m1, m2, c1, c2, p[1], p[2], p[3], p[0], mass);
-  s.append(line, size_t(k));
+// Writes v in the layout of printf's "%+.10e" (sign, d.dddddddddd, 'e',
+// exponent sign, at least two exponent digits) and returns the end.  The
+// eleven significant digits are llround(|v| 10^(10 - e)) with e the decimal
+// exponent, the scaling done in double precision by exact powers of ten
+// (|e| <= 22), so the last digit can differ from exact decimal rounding when
+// |v| lies within a few units of 1e-16 (relative) of a rounding boundary.
+// Non-finite values go through snprintf.
+char* put_e10(char* o, double v) {
+  static const double p10[23] = {1e0,  1e1,  1e2,  1e3,  1e4,  1e5,  1e6,  1e7,  1e8,  1e9,  1e10, 1e11,
+                                 1e12, 1e13, 1e14, 1e15, 1e16, 1e17, 1e18, 1e19, 1e20, 1e21, 1e22};
+  if (!std::isfinite(v)) return o + snprintf(o, 32, "%+.10e", v);
+  *o++ = std::signbit(v) ? '-' : '+';
+  const double a = std::fabs(v);
+  if (a == 0.0) {
+    std::memcpy(o, "0.0000000000e+00", 16);
+    return o + 16;
+  }
+  int e = int(std::floor(std::log10(a)));
+  auto digits = [&](int ex) {
+    int k = 10 - ex;  // |v| 10^k has eleven digits before the point
+    double m = a;
+    if (k > 22 || k < -22) {  // outside the exact powers: steps of at most 10^200, no overflow
+      while (k > 200) {
+        m *= 1e200;
+        k -= 200;
+      }
+      while (k < -200) {
+        m /= 1e200;
+        k += 200;
+      }
+      m = k >= 0 ? m * std::pow(10.0, k) : m / std::pow(10.0, -k);
+    } else {
+      m = k >= 0 ? m * p10[k] : m / p10[-k];
+    }
+    return (unsigned long long)std::llround(m);
+  };
+  unsigned long long d = digits(e);
+  if (d >= 100000000000ull) d = digits(++e);  // log10 fell short, or rounding carried
+  if (d < 10000000000ull) d = digits(--e);    // log10 overshot
+  if (d >= 100000000000ull) {                 // the carry case of the retry: 9.99...95 -> 10
+    d = 10000000000ull;
+    ++e;
+  }
+  char dig[11];
+  for (int i = 10; i >= 0; --i) {
+    dig[i] = char('0' + d % 10);
+    d /= 10;
+  }
+  *o++ = dig[0];
+  *o++ = '.';
+  std::memcpy(o, dig + 1, 10);
+  o += 10;
+  *o++ = 'e';
+  *o++ = e < 0 ? '-' : '+';
+  const int ae = e < 0 ? -e : e;
+  if (ae >= 100) *o++ = char('0' + ae / 100);
+  *o++ = char('0' + (ae / 10) % 10);
+  *o++ = char('0' + ae % 10);
+  return o;
+}
+
+// One particle line: IDUP ISTUP MOTHUP(1,2) ICOLUP(1,2) PUP(1..5) VTIMUP
+// SPINUP; the integer part of a particle slot is fixed and formatted once.
+struct ParticleSlot {
+  char head[48];
+  int len;
+  ParticleSlot(int id, int status, int m1, int m2, int c1, int c2) {
+    len = snprintf(head, sizeof(head), " %8d %2d %4d %4d %4d %4d", id, status, m1, m2, c1, c2);
+  }
+};
+
+void put_particle(std::string& s, const ParticleSlot& slot, const double* p, double mass) {
+  char line[160];
+  char* o = line;
+  std::memcpy(o, slot.head, size_t(slot.len));
+  o += slot.len;
+  const double v[5] = {p[1], p[2], p[3], p[0], mass};
+  for (double x : v) {
+    *o++ = ' ';
+    o = put_e10(o, x);
+  }
+  std::memcpy(o, " 0. 9.\n", 7);
+  o += 7;
+  s.append(line, size_t(o - line));
 }
 
 }  // namespace
@@ -81,45 +159,50 @@ struct mc_lhe_s {
   int64_t written = 0;
   int error = MC_OK;
   std::string err_msg;
+  std::vector<std::string> parts;  // formatted slices of the current batch (writer thread only)
 
   void append_event(std::string& s, const mc_event& e) const {
+    // e+e- -> mu+mu-, and g g -> t tbar g with the leading-colour flow
+    // g1(501,502) g2(503,504) -> t(501,0) tbar(0,504) g(503,502)
+    static const ParticleSlot ee[4] = {{11, -1, 0, 0, 0, 0}, {-11, -1, 0, 0, 0, 0}, {13, 1, 1, 2, 0, 0},
+                                       {-13, 1, 1, 2, 0, 0}};
+    static const ParticleSlot gg[5] = {{21, -1, 0, 0, 501, 502}, {21, -1, 0, 0, 503, 504}, {6, 1, 1, 2, 501, 0},
+                                       {-6, 1, 1, 2, 0, 504}, {21, 1, 1, 2, 503, 502}};
     char line[160];
-    const int nup = 2 + e.nout;
-    int k = snprintf(line, sizeof(line), "<event>\n %d 1 +1.0000000000e+00 %+.10e %+.10e %+.10e\n", nup, scale, aqed,
-                     aqcd);
-    s.append(line, size_t(k));
-    if (proc == MC_EE_MUMU) {
-      put_particle(s, 11, -1, 0, 0, 0, 0, e.p[0], 0.0);
-      put_particle(s, -11, -1, 0, 0, 0, 0, e.p[1], 0.0);
-      put_particle(s, 13, 1, 1, 2, 0, 0, e.p[2], 0.0);
-      put_particle(s, -13, 1, 1, 2, 0, 0, e.p[3], 0.0);
-    } else {
-      // leading-colour flow g1(501,502) g2(503,504) -> t(501,0) tbar(0,504) g(503,502)
-      put_particle(s, 21, -1, 0, 0, 501, 502, e.p[0], 0.0);
-      put_particle(s, 21, -1, 0, 0, 503, 504, e.p[1], 0.0);
-      put_particle(s, 6, 1, 1, 2, 501, 0, e.p[2], m_top);
-      put_particle(s, -6, 1, 1, 2, 0, 504, e.p[3], m_top);
-      put_particle(s, 21, 1, 1, 2, 503, 502, e.p[4], 0.0);
+    int k = snprintf(line, sizeof(line), "<event>\n %d 1 +1.0000000000e+00", 2 + e.nout);
+    char* o = line + k;
+    for (double x : {scale, aqed, aqcd}) {
+      *o++ = ' ';
+      o = put_e10(o, x);
     }
-    k = snprintf(line, sizeof(line), "# mcint %lld %+.10e\n</event>\n", (long long)e.event, e.weight);
-    s.append(line, size_t(k));
+    *o++ = '\n';
+    s.append(line, size_t(o - line));
+    if (proc == MC_EE_MUMU) {
+      for (int i = 0; i < 4; ++i) put_particle(s, ee[i], e.p[i], 0.0);
+    } else {
+      for (int i = 0; i < 5; ++i) put_particle(s, gg[i], e.p[i], i == 2 || i == 3 ? m_top : 0.0);
+    }
+    k = snprintf(line, sizeof(line), "# mcint %lld ", (long long)e.event);
+    o = put_e10(line + k, e.weight);
+    std::memcpy(o, "\n</event>\n", 10);
+    o += 10;
+    s.append(line, size_t(o - line));
   }
 
-  // Formats events[0 .. n) with `threads` threads and appends them in order.
+  // Formats events[0 .. n) in `threads` slices, one string each (kept
+  // between batches), and appends them in order; slice t is written while
+  // the slices after it are still being formatted.
   void format_and_write(const mc_event* ev, int64_t n) {
     const int T = int(std::min<int64_t>(threads, std::max<int64_t>(1, n / 256)));
-    std::vector<std::string> parts(static_cast<size_t>(T));
+    if (int(parts.size()) < T) parts.resize(size_t(T));
     auto work = [&](int t) {
       const int64_t lo = n * t / T, hi = n * (t + 1) / T;
       std::string& s = parts[size_t(t)];
+      s.clear();
       s.reserve(size_t(hi - lo) * 1024);
       for (int64_t i = lo; i < hi; ++i) append_event(s, ev[i]);
     };
-    std::vector<std::thread> pool_threads;
-    for (int t = 1; t < T; ++t) pool_threads.emplace_back(work, t);
-    work(0);
-    for (auto& th : pool_threads) th.join();
-    for (const auto& s : parts)
+    auto put = [&](const std::string& s) {
       if (fwrite(s.data(), 1, s.size(), f) != s.size()) {
         std::lock_guard<std::mutex> lk(m);
         if (!error) {
@@ -127,6 +210,15 @@ struct mc_lhe_s {
           err_msg = "mc_lhe: short write";
         }
       }
+    };
+    std::vector<std::thread> pool_threads;
+    for (int t = 1; t < T; ++t) pool_threads.emplace_back(work, t);
+    work(0);
+    put(parts[0]);
+    for (int t = 1; t < T; ++t) {
+      pool_threads[size_t(t - 1)].join();
+      put(parts[size_t(t)]);
+    }
   }
 
   void run() {

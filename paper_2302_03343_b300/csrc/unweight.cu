@@ -8,13 +8,15 @@
 // (KernelArgs::wout, 8 bytes per event); r_i is Philox call 255 of the
 // event's own counter, a call the integrand never makes, so every decision
 // can be re-derived from (seed, iteration, integrand id, event index).
-// Four passes, all bound by reading the weights except the last:
-//  * uw_count_kernel: block b takes the contiguous chunk b of the events and
-//    counts its accepted events;
+// Four passes:
+//  * uw_count_kernel: block b takes the contiguous chunk b of the events,
+//    decides every event (one read of its weight, one Philox call for the
+//    events of positive weight), stores the decisions as a bit mask (one
+//    word per 32 events, a warp ballot) and counts them;
 //  * uw_scan_kernel: exclusive scan of the per-chunk counts (one block);
-//  * uw_compact_kernel: re-evaluates the decisions chunk by chunk and writes
-//    the indices of the accepted events in event order (warp ballots plus a
-//    block prefix), so the output order does not depend on scheduling;
+//  * uw_compact_kernel: reads the mask chunk by chunk and writes the indices
+//    of the accepted events in event order (block prefix over the warps'
+//    population counts), so the output order does not depend on scheduling;
 //  * uw_export_kernel: one thread per accepted event regenerates the event
 //    from its Philox counter (uniforms, VEGAS map, phase space) through the
 //    recording path of the fused integrand and writes its mc_event record in
@@ -55,11 +57,20 @@ MC_D bool uw_accept(const UwArgs& u, long long i) {
   return wi > 0.0 && wi > acceptance_uniform(u.seed, u.iteration, u.gid, u.first + uint64_t(i)) * u.wmax;
 }
 
-__global__ void __launch_bounds__(kUwBlock) uw_count_kernel(UwArgs u, unsigned long long* counts) {
+// Chunks are multiples of kUwBlock events, so the 32 events of a warp in one
+// round share one mask word: word (r0 + 32 warp) / 32.
+__global__ void __launch_bounds__(kUwBlock) uw_count_kernel(UwArgs u, unsigned long long* counts, uint32_t* mask) {
   const long long lo = (long long)blockIdx.x * u.chunk;
   const long long hi = min(u.n, lo + u.chunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned int c = 0;
-  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) c += uw_accept(u, i);
+  for (long long r0 = lo; r0 < hi; r0 += kUwBlock) {
+    const long long i = r0 + threadIdx.x;
+    const bool acc = i < hi && uw_accept(u, i);
+    const unsigned m = __ballot_sync(0xffffffffu, acc);
+    if (lane == 0 && r0 + 32 * wid < hi) mask[(r0 >> 5) + wid] = m;
+    c += acc;
+  }
   for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
   __shared__ unsigned int part[kUwBlock / 32];
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
@@ -99,9 +110,9 @@ __global__ void __launch_bounds__(1024) uw_scan_kernel(unsigned long long* count
 }
 
 // Indices (within the launch) of the accepted events, in event order, to
-// idx[offset ..], the first `cap` of them.
+// idx[offset ..], the first `cap` of them, from the decision mask.
 __global__ void __launch_bounds__(kUwBlock) uw_compact_kernel(UwArgs u, const unsigned long long* offsets,
-                                                               uint32_t* idx, long long cap) {
+                                                               const uint32_t* mask, uint32_t* idx, long long cap) {
   const long long lo = (long long)blockIdx.x * u.chunk;
   const long long hi = min(u.n, lo + u.chunk);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -109,8 +120,8 @@ __global__ void __launch_bounds__(kUwBlock) uw_compact_kernel(UwArgs u, const un
   unsigned long long base = offsets[blockIdx.x];
   for (long long r0 = lo; r0 < hi; r0 += kUwBlock) {
     const long long i = r0 + threadIdx.x;
-    const bool acc = i < hi && uw_accept(u, i);
-    const unsigned m = __ballot_sync(0xffffffffu, acc);
+    const unsigned m = r0 + 32 * wid < hi ? mask[(r0 >> 5) + wid] : 0u;
+    const bool acc = (m >> lane) & 1u;
     if (lane == 0) wcount[wid] = __popc(m);
     __syncthreads();
     unsigned int before = 0, round = 0;
@@ -216,20 +227,24 @@ static cudaError_t launch_export(const KernelArgs& a, const uint32_t* idx, const
 }
 
 // The four passes on `st`.  a: the arguments of the weights pass (grid,
-// seed, iteration, gid, first, n); scratch: counts [kUwMaxChunks + 1]
-// (the last entry receives the total) and idx [min(n, cap)].
-cudaError_t unweight_launch(int proc, bool fp64, const KernelArgs& a, const double* w, double wmax,
-                            unsigned long long* counts, uint32_t* idx, mc_event* out, long long cap, int nsm,
-                            cudaStream_t st) {
+// seed, iteration, gid, first, n); scratch (unweight_scratch_bytes): counts
+// [kUwMaxChunks + 1] (the last entry receives the total), the decision mask
+// [ceil(n / 32)], idx [min(n, cap)].
+cudaError_t unweight_launch(int proc, bool fp64, const KernelArgs& a, const double* w, double wmax, void* scratch,
+                            mc_event* out, long long cap, int nsm, cudaStream_t st) {
   const long long n = a.n;
+  auto* counts = static_cast<unsigned long long*>(scratch);
   unsigned long long* total = counts + kUwMaxChunks;
+  auto* mask = reinterpret_cast<uint32_t*>(counts + kUwMaxChunks + 1);
+  uint32_t* idx = mask + (n + 31) / 32;
   int nchunks = int(min((long long)kUwMaxChunks, (n + 4 * kUwBlock - 1) / (4 * kUwBlock)));
   if (nchunks < 1) nchunks = 1;
-  UwArgs u = {w, n, (n + nchunks - 1) / nchunks, wmax, a.seed, a.first, a.iteration, a.gid};
+  const long long chunk = ((n + nchunks - 1) / nchunks + kUwBlock - 1) / kUwBlock * kUwBlock;
+  UwArgs u = {w, n, chunk, wmax, a.seed, a.first, a.iteration, a.gid};
   (void)cudaGetLastError();
-  uw_count_kernel<<<nchunks, kUwBlock, 0, st>>>(u, counts);
+  uw_count_kernel<<<nchunks, kUwBlock, 0, st>>>(u, counts, mask);
   uw_scan_kernel<<<1, 1024, 0, st>>>(counts, nchunks, total);
-  uw_compact_kernel<<<nchunks, kUwBlock, 0, st>>>(u, counts, idx, cap);
+  uw_compact_kernel<<<nchunks, kUwBlock, 0, st>>>(u, counts, mask, idx, cap);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || cap == 0) return e;
   const long long maxg = (min(n, cap) + kBlock - 1) / kBlock;
@@ -249,7 +264,8 @@ cudaError_t unweight_launch(int proc, bool fp64, const KernelArgs& a, const doub
 }
 
 size_t unweight_scratch_bytes(long long n, long long cap) {
-  return sizeof(unsigned long long) * (kUwMaxChunks + 1) + sizeof(uint32_t) * size_t(max(0ll, min(n, cap)));
+  return sizeof(unsigned long long) * (kUwMaxChunks + 1) + sizeof(uint32_t) * size_t((n + 31) / 32) +
+         sizeof(uint32_t) * size_t(max(0ll, min(n, cap)));
 }
 
 }  // namespace mc

@@ -2,7 +2,11 @@
 "Unweighted event exporter") against the FP64 oracle (oracle/src/unweight.cpp)
 on the same Philox streams.
 
-Bars: FP64 weights within 1e-12 relative with the same zero pattern; the
+Bars: FP64 weights within 1e-12 relative with the same zero pattern (where
+the synthetic PDF's interpolant crosses zero near x -> 1 a weight is small
+and carries the rounding of the stencil, so the bound there is 1e-12 of
+1e-3 of the sample's largest weight, as for the luminosities in
+test_gpu_parity.py); the
 accepted sets equal, except for events whose weight lies within rounding of
 the acceptance threshold r_i w_max (both sides decide in FP64); exported
 laboratory-frame records within 1e-12 of the oracle's (FP64) or FP32
@@ -87,7 +91,8 @@ def test_weights_pass(gpu, oracle_pdf, name, prec, n):
     both = (wg != 0) & (wo != 0)
     if prec == M.MC_FP64:
         assert np.array_equal(wg != 0, wo != 0)
-        assert np.max(rel(wg[both], wo[both])) < 1e-12
+        floor = 1e-3 * np.abs(wo).max()
+        assert np.all(np.abs(wg - wo) <= 1e-12 * np.maximum(np.abs(wo), floor)), np.max(rel(wg[both], wo[both]))
     else:
         assert np.count_nonzero((wg != 0) != (wo != 0)) <= max(1, n // 1000)
         e = rel(wg[both], wo[both])
@@ -98,16 +103,17 @@ def test_weights_pass(gpu, oracle_pdf, name, prec, n):
 @pytest.mark.parametrize("name,prec,n", [("ee", M.MC_FP64, 20000), ("gg", M.MC_FP64, 6000), ("gg7", M.MC_FP64, 6000),
                                          ("gg", M.MC_FP32_KAHAN, 20000), ("gg7", M.MC_FP32_KAHAN, 20000)])
 def test_unweighted_sample_against_oracle(gpu, oracle_pdf, name, prec, n):
-    """The accepted set and the laboratory-frame records.  w_max: 5% of each
+    """The accepted set and the laboratory-frame records.  w_max: 2% of each
     side's own largest weight (events above it are always kept), so that a
-    few hundred events survive on a grid that is far from adapted."""
+    hundred events or more survive on a grid that is far from adapted."""
     itg = PROCS[name]
+    frac = 0.02
     edges = random_grid(O.process_ndim(itg), 50, 4)
     v, w, r = gpu_weights(gpu, itg, prec, edges, n, iteration=1, seed=3)
-    nacc, ev = gpu_unweight(v, gpu, itg, w, n, 0.05 * r.wmax, n)
+    nacc, ev = gpu_unweight(v, gpu, itg, w, n, frac * r.wmax, n)
     assert nacc == len(ev) > 50
     wo, wmax_o, evo, nacc_o = O.unweight_events(itg, oracle_pdf, edges, prec, 3, 1, 0, 0, n)
-    wo2, _, evo, nacc_o = O.unweight_events(itg, oracle_pdf, edges, prec, 3, 1, 0, 0, n, wmax=0.05 * wmax_o)
+    wo2, _, evo, nacc_o = O.unweight_events(itg, oracle_pdf, edges, prec, 3, 1, 0, 0, n, wmax=frac * wmax_o)
     assert np.array_equal(wo, wo2)
     ig = [int(e) for e in ev["event"]]
     io = [e.event for e in evo]
@@ -119,7 +125,7 @@ def test_unweighted_sample_against_oracle(gpu, oracle_pdf, name, prec, n):
     tol = 1e-11 if prec == M.MC_FP64 else 2e-2
     diff = set(ig) ^ set(io)
     for i in diff:
-        assert abs(wo[i] - r_acc[i] * 0.05 * wmax_o) <= tol * max(wo[i], r_acc[i] * 0.05 * wmax_o), i
+        assert abs(wo[i] - r_acc[i] * frac * wmax_o) <= tol * max(wo[i], r_acc[i] * frac * wmax_o), i
     assert len(diff) <= (0 if prec == M.MC_FP64 else max(2, nacc // 50)) + 2
     # records of the events both accepted
     rec_o = {e.event: e for e in evo}

@@ -128,3 +128,42 @@ def test_empty_file_and_errors(L, tmp_path):
     with pytest.raises(M.McError):
         M.mc_lhe_open(str(tmp_path / "x.lhe"), itg, threads=0)
     assert not os.path.exists(tmp_path / "x.lhe")
+
+
+def _same_e10(got, ref):
+    """got equals printf's %+.10e string ref, or differs from it by one unit
+    in the eleventh significant digit (the writer scales in double precision)."""
+    if got == ref:
+        return True
+    unit = 10.0 ** (int(ref.split("e")[1]) - 10)
+    return abs(float(got) - float(ref)) <= 1.01 * unit
+
+
+def test_number_format_matches_printf(L, tmp_path):
+    """The writer's own %+.10e formatter against Python's printf-style
+    formatting of the same doubles, including zeros of both signs, extreme
+    exponents and values at decade boundaries."""
+    itg = W.gg_ttbarg(13000.0)
+    ev = oracle_sample(itg, 1500, pdf=O.Pdf(W.synthetic_pdf_grid(0)))
+    special = np.zeros(3, dtype=M.EVENT_DTYPE)
+    vals = [[0.0, -0.0, 1e-300, -2.5e300], [9.99999999999995, 99999.99999999995, 1e22, 1e23],
+            [123456.789012345678, -7.0e-5, 5e-324, 1.7976931348623157e308]]
+    for i in range(3):
+        special[i]["event"] = 10 ** 9 + i
+        special[i]["weight"] = [1e-150, 9.999999999995e-7, 1e100][i]
+        special[i]["nout"] = 3
+        special[i]["proc"] = M.MC_GG_TTBARG
+        for k in range(5):
+            special[i]["p"][k] = vals[i]
+    path = tmp_path / "fmt.lhe"
+    write(path, itg, [ev, special], threads=2)
+    text = path.read_text()
+    lines = [ln.split() for ln in text.split("<event>")[1:]]
+    for e, toks in zip(np.concatenate([ev, special]), lines):
+        # 6 header tokens, then 5 particle lines of 13 tokens, then "# mcint idx weight"
+        for k in range(5):
+            t = toks[6 + 13 * k: 6 + 13 * (k + 1)]
+            for got, v in zip(t[6:10], (e["p"][k][1], e["p"][k][2], e["p"][k][3], e["p"][k][0])):
+                ref = f"{v:+.10e}"
+                assert _same_e10(got, ref), (got, ref)
+        assert _same_e10(toks[6 + 65 + 3], f"{e['weight']:+.10e}")
