@@ -22,6 +22,8 @@
 //    recording path of the fused integrand and writes its mc_event record in
 //    the laboratory frame.  Only the accepted fraction (a few per cent) is
 //    regenerated, densely packed, so no warp runs a mostly idle |M|^2.
+#include <cstring>
+
 #include "../../include/mcint.h"
 #include "event.cuh"
 #include "handles.h"
@@ -35,26 +37,60 @@ constexpr int kUwBlock = 256;  // kUwMaxChunks (launch.h): chunks of the count /
 
 // Acceptance uniform of event ev: counter (ev lo, ev hi, iteration,
 // gid | 255 << 8), r = (2k + 1) 2^-53 with k the top 52 bits of words 0:1,
-// so r lies strictly inside (0, 1).
-MC_D double acceptance_uniform(uint64_t seed, uint32_t iteration, uint32_t gid, uint64_t ev) {
+// so r lies strictly inside (0, 1).  Returned as the odd integer 2k + 1.
+MC_D uint64_t acceptance_odd(uint64_t seed, uint32_t iteration, uint32_t gid, uint64_t ev) {
   const uint4 w = philox4x32_10(make_uint4(uint32_t(ev), uint32_t(ev >> 32), iteration, (gid & 0xffu) | (255u << 8)),
                                 make_uint2(uint32_t(seed), uint32_t(seed >> 32)));
-  const uint64_t k = ((uint64_t(w.x) << 32) | w.y) >> 12;
-  return double(2 * k + 1) * 0x1p-53;
+  return ((((uint64_t(w.x) << 32) | w.y) >> 12) << 1) | 1u;
+}
+
+// The FP64 bits of RN(r w_max), r = odd 2^-53, for a w_max whose biased
+// exponent e_b is at least 54 (so the product is a normal number): the
+// integer product P = odd * M (M the 53-bit significand of w_max, P below
+// 2^106) rounded to 53 significant bits, to nearest with ties to even, and
+// the exponent e_b - 53 + (bits dropped).  This is the IEEE product done
+// with integer multiply-adds; B300 issues FP64 arithmetic at 1/64 of the
+// FP32 rate, and three FP64 operations per event made the decision pass
+// FP64-bound.
+MC_D uint64_t product_bits(uint64_t odd, uint64_t m_w, int e_b) {
+  const uint64_t lo = odd * m_w, hi = __umul64hi(odd, m_w);
+  const int lead = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // >= 52
+  const int s = lead - 52;                                                               // 0 .. 53
+  uint64_t m = lo;
+  if (s > 0) {
+    m = (lo >> s) | (hi << (64 - s));
+    const uint64_t rem = lo & ((1ull << s) - 1), half = 1ull << (s - 1);
+    m += (rem > half || (rem == half && (m & 1u))) ? 1u : 0u;
+  }
+  int e = e_b - 53 + s;
+  if (m == (1ull << 53)) {
+    m >>= 1;
+    ++e;
+  }
+  return (uint64_t(e) << 52) | (m - (1ull << 52));
 }
 
 struct UwArgs {
   const double* w;  // [n] weights of the sample
   long long n, chunk;
   double wmax;
+  uint64_t m_w;     // significand of wmax with its hidden bit (integer path)
+  int e_w;          // biased exponent of wmax; 0: take the FP64 path
   uint64_t seed, first;
   uint32_t iteration, gid;
 };
 
+// The decision w > r w_max, identical to the FP64 comparison: positive
+// doubles order like their bit patterns, so the integer path compares the
+// weight's bits with those of RN(r w_max); zero, negative and NaN weights are
+// never accepted, and cut events (w = 0) never draw their uniform.
 MC_D bool uw_accept(const UwArgs& u, long long i) {
   const double wi = u.w[i];
-  // w > 0 first: cut events (w = 0) never draw their uniform
-  return wi > 0.0 && wi > acceptance_uniform(u.seed, u.iteration, u.gid, u.first + uint64_t(i)) * u.wmax;
+  const uint64_t wb = uint64_t(__double_as_longlong(wi));
+  if (wb == 0u || wb > 0x7FF0000000000000ull) return false;  // +0, negative (sign bit), NaN
+  const uint64_t odd = acceptance_odd(u.seed, u.iteration, u.gid, u.first + uint64_t(i));
+  if (u.e_w) return wb > product_bits(odd, u.m_w, u.e_w);
+  return wi > double(odd) * 0x1p-53 * u.wmax;
 }
 
 // Chunks are multiples of kUwBlock events, so the 32 events of a warp in one
@@ -240,7 +276,13 @@ cudaError_t unweight_launch(int proc, bool fp64, const KernelArgs& a, const doub
   int nchunks = int(min((long long)kUwMaxChunks, (n + 4 * kUwBlock - 1) / (4 * kUwBlock)));
   if (nchunks < 1) nchunks = 1;
   const long long chunk = ((n + nchunks - 1) / nchunks + kUwBlock - 1) / kUwBlock * kUwBlock;
-  UwArgs u = {w, n, chunk, wmax, a.seed, a.first, a.iteration, a.gid};
+  uint64_t wbits;
+  std::memcpy(&wbits, &wmax, sizeof(wbits));
+  const int e_b = int(wbits >> 52) & 0x7ff;
+  // integer path for normal w_max >= 2^-969 (products stay normal)
+  const int e_w = (wbits >> 63) == 0 && e_b >= 54 && e_b < 0x7ff ? e_b : 0;
+  UwArgs u = {w, n, chunk, wmax, (wbits & ((1ull << 52) - 1)) | (1ull << 52), e_w, a.seed, a.first, a.iteration,
+              a.gid};
   (void)cudaGetLastError();
   uw_count_kernel<<<nchunks, kUwBlock, 0, st>>>(u, counts, mask);
   uw_scan_kernel<<<1, 1024, 0, st>>>(counts, nchunks, total);

@@ -173,6 +173,25 @@ def test_capacity_count_only_and_argument_checks(gpu):
     v.free()
 
 
+def test_decision_at_the_threshold_is_exact(gpu):
+    """Weights set to RN(r_i w_max) exactly (w > r w_max is false: rejected)
+    and to the next double above it (accepted), r_i from the oracle, for
+    w_max on the device's integer path and for a w_max so small that the
+    products are subnormal (its FP64 path): the decision is the FP64
+    comparison, bit for bit."""
+    itg = PROCS["ee"]
+    n = 50000
+    v, w, r = gpu_weights(gpu, itg, M.MC_FP64, W.uniform_grid(2, 50), n)
+    racc = O.acceptance_uniforms(0, 0, 0, 0, n)
+    for wmax in (1234.5678, 3.0e-10, 1.0, 2.0 ** -1000):
+        thr = racc * wmax
+        crafted = np.where(np.arange(n) % 2 == 0, thr, np.nextafter(thr, np.inf))
+        w.copy_(torch.from_numpy(crafted))
+        nacc, ev = gpu_unweight(v, gpu, itg, w, n, wmax, n)
+        assert nacc == n // 2 and np.array_equal(ev["event"], np.arange(1, n, 2)), wmax
+    v.free()
+
+
 def test_full_size_gg_ttbarg_sampled(gpu, oracle_pdf):
     """At the benchmark launch (gg -> ttg, FP32+Kahan, 1e7 events, uniform
     grid): w_max fixed in advance from an oracle sample; sampled decisions and
