@@ -26,7 +26,7 @@ class EventRecord(ctypes.Structure):
                 ("shat", ctypes.c_double), ("lumi", ctypes.c_double), ("lumi_qq", ctypes.c_double),
                 ("me2", ctypes.c_double), ("me2_qq", ctypes.c_double), ("ps_weight", ctypes.c_double),
                 ("f", ctypes.c_double), ("weight", ctypes.c_double), ("pass_", ctypes.c_int32),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("channel", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class LabEvent(ctypes.Structure):
@@ -92,6 +92,18 @@ def lib():
                                           ctypes.c_int64, ctypes.c_int64, _d, _dp, ctypes.POINTER(LabEvent),
                                           ctypes.c_int64, _dp]
         L.orc_unweight_events.restype = ctypes.c_int64
+        L.orc_set_channel_alpha.argtypes = [_dp]
+        L.orc_channel_forward.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _dp, _dp, _dp]
+        L.orc_channel_forward.restype = ctypes.c_int
+        L.orc_channel_inverse.argtypes = [ctypes.c_int, _d, _d, _d, _d, _d, _dp, _dp, _dp]
+        L.orc_channel_inverse.restype = ctypes.c_int
+        L.orc_channels_event.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
+                                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
+                                         ctypes.POINTER(EventRecord), _dp]
+        L.orc_channels_iterate.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp,
+                                           ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_int64, ctypes.c_int64, _dp, _dp]
+        L.orc_channel_update.argtypes = [ctypes.c_int, _dp, _dp, _d, _d, _dp]
         for name, args in [("orc_me2_eemumu", [_d] * 6), ("orc_me2_eemumu_trace", [_d] * 4 + [_dp]),
                            ("orc_me2_qqbar_ttbar", [_d] * 4), ("orc_me2_qqbar_ttbar_trace", [_d, _d, _dp]),
                            ("orc_me2_gg_ttbar", [_d] * 4), ("orc_me2_gg_ttbar_colour_ordered", [_d, _d, _dp]),
@@ -293,6 +305,65 @@ def unweight_events(itg, pdf, edges, prec, seed, iteration, gid, first, n, wmax=
     if nacc < 0:
         raise ValueError("process has no event record")
     return w, wm.value, list(out[:min(nacc, cap)]), nacc
+
+
+# ----------------------------------------------------------------- channels
+def set_channel_alpha(alpha):
+    """Channel probabilities of the multi-channel process (normalised)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    lib().orc_set_channel_alpha(_ptr(a))
+
+
+def channel_forward(ch, m, rs, ptcut, etacut, yb, u):
+    """Channel ch's map of u[5] at partonic energy rs (cuts pT > ptcut,
+    |eta + yb| < etacut): (momenta [3][4] t, tbar, g, weight) or None."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    p = np.zeros((3, 4))
+    w = ctypes.c_double()
+    if lib().orc_channel_forward(ch, m, rs, ptcut, etacut, yb, _ptr(u), _ptr(p), ctypes.byref(w)):
+        return None
+    return p, w.value
+
+
+def channel_inverse(ch, m, rs, ptcut, etacut, yb, p):
+    """The channel-ch variables of the momenta p [3][4] and the channel's
+    weight there, or None outside its support."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    u = np.zeros(5)
+    w = ctypes.c_double()
+    if lib().orc_channel_inverse(ch, m, rs, ptcut, etacut, yb, _ptr(p), _ptr(u), ctypes.byref(w)):
+        return None
+    return u, w.value
+
+
+def channels_event(itg, pdf, edges, prec, seed, iteration, gid, ev):
+    """One multi-channel event: (EventRecord, densities of the three channels)."""
+    c = _integrand_c(itg)
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    rec = EventRecord()
+    dens = np.zeros(3)
+    lib().orc_channels_event(ctypes.byref(c), pdf.handle if pdf is not None else None, edges.shape[1] - 1,
+                             _ptr(edges), prec, seed, iteration, gid, ev, ctypes.byref(rec), _ptr(dens))
+    return rec, dens
+
+
+def channels_iterate(itg, pdf, edges, prec, seed, iteration, gid, first, n):
+    """(sum w, sum w^2, w_max) and the alpha-update sums W[3] of n events."""
+    c = _integrand_c(itg)
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    sums = np.zeros(3)
+    wch = np.zeros(3)
+    lib().orc_channels_iterate(ctypes.byref(c), pdf.handle if pdf is not None else None, edges.shape[1] - 1,
+                               _ptr(edges), prec, seed, iteration, gid, first, n, _ptr(sums), _ptr(wch))
+    return sums, wch
+
+
+def channel_update(alpha, w, beta=0.5, amin=0.0):
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros(len(a))
+    lib().orc_channel_update(len(a), _ptr(a), _ptr(ww), beta, amin, _ptr(out))
+    return out
 
 
 # ----------------------------------------------------------------- |M|^2

@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["philox.cpp", "vegas.cpp", "phasespace.cpp", "pdf.cpp", "pdfset.cpp", "unweight.cpp", "matrix_elements.cpp",
+SOURCES = ["philox.cpp", "vegas.cpp", "phasespace.cpp", "pdf.cpp", "pdfset.cpp", "unweight.cpp", "channels.cpp", "matrix_elements.cpp",
            "integrand.cpp"]
 LIB = os.path.join(HERE, "liboracle.so")
 

@@ -42,6 +42,7 @@ int process_ndim(const orc_integrand& in) {
     case GG_TTBARG: return 14;
     case GAUSS: return in.gauss_dim;
     case GG_TTBARG_7D: return 7;
+    case GG_TTBARG_MC: return 17;  // grid dimensions; 7 uniforms per event
   }
   return -1;
 }
@@ -165,6 +166,11 @@ static double integrand_value(const orc_integrand& in, const Pdf* pdf, const dou
 
 void eval_event(const orc_integrand& in, const Pdf* pdf, int nbins, const double* edges, int prec,
                 uint64_t seed, uint32_t iteration, uint32_t gid, int64_t ev, orc_event_record* rec) {
+  if (in.proc == GG_TTBARG_MC) {  // channel choice and densities need the event and the grid
+    double dens[3];
+    channels_event(in, pdf, nbins, edges, prec, seed, iteration, gid, ev, rec, dens);
+    return;
+  }
   std::memset(rec, 0, sizeof(*rec));
   const int ndim = process_ndim(in);
   uint64_t k[16];
@@ -240,9 +246,11 @@ void orc_iterate(const orc_integrand* in, const void* pdf_v, int nbins, const do
       p.sum2 += (long double)w * w;
       if (w != 0.0) ++p.nz;
       if (w > p.wmax) p.wmax = w;
-      for (int d = 0; d < ndim; ++d) {
-        p.h[size_t(d) * nbins + rec.bin[d]] += (long double)w * w;
-        p.c[size_t(d) * nbins + rec.bin[d]] += 1;
+      const bool mc = in->proc == orc::GG_TTBARG_MC;
+      for (int d = 0; d < (mc ? 7 : ndim); ++d) {
+        const int gd = mc ? orc::channel_grid_dim(d, rec.channel) : d;
+        p.h[size_t(gd) * nbins + rec.bin[d]] += (long double)w * w;
+        p.c[size_t(gd) * nbins + rec.bin[d]] += 1;
       }
     }
   };

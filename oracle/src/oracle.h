@@ -84,7 +84,7 @@ void ggttg_partial_amplitudes(double alpha_s, double mt, const P4* q_in, const c
                               int ngluon, const cplx* ubar, const cplx* v, cplx* amps);
 
 // ---------------------------------------------------------------- integrand
-enum Process { EE_MUMU = 0, PP_TTBAR = 1, GG_TTBARG = 2, GAUSS = 3, GG_TTBARG_7D = 4 };
+enum Process { EE_MUMU = 0, PP_TTBAR = 1, GG_TTBARG = 2, GAUSS = 3, GG_TTBARG_7D = 4, GG_TTBARG_MC = 5 };
 
 }  // namespace orc
 
@@ -111,6 +111,8 @@ typedef struct {
   double weight;     // f * jac
   int32_t pass;      // 1 = inside the cuts/threshold, 0 = zero weight
   int32_t status;
+  int32_t channel;   // multi-channel process: the channel that generated the event
+  int32_t pad_;
 } orc_event_record;
 
 typedef struct {
@@ -138,4 +140,12 @@ namespace orc {
 void eval_event(const orc_integrand& in, const Pdf* pdf, int nbins, const double* edges, int prec, uint64_t seed,
                 uint32_t iteration, uint32_t gid, int64_t ev, orc_event_record* rec);
 double acceptance_uniform(uint64_t seed, uint32_t iteration, uint32_t gid, int64_t ev);
+// Multi-channel g g -> t tbar g (channels.cpp): 7 uniforms per event, a
+// 17-dimension grid (x1, x2, then 5 dimensions per channel); used dimension
+// d of an event of channel ch lives in grid dimension channel_grid_dim(d, ch).
+// dens[3] receives the three channel densities at the event's point.
+inline int channel_grid_dim(int d, int ch) { return d < 2 ? d : 2 + 5 * ch + (d - 2); }
+void channels_event(const orc_integrand& in, const Pdf* pdf, int nbins, const double* edges, int prec, uint64_t seed,
+                    uint32_t iteration, uint32_t gid, int64_t ev, orc_event_record* rec, double* dens);
+double vegas_map_1d(const double* edges, int nbins, int bits, uint64_t k, int* bin, double* jac);
 }  // namespace orc

@@ -22,7 +22,7 @@ import numpy as np
 PIDS = (-5, -4, -3, -2, -1, 21, 1, 2, 3, 4, 5)
 GEV2_TO_PB = 0.3893794e9
 
-EE_MUMU, PP_TTBAR, GG_TTBARG, GAUSS, GG_TTBARG_7D = 0, 1, 2, 3, 4
+EE_MUMU, PP_TTBAR, GG_TTBARG, GAUSS, GG_TTBARG_7D, GG_TTBARG_MC = 0, 1, 2, 3, 4, 5
 FP64, FP32 = 0, 1
 
 
@@ -184,7 +184,7 @@ class Integrand:
     gev2pb: float = GEV2_TO_PB
 
     def ndim(self):
-        return {EE_MUMU: 2, PP_TTBAR: 4, GG_TTBARG: 14, GG_TTBARG_7D: 7}.get(self.proc, self.gauss_dim)
+        return {EE_MUMU: 2, PP_TTBAR: 4, GG_TTBARG: 14, GG_TTBARG_7D: 7, GG_TTBARG_MC: 17}.get(self.proc, self.gauss_dim)
 
     def asdict(self):
         return asdict(self)
@@ -208,6 +208,12 @@ def gg_ttbarg(sqrt_s=13000.0):
 def gg_ttbarg_7d(sqrt_s=13000.0):
     """gg -> t tbar g with the hierarchical three-body generator (2 + 5 = 7 dims), same cuts."""
     return Integrand(proc=GG_TTBARG_7D, sqrt_s=sqrt_s)
+
+
+def gg_ttbarg_mc(sqrt_s=13000.0):
+    """gg -> t tbar g with three-channel sampling (7 uniforms per event; a
+    17-dimension VEGAS grid: x1, x2 and 5 dimensions per channel), same cuts."""
+    return Integrand(proc=GG_TTBARG_MC, sqrt_s=sqrt_s)
 
 
 def gauss(dim, sigma=0.1):
