@@ -409,21 +409,25 @@ def time_to_target(M, pdf, stream, seed=0):
     """GPU time (CUDA events around every launch of the arm) from the first
     launch to the end of the first iteration whose combined relative error is
     at most TTT_TARGET, for plain FP64 VEGAS, FP32 VEGAS and FP32 + flow on
-    gg -> t tbar g (7 dims), each from scratch (uniform grid / identity flow)."""
+    gg -> t tbar g (7 dims), and FP32 three-channel sampling of the same
+    process, each from scratch (uniform grids / identity flow)."""
     import torch
     itg = W.gg_ttbarg_7d()
     out = {"target_rel_err": TTT_TARGET, "events_per_iteration": TTT_EVENTS, "workload":
            "gg->ttg 13 TeV, hierarchical 2->3 phase space (7 dims), same cuts and PDF grid"}
 
-    def vegas(prec, name):
-        v = M.mc_vegas_init(7, NBINS, seed, prec)
+    def vegas(prec, name, integrand=itg):
+        v = M.mc_vegas_init(integrand.ndim(), NBINS, seed, prec)
         res, per_event, eff = [], None, None
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for it in range(TTT_MAX_ITER):
-            r = M.mc_vegas_iterate(v, itg, pdf, TTT_EVENTS, stream)
+            r = M.mc_vegas_iterate(v, integrand, pdf, TTT_EVENTS, stream)
+            if integrand.proc == W.GG_TTBARG_MC:  # Kleiss-Pittau step of the channel probabilities
+                a, w = M.mc_vegas_get_channels(v)
+                M.mc_vegas_set_channels(v, M.mc_channel_update(a, w, 0.5, 0.02))
             M.mc_vegas_refine(v, ALPHA, stream)
             res.append(_iter_stats(r))
             mean, sig = _combine(res)
@@ -434,12 +438,20 @@ def time_to_target(M, pdf, stream, seed=0):
         m_it, v_it = res[-1]
         per_event = v_it * r.n / (m_it * m_it)
         eff = m_it / r.wmax if r.wmax > 0 else None
+        arm = {"ms": t0.elapsed_time(t1), "iterations": len(res), "mean_pb": mean, "rel_err": sig / abs(mean),
+               "rel_var_per_event_last": per_event, "unweighting_eff_last": eff}
+        if integrand.proc == W.GG_TTBARG_MC:
+            arm["alpha_final"] = [round(x, 4) for x in M.mc_vegas_get_channels(v)[0]]
         v.free()
-        return {"ms": t0.elapsed_time(t1), "iterations": len(res), "mean_pb": mean, "rel_err": sig / abs(mean),
-                "rel_var_per_event_last": per_event, "unweighting_eff_last": eff}
+        return arm
 
     out["vegas_fp64"] = vegas(M.MC_FP64, "fp64")
     out["vegas_fp32"] = vegas(M.MC_FP32_KAHAN, "fp32")
+    # three-channel sampling (thesis Sec. "Multi-channel Monte Carlo"), FP32,
+    # per-channel grids, channel probabilities updated after every iteration
+    out["multichannel_fp32"] = vegas(M.MC_FP32_KAHAN, "mc", W.gg_ttbarg_mc())
+    out["multichannel_fp32"]["workload"] = ("gg->ttg, three channels (initial-state radiation, radiation off t, "
+                                            "off tbar), 7 uniforms per event, 17-dimension grid")
     # flow arm: training included in the timed region
     init = W.flow_init_params(7, L=FLOW_LAYERS, K=FLOW_BINS, seed=seed)
     f = M.mc_flow_create(7, FLOW_LAYERS, FLOW_BINS, init, FLOW_BATCH, seed=seed + 1)

@@ -58,8 +58,10 @@ extern "C" {
 #define MC_GG_TTBARG 2  /* g g -> t tbar g, RAMBO, 14 dims (7 physical)          */
 #define MC_GAUSS 3      /* normalised Gaussian centred at 1/2, gauss_dim dims     */
 #define MC_GG_TTBARG_7D 4 /* g g -> t tbar g, hierarchical 2->3 generator, 7 dims */
+#define MC_GG_TTBARG_MC 5 /* g g -> t tbar g, three-channel sampling: 7 uniforms  */
+                          /* per event, 17 grid dimensions (see below)           */
 
-#define MC_MAX_DIM 16
+#define MC_MAX_DIM 17   /* grid dimensions: 16, or 17 for MC_GG_TTBARG_MC */
 #define MC_MAX_BINS 256
 
 typedef struct mc_pdf_s* mc_pdf;
@@ -232,6 +234,34 @@ int mc_integrate(const mc_integrand* itg, mc_pdf pdf, int niter, int64_t nevents
                  uint64_t seed, uint32_t gid, int prec, double alpha, double target_rel_err,
                  void* stream, mc_result* out, mc_iter_result* per_iter);
 
+/* -------------------------------------------- multi-channel sampling
+ * Thesis Sec. "Multi-channel Monte Carlo": points are drawn from channel i
+ * with probability alpha_i and weighted by f / p, p = sum_i alpha_i p_i; the
+ * alpha_i leave the estimate unchanged and are adjusted to reduce its
+ * variance (Kleiss & Pittau, cited there).  MC_GG_TTBARG_MC has three
+ * channels, each a sequential splitting whose variables flatten one peak of
+ * |M|^2: 0, initial-state radiation (gluon first: ln pT flat from the pT cut,
+ * rapidity flat inside the lab-frame eta cut); 1 and 2, radiation off the
+ * top and off the anti-top (t g or tbar g pair first, ln(s_pair - m^2 +
+ * m pTcut) flat).  Every channel has its own VEGAS grid over its 5 variables
+ * and all share the (x1, x2) grid: a 17-dimension grid (dims 0-1 x1, x2;
+ * 2-6 channel 0; 7-11 channel 1; 12-16 channel 2), of which an event uses
+ * and fills the 7 of its channel.  The channel of an event is Philox call
+ * 254: u = (k + 0.5) 2^-24, k the top 24 bits of word 0, channel i the first
+ * with u < alpha_0 + ... + alpha_i.  Needs ptcut_g > 0.
+ *
+ * mc_vegas_set_channels: alpha[3] (host, non-negative, positive sum;
+ * normalised), default 1/3 each.  mc_vegas_get_channels: the current
+ * alpha[3] and (w, may be NULL) the last iteration's update sums
+ * W_i = (1/N) sum_events w^2 p_i / p.  mc_channel_update: one update
+ * alpha_i <- alpha_i W_i^beta / sum_j alpha_j W_j^beta, then a floor amin
+ * and renormalisation (host arithmetic, n <= 16).  mc_integrate applies it
+ * (beta = 1/2, amin = 0.02) after every iteration of MC_GG_TTBARG_MC.
+ */
+int mc_vegas_set_channels(mc_vegas v, const double* alpha);
+int mc_vegas_get_channels(mc_vegas v, double* alpha, double* w);
+int mc_channel_update(int n, const double* alpha, const double* w, double beta, double amin, double* alpha_out);
+
 /* ------------------------------------------------- unweighted events
  * Thesis Sec. "Unweighted event exporter" (acceptance-rejection as in
  * Sec. "Monte Carlo integration"): from a weighted sample with largest
@@ -353,6 +383,8 @@ int mc_generate_lhe(const mc_integrand* itg, mc_pdf pdf, int ntrain, int niter, 
 #define MC_REC_W 86       /* event weight f * J                                  */
 #define MC_REC_PASS 87    /* 1 inside cuts and thresholds, else 0                */
 #define MC_REC_STATUS 88  /* 0, or MC_ENAN / MC_ENOCONV                          */
+#define MC_REC_CHANNEL 89 /* three-channel process: the event's channel          */
+#define MC_REC_DENS 90    /* 3: the channels' densities at the event's point     */
 #define MC_REC_STRIDE 96
 int mc_debug_events(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t first, int64_t k,
                     double* out, void* stream);

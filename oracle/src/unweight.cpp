@@ -63,7 +63,8 @@ int64_t orc_unweight_events(const orc_integrand* in, const void* pdf, int nbins,
   switch (in->proc) {
     case orc::EE_MUMU: nout = 2; break;
     case orc::GG_TTBARG:
-    case orc::GG_TTBARG_7D: nout = 3; break;
+    case orc::GG_TTBARG_7D:
+    case orc::GG_TTBARG_MC: nout = 3; break;
     default: return -1;
   }
   const orc::Pdf* P = static_cast<const orc::Pdf*>(pdf);

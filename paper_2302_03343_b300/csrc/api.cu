@@ -48,6 +48,7 @@ int process_ndim(const mc_integrand* itg) {
     case MC_GG_TTBARG: return 14;
     case MC_GAUSS: return itg->gauss_dim;
     case MC_GG_TTBARG_7D: return 7;
+    case MC_GG_TTBARG_MC: return mc::kChannelGridDims;
   }
   return -1;
 }
@@ -169,6 +170,7 @@ int mc_vegas_free(mc_vegas v) {
   if (v->k0) cudaEventDestroy(v->k0);
   if (v->k1) cudaEventDestroy(v->k1);
   if (v->d_uw) cudaFree(v->d_uw);
+  if (v->d_wch) cudaFree(v->d_wch);
   if (v->h_count) cudaFreeHost(v->h_count);
   if (v->u0) cudaEventDestroy(v->u0);
   if (v->u1) cudaEventDestroy(v->u1);
@@ -270,6 +272,39 @@ int mc_vegas_get_iteration(mc_vegas v, uint32_t* it) {
   *it = v->iteration;
   return MC_OK;
 }
+int mc_vegas_set_channels(mc_vegas v, const double* alpha) {
+  if (!v || !alpha) return fail(MC_EINVAL, "mc_vegas_set_channels: NULL argument");
+  const double t = alpha[0] + alpha[1] + alpha[2];
+  if (!(alpha[0] >= 0.0 && alpha[1] >= 0.0 && alpha[2] >= 0.0) || !(t > 0.0) || !std::isfinite(t))
+    return fail(MC_EINVAL, "mc_vegas_set_channels: alpha must be non-negative with a positive sum");
+  for (int i = 0; i < 3; ++i) v->alpha[i] = alpha[i] / t;
+  return MC_OK;
+}
+
+int mc_vegas_get_channels(mc_vegas v, double* alpha, double* w) {
+  if (!v) return fail(MC_EINVAL, "mc_vegas_get_channels: NULL handle");
+  for (int i = 0; i < 3; ++i) {
+    if (alpha) alpha[i] = v->alpha[i];
+    if (w) w[i] = v->wch[i];
+  }
+  return MC_OK;
+}
+
+int mc_channel_update(int n, const double* alpha, const double* w, double beta, double amin, double* out) {
+  if (n < 1 || n > 16 || !alpha || !w || !out || !(beta >= 0.0) || !(amin >= 0.0) || !(amin * n < 1.0))
+    return fail(MC_EINVAL, "mc_channel_update: bad arguments");
+  double t = 0.0;
+  for (int i = 0; i < n; ++i) t += (out[i] = alpha[i] * std::pow(w[i], beta));
+  if (!(t > 0.0) || !std::isfinite(t)) {
+    for (int i = 0; i < n; ++i) out[i] = alpha[i];
+    return MC_OK;
+  }
+  double t2 = 0.0;
+  for (int i = 0; i < n; ++i) t2 += (out[i] = std::fmax(out[i] / t, amin));
+  for (int i = 0; i < n; ++i) out[i] /= t2;
+  return MC_OK;
+}
+
 int mc_vegas_set_gid(mc_vegas v, uint32_t gid) {
   if (!v || gid > 255) return fail(MC_EINVAL, "mc_vegas_set_gid: bad argument");
   v->gid = gid;
@@ -285,8 +320,11 @@ int mc::fill_process_args(const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
   if (!itg) return fail(MC_EINVAL, "NULL integrand");
   int dev;
   if (int rc = current_device(&dev)) return rc;
-  if (itg->proc < MC_EE_MUMU || itg->proc > MC_GG_TTBARG_7D) return fail(MC_EINVAL, "unknown process %d", itg->proc);
-  const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG || itg->proc == MC_GG_TTBARG_7D;
+  if (itg->proc < MC_EE_MUMU || itg->proc > MC_GG_TTBARG_MC) return fail(MC_EINVAL, "unknown process %d", itg->proc);
+  const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG || itg->proc == MC_GG_TTBARG_7D ||
+                        itg->proc == MC_GG_TTBARG_MC;
+  if (itg->proc == MC_GG_TTBARG_MC && !(itg->ptcut_g > 0.0))
+    return fail(MC_EINVAL, "the three-channel process needs ptcut_g > 0");
   if (!(itg->sqrt_s > 0.0) && itg->proc != MC_GAUSS) return fail(MC_EINVAL, "sqrt_s must be positive");
   if (itg->proc == MC_GAUSS && !(itg->gauss_sigma > 0.0)) return fail(MC_EINVAL, "gauss_sigma must be positive");
   std::memset(a, 0, sizeof(*a));
@@ -340,6 +378,17 @@ static int prepare(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, KernelArgs* 
   a->hist_w2 = v->d_hist_w2;
   a->hist_n = v->d_hist_n;
   a->partials = v->d_partials;
+  // channel probabilities (three-channel process): cumulative sums in the
+  // order the channel choice compares them
+  for (int i = 0; i < 3; ++i) a->alpha[i] = v->alpha[i];
+  a->alpha_cum[0] = v->alpha[0];
+  a->alpha_cum[1] = v->alpha[0] + v->alpha[1];
+  a->alpha_cum[2] = a->alpha_cum[1] + v->alpha[2];
+  if (itg->proc == MC_GG_TTBARG_MC) {
+    if (!v->d_wch && cudaMalloc(&v->d_wch, 3 * sizeof(double)) != cudaSuccess)
+      return fail(MC_ENOMEM, "channel sums");
+    a->wch = v->d_wch;
+  }
   return MC_OK;
 }
 
@@ -385,6 +434,7 @@ static int iterate_impl(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t
     int* d_status = reinterpret_cast<int*>(v->d_total + 1);
     a.status = d_status;
     MC_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
+    if (a.wch) MC_CUDA(cudaMemsetAsync(a.wch, 0, 3 * sizeof(double), st));
     MC_CUDA(cudaEventRecord(v->k0, st));
     MC_CUDA(mc::launch_integrand(itg->proc, fp64, a, grid, smem, st));
     MC_CUDA(cudaEventRecord(v->k1, st));
@@ -401,6 +451,10 @@ static int iterate_impl(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t
     out->n_nonzero = t.n_nonzero;
     out->n_bad = t.n_bad + t.n_noconv;
     out->status = t.n_bad ? MC_ENAN : (t.n_noconv ? MC_ENOCONV : MC_OK);
+    if (a.wch) {
+      MC_CUDA(cudaMemcpy(v->wch, a.wch, 3 * sizeof(double), cudaMemcpyDeviceToHost));
+      for (int j = 0; j < 3; ++j) v->wch[j] /= double(nevents);
+    }
   }
   v->last_iteration = v->iteration;
   v->last_n = nevents;
@@ -427,7 +481,8 @@ int mc_unweight(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, const double* w
   if (!n_accepted) return fail(MC_EINVAL, "mc_unweight: n_accepted is NULL");
   *n_accepted = 0;
   if (!v || !itg) return fail(MC_EINVAL, "mc_unweight: NULL handle or integrand");
-  if (itg->proc != MC_EE_MUMU && itg->proc != MC_GG_TTBARG && itg->proc != MC_GG_TTBARG_7D)
+  if (itg->proc != MC_EE_MUMU && itg->proc != MC_GG_TTBARG && itg->proc != MC_GG_TTBARG_7D &&
+      itg->proc != MC_GG_TTBARG_MC)
     return fail(MC_EINVAL, "mc_unweight: process %d has no event record", itg->proc);
   if (!v->last_valid) return fail(MC_EINVAL, "mc_unweight: no iteration on the current grid");
   if (nevents != v->last_n) return fail(MC_EINVAL, "mc_unweight: nevents differs from the last iteration's");
@@ -575,6 +630,12 @@ int mc_integrate(const mc_integrand* itg, mc_pdf pdf, int niter, int64_t nevents
     cudaEventRecord(e0, st);
     rc = mc_vegas_iterate(v, itg, pdf, nevents, stream, &r);
     if (rc) break;
+    if (itg->proc == MC_GG_TTBARG_MC) {  // Kleiss-Pittau step of the channel probabilities
+      double al[3], w[3], next[3];
+      mc_vegas_get_channels(v, al, w);
+      mc_channel_update(3, al, w, 0.5, 0.02, next);
+      mc_vegas_set_channels(v, next);
+    }
     rc = mc_vegas_refine(v, alpha, stream);
     if (rc) break;
     cudaEventRecord(e1, st);

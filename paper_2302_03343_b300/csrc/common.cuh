@@ -23,6 +23,16 @@ MC_D float m_abs(float x) { return fabsf(x); }
 MC_D double m_abs(double x) { return fabs(x); }
 MC_D float m_max(float a, float b) { return fmaxf(a, b); }
 MC_D double m_max(double a, double b) { return fmax(a, b); }
+MC_D float m_cosh(float x) { return coshf(x); }
+MC_D double m_cosh(double x) { return cosh(x); }
+MC_D float m_sinh(float x) { return sinhf(x); }
+MC_D double m_sinh(double x) { return sinh(x); }
+MC_D float m_acosh(float x) { return acoshf(x); }
+MC_D double m_acosh(double x) { return acosh(x); }
+MC_D float m_atan2(float y, float x) { return atan2f(y, x); }
+MC_D double m_atan2(double y, double x) { return atan2(y, x); }
+MC_D float m_min(float a, float b) { return fminf(a, b); }
+MC_D double m_min(double a, double b) { return fmin(a, b); }
 // sin and cos of 2 pi u for u in (0, 1)
 MC_D void m_sincos2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
 MC_D void m_sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }

@@ -13,6 +13,7 @@ namespace mc {
 struct Acc {
   double s_hi = 0.0, s_c = 0.0, q_hi = 0.0, q_c = 0.0, wmax = 0.0;
   unsigned int nnz = 0, nbad = 0, nnoconv = 0;  // per thread: below 2^32 events
+  double wch[kChannels] = {0.0, 0.0, 0.0};      // three-channel process: sums of w^2 p_i / p
 };
 
 // value = hi + lo pairs: compensated addition of two such pairs
@@ -33,13 +34,152 @@ MC_HD void partial_add(BlockPartial& b, const BlockPartial& o) {
   b.n_noconv += o.n_noconv;
 }
 
+// Kahan sums, count and maximum of one event's weight.
+MC_D void acc_add(Acc& acc, double w) {
+  const double y = w - acc.s_c;
+  const double t = acc.s_hi + y;
+  acc.s_c = (t - acc.s_hi) - y;
+  acc.s_hi = t;
+  const double w2 = w * w;
+  const double y2 = w2 - acc.q_c;
+  const double t2 = acc.q_hi + y2;
+  acc.q_c = (t2 - acc.q_hi) - y2;
+  acc.q_hi = t2;
+  if (w != 0.0) ++acc.nnz;
+  acc.wmax = fmax(acc.wmax, w);
+}
+
+// One event of the three-channel gg -> t tbar g process (thesis Sec.
+// "Multi-channel Monte Carlo"): the channel from Philox call 254, the 7
+// uniforms through the (x1, x2) grid and that channel's grid, the channel's
+// map, the densities of all three channels at the point (the others by their
+// inverse maps and grid densities), w = f J_x / sum_j alpha_j p_j, the
+// alpha-update sums and the histograms of the grid dimensions used.
+template <bool FP64, bool RECORD, class R, class H>
+MC_D double process_event_mc(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, H* sh_w2,
+                             unsigned int* sh_n, uint64_t ev, double* rec, Acc& acc) {
+  constexpr int ND = 7;
+  const int nb = a.nbins;
+  const uint4 cw = philox4x32_10(make_uint4(uint32_t(ev), uint32_t(ev >> 32), a.iteration,
+                                            (a.gid & 0xffu) | (254u << 8)),
+                                 make_uint2(uint32_t(a.seed), uint32_t(a.seed >> 32)));
+  const double uc = (double(cw.x >> 8) + 0.5) * 0x1p-24;
+  const int ch = uc < a.alpha_cum[0] ? 0 : (uc < a.alpha_cum[1] ? 1 : 2);
+  uint64_t k[ND];
+  event_uniforms<ND, FP64>(a.seed, a.iteration, a.gid, ev, ND, k);
+  R x[ND];
+  int bin[ND];
+  R jx = R(1), jrest = R(1);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    R jd;
+    x[d] = vegas_map_1d<R, FP64>(sh_edges + ch_grid_dim(d, ch) * (nb + 1), nb, k[d], &bin[d], &jd);
+    if (d < 2) jx *= jd; else jrest *= jd;
+  }
+  const Params& p = a.prm;
+  const R m = R(p.m_top);
+  const R x1 = x[0], x2 = x[1];
+  const R shat = sizeof(R) == 4 ? R(x1 * x2 * R(p.sqrt_s * p.sqrt_s)) : R(double(x1) * double(x2) * p.sqrt_s * p.sqrt_s);
+  double w = 0.0, dens[kChannels] = {0.0, 0.0, 0.0}, pden = 0.0;
+  int pass = 0;
+  v4<R> t = {}, tb = {}, g = {};
+  GgKin<R> kin;
+  R me2 = R(0);
+  if (shat > R(4) * m * m) {
+    const R rs = m_sqrt(shat);
+    const ChCtx<R> c = ch_ctx<R>(m, rs, R(p.ptcut_g), R(p.etacut_g), R(0.5) * m_log(x1 / x2));
+    R wi;
+    if (ch_forward<R>(ch, c, x + 2, &t, &tb, &g, &wi) && wi > R(0)) {
+      dens[ch] = 1.0 / (double(jrest) * double(wi));
+#pragma unroll
+      for (int j = 0; j < kChannels; ++j) {
+        if (j == ch) continue;
+        R uj[5], wj;
+        if (ch_inverse<R>(j, c, t, tb, g, uj, &wj) && wj > R(0)) {
+          R rho = R(1);
+#pragma unroll
+          for (int d = 0; d < 5; ++d) rho *= grid_density<R>(sh_edges + ch_grid_dim(d + 2, j) * (nb + 1), nb, uj[d]);
+          dens[j] = double(rho) / double(wj);
+        }
+      }
+      pden = a.alpha[0] * dens[0] + a.alpha[1] * dens[1] + a.alpha[2] * dens[2];
+      // the gluon cuts in the lab frame (pT, and |eta_cm + y_b| < cut without logarithms)
+      const R pt2 = g.x * g.x + g.y * g.y, ptc = R(p.ptcut_g);
+      const R pabs = m_sqrt(pt2 + g.z * g.z);
+      const R fwd = (pabs + g.z) * x1, bwd = (pabs - g.z) * x2, e2 = R(a.e2eta);
+      if (pt2 > ptc * ptc && fwd < e2 * bwd && bwd < e2 * fwd) {
+        pass = 1;
+        kin.k[0] = t;
+        kin.k[1] = tb;
+        kin.k[2] = g;
+        kin.shat = shat;
+        kin.rs = rs;
+        kin.lgg = xf_over_x(pdf.tab[0], x1) * xf_over_x(pdf.tab[0], x2);
+        kin.flux = sizeof(R) == 4 ? R(p.gev2pb) / (R(2) * shat) : R(0);
+        kin.psw = 1.0 / pden;
+        me2 = gg_me2<R>(a, kin);
+        w = gg_weight<R>(a, kin, me2) * double(jx);
+      }
+    }
+  }
+  int status = 0;
+  if (!isfinite(w)) {
+    status = MC_ENAN;
+    w = 0.0;
+  }
+  if (RECORD) {
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      rec[MC_REC_K + d] = double(k[d]);
+      rec[MC_REC_X + d] = double(x[d]);
+      rec[MC_REC_BIN + d] = double(bin[d]);
+    }
+    const R h = m_sqrt(m_max(shat, R(0))) * R(0.5);
+    rec_p4(rec, 0, v4<R>{h, R(0), R(0), h});
+    rec_p4(rec, 1, v4<R>{h, R(0), R(0), -h});
+    rec_p4(rec, 2, t);
+    rec_p4(rec, 3, tb);
+    rec_p4(rec, 4, g);
+    rec[MC_REC_X1] = double(x1);
+    rec[MC_REC_X2] = double(x2);
+    rec[MC_REC_SHAT] = double(shat);
+    rec[MC_REC_LUMI] = pass ? double(kin.lgg) : 0.0;
+    rec[MC_REC_ME2] = double(me2);
+    rec[MC_REC_PSW] = pden > 0.0 ? 1.0 / pden : 0.0;
+    rec[MC_REC_JAC] = double(jx) * double(jrest);
+    rec[MC_REC_F] = w / double(jx);
+    rec[MC_REC_W] = w;
+    rec[MC_REC_PASS] = double(pass);
+    rec[MC_REC_STATUS] = double(status);
+    rec[MC_REC_CHANNEL] = double(ch);
+#pragma unroll
+    for (int j = 0; j < kChannels; ++j) rec[MC_REC_DENS + j] = dens[j];
+    return w;
+  }
+  if (status != 0) ++acc.nbad;
+  acc_add(acc, w);
+  if (w != 0.0) {
+    const double w2p = w * w / pden;
+#pragma unroll
+    for (int j = 0; j < kChannels; ++j) acc.wch[j] += w2p * dens[j];
+  }
+  const H w2h = H(w * w);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const int gd = ch_grid_dim(d, ch);
+    atomicAdd(&sh_w2[gd * nb + bin[d]], w2h);
+    atomicAdd(&sh_n[gd * nb + bin[d]], 1u);
+  }
+  return w;
+}
+
 // Uniforms -> VEGAS map (grid in shared memory) -> integrand -> weight, then
 // the Kahan sums and the shared-memory histograms (or, with RECORD, the
 // per-event record `rec`).  H is the histogram accumulation type.  Returns
 // the event's weight (0 when it is cut or its weight is not finite).
 template <int PROC, bool FP64, bool RECORD, class R, class H>
-MC_D double process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, H* sh_w2, unsigned int* sh_n,
-                          uint64_t ev, double* rec, Acc& acc) {
+MC_D double process_event_one(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, H* sh_w2,
+                              unsigned int* sh_n, uint64_t ev, double* rec, Acc& acc) {
   constexpr int MAXD = ProcTraits<PROC>::MAXD;
   const int ndim = a.ndim, nb = a.nbins;
   uint64_t k[MAXD];
@@ -109,6 +249,26 @@ MC_D double process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_
     }
   }
   return w;
+}
+
+template <int PROC, bool FP64, bool RECORD, class R, class H>
+MC_D double process_event(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, H* sh_w2, unsigned int* sh_n,
+                          uint64_t ev, double* rec, Acc& acc) {
+  if constexpr (PROC == P_GG_TTBARG_MC)
+    return process_event_mc<FP64, RECORD, R, H>(a, pdf, sh_edges, sh_w2, sh_n, ev, rec, acc);
+  else
+    return process_event_one<PROC, FP64, RECORD, R, H>(a, pdf, sh_edges, sh_w2, sh_n, ev, rec, acc);
+}
+
+// Adds the block's alpha-update sums (three-channel process) to out[3]:
+// warp shuffles, then one FP64 atomic per warp and channel.
+MC_D void channel_sums_add(const Acc& acc, double* out) {
+#pragma unroll
+  for (int j = 0; j < kChannels; ++j) {
+    double v = acc.wch[j];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&out[j], v);
+  }
 }
 
 // Block reduction of the accumulators (warp shuffles, then thread 0 over the

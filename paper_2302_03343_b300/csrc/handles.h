@@ -59,5 +59,9 @@ struct mc_vegas_s {
   unsigned long long* h_count = nullptr;
   cudaEvent_t u0 = nullptr, u1 = nullptr;
   bool uw_timed = false;
+  // three-channel process: probabilities and the last iteration's update sums
+  double alpha[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0};
+  double wch[3] = {0.0, 0.0, 0.0};
+  double* d_wch = nullptr;
 };
 

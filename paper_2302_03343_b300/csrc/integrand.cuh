@@ -7,11 +7,12 @@
 #include "matrix_elements.cuh"
 #include "pdf.cuh"
 #include "phasespace.cuh"
+#include "channels.cuh"
 #include "sampling.cuh"
 
 namespace mc {
 
-enum : int { P_EE_MUMU = 0, P_PP_TTBAR = 1, P_GG_TTBARG = 2, P_GAUSS = 3, P_GG_TTBARG_7D = 4 };
+enum : int { P_EE_MUMU = 0, P_PP_TTBAR = 1, P_GG_TTBARG = 2, P_GAUSS = 3, P_GG_TTBARG_7D = 4, P_GG_TTBARG_MC = 5 };
 
 template <int PROC> struct ProcTraits;
 template <> struct ProcTraits<P_EE_MUMU> { static constexpr int MAXD = 2, NFL = 0; };
@@ -19,6 +20,8 @@ template <> struct ProcTraits<P_PP_TTBAR> { static constexpr int MAXD = 4, NFL =
 template <> struct ProcTraits<P_GG_TTBARG> { static constexpr int MAXD = 14, NFL = 1; };
 template <> struct ProcTraits<P_GAUSS> { static constexpr int MAXD = 16, NFL = 0; };
 template <> struct ProcTraits<P_GG_TTBARG_7D> { static constexpr int MAXD = 7, NFL = 1; };
+// three-channel gg -> t tbar g: 7 uniforms per event, 17 grid dimensions
+template <> struct ProcTraits<P_GG_TTBARG_MC> { static constexpr int MAXD = 7, NFL = 1; };
 
 // Arguments of one launch of the fused kernel (passed by value).
 struct BlockPartial {
@@ -46,6 +49,11 @@ struct KernelArgs {
   double* record;          // [n][MC_REC_STRIDE] (debug launches only)
   int* status;             // optional: MC_ETIMEOUT when a bounded wait of the launch gave up
   double* wout;            // optional, [n]: weight of every event (0 outside the cuts), weights pass
+  // three-channel process: cumulative channel probabilities (the channel of
+  // an event is the first i with u < alpha_cum[i], u from Philox call 254),
+  // the probabilities, and the alpha-update sums W_i (device, [3], added to)
+  double alpha_cum[3], alpha[3];
+  double* wch;
 };
 
 // Shared-memory PDF tables of a launch.

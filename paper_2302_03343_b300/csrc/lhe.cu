@@ -278,7 +278,8 @@ int mc_lhe_open(const char* path, const mc_integrand* itg, int threads, mc_lhe* 
   if (!out) return lfail(MC_EINVAL, "mc_lhe_open: out is NULL");
   *out = nullptr;
   if (!path || !itg || threads < 1 || threads > 64) return lfail(MC_EINVAL, "mc_lhe_open: bad arguments");
-  if (itg->proc != MC_EE_MUMU && itg->proc != MC_GG_TTBARG && itg->proc != MC_GG_TTBARG_7D)
+  if (itg->proc != MC_EE_MUMU && itg->proc != MC_GG_TTBARG && itg->proc != MC_GG_TTBARG_7D &&
+      itg->proc != MC_GG_TTBARG_MC)
     return lfail(MC_EINVAL, "mc_lhe_open: process %d has no event record", itg->proc);
   FILE* f = fopen(path, "wb");
   if (!f) return lfail(MC_EIO, "mc_lhe_open: cannot create %s", path);
@@ -301,7 +302,8 @@ int mc_lhe_open(const char* path, const mc_integrand* itg, int threads, mc_lhe* 
     fprintf(f,
             " process: g g > t t~ g (%s), sqrt(s) = %.6g GeV, m_top = %.6g, alpha_s = %.6g, mu_F = %.6g,\n"
             " gluon pT > %.6g GeV, |eta| < %.6g\n",
-            itg->proc == MC_GG_TTBARG ? "RAMBO" : "hierarchical 2 -> 3", itg->sqrt_s, itg->m_top, itg->alpha_s,
+            itg->proc == MC_GG_TTBARG ? "RAMBO" : (itg->proc == MC_GG_TTBARG_7D ? "hierarchical 2 -> 3" : "three channels"),
+            itg->sqrt_s, itg->m_top, itg->alpha_s,
             itg->mu_f, itg->ptcut_g, itg->etacut_g);
   fprintf(f, " unweighted events: w_i > r_i w_max (acceptance-rejection), unit weights\n-->\n</header>\n<init>\n");
   fprintf(f, " %d %d %+.10e %+.10e 0 0 0 0 3 1\n", ee ? 11 : 2212, ee ? -11 : 2212, eb, eb);
@@ -432,7 +434,8 @@ int mc_generate_lhe(const mc_integrand* itg, mc_pdf pdf, int ntrain, int niter, 
   std::memset(out, 0, sizeof(*out));
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (ntrain < 0 || niter < 1 || nevents < 2) return lfail(MC_EINVAL, "mc_generate_lhe: bad iteration counts");
-  if (itg->proc != MC_EE_MUMU && itg->proc != MC_GG_TTBARG && itg->proc != MC_GG_TTBARG_7D)
+  if (itg->proc != MC_EE_MUMU && itg->proc != MC_GG_TTBARG && itg->proc != MC_GG_TTBARG_7D &&
+      itg->proc != MC_GG_TTBARG_MC)
     return lfail(MC_EINVAL, "mc_generate_lhe: process %d has no event record", itg->proc);
   const int nd = mc::process_dim(itg);
   mc_vegas v = nullptr;

@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(kBlock) uw_export_kernel(KernelArgs a, const u
     const double x1 = rec[MC_REC_X1], x2 = rec[MC_REC_X2], half = 0.5 * a.prm.sqrt_s;
     e.x1 = x1;
     e.x2 = x2;
-    e.proc = PROC == P_EE_MUMU ? MC_EE_MUMU : (PROC == P_GG_TTBARG ? MC_GG_TTBARG : MC_GG_TTBARG_7D);
+    e.proc = PROC == P_EE_MUMU ? MC_EE_MUMU
+                               : (PROC == P_GG_TTBARG ? MC_GG_TTBARG : (PROC == P_GG_TTBARG_7D ? MC_GG_TTBARG_7D : MC_GG_TTBARG_MC));
     e.nout = NOUT;
     // incoming partons along the beams; outgoing momenta boosted along z from
     // the partonic frame: gamma = (x1 + x2) / (2 sqrt(x1 x2)),
@@ -301,6 +302,9 @@ cudaError_t unweight_launch(int proc, bool fp64, const KernelArgs& a, const doub
     case P_GG_TTBARG_7D:
       return fp64 ? launch_export<P_GG_TTBARG_7D, true>(a, idx, total, cap, w, out, grid, st)
                   : launch_export<P_GG_TTBARG_7D, false>(a, idx, total, cap, w, out, grid, st);
+    case P_GG_TTBARG_MC:
+      return fp64 ? launch_export<P_GG_TTBARG_MC, true>(a, idx, total, cap, w, out, grid, st)
+                  : launch_export<P_GG_TTBARG_MC, false>(a, idx, total, cap, w, out, grid, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -17,10 +17,10 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmcint.so
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ENAN, MC_ENOCONV, MC_ETIMEOUT, MC_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 MC_FP64, MC_FP32_KAHAN = 0, 1
-MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS, MC_GG_TTBARG_7D = 0, 1, 2, 3, 4
-MC_MAX_DIM, MC_MAX_BINS = 16, 256
+MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS, MC_GG_TTBARG_7D, MC_GG_TTBARG_MC = 0, 1, 2, 3, 4, 5
+MC_MAX_DIM, MC_MAX_BINS = 17, 256
 REC = dict(K=0, X=16, BIN=32, JAC=48, P=49, X1=77, X2=78, SHAT=79, LUMI=80, LUMI_QQ=81, ME2=82, ME2_QQ=83,
-           PSW=84, F=85, W=86, PASS=87, STATUS=88)
+           PSW=84, F=85, W=86, PASS=87, STATUS=88, CHANNEL=89, DENS=90)
 REC_STRIDE = 96
 
 # exported symbols (each declared in include/mcint.h)
@@ -34,7 +34,8 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_flow_train", "mc_flow_iterate", "mc_flow_set_fused", "mc_integrate_flow", "mc_pdfset_load",
            "mc_pdfset_free", "mc_pdfset_xfxq2", "mc_alphas_load", "mc_alphas_free", "mc_alphas_q2",
            "mc_vegas_iterate_weights", "mc_unweight", "mc_unweight_ms", "mc_lhe_open", "mc_lhe_write",
-           "mc_lhe_write_device", "mc_lhe_close", "mc_generate_lhe")
+           "mc_lhe_write_device", "mc_lhe_close", "mc_generate_lhe", "mc_vegas_set_channels", "mc_vegas_get_channels",
+           "mc_channel_update")
 
 # mc_event (include/mcint.h): one accepted event in the laboratory frame, 200 bytes
 EVENT_DTYPE = np.dtype([("event", "<i8"), ("weight", "<f8"), ("x1", "<f8"), ("x2", "<f8"), ("p", "<f8", (5, 4)),
@@ -161,6 +162,9 @@ def lib():
             "mc_lhe_write": [_vp, _vp, i64],
             "mc_lhe_write_device": [_vp, _vp, i64, _vp],
             "mc_lhe_close": [_vp, d, d, d, ctypes.POINTER(ctypes.c_int64)],
+            "mc_vegas_set_channels": [_vp, _dp],
+            "mc_vegas_get_channels": [_vp, _dp, _dp],
+            "mc_channel_update": [i32, _dp, _dp, d, d, _dp],
             "mc_generate_lhe": [ctypes.POINTER(Integrand), _vp, i32, i32, i64, i32, u64, i32, d, ctypes.c_char_p, i32,
                                 _vp, ctypes.POINTER(Result), ctypes.POINTER(GenStats)],
         }
@@ -468,6 +472,27 @@ def mc_generate_lhe(itg, pdf, path, ntrain, niter, nevents, nbins=50, seed=0, pr
 def events_from_bytes(buf):
     """View raw mc_event bytes (e.g. a uint8 tensor copied to the host) as records."""
     return np.frombuffer(memoryview(buf), dtype=EVENT_DTYPE)
+
+
+def mc_vegas_set_channels(v, alpha):
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    _check(lib().mc_vegas_set_channels(v.handle, a.ctypes.data_as(_dp)))
+
+
+def mc_vegas_get_channels(v):
+    """(alpha[3], W[3]) of the three-channel process."""
+    a, w = np.zeros(3), np.zeros(3)
+    _check(lib().mc_vegas_get_channels(v.handle, a.ctypes.data_as(_dp), w.ctypes.data_as(_dp)))
+    return a, w
+
+
+def mc_channel_update(alpha, w, beta=0.5, amin=0.02):
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros(len(a))
+    _check(lib().mc_channel_update(len(a), a.ctypes.data_as(_dp), ww.ctypes.data_as(_dp), beta, amin,
+                                   out.ctypes.data_as(_dp)))
+    return out
 
 
 def mc_vegas_refine(v, alpha=1.5, stream=None):
