@@ -9,7 +9,8 @@ followed by the grid refinement.  Inputs are synthetic and seeded.
 
 The line also carries "time_to_target": the GPU time to a 1e-3 relative
 error on gg -> t tbar g in 7 sampled dimensions for plain FP64 VEGAS, FP32
-VEGAS and FP32 + normalizing-flow sampling with VEGAS as its judge and
+VEGAS, FP32 three-channel sampling (per-channel grids, Kleiss-Pittau channel
+weights) and FP32 + normalizing-flow sampling with VEGAS as its judge and
 fallback (200 online training steps and the judge's VEGAS iteration
 included; mc_integrate_flow), each run from scratch, with the variance per
 event and the unweighting efficiency of each (the flow's from a separately
