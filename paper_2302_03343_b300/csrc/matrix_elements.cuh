@@ -289,6 +289,17 @@ MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4
   return g2 * g2 * g2 * total * R(2) / (R(27) * R(256));
 }
 
+// Unroll factors of the helicity loops of me2_gg_ttbarg_p (1: a rolled loop,
+// which keeps the consumer warps' register count down).
+#ifndef MC_ME_UNROLL_H0
+#define MC_ME_UNROLL_H0 1
+#define MC_ME_UNROLL_H1 1
+#define MC_ME_UNROLL_H2 1
+#endif
+#define MC_PRAGMA(x) _Pragma(#x)
+#define MC_UNROLL_(n) MC_PRAGMA(unroll n)
+#define MC_UNROLL(n) MC_UNROLL_(n)
+
 // FP32 gg -> t tbar g with packed (re, im) complex arithmetic: the same
 // colour-ordered amplitudes as me2_gg_ttbarg, regrouped per ordering (abc):
 //   Gamma(abc) v = eps_a S_a [eps_b X_c - J(bc) v] - J(ab) X_c + J(abc) v,
@@ -336,17 +347,17 @@ MC_D float me2_gg_ttbarg_p(const v4<float>& pa, const v4<float>& pb, const v4<fl
     }
   }
   f2 total0 = bc2(0.0f), total1 = bc2(0.0f);
-#pragma unroll 1
+  MC_UNROLL(MC_ME_UNROLL_H0)
   for (int h0 = 0; h0 < 2; ++h0) {
     const v4<float> e0 = eps[0][h0];
     const sp4p x0 = prop_colp(kc[0], mc_[0], slash_colp(make_sv(e0), v));
-#pragma unroll 1
+    MC_UNROLL(MC_ME_UNROLL_H1)
     for (int h1 = 0; h1 < 2; ++h1) {
       const v4<float> e1 = eps[1][h1];
       const sp4p x1 = prop_colp(kc[1], mc_[1], slash_colp(make_sv(e1), v));
       const v4<float> j01 = gluon_current(e0, q[0], e1, q[1], i01);
       const sp4p u01 = slash_colp(make_sv(j01), v);
-#pragma unroll 1
+      MC_UNROLL(MC_ME_UNROLL_H2)
       for (int h2 = 0; h2 < 2; ++h2) {
         const v4<float> e2 = eps[2][h2];
         const v4<float> j02 = gluon_current(e0, q[0], e2, q[2], i02);
