@@ -56,10 +56,10 @@ METRIC = "events/sec and GPU time to 1e-3 rel. error: FP32+flow vs plain FP64 VE
 # the launch's 8 049 119 in-cut events; see profiles/.
 FLOP_PER_EVENT = 22434.0
 # DRAM bytes (read + write) of one launch of that kernel, from an ncu capture
-# of this workload (0.46 MB read + 2.18 MB written; see profiles/).  Nothing
+# of this workload (0.47 MB read + 2.62 MB written; see profiles/).  Nothing
 # per event reaches DRAM: the kernel reads the grid and the PDF grid and
 # writes histograms and per-block partials.
-TRAFFIC_BYTES = 2643712
+TRAFFIC_BYTES = 3088128
 FP32_LANES_PER_SM = 128
 # time to a target relative error (gg -> t tbar g, 7 sampled dimensions):
 # FP32 + normalizing flow (6 coupling layers, 32 bins, 3 x 256 BF16 hidden
