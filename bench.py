@@ -21,7 +21,9 @@ graph, autotuned shape) against the sum of their single launches; and
 tab:fktable (400 members, 11 flavours, 2415 x points) against HBM; and
 "unweighting": unweighted event generation on the benchmark workload (weights
 pass, device-side acceptance-rejection and export of the accepted events,
-and the native LHE writer's throughput on them).
+and the native LHE writer's throughput on them); and "samplers": RAMBO, the
+hierarchical generator and three-channel sampling side by side (time per
+iteration, variance per event, unweighting efficiency).
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a
 bounded sample of events per step on the host cores).
@@ -364,6 +366,40 @@ def unweighting(M, pdf, stream, edges, plain_ms, reps=3):
     return out
 
 
+def samplers(M, pdf, stream, iterations=10):
+    """The three phase-space samplers of gg -> t tbar g side by side, FP32,
+    1e7 events per iteration, each adapted for `iterations` iterations from
+    a uniform grid (the three-channel sampler also updating its channel
+    probabilities): the fused kernel's time per iteration (median of the
+    last 7), the relative variance per event and the unweighting efficiency
+    <w>/w_max of the last iteration, and their product variance x time, the
+    cost of a given precision (thesis Sec. "Multi-channel Monte Carlo" and
+    Sec. "Unweighted event exporter": RAMBO's flat sampling against
+    channels that follow the peaks of |M|^2)."""
+    out = {}
+    for name, itg in (("rambo_14d", W.gg_ttbarg()), ("hierarchical_7d", W.gg_ttbarg_7d()),
+                      ("three_channel", W.gg_ttbarg_mc())):
+        v = M.mc_vegas_init(itg.ndim(), NBINS, 2000, M.MC_FP32_KAHAN)
+        ms = []
+        for i in range(iterations):
+            r = M.mc_vegas_iterate(v, itg, pdf, EVENTS, stream)
+            if itg.proc == W.GG_TTBARG_MC:
+                a, w = M.mc_vegas_get_channels(v)
+                M.mc_vegas_set_channels(v, M.mc_channel_update(a, w, 0.5, 0.02))
+            M.mc_vegas_refine(v, ALPHA, stream)
+            if i >= iterations - 7:
+                ms.append(M.mc_vegas_kernel_ms(v))
+        mean = r.sum / r.n
+        rv = (r.sum2 / r.n) / (mean * mean) - 1.0
+        kms = statistics.median(ms)
+        out[name] = {"kernel_ms": kms, "rel_var_per_event": rv, "unweighting_eff": mean / r.wmax,
+                     "events_in_cuts": r.n_nonzero, "var_x_ms": rv * kms, "mean_pb": mean}
+        if itg.proc == W.GG_TTBARG_MC:
+            out[name]["alpha"] = [round(x, 4) for x in M.mc_vegas_get_channels(v)[0]]
+        v.free()
+    return out
+
+
 def profile_case(case):
     """A small fixed workload for ncu captures (no timing output)."""
     import torch
@@ -610,6 +646,7 @@ def run_native(args, rank, world):
         line["batch16"] = batch16(M, pdf, stream)
         line["pdf_members"] = pdf_members(M, stream)
         line["unweighting"] = unweighting(M, pdf, stream, M.mc_vegas_get_grid(v), mean_kernel_ms)
+        line["samplers"] = samplers(M, pdf, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

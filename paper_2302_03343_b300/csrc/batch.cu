@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
   const int nb = b.nbins;
   const int nhist = MC_MAX_DIM * nb, nedge = MC_MAX_DIM * (nb + 1);
   const WsRing ring = {reinterpret_cast<uint32_t*>(smem), full, empty, count};
-  unsigned char* rest = smem + size_t(kWsSlots) * kWsWords * 32 * 4;
+  unsigned char* rest = smem + size_t(kWsSlots) * ws_words(P_GG_TTBARG) * 32 * 4;
   float* sh_w2 = reinterpret_cast<float*>(rest);
   unsigned int* sh_n = reinterpret_cast<unsigned int*>(rest + size_t(nhist) * 4);
   float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
@@ -449,7 +449,7 @@ int build_tiles(mc_batch b) {
   b->smem = ((nhist * 12 + 15) / 16) * 16 + r * (size_t(MC_MAX_DIM) * (b->nbins + 1)) +
             (b->pdf ? r * size_t(b->pdf->nx) * 23 : 0);
   if (b->ws)
-    b->smem = size_t(mc::kWsSlots) * mc::kWsWords * 32 * 4 + ((nhist * 8 + 15) / 16) * 16 +
+    b->smem = size_t(mc::kWsSlots) * mc::ws_words(mc::P_GG_TTBARG) * 32 * 4 + ((nhist * 8 + 15) / 16) * 16 +
               4 * (size_t(MC_MAX_DIM) * (b->nbins + 1)) + (b->pdf ? 4 * size_t(b->pdf->nx) * 23 : 0);
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);

@@ -49,15 +49,26 @@ MC_D void acc_add(Acc& acc, double w) {
   acc.wmax = fmax(acc.wmax, w);
 }
 
-// One event of the three-channel gg -> t tbar g process (thesis Sec.
+// The kinematic part of one three-channel gg -> t tbar g event (thesis Sec.
 // "Multi-channel Monte Carlo"): the channel from Philox call 254, the 7
 // uniforms through the (x1, x2) grid and that channel's grid, the channel's
-// map, the densities of all three channels at the point (the others by their
-// inverse maps and grid densities), w = f J_x / sum_j alpha_j p_j, the
-// alpha-update sums and the histograms of the grid dimensions used.
-template <bool FP64, bool RECORD, class R, class H>
-MC_D double process_event_mc(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, H* sh_w2,
-                             unsigned int* sh_n, uint64_t ev, double* rec, Acc& acc) {
+// map, the densities of all three channels at the point (the others by
+// their inverse maps and grid densities), the lab-frame gluon cuts and the
+// gluon luminosity.  kin.psw = 1 / sum_j alpha_j p_j, so that the weight is
+// gg_weight(kin, |M|^2) * jx.
+template <class R>
+struct McEvent {
+  int ch, pass;
+  uint64_t k[7];
+  R x[7];
+  int bin[7];
+  R jx, jrest;
+  double dens[kChannels], pden;
+  GgKin<R> kin;
+};
+
+template <bool FP64, class R>
+MC_D void mc_prepare(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, uint64_t ev, McEvent<R>& e) {
   constexpr int ND = 7;
   const int nb = a.nbins;
   const uint4 cw = philox4x32_10(make_uint4(uint32_t(ev), uint32_t(ev >> 32), a.iteration,
@@ -65,62 +76,73 @@ MC_D double process_event_mc(const KernelArgs& a, const SmPdf<R>& pdf, const R* 
                                  make_uint2(uint32_t(a.seed), uint32_t(a.seed >> 32)));
   const double uc = (double(cw.x >> 8) + 0.5) * 0x1p-24;
   const int ch = uc < a.alpha_cum[0] ? 0 : (uc < a.alpha_cum[1] ? 1 : 2);
-  uint64_t k[ND];
-  event_uniforms<ND, FP64>(a.seed, a.iteration, a.gid, ev, ND, k);
-  R x[ND];
-  int bin[ND];
-  R jx = R(1), jrest = R(1);
+  e.ch = ch;
+  e.pass = 0;
+  event_uniforms<ND, FP64>(a.seed, a.iteration, a.gid, ev, ND, e.k);
+  e.jx = R(1);
+  e.jrest = R(1);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     R jd;
-    x[d] = vegas_map_1d<R, FP64>(sh_edges + ch_grid_dim(d, ch) * (nb + 1), nb, k[d], &bin[d], &jd);
-    if (d < 2) jx *= jd; else jrest *= jd;
+    e.x[d] = vegas_map_1d<R, FP64>(sh_edges + ch_grid_dim(d, ch) * (nb + 1), nb, e.k[d], &e.bin[d], &jd);
+    if (d < 2) e.jx *= jd; else e.jrest *= jd;
   }
   const Params& p = a.prm;
   const R m = R(p.m_top);
-  const R x1 = x[0], x2 = x[1];
+  const R x1 = e.x[0], x2 = e.x[1];
   const R shat = sizeof(R) == 4 ? R(x1 * x2 * R(p.sqrt_s * p.sqrt_s)) : R(double(x1) * double(x2) * p.sqrt_s * p.sqrt_s);
-  double w = 0.0, dens[kChannels] = {0.0, 0.0, 0.0}, pden = 0.0;
-  int pass = 0;
-  v4<R> t = {}, tb = {}, g = {};
-  GgKin<R> kin;
-  R me2 = R(0);
-  if (shat > R(4) * m * m) {
-    const R rs = m_sqrt(shat);
-    const ChCtx<R> c = ch_ctx<R>(m, rs, R(p.ptcut_g), R(p.etacut_g), R(0.5) * m_log(x1 / x2));
-    R wi;
-    if (ch_forward<R>(ch, c, x + 2, &t, &tb, &g, &wi) && wi > R(0)) {
-      dens[ch] = 1.0 / (double(jrest) * double(wi));
+  e.dens[0] = e.dens[1] = e.dens[2] = 0.0;
+  e.pden = 0.0;
+  e.kin.shat = shat;
+  e.kin.k[0] = e.kin.k[1] = e.kin.k[2] = v4<R>{R(0), R(0), R(0), R(0)};
+  if (!(shat > R(4) * m * m)) return;
+  const R rs = m_sqrt(shat);
+  e.kin.rs = rs;
+  const ChCtx<R> c = ch_ctx<R>(m, rs, R(p.ptcut_g), R(p.etacut_g), R(0.5) * m_log(x1 / x2));
+  v4<R>& t = e.kin.k[0];
+  v4<R>& tb = e.kin.k[1];
+  v4<R>& g = e.kin.k[2];
+  R wi;
+  if (!ch_forward<R>(ch, c, e.x + 2, &t, &tb, &g, &wi) || !(wi > R(0))) return;
+  e.dens[ch] = 1.0 / (double(e.jrest) * double(wi));
 #pragma unroll
-      for (int j = 0; j < kChannels; ++j) {
-        if (j == ch) continue;
-        R uj[5], wj;
-        if (ch_inverse<R>(j, c, t, tb, g, uj, &wj) && wj > R(0)) {
-          R rho = R(1);
+  for (int j = 0; j < kChannels; ++j) {
+    if (j == ch) continue;
+    R uj[5], wj;
+    if (ch_inverse<R>(j, c, t, tb, g, uj, &wj) && wj > R(0)) {
+      R rho = R(1);
 #pragma unroll
-          for (int d = 0; d < 5; ++d) rho *= grid_density<R>(sh_edges + ch_grid_dim(d + 2, j) * (nb + 1), nb, uj[d]);
-          dens[j] = double(rho) / double(wj);
-        }
-      }
-      pden = a.alpha[0] * dens[0] + a.alpha[1] * dens[1] + a.alpha[2] * dens[2];
-      // the gluon cuts in the lab frame (pT, and |eta_cm + y_b| < cut without logarithms)
-      const R pt2 = g.x * g.x + g.y * g.y, ptc = R(p.ptcut_g);
-      const R pabs = m_sqrt(pt2 + g.z * g.z);
-      const R fwd = (pabs + g.z) * x1, bwd = (pabs - g.z) * x2, e2 = R(a.e2eta);
-      if (pt2 > ptc * ptc && fwd < e2 * bwd && bwd < e2 * fwd) {
-        pass = 1;
-        kin.k[0] = t;
-        kin.k[1] = tb;
-        kin.k[2] = g;
-        kin.shat = shat;
-        kin.rs = rs;
-        kin.lgg = xf_over_x(pdf.tab[0], x1) * xf_over_x(pdf.tab[0], x2);
-        kin.flux = sizeof(R) == 4 ? R(p.gev2pb) / (R(2) * shat) : R(0);
-        kin.psw = 1.0 / pden;
-        me2 = gg_me2<R>(a, kin);
-        w = gg_weight<R>(a, kin, me2) * double(jx);
-      }
+      for (int d = 0; d < 5; ++d) rho *= grid_density<R>(sh_edges + ch_grid_dim(d + 2, j) * (nb + 1), nb, uj[d]);
+      e.dens[j] = double(rho) / double(wj);
     }
+  }
+  e.pden = a.alpha[0] * e.dens[0] + a.alpha[1] * e.dens[1] + a.alpha[2] * e.dens[2];
+  // the gluon cuts in the lab frame (pT, and |eta_cm + y_b| < cut without logarithms)
+  const R pt2 = g.x * g.x + g.y * g.y, ptc = R(p.ptcut_g);
+  const R pabs = m_sqrt(pt2 + g.z * g.z);
+  const R fwd = (pabs + g.z) * x1, bwd = (pabs - g.z) * x2, e2 = R(a.e2eta);
+  if (!(pt2 > ptc * ptc && fwd < e2 * bwd && bwd < e2 * fwd)) return;
+  e.pass = 1;
+  e.kin.lgg = xf_over_x(pdf.tab[0], x1) * xf_over_x(pdf.tab[0], x2);
+  e.kin.flux = sizeof(R) == 4 ? R(p.gev2pb) / (R(2) * shat) : R(0);
+  e.kin.psw = 1.0 / e.pden;
+}
+
+// One three-channel event: mc_prepare, |M|^2 and w = f J_x / sum_j alpha_j
+// p_j, then the sums, the alpha-update sums and the histograms of the grid
+// dimensions used (or, with RECORD, the per-event record).
+template <bool FP64, bool RECORD, class R, class H>
+MC_D double process_event_mc(const KernelArgs& a, const SmPdf<R>& pdf, const R* sh_edges, H* sh_w2,
+                             unsigned int* sh_n, uint64_t ev, double* rec, Acc& acc) {
+  constexpr int ND = 7;
+  const int nb = a.nbins;
+  McEvent<R> e;
+  mc_prepare<FP64, R>(a, pdf, sh_edges, ev, e);
+  double w = 0.0;
+  R me2 = R(0);
+  if (e.pass) {
+    me2 = gg_me2<R>(a, e.kin);
+    w = gg_weight<R>(a, e.kin, me2) * double(e.jx);
   }
   int status = 0;
   if (!isfinite(w)) {
@@ -130,45 +152,45 @@ MC_D double process_event_mc(const KernelArgs& a, const SmPdf<R>& pdf, const R* 
   if (RECORD) {
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      rec[MC_REC_K + d] = double(k[d]);
-      rec[MC_REC_X + d] = double(x[d]);
-      rec[MC_REC_BIN + d] = double(bin[d]);
+      rec[MC_REC_K + d] = double(e.k[d]);
+      rec[MC_REC_X + d] = double(e.x[d]);
+      rec[MC_REC_BIN + d] = double(e.bin[d]);
     }
-    const R h = m_sqrt(m_max(shat, R(0))) * R(0.5);
+    const R h = m_sqrt(m_max(e.kin.shat, R(0))) * R(0.5);
     rec_p4(rec, 0, v4<R>{h, R(0), R(0), h});
     rec_p4(rec, 1, v4<R>{h, R(0), R(0), -h});
-    rec_p4(rec, 2, t);
-    rec_p4(rec, 3, tb);
-    rec_p4(rec, 4, g);
-    rec[MC_REC_X1] = double(x1);
-    rec[MC_REC_X2] = double(x2);
-    rec[MC_REC_SHAT] = double(shat);
-    rec[MC_REC_LUMI] = pass ? double(kin.lgg) : 0.0;
+    rec_p4(rec, 2, e.kin.k[0]);
+    rec_p4(rec, 3, e.kin.k[1]);
+    rec_p4(rec, 4, e.kin.k[2]);
+    rec[MC_REC_X1] = double(e.x[0]);
+    rec[MC_REC_X2] = double(e.x[1]);
+    rec[MC_REC_SHAT] = double(e.kin.shat);
+    rec[MC_REC_LUMI] = e.pass ? double(e.kin.lgg) : 0.0;
     rec[MC_REC_ME2] = double(me2);
-    rec[MC_REC_PSW] = pden > 0.0 ? 1.0 / pden : 0.0;
-    rec[MC_REC_JAC] = double(jx) * double(jrest);
-    rec[MC_REC_F] = w / double(jx);
+    rec[MC_REC_PSW] = e.pden > 0.0 ? 1.0 / e.pden : 0.0;
+    rec[MC_REC_JAC] = double(e.jx) * double(e.jrest);
+    rec[MC_REC_F] = w / double(e.jx);
     rec[MC_REC_W] = w;
-    rec[MC_REC_PASS] = double(pass);
+    rec[MC_REC_PASS] = double(e.pass);
     rec[MC_REC_STATUS] = double(status);
-    rec[MC_REC_CHANNEL] = double(ch);
+    rec[MC_REC_CHANNEL] = double(e.ch);
 #pragma unroll
-    for (int j = 0; j < kChannels; ++j) rec[MC_REC_DENS + j] = dens[j];
+    for (int j = 0; j < kChannels; ++j) rec[MC_REC_DENS + j] = e.dens[j];
     return w;
   }
   if (status != 0) ++acc.nbad;
   acc_add(acc, w);
   if (w != 0.0) {
-    const double w2p = w * w / pden;
+    const double w2p = w * w / e.pden;
 #pragma unroll
-    for (int j = 0; j < kChannels; ++j) acc.wch[j] += w2p * dens[j];
+    for (int j = 0; j < kChannels; ++j) acc.wch[j] += w2p * e.dens[j];
   }
   const H w2h = H(w * w);
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
-    const int gd = ch_grid_dim(d, ch);
-    atomicAdd(&sh_w2[gd * nb + bin[d]], w2h);
-    atomicAdd(&sh_n[gd * nb + bin[d]], 1u);
+    const int gd = ch_grid_dim(d, e.ch);
+    atomicAdd(&sh_w2[gd * nb + e.bin[d]], w2h);
+    atomicAdd(&sh_n[gd * nb + e.bin[d]], 1u);
   }
   return w;
 }

@@ -172,7 +172,7 @@ static cudaError_t launch_one(const KernelArgs& a, int grid, size_t smem, cudaSt
 template <int PROC>
 static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
   auto k = a.wout ? ws_integrand_kernel<PROC, true> : ws_integrand_kernel<PROC, false>;
-  const size_t smem = ws_smem_bytes(a.ndim, a.nbins, a.pdf.nx);
+  const size_t smem = ws_smem_bytes(PROC, a.ndim, a.nbins, a.pdf.nx);
   (void)cudaGetLastError();
   const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
@@ -180,7 +180,9 @@ static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-bool integrand_ws(int proc, bool fp64) { return !fp64 && (proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D); }
+bool integrand_ws(int proc, bool fp64) {
+  return !fp64 && (proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_GG_TTBARG_MC);
+}
 int integrand_threads(int proc, bool fp64) { return integrand_ws(proc, fp64) ? kWsThreads : kBlock; }
 // events one block takes per round of its grid-stride loop
 int integrand_block_events(int proc, bool fp64) { return integrand_ws(proc, fp64) ? 32 * kWsProducerWarps : kBlock; }
@@ -188,7 +190,9 @@ int integrand_block_events(int proc, bool fp64) { return integrand_ws(proc, fp64
 template <bool RECORD>
 static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem, cudaStream_t st) {
   if (!RECORD && integrand_ws(proc, fp64))
-    return proc == P_GG_TTBARG ? launch_ws<P_GG_TTBARG>(a, grid, st) : launch_ws<P_GG_TTBARG_7D>(a, grid, st);
+    return proc == P_GG_TTBARG      ? launch_ws<P_GG_TTBARG>(a, grid, st)
+           : proc == P_GG_TTBARG_7D ? launch_ws<P_GG_TTBARG_7D>(a, grid, st)
+                                    : launch_ws<P_GG_TTBARG_MC>(a, grid, st);
   switch (proc) {
     case P_EE_MUMU:
       return fp64 ? launch_one<P_EE_MUMU, true, RECORD>(a, grid, smem, st)
@@ -213,7 +217,7 @@ static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, 
 }
 
 size_t integrand_smem(int proc, bool fp64, int ndim, int nbins, int nx) {
-  if (integrand_ws(proc, fp64)) return ws_smem_bytes(ndim, nbins, nx);
+  if (integrand_ws(proc, fp64)) return ws_smem_bytes(proc, ndim, nbins, nx);
   const size_t r = fp64 ? 8 : 4;
   const int nfl = proc == P_PP_TTBAR ? 11 : ((proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_GG_TTBARG_MC) ? 1 : 0);
   const size_t hist = ((size_t(ndim) * nbins * 12 + 15) / 16) * 16;

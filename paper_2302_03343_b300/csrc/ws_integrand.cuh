@@ -54,10 +54,16 @@ constexpr int kWsSlotsPerProducer = 4;
 constexpr int kWsSlots = kWsSlotsPerProducer * kWsProducerWarps;
 // record words of one event (structure of arrays inside a slot: word j of
 // lane e at [j][e]): k[3] (12), rs, lgg, flux, jac, psw (2 words), bins (4),
-// and the event's index in the launch (weights pass only)
+// the event's index in the launch (weights pass only), and for the
+// three-channel process its channel and the ratios p_j / p (3)
 enum : int {
-  kWK = 0, kWRs = 12, kWLgg = 13, kWFlux = 14, kWJac = 15, kWPsw = 16, kWBin = 18, kWIdx = 22, kWsWords = 23
+  kWK = 0, kWRs = 12, kWLgg = 13, kWFlux = 14, kWJac = 15, kWPsw = 16, kWBin = 18, kWIdx = 22, kWCh = 23,
+  kWDens = 24
 };
+// words per record: 23, and 27 for the three-channel process (the ring of
+// the others stays at 23 words so their shared-memory carveout, and the L1
+// left for their register spills, does not change)
+MC_HD constexpr int ws_words(int proc) { return proc == P_GG_TTBARG_MC ? 27 : 23; }
 constexpr unsigned long long kWsWaitNs = 2000000000ull;
 // Registers per thread: the launch gets kWsRegs (65536 / threads, rounded
 // down to a multiple of 8); producers give up to kWsProducerRegs, consumers
@@ -96,8 +102,8 @@ MC_D bool ws_wait(uint64_t* bar, uint32_t parity) {
 
 // Dynamic shared memory of one block: the ring, then the histograms, the
 // grid edges and the PDF tables (as in the per-thread fused kernel).
-inline size_t ws_smem_bytes(int ndim, int nbins, int nx) {
-  const size_t ring = size_t(kWsSlots) * kWsWords * 32 * 4;
+inline size_t ws_smem_bytes(int proc, int ndim, int nbins, int nx) {
+  const size_t ring = size_t(kWsSlots) * ws_words(proc) * 32 * 4;
   const size_t hist = ((size_t(ndim) * nbins * 8 + 15) / 16) * 16;
   return ring + hist + 4 * (size_t(ndim) * (nbins + 1) + size_t(nx) * 3);
 }
@@ -105,7 +111,7 @@ inline size_t ws_smem_bytes(int ndim, int nbins, int nx) {
 // Shared-memory ring of one block: kWsSlots slots of 32 event records, their
 // full/empty mbarriers and counts (-1 = end marker).
 struct WsRing {
-  uint32_t* rec;   // [kWsSlots][kWsWords][32]
+  uint32_t* rec;   // [kWsSlots][ws_words(PROC)][32]
   uint64_t* full;  // [kWsSlots], arrival count 32 (the producer's lanes)
   uint64_t* empty;  // [kWsSlots], arrival count 32 (the consumer's lanes)
   int* count;      // [kWsSlots]
@@ -149,8 +155,28 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
 #pragma unroll
     for (int j = 0; j < NW; ++j) binw[j] = 0u;
     float jac = 1.0f;
-    int st = 0;
-    if (i < hi) {
+    int st = 0, ch = 0;
+    float dr[kChannels] = {0.0f, 0.0f, 0.0f};
+    if constexpr (PROC == P_GG_TTBARG_MC) {
+      if (i < hi) {
+        McEvent<float> e;
+        mc_prepare<false, float>(a, pdf, sh_edges, a.first + uint64_t(i), e);
+#pragma unroll
+        for (int d = 0; d < 7; ++d) {
+          binw[d / 4] |= uint32_t(e.bin[d]) << (8 * (d % 4));
+          atomicAdd(&sh_n[ch_grid_dim(d, e.ch) * nb + e.bin[d]], 1u);
+        }
+        ch = e.ch;
+        jac = e.jx;
+        kin = e.kin;
+        st = e.pass;
+        if (e.pass) {
+#pragma unroll
+          for (int j = 0; j < kChannels; ++j) dr[j] = float(e.dens[j] / e.pden);
+        }
+        if (WOUT && !e.pass) a.wout[i] = 0.0;
+      }
+    } else if (i < hi) {
       uint64_t k[MAXD];
       event_uniforms<MAXD, false>(a.seed, a.iteration, a.gid, a.first + uint64_t(i), ndim, k);
       float x[MAXD];
@@ -179,7 +205,7 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
     }
     if (pass) {
       const int pos = fill + __popc(m & ((1u << lane) - 1u));
-      uint32_t* r = ring.rec + size_t(slot_of(pos < 32 ? seq : seq + 1)) * kWsWords * 32 + (pos & 31);
+      uint32_t* r = ring.rec + size_t(slot_of(pos < 32 ? seq : seq + 1)) * ws_words(PROC) * 32 + (pos & 31);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         r[(kWK + 4 * j + 0) * 32] = __float_as_uint(kin.k[j].e);
@@ -196,6 +222,11 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
 #pragma unroll
       for (int j = 0; j < NW; ++j) r[(kWBin + j) * 32] = binw[j];
       if (WOUT) r[kWIdx * 32] = uint32_t(i);
+      if constexpr (PROC == P_GG_TTBARG_MC) {
+        r[kWCh * 32] = uint32_t(ch);
+#pragma unroll
+        for (int j = 0; j < kChannels; ++j) r[(kWDens + j) * 32] = __float_as_uint(dr[j]);
+      }
     }
     fill += tot;
     if (fill >= 32) {
@@ -249,7 +280,7 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int 
       continue;
     }
     if (lane < cnt) {
-      const uint32_t* r = ring.rec + size_t(s) * kWsWords * 32 + lane;
+      const uint32_t* r = ring.rec + size_t(s) * ws_words(PROC) * 32 + lane;
       GgKin<float> kin;
 #pragma unroll
       for (int j = 0; j < 3; ++j)
@@ -281,9 +312,20 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int 
       acc.q_hi = t2;
       if (w != 0.0) ++acc.nnz;
       acc.wmax = fmax(acc.wmax, w);
+      if constexpr (PROC == P_GG_TTBARG_MC) {
+        const int ch = int(r[kWCh * 32]);
+        if (w != 0.0) {
 #pragma unroll
-      for (int dd = 0; dd < MAXD; ++dd)
-        if (dd < ndim) atomicAdd(&sh_w2[dd * nb + int((binw[dd / 4] >> (8 * (dd % 4))) & 0xffu)], float(w2));
+          for (int j = 0; j < kChannels; ++j) acc.wch[j] += w2 * double(__uint_as_float(r[(kWDens + j) * 32]));
+        }
+#pragma unroll
+        for (int d = 0; d < 7; ++d)
+          atomicAdd(&sh_w2[ch_grid_dim(d, ch) * nb + int((binw[d / 4] >> (8 * (d % 4))) & 0xffu)], float(w2));
+      } else {
+#pragma unroll
+        for (int dd = 0; dd < MAXD; ++dd)
+          if (dd < ndim) atomicAdd(&sh_w2[dd * nb + int((binw[dd / 4] >> (8 * (dd % 4))) & 0xffu)], float(w2));
+      }
     }
     mbar_arrive(&ring.empty[s]);
   }
@@ -294,7 +336,7 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int 
 // at most 2^32 - 1 events).
 template <int PROC, bool WOUT>
 __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs a) {
-  static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D, "gg -> t tbar g only");
+  static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D || PROC == P_GG_TTBARG_MC, "gg -> t tbar g only");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kWsSlots], empty[kWsSlots];
   __shared__ int count[kWsSlots];
@@ -303,7 +345,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
   const int ndim = a.ndim, nb = a.nbins;
   const int nedge = ndim * (nb + 1), nhist = ndim * nb;
   const WsRing ring = {reinterpret_cast<uint32_t*>(smem), full, empty, count};
-  unsigned char* rest = smem + size_t(kWsSlots) * kWsWords * 32 * 4;
+  unsigned char* rest = smem + size_t(kWsSlots) * ws_words(PROC) * 32 * 4;
   float* sh_w2 = reinterpret_cast<float*>(rest);
   unsigned int* sh_n = reinterpret_cast<unsigned int*>(rest + size_t(nhist) * 4);
   float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
@@ -349,6 +391,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
   }
   if (!ok) atomicExch(&failed, 1);
   __syncthreads();
+  if constexpr (PROC == P_GG_TTBARG_MC) channel_sums_add(acc, a.wch);
   block_reduce(acc, warp_part, &a.partials[blockIdx.x]);
   if (threadIdx.x == 0 && failed) {
     const double nan = __longlong_as_double(0x7ff8000000000000LL);

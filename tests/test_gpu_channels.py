@@ -153,6 +153,46 @@ def test_iteration_sums_histograms_and_channel_sums(gpu, oracle_pdf):
     assert np.max(np.abs(w2[nzb] / ref["hist_w2"][nzb] - 1)) < 1e-10
 
 
+def test_fp32_warp_specialised_iteration_matches_the_event_records(gpu):
+    """FP32 iterations run the warp-specialised kernel (producer warps: channel
+    choice, maps, densities, cuts; consumer warps: |M|^2).  Against the
+    per-event records of the one-event-per-thread path for the same events:
+    the weights (from the weights pass) agree to FP32 rounding (the two
+    kernels inline the same FP32 code, but the compiler may fuse its
+    multiply-adds differently), the launch's sums are the sums of its
+    weights, and the bin counts of all 17 grid dimensions are identical."""
+    itg = W.gg_ttbarg_mc()
+    edges = random_grid(17, 50, 12).astype(np.float32).astype(np.float64)
+    n = 60000
+    v = make_vegas(M.MC_FP32_KAHAN, edges, iteration=1, seed=6)
+    rec = torch.empty((n, M.REC_STRIDE), dtype=torch.float64, device="cuda")
+    M.mc_debug_events(v, itg, gpu, 0, n, rec)
+    wd = torch.empty(n, dtype=torch.float64, device="cuda")
+    r = M.mc_vegas_iterate_weights(v, itg, gpu, n, wd)
+    _, cnt = M.mc_vegas_get_hist(v)
+    alpha, wch = M.mc_vegas_get_channels(v)
+    v.free()
+    g = rec.cpu().numpy()
+    w = g[:, R["W"]]
+    ws = wd.cpu().numpy()
+    assert np.array_equal(ws != 0, w != 0) and r.n_nonzero == np.count_nonzero(w)
+    nz = w != 0
+    e = np.abs(ws[nz] / w[nz] - 1)
+    assert np.median(e) < 1e-6 and e.max() < 1e-3, (np.median(e), e.max())
+    assert abs(r.sum - math.fsum(ws)) <= 1e-12 * abs(r.sum)
+    assert abs(r.sum2 - math.fsum(ws * ws)) <= 1e-12 * r.sum2
+    ch = g[:, R["CHANNEL"]].astype(int)
+    ref = np.zeros((17, 50), dtype=np.int64)
+    for d in range(7):
+        gd = np.where(d < 2, d, 2 + 5 * ch + (d - 2))
+        np.add.at(ref, (gd, g[:, R["BIN"] + d].astype(int)), 1)
+    assert np.array_equal(cnt, ref)
+    dens = g[:, R["DENS"]:R["DENS"] + 3]
+    pden = dens[nz] @ alpha
+    wref = (ws[nz, None] ** 2 * dens[nz] / pden[:, None]).sum(axis=0) / n
+    assert np.max(np.abs(wch / wref - 1)) < 1e-5
+
+
 def test_adaptation_and_alpha_update(gpu):
     """From uniform grids and equal channel probabilities, FP32: the
     integral agrees with the hierarchical single-channel integrand's, the
