@@ -26,7 +26,8 @@ class EventRecord(ctypes.Structure):
                 ("shat", ctypes.c_double), ("lumi", ctypes.c_double), ("lumi_qq", ctypes.c_double),
                 ("me2", ctypes.c_double), ("me2_qq", ctypes.c_double), ("ps_weight", ctypes.c_double),
                 ("f", ctypes.c_double), ("weight", ctypes.c_double), ("pass_", ctypes.c_int32),
-                ("status", ctypes.c_int32), ("channel", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("channel", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("me2_x", ctypes.c_double * 5), ("lumi_x", ctypes.c_double * 7)]
 
 
 class LabEvent(ctypes.Structure):
@@ -110,6 +111,11 @@ def lib():
                            ("orc_me2_gg_ttbarg", [_d, _d, _dp]), ("orc_me2_gg_ttbarg_brute", [_d, _d, _dp])]:
             getattr(L, name).argtypes = args
             getattr(L, name).restype = _d
+        for name in ("orc_me2_qqbar_ttbarg", "orc_me2_qg_ttbarq"):
+            getattr(L, name).argtypes = [_d, _d, _dp]
+            getattr(L, name).restype = _d
+        L.orc_me2_qqbar_ttbarg_eps.argtypes = [_d, _d, _dp, _dp]
+        L.orc_me2_qqbar_ttbarg_eps.restype = _d
         L.orc_ggttg_partial_amplitudes.argtypes = [_d, _d, _dp, _dp, ctypes.c_int, _dp, _dp, _dp]
         L.orc_process_ndim.argtypes = [ctypes.POINTER(IntegrandC)]
         L.orc_process_ndim.restype = ctypes.c_int
@@ -393,6 +399,25 @@ def me2_gg_ttbar_colour_ordered(alpha_s, mt, p):
 
 def me2_gg_ttbarg(alpha_s, mt, p):
     return lib().orc_me2_gg_ttbarg(alpha_s, mt, _ptr(np.ascontiguousarray(p, dtype=np.float64)))
+
+
+def me2_qqbar_ttbarg(alpha_s, mt, p):
+    """<|M|^2> of q(p0) qbar(p1) -> t(p2) tbar(p3) g(p4); p [5][4]."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    return lib().orc_me2_qqbar_ttbarg(alpha_s, mt, _ptr(p))
+
+
+def me2_qg_ttbarq(alpha_s, mt, p):
+    """<|M|^2> of q(p0) g(p1) -> t(p2) tbar(p3) q(p4) (crossing); p [5][4]."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    return lib().orc_me2_qg_ttbarq(alpha_s, mt, _ptr(p))
+
+
+def me2_qqbar_ttbarg_eps(alpha_s, mt, p, eps):
+    """Spin- and colour-summed |M|^2 /36 with the gluon polarisation replaced by eps [4] (complex)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    e = np.ascontiguousarray(np.stack([np.real(eps), np.imag(eps)], axis=1).reshape(-1), dtype=np.float64)
+    return lib().orc_me2_qqbar_ttbarg_eps(alpha_s, mt, _ptr(p), _ptr(e))
 
 
 def me2_gg_ttbarg_brute(alpha_s, mt, p):

@@ -43,6 +43,7 @@ int process_ndim(const orc_integrand& in) {
     case GAUSS: return in.gauss_dim;
     case GG_TTBARG_7D: return 7;
     case GG_TTBARG_MC: return 17;  // grid dimensions; 7 uniforms per event
+    case PP_TTBARJ: return 7;
   }
   return -1;
 }
@@ -148,6 +149,73 @@ static double integrand_value(const orc_integrand& in, const Pdf* pdf, const dou
       rec->lumi = pdf_xfxq2(*pdf, 21, x1, q2) / x1 * pdf_xfxq2(*pdf, 21, x2, q2) / x2;
       rec->me2 = me2_gg_ttbarg(in.alpha_s, m, p);
       return rec->lumi * rec->me2 / (2.0 * shat) * w * in.gev2pb;
+    }
+    case PP_TTBARJ: {
+      // p p -> t tbar + one parton at LO: every partonic channel at the same
+      // point of the hierarchical three-body phase space (the light parton
+      // massless, so the kinematics do not depend on the channel)
+      const double x1 = x[0], x2 = x[1], shat = x1 * x2 * s, m = in.m_top;
+      rec->x1 = x1;
+      rec->x2 = x2;
+      rec->shat = shat;
+      if (!(shat > 4.0 * m * m)) {
+        rec->pass = 0;
+        return 0.0;
+      }
+      const double rs = std::sqrt(shat);
+      const double masses[3] = {m, m, 0.0};
+      P4 p[5];
+      p[0] = {rs / 2.0, 0.0, 0.0, rs / 2.0};
+      p[1] = {rs / 2.0, 0.0, 0.0, -rs / 2.0};
+      double w;
+      hierarchical(3, masses, rs, x + 2, p + 2, &w);
+      for (int i = 0; i < 5; ++i) put(rec->p, i, p[i]);
+      rec->ps_weight = w;
+      // cuts on the light parton in the lab frame
+      const P4& pk = p[4];
+      const double pt = std::sqrt(pk.x * pk.x + pk.y * pk.y);
+      const double pabs = std::sqrt(pt * pt + pk.z * pk.z);
+      const double eta = 0.5 * std::log((pabs + pk.z) / (pabs - pk.z)) + 0.5 * std::log(x1 / x2);
+      if (!(pt > in.ptcut_g) || !(std::fabs(eta) < in.etacut_g)) {
+        rec->pass = 0;
+        return 0.0;
+      }
+      const double q2 = in.mu_f * in.mu_f;
+      auto f1 = [&](int pid) { return pdf_xfxq2(*pdf, pid, x1, q2) / x1; };
+      auto f2 = [&](int pid) { return pdf_xfxq2(*pdf, pid, x2, q2) / x2; };
+      double l[7] = {f1(21) * f2(21), 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int q = 1; q <= 5; ++q) {
+        l[1] += f1(q) * f2(-q);
+        l[2] += f1(-q) * f2(q);
+        l[3] += f1(q) * f2(21);
+        l[4] += f1(21) * f2(q);
+        l[5] += f1(-q) * f2(21);
+        l[6] += f1(21) * f2(-q);
+      }
+      const P4 ab[5] = {p[0], p[1], p[2], p[3], p[4]};
+      const P4 ba[5] = {p[1], p[0], p[2], p[3], p[4]};
+      const P4 abc[5] = {p[0], p[1], p[3], p[2], p[4]};  // t and tbar exchanged (charge conjugation)
+      const P4 bac[5] = {p[1], p[0], p[3], p[2], p[4]};
+      double me[7];
+      me[0] = me2_gg_ttbarg(in.alpha_s, m, p);
+      me[1] = me2_qqbar_ttbarg(in.alpha_s, m, ab);
+      me[2] = me2_qqbar_ttbarg(in.alpha_s, m, ba);
+      me[3] = me2_qg_ttbarq(in.alpha_s, m, ab);
+      me[4] = me2_qg_ttbarq(in.alpha_s, m, ba);
+      // qbar g -> t tbar qbar is q g -> t tbar q with t and tbar exchanged
+      me[5] = me2_qg_ttbarq(in.alpha_s, m, abc);
+      me[6] = me2_qg_ttbarq(in.alpha_s, m, bac);
+      double sum = 0.0;
+      for (int c = 0; c < 7; ++c) {
+        rec->lumi_x[c] = l[c];
+        sum += l[c] * me[c];
+      }
+      for (int c = 0; c < 5; ++c) rec->me2_x[c] = me[c + 2];
+      rec->lumi = l[0];
+      rec->lumi_qq = l[1];
+      rec->me2 = me[0];
+      rec->me2_qq = me[1];
+      return sum / (2.0 * shat) * w * in.gev2pb;
     }
     case GAUSS: {
       // normalised Gaussian of width sigma centred at 1/2 in every dimension

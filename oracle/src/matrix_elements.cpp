@@ -474,6 +474,119 @@ void ggttg_partial_amplitudes(double alpha_s, double mt, const P4* q_in, const c
   }
 }
 
+// ------------------------------------------------------------ q qbar -> t tbar g
+// The five Feynman diagrams of q(p0) qbar(p1) -> t(p2) tbar(p3) g(p4), with
+// the rules above: gluon emission off the quark, the antiquark, the top, the
+// anti-top, and off the s-channel gluon (three-gluon vertex).  Each diagram
+// d is written as sum_alpha [vbar(p1) Lambda_d^alpha u(p0)] [ubar(p2)
+// Theta_{d,alpha} v(p3)] times a colour factor c_d(i, j, k, l, a) (quark,
+// antiquark, top, anti-top, gluon colours), so that the spin sum is
+//   sum_{d,d'} C_{dd'} sum_{alpha,alpha'} tr[Lambda_d p0slash Lambdabar_d' p1slash]
+//                                          tr[Theta_d (p3slash - m) Thetabar_d' (p2slash + m)]
+// with the colour matrix C_{dd'} = sum over colours of c_d c_d'^* (complex)
+// and the real part of the double sum taken at the end.  The
+// gluon polarisation is summed over the two real transverse vectors, or
+// replaced by `eps_override` (the gauge-invariance pin sets it to p4).
+// Average: 1/4 (spins) x 1/9 (colours).
+static double me2_qqbar_ttbarg_impl(double alpha_s, double mt, const P4* p, const CVec4* eps_override) {
+  const double g = std::sqrt(4.0 * M_PI * alpha_s);
+  const auto& gm = gammas();
+  const double metric[4] = {1.0, -1.0, -1.0, -1.0};
+  // colour matrix of the five diagrams (complex: the three-gluon diagram's
+  // colour factor is i times a combination of the others')
+  static const std::vector<cplx> cmat = [] {
+    const auto& tt = generators();
+    std::vector<cplx> c(25, 0.0);
+    for (int a = 0; a < 8; ++a)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) {
+              cplx cf[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+              for (int b = 0; b < 8; ++b) {
+                const Mat3 ba = m3mul(tt[b], tt[a]), ab = m3mul(tt[a], tt[b]);
+                cf[0] += ba[j * 3 + i] * tt[b][k * 3 + l];
+                cf[1] += ab[j * 3 + i] * tt[b][k * 3 + l];
+                cf[2] += tt[b][j * 3 + i] * ab[k * 3 + l];
+                cf[3] += tt[b][j * 3 + i] * ba[k * 3 + l];
+                for (int c3 = 0; c3 < 8; ++c3) cf[4] += tt[b][j * 3 + i] * tt[c3][k * 3 + l] * fabc(b, c3, a);
+              }
+              for (int d = 0; d < 5; ++d)
+                for (int e = 0; e < 5; ++e) c[d * 5 + e] += cf[d] * std::conj(cf[e]);
+            }
+    return c;
+  }();
+  const P4 pp = add(p[0], p[1]), qq = add(p[2], p[3]);
+  const double P2 = dot(pp, pp), Q2 = dot(qq, qq);
+  const Mat4 s0 = slash(p[0]), s1 = slash(p[1]);
+  const Mat4 h2 = madd(slash(p[2]), mscale(meye(), mt)), h3 = madd(slash(p[3]), mscale(meye(), -mt));
+  CVec4 pol[2];
+  linear_pols(p[4], &pol[0], &pol[1]);
+  const int npol = eps_override ? 1 : 2;
+  double total = 0.0;
+  for (int h = 0; h < npol; ++h) {
+    const CVec4 eps = eps_override ? *eps_override : pol[h];
+    const Mat4 se = slash(eps);
+    const Mat4 sq1 = quark_prop(sub(p[0], p[4]), 0.0), sq2 = quark_prop(sub(p[4], p[1]), 0.0);
+    const Mat4 st3 = quark_prop(add(p[2], p[4]), mt), st4 = quark_prop(scale(add(p[3], p[4]), -1.0), mt);
+    // lower-index eps and the momenta of the three-gluon vertex (incoming P, -Q, -p4)
+    const CVec4 ce = eps;
+    const CVec4 kp = cv(add(pp, qq));                      // k - p = P + Q
+    const CVec4 pq = cv(sub(p[4], qq));                    // p - q = -Q + p4
+    const CVec4 qk = cv(scale(add(p[4], pp), -1.0));      // q - k = -p4 - P
+    const cplx kpe = cdot(kp, ce);
+    Mat4 L[5][4], H[5][4];
+    for (int al = 0; al < 4; ++al) {
+      const Mat4& ga = gm[al];
+      L[0][al] = mscale(mmul(mmul(ga, sq1), se), -I * g * g * g / Q2);
+      L[1][al] = mscale(mmul(mmul(se, sq2), ga), -I * g * g * g / Q2);
+      L[2][al] = mscale(ga, -I * g * g * g / P2);
+      L[3][al] = mscale(ga, -I * g * g * g / P2);
+      L[4][al] = mscale(ga, g * g * g / (P2 * Q2));
+      H[0][al] = mscale(ga, metric[al]);
+      H[1][al] = mscale(ga, metric[al]);
+      H[2][al] = mscale(mmul(mmul(se, st3), ga), metric[al]);
+      H[3][al] = mscale(mmul(mmul(ga, st4), se), metric[al]);
+      // Theta_{5,alpha} = sum_beta T_{alpha beta} gamma^beta,
+      // T_{ab} = g_ab (k-p).eps + eps_b (p-q)_a + eps_a (q-k)_b (lower indices)
+      Mat4 th = mzero();
+      for (int be = 0; be < 4; ++be) {
+        cplx tab = (al == be ? metric[al] : 0.0) * kpe + metric[be] * ce[be] * metric[al] * pq[al] +
+                   metric[al] * ce[al] * metric[be] * qk[be];
+        if (tab != 0.0) th = madd(th, mscale(gm[be], tab));
+      }
+      H[4][al] = th;
+    }
+    for (int d = 0; d < 5; ++d)
+      for (int e = 0; e < 5; ++e) {
+        const cplx c = cmat[d * 5 + e];
+        if (c == 0.0) continue;
+        cplx acc = 0.0;
+        for (int al = 0; al < 4; ++al)
+          for (int ap = 0; ap < 4; ++ap) {
+            const cplx tl = mtrace(mmul(mmul(L[d][al], s0), mmul(dirac_bar(L[e][ap]), s1)));
+            if (tl == 0.0) continue;
+            const cplx th = mtrace(mmul(mmul(H[d][al], h3), mmul(dirac_bar(H[e][ap]), h2)));
+            acc += tl * th;
+          }
+        total += (c * acc).real();
+      }
+  }
+  return total / 36.0;
+}
+
+double me2_qqbar_ttbarg(double alpha_s, double mt, const P4* p) { return me2_qqbar_ttbarg_impl(alpha_s, mt, p, nullptr); }
+
+// q(p0) g(p1) -> t(p2) tbar(p3) q(p4) by crossing: the antiquark of
+// q qbar -> t tbar g becomes the outgoing quark and the outgoing gluon the
+// incoming one, |M|^2(qg) = -|M|^2(q qbar)(p0, -p4; p2, p3, -p1) summed over
+// spins and colours (one fermion crossed), averaged 1/(4 x 3 x 8) instead of
+// 1/(4 x 9).
+double me2_qg_ttbarq(double alpha_s, double mt, const P4* p) {
+  const P4 q[5] = {p[0], scale(p[4], -1.0), p[2], p[3], scale(p[1], -1.0)};
+  return -me2_qqbar_ttbarg(alpha_s, mt, q) * 36.0 / 96.0;
+}
+
 }  // namespace orc
 
 extern "C" {
@@ -537,5 +650,23 @@ void orc_ggttg_partial_amplitudes(double alpha_s, double mt, const double* q_in,
     amps[2 * s] = out[s].real();
     amps[2 * s + 1] = out[s].imag();
   }
+}
+double orc_me2_qqbar_ttbarg(double alpha_s, double mt, const double* p) {
+  orc::P4 q[5];
+  pack(p, 5, q);
+  return orc::me2_qqbar_ttbarg(alpha_s, mt, q);
+}
+double orc_me2_qg_ttbarq(double alpha_s, double mt, const double* p) {
+  orc::P4 q[5];
+  pack(p, 5, q);
+  return orc::me2_qg_ttbarq(alpha_s, mt, q);
+}
+// |M|^2 with the gluon polarisation replaced by eps[4] (complex, pairs re/im).
+double orc_me2_qqbar_ttbarg_eps(double alpha_s, double mt, const double* p, const double* eps) {
+  orc::P4 q[5];
+  pack(p, 5, q);
+  const orc::CVec4 e = {orc::cplx(eps[0], eps[1]), orc::cplx(eps[2], eps[3]), orc::cplx(eps[4], eps[5]),
+                        orc::cplx(eps[6], eps[7])};
+  return orc::me2_qqbar_ttbarg_impl(alpha_s, mt, q, &e);
 }
 }

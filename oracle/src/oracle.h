@@ -78,13 +78,19 @@ double me2_gg_ttbar_colour_ordered(double alpha_s, double mt, const P4* p);
 double me2_gg_ttbarg(double alpha_s, double mt, const P4* p);
 // Feynman diagrams with explicit SU(3) colour indices (formulation B).
 double me2_gg_ttbarg_brute(double alpha_s, double mt, const P4* p);
+// q(p0) qbar(p1) -> t(p2) tbar(p3) g(p4) (five diagrams, explicit colours, Dirac
+// traces) and q(p0) g(p1) -> t(p2) tbar(p3) q(p4) by crossing; spin- and
+// colour-averaged.
+double me2_qqbar_ttbarg(double alpha_s, double mt, const P4* p);
+double me2_qg_ttbarq(double alpha_s, double mt, const P4* p);
 // Colour-ordered partial amplitudes A(sigma) for given gluon polarisation
 // vectors and explicit spinor pair (for gauge and soft-limit pins).
 void ggttg_partial_amplitudes(double alpha_s, double mt, const P4* q_in, const cplx (*eps)[4],
                               int ngluon, const cplx* ubar, const cplx* v, cplx* amps);
 
 // ---------------------------------------------------------------- integrand
-enum Process { EE_MUMU = 0, PP_TTBAR = 1, GG_TTBARG = 2, GAUSS = 3, GG_TTBARG_7D = 4, GG_TTBARG_MC = 5 };
+enum Process { EE_MUMU = 0, PP_TTBAR = 1, GG_TTBARG = 2, GAUSS = 3, GG_TTBARG_7D = 4, GG_TTBARG_MC = 5,
+               PP_TTBARJ = 6 };
 
 }  // namespace orc
 
@@ -113,6 +119,12 @@ typedef struct {
   int32_t status;
   int32_t channel;   // multi-channel process: the channel that generated the event
   int32_t pad_;
+  // p p -> t tbar + parton: |M|^2 of q qbar with the quark from beam b, of
+  // q g, g q, qbar g, g qbar (quark or antiquark from beam a or b), and the
+  // luminosities of the seven partonic channels in the order gg, q qbar,
+  // qbar q, q g, g q, qbar g, g qbar
+  double me2_x[5];
+  double lumi_x[7];
 } orc_event_record;
 
 typedef struct {

@@ -22,7 +22,7 @@ import numpy as np
 PIDS = (-5, -4, -3, -2, -1, 21, 1, 2, 3, 4, 5)
 GEV2_TO_PB = 0.3893794e9
 
-EE_MUMU, PP_TTBAR, GG_TTBARG, GAUSS, GG_TTBARG_7D, GG_TTBARG_MC = 0, 1, 2, 3, 4, 5
+EE_MUMU, PP_TTBAR, GG_TTBARG, GAUSS, GG_TTBARG_7D, GG_TTBARG_MC, PP_TTBARJ = 0, 1, 2, 3, 4, 5, 6
 FP64, FP32 = 0, 1
 
 
@@ -184,7 +184,7 @@ class Integrand:
     gev2pb: float = GEV2_TO_PB
 
     def ndim(self):
-        return {EE_MUMU: 2, PP_TTBAR: 4, GG_TTBARG: 14, GG_TTBARG_7D: 7, GG_TTBARG_MC: 17}.get(self.proc, self.gauss_dim)
+        return {EE_MUMU: 2, PP_TTBAR: 4, GG_TTBARG: 14, GG_TTBARG_7D: 7, GG_TTBARG_MC: 17, PP_TTBARJ: 7}.get(self.proc, self.gauss_dim)
 
     def asdict(self):
         return asdict(self)
@@ -214,6 +214,13 @@ def gg_ttbarg_mc(sqrt_s=13000.0):
     """gg -> t tbar g with three-channel sampling (7 uniforms per event; a
     17-dimension VEGAS grid: x1, x2 and 5 dimensions per channel), same cuts."""
     return Integrand(proc=GG_TTBARG_MC, sqrt_s=sqrt_s)
+
+
+def pp_ttbarj(sqrt_s=13000.0):
+    """p p -> t tbar + one parton at LO (gg -> t tbar g, q qbar -> t tbar g,
+    q g -> t tbar q and the charge conjugates), hierarchical 2 -> 3 phase
+    space (2 + 5 = 7 dims), the parton with pT > 20 GeV, |eta| < 2.5."""
+    return Integrand(proc=PP_TTBARJ, sqrt_s=sqrt_s)
 
 
 def gauss(dim, sigma=0.1):

@@ -97,3 +97,46 @@ def test_gg_ttbarg_rambo_and_hierarchical_integrate_alike(oracle_pdf):
     r14 = O.integrate(W.gg_ttbarg(), oracle_pdf, W.uniform_grid(14, 20), 0, seed=1, gid=0, niter=3, nevents=12000)
     r7 = O.integrate(W.gg_ttbarg_7d(), oracle_pdf, W.uniform_grid(7, 20), 0, seed=1, gid=0, niter=3, nevents=12000)
     assert abs(r14["mean"] - r7["mean"]) < 4 * math.hypot(r14["sigma"], r7["sigma"]), (r14, r7)
+
+
+def test_pp_ttbarj_channel_sum():
+    """p p -> t tbar + parton: with the quark densities set to zero it is the
+    gg -> t tbar g integrand of the same generator, event by event; with
+    only the u and ubar densities, the q qbar and qbar q channels (gluon
+    density zero) give the sum of the two orientations, and swapping the
+    beams' u and ubar swaps them."""
+    import numpy as np
+    import oracle as O
+    from paper_2302_03343_b300 import workloads as W
+    g = W.synthetic_pdf_grid(0)
+    pids = list(g.pids)
+    glue = g.xf.copy()
+    for i, pid in enumerate(pids):
+        if pid != 21:
+            glue[:, :, i] = 0.0
+    Pg = O.Pdf(W.PdfGrid(x=g.x, q=g.q, pids=g.pids, xf=glue, params=g.params))
+    edges = W.uniform_grid(7, 50)
+    n_pass = 0
+    for ev in range(300):
+        a = O.event(W.pp_ttbarj(), Pg, edges, W.FP64, 1, 0, 0, ev)
+        b = O.event(W.gg_ttbarg_7d(), Pg, edges, W.FP64, 1, 0, 0, ev)
+        assert abs(a.weight - b.weight) <= 1e-14 * abs(b.weight)  # the luminosity's division order
+        n_pass += a.pass_
+    assert n_pass > 100
+    uu = g.xf.copy()
+    for i, pid in enumerate(pids):
+        if pid not in (2, -2):
+            uu[:, :, i] = 0.0
+    Pu = O.Pdf(W.PdfGrid(x=g.x, q=g.q, pids=g.pids, xf=uu, params=g.params))
+    for ev in range(100):
+        r = O.event(W.pp_ttbarj(), Pu, edges, W.FP64, 1, 0, 0, ev)
+        if not r.pass_:
+            continue
+        l = list(r.lumi_x)
+        assert l[0] == 0 and l[3] == l[4] == l[5] == l[6] == 0 and l[1] > 0 and l[2] > 0
+        p = np.array([list(q) for q in r.p])
+        m12 = O.me2_qqbar_ttbarg(0.118, 173.0, p)
+        m21 = O.me2_qqbar_ttbarg(0.118, 173.0, p[[1, 0, 2, 3, 4]])
+        assert r.me2_qq == m12 and r.me2_x[0] == m21
+        f = (l[1] * m12 + l[2] * m21) / (2 * r.shat) * r.ps_weight * 0.3893794e9
+        assert abs(r.f / f - 1) < 1e-13

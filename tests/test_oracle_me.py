@@ -273,3 +273,66 @@ def test_ggttg_spin_flip_symmetry():
                 ratio = b / np.conj(a)
                 assert np.max(np.abs(ratio - ratio[0])) < 1e-10 * np.abs(ratio[0])
                 assert abs(abs(ratio[0]) - 1.0) < 1e-10
+
+
+# ---------------------------------------------------------------- q qbar -> t tbar g, q g -> t tbar q
+def test_qqbar_ttbarg_gauge_invariance_and_symmetries():
+    """The five diagrams of q qbar -> t tbar g: replacing the gluon
+    polarisation by its momentum gives zero (the relative factors of the
+    diagrams, including the three-gluon one with its complex colour factor,
+    are fixed by this); charge conjugation (q <-> qbar with t <-> tbar);
+    rotation and boost invariance; the crossed q g -> t tbar q is gauge
+    invariant in its incoming gluon and positive."""
+    rng = np.random.default_rng(21)
+    for rs in (420.0, 900.0, 4000.0):
+        for _ in range(4):
+            P = ggttg_point(rs, rng.uniform(size=12))
+            ref = O.me2_qqbar_ttbarg(AS, MT, P)
+            assert ref > 0
+            eg = P[4][0]
+            assert abs(O.me2_qqbar_ttbarg_eps(AS, MT, P, P[4].astype(complex))) < 1e-12 * ref * eg ** 2
+            assert abs(O.me2_qqbar_ttbarg(AS, MT, P[[1, 0, 3, 2, 4]]) / ref - 1) < 1e-12
+            th = rng.uniform(0, math.pi)
+            R = np.array([[1, 0, 0, 0], [0, math.cos(th), 0, math.sin(th)], [0, 0, 1, 0],
+                          [0, -math.sin(th), 0, math.cos(th)]])
+            assert abs(O.me2_qqbar_ttbarg(AS, MT, P @ R.T) / ref - 1) < 1e-11
+            y = -0.9
+            B = np.array([[math.cosh(y), 0, 0, math.sinh(y)], [0, 1, 0, 0], [0, 0, 1, 0],
+                          [math.sinh(y), 0, 0, math.cosh(y)]])
+            assert abs(O.me2_qqbar_ttbarg(AS, MT, P @ B.T) / ref - 1) < 1e-10
+            # q(p0) g(p1) -> t t~ q(p4): positive, and gauge invariant in the
+            # incoming gluon (the crossed momenta of q qbar -> t t~ g)
+            qg = O.me2_qg_ttbarq(AS, MT, P)
+            assert qg > 0
+            crossed = np.array([P[0], -P[4], P[2], P[3], -P[1]])
+            gauge = O.me2_qqbar_ttbarg_eps(AS, MT, crossed, (-P[1]).astype(complex))
+            assert abs(gauge) < 1e-12 * qg * P[1][0] ** 2
+
+
+def test_qqbar_ttbarg_soft_gluon_scaling():
+    """A soft gluon radiates like dE/E: |M|^2 grows as 1/E_g^2 when the gluon
+    momentum is scaled down (the tops keep the rest of the energy)."""
+    rng = np.random.default_rng(22)
+    rs = 800.0
+    P = ggttg_point(rs, rng.uniform(size=12))
+    k = P[4] / P[4][0]  # unit-energy gluon direction
+    vals = []
+    for lam in (1e-2, 1e-3, 1e-4):
+        eg = lam * rs / 4
+        # the tops share sqrt(s) - E_g back to back against the gluon in their pair frame:
+        # generate them as a two-body decay of Q = P - k eg
+        q = np.array([rs, 0, 0, 0]) - k * eg
+        mq = math.sqrt(mdot(q, q))
+        pt_rest, _ = O.two_body(mq, MT, MT, 0.3, 1.1)
+        bq = q[1:] / q[0]
+        g = 1 / math.sqrt(1 - bq @ bq)
+
+        def boost(v):
+            bp = bq @ v[1:]
+            e = g * (v[0] + bp)
+            return np.array([e, *(v[1:] + ((g - 1) * bp / (bq @ bq) + g * v[0]) * bq)])
+        pts = [boost(pt_rest[0]), boost(pt_rest[1])]
+        Pl = np.array([P[0], P[1], pts[0], pts[1], k * eg])
+        assert np.allclose(Pl[2] + Pl[3] + Pl[4], [rs, 0, 0, 0], atol=1e-9 * rs)
+        vals.append(O.me2_qqbar_ttbarg(AS, MT, Pl) * eg ** 2)
+    assert abs(vals[2] / vals[1] - 1) < 1e-2 and abs(vals[1] / vals[0] - 1) < 1e-1
