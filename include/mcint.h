@@ -60,6 +60,10 @@ extern "C" {
 #define MC_GG_TTBARG_7D 4 /* g g -> t tbar g, hierarchical 2->3 generator, 7 dims */
 #define MC_GG_TTBARG_MC 5 /* g g -> t tbar g, three-channel sampling: 7 uniforms  */
                           /* per event, 17 grid dimensions (see below)           */
+#define MC_PP_TTBARJ 6    /* p p -> t tbar + parton (gg, q qbar, q g, qbar g and  */
+                          /* the beam-swapped channels), hierarchical 2 -> 3,     */
+                          /* 7 dims; the parton with pT > ptcut_g (> 0),          */
+                          /* |eta| < etacut_g                                     */
 
 #define MC_MAX_DIM 17   /* grid dimensions: 16, or 17 for MC_GG_TTBARG_MC */
 #define MC_MAX_BINS 256
@@ -385,6 +389,9 @@ int mc_generate_lhe(const mc_integrand* itg, mc_pdf pdf, int ntrain, int niter, 
 #define MC_REC_STATUS 88  /* 0, or MC_ENAN / MC_ENOCONV                          */
 #define MC_REC_CHANNEL 89 /* three-channel process: the event's channel          */
 #define MC_REC_DENS 90    /* 3: the channels' densities at the event's point     */
+#define MC_REC_ME2_X 89   /* p p -> t tbar + parton: 5 averaged |M|^2 of q qbar   */
+                          /* (quark from beam b), q g, g q, qbar g, g qbar         */
+                          /* (slots 89.. shared with the three-channel entries)   */
 #define MC_REC_STRIDE 96
 int mc_debug_events(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t first, int64_t k,
                     double* out, void* stream);

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/mcint.h): handles, argument
 // validation, launch shapes and the host-side VEGAS driver.
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -49,6 +50,7 @@ int process_ndim(const mc_integrand* itg) {
     case MC_GAUSS: return itg->gauss_dim;
     case MC_GG_TTBARG_7D: return 7;
     case MC_GG_TTBARG_MC: return mc::kChannelGridDims;
+    case MC_PP_TTBARJ: return 7;
   }
   return -1;
 }
@@ -58,6 +60,61 @@ int num_sms() {
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
   return n;
+}
+
+// Colour matrix C_de = sum over the colours of the quark, antiquark, top,
+// anti-top and gluon of c_d c_e^* for the five diagrams of me2_qline_ttbarg:
+// c_1 = (T^b T^a)_ji T^b_kl, c_2 = (T^a T^b)_ji T^b_kl, c_3 = T^b_ji (T^a T^b)_kl,
+// c_4 = T^b_ji (T^b T^a)_kl, c_5 = f^bca T^b_ji T^c_kl, with the Gell-Mann
+// generators T^a = lambda^a / 2 and f^abc = -2 i tr([T^a, T^b] T^c).
+// Re/im pairs, row-major.
+void light_line_colour(double* out) {
+  using C = std::complex<double>;
+  C t[8][3][3] = {};
+  const C i1(0.0, 1.0);
+  t[0][0][1] = t[0][1][0] = 0.5;
+  t[1][0][1] = -0.5 * i1; t[1][1][0] = 0.5 * i1;
+  t[2][0][0] = 0.5; t[2][1][1] = -0.5;
+  t[3][0][2] = t[3][2][0] = 0.5;
+  t[4][0][2] = -0.5 * i1; t[4][2][0] = 0.5 * i1;
+  t[5][1][2] = t[5][2][1] = 0.5;
+  t[6][1][2] = -0.5 * i1; t[6][2][1] = 0.5 * i1;
+  t[7][0][0] = t[7][1][1] = 0.5 / std::sqrt(3.0); t[7][2][2] = -1.0 / std::sqrt(3.0);
+  auto prod = [&](int a, int b, int r, int c) {  // (T^a T^b)_rc
+    C v = 0.0;
+    for (int k = 0; k < 3; ++k) v += t[a][r][k] * t[b][k][c];
+    return v;
+  };
+  double f[8][8][8];
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b)
+      for (int c = 0; c < 8; ++c) {
+        C tr = 0.0;
+        for (int r = 0; r < 3; ++r)
+          for (int s = 0; s < 3; ++s) tr += (prod(a, b, r, s) - prod(b, a, r, s)) * t[c][s][r];
+        f[a][b][c] = (-2.0 * i1 * tr).real();
+      }
+  C acc[25] = {};
+  for (int a = 0; a < 8; ++a)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) {
+            C c[5] = {};
+            for (int b = 0; b < 8; ++b) {
+              c[0] += prod(b, a, j, i) * t[b][k][l];
+              c[1] += prod(a, b, j, i) * t[b][k][l];
+              c[2] += t[b][j][i] * prod(a, b, k, l);
+              c[3] += t[b][j][i] * prod(b, a, k, l);
+              for (int e = 0; e < 8; ++e) c[4] += f[b][e][a] * t[b][j][i] * t[e][k][l];
+            }
+            for (int d = 0; d < 5; ++d)
+              for (int e = 0; e < 5; ++e) acc[d * 5 + e] += c[d] * std::conj(c[e]);
+          }
+  for (int n = 0; n < 25; ++n) {
+    out[2 * n] = acc[n].real();
+    out[2 * n + 1] = acc[n].imag();
+  }
 }
 
 }  // namespace
@@ -320,11 +377,11 @@ int mc::fill_process_args(const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
   if (!itg) return fail(MC_EINVAL, "NULL integrand");
   int dev;
   if (int rc = current_device(&dev)) return rc;
-  if (itg->proc < MC_EE_MUMU || itg->proc > MC_GG_TTBARG_MC) return fail(MC_EINVAL, "unknown process %d", itg->proc);
+  if (itg->proc < MC_EE_MUMU || itg->proc > MC_PP_TTBARJ) return fail(MC_EINVAL, "unknown process %d", itg->proc);
   const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG || itg->proc == MC_GG_TTBARG_7D ||
-                        itg->proc == MC_GG_TTBARG_MC;
-  if (itg->proc == MC_GG_TTBARG_MC && !(itg->ptcut_g > 0.0))
-    return fail(MC_EINVAL, "the three-channel process needs ptcut_g > 0");
+                        itg->proc == MC_GG_TTBARG_MC || itg->proc == MC_PP_TTBARJ;
+  if ((itg->proc == MC_GG_TTBARG_MC || itg->proc == MC_PP_TTBARJ) && !(itg->ptcut_g > 0.0))
+    return fail(MC_EINVAL, "process %d needs ptcut_g > 0", itg->proc);
   if (!(itg->sqrt_s > 0.0) && itg->proc != MC_GAUSS) return fail(MC_EINVAL, "sqrt_s must be positive");
   if (itg->proc == MC_GAUSS && !(itg->gauss_sigma > 0.0)) return fail(MC_EINVAL, "gauss_sigma must be positive");
   std::memset(a, 0, sizeof(*a));
@@ -342,7 +399,18 @@ int mc::fill_process_args(const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
     const int g = pdf->index(21);
     if (g < 0) return fail(MC_EINVAL, "PDF has no gluon (pid 21)");
     a->fl[0] = g;
-    if (itg->proc == MC_PP_TTBAR)
+    if (itg->proc == MC_PP_TTBARJ) {
+      static const std::vector<double> cq = [] {
+        std::vector<double> c(50);
+        light_line_colour(c.data());
+        return c;
+      }();
+      for (int n = 0; n < 50; ++n) {
+        a->cqq[n] = cq[n];
+        a->cqqf[n] = float(cq[n]);
+      }
+    }
+    if (itg->proc == MC_PP_TTBAR || itg->proc == MC_PP_TTBARJ)
       for (int qf = 1; qf <= 5; ++qf) {
         a->fl[qf] = pdf->index(qf);
         a->fl[qf + 5] = pdf->index(-qf);

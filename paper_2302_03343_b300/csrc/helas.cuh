@@ -142,6 +142,27 @@ template <class R> MC_D sp4<R> vbar_spinor(const v4<R>& p, R m, int hel) {
   return {conj(v.r0), conj(v.r1), conj(v.l0), conj(v.l1)};
 }
 
+// Vector current J^mu = rbar gamma^mu c of a barred row spinor and a column
+// spinor (the components of rbar (a-slash) c = J^mu a_mu, read off
+// slash_col): J^0 = L0 r0 + L1 r1 + R0 l0 + R1 l1,
+// J^1 = L0 r1 + L1 r0 - R0 l1 - R1 l0, J^2 = -i (L0 r1 - L1 r0 - R0 l1 + R1 l0),
+// J^3 = L0 r0 - L1 r1 - R0 l0 + R1 l1 (L, R the row's parts, l, r the column's).
+template <class R> MC_D void vector_current(const sp4<R>& b, const sp4<R>& c, cx<R>* j) {
+  const cx<R> a = b.l0 * c.r0, d = b.l1 * c.r1, e = b.r0 * c.l0, f = b.r1 * c.l1;
+  const cx<R> g = b.l0 * c.r1, h = b.l1 * c.r0, k = b.r0 * c.l1, l = b.r1 * c.l0;
+  j[0] = a + d + e + f;
+  j[1] = g + h - k - l;
+  const cx<R> t = g - h - k + l;
+  j[2] = mkc(t.im, -t.re);  // -i t
+  j[3] = a - d - e + f;
+}
+template <class R> MC_D cx<R> cdot4(const cx<R>* a, const cx<R>* b) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+template <class R> MC_D cx<R> cdot4(const cx<R>* a, const v4<R>& b) {
+  return a[0] * b.e - a[1] * b.x - a[2] * b.y - a[3] * b.z;
+}
+
 // Two real transverse polarisation vectors of a massless momentum:
 // eps1 = (0, cos th cos ph, cos th sin ph, -sin th), eps2 = (0, -sin ph, cos ph, 0).
 template <class R> MC_D void linear_polarisations(const v4<R>& k, v4<R>* e1, v4<R>* e2) {

@@ -12,7 +12,9 @@
 
 namespace mc {
 
-enum : int { P_EE_MUMU = 0, P_PP_TTBAR = 1, P_GG_TTBARG = 2, P_GAUSS = 3, P_GG_TTBARG_7D = 4, P_GG_TTBARG_MC = 5 };
+enum : int {
+  P_EE_MUMU = 0, P_PP_TTBAR = 1, P_GG_TTBARG = 2, P_GAUSS = 3, P_GG_TTBARG_7D = 4, P_GG_TTBARG_MC = 5, P_PP_TTBARJ = 6
+};
 
 template <int PROC> struct ProcTraits;
 template <> struct ProcTraits<P_EE_MUMU> { static constexpr int MAXD = 2, NFL = 0; };
@@ -22,6 +24,8 @@ template <> struct ProcTraits<P_GAUSS> { static constexpr int MAXD = 16, NFL = 0
 template <> struct ProcTraits<P_GG_TTBARG_7D> { static constexpr int MAXD = 7, NFL = 1; };
 // three-channel gg -> t tbar g: 7 uniforms per event, 17 grid dimensions
 template <> struct ProcTraits<P_GG_TTBARG_MC> { static constexpr int MAXD = 7, NFL = 1; };
+// p p -> t tbar + parton: 7 dims, gluon and the five quark and antiquark flavours
+template <> struct ProcTraits<P_PP_TTBARJ> { static constexpr int MAXD = 7, NFL = 11; };
 
 // Arguments of one launch of the fused kernel (passed by value).
 struct BlockPartial {
@@ -54,6 +58,10 @@ struct KernelArgs {
   // the probabilities, and the alpha-update sums W_i (device, [3], added to)
   double alpha_cum[3], alpha[3];
   double* wch;
+  // p p -> t tbar + parton: colour matrix of the light-line amplitudes
+  // (me2_qline_ttbarg), re/im pairs, in FP64 and FP32
+  double cqq[50];
+  float cqqf[50];
 };
 
 // Shared-memory PDF tables of a launch.
@@ -238,6 +246,70 @@ MC_D EventOut integrand(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, do
     if (rec) {
       rec_put(rec, 80, kin.lgg);
       rec_put(rec, 82, me2);
+    }
+  } else if constexpr (PROC == P_PP_TTBARJ) {
+    // every partonic channel at one point of the hierarchical three-body
+    // phase space (the light parton massless): gg, q qbar, qbar q, q g, g q,
+    // qbar g, g qbar, luminosities summed over the five light flavours
+    const R x1 = x[0], x2 = x[1];
+    const R m = R(p.m_top);
+    const R shat = sizeof(R) == 4 ? R(x1 * x2 * R(s)) : R(double(x1) * double(x2) * s);
+    rec_put(rec, 77, x1); rec_put(rec, 78, x2); rec_put(rec, 79, shat);
+    if (!(shat > R(4) * m * m)) {
+      out.pass = 0;
+      return out;
+    }
+    const R rs = m_sqrt(shat);
+    v4<double> kd[3];
+    double psw;
+    hierarchical3<R>(double(m), double(rs), x + 2, kd, &psw);
+    GgKin<R> kin;
+    for (int i = 0; i < 3; ++i) kin.k[i] = vcast<R>(kd[i]);
+    kin.rs = rs;
+    const v4<R> pa = {rs * R(0.5), R(0), R(0), rs * R(0.5)}, pb = {rs * R(0.5), R(0), R(0), -rs * R(0.5)};
+    const v4<R>& pt = kin.k[0];
+    const v4<R>& ptb = kin.k[1];
+    const v4<R>& pk = kin.k[2];
+    if (rec) {
+      rec_p4(rec, 0, pa); rec_p4(rec, 1, pb); rec_p4(rec, 2, pt); rec_p4(rec, 3, ptb); rec_p4(rec, 4, pk);
+      rec_put(rec, 84, psw);
+    }
+    // cuts on the light parton in the lab frame
+    const R pt2 = pk.x * pk.x + pk.y * pk.y, ptc = R(p.ptcut_g);
+    const R pabs = m_sqrt(pt2 + pk.z * pk.z);
+    const R fwd = (pabs + pk.z) * x1, bwd = (pabs - pk.z) * x2, e2 = R(a.e2eta);
+    if (!(pt2 > ptc * ptc && fwd < e2 * bwd && bwd < e2 * fwd)) {
+      out.pass = 0;
+      return out;
+    }
+    const R lx1 = m_log(x1), lx2 = m_log(x2);
+    const R g1 = pdf_interp_1d(pdf.tab[0], lx1) / x1, g2x = pdf_interp_1d(pdf.tab[0], lx2) / x2;
+    R q1 = R(0), qb1 = R(0), q2 = R(0), qb2 = R(0), lqq = R(0), lqbq = R(0);
+#pragma unroll
+    for (int f = 1; f <= 5; ++f) {
+      const R a1 = pdf_interp_1d(pdf.tab[f], lx1) / x1, ab1 = pdf_interp_1d(pdf.tab[f + 5], lx1) / x1;
+      const R a2 = pdf_interp_1d(pdf.tab[f], lx2) / x2, ab2 = pdf_interp_1d(pdf.tab[f + 5], lx2) / x2;
+      q1 += a1; qb1 += ab1; q2 += a2; qb2 += ab2;
+      lqq += a1 * ab2;
+      lqbq += ab1 * a2;
+    }
+    const R g2c = R(4.0 * kPi * p.alpha_s);
+    const R* cm;
+    if constexpr (sizeof(R) == 4) cm = a.cqqf; else cm = a.cqq;
+    const R me_gg = gg_me2<R>(a, kin);
+    const R me[6] = {me2_qline_ttbarg<R>(0, pa, pb, pt, ptb, pk, m, g2c, cm),
+                     me2_qline_ttbarg<R>(0, pb, pa, pt, ptb, pk, m, g2c, cm),
+                     me2_qline_ttbarg<R>(1, pa, pb, pt, ptb, pk, m, g2c, cm),
+                     me2_qline_ttbarg<R>(1, pb, pa, pt, ptb, pk, m, g2c, cm),
+                     me2_qline_ttbarg<R>(2, pa, pb, pt, ptb, pk, m, g2c, cm),
+                     me2_qline_ttbarg<R>(2, pb, pa, pt, ptb, pk, m, g2c, cm)};
+    const double sum = double(g1 * g2x) * double(me_gg) + double(lqq) * double(me[0]) + double(lqbq) * double(me[1]) +
+                       double(q1 * g2x) * double(me[2]) + double(g1 * q2) * double(me[3]) +
+                       double(qb1 * g2x) * double(me[4]) + double(g1 * qb2) * double(me[5]);
+    out.f = sum / (2.0 * double(shat)) * psw * p.gev2pb;
+    if (rec) {
+      rec_put(rec, 80, g1 * g2x); rec_put(rec, 81, lqq); rec_put(rec, 82, me_gg); rec_put(rec, 83, me[0]);
+      for (int c = 0; c < 5; ++c) rec_put(rec, 89 + c, me[c + 1]);
     }
   } else {  // Gaussian
     const R sg = R(p.gauss_sigma);

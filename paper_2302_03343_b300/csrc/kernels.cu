@@ -212,6 +212,9 @@ static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, 
     case P_GG_TTBARG_MC:
       return fp64 ? launch_one<P_GG_TTBARG_MC, true, RECORD>(a, grid, smem, st)
                   : launch_one<P_GG_TTBARG_MC, false, RECORD>(a, grid, smem, st);
+    case P_PP_TTBARJ:
+      return fp64 ? launch_one<P_PP_TTBARJ, true, RECORD>(a, grid, smem, st)
+                  : launch_one<P_PP_TTBARJ, false, RECORD>(a, grid, smem, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -219,7 +222,9 @@ static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, 
 size_t integrand_smem(int proc, bool fp64, int ndim, int nbins, int nx) {
   if (integrand_ws(proc, fp64)) return ws_smem_bytes(proc, ndim, nbins, nx);
   const size_t r = fp64 ? 8 : 4;
-  const int nfl = proc == P_PP_TTBAR ? 11 : ((proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_GG_TTBARG_MC) ? 1 : 0);
+  const int nfl = (proc == P_PP_TTBAR || proc == P_PP_TTBARJ)
+                      ? 11
+                      : ((proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_GG_TTBARG_MC) ? 1 : 0);
   const size_t hist = ((size_t(ndim) * nbins * 12 + 15) / 16) * 16;
   return hist + r * (size_t(ndim) * (nbins + 1) + (nfl > 0 ? size_t(nx) * (1 + 2 * nfl) : 0));
 }
@@ -237,6 +242,7 @@ int integrand_max_blocks_per_sm(int proc, bool fp64, size_t smem) {
     case P_GG_TTBARG: MC_OCC(P_GG_TTBARG); break;
     case P_GG_TTBARG_7D: MC_OCC(P_GG_TTBARG_7D); break;
     case P_GG_TTBARG_MC: MC_OCC(P_GG_TTBARG_MC); break;
+    case P_PP_TTBARJ: MC_OCC(P_PP_TTBARJ); break;
     default: MC_OCC(P_GAUSS); break;
   }
 #undef MC_OCC

@@ -289,6 +289,95 @@ MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4
   return g2 * g2 * g2 * total * R(2) / (R(27) * R(256));
 }
 
+// ------------------------------------------ light-quark line -> t tbar g
+// q qbar -> t tbar g and its crossings with a light-quark line and one
+// external gluon, from helicity amplitudes of the five diagrams (emission
+// off the light line before and after the internal gluon, off the top and
+// the anti-top, and off the internal gluon through the three-gluon vertex),
+// with vertices i g gamma T, quark propagators i (pslash + m)/(p^2 - m^2),
+// gluon propagators -i g / k^2 and the three-gluon vertex
+// g f [g (k - p) + g (p - q) + g (q - k)] (momenta incoming).  The light line
+// is the column spinor `col` entering with fermion-flow momentum Pin and the
+// row spinor `row` leaving with Pout; the gluon has outgoing-convention
+// momentum k:
+//   kind 0, q(pa) qbar(pb) -> t tbar g(pk): col u(pa), row vbar(pb), Pin pa,
+//           Pout -pb, k pk, average 1/36;
+//   kind 1, q(pa) g(pb) -> t tbar q(pk): col u(pa), row ubar(pk), Pin pa,
+//           Pout pk, k -pb, average 1/96;
+//   kind 2, qbar(pa) g(pb) -> t tbar qbar(pk): col v(pk), row vbar(pa),
+//           Pin -pk, Pout -pa, k -pb, average 1/96.
+// Colour-stripped amplitudes A_d (d: emission before / after on the light
+// line, off t, off tbar, three-gluon) combine with the colour matrix
+// C_de = sum over colours of c_d c_e^* (Hermitian, complex), passed as
+// re/im pairs: |M|^2 = sum_d C_dd |A_d|^2 + 2 sum_{d<e} Re(C_de A_d A_e^*).
+template <class R>
+MC_D R me2_qline_ttbarg(int kind, const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4<R>& ptb,
+                        const v4<R>& pk, R m, R g2, const R* cmat) {
+  const v4<R> k = kind == 0 ? pk : -pb;
+  const v4<R> kphys = kind == 0 ? pk : pb;
+  const v4<R> pin = kind == 2 ? -pk : pa;
+  const v4<R> pout = kind == 0 ? -pb : (kind == 1 ? pk : -pa);
+  const v4<R> q = pt + ptb, pl = pin - pout;
+  const R iq2 = R(1) / mdot(q, q), ip2 = R(1) / mdot(pl, pl);
+  const v4<R> s1 = pin - k, s2 = pout + k, s3 = pt + k, s4 = -(ptb + k);
+  const R i1 = R(1) / mdot(s1, s1), i2 = R(1) / mdot(s2, s2);
+  const R i3 = R(1) / (mdot(s3, s3) - m * m), i4 = R(1) / (mdot(s4, s4) - m * m);
+  const v4<R> kpq = pl + q, kmq = k - q, mkp = -(k + pl);
+  v4<R> eps[2];
+  linear_polarisations(kphys, &eps[0], &eps[1]);
+  const R g3 = g2 * m_sqrt(g2);
+  R total = R(0);
+#pragma unroll 1
+  for (int h1 = -1; h1 <= 1; h1 += 2) {
+    const sp4<R> col = kind == 2 ? v_spinor(pk, R(0), h1) : u_spinor(pa, R(0), h1);
+#pragma unroll 1
+    for (int h2 = -1; h2 <= 1; h2 += 2) {
+      const sp4<R> row = kind == 0 ? vbar_spinor(pb, R(0), h2)
+                                   : (kind == 1 ? ubar_spinor(pk, R(0), h2) : vbar_spinor(pa, R(0), h2));
+      cx<R> vl[4];
+      vector_current(row, col, vl);
+#pragma unroll 1
+      for (int h3 = -1; h3 <= 1; h3 += 2) {
+        const sp4<R> ut = ubar_spinor(pt, m, h3);
+#pragma unroll 1
+        for (int h4 = -1; h4 <= 1; h4 += 2) {
+          const sp4<R> vt = v_spinor(ptb, m, h4);
+          cx<R> hh[4];
+          vector_current(ut, vt, hh);
+          const cx<R> vlh = cdot4(vl, hh);
+#pragma unroll
+          for (int lam = 0; lam < 2; ++lam) {
+            const v4<R>& e = eps[lam];
+            cx<R> v1[4], v2[4], h3v[4], h4v[4];
+            vector_current(row, prop_col(s1, R(0), i1, slash_col(e, col)), v1);
+            vector_current(prop_row(slash_row(row, e), s2, R(0), i2), col, v2);
+            vector_current(prop_row(slash_row(ut, e), s3, m, i3), vt, h3v);
+            vector_current(ut, prop_col(s4, m, i4, slash_col(e, vt)), h4v);
+            cx<R> amp[5];
+            const cx<R> mi = mkc(R(0), -g3);  // -i g^3
+            amp[0] = mi * (cdot4(v1, hh) * iq2);
+            amp[1] = mi * (cdot4(v2, hh) * iq2);
+            amp[2] = mi * (cdot4(vl, h3v) * ip2);
+            amp[3] = mi * (cdot4(vl, h4v) * ip2);
+            amp[4] = (vlh * mdot(kpq, e) + cdot4(vl, kmq) * cdot4(hh, e) + cdot4(vl, e) * cdot4(hh, mkp)) *
+                     (g3 * ip2 * iq2);
+#pragma unroll
+            for (int d = 0; d < 5; ++d) {
+              total += cmat[2 * (d * 5 + d)] * norm2(amp[d]);
+#pragma unroll
+              for (int f = d + 1; f < 5; ++f) {
+                const cx<R> x = mul_conj(amp[d], amp[f]);  // A_d A_f^*
+                total += R(2) * (cmat[2 * (d * 5 + f)] * x.re - cmat[2 * (d * 5 + f) + 1] * x.im);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  return total / (kind == 0 ? R(36) : R(96));
+}
+
 // Unroll factors of the helicity loops of me2_gg_ttbarg_p (1: a rolled loop,
 // which keeps the consumer warps' register count down).
 #ifndef MC_ME_UNROLL_H0

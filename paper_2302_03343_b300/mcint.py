@@ -17,10 +17,10 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmcint.so
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ENAN, MC_ENOCONV, MC_ETIMEOUT, MC_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 MC_FP64, MC_FP32_KAHAN = 0, 1
-MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS, MC_GG_TTBARG_7D, MC_GG_TTBARG_MC = 0, 1, 2, 3, 4, 5
+MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS, MC_GG_TTBARG_7D, MC_GG_TTBARG_MC, MC_PP_TTBARJ = 0, 1, 2, 3, 4, 5, 6
 MC_MAX_DIM, MC_MAX_BINS = 17, 256
 REC = dict(K=0, X=16, BIN=32, JAC=48, P=49, X1=77, X2=78, SHAT=79, LUMI=80, LUMI_QQ=81, ME2=82, ME2_QQ=83,
-           PSW=84, F=85, W=86, PASS=87, STATUS=88, CHANNEL=89, DENS=90)
+           PSW=84, F=85, W=86, PASS=87, STATUS=88, CHANNEL=89, DENS=90, ME2_X=89)
 REC_STRIDE = 96
 
 # exported symbols (each declared in include/mcint.h)
