@@ -23,7 +23,8 @@ tab:fktable (400 members, 11 flavours, 2415 x points) against HBM; and
 pass, device-side acceptance-rejection and export of the accepted events,
 and the native LHE writer's throughput on them); and "samplers": RAMBO, the
 hierarchical generator and three-channel sampling side by side (time per
-iteration, variance per event, unweighting efficiency).
+iteration, variance per event, unweighting efficiency); and "pp_ttbarj": the
+higher-multiplicity process p p -> t tbar + parton (all partonic channels).
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a
 bounded sample of events per step on the host cores).
@@ -400,6 +401,29 @@ def samplers(M, pdf, stream, iterations=10):
     return out
 
 
+def pp_ttbarj(M, pdf, stream, iterations=6):
+    """p p -> t tbar + parton at LO (gg -> t tbar g and the six light-quark
+    channels at every point; hierarchical phase space, 7 dims), FP32, 1e7
+    events per iteration from a uniform grid: kernel time per iteration
+    (median of the last 3), events per second, and the combined cross
+    section of the last 3 iterations."""
+    itg = W.pp_ttbarj()
+    v = M.mc_vegas_init(7, NBINS, 3000, M.MC_FP32_KAHAN)
+    ms, res = [], []
+    for i in range(iterations):
+        r = M.mc_vegas_iterate(v, itg, pdf, EVENTS, stream)
+        M.mc_vegas_refine(v, ALPHA, stream)
+        if i >= iterations - 3:
+            ms.append(M.mc_vegas_kernel_ms(v))
+            res.append(_iter_stats(r))
+    v.free()
+    mean, sig = _combine(res)
+    kms = statistics.median(ms)
+    return {"workload": "p p -> t tbar + parton, 13 TeV, parton pT > 20 GeV |eta| < 2.5, hierarchical 2->3, FP32, "
+                        "1e7 events per iteration", "kernel_ms": kms, "events_per_s": EVENTS / (kms / 1e3),
+            "xsec_pb": mean, "xsec_rel_err": sig / mean, "events_in_cuts": r.n_nonzero}
+
+
 def profile_case(case):
     """A small fixed workload for ncu captures (no timing output)."""
     import torch
@@ -647,6 +671,7 @@ def run_native(args, rank, world):
         line["pdf_members"] = pdf_members(M, stream)
         line["unweighting"] = unweighting(M, pdf, stream, M.mc_vegas_get_grid(v), mean_kernel_ms)
         line["samplers"] = samplers(M, pdf, stream)
+        line["pp_ttbarj"] = pp_ttbarj(M, pdf, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
