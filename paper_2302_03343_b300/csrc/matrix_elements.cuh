@@ -332,6 +332,9 @@ MC_D R me2_qline_ttbarg(int kind, const v4<R>& pa, const v4<R>& pb, const v4<R>&
     const sp4<R> col = kind == 2 ? v_spinor(pk, R(0), h1) : u_spinor(pa, R(0), h1);
 #pragma unroll 1
     for (int h2 = -1; h2 <= 1; h2 += 2) {
+      // a massless line keeps its chirality through an odd number of gamma
+      // matrices: u(+) pairs with vbar(-) and ubar(+), v(+) with vbar(+)
+      if (kind == 0 ? h2 == h1 : h2 != h1) continue;
       const sp4<R> row = kind == 0 ? vbar_spinor(pb, R(0), h2)
                                    : (kind == 1 ? ubar_spinor(pk, R(0), h2) : vbar_spinor(pa, R(0), h2));
       cx<R> vl[4];
