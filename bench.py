@@ -64,6 +64,12 @@ FLOP_PER_EVENT = 22434.0
 # writes histograms and per-block partials.
 TRAFFIC_BYTES = 3088128
 FP32_LANES_PER_SM = 128
+# FP32 FLOP per FP32 lane operation of that launch: its ncu counts give
+# 2 ffma + fmul + fadd + 4 ffma2 + 2 fmul2 + 2 fadd2 = 1.807e11 FLOP over
+# ffma + fmul + fadd + 2 (ffma2 + fmul2 + fadd2) = 1.102e11 lane operations;
+# a multiply or an add alone does one FLOP in a slot that could do two, so
+# the kernel's mix caps it at this fraction of the FMA peak.
+FLOP_PER_LANE_OP = 1.807e11 / 1.102e11
 # time to a target relative error (gg -> t tbar g, 7 sampled dimensions):
 # FP32 + normalizing flow (6 coupling layers, 32 bins, 3 x 256 BF16 hidden
 # units, Adam lr 1e-3, 200 training steps of 65536 events, then 1e7 events per
@@ -642,7 +648,10 @@ def run_native(args, rank, world):
         achieved = FLOP_PER_EVENT * mean_nnz / (mean_kernel_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": TRAFFIC_BYTES,
-                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz"}
+                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                "frac_of_mix_bound": achieved / (fp32_peak * FLOP_PER_LANE_OP / 2.0),
+                "mix_bound_note": "the same peak times the kernel's FLOP per FP32 lane operation / 2 "
+                                  f"({FLOP_PER_LANE_OP:.3f} / 2): the rate if every lane slot issued its mix"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "note": "FLOP/event not yet counted"}
