@@ -442,6 +442,15 @@ def profile_case(case):
         for _ in range(3):
             M.mc_vegas_iterate(v, W.gg_ttbarg(), pdf, 1 << 20)
             M.mc_vegas_refine(v, ALPHA)
+    elif case in ("mc", "ppttj"):  # three-channel gg -> ttg, or p p -> t tbar + parton: 3 iterations of 2^20
+        itg = W.gg_ttbarg_mc() if case == "mc" else W.pp_ttbarj()
+        v = M.mc_vegas_init(itg.ndim(), NBINS, 0, M.MC_FP32_KAHAN)
+        for _ in range(3):
+            M.mc_vegas_iterate(v, itg, pdf, 1 << 20)
+            if case == "mc":
+                a, w = M.mc_vegas_get_channels(v)
+                M.mc_vegas_set_channels(v, M.mc_channel_update(a, w, 0.5, 0.02))
+            M.mc_vegas_refine(v, ALPHA)
     elif case == "unweight":  # weights pass and unweighting of 2^24 events (134 MB of weights > L2)
         n = 1 << 24
         itg = W.gg_ttbarg()
@@ -695,7 +704,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-target", action="store_true")
-    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdfset", "unweight"], default=None,
+    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdfset", "unweight", "mc", "ppttj"], default=None,
                     help="run a small fixed workload for profiling and exit")
     args = ap.parse_args()
     if args.profile_case:
