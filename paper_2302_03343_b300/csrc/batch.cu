@@ -148,11 +148,15 @@ __global__ void __launch_bounds__(BLOCK) batch_kernel(BatchArgs b) {
   if (cur >= 0) flush(cur);
 }
 
-// FP32 batch kernel with the warp-specialised path for gg -> t tbar g tiles.
+// FP32 batch kernel with the warp-specialised path for gg -> t tbar g tiles
+// (both processes share the ring of P_GG_TTBARG: 23 words, ws_slots slots).
 __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kWsSlots], empty[kWsSlots];
-  __shared__ int count[kWsSlots];
+  constexpr int kSlots = ws_slots(P_GG_TTBARG) * kWsProducerWarps;
+  static_assert(ws_slots(P_GG_TTBARG) == ws_slots(P_GG_TTBARG_7D) && ws_words(P_GG_TTBARG) == ws_words(P_GG_TTBARG_7D),
+                "the two processes share one ring");
+  __shared__ __align__(8) uint64_t full[kSlots], empty[kSlots];
+  __shared__ int count[kSlots];
   __shared__ int failed;
   __shared__ KernelArgs ka;
   __shared__ int sh_tile;
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
   const int nb = b.nbins;
   const int nhist = MC_MAX_DIM * nb, nedge = MC_MAX_DIM * (nb + 1);
   const WsRing ring = {reinterpret_cast<uint32_t*>(smem), full, empty, count};
-  unsigned char* rest = smem + size_t(kWsSlots) * ws_words(P_GG_TTBARG) * 32 * 4;
+  unsigned char* rest = smem + size_t(kSlots) * ws_words(P_GG_TTBARG) * 32 * 4;
   float* sh_w2 = reinterpret_cast<float*>(rest);
   unsigned int* sh_n = reinterpret_cast<unsigned int*>(rest + size_t(nhist) * 4);
   float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
     sh_n[i] = 0u;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWsSlots; ++s) {
+    for (int s = 0; s < kSlots; ++s) {
       mbar_init(&full[s], 32);
       mbar_init(&empty[s], 32);
     }
@@ -242,8 +246,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
       } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
         const int c = warp - kWsProducerWarps;
-        ok = it.proc == P_GG_TTBARG ? ws_consume<P_GG_TTBARG, false>(ka, sh_w2, ring, c, q0, q1, acc)
-                                    : ws_consume<P_GG_TTBARG_7D, false>(ka, sh_w2, ring, c, q0, q1, acc);
+        ok = it.proc == P_GG_TTBARG ? ws_consume<P_GG_TTBARG, false>(ka, sh_w2, ring, NoRows{}, c, q0, q1, acc)
+                                    : ws_consume<P_GG_TTBARG_7D, false>(ka, sh_w2, ring, NoRows{}, c, q0, q1, acc);
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
       }
     } else {
@@ -449,8 +453,9 @@ int build_tiles(mc_batch b) {
   b->smem = ((nhist * 12 + 15) / 16) * 16 + r * (size_t(MC_MAX_DIM) * (b->nbins + 1)) +
             (b->pdf ? r * size_t(b->pdf->nx) * 23 : 0);
   if (b->ws)
-    b->smem = size_t(mc::kWsSlots) * mc::ws_words(mc::P_GG_TTBARG) * 32 * 4 + ((nhist * 8 + 15) / 16) * 16 +
-              4 * (size_t(MC_MAX_DIM) * (b->nbins + 1)) + (b->pdf ? 4 * size_t(b->pdf->nx) * 23 : 0);
+    b->smem = size_t(mc::ws_slots(mc::P_GG_TTBARG)) * mc::kWsProducerWarps * mc::ws_words(mc::P_GG_TTBARG) * 32 * 4 +
+              ((nhist * 8 + 15) / 16) * 16 + 4 * (size_t(MC_MAX_DIM) * (b->nbins + 1)) +
+              (b->pdf ? 4 * size_t(b->pdf->nx) * 23 : 0);
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   const int per_sm = b->ws ? 1 : mc::batch_blocks_per_sm(fp64, b->block, b->smem);

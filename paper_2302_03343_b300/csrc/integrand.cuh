@@ -158,16 +158,21 @@ MC_D int gg_kinematics(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, GgK
 }
 
 // |M|^2 of an event that passed the cuts: packed FP32x2 arithmetic in FP32
-// mode, the precision-generic routine in FP64 mode.
-template <class R>
-MC_D R gg_me2(const KernelArgs& a, const GgKin<R>& kin) {
+// mode (me2_gg_ttbarg_rows with a shared-memory row store, me2_gg_ttbarg_p
+// without), the precision-generic routine in FP64 mode.
+template <class R, class Rows = NoRows>
+MC_D R gg_me2(const KernelArgs& a, const GgKin<R>& kin, Rows rows = Rows{}) {
   const R h = kin.rs * R(0.5);
   const v4<R> pa = {h, R(0), R(0), h}, pb = {h, R(0), R(0), -h};
   const R m = R(a.prm.m_top), g2 = R(4.0 * kPi * a.prm.alpha_s);
-  if constexpr (sizeof(R) == 4)
-    return me2_gg_ttbarg_p(pa, pb, kin.k[0], kin.k[1], kin.k[2], m, g2);
-  else
+  if constexpr (sizeof(R) == 4) {
+    if constexpr (std::is_same<Rows, NoRows>::value)
+      return me2_gg_ttbarg_p(pa, pb, kin.k[0], kin.k[1], kin.k[2], m, g2);
+    else
+      return me2_gg_ttbarg_rows(pa, pb, kin.k[0], kin.k[1], kin.k[2], m, g2, rows);
+  } else {
     return me2_gg_ttbarg<R>(pa, pb, kin.k[0], kin.k[1], kin.k[2], m, g2);
+  }
 }
 
 // f = L_gg <|M|^2> / (2 shat) * w_PS * gev2pb (the VEGAS Jacobian is applied

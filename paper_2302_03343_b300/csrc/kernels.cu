@@ -171,8 +171,10 @@ static cudaError_t launch_one(const KernelArgs& a, int grid, size_t smem, cudaSt
 
 template <int PROC>
 static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
-  auto k = a.wout ? ws_integrand_kernel<PROC, true> : ws_integrand_kernel<PROC, false>;
-  const size_t smem = ws_smem_bytes(PROC, a.ndim, a.nbins, a.pdf.nx);
+  const bool rows = ws_rows_in_smem(PROC, a.ndim, a.nbins, a.pdf.nx);
+  auto k = a.wout ? (rows ? ws_integrand_kernel<PROC, true, true> : ws_integrand_kernel<PROC, true, false>)
+                  : (rows ? ws_integrand_kernel<PROC, false, true> : ws_integrand_kernel<PROC, false, false>);
+  const size_t smem = ws_smem_bytes(PROC, a.ndim, a.nbins, a.pdf.nx, rows);
   (void)cudaGetLastError();
   const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;

@@ -4,6 +4,8 @@
 // pp -> tt diagrams).  All functions return the spin- and colour-averaged
 // |M|^2 for momenta in the partonic centre-of-mass frame.
 #pragma once
+#include <type_traits>
+
 #include "helas.cuh"
 #include "packed.cuh"
 
@@ -392,6 +394,28 @@ MC_D R me2_qline_ttbarg(int kind, const v4<R>& pa, const v4<R>& pb, const v4<R>&
 #define MC_UNROLL_(n) MC_PRAGMA(unroll n)
 #define MC_UNROLL(n) MC_UNROLL_(n)
 
+// Products used by me2_gg_ttbarg_p.  A gluon's linear polarisation vector
+// has no time component and is orthogonal to the gluon's momentum.
+// a . T for a real four-vector a and a complex one T (packed components)
+MC_D f2 rdot_c(const v4<float>& a, const f2* T) {
+  return fma2(bc2(a.e), T[0], fma2(bc2(-a.x), T[1], fma2(bc2(-a.y), T[2], mul2(bc2(-a.z), T[3]))));
+}
+// the same for a polarisation vector e (e^0 = 0)
+MC_D f2 pdot_c(const v4<float>& e, const f2* T) {
+  return fma2(bc2(-e.x), T[1], fma2(bc2(-e.y), T[2], mul2(bc2(-e.z), T[3])));
+}
+// a . e for a polarisation vector e
+MC_D float pdot(const v4<float>& a, const v4<float>& e) { return -(a.x * e.x + a.y * e.y + a.z * e.z); }
+// The pair current gluon_current(ea, qa, eb, qb, inv) of two external gluons:
+// with ea . qa = eb . qb = 0 the vertex reduces to
+// (ea . eb)(qa - qb) + 2 (ea . qb) eb - 2 (eb . qa) ea.
+MC_D v4<float> pair_current(const v4<float>& ea, const v4<float>& eb, const v4<float>& dq, float eaqb, float ebqa,
+                            float inv) {
+  const float c1 = -inv * pdot(ea, eb), c2 = -2.0f * inv * eaqb, c3 = 2.0f * inv * ebqa;
+  return {c1 * dq.e, c1 * dq.x + c2 * eb.x + c3 * ea.x, c1 * dq.y + c2 * eb.y + c3 * ea.y,
+          c1 * dq.z + c2 * eb.z + c3 * ea.z};
+}
+
 // FP32 gg -> t tbar g with packed (re, im) complex arithmetic: the same
 // colour-ordered amplitudes as me2_gg_ttbarg, regrouped per ordering (abc):
 //   Gamma(abc) v = eps_a S_a [eps_b X_c - J(bc) v] - J(ab) X_c + J(abc) v,
@@ -505,6 +529,200 @@ MC_D float me2_gg_ttbarg_p(const v4<float>& pa, const v4<float>& pb, const v4<fl
                           fma2(bc2(-j021.y), T[ht][2], mul2(bc2(-j021.z), T[ht][3]))));
             const f2 wc = fma2(bc2(j102.e), T[ht][0], fma2(bc2(-j102.x), T[ht][1],
                           fma2(bc2(-j102.y), T[ht][2], mul2(bc2(-j102.z), T[ht][3]))));
+            amp[ht][0] = add2(amp[ht][0], wa);
+            amp[ht][5] = add2(amp[ht][5], wa);
+            amp[ht][1] = add2(amp[ht][1], wb);
+            amp[ht][3] = add2(amp[ht][3], wb);
+            amp[ht][2] = add2(amp[ht][2], wc);
+            amp[ht][4] = add2(amp[ht][4], wc);
+          }
+        }
+#pragma unroll
+        for (int ht = 0; ht < 2; ++ht) {
+#pragma unroll
+          for (int s = 0; s < 6; ++s) {
+            f2 c = mul2(bc2(kColour3[s * 6 + s]), amp[ht][s]);
+#pragma unroll
+            for (int t = s + 1; t < 6; ++t) c = fma2(bc2(2.0f * kColour3[s * 6 + t]), amp[ht][t], c);
+            if (ht == 0)
+              total0 = fma2(amp[ht][s], c, total0);
+            else
+              total1 = fma2(amp[ht][s], c, total1);
+          }
+        }
+      }
+    }
+  }
+  const f2 total = add2(total0, total1);
+  return g2 * g2 * g2 * (lo2(total) + hi2(total)) * 2.0f / (27.0f * 256.0f);
+}
+
+// The same |M|^2 as me2_gg_ttbarg_p with fewer operations and more per-event
+// state, for a kernel that can hold that state in shared memory:
+//   ubar Gamma(abc) v = R(a) [eps_b X_c - J(bc) v] - ubar J(ab) X_c + J(abc) . T,
+// with the row spinors R(a) = ubar eps_a S_a and the column spinors
+// X_c = S_{pair != c} eps_c v, T^mu = ubar gamma^mu v.  The twelve rows
+// R(a, h_a, s_t) depend on one gluon's polarisation only: they are formed
+// once per event, kept in the row store (index (2a + h_a) 2 + s_t) and read
+// back in the helicity loops, which then cost one slash and two products per
+// ordering instead of two slashes, a propagator and two products.
+// The triple currents enter only through J(abc) . T.  Each is a sum of two
+// three-gluon vertices and a contact term, all bilinear in the currents they
+// join, so J(abc) . T is assembled from scalar products instead of the
+// four-vector: with V(x, qx, y, qy) = (x.y)(qx - qy) + y (x.(qx + 2 qy))
+// - x (y.(2 qx + qy)) (the vertex of gluon_current without -1/Q^2),
+//   V . T = (x.y)((qx - qy).T) + (y.T)(x.(qx + 2 qy)) - (x.T)(y.(2 qx + qy)),
+// and V(-x, ...) = -V(x, ...) lets the three orderings share four vertices:
+//   J(012) = -[V(j01, q01, e2, q2) + V(e0, q0, j12, q12)]/Q^2 + C(0, 1, 2),
+//   J(021) = -[V(j02, q02, e1, q1) - V(e0, q0, j12, q12)]/Q^2 + C(0, 2, 1),
+//   J(102) = -[-V(j01, q01, e2, q2) + V(e1, q1, j02, q02)]/Q^2 + C(1, 0, 2),
+// with the contact terms C(x, y, z) = [2 (x.z) y - (y.z) x - (x.y) z]/Q^2
+// (gluon_contact) and Q the sum of the three gluon momenta.
+template <class Rows>
+MC_D float me2_gg_ttbarg_rows(const v4<float>& pa, const v4<float>& pb, const v4<float>& pt, const v4<float>& ptb,
+                           const v4<float>& pg, float m, float g2, Rows rows) {
+  const v4<float> q[3] = {pa, pb, -pg};
+  v4<float> eps[3][2];
+  linear_polarisations(pa, &eps[0][0], &eps[0][1]);
+  linear_polarisations(pb, &eps[1][0], &eps[1][1]);
+  linear_polarisations(pg, &eps[2][0], &eps[2][1]);
+  const sp4<float> ub[2] = {ubar_spinor(pt, m, -1), ubar_spinor(pt, m, +1)};
+  const sp4p v = to_p(v_spinor(ptb, m, +1));
+  sv kc[3];
+  float mc_[3];
+#pragma unroll 1
+  for (int a = 0; a < 3; ++a) {
+    const v4<float> k1 = pt - q[a];
+    const float i1 = 1.0f / (mdot(k1, k1) - m * m);
+    const sv ka = make_sv(k1, i1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const sv e = make_sv(eps[a][h]);
+#pragma unroll
+      for (int ht = 0; ht < 2; ++ht) rows.put((2 * a + h) * 2 + ht, prop_rowp(slash_rowp(to_p(ub[ht]), e), ka, m * i1));
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const v4<float> k2 = q[a] - ptb;
+    const float i2 = 1.0f / (mdot(k2, k2) - m * m);
+    kc[a] = make_sv(k2, i2);
+    mc_[a] = m * i2;
+  }
+  const v4<float> q01 = q[0] + q[1], q02 = q[0] + q[2], q12 = q[1] + q[2];
+  const float i01 = 1.0f / mdot(q01, q01), i02 = 1.0f / mdot(q02, q02), i12 = 1.0f / mdot(q12, q12);
+  const v4<float> qall = q01 + q[2];
+  const float iall = 1.0f / mdot(qall, qall);
+  const v4<float> d01 = q[0] - q[1], d02 = q[0] - q[2], d12 = q[1] - q[2];
+  // T[ht][mu] = ubar gamma^mu v / Q^2, gamma^0 = slash(1,0,0,0), gamma^k = slash(-e_k)
+  f2 T[2][4];
+  {
+    const sp4p g0 = slash_colp(make_sv(v4<float>{iall, 0.0f, 0.0f, 0.0f}), v);
+    const sp4p g1 = slash_colp(make_sv(v4<float>{0.0f, -iall, 0.0f, 0.0f}), v);
+    const sp4p g2v = slash_colp(make_sv(v4<float>{0.0f, 0.0f, -iall, 0.0f}), v);
+    const sp4p g3 = slash_colp(make_sv(v4<float>{0.0f, 0.0f, 0.0f, -iall}), v);
+#pragma unroll
+    for (int ht = 0; ht < 2; ++ht) {
+      T[ht][0] = dotp(ub[ht], g0);
+      T[ht][1] = dotp(ub[ht], g1);
+      T[ht][2] = dotp(ub[ht], g2v);
+      T[ht][3] = dotp(ub[ht], g3);
+    }
+  }
+  // (qx - qy) . T of the vertices V1 = V(j01, q01, e2, q2), V2 = V(e0, q0, j12, q12),
+  // V3 = V(j02, q02, e1, q1) and V4 = V(e1, q1, j02, q02) (the last is -DT[.][2])
+  f2 DT[2][3];
+#pragma unroll
+  for (int ht = 0; ht < 2; ++ht) {
+    DT[ht][0] = rdot_c(q01 - q[2], T[ht]);
+    DT[ht][1] = rdot_c(q[0] - q12, T[ht]);
+    DT[ht][2] = rdot_c(q02 - q[1], T[ht]);
+  }
+  const v4<float> A1 = q01 + q[2] * 2.0f, B2 = q[0] * 2.0f + q12, A3 = q02 + q[1] * 2.0f, B4 = q[1] * 2.0f + q02;
+  f2 total0 = bc2(0.0f), total1 = bc2(0.0f);
+  MC_UNROLL(MC_ME_UNROLL_H0)
+  for (int h0 = 0; h0 < 2; ++h0) {
+    const v4<float> e0 = eps[0][h0];
+    const sp4p x0 = prop_colp(kc[0], mc_[0], slash_colp(make_sv(e0), v));
+    const float e0q1 = pdot(q[1], e0), e0q2 = pdot(q[2], e0);
+    const float e0A2 = 2.0f * pdot(q12, e0);  // e0 . (q0 + 2 q12)
+    const f2 e0T[2] = {pdot_c(e0, T[0]), pdot_c(e0, T[1])};
+    MC_UNROLL(MC_ME_UNROLL_H1)
+    for (int h1 = 0; h1 < 2; ++h1) {
+      const v4<float> e1 = eps[1][h1];
+      const sp4p x1 = prop_colp(kc[1], mc_[1], slash_colp(make_sv(e1), v));
+      const float e1q2 = pdot(q[2], e1);
+      const float e1B3 = 2.0f * pdot(q02, e1);  // e1 . (2 q02 + q1) = e1 . (q1 + 2 q02)
+      const float e0e1 = pdot(e0, e1);
+      const v4<float> j01 = pair_current(e0, e1, d01, e0q1, pdot(q[0], e1), i01);
+      const sp4p u01 = slash_colp(make_sv(j01), v);
+      const float j01A1 = mdot(j01, A1);
+      const f2 j01T[2] = {rdot_c(j01, T[0]), rdot_c(j01, T[1])};
+      const f2 e1T[2] = {pdot_c(e1, T[0]), pdot_c(e1, T[1])};
+      MC_UNROLL(MC_ME_UNROLL_H2)
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const v4<float> e2 = eps[2][h2];
+        const float e2q0 = pdot(q[0], e2), e2q1 = pdot(q[1], e2);
+        const v4<float> j02 = pair_current(e0, e2, d02, e0q2, e2q0, i02);
+        const v4<float> j12 = pair_current(e1, e2, d12, e1q2, e2q1, i12);
+        const sp4p x2 = prop_colp(kc[2], mc_[2], slash_colp(make_sv(e2), v));
+        f2 amp[2][6];
+        // orderings 012 021 102 120 201 210: (a, b, c) with the row of a
+        // times eps_b X_c -/+ J(bc) v
+#define MC_PUT2(S0, S1, A, HA, COL0, COL1)                           \
+  {                                                                 \
+    const sp4p r0_ = rows.get((2 * A + HA) * 2 + 0);                \
+    const sp4p r1_ = rows.get((2 * A + HA) * 2 + 1);                \
+    const sp4p c0_ = COL0;                                          \
+    amp[0][S0] = dotpp(r0_, c0_);                                   \
+    amp[1][S0] = dotpp(r1_, c0_);                                   \
+    const sp4p c1_ = COL1;                                          \
+    amp[0][S1] = dotpp(r0_, c1_);                                   \
+    amp[1][S1] = dotpp(r1_, c1_);                                   \
+  }
+        {
+          const sp4p u12 = slash_colp(make_sv(j12), v);
+          MC_PUT2(0, 1, 0, h0, slash_colp(make_sv(e1), x2) - u12, slash_colp(make_sv(e2), x1) + u12)
+        }
+        {
+          const sp4p u02 = slash_colp(make_sv(j02), v);
+          MC_PUT2(2, 3, 1, h1, slash_colp(make_sv(e0), x2) - u02, slash_colp(make_sv(e2), x0) + u02)
+        }
+        MC_PUT2(4, 5, 2, h2, slash_colp(make_sv(e0), x1) - u01, slash_colp(make_sv(e1), x0) + u01)
+#undef MC_PUT2
+        // -J(ab) X_c, with J(ba) = -J(ab)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const sp4p y = c == 2 ? slash_colp(make_sv(j01), x2) : (c == 1 ? slash_colp(make_sv(j02), x1)
+                                                                         : slash_colp(make_sv(j12), x0));
+          const int sm = c == 2 ? 0 : (c == 1 ? 1 : 3), sp = c == 2 ? 2 : (c == 1 ? 4 : 5);
+#pragma unroll
+          for (int ht = 0; ht < 2; ++ht) {
+            const f2 d = dotp(ub[ht], y);
+            amp[ht][sm] = sub2(amp[ht][sm], d);
+            amp[ht][sp] = add2(amp[ht][sp], d);
+          }
+        }
+        // J(abc) v contracted with ubar: J(abc) . T ; J(012) = J(210), J(021) = J(120), J(102) = J(201)
+        {
+          const float j01e2 = pdot(j01, e2), e0j12 = pdot(j12, e0), j12B2 = mdot(j12, B2);
+          const float j02e1 = pdot(j02, e1), j02A3 = mdot(j02, A3), j02B4 = mdot(j02, B4);
+          const float e2B1 = 2.0f * (e2q0 + e2q1);  // e2 . (2 q01 + q2)
+          const float e0e2 = pdot(e0, e2), e1e2 = pdot(e1, e2);
+#pragma unroll
+          for (int ht = 0; ht < 2; ++ht) {
+            const f2 e2T = pdot_c(e2, T[ht]), j12T = rdot_c(j12, T[ht]), j02T = rdot_c(j02, T[ht]);
+            const f2 v1 = fma2(bc2(j01e2), DT[ht][0], fma2(bc2(j01A1), e2T, mul2(bc2(-e2B1), j01T[ht])));
+            const f2 v2 = fma2(bc2(e0j12), DT[ht][1], fma2(bc2(e0A2), j12T, mul2(bc2(-j12B2), e0T[ht])));
+            const f2 v3 = fma2(bc2(j02e1), DT[ht][2], fma2(bc2(j02A3), e1T[ht], mul2(bc2(-e1B3), j02T)));
+            const f2 v4_ = fma2(bc2(-j02e1), DT[ht][2], fma2(bc2(e1B3), j02T, mul2(bc2(-j02B4), e1T[ht])));
+            // contact terms: with P0 = -(e1.e2) e0T, P1 = -(e0.e2) e1T, P2 = -(e0.e1) e2T
+            // and S = P0 + P1 + P2: C(012) = S - 3 P1, C(021) = S - 3 P2, C(102) = S - 3 P0
+            const f2 p0 = mul2(bc2(-e1e2), e0T[ht]), p1 = mul2(bc2(-e0e2), e1T[ht]), p2 = mul2(bc2(-e0e1), e2T);
+            const f2 sc = add2(add2(p0, p1), p2);
+            const f2 wa = sub2(fma2(bc2(-3.0f), p1, sc), add2(v1, v2));
+            const f2 wb = add2(fma2(bc2(-3.0f), p2, sc), sub2(v2, v3));
+            const f2 wc = add2(fma2(bc2(-3.0f), p0, sc), sub2(v1, v4_));
             amp[ht][0] = add2(amp[ht][0], wa);
             amp[ht][5] = add2(amp[ht][5], wa);
             amp[ht][1] = add2(amp[ht][1], wb);

@@ -99,6 +99,28 @@ MC_D sp4p prop_colp(const sv& k, float m, const sp4p& p) {
   return o;
 }
 
+// Row spinor times (a-slash): (b aslash).L = b.R (a.sigmabar),
+// (b aslash).R = b.L (a.sigma), with the same prepared vector as slash_colp.
+MC_D sp4p slash_rowp(const sp4p& b, const sv& a) {
+  const f2 N = swp2(a.P);
+  sp4p o;
+  o.l0 = fma2(N, swp2(b.r1), fma2(bc2(a.x), b.r1, mul2(bc2(a.D), b.r0)));
+  o.l1 = fma2(a.P, swp2(b.r0), fma2(bc2(a.x), b.r0, mul2(bc2(a.A), b.r1)));
+  o.r0 = fma2(a.P, swp2(b.l1), fma2(bc2(-a.x), b.l1, mul2(bc2(a.A), b.l0)));
+  o.r1 = fma2(N, swp2(b.l0), fma2(bc2(-a.x), b.l0, mul2(bc2(a.D), b.l1)));
+  return o;
+}
+// b (k-slash + m) for a row spinor, the denominator folded as in prop_colp
+MC_D sp4p prop_rowp(const sp4p& b, const sv& k, float m) {
+  const f2 N = swp2(k.P);
+  sp4p o;
+  o.l0 = fma2(N, swp2(b.r1), fma2(bc2(k.x), b.r1, fma2(bc2(k.D), b.r0, mul2(bc2(m), b.l0))));
+  o.l1 = fma2(k.P, swp2(b.r0), fma2(bc2(k.x), b.r0, fma2(bc2(k.A), b.r1, mul2(bc2(m), b.l1))));
+  o.r0 = fma2(k.P, swp2(b.l1), fma2(bc2(-k.x), b.l1, fma2(bc2(k.A), b.l0, mul2(bc2(m), b.r0))));
+  o.r1 = fma2(N, swp2(b.l0), fma2(bc2(-k.x), b.l0, fma2(bc2(k.D), b.l1, mul2(bc2(m), b.r1))));
+  return o;
+}
+
 // bar . col for a barred row spinor with scalar parts: the real parts of the
 // row times col plus the imaginary parts times swap(col), combined with the
 // sign pair (-1, 1) at the end.
@@ -113,5 +135,42 @@ MC_D f2 dotp(const sp4<float>& b, const sp4p& c) {
   ia = fma2(bc2(b.r1.im), swp2(c.r1), ia);
   return fma2(pk2(-1.0f, 1.0f), ia, ra);
 }
+
+// The same product for a packed row spinor.
+MC_D f2 dotpp(const sp4p& b, const sp4p& c) {
+  f2 ra = mul2(bc2(lo2(b.l0)), c.l0);
+  f2 ia = mul2(bc2(hi2(b.l0)), swp2(c.l0));
+  ra = fma2(bc2(lo2(b.l1)), c.l1, ra);
+  ia = fma2(bc2(hi2(b.l1)), swp2(c.l1), ia);
+  ra = fma2(bc2(lo2(b.r0)), c.r0, ra);
+  ia = fma2(bc2(hi2(b.r0)), swp2(c.r0), ia);
+  ra = fma2(bc2(lo2(b.r1)), c.r1, ra);
+  ia = fma2(bc2(hi2(b.r1)), swp2(c.r1), ia);
+  return fma2(pk2(-1.0f, 1.0f), ia, ra);
+}
+
+// Stores of packed row spinors that an amplitude routine forms once per
+// event and reads back inside its helicity loops.  Row i is the pair of
+// 16-byte words 2i, 2i + 1 ((l0, l1) and (r0, r1)).
+// In shared memory: word j of this thread at byte base + j * step, so that
+// with step = 16 x (threads sharing the array) and consecutive threads at
+// consecutive 16-byte offsets a warp's access covers one contiguous 512 bytes.
+struct SmemRows {
+  uint32_t base, step;
+  MC_D void put(int i, const sp4p& r) const {
+    const uint32_t ad = base + uint32_t(2 * i) * step;
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(ad), "l"(r.l0.v), "l"(r.l1.v) : "memory");
+    asm volatile("st.shared.v2.u64 [%0], {%1, %2};" ::"r"(ad + step), "l"(r.r0.v), "l"(r.r1.v) : "memory");
+  }
+  MC_D sp4p get(int i) const {
+    const uint32_t ad = base + uint32_t(2 * i) * step;
+    sp4p r;
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(r.l0.v), "=l"(r.l1.v) : "r"(ad));
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%2];" : "=l"(r.r0.v), "=l"(r.r1.v) : "r"(ad + step));
+    return r;
+  }
+};
+// No store: the routine forms each row where it is used.
+struct NoRows {};
 
 }  // namespace mc

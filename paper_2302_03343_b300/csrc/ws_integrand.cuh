@@ -19,7 +19,7 @@
 //    shared-memory histogram of w^2.
 // Slots pass between the roles through mbarriers (full: 32 producer-lane
 // arrivals; empty: 32 consumer-lane arrivals).  Producer warp p owns the
-// slots 4p .. 4p+3, used in turn; with equal counts consumer warp c takes
+// slots Sp .. Sp + S - 1 (S = ws_slots(process)), used in turn; with equal counts consumer warp c takes
 // producer c's slots (the general mapping is below).  The assignment of
 // events to lanes is fixed by the launch shape, so the sums are
 // deterministic for a given grid.  A producer ends its stream with a partial
@@ -50,8 +50,12 @@ namespace mc {
 constexpr int kWsProducerWarps = WS_NP;
 constexpr int kWsConsumerWarps = WS_NC;
 constexpr int kWsThreads = 32 * (kWsProducerWarps + kWsConsumerWarps);
-constexpr int kWsSlotsPerProducer = 4;
-constexpr int kWsSlots = kWsSlotsPerProducer * kWsProducerWarps;
+// Slots per producer warp (a producer holds up to two at once, so at least
+// three for the producer to work ahead of its consumer); 4 measured fastest
+// on B300 for every process (3 and 2 return 24 and 47 KB to L1 but starve
+// the three-channel consumers).
+MC_HD constexpr int ws_slots(int) { return 4; }
+constexpr int kWsMaxSlots = 4 * kWsProducerWarps;  // mbarrier arrays, sized for the deepest ring
 // record words of one event (structure of arrays inside a slot: word j of
 // lane e at [j][e]): k[3] (12), rs, lgg, flux, jac, psw (2 words), bins (4),
 // the event's index in the launch (weights pass only), and for the
@@ -102,19 +106,35 @@ MC_D bool ws_wait(uint64_t* bar, uint32_t parity) {
 
 // Dynamic shared memory of one block: the ring, then the histograms, the
 // grid edges and the PDF tables (as in the per-thread fused kernel).
-inline size_t ws_smem_bytes(int proc, int ndim, int nbins, int nx) {
-  const size_t ring = size_t(kWsSlots) * ws_words(proc) * 32 * 4;
+// With `rows`, each consumer thread also keeps the twelve row spinors of its
+// current event's |M|^2 there (kWsRowBytes, after the ring) and evaluates it
+// with me2_gg_ttbarg_rows, else with me2_gg_ttbarg_p.  Measured on B300, the
+// rows pay for the three-channel process only (8 % faster there; for the
+// others the L1 they take from the consumers' register spills costs more,
+// 10 % with L2 flushed between launches), and only while the block's shared
+// memory stays within kWsSmemRows (the histograms and edges grow with nbins).
+constexpr int kWsRowBytes = 12 * 32;
+constexpr size_t kWsSmemRows = 224 * 1024;  // 227 KB per block less the static shared memory
+inline size_t ws_smem_bytes(int proc, int ndim, int nbins, int nx, bool rows) {
+  const size_t ring = size_t(ws_slots(proc)) * kWsProducerWarps * ws_words(proc) * 32 * 4 +
+                      (rows ? size_t(kWsConsumerWarps) * 32 * kWsRowBytes : 0);
   const size_t hist = ((size_t(ndim) * nbins * 8 + 15) / 16) * 16;
   return ring + hist + 4 * (size_t(ndim) * (nbins + 1) + size_t(nx) * 3);
 }
+inline bool ws_rows_in_smem(int proc, int ndim, int nbins, int nx) {
+  return proc == P_GG_TTBARG_MC && ws_smem_bytes(proc, ndim, nbins, nx, true) <= kWsSmemRows;
+}
+inline size_t ws_smem_bytes(int proc, int ndim, int nbins, int nx) {
+  return ws_smem_bytes(proc, ndim, nbins, nx, ws_rows_in_smem(proc, ndim, nbins, nx));
+}
 
-// Shared-memory ring of one block: kWsSlots slots of 32 event records, their
+// Shared-memory ring of one block: ws_slots(PROC) x kWsProducerWarps slots of 32 event records, their
 // full/empty mbarriers and counts (-1 = end marker).
 struct WsRing {
-  uint32_t* rec;   // [kWsSlots][ws_words(PROC)][32]
-  uint64_t* full;  // [kWsSlots], arrival count 32 (the producer's lanes)
-  uint64_t* empty;  // [kWsSlots], arrival count 32 (the consumer's lanes)
-  int* count;      // [kWsSlots]
+  uint32_t* rec;   // [slots][ws_words(PROC)][32]
+  uint64_t* full;  // [slots], arrival count 32 (the producer's lanes)
+  uint64_t* empty;  // [slots], arrival count 32 (the consumer's lanes)
+  int* count;      // [slots]
 };
 
 // Producer warp p (0 <= p < kWsProducerWarps): evaluates the kinematics of the
@@ -123,8 +143,8 @@ struct WsRing {
 // every event to the bin counts, appends the events that pass the cuts to its
 // slots, and ends the stream with a partial slot and one end marker per
 // consumer it feeds.  seq is the warp's slot sequence number and carries
-// over between calls (the slot of seq is p * 4 + seq % 4, used for the
-// (seq / 4)-th time).  The Philox event index is a.first + i.  With WOUT the
+// over between calls (the slot of seq is p S + seq % S, used for the
+// (seq / S)-th time).  The Philox event index is a.first + i.  With WOUT the
 // weights pass writes a.wout[i] = 0 for the events that are cut and passes i
 // on in the record.  Returns false when a wait gave up.
 template <int PROC, bool WOUT>
@@ -135,9 +155,10 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
   constexpr int NW = (MAXD + 3) / 4;
   const int lane = threadIdx.x & 31;
   const int ndim = a.ndim, nb = a.nbins;
-  auto slot_of = [&](int q) { return p * kWsSlotsPerProducer + (q & 3); };
+  constexpr int S = ws_slots(PROC);
+  auto slot_of = [&](int q) { return p * S + q % S; };
   auto acquire = [&](int q) -> bool {
-    const int u = q >> 2;  // earlier uses of this slot
+    const int u = q / S;  // earlier uses of this slot
     return u == 0 || ws_wait(&ring.empty[slot_of(q)], uint32_t(u - 1) & 1u);
   };
   auto publish = [&](int q, int cnt) {
@@ -248,14 +269,23 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
   return ok;
 }
 
+// This consumer thread's row store in the block's array of kWsConsumerWarps
+// x 32 x kWsRowBytes bytes (word j of consumer thread t at 16 (j C + t), C
+// the consumer threads).
+MC_D SmemRows ws_rows(const unsigned char* sh_rows) {
+  return {uint32_t(__cvta_generic_to_shared(sh_rows)) + 16u * uint32_t(threadIdx.x - 32 * kWsProducerWarps),
+          16u * 32u * kWsConsumerWarps};
+}
+
 // Consumer warp c (0 <= c < kWsConsumerWarps): evaluates |M|^2 for the events
 // of its producers' slots until every stream it serves has delivered an end
 // marker, and adds the weights w = f J to the Kahan sums, w_max and the
 // histogram of w^2.  q0, q1: the next slot sequence numbers of its (up to two)
 // streams, carried over between calls.  With WOUT the weights pass writes
 // a.wout[i] = w.  Returns false when a wait gave up.
-template <int PROC, bool WOUT>
-MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int c, int& q0, int& q1, Acc& acc) {
+template <int PROC, bool WOUT, class Rows>
+MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows rows, int c, int& q0, int& q1,
+                     Acc& acc) {
   constexpr int MAXD = ProcTraits<PROC>::MAXD;
   constexpr int NW = (MAXD + 3) / 4;
   const int lane = threadIdx.x & 31;
@@ -265,8 +295,9 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int 
     if (si == 0 ? !live0 : !live1) si ^= 1;
     const int p = (c % kWsProducerWarps) + si * kWsConsumerWarps;
     int& q = si == 0 ? q0 : q1;
-    const int s = p * kWsSlotsPerProducer + (q & 3);
-    if (!ws_wait(&ring.full[s], uint32_t(q >> 2) & 1u)) return false;
+    constexpr int S = ws_slots(PROC);
+    const int s = p * S + q % S;
+    if (!ws_wait(&ring.full[s], uint32_t(q / S) & 1u)) return false;
     const int cnt = ring.count[s];
     q += kWsClasses;
     if (cnt < 0) {
@@ -294,7 +325,7 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int 
       uint32_t binw[NW];
 #pragma unroll
       for (int j = 0; j < NW; ++j) binw[j] = r[(kWBin + j) * 32];
-      const float me2 = gg_me2<float>(a, kin);
+      const float me2 = gg_me2<float>(a, kin, rows);
       double w = gg_weight<float>(a, kin, me2) * double(jac);
       if (!isfinite(w)) {
         ++acc.nbad;
@@ -333,19 +364,21 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, int 
 }
 
 // WOUT: the weights pass (a.wout receives every event's weight; launches of
-// at most 2^32 - 1 events).
-template <int PROC, bool WOUT>
+// at most 2^32 - 1 events).  SMROWS: the consumers' row spinors in shared
+// memory (ws_rows_in_smem).
+template <int PROC, bool WOUT, bool SMROWS>
 __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs a) {
   static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D || PROC == P_GG_TTBARG_MC, "gg -> t tbar g only");
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kWsSlots], empty[kWsSlots];
-  __shared__ int count[kWsSlots];
+  __shared__ __align__(8) uint64_t full[kWsMaxSlots], empty[kWsMaxSlots];
+  __shared__ int count[kWsMaxSlots];
   __shared__ int failed;
   __shared__ BlockPartial warp_part[kWsThreads / 32];
   const int ndim = a.ndim, nb = a.nbins;
   const int nedge = ndim * (nb + 1), nhist = ndim * nb;
   const WsRing ring = {reinterpret_cast<uint32_t*>(smem), full, empty, count};
-  unsigned char* rest = smem + size_t(kWsSlots) * ws_words(PROC) * 32 * 4;
+  unsigned char* sh_rows = smem + size_t(ws_slots(PROC)) * kWsProducerWarps * ws_words(PROC) * 32 * 4;
+  unsigned char* rest = sh_rows + (SMROWS ? size_t(kWsConsumerWarps) * 32 * kWsRowBytes : 0);
   float* sh_w2 = reinterpret_cast<float*>(rest);
   unsigned int* sh_n = reinterpret_cast<unsigned int*>(rest + size_t(nhist) * 4);
   float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
@@ -357,7 +390,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
     sh_n[i] = 0u;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kWsSlots; ++s) {
+    for (int s = 0; s < ws_slots(PROC) * kWsProducerWarps; ++s) {
       mbar_init(&full[s], 32);
       mbar_init(&empty[s], 32);
     }
@@ -386,7 +419,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
     const int c = warp - kWsProducerWarps;
     int q0 = c / kWsProducerWarps, q1 = q0;
-    ok = ws_consume<PROC, WOUT>(a, sh_w2, ring, c, q0, q1, acc);
+    if constexpr (SMROWS) {
+      SmemRows rows = ws_rows(sh_rows);
+      ok = ws_consume<PROC, WOUT>(a, sh_w2, ring, rows, c, q0, q1, acc);
+    } else {
+      ok = ws_consume<PROC, WOUT>(a, sh_w2, ring, NoRows{}, c, q0, q1, acc);
+    }
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
   }
   if (!ok) atomicExch(&failed, 1);
