@@ -55,21 +55,21 @@ METRIC = "events/sec and GPU time to 1e-3 rel. error: FP32+flow vs plain FP64 VE
 # warp-specialised fused kernel (packed |M|^2 over 16 polarisation
 # configurations, RAMBO, PDFs and the map of every event, in-cut or not),
 # counted by ncu over one full-size launch of this workload as
-# 2 ffma + fmul + fadd + 4 ffma2 + 2 fmul2 + 2 fadd2 (1.806e11 FLOP) divided by
-# the launch's 8 049 119 in-cut events; see profiles/.
-FLOP_PER_EVENT = 22434.0
+# 2 ffma + fmul + fadd + 4 ffma2 + 2 fmul2 + 2 fadd2 (1.668e11 FLOP) divided by
+# the launch's 8 049 117 in-cut events; see profiles/.
+FLOP_PER_EVENT = 20720.0
 # DRAM bytes (read + write) of one launch of that kernel, from an ncu capture
-# of this workload (0.47 MB read + 2.62 MB written; see profiles/).  Nothing
+# of this workload (0.47 MB read + 3.32 MB written; see profiles/).  Nothing
 # per event reaches DRAM: the kernel reads the grid and the PDF grid and
 # writes histograms and per-block partials.
-TRAFFIC_BYTES = 3088128
+TRAFFIC_BYTES = 3787264
 FP32_LANES_PER_SM = 128
 # FP32 FLOP per FP32 lane operation of that launch: its ncu counts give
-# 2 ffma + fmul + fadd + 4 ffma2 + 2 fmul2 + 2 fadd2 = 1.807e11 FLOP over
-# ffma + fmul + fadd + 2 (ffma2 + fmul2 + fadd2) = 1.102e11 lane operations;
+# 2 ffma + fmul + fadd + 4 ffma2 + 2 fmul2 + 2 fadd2 = 1.668e11 FLOP over
+# ffma + fmul + fadd + 2 (ffma2 + fmul2 + fadd2) = 1.032e11 lane operations;
 # a multiply or an add alone does one FLOP in a slot that could do two, so
 # the kernel's mix caps it at this fraction of the FMA peak.
-FLOP_PER_LANE_OP = 1.807e11 / 1.102e11
+FLOP_PER_LANE_OP = 1.668e11 / 1.032e11
 # time to a target relative error (gg -> t tbar g, 7 sampled dimensions):
 # FP32 + normalizing flow (6 coupling layers, 32 bins, 3 x 256 BF16 hidden
 # units, Adam lr 1e-3, 200 training steps of 65536 events, then 1e7 events per
