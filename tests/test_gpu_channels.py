@@ -153,16 +153,19 @@ def test_iteration_sums_histograms_and_channel_sums(gpu, oracle_pdf):
     assert np.max(np.abs(w2[nzb] / ref["hist_w2"][nzb] - 1)) < 1e-10
 
 
-def test_fp32_warp_specialised_iteration_matches_the_event_records(gpu):
+@pytest.mark.parametrize("nbins", [50, 256])
+def test_fp32_warp_specialised_iteration_matches_the_event_records(gpu, nbins):
     """FP32 iterations run the warp-specialised kernel (producer warps: channel
     choice, maps, densities, cuts; consumer warps: |M|^2).  Against the
     per-event records of the one-event-per-thread path for the same events:
-    the weights (from the weights pass) agree to FP32 rounding (the two
-    kernels inline the same FP32 code, but the compiler may fuse its
-    multiply-adds differently), the launch's sums are the sums of its
-    weights, and the bin counts of all 17 grid dimensions are identical."""
+    the weights (from the weights pass) agree to FP32 rounding (the kernels
+    evaluate the same amplitudes in different orders of operations: with 50
+    bins the consumers keep each event's row spinors in shared memory, with
+    256 bins that memory goes to the histograms and they recompute the rows
+    as the one-event-per-thread path does), the launch's sums are the sums of
+    its weights, and the bin counts of all 17 grid dimensions are identical."""
     itg = W.gg_ttbarg_mc()
-    edges = random_grid(17, 50, 12).astype(np.float32).astype(np.float64)
+    edges = random_grid(17, nbins, 12).astype(np.float32).astype(np.float64)
     n = 60000
     v = make_vegas(M.MC_FP32_KAHAN, edges, iteration=1, seed=6)
     rec = torch.empty((n, M.REC_STRIDE), dtype=torch.float64, device="cuda")
@@ -182,7 +185,7 @@ def test_fp32_warp_specialised_iteration_matches_the_event_records(gpu):
     assert abs(r.sum - math.fsum(ws)) <= 1e-12 * abs(r.sum)
     assert abs(r.sum2 - math.fsum(ws * ws)) <= 1e-12 * r.sum2
     ch = g[:, R["CHANNEL"]].astype(int)
-    ref = np.zeros((17, 50), dtype=np.int64)
+    ref = np.zeros((17, nbins), dtype=np.int64)
     for d in range(7):
         gd = np.where(d < 2, d, 2 + 5 * ch + (d - 2))
         np.add.at(ref, (gd, g[:, R["BIN"] + d].astype(int)), 1)
