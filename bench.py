@@ -257,6 +257,60 @@ def batch16(M, pdf, stream, iterations=10):
 
 
 PDF_MEMBERS, PDF_POINTS, PDF_Q = 400, 2415, 100.0
+PDF_SWEEP = (10, 14, 18, 22, 26)  # log2 of the batch sizes of the single-set sweep
+
+
+def pdf_sweep_inputs(n, seed=0):
+    """n query points log-uniform inside the synthetic grid: x in [1e-7, 1],
+    Q in [1.65, 1e4] GeV (Q^2 passed), from a seeded torch generator."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    u = torch.rand((2, n), generator=g, dtype=torch.float64, device="cuda")
+    x = torch.pow(10.0, -7.0 * (1.0 - u[0]))
+    q = 1.65 * torch.pow(1e4 / 1.65, u[1])
+    return x.contiguous(), (q * q).contiguous()
+
+
+def pdf_xfxq2_sweep(M, pdf, stream, reps=10):
+    """The PDF-only benchmark of the thesis (Sec. "Software design and
+    benchmarks": PDFFlow against LHAPDF over growing numbers of query
+    points): all 11 flavours of the synthetic grid at 2^10 .. 2^26 random
+    (x, Q) points, FP32 and FP64, each launch timed alone with CUDA events
+    after an L2 flush.  Roofline: HBM, algorithmic bytes = 16 B of input and
+    8 B per flavour of output per point (the grid itself stays in L2)."""
+    import torch
+    nfl = 11
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    hbm = peaks().get("hbm_gbs", 6400.0)
+    out = {"workload": "synthetic 100 x 40 x 11 grid, all 11 flavours, random (x, Q) log-uniform in the grid",
+           "bytes_per_point": 16 + 8 * nfl, "hbm_peak_gbs": hbm,
+           "thesis_context": "PDFFlow's xfxQ2 over growing batches of query points against LHAPDF"}
+    for name, prec in (("fp32", M.MC_FP32_KAHAN), ("fp64", M.MC_FP64)):
+        rows = []
+        for lg in PDF_SWEEP:
+            n = 1 << lg
+            x, q2 = pdf_sweep_inputs(n, seed=lg)
+            res = torch.empty((n, nfl), dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                M.mc_pdf_xfxq2(pdf, prec, n, x, q2, res, stream)
+            times = []
+            for _ in range(reps):
+                flush_l2(flush)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                M.mc_pdf_xfxq2(pdf, prec, n, x, q2, res, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            gbs = n * (16 + 8 * nfl) / (ms / 1e3) / 1e9
+            rows.append({"points": n, "ms": ms, "points_per_s": n / (ms / 1e3), "achieved_gbs": gbs,
+                         "hbm_frac": gbs / hbm})
+            del x, q2, res
+        out[name] = rows
+    return out
 
 
 def pdf_members(M, stream, reps=20):
@@ -460,6 +514,11 @@ def profile_case(case):
         for _ in range(2):
             r = M.mc_vegas_iterate_weights(v, itg, pdf, n, w)
             M.mc_unweight(v, itg, pdf, w, n, r.wmax, ev, n // 8)
+    elif case == "pdf":  # the single-set batch interpolation, 2^24 points, FP32 then FP64
+        x, q2 = pdf_sweep_inputs(1 << 24, seed=24)
+        res = torch.empty((1 << 24, 11), dtype=torch.float64, device="cuda")
+        for prec in (M.MC_FP32_KAHAN, M.MC_FP64):
+            M.mc_pdf_xfxq2(pdf, prec, 1 << 24, x, q2, res)
     elif case == "pdfset":  # the multi-member PDF evaluation, FP32 then FP64
         import numpy as _np
         pset = W.synthetic_pdf_set(nmem=PDF_MEMBERS, seed=0)
@@ -687,6 +746,7 @@ def run_native(args, rank, world):
         line["time_to_target"] = time_to_target(M, pdf, stream)
         line["batch16"] = batch16(M, pdf, stream)
         line["pdf_members"] = pdf_members(M, stream)
+        line["pdf_xfxq2"] = pdf_xfxq2_sweep(M, pdf, stream)
         line["unweighting"] = unweighting(M, pdf, stream, M.mc_vegas_get_grid(v), mean_kernel_ms)
         line["samplers"] = samplers(M, pdf, stream)
         line["pp_ttbarj"] = pp_ttbarj(M, pdf, stream)
@@ -704,7 +764,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-target", action="store_true")
-    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdfset", "unweight", "mc", "ppttj"], default=None,
+    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdf", "pdfset", "unweight", "mc", "ppttj"], default=None,
                     help="run a small fixed workload for profiling and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -159,9 +159,15 @@ int mc_pdf_load(const double* x, int nx, const double* q, int nq, const int32_t*
   p->nq = nq;
   p->nflav = nflav;
   p->pids.assign(pids, pids + nflav);
+  p->x_lo = x[0];
+  p->x_hi = x[nx - 1];
+  p->q2_lo = q[0] * q[0];
+  p->q2_hi = q[nq - 1] * q[nq - 1];
   std::vector<double> lx(nx), lq(nq), v64(nval);
   p->logq2.resize(nq);
   std::vector<float> v32(nval);
+  p->nfp = (nflav + 3) / 4 * 4;
+  std::vector<float> v32t(size_t(nq) * nx * p->nfp, 0.0f);
   for (int i = 0; i < nx; ++i) lx[i] = std::log(x[i]);
   for (int j = 0; j < nq; ++j) lq[j] = p->logq2[j] = std::log(q[j] * q[j]);
   // device layout [flavour][Q][x]
@@ -171,6 +177,7 @@ int mc_pdf_load(const double* x, int nx, const double* q, int nq, const int32_t*
         const double v = xf[(size_t(i) * nq + j) * nflav + f];
         v64[(size_t(f) * nq + j) * nx + i] = v;
         v32[(size_t(f) * nq + j) * nx + i] = float(v);
+        v32t[(size_t(j) * nx + i) * p->nfp + f] = float(v);
       }
   auto cleanup = [&](int code, const char* what, cudaError_t e) {
     mc_pdf_free(p);
@@ -181,6 +188,8 @@ int mc_pdf_load(const double* x, int nx, const double* q, int nq, const int32_t*
   if ((e = cudaMalloc(&p->d_logq2, sizeof(double) * nq)) != cudaSuccess) return cleanup(MC_ENOMEM, "cudaMalloc", e);
   if ((e = cudaMalloc(&p->d_xf64, sizeof(double) * nval)) != cudaSuccess) return cleanup(MC_ENOMEM, "cudaMalloc", e);
   if ((e = cudaMalloc(&p->d_xf32, sizeof(float) * nval)) != cudaSuccess) return cleanup(MC_ENOMEM, "cudaMalloc", e);
+  if ((e = cudaMalloc(&p->d_xf32t, sizeof(float) * v32t.size())) != cudaSuccess)
+    return cleanup(MC_ENOMEM, "cudaMalloc", e);
   if ((e = cudaMemcpy(p->d_logx, lx.data(), sizeof(double) * nx, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cleanup(MC_ECUDA, "cudaMemcpy", e);
   if ((e = cudaMemcpy(p->d_logq2, lq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -188,6 +197,8 @@ int mc_pdf_load(const double* x, int nx, const double* q, int nq, const int32_t*
   if ((e = cudaMemcpy(p->d_xf64, v64.data(), sizeof(double) * nval, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cleanup(MC_ECUDA, "cudaMemcpy", e);
   if ((e = cudaMemcpy(p->d_xf32, v32.data(), sizeof(float) * nval, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cleanup(MC_ECUDA, "cudaMemcpy", e);
+  if ((e = cudaMemcpy(p->d_xf32t, v32t.data(), sizeof(float) * v32t.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cleanup(MC_ECUDA, "cudaMemcpy", e);
   *out = p;
   return MC_OK;
@@ -199,6 +210,7 @@ int mc_pdf_free(mc_pdf p) {
   cudaFree(p->d_logq2);
   cudaFree(p->d_xf64);
   cudaFree(p->d_xf32);
+  cudaFree(p->d_xf32t);
   delete p;
   return MC_OK;
 }

@@ -26,7 +26,12 @@ struct mc_pdf_s {
   double* d_logq2 = nullptr;
   double* d_xf64 = nullptr;
   float* d_xf32 = nullptr;
-  mc::PdfDev dev() const { return {nx, nq, nflav, d_logx, d_logq2, d_xf64, d_xf32}; }
+  double x_lo = 0, x_hi = 0, q2_lo = 0, q2_hi = 0;  // first and last knots
+  float* d_xf32t = nullptr;  // [nq][nx][nfp], flavours innermost, padded with zeros
+  int nfp = 0;
+  mc::PdfDev dev() const {
+    return {nx, nq, nflav, d_logx, d_logq2, d_xf64, d_xf32, x_lo, x_hi, q2_lo, q2_hi, d_xf32t, nfp};
+  }
   int index(int pid) const {
     for (int i = 0; i < nflav; ++i)
       if (pids[i] == pid) return i;

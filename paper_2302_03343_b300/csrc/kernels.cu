@@ -106,54 +106,250 @@ __global__ void refine_kernel(double* edges, float* edges32, double* hist_w2, un
                    hist_n + size_t(d) * nbins, nbins, alpha, refine_smem + size_t(d) * (3 * nbins + 2));
 }
 
-// Batched xf(x, Q^2) for all flavours: one thread per (point, flavour).
+// Batched xf(x, Q^2) for all flavours, one thread per point: the range
+// check, the logarithms, both cell searches, the Q weights and the x stencil
+// are formed once per point, in the working precision R (FP32 mode: FP32
+// logarithms, whose rounding at the grid's edges is clamped back into the
+// grid), and every flavour is interpolated from them.  The block's outputs
+// are staged in shared memory and written as one contiguous range.
+constexpr int kPdfBlock = 128;
 template <class R>
-__global__ void pdf_xfxq2_kernel(PdfDev pdf, long long n, const double* x, const double* q2, double* out) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * pdf.nflav) return;
-  const long long i = idx / pdf.nflav;
-  const int fl = int(idx % pdf.nflav);
-  const double xv = x[i], qv = q2[i];
-  const int nx = pdf.nx, nq = pdf.nq;
-  const double lx = log(xv), lq = log(qv);
-  if (!(lx >= pdf.logx[0] && lx <= pdf.logx[nx - 1] && lq >= pdf.logq2[0] && lq <= pdf.logq2[nq - 1])) {
-    out[idx] = __longlong_as_double(0x7ff8000000000000LL);
-    return;
-  }
-  int j0;
-  double w[4];
-  q_weights(pdf.logq2, nq, lq, &j0, w);
-  const int ix = knot_cell(pdf.logx, nx, lx);
-  const R h = R(pdf.logx[ix + 1] - pdf.logx[ix]);
-  const R tau = R((lx - pdf.logx[ix]) / double(h));
-  // slope stencil in x: knots ix-1 .. ix+2
-  R tk[4];
-  for (int t = 0; t < 4; ++t) {
-    const int ii = min(max(ix - 1 + t, 0), nx - 1);
-    tk[t] = R(pdf.logx[ii]);
-  }
-  double acc = 0.0;
-  for (int t = 0; t < 4; ++t) {
-    const int j = j0 + t;
-    if (j < 0 || j >= nq || w[t] == 0.0) continue;
-    const size_t base = (size_t(fl) * nq + j) * nx;
-    R f[4];
-    for (int u = 0; u < 4; ++u) {
-      const int ii = min(max(ix - 1 + u, 0), nx - 1);
-      f[u] = sizeof(R) == 8 ? R(pdf.xf64[base + ii]) : R(pdf.xf32[base + ii]);
+__global__ void __launch_bounds__(kPdfBlock) pdf_xfxq2_kernel(PdfDev pdf, long long n, const double* x,
+                                                               const double* q2, double* out) {
+  extern __shared__ double sh_xf[];  // [kPdfBlock][nflav]
+  const int nfl = pdf.nflav, nx = pdf.nx, nq = pdf.nq;
+  const long long i0 = (long long)blockIdx.x * kPdfBlock;
+  const long long i = i0 + threadIdx.x;
+  double* mine = sh_xf + threadIdx.x * nfl;
+  if (i < n) {
+    const double xv = x[i], qv = q2[i];
+    if (!(xv >= pdf.x_lo && xv <= pdf.x_hi && qv >= pdf.q2_lo && qv <= pdf.q2_hi)) {
+      for (int fl = 0; fl < nfl; ++fl) mine[fl] = __longlong_as_double(0x7ff8000000000000LL);
+    } else {
+      R lx, lq;
+      if constexpr (sizeof(R) == 8) {
+        lx = log(xv);
+        lq = log(qv);
+      } else {
+        lx = fminf(fmaxf(logf(float(xv)), float(pdf.logx[0])), float(pdf.logx[nx - 1]));
+        lq = fminf(fmaxf(logf(float(qv)), float(pdf.logq2[0])), float(pdf.logq2[nq - 1]));
+      }
+      int j0;
+      R w[4];
+      q_weights_r<R>(pdf.logq2, nq, lq, &j0, w);
+      const int ix = knot_cell(pdf.logx, nx, double(lx));
+      const R h = R(pdf.logx[ix + 1] - pdf.logx[ix]);
+      const R tau = (lx - R(pdf.logx[ix])) / h;
+      // slope stencil in x: knots ix-1 .. ix+2 (clamped at the ends, where the
+      // one-sided slope below does not use them)
+      int ii[4];
+      R rdx[3];  // 1 / (t[k+1] - t[k]) over the stencil
+#pragma unroll
+      for (int t = 0; t < 4; ++t) ii[t] = min(max(ix - 1 + t, 0), nx - 1);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const double d = pdf.logx[ii[t + 1]] - pdf.logx[ii[t]];
+        rdx[t] = d != 0.0 ? R(1.0 / d) : R(0);
+      }
+      const bool first = ix == 0, last = ix + 1 == nx - 1;
+      const R t2 = tau * tau, t3 = t2 * tau;
+      const R c0 = R(2) * t3 - R(3) * t2 + R(1), c1 = (t3 - R(2) * t2 + tau) * h, c2 = R(-2) * t3 + R(3) * t2,
+              c3 = (t3 - t2) * h;
+      for (int fl = 0; fl < nfl; ++fl) {
+        R acc = R(0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int j = j0 + t;
+          if (j < 0 || j >= nq || w[t] == R(0)) continue;
+          const size_t base = (size_t(fl) * nq + j) * nx;
+          R f[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) f[u] = sizeof(R) == 8 ? R(pdf.xf64[base + ii[u]]) : R(pdf.xf32[base + ii[u]]);
+          const R s01 = (f[1] - f[0]) * rdx[0], s12 = (f[2] - f[1]) * rdx[1], s23 = (f[3] - f[2]) * rdx[2];
+          const R d0 = first ? s12 : R(0.5) * (s12 + s01);
+          const R d1 = last ? s12 : R(0.5) * (s23 + s12);
+          acc += w[t] * (c0 * f[1] + c1 * d0 + c2 * f[2] + c3 * d1);
+        }
+        mine[fl] = double(acc);
+      }
     }
-    R d0, d1;
-    if (ix == 0)
-      d0 = (f[2] - f[1]) / (tk[2] - tk[1]);
-    else
-      d0 = R(0.5) * ((f[2] - f[1]) / (tk[2] - tk[1]) + (f[1] - f[0]) / (tk[1] - tk[0]));
-    if (ix + 1 == nx - 1)
-      d1 = (f[2] - f[1]) / (tk[2] - tk[1]);
-    else
-      d1 = R(0.5) * ((f[3] - f[2]) / (tk[3] - tk[2]) + (f[2] - f[1]) / (tk[2] - tk[1]));
-    acc += w[t] * double(hermite<R>(tau, h, f[1], f[2], d0, d1));
   }
-  out[idx] = acc;
+  __syncthreads();
+  const long long npts = n - i0 < kPdfBlock ? n - i0 : kPdfBlock;
+  double* dst = out + i0 * nfl;
+  for (int k = threadIdx.x; k < npts * nfl; k += kPdfBlock) dst[k] = sh_xf[k];
+}
+
+// Helpers of the FP32 path that keep it off the FP64 pipe (on B300 about
+// 1/64 of the FP32 rate, f32 <-> f64 conversions included):
+// positive doubles order like their bit patterns read as integers
+MC_D bool pos_f64_le(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+// log v in FP32 for a positive normal double, from its binary exponent and
+// its significand cut to 23 bits: e ln 2 + log m, m in [1, 2)
+MC_D float log_f64_to_f32(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = int((b >> 52) & 0x7ff) - 1023;
+  const float m = __uint_as_float(0x3f800000u | uint32_t((b >> 29) & 0x7fffffu));
+  return float(e) * 0.693147180559945309f + logf(m);
+}
+// float -> double by re-biasing the exponent (normal numbers); zeros,
+// subnormals, infinities and NaN take the conversion instruction
+MC_D double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return double(f);
+  return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32 |
+                                          (unsigned long long)(e + 896u) << 52 |
+                                          (unsigned long long)(u & 0x7fffffu) << 29));
+}
+// largest i in [0, n-2] with t[i] <= v
+MC_D int knot_cell_f(const float* t, int n, float v) {
+  int lo = 0, hi = n - 2;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t[mid] <= v)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// FP32 batch interpolation with the whole grid in shared memory (when it
+// fits, 176 KB for 100 x 40 knots and 11 flavours): flavours innermost, so one
+// 16-byte load brings four flavours of a knot.  Per point the sixteen (Q, x)
+// stencil knots combine with coefficients formed once: the Q weights times
+// the x Hermite weights of the four x knots (the knot slopes written out as
+// differences, one-sided at the grid's ends), so each flavour costs sixteen
+// multiply-adds.  The knots and their reciprocal spacings are kept in FP32 in
+// shared memory too, and nothing in the loop runs on the FP64 pipe.  A
+// persistent grid of one block per SM walks the points in tiles of kPdfTile;
+// outputs are staged in FP32 and widened to FP64 as the block writes them
+// out as one contiguous range.
+constexpr int kPdfTile = 512;
+constexpr size_t kPdfSmemMax = 224 * 1024;
+inline size_t pdf_smem_bytes(const PdfDev& p) {
+  return size_t(p.nq) * p.nx * p.nfp * 4 + size_t(kPdfTile) * p.nflav * 4 + 8 * size_t(p.nx + p.nq);
+}
+__global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf, long long n, const double* x,
+                                                                      const double* q2, double* out) {
+  extern __shared__ __align__(16) unsigned char pdf_smem[];
+  float4* tab = reinterpret_cast<float4*>(pdf_smem);
+  const int nx = pdf.nx, nq = pdf.nq, nfl = pdf.nflav, nf4 = pdf.nfp / 4;
+  float* stage = reinterpret_cast<float*>(pdf_smem + size_t(nq) * nx * pdf.nfp * 4);
+  float* lxf = stage + size_t(kPdfTile) * nfl;  // [nx] knots, [nx] 1/spacing
+  float* rxf = lxf + nx;
+  float* lqf = rxf + nx;  // [nq], [nq]
+  float* rqf = lqf + nq;
+  {
+    const float4* g = reinterpret_cast<const float4*>(pdf.xf32t);
+    const int n4 = nq * nx * nf4;
+    for (int k = threadIdx.x; k < n4; k += kPdfTile) tab[k] = g[k];
+    for (int k = threadIdx.x; k < nx; k += kPdfTile) {
+      lxf[k] = float(pdf.logx[k]);
+      rxf[k] = k + 1 < nx ? float(1.0 / (pdf.logx[k + 1] - pdf.logx[k])) : 0.0f;
+    }
+    for (int k = threadIdx.x; k < nq; k += kPdfTile) {
+      lqf[k] = float(pdf.logq2[k]);
+      rqf[k] = k + 1 < nq ? float(1.0 / (pdf.logq2[k + 1] - pdf.logq2[k])) : 0.0f;
+    }
+  }
+  __syncthreads();
+  const long long ntiles = (n + kPdfTile - 1) / kPdfTile;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long i0 = tile * kPdfTile, i = i0 + threadIdx.x;
+    float* mine = stage + threadIdx.x * nfl;
+    if (i < n) {
+      const double xv = x[i], qv = q2[i];
+      // x_lo, q2_lo > 0, so a NaN or a negative query fails one of the tests
+      if (!(pos_f64_le(pdf.x_lo, xv) && pos_f64_le(xv, pdf.x_hi) && pos_f64_le(pdf.q2_lo, qv) &&
+            pos_f64_le(qv, pdf.q2_hi))) {
+        for (int fl = 0; fl < nfl; ++fl) mine[fl] = __int_as_float(0x7fc00000);
+      } else {
+        const float lx = fminf(fmaxf(log_f64_to_f32(xv), lxf[0]), lxf[nx - 1]);
+        const float lq = fminf(fmaxf(log_f64_to_f32(qv), lqf[0]), lqf[nq - 1]);
+        // Q weights of the knots j0 .. j0+3 (as q_weights)
+        const int iq = knot_cell_f(lqf, nq, lq);
+        const int j0 = iq - 1;
+        float w[4];
+        {
+          const float hq = lqf[iq + 1] - lqf[iq];
+          const float tq = (lq - lqf[iq]) * rqf[iq];
+          const float q2_ = tq * tq, q3 = q2_ * tq;
+          w[0] = 0.0f;
+          w[1] = 2.0f * q3 - 3.0f * q2_ + 1.0f;
+          w[2] = -2.0f * q3 + 3.0f * q2_;
+          w[3] = 0.0f;
+          auto add_slope = [&](int k, float coef) {
+            const int b = k - j0;
+            if (k == 0) {
+              w[b] -= coef * rqf[0];
+              w[b + 1] += coef * rqf[0];
+            } else if (k == nq - 1) {
+              w[b] += coef * rqf[k - 1];
+              w[b - 1] -= coef * rqf[k - 1];
+            } else {
+              w[b + 1] += 0.5f * coef * rqf[k];
+              w[b] += 0.5f * coef * (rqf[k - 1] - rqf[k]);
+              w[b - 1] -= 0.5f * coef * rqf[k - 1];
+            }
+          };
+          add_slope(iq, (q3 - 2.0f * q2_ + tq) * hq);
+          add_slope(iq + 1, (q3 - q2_) * hq);
+        }
+        const int ix = knot_cell_f(lxf, nx, lx);
+        const float h = lxf[ix + 1] - lxf[ix];
+        const float tau = (lx - lxf[ix]) * rxf[ix];
+        int ii[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) ii[t] = min(max(ix - 1 + t, 0), nx - 1);
+        const float r[3] = {ix >= 1 ? rxf[ix - 1] : 0.0f, rxf[ix], ix + 2 <= nx - 1 ? rxf[ix + 1] : 0.0f};
+        const bool first = ix == 0, last = ix + 1 == nx - 1;
+        const float t2 = tau * tau, t3 = t2 * tau;
+        const float c0 = 2.0f * t3 - 3.0f * t2 + 1.0f, c1 = (t3 - 2.0f * t2 + tau) * h, c2 = -2.0f * t3 + 3.0f * t2,
+                    c3 = (t3 - t2) * h;
+        // slopes d0 = al s12 + be s01, d1 = ga s12 + de s23 (one-sided at the ends),
+        // s01 = r0 (f1 - f0), s12 = r1 (f2 - f1), s23 = r2 (f3 - f2)
+        const float al = first ? 1.0f : 0.5f, be = first ? 0.0f : 0.5f, ga = last ? 1.0f : 0.5f,
+                    de = last ? 0.0f : 0.5f;
+        const float m12 = (c1 * al + c3 * ga) * r[1];
+        const float a[4] = {-c1 * be * r[0], c0 + c1 * be * r[0] - m12, c2 + m12 - c3 * de * r[2], c3 * de * r[2]};
+        float cc[16];
+        int off[16];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int j = j0 + t;
+          const bool in = j >= 0 && j < nq;
+          const int jr = min(max(j, 0), nq - 1);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            cc[4 * t + u] = in ? w[t] * a[u] : 0.0f;
+            off[4 * t + u] = (jr * nx + ii[u]) * nf4;
+          }
+        }
+        for (int k = 0; k < nf4; ++k) {
+          float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float4 f = tab[off[e] + k];
+            acc.x = fmaf(cc[e], f.x, acc.x);
+            acc.y = fmaf(cc[e], f.y, acc.y);
+            acc.z = fmaf(cc[e], f.z, acc.z);
+            acc.w = fmaf(cc[e], f.w, acc.w);
+          }
+          const float v4_[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (4 * k + q < nfl) mine[4 * k + q] = v4_[q];
+        }
+      }
+    }
+    __syncthreads();
+    const long long npts = n - i0 < kPdfTile ? n - i0 : kPdfTile;
+    double* dst = out + i0 * nfl;
+    for (int k = threadIdx.x; k < npts * nfl; k += kPdfTile) dst[k] = f32_to_f64(stage[k]);
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -277,15 +473,30 @@ cudaError_t launch_refine(double* edges, float* edges32, double* hist_w2, unsign
 }
 cudaError_t launch_pdf_xfxq2(const PdfDev& pdf, bool fp64, long long n, const double* x, const double* q2,
                              double* out, cudaStream_t st) {
-  const long long total = n * pdf.nflav;
-  if (total == 0) return cudaSuccess;
+  if (n == 0) return cudaSuccess;
   (void)cudaGetLastError();
-  const int block = 256;
-  const long long grid = (total + block - 1) / block;
-  if (fp64)
-    pdf_xfxq2_kernel<double><<<unsigned(grid), block, 0, st>>>(pdf, n, x, q2, out);
-  else
-    pdf_xfxq2_kernel<float><<<unsigned(grid), block, 0, st>>>(pdf, n, x, q2, out);
+  if (!fp64 && pdf.xf32t && pdf_smem_bytes(pdf) <= kPdfSmemMax) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long ntiles = (n + kPdfTile - 1) / kPdfTile;
+    const int grid = int(ntiles < sms ? ntiles : sms);
+    const size_t smem = pdf_smem_bytes(pdf);
+    const cudaError_t e =
+        cudaFuncSetAttribute(pdf_xfxq2_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    pdf_xfxq2_smem_kernel<<<grid, kPdfTile, smem, st>>>(pdf, n, x, q2, out);
+    return cudaGetLastError();
+  }
+  const long long grid = (n + kPdfBlock - 1) / kPdfBlock;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const size_t smem = size_t(kPdfBlock) * pdf.nflav * sizeof(double);  // nflav <= 64: at most 64 KB
+  auto k = fp64 ? pdf_xfxq2_kernel<double> : pdf_xfxq2_kernel<float>;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  k<<<unsigned(grid), kPdfBlock, smem, st>>>(pdf, n, x, q2, out);
   return cudaGetLastError();
 }
 

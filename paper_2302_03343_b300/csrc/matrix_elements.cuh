@@ -312,6 +312,11 @@ MC_D R me2_gg_ttbarg(const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4
 // line, off t, off tbar, three-gluon) combine with the colour matrix
 // C_de = sum over colours of c_d c_e^* (Hermitian, complex), passed as
 // re/im pairs: |M|^2 = sum_d C_dd |A_d|^2 + 2 sum_{d<e} Re(C_de A_d A_e^*).
+// The light-line currents depend only on the light helicities and the gluon
+// polarisation, the heavy-line ones only on the top spins and the
+// polarisation: both are formed once (the light side for the two helicity
+// pairs the massless line allows, kept; the heavy side per top-spin
+// configuration) and contracted for every combination.
 template <class R>
 MC_D R me2_qline_ttbarg(int kind, const v4<R>& pa, const v4<R>& pb, const v4<R>& pt, const v4<R>& ptb,
                         const v4<R>& pk, R m, R g2, const R* cmat) {
@@ -328,52 +333,63 @@ MC_D R me2_qline_ttbarg(int kind, const v4<R>& pa, const v4<R>& pb, const v4<R>&
   v4<R> eps[2];
   linear_polarisations(kphys, &eps[0], &eps[1]);
   const R g3 = g2 * m_sqrt(g2);
+  // light side: a massless line keeps its chirality through an odd number of
+  // gamma matrices, so u(h) pairs with vbar(-h) and ubar(h), v(h) with vbar(h)
+  cx<R> vl[2][4], v1[2][2][4], v2[2][2][4];  // [helicity pair][polarisation][mu]
+#pragma unroll 1
+  for (int ip = 0; ip < 2; ++ip) {
+    const int h1 = 2 * ip - 1, h2 = kind == 0 ? -h1 : h1;
+    const sp4<R> col = kind == 2 ? v_spinor(pk, R(0), h1) : u_spinor(pa, R(0), h1);
+    const sp4<R> row = kind == 0 ? vbar_spinor(pb, R(0), h2)
+                                 : (kind == 1 ? ubar_spinor(pk, R(0), h2) : vbar_spinor(pa, R(0), h2));
+    vector_current(row, col, vl[ip]);
+#pragma unroll
+    for (int lam = 0; lam < 2; ++lam) {
+      vector_current(row, prop_col(s1, R(0), i1, slash_col(eps[lam], col)), v1[ip][lam]);
+      vector_current(prop_row(slash_row(row, eps[lam]), s2, R(0), i2), col, v2[ip][lam]);
+    }
+  }
+  cx<R> vlk[2], vle[2][2];  // vl . (k - q), vl . eps
+#pragma unroll
+  for (int ip = 0; ip < 2; ++ip) {
+    vlk[ip] = cdot4(vl[ip], kmq);
+#pragma unroll
+    for (int lam = 0; lam < 2; ++lam) vle[ip][lam] = cdot4(vl[ip], eps[lam]);
+  }
+  const cx<R> mi = mkc(R(0), -g3);  // -i g^3
   R total = R(0);
 #pragma unroll 1
-  for (int h1 = -1; h1 <= 1; h1 += 2) {
-    const sp4<R> col = kind == 2 ? v_spinor(pk, R(0), h1) : u_spinor(pa, R(0), h1);
+  for (int h3 = -1; h3 <= 1; h3 += 2) {
+    const sp4<R> ut = ubar_spinor(pt, m, h3);
 #pragma unroll 1
-    for (int h2 = -1; h2 <= 1; h2 += 2) {
-      // a massless line keeps its chirality through an odd number of gamma
-      // matrices: u(+) pairs with vbar(-) and ubar(+), v(+) with vbar(+)
-      if (kind == 0 ? h2 == h1 : h2 != h1) continue;
-      const sp4<R> row = kind == 0 ? vbar_spinor(pb, R(0), h2)
-                                   : (kind == 1 ? ubar_spinor(pk, R(0), h2) : vbar_spinor(pa, R(0), h2));
-      cx<R> vl[4];
-      vector_current(row, col, vl);
-#pragma unroll 1
-      for (int h3 = -1; h3 <= 1; h3 += 2) {
-        const sp4<R> ut = ubar_spinor(pt, m, h3);
-#pragma unroll 1
-        for (int h4 = -1; h4 <= 1; h4 += 2) {
-          const sp4<R> vt = v_spinor(ptb, m, h4);
-          cx<R> hh[4];
-          vector_current(ut, vt, hh);
-          const cx<R> vlh = cdot4(vl, hh);
+    for (int h4 = -1; h4 <= 1; h4 += 2) {
+      const sp4<R> vt = v_spinor(ptb, m, h4);
+      cx<R> hh[4];
+      vector_current(ut, vt, hh);
+      const cx<R> hhm = cdot4(hh, mkp);
 #pragma unroll
-          for (int lam = 0; lam < 2; ++lam) {
-            const v4<R>& e = eps[lam];
-            cx<R> v1[4], v2[4], h3v[4], h4v[4];
-            vector_current(row, prop_col(s1, R(0), i1, slash_col(e, col)), v1);
-            vector_current(prop_row(slash_row(row, e), s2, R(0), i2), col, v2);
-            vector_current(prop_row(slash_row(ut, e), s3, m, i3), vt, h3v);
-            vector_current(ut, prop_col(s4, m, i4, slash_col(e, vt)), h4v);
-            cx<R> amp[5];
-            const cx<R> mi = mkc(R(0), -g3);  // -i g^3
-            amp[0] = mi * (cdot4(v1, hh) * iq2);
-            amp[1] = mi * (cdot4(v2, hh) * iq2);
-            amp[2] = mi * (cdot4(vl, h3v) * ip2);
-            amp[3] = mi * (cdot4(vl, h4v) * ip2);
-            amp[4] = (vlh * mdot(kpq, e) + cdot4(vl, kmq) * cdot4(hh, e) + cdot4(vl, e) * cdot4(hh, mkp)) *
-                     (g3 * ip2 * iq2);
+      for (int lam = 0; lam < 2; ++lam) {
+        const v4<R>& e = eps[lam];
+        cx<R> h3v[4], h4v[4];
+        vector_current(prop_row(slash_row(ut, e), s3, m, i3), vt, h3v);
+        vector_current(ut, prop_col(s4, m, i4, slash_col(e, vt)), h4v);
+        const cx<R> hhe = cdot4(hh, e);
+        const R ke = mdot(kpq, e);
 #pragma unroll
-            for (int d = 0; d < 5; ++d) {
-              total += cmat[2 * (d * 5 + d)] * norm2(amp[d]);
+        for (int ip = 0; ip < 2; ++ip) {
+          cx<R> amp[5];
+          amp[0] = mi * (cdot4(v1[ip][lam], hh) * iq2);
+          amp[1] = mi * (cdot4(v2[ip][lam], hh) * iq2);
+          amp[2] = mi * (cdot4(vl[ip], h3v) * ip2);
+          amp[3] = mi * (cdot4(vl[ip], h4v) * ip2);
+          amp[4] = (cdot4(vl[ip], hh) * ke + vlk[ip] * hhe + vle[ip][lam] * hhm) * (g3 * ip2 * iq2);
 #pragma unroll
-              for (int f = d + 1; f < 5; ++f) {
-                const cx<R> x = mul_conj(amp[d], amp[f]);  // A_d A_f^*
-                total += R(2) * (cmat[2 * (d * 5 + f)] * x.re - cmat[2 * (d * 5 + f) + 1] * x.im);
-              }
+          for (int d = 0; d < 5; ++d) {
+            total += cmat[2 * (d * 5 + d)] * norm2(amp[d]);
+#pragma unroll
+            for (int f = d + 1; f < 5; ++f) {
+              const cx<R> x = mul_conj(amp[d], amp[f]);  // A_d A_f^*
+              total += R(2) * (cmat[2 * (d * 5 + f)] * x.re - cmat[2 * (d * 5 + f) + 1] * x.im);
             }
           }
         }

@@ -23,6 +23,9 @@ struct PdfDev {
   const double* logq2;  // [nq]
   const double* xf64;   // [nflav][nq][nx]
   const float* xf32;    // same, FP32
+  double x_lo, x_hi, q2_lo, q2_hi;  // the grid's range (first and last knots)
+  const float* xf32t;  // FP32, [nq][nx][nfp]: the flavours of a knot together, padded to nfp (a multiple of 4)
+  int nfp;
 };
 
 MC_HD int knot_cell(const double* t, int n, double v) {
@@ -66,6 +69,41 @@ MC_HD void q_weights(const double* lq, int nq, double s, int* j0_out, double* w)
       w[b + 1] += 0.5 * coef / dr;
       w[b] += 0.5 * coef * (-1.0 / dr + 1.0 / dl);
       w[b - 1] -= 0.5 * coef / dl;
+    }
+  };
+  add_slope(iq, h10 * h);
+  add_slope(iq + 1, h11 * h);
+  *j0_out = iq - 1;
+}
+
+// q_weights in the working precision R: the knots are read in FP64 and
+// rounded, the weights formed in R.
+template <class R>
+MC_D void q_weights_r(const double* lq, int nq, R s, int* j0_out, R* w) {
+  const int iq = knot_cell(lq, nq, double(s));
+  const R h = R(lq[iq + 1] - lq[iq]);
+  const R tau = (s - R(lq[iq])) / h;
+  const R t2 = tau * tau, t3 = t2 * tau;
+  const R h00 = R(2) * t3 - R(3) * t2 + R(1), h10 = t3 - R(2) * t2 + tau, h01 = R(-2) * t3 + R(3) * t2,
+          h11 = t3 - t2;
+  for (int t = 0; t < 4; ++t) w[t] = R(0);
+  w[1] += h00;
+  w[2] += h01;
+  auto add_slope = [&](int k, R coef) {
+    const int b = k - (iq - 1);
+    if (k == 0) {
+      const R d = R(lq[1] - lq[0]);
+      w[b] -= coef / d;
+      w[b + 1] += coef / d;
+    } else if (k == nq - 1) {
+      const R d = R(lq[k] - lq[k - 1]);
+      w[b] += coef / d;
+      w[b - 1] -= coef / d;
+    } else {
+      const R dr = R(lq[k + 1] - lq[k]), dl = R(lq[k] - lq[k - 1]);
+      w[b + 1] += R(0.5) * coef / dr;
+      w[b] += R(0.5) * coef * (R(-1) / dr + R(1) / dl);
+      w[b - 1] -= R(0.5) * coef / dl;
     }
   };
   add_slope(iq, h10 * h);

@@ -258,6 +258,44 @@ def test_pdf_xfxq2(gpu, oracle_pdf, pdf_grid, prec, tol):
     assert torch.isnan(out).all()
 
 
+@pytest.mark.parametrize("prec,tol", [(M.MC_FP64, 1e-13), (M.MC_FP32_KAHAN, 1e-5)])
+def test_pdf_xfxq2_paths(gpu, prec, tol):
+    """FP32 batches run from a shared-memory copy of the grid when it fits
+    (the 100 x 40 grid above) and from global memory otherwise (this 400 x 80
+    grid, 1.5 MB in FP32); both against the oracle, at every flavour of points
+    spread over the grid (x up to 0.5, as above: towards x = 1 the densities
+    fall as (1 - x)^b and FP32 keeps fewer digits of them), including the
+    first x knot and the first and last Q knots, the ragged last tile (n not a
+    multiple of the block) and one point outside."""
+    grid = W.synthetic_pdf_grid(3, nx=400, nq=80)
+    ora = O.Pdf(grid)
+    big = M.mc_pdf_load(grid)
+    rng = np.random.default_rng(4)
+    n = 1001
+    x = 10 ** rng.uniform(-7, math.log10(0.5), n)
+    q2 = (10 ** rng.uniform(math.log10(1.65), 4, n)) ** 2
+    x[:4] = [grid.x[0], 0.5, grid.x[0], 0.5]
+    q2[:4] = [grid.q[0] ** 2, grid.q[0] ** 2, grid.q[-1] ** 2, grid.q[-1] ** 2]
+    x[-1] = 2.0
+    for pdf_dev, ref_pdf, g in ((big, ora, grid), (gpu, None, None)):
+        if ref_pdf is None:  # the default grid: its oracle is the module's fixture grid
+            g = W.synthetic_pdf_grid(0)
+            ref_pdf = O.Pdf(g)
+        xd = torch.tensor(x, device="cuda")
+        qd = torch.tensor(q2, device="cuda")
+        out = torch.empty((n, len(g.pids)), dtype=torch.float64, device="cuda")
+        M.mc_pdf_xfxq2(pdf_dev, prec, n, xd, qd, out)
+        got = out.cpu().numpy()
+        assert np.isnan(got[-1]).all() and np.isfinite(got[:-1]).all()
+        worst = 0.0
+        for i in list(range(8)) + list(range(8, n - 1, 13)):
+            for fl, pid in enumerate(g.pids):
+                ref = ref_pdf.xfxq2(int(pid), x[i], q2[i])
+                worst = max(worst, abs(got[i, fl] - ref) / (abs(ref) + 1e-16))
+        assert worst < tol, worst
+    big.free()
+
+
 # ------------------------------------------------------------------ edge cases
 def test_empty_single_and_ragged(gpu, oracle_pdf):
     itg = PROCS["gauss"]
