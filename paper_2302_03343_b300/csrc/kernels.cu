@@ -140,36 +140,48 @@ __global__ void __launch_bounds__(kPdfBlock) pdf_xfxq2_kernel(PdfDev pdf, long l
       const int ix = knot_cell(pdf.logx, nx, double(lx));
       const R h = R(pdf.logx[ix + 1] - pdf.logx[ix]);
       const R tau = (lx - R(pdf.logx[ix])) / h;
-      // slope stencil in x: knots ix-1 .. ix+2 (clamped at the ends, where the
-      // one-sided slope below does not use them)
+      // the x stencil ix-1 .. ix+2 (clamped at the ends, where the one-sided
+      // slopes do not use the clamped knot) and its reciprocal spacings
       int ii[4];
-      R rdx[3];  // 1 / (t[k+1] - t[k]) over the stencil
+      R r[3];
 #pragma unroll
       for (int t = 0; t < 4; ++t) ii[t] = min(max(ix - 1 + t, 0), nx - 1);
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
         const double d = pdf.logx[ii[t + 1]] - pdf.logx[ii[t]];
-        rdx[t] = d != 0.0 ? R(1.0 / d) : R(0);
+        r[t] = d != 0.0 ? R(1.0 / d) : R(0);
       }
       const bool first = ix == 0, last = ix + 1 == nx - 1;
       const R t2 = tau * tau, t3 = t2 * tau;
       const R c0 = R(2) * t3 - R(3) * t2 + R(1), c1 = (t3 - R(2) * t2 + tau) * h, c2 = R(-2) * t3 + R(3) * t2,
               c3 = (t3 - t2) * h;
+      // the Hermite step as weights of the four x knots: slopes
+      // d0 = al s12 + be s01, d1 = ga s12 + de s23 (one-sided at the ends),
+      // s01 = r0 (f1 - f0), s12 = r1 (f2 - f1), s23 = r2 (f3 - f2)
+      const R al = first ? R(1) : R(0.5), be = first ? R(0) : R(0.5), ga = last ? R(1) : R(0.5),
+              de = last ? R(0) : R(0.5);
+      const R m12 = (c1 * al + c3 * ga) * r[1];
+      const R ax[4] = {-c1 * be * r[0], c0 + c1 * be * r[0] - m12, c2 + m12 - c3 * de * r[2], c3 * de * r[2]};
+      R cc[16];
+      size_t off[16];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = j0 + t;
+        const bool in = j >= 0 && j < nq;
+        const int jr = min(max(j, 0), nq - 1);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          cc[4 * t + u] = in ? w[t] * ax[u] : R(0);
+          off[4 * t + u] = size_t(jr) * nx + ii[u];
+        }
+      }
+      const size_t fstride = size_t(nq) * nx;
       for (int fl = 0; fl < nfl; ++fl) {
+        const size_t base = size_t(fl) * fstride;
         R acc = R(0);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int j = j0 + t;
-          if (j < 0 || j >= nq || w[t] == R(0)) continue;
-          const size_t base = (size_t(fl) * nq + j) * nx;
-          R f[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) f[u] = sizeof(R) == 8 ? R(pdf.xf64[base + ii[u]]) : R(pdf.xf32[base + ii[u]]);
-          const R s01 = (f[1] - f[0]) * rdx[0], s12 = (f[2] - f[1]) * rdx[1], s23 = (f[3] - f[2]) * rdx[2];
-          const R d0 = first ? s12 : R(0.5) * (s12 + s01);
-          const R d1 = last ? s12 : R(0.5) * (s23 + s12);
-          acc += w[t] * (c0 * f[1] + c1 * d0 + c2 * f[2] + c3 * d1);
-        }
+        for (int e = 0; e < 16; ++e)
+          acc += cc[e] * (sizeof(R) == 8 ? R(pdf.xf64[base + off[e]]) : R(pdf.xf32[base + off[e]]));
         mine[fl] = double(acc);
       }
     }
