@@ -202,17 +202,32 @@ MC_D float log_f64_to_f32(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const int e = int((b >> 52) & 0x7ff) - 1023;
   const float m = __uint_as_float(0x3f800000u | uint32_t((b >> 29) & 0x7fffffu));
-  return float(e) * 0.693147180559945309f + logf(m);
+  // e as a float without a conversion instruction: 1.5 2^23 + e has e in its
+  // low significand bits (|e| < 2^22)
+  const float ef = __int_as_float(0x4b400000 + e) - 12582912.0f;
+  return ef * 0.693147180559945309f + logf(m);
 }
-// float -> double by re-biasing the exponent (normal numbers); zeros,
-// subnormals, infinities and NaN take the conversion instruction
+// float -> double from the IEEE-754 fields (exactly, every class of value):
+// normal numbers re-bias the exponent (127 -> 1023) and widen the
+// significand; subnormals m 2^-149 are normalised at their leading bit p
+// (exponent field p + 874); zeros keep their sign; infinities and NaN keep
+// their significand bits
 MC_D double f32_to_f64(float f) {
   const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return double(f);
-  return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32 |
-                                          (unsigned long long)(e + 896u) << 52 |
-                                          (unsigned long long)(u & 0x7fffffu) << 29));
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned long long bits;
+  if (e == 0xffu) {
+    bits = sign | 0x7ff0000000000000ull | (unsigned long long)m << 29;
+  } else if (e != 0u) {
+    bits = sign | (unsigned long long)(e + 896u) << 52 | (unsigned long long)m << 29;
+  } else if (m == 0u) {
+    bits = sign;
+  } else {
+    const int p = 31 - __clz(m);
+    bits = sign | (unsigned long long)(p + 874) << 52 | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+  }
+  return __longlong_as_double((long long)bits);
 }
 // largest i in [0, n-2] with t[i] <= v
 MC_D int knot_cell_f(const float* t, int n, float v) {
