@@ -199,6 +199,37 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+# ---- one process per GPU (torchrun): every rank runs its own integration
+# (a replica with its own Philox stream, weak scaling, no data-path
+# collective); the job's time is the slowest rank's and its rate counts the
+# events of all ranks.
+def replica_seed(rank):
+    """Philox seed of rank `rank`'s integration."""
+    return 1000 + rank
+
+
+def ranks_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def max_over_ranks(value, device=None):
+    """The largest of the ranks' values (the value itself on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step, steps, world, total_ms):
+    """Whole-job throughput: the units of all ranks over the slowest rank's time."""
+    return units_per_rank_step * steps * world / (total_ms / 1e3)
+
+
 def _combine(res):
     """Inverse-variance combination of per-iteration (mean, variance of the mean)."""
     w = [1.0 / v for _, v in res if v > 0]
@@ -649,20 +680,15 @@ def run_native(args, rank, world):
     itg = W.gg_ttbarg()
     l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
     # weak scaling: every rank runs its own integration (its own Philox stream)
-    v = M.mc_vegas_init(14, NBINS, 1000 + rank, M.MC_FP32_KAHAN)
+    v = M.mc_vegas_init(14, NBINS, replica_seed(rank), M.MC_FP32_KAHAN)
     for _ in range(args.warmup):
         M.mc_vegas_iterate(v, itg, pdf, args.events, stream)
         M.mc_vegas_refine(v, ALPHA, stream)
     torch.cuda.synchronize()
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kernel_ms, nnz, results = [], [], []
-    barrier()
+    ranks_barrier()
     torch.cuda.synchronize()
     with ClockSampler() as clk:
         for i in range(args.steps):
@@ -676,20 +702,16 @@ def run_native(args, rank, world):
             results.append(r)
         torch.cuda.synchronize()
         step_ms = [a.elapsed_time(b) for a, b in ev]
-    barrier()
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    ranks_barrier()
+    total_ms = max_over_ranks(sum(step_ms), dev)
     clocks = clk.summary(local)
 
     # end to end through the public API with host buffers: upload the host
     # grid, iterate (sums back to the host), refine, read the grid back
     edges = M.mc_vegas_get_grid(v)
-    ve = M.mc_vegas_init(14, NBINS, 5000 + rank, M.MC_FP32_KAHAN)
+    ve = M.mc_vegas_init(14, NBINS, replica_seed(rank) + 4000, M.MC_FP32_KAHAN)
     e2e_s = []
+    ranks_barrier()
     for i in range(args.steps):
         flush_l2(l2)
         torch.cuda.synchronize()
@@ -702,10 +724,11 @@ def run_native(args, rank, world):
     ngrid = 14 * (NBINS + 1)
     h2d = ngrid * 8 + ngrid * 4
     d2h = 64 + ngrid * 8
+    e2e_ms = max_over_ranks(1e3 * sum(e2e_s), dev)
 
     if rank != 0:
         return
-    value = args.events * args.steps * world / (total_ms / 1e3)
+    value = job_rate(args.events, args.steps, world, total_ms)
     pk = peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = pk.get("sm_max_mhz", 2032.0)
@@ -735,7 +758,7 @@ def run_native(args, rank, world):
             "config": {"workload": WORKLOAD, "events_per_step": args.events, "nbins": NBINS,
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "clocks": clocks,
-            "e2e": {"value": args.events * args.steps / sum(e2e_s), "unit": "events/s",
+            "e2e": {"value": job_rate(args.events, args.steps, world, e2e_ms), "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 3 * args.steps,
             "roofline": roof,
