@@ -203,6 +203,11 @@ int mc_vegas_get_grid(mc_vegas v, double* edges);
 /* Accumulated histograms since the last refine: w2[ndim][nbins] (sum of w^2)
  * and counts[ndim][nbins] (events), host outputs; synchronises the device. */
 int mc_vegas_get_hist(mc_vegas v, double* w2, uint32_t* counts);
+/* mc_vegas_set_hist: replace the accumulated histograms (same layout as
+ * mc_vegas_get_hist, host inputs, copied) -- the sums over the ranks of a
+ * sharded iteration, before mc_vegas_refine.  EINVAL on NULL or on a
+ * negative or non-finite w2 entry; synchronises the device. */
+int mc_vegas_set_hist(mc_vegas v, const double* w2, const uint32_t* counts);
 int mc_vegas_set_iteration(mc_vegas v, uint32_t iteration);
 int mc_vegas_get_iteration(mc_vegas v, uint32_t* iteration);
 /* Integrand id (0..255) mixed into the Philox counter (batched runs). */
@@ -220,6 +225,22 @@ int mc_vegas_set_gid(mc_vegas v, uint32_t gid);
  */
 int mc_vegas_iterate(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents,
                      void* stream, mc_iter_result* out);
+
+/* mc_vegas_iterate_shard: the events first .. first+count-1 of the current
+ * iteration (Philox event indices first + i; the same points as those events
+ * of an mc_vegas_iterate over the whole range), for one device of several
+ * that split an iteration (thesis Sec. VEGAS: the iteration's estimate and
+ * its histogram are sums over its events, so the parts' sums add up to the
+ * whole's).  out holds the part's sums (out->n = count); the histograms
+ * accumulate the part's events.  The caller adds the parts' sums and
+ * histograms across devices (mc_vegas_get_hist / mc_vegas_set_hist) before
+ * mc_vegas_refine, which then yields the same grid on every device.  Like
+ * mc_vegas_iterate it advances the iteration counter.  For the three-channel
+ * process the channel sums W_i are the part's means.  EINVAL on first < 0,
+ * count < 0 or first + count beyond 2^63 - 1; otherwise as mc_vegas_iterate.
+ */
+int mc_vegas_iterate_shard(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t first, int64_t count,
+                           void* stream, mc_iter_result* out);
 
 /* mc_vegas_refine: rebins every dimension from the accumulated histograms
  * (smoothing, damping exponent alpha, equal-importance rebinning after

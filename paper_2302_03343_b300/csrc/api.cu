@@ -495,10 +495,11 @@ int mc_launch_shape(const mc_integrand* itg, int prec, int64_t nevents, int* blo
 
 // One iteration (weights: optional per-event weight output, device).
 static int iterate_impl(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, double* weights,
-                        void* stream, mc_iter_result* out) {
+                        void* stream, mc_iter_result* out, int64_t first = 0) {
   if (!out) return fail(MC_EINVAL, "mc_vegas_iterate: out is NULL");
   std::memset(out, 0, sizeof(*out));
   if (nevents < 0) return fail(MC_EINVAL, "mc_vegas_iterate: negative event count");
+  if (first < 0 || nevents > INT64_MAX - first) return fail(MC_EINVAL, "mc_vegas_iterate: bad event range");
   KernelArgs a;
   if (int rc = prepare(v, itg, pdf, &a)) return rc;
   a.wout = weights;
@@ -509,7 +510,7 @@ static int iterate_impl(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t
   if (nevents > 0) {
     const size_t smem = mc::integrand_smem(itg->proc, fp64, v->ndim, v->nbins, pdf ? pdf->nx : 0);
     const int grid = launch_grid(itg->proc, fp64, nevents, smem, v->max_partials);
-    a.first = 0;
+    a.first = uint64_t(first);
     a.n = nevents;
     int* d_status = reinterpret_cast<int*>(v->d_total + 1);
     a.status = d_status;
@@ -546,6 +547,22 @@ static int iterate_impl(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t
 int mc_vegas_iterate(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, void* stream,
                      mc_iter_result* out) {
   return iterate_impl(v, itg, pdf, nevents, nullptr, stream, out);
+}
+
+int mc_vegas_iterate_shard(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t first, int64_t count,
+                           void* stream, mc_iter_result* out) {
+  return iterate_impl(v, itg, pdf, count, nullptr, stream, out, first);
+}
+
+int mc_vegas_set_hist(mc_vegas v, const double* w2, const uint32_t* counts) {
+  if (!v || !w2 || !counts) return fail(MC_EINVAL, "mc_vegas_set_hist: NULL argument");
+  const size_t nh = size_t(v->ndim) * v->nbins;
+  for (size_t i = 0; i < nh; ++i)
+    if (!(w2[i] >= 0.0) || !std::isfinite(w2[i])) return fail(MC_EINVAL, "mc_vegas_set_hist: bad w2 at %zu", i);
+  MC_CUDA(cudaDeviceSynchronize());
+  MC_CUDA(cudaMemcpy(v->d_hist_w2, w2, sizeof(double) * nh, cudaMemcpyHostToDevice));
+  MC_CUDA(cudaMemcpy(v->d_hist_n, counts, sizeof(uint32_t) * nh, cudaMemcpyHostToDevice));
+  return MC_OK;
 }
 
 int mc_vegas_iterate_weights(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, int64_t nevents, double* weights,

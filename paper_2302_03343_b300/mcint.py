@@ -25,7 +25,8 @@ REC_STRIDE = 96
 
 # exported symbols (each declared in include/mcint.h)
 SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_vegas_init", "mc_vegas_free",
-           "mc_vegas_set_grid", "mc_vegas_get_grid", "mc_vegas_get_hist", "mc_vegas_set_iteration",
+           "mc_vegas_set_grid", "mc_vegas_get_grid", "mc_vegas_get_hist", "mc_vegas_set_hist",
+           "mc_vegas_iterate_shard", "mc_vegas_set_iteration",
            "mc_vegas_get_iteration", "mc_vegas_set_gid", "mc_vegas_iterate", "mc_vegas_refine", "mc_integrate",
            "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms", "mc_vegas_iterate_noalloc",
            "mc_batch_create", "mc_batch_iterate", "mc_batch_get_grid", "mc_batch_shape", "mc_batch_kernel_ms",
@@ -109,6 +110,8 @@ def lib():
             "mc_vegas_set_grid": [_vp, _dp],
             "mc_vegas_get_grid": [_vp, _dp],
             "mc_vegas_get_hist": [_vp, _dp, ctypes.POINTER(ctypes.c_uint32)],
+            "mc_vegas_set_hist": [_vp, _dp, ctypes.POINTER(ctypes.c_uint32)],
+            "mc_vegas_iterate_shard": [_vp, _vp, _vp, i64, i64, _vp, _vp],
             "mc_vegas_set_iteration": [_vp, u32],
             "mc_vegas_get_iteration": [_vp, ctypes.POINTER(ctypes.c_uint32)],
             "mc_vegas_set_gid": [_vp, u32],
@@ -366,6 +369,15 @@ def mc_vegas_get_hist(v):
     return w2, n
 
 
+def mc_vegas_set_hist(v, w2, counts):
+    w2 = np.ascontiguousarray(w2, dtype=np.float64)
+    counts = np.ascontiguousarray(counts, dtype=np.uint32)
+    if w2.shape != (v.ndim, v.nbins) or counts.shape != (v.ndim, v.nbins):
+        raise ValueError("histograms must be [ndim][nbins]")
+    _check(lib().mc_vegas_set_hist(v.handle, w2.ctypes.data_as(_dp),
+                                   counts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+
+
 def mc_vegas_set_iteration(v, it):
     _check(lib().mc_vegas_set_iteration(v.handle, it))
 
@@ -385,6 +397,14 @@ def mc_vegas_iterate(v, itg, pdf, nevents, stream=None):
     c = _integrand(itg)
     _check(lib().mc_vegas_iterate(v.handle, ctypes.byref(c), pdf.handle if pdf else None, nevents,
                                   _stream(stream), ctypes.byref(r)))
+    return r
+
+
+def mc_vegas_iterate_shard(v, itg, pdf, first, count, stream=None):
+    r = IterResult()
+    c = _integrand(itg)
+    _check(lib().mc_vegas_iterate_shard(v.handle, ctypes.byref(c), pdf.handle if pdf else None, first, count,
+                                        _stream(stream), ctypes.byref(r)))
     return r
 
 
