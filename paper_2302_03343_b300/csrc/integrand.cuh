@@ -302,12 +302,15 @@ MC_D EventOut integrand(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, do
     const R* cm;
     if constexpr (sizeof(R) == 4) cm = a.cqqf; else cm = a.cqq;
     const R me_gg = gg_me2<R>(a, kin);
-    const R me[6] = {me2_qline_ttbarg<R>(0, pa, pb, pt, ptb, pk, m, g2c, cm),
-                     me2_qline_ttbarg<R>(0, pb, pa, pt, ptb, pk, m, g2c, cm),
-                     me2_qline_ttbarg<R>(1, pa, pb, pt, ptb, pk, m, g2c, cm),
-                     me2_qline_ttbarg<R>(1, pb, pa, pt, ptb, pk, m, g2c, cm),
-                     me2_qline_ttbarg<R>(2, pa, pb, pt, ptb, pk, m, g2c, cm),
-                     me2_qline_ttbarg<R>(2, pb, pa, pt, ptb, pk, m, g2c, cm)};
+    // the light-quark channels: packed complex arithmetic in FP32
+    auto qline = [&](int kind, const v4<R>& x, const v4<R>& y) -> R {
+      if constexpr (sizeof(R) == 4)
+        return me2_qline_ttbarg_p(kind, x, y, pt, ptb, pk, m, g2c, cm);
+      else
+        return me2_qline_ttbarg<R>(kind, x, y, pt, ptb, pk, m, g2c, cm);
+    };
+    const R me[6] = {qline(0, pa, pb), qline(0, pb, pa), qline(1, pa, pb),
+                     qline(1, pb, pa), qline(2, pa, pb), qline(2, pb, pa)};
     const double sum = double(g1 * g2x) * double(me_gg) + double(lqq) * double(me[0]) + double(lqbq) * double(me[1]) +
                        double(q1 * g2x) * double(me[2]) + double(g1 * q2) * double(me[3]) +
                        double(qb1 * g2x) * double(me[4]) + double(g1 * qb2) * double(me[5]);

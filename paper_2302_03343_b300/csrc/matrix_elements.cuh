@@ -399,6 +399,144 @@ MC_D R me2_qline_ttbarg(int kind, const v4<R>& pa, const v4<R>& pb, const v4<R>&
   return total / (kind == 0 ? R(36) : R(96));
 }
 
+// ---- packed complex helpers of me2_qline_ttbarg_p (FP32): a complex
+// number is the pair (re, im); x y = re(x) y + im(x) (i y), i y =
+// (-1, 1) * swap(y), so sums of products gather the re(x) y and the
+// im(x) swap(y) terms apart and combine them once.
+MC_D f2 cx_i(f2 ra, f2 ia) { return fma2(pk2(-1.0f, 1.0f), ia, ra); }
+MC_D f2 cmul2(f2 x, f2 y) { return cx_i(mul2(bc2(lo2(x)), y), mul2(bc2(hi2(x)), swp2(y))); }
+// J^mu = rbar gamma^mu c (vector_current) for packed spinors
+MC_D void vcur_p(const sp4p& b, const sp4p& c, f2* j) {
+  const float L0r = lo2(b.l0), L0i = hi2(b.l0), L1r = lo2(b.l1), L1i = hi2(b.l1);
+  const float R0r = lo2(b.r0), R0i = hi2(b.r0), R1r = lo2(b.r1), R1i = hi2(b.r1);
+  const f2 sr0 = swp2(c.r0), sr1 = swp2(c.r1), sl0 = swp2(c.l0), sl1 = swp2(c.l1);
+  // J0 = a + d + e + f, J3 = a - d - e + f, J1 = g + h - k - l, J2 = -i (g - h - k + l)
+  // with a = L0 r0, d = L1 r1, e = R0 l0, f = R1 l1, g = L0 r1, h = L1 r0, k = R0 l1, l = R1 l0
+  const f2 ad_r = fma2(bc2(L0r), c.r0, mul2(bc2(L1r), c.r1)), ad_i = fma2(bc2(L0i), sr0, mul2(bc2(L1i), sr1));
+  const f2 ef_r = fma2(bc2(R0r), c.l0, mul2(bc2(R1r), c.l1)), ef_i = fma2(bc2(R0i), sl0, mul2(bc2(R1i), sl1));
+  const f2 af_r = fma2(bc2(L0r), c.r0, mul2(bc2(R1r), c.l1)), af_i = fma2(bc2(L0i), sr0, mul2(bc2(R1i), sl1));
+  const f2 de_r = fma2(bc2(L1r), c.r1, mul2(bc2(R0r), c.l0)), de_i = fma2(bc2(L1i), sr1, mul2(bc2(R0i), sl0));
+  j[0] = cx_i(add2(ad_r, ef_r), add2(ad_i, ef_i));
+  j[3] = cx_i(sub2(af_r, de_r), sub2(af_i, de_i));
+  const f2 gh_r = fma2(bc2(L0r), c.r1, mul2(bc2(L1r), c.r0)), gh_i = fma2(bc2(L0i), sr1, mul2(bc2(L1i), sr0));
+  const f2 kl_r = fma2(bc2(R0r), c.l1, mul2(bc2(R1r), c.l0)), kl_i = fma2(bc2(R0i), sl1, mul2(bc2(R1i), sl0));
+  j[1] = cx_i(sub2(gh_r, kl_r), sub2(gh_i, kl_i));
+  const f2 gl_r = fma2(bc2(L0r), c.r1, mul2(bc2(R1r), c.l0)), gl_i = fma2(bc2(L0i), sr1, mul2(bc2(R1i), sl0));
+  const f2 hk_r = fma2(bc2(L1r), c.r0, mul2(bc2(R0r), c.l1)), hk_i = fma2(bc2(L1i), sr0, mul2(bc2(R0i), sl1));
+  const f2 t = cx_i(sub2(gl_r, hk_r), sub2(gl_i, hk_i));
+  j[2] = mul2(pk2(1.0f, -1.0f), swp2(t));  // -i t
+}
+// a . b for complex four-vectors
+MC_D f2 cdot4_p(const f2* a, const f2* b) {
+  const f2 ra = fma2(bc2(lo2(a[0])), b[0], fma2(bc2(-lo2(a[1])), b[1],
+                fma2(bc2(-lo2(a[2])), b[2], mul2(bc2(-lo2(a[3])), b[3]))));
+  const f2 ia = fma2(bc2(hi2(a[0])), swp2(b[0]), fma2(bc2(-hi2(a[1])), swp2(b[1]),
+                fma2(bc2(-hi2(a[2])), swp2(b[2]), mul2(bc2(-hi2(a[3])), swp2(b[3])))));
+  return cx_i(ra, ia);
+}
+// a . v for a complex four-vector and a real one
+MC_D f2 cdot4_pr(const f2* a, const v4<float>& v) {
+  return fma2(bc2(v.e), a[0], fma2(bc2(-v.x), a[1], fma2(bc2(-v.y), a[2], mul2(bc2(-v.z), a[3]))));
+}
+
+// me2_qline_ttbarg in FP32 with packed complex arithmetic: the same
+// amplitudes, currents formed once per channel as there, and the colour sum
+// as sum_d Re(A_d conj(sum_e conj(C_de) ... )) written out below.
+MC_D float me2_qline_ttbarg_p(int kind, const v4<float>& pa, const v4<float>& pb, const v4<float>& pt,
+                              const v4<float>& ptb, const v4<float>& pk, float m, float g2, const float* cmat) {
+  const v4<float> k = kind == 0 ? pk : -pb;
+  const v4<float> kphys = kind == 0 ? pk : pb;
+  const v4<float> pin = kind == 2 ? -pk : pa;
+  const v4<float> pout = kind == 0 ? -pb : (kind == 1 ? pk : -pa);
+  const v4<float> q = pt + ptb, pl = pin - pout;
+  const float iq2 = 1.0f / mdot(q, q), ip2 = 1.0f / mdot(pl, pl);
+  const v4<float> s1 = pin - k, s2 = pout + k, s3 = pt + k, s4 = -(ptb + k);
+  const float i1 = 1.0f / mdot(s1, s1), i2 = 1.0f / mdot(s2, s2);
+  const float i3 = 1.0f / (mdot(s3, s3) - m * m), i4 = 1.0f / (mdot(s4, s4) - m * m);
+  const sv S1 = make_sv(s1, i1), S2 = make_sv(s2, i2), S3 = make_sv(s3, i3), S4 = make_sv(s4, i4);
+  const float m3 = m * i3, m4 = m * i4;
+  const v4<float> kpq = pl + q, kmq = k - q, mkp = -(k + pl);
+  v4<float> eps[2];
+  linear_polarisations(kphys, &eps[0], &eps[1]);
+  const sv E[2] = {make_sv(eps[0]), make_sv(eps[1])};
+  const float g3 = g2 * sqrtf(g2);
+  // -i g^3 iq2 z = (g3 iq2 im z, -g3 iq2 re z): the swap of z times this pair
+  const f2 mq = pk2(g3 * iq2, -g3 * iq2), mp = pk2(g3 * ip2, -g3 * ip2);
+  const float c4 = g3 * ip2 * iq2;
+  f2 vl[2][4], v1[2][2][4], v2[2][2][4];
+#pragma unroll 1
+  for (int ip = 0; ip < 2; ++ip) {
+    const int h1 = 2 * ip - 1, h2 = kind == 0 ? -h1 : h1;
+    const sp4p col = to_p(kind == 2 ? v_spinor(pk, 0.0f, h1) : u_spinor(pa, 0.0f, h1));
+    const sp4p row = to_p(kind == 0 ? vbar_spinor(pb, 0.0f, h2)
+                                    : (kind == 1 ? ubar_spinor(pk, 0.0f, h2) : vbar_spinor(pa, 0.0f, h2)));
+    vcur_p(row, col, vl[ip]);
+#pragma unroll
+    for (int lam = 0; lam < 2; ++lam) {
+      vcur_p(row, prop_colp(S1, 0.0f, slash_colp(E[lam], col)), v1[ip][lam]);
+      vcur_p(prop_rowp(slash_rowp(row, E[lam]), S2, 0.0f), col, v2[ip][lam]);
+    }
+  }
+  f2 vlk[2], vle[2][2];
+#pragma unroll
+  for (int ip = 0; ip < 2; ++ip) {
+    vlk[ip] = cdot4_pr(vl[ip], kmq);
+#pragma unroll
+    for (int lam = 0; lam < 2; ++lam) vle[ip][lam] = cdot4_pr(vl[ip], eps[lam]);
+  }
+  float total = 0.0f;
+#pragma unroll 1
+  for (int h3 = -1; h3 <= 1; h3 += 2) {
+    const sp4p ut = to_p(ubar_spinor(pt, m, h3));
+#pragma unroll 1
+    for (int h4 = -1; h4 <= 1; h4 += 2) {
+      const sp4p vt = to_p(v_spinor(ptb, m, h4));
+      f2 hh[4];
+      vcur_p(ut, vt, hh);
+      const f2 hhm = cdot4_pr(hh, mkp);
+#pragma unroll
+      for (int lam = 0; lam < 2; ++lam) {
+        f2 h3v[4], h4v[4];
+        vcur_p(prop_rowp(slash_rowp(ut, E[lam]), S3, m3), vt, h3v);
+        vcur_p(ut, prop_colp(S4, m4, slash_colp(E[lam], vt)), h4v);
+        const f2 hhe = cdot4_pr(hh, eps[lam]);
+        const float ke = mdot(kpq, eps[lam]);
+#pragma unroll
+        for (int ip = 0; ip < 2; ++ip) {
+          f2 amp[5];
+          amp[0] = mul2(mq, swp2(cdot4_p(v1[ip][lam], hh)));
+          amp[1] = mul2(mq, swp2(cdot4_p(v2[ip][lam], hh)));
+          amp[2] = mul2(mp, swp2(cdot4_p(vl[ip], h3v)));
+          amp[3] = mul2(mp, swp2(cdot4_p(vl[ip], h4v)));
+          amp[4] = mul2(bc2(c4), fma2(bc2(ke), cdot4_p(vl[ip], hh),
+                                      add2(cmul2(vlk[ip], hhe), cmul2(vle[ip][lam], hhm))));
+          // sum_d C_dd |A_d|^2 + 2 sum_{d<f} Re(C_df A_d conj(A_f)):
+          // per d, s_d = sum_{f>d} C_df conj(A_f), then Re(A_d s_d)
+#pragma unroll
+          for (int d = 0; d < 5; ++d) {
+            const f2 sq = mul2(amp[d], amp[d]);
+            total += cmat[2 * (d * 5 + d)] * (lo2(sq) + hi2(sq));
+            if (d < 4) {
+              // C conj(A) = (Cr ar + Ci ai, Ci ar - Cr ai) = Cr (ar, -ai) + Ci (ai, ar)
+              f2 sr = bc2(0.0f), si = bc2(0.0f);
+#pragma unroll
+              for (int f = d + 1; f < 5; ++f) {
+                sr = fma2(bc2(cmat[2 * (d * 5 + f)]), amp[f], sr);
+                si = fma2(bc2(cmat[2 * (d * 5 + f) + 1]), swp2(amp[f]), si);
+              }
+              // s = conj-combination: s = (sr.re + si.re, si.im - sr.im)
+              const f2 sd = fma2(pk2(1.0f, -1.0f), sr, mul2(pk2(1.0f, 1.0f), si));
+              const f2 p = mul2(amp[d], pk2(lo2(sd), -hi2(sd)));  // (ar sr, -ai si)
+              total += 2.0f * (lo2(p) + hi2(p));
+            }
+          }
+        }
+      }
+    }
+  }
+  return total / (kind == 0 ? 36.0f : 96.0f);
+}
+
 // Unroll factors of the helicity loops of me2_gg_ttbarg_p (1: a rolled loop,
 // which keeps the consumer warps' register count down).
 #ifndef MC_ME_UNROLL_H0
