@@ -501,18 +501,20 @@ def pp_ttbarj(M, pdf, stream, iterations=6):
     itg = W.pp_ttbarj()
     v = M.mc_vegas_init(7, NBINS, 3000, M.MC_FP32_KAHAN)
     ms, res = [], []
-    for i in range(iterations):
-        r = M.mc_vegas_iterate(v, itg, pdf, EVENTS, stream)
-        M.mc_vegas_refine(v, ALPHA, stream)
-        if i >= iterations - 3:
-            ms.append(M.mc_vegas_kernel_ms(v))
-            res.append(_iter_stats(r))
+    with ClockSampler() as clk:
+        for i in range(iterations):
+            r = M.mc_vegas_iterate(v, itg, pdf, EVENTS, stream)
+            M.mc_vegas_refine(v, ALPHA, stream)
+            if i >= iterations - 3:
+                ms.append(M.mc_vegas_kernel_ms(v))
+                res.append(_iter_stats(r))
     v.free()
     mean, sig = _combine(res)
     kms = statistics.median(ms)
     return {"workload": "p p -> t tbar + parton, 13 TeV, parton pT > 20 GeV |eta| < 2.5, hierarchical 2->3, FP32, "
                         "1e7 events per iteration", "kernel_ms": kms, "events_per_s": EVENTS / (kms / 1e3),
-            "xsec_pb": mean, "xsec_rel_err": sig / mean, "events_in_cuts": r.n_nonzero}
+            "xsec_pb": mean, "xsec_rel_err": sig / mean, "events_in_cuts": r.n_nonzero,
+            "clocks": clk.summary(int(os.environ.get("LOCAL_RANK", "0")))}
 
 
 def profile_case(case):

@@ -525,7 +525,7 @@ MC_D float me2_qline_ttbarg_p(int kind, const v4<float>& pa, const v4<float>& pb
                 si = fma2(bc2(cmat[2 * (d * 5 + f) + 1]), swp2(amp[f]), si);
               }
               // s = conj-combination: s = (sr.re + si.re, si.im - sr.im)
-              const f2 sd = fma2(pk2(1.0f, -1.0f), sr, mul2(pk2(1.0f, 1.0f), si));
+              const f2 sd = fma2(pk2(1.0f, -1.0f), sr, si);
               const f2 p = mul2(amp[d], pk2(lo2(sd), -hi2(sd)));  // (ar sr, -ai si)
               total += 2.0f * (lo2(p) + hi2(p));
             }
