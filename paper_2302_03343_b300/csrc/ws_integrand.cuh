@@ -19,14 +19,18 @@
 //    shared-memory histogram of w^2.
 // Slots pass between the roles through mbarriers (full: 32 producer-lane
 // arrivals; empty: 32 consumer-lane arrivals).  Producer warp p owns the
-// slots Sp .. Sp + S - 1 (S = ws_slots(process)), used in turn; with equal counts consumer warp c takes
-// producer c's slots (the general mapping is below).  The assignment of
+// slots Sp .. Sp + S - 1 (S = ws_slots(process)), used in turn; with equal
+// counts consumer warp c takes producer c's slots (the general mapping is
+// below).  The assignment of
 // events to lanes is fixed by the launch shape, so the sums are
 // deterministic for a given grid.  A producer ends its stream with a partial
 // slot and one end marker (count -1) for each consumer it feeds.  Sixteen
 // warps of 128 registers at launch, rebalanced to 88 (producers) and 168
 // (consumers) with setmaxnreg, measured fastest among the 4+8, 8+4 and 8+8
-// shapes on B300.
+// shapes on B300.  The compiled code of both roles is held to the launch's
+// 128 registers, so the consumers' |M|^2 runs on register spills, which
+// must stay in L1: the shared memory of a block is kept small for that
+// (see ws_rows_in_smem).
 //
 // Every wait is bounded (kWsWaitNs of %globaltimer); a warp that gives up
 // stops, the block poisons its partial sums with NaN and, when the launch
