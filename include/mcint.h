@@ -512,6 +512,11 @@ int mc_gemm_bf16_rs(int M, int N, int K, int bn, int epilogue, const void* a, in
  * (serialise them on one stream).  Each launch writes every slot it later
  * reads, so nothing in the array needs clearing between calls.
  *
+ * Processes: MC_EE_MUMU, MC_PP_TTBAR, MC_GG_TTBARG, MC_GAUSS,
+ * MC_GG_TTBARG_7D and MC_PP_TTBARJ, validated exactly as mc_vegas_iterate
+ * validates them.  MC_GG_TTBARG_MC is rejected with EINVAL: its channel
+ * probabilities and update sums belong to a VEGAS handle.
+ *
  * Inputs (caller-owned): itg (host), pdf (an mc_pdf loaded earlier, or NULL
  * for processes without hadrons), the grid as device arrays edges64 (FP64)
  * and, for MC_FP32_KAHAN, edges32 (FP32), both [ndim][nbins+1]; seed,
@@ -522,7 +527,11 @@ int mc_gemm_bf16_rs(int M, int N, int K, int bn, int epilogue, const void* a, in
  * hist_n[ndim][nbins] are accumulated into (zero them to start a fresh
  * histogram); *sums receives the compensated sums of the launch.
  * Asynchronous on `stream`; the outputs are valid once the stream reaches
- * the end of the call.
+ * the end of the call.  There is no status word: if a bounded wait inside
+ * the warp-specialised FP32 gg -> t tbar g kernel gives up (where
+ * mc_vegas_iterate returns MC_ETIMEOUT), the call still returns MC_OK and
+ * the timeout shows in *sums as sum_hi = sum2_hi = NaN with n_bad increased
+ * by one per block that gave up.
  */
 #define MC_NOALLOC_MAX_BLOCKS 4096
 typedef struct {
@@ -546,9 +555,10 @@ int mc_vegas_iterate_noalloc(const mc_integrand* itg, mc_pdf pdf, int ndim, int 
  * maps u = 2 x_A - 1 through dense layers of `hidden` units with ReLU to
  * 2 * bins + 1 logits per transformed coordinate (bins width logits ->
  * softmax; bins + 1 vertex-height logits -> exp, normalised to unit area).
- * The first dense layer runs in FP32; the three hidden-width layers run on
- * the tcgen05 tensor cores with BF16 weights and activations and FP32
- * accumulation; the splines and log-determinants are FP32.
+ * Every dense layer runs on the tcgen05 tensor cores with BF16 weights and
+ * activations and FP32 accumulation; the first layer's bias b1 enters as a
+ * BF16 weight on a constant input of one (b2..b4 are added in FP32); the
+ * splines and log-determinants are FP32.
  *
  * Parameters (host, packed FP32): for each layer in order, W1 [hidden x n_A],
  * b1 [hidden], W2 [hidden x hidden], b2, W3 [hidden x hidden], b3,

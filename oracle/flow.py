@@ -9,7 +9,7 @@ trains networks made of dense layers y = phi(W x + b) (Sec. "Deep learning")
 with Adam (Sec. "Optimizers": m_t, v_t, bias-corrected m_hat, v_hat, update
 theta -= eta m_hat / (sqrt(v_hat) + eps)).  It prints no flow; the sampler is
 the piecewise-quadratic coupling flow of Mueller et al. ("Neural Importance
-Sampling", 2019), readings listed in the design doc:
+Sampling", 2019), with these readings of what the thesis leaves open:
 
 * D dimensions, L coupling layers; layer l transforms the dimensions with
   d % 2 == l % 2 and conditions on the others.
@@ -25,10 +25,12 @@ Sampling", 2019), readings listed in the design doc:
 * Loss (forward KL with importance weights, x sampled from the flow and held
   fixed): L = -sum_i w_i log q(x_i) / sum_i w_i, w_i = |f(x_i)| / q(x_i).
 
-`bf16=True` rounds what the CUDA path holds in BF16 (the inputs u, the
-weights and the first layer's bias of the dense layers, and the hidden
-activations after each ReLU) so the GPU can be compared with the same
-rounding.
+`bf16=True` rounds to BF16 (round to nearest even) every operand the CUDA
+path feeds its tensor cores: the conditioner input u, the weights W1..W4, the
+first layer's bias b1 (a weight on a constant input of one there), and the
+hidden activations after each ReLU.  b2..b4 are added in FP32 and every
+product accumulates in FP32, so the GPU can be compared with the same
+roundings.
 """
 import math
 

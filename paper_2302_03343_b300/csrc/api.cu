@@ -47,7 +47,8 @@ int process_ndim(const mc_integrand* itg) {
     case MC_EE_MUMU: return 2;
     case MC_PP_TTBAR: return 4;
     case MC_GG_TTBARG: return 14;
-    case MC_GAUSS: return itg->gauss_dim;
+    // the Gaussian kernels loop over at most 16 dimensions
+    case MC_GAUSS: return itg->gauss_dim >= 1 && itg->gauss_dim <= 16 ? itg->gauss_dim : -1;
     case MC_GG_TTBARG_7D: return 7;
     case MC_GG_TTBARG_MC: return mc::kChannelGridDims;
     case MC_PP_TTBARJ: return 7;
@@ -387,15 +388,17 @@ int mc_vegas_set_gid(mc_vegas v, uint32_t gid) {
 // sampler (flow.cu).
 int mc::fill_process_args(const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
   if (!itg) return fail(MC_EINVAL, "NULL integrand");
-  int dev;
-  if (int rc = current_device(&dev)) return rc;
   if (itg->proc < MC_EE_MUMU || itg->proc > MC_PP_TTBARJ) return fail(MC_EINVAL, "unknown process %d", itg->proc);
+  if (itg->proc == MC_GAUSS && process_ndim(itg) < 1)
+    return fail(MC_EINVAL, "gauss_dim %d outside 1..16", itg->gauss_dim);
   const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG || itg->proc == MC_GG_TTBARG_7D ||
                         itg->proc == MC_GG_TTBARG_MC || itg->proc == MC_PP_TTBARJ;
   if ((itg->proc == MC_GG_TTBARG_MC || itg->proc == MC_PP_TTBARJ) && !(itg->ptcut_g > 0.0))
     return fail(MC_EINVAL, "process %d needs ptcut_g > 0", itg->proc);
   if (!(itg->sqrt_s > 0.0) && itg->proc != MC_GAUSS) return fail(MC_EINVAL, "sqrt_s must be positive");
   if (itg->proc == MC_GAUSS && !(itg->gauss_sigma > 0.0)) return fail(MC_EINVAL, "gauss_sigma must be positive");
+  int dev;
+  if (int rc = current_device(&dev)) return rc;
   std::memset(a, 0, sizeof(*a));
   a->prm = {itg->proc, itg->gauss_dim, itg->sqrt_s, itg->m_top, itg->alpha, itg->alpha_s, itg->mz, itg->gz,
             itg->sw2, itg->mu_f, itg->ptcut_g, itg->etacut_g, itg->gauss_sigma, itg->gev2pb};
@@ -442,11 +445,12 @@ extern "C" {
 // Validates an integrand against a grid and fills the kernel arguments.
 static int prepare(mc_vegas v, const mc_integrand* itg, mc_pdf pdf, KernelArgs* a) {
   if (!v || !itg) return fail(MC_EINVAL, "NULL handle or integrand");
+  const int nd = process_ndim(itg);
+  if (nd < 1) return fail(MC_EINVAL, "process %d: bad dimension (gauss_dim %d)", itg->proc, itg->gauss_dim);
+  if (nd != v->ndim) return fail(MC_EINVAL, "process needs %d dimensions, grid has %d", nd, v->ndim);
   int dev;
   if (int rc = current_device(&dev)) return rc;
   if (dev != v->device) return fail(MC_EINVAL, "grid lives on device %d, current device is %d", v->device, dev);
-  const int nd = process_ndim(itg);
-  if (nd != v->ndim) return fail(MC_EINVAL, "process needs %d dimensions, grid has %d", nd, v->ndim);
   if (int rc = mc::fill_process_args(itg, pdf, a)) return rc;
   a->ndim = v->ndim;
   a->nbins = v->nbins;

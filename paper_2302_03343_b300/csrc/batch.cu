@@ -609,14 +609,10 @@ int mc_batch_create(int n, const mc_integrand* itgs, const int64_t* nevents, mc_
   bool have_mu = false;
   for (int i = 0; i < n; ++i) {
     const mc_integrand& t = itgs[i];
-    int nd = -1;
-    switch (t.proc) {
-      case MC_EE_MUMU: nd = 2; break;
-      case MC_PP_TTBAR: nd = 4; break;
-      case MC_GG_TTBARG: nd = 14; break;
-      case MC_GAUSS: nd = t.gauss_dim; break;
-      case MC_GG_TTBARG_7D: nd = 7; break;
-    }
+    // the batch kernels run these five processes (Gaussian: gauss_dim 1..16)
+    const bool supported = t.proc == MC_EE_MUMU || t.proc == MC_PP_TTBAR || t.proc == MC_GG_TTBARG ||
+                           t.proc == MC_GAUSS || t.proc == MC_GG_TTBARG_7D;
+    const int nd = supported ? mc::process_dim(&t) : -1;
     if (nd < 1 || nd > MC_MAX_DIM || nevents[i] < 0) {
       mc_batch_free(b);
       return bfail(MC_EINVAL, "mc_batch_create: bad integrand or event count");

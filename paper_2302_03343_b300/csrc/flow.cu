@@ -4,10 +4,12 @@
 // Flow: L piecewise-quadratic coupling layers (flow_spline.cuh) over the unit
 // cube; layer l transforms the coordinates d with d % 2 == l % 2 and
 // conditions on the others through a dense network u = 2 x_A - 1 -> 256 ->
-// 256 -> 256 -> (2K + 1) logits per transformed coordinate, with ReLU.  The
-// first dense layer (K = d_A) runs on the CUDA cores in FP32; the three
-// 256-wide layers run on the tcgen05 tensor cores (tc_gemm.cu, persistent
-// B-resident kernel) with BF16 operands and FP32 accumulation.
+// 256 -> 256 -> (2K + 1) logits per transformed coordinate, with ReLU.  All
+// four dense layers run on the tcgen05 tensor cores with BF16 operands and
+// FP32 accumulation; the first one (K = d_A) takes the input (u, 1, 0, ..)
+// padded to 16 columns against W1e = (W1 | b1 | 0), so its bias is a BF16
+// weight on a constant input of one.  The splines and log-determinants are
+// FP32.
 //
 // Sampling (thesis Sec. "Importance sampling", eq. mc_est_is): Philox
 // uniforms z -> flow forward -> x, log q(x) -> integrand at x -> w = f / q ->
@@ -479,9 +481,10 @@ __global__ void to_bf16_kernel(const float* W, int rows, int cols, __nv_bfloat16
 // ---------------------------------------------------------------------------
 // Fused coupling layer (K = 32 bins): one persistent kernel per layer with
 // two 128-event tiles in flight per SM.  For each tile the conditioner runs
-// without leaving the SM: dense1 on the CUDA cores writes h1 (BF16) into the
-// tile's shared-memory operand buffer in the 128-byte-swizzled K-major layout
-// the tensor cores read; three tcgen05 products (W2, W3, then W4 in
+// without leaving the SM: the compute warps write the first layer's input
+// (u, 1, 0, ..) (BF16) into the tile's shared-memory operand buffer in the
+// 128-byte-swizzled K-major layout the tensor cores read; four tcgen05
+// products (W1e, W2, W3, then W4 in
 // two-coordinate sub-blocks) stream the weights from L2 through a TMA ring
 // into the tile's 256 TMEM columns, and the tile's compute warps turn each
 // accumulator into the next operand (bias, ReLU, BF16) in the same buffer or

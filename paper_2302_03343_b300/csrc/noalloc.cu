@@ -34,17 +34,6 @@ cudaError_t scratch_for(int dev, mc::BlockPartial** out) {
   return cudaSuccess;
 }
 
-int ndim_of(const mc_integrand* itg) {
-  switch (itg->proc) {
-    case MC_EE_MUMU: return 2;
-    case MC_PP_TTBAR: return 4;
-    case MC_GG_TTBARG: return 14;
-    case MC_GAUSS: return itg->gauss_dim;
-    case MC_GG_TTBARG_7D: return 7;
-  }
-  return -1;
-}
-
 int reject(int code, const char* msg) {
   mc::set_last_error((std::string("mc_vegas_iterate_noalloc: ") + msg).c_str());
   return code;
@@ -60,42 +49,33 @@ extern "C" int mc_vegas_iterate_noalloc(const mc_integrand* itg, mc_pdf pdf, int
   if (prec != MC_FP64 && prec != MC_FP32_KAHAN) return reject(MC_EINVAL, "bad precision");
   if (prec == MC_FP32_KAHAN && !edges32) return reject(MC_EINVAL, "FP32 mode needs edges32");
   if (ndim < 1 || ndim > MC_MAX_DIM || nbins < 2 || nbins > MC_MAX_BINS) return reject(MC_EINVAL, "bad grid shape");
-  if (ndim_of(itg) != ndim) return reject(MC_EINVAL, "grid dimension does not match the process");
+  // the three-channel process keeps its channel probabilities and their
+  // update sums in a VEGAS handle, which this entry point does not take
+  if (itg->proc == MC_GG_TTBARG_MC)
+    return reject(MC_EINVAL, "MC_GG_TTBARG_MC is not supported (it needs a VEGAS handle; use mc_vegas_iterate)");
+  const int nd = mc::process_dim(itg);
+  if (nd < 1) return reject(MC_EINVAL, "unknown process or gauss_dim outside 1..16");
+  if (nd != ndim) return reject(MC_EINVAL, "grid dimension does not match the process");
   if (nevents < 0) return reject(MC_EINVAL, "negative event count");
   if (blocks < 0 || blocks > MC_NOALLOC_MAX_BLOCKS)
     return reject(MC_EINVAL, "blocks exceeds MC_NOALLOC_MAX_BLOCKS (the size of the static scratch)");
   if (gid > 255) return reject(MC_EINVAL, "gid outside 0..255");
-  const bool hadronic = itg->proc == MC_PP_TTBAR || itg->proc == MC_GG_TTBARG || itg->proc == MC_GG_TTBARG_7D;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return reject(MC_ECUDA, "no device");
   mc::BlockPartial* scratch = nullptr;
   if (scratch_for(dev, &scratch) != cudaSuccess) return reject(MC_ECUDA, "cudaGetSymbolAddress failed");
 
+  // the same validation and process arguments as mc_vegas_iterate (host
+  // work only: it allocates nothing on the device)
   mc::KernelArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.prm = {itg->proc, itg->gauss_dim, itg->sqrt_s, itg->m_top, itg->alpha, itg->alpha_s, itg->mz, itg->gz,
-           itg->sw2, itg->mu_f, itg->ptcut_g, itg->etacut_g, itg->gauss_sigma, itg->gev2pb};
+  if (int rc = mc::fill_process_args(itg, pdf, &a)) {
+    const std::string msg = mc_last_error();
+    return reject(rc, msg.c_str());
+  }
   a.ndim = ndim;
   a.nbins = nbins;
   a.edges64 = edges64;
   a.edges32 = edges32;
-  if (hadronic) {
-    if (!pdf || pdf->device != dev) return reject(MC_EINVAL, "process needs a PDF on the current device");
-    const double lq = std::log(itg->mu_f * itg->mu_f);
-    if (!(lq >= pdf->logq2.front() && lq <= pdf->logq2.back())) return reject(MC_EINVAL, "mu_f outside the PDF grid");
-    a.pdf = pdf->dev();
-    a.logq2_f = lq;
-    a.fl[0] = pdf->index(21);
-    if (a.fl[0] < 0) return reject(MC_EINVAL, "PDF has no gluon");
-    if (itg->proc == MC_PP_TTBAR)
-      for (int q = 1; q <= 5; ++q) {
-        a.fl[q] = pdf->index(q);
-        a.fl[q + 5] = pdf->index(-q);
-        if (a.fl[q] < 0 || a.fl[q + 5] < 0) return reject(MC_EINVAL, "PDF lacks a quark flavour");
-      }
-  }
-  a.w0_coef3 = std::pow(2.0 * M_PI, -5.0) * std::pow(M_PI / 2.0, 2.0) / 2.0;
-  a.e2eta = std::exp(2.0 * itg->etacut_g);
   a.seed = seed;
   a.iteration = iteration;
   a.gid = gid;

@@ -1,6 +1,6 @@
 // Internal: inline-PTX building blocks for the tcgen05 kernels (tensor
 // memory, mbarriers, TMA, UMMA shared-memory descriptors); shared by the GEMM
-// (tc_gemm.cu) and the fused flow layer (flow_fused.cu).
+// (tc_gemm.cu) and the fused flow layers (flow.cu).
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>

@@ -48,14 +48,12 @@ def test_validation_without_device_work(L):
     with pytest.raises(M.McError) as e:
         M.mc_vegas_init(0, 50, 0, M.MC_FP64)
     assert e.value.code == M.MC_EINVAL
-    with pytest.raises(M.McError):
-        M.mc_vegas_init(17, 50, 0, M.MC_FP64)
-    with pytest.raises(M.McError):
-        M.mc_vegas_init(4, 1, 0, M.MC_FP64)
-    with pytest.raises(M.McError):
-        M.mc_vegas_init(4, 257, 0, M.MC_FP64)
-    with pytest.raises(M.McError):
-        M.mc_vegas_init(4, 50, 0, 7)
+    # MC_MAX_DIM (17) is the three-channel grid; one more is rejected
+    for args in ((M.MC_MAX_DIM + 1, 50, 0, M.MC_FP64), (4, 1, 0, M.MC_FP64), (4, 257, 0, M.MC_FP64),
+                 (4, 50, 0, 7)):
+        with pytest.raises(M.McError) as e:
+            M.mc_vegas_init(*args)
+        assert e.value.code == M.MC_EINVAL, args
     g = W.synthetic_pdf_grid(0)
     bad = W.PdfGrid(x=g.x[::-1].copy(), q=g.q, pids=g.pids, xf=g.xf, params=g.params)
     with pytest.raises(M.McError) as e:
@@ -66,3 +64,16 @@ def test_validation_without_device_work(L):
     with pytest.raises(M.McError) as e:
         M.mc_pdf_load(W.PdfGrid(x=g.x, q=g.q, pids=g.pids, xf=xf, params=g.params))
     assert "non-finite" in str(e.value)
+
+
+def test_gauss_dim_is_bounded_before_device_work(L):
+    """The Gaussian kernels loop over at most 16 dimensions: gauss_dim 0 and 17
+    are rejected as invalid input by every entry point that reads it, before
+    any device call (so the answer is the same with or without a GPU)."""
+    for d in (0, 17):
+        with pytest.raises(M.McError) as e:
+            M.mc_integrate(W.gauss(d), None, 2, 1000)
+        assert e.value.code == M.MC_EINVAL, d
+        with pytest.raises(M.McError) as e:
+            M.mc_launch_shape(W.gauss(d), M.MC_FP64, 1000)
+        assert e.value.code == M.MC_EINVAL, d

@@ -32,9 +32,19 @@ def gpdf(pdf_grid):
     return M.mc_pdf_load(pdf_grid)
 
 
-@pytest.mark.parametrize("itg,prec,n", [(W.pp_ttbar(), M.MC_FP64, 30000),
-                                        (W.gg_ttbarg(), M.MC_FP32_KAHAN, 200000)])
-def test_noalloc_matches_iterate_on_two_calls(gpdf, itg, prec, n):
+# blocks = 0: the library picks the grid; 7: a caller's small grid; MC_NOALLOC_MAX_BLOCKS:
+# the largest grid the scratch holds (for the warp-specialised FP32 gg -> ttg kernel, sized
+# for one block per SM, that is many more blocks than SMs, most of them without events).
+# The Philox counter of an event does not depend on the grid, so every shape must agree with
+# mc_vegas_iterate.
+@pytest.mark.parametrize("itg,prec,n,blocks", [(W.pp_ttbar(), M.MC_FP64, 30000, 0),
+                                               (W.pp_ttbar(), M.MC_FP64, 30000, 7),
+                                               (W.pp_ttbar(), M.MC_FP64, 30000, M.MC_NOALLOC_MAX_BLOCKS),
+                                               (W.gg_ttbarg(), M.MC_FP32_KAHAN, 200000, 0),
+                                               (W.gg_ttbarg(), M.MC_FP32_KAHAN, 200000, 7),
+                                               (W.gg_ttbarg(), M.MC_FP32_KAHAN, 200000, M.MC_NOALLOC_MAX_BLOCKS),
+                                               (W.pp_ttbarj(), M.MC_FP32_KAHAN, 30000, 0)])
+def test_noalloc_matches_iterate_on_two_calls(gpdf, itg, prec, n, blocks):
     nd, nb, seed, gid = itg.ndim(), 50, 21, 3
     rng = np.random.default_rng(1)
     edges = np.sort(np.concatenate([np.zeros((nd, 1)), rng.uniform(size=(nd, nb - 1)), np.ones((nd, 1))], axis=1),
@@ -51,8 +61,12 @@ def test_noalloc_matches_iterate_on_two_calls(gpdf, itg, prec, n):
     for it in (5, 6):
         hw2.zero_()
         hn.zero_()
-        M.mc_vegas_iterate_noalloc(itg, gpdf, nd, nb, e64, e32, prec, seed, it, gid, n, 0, hw2, hn, sums)
         torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        M.mc_vegas_iterate_noalloc(itg, gpdf, nd, nb, e64, e32, prec, seed, it, gid, n, blocks, hw2, hn, sums)
+        torch.cuda.synchronize()
+        if it == 6:  # after the first call (which may load the kernels' code): no device memory taken
+            assert torch.cuda.mem_get_info()[0] == free0
         s = sums.cpu().numpy()
         counts = s.view(np.int64)[5:8]
         M.mc_vegas_set_iteration(ref, it)
@@ -84,3 +98,20 @@ def test_noalloc_rejects_oversized_launch(gpdf):
         M.mc_vegas_iterate_noalloc(itg, None, 4, 10, e64, None, M.MC_FP64, 0, 0, 0, 1000,
                                    M.MC_NOALLOC_MAX_BLOCKS + 1, hw2, hn, sums)
     assert "MC_NOALLOC_MAX_BLOCKS" in str(e.value)
+
+
+def test_noalloc_rejects_unsupported_input(gpdf):
+    """The three-channel process needs a VEGAS handle (its channel probabilities
+    and update sums), and the Gaussian kernels stop at 16 dimensions: both are
+    refused with EINVAL and a message that says why."""
+    dev = torch.device("cuda")
+    for itg, nd in ((W.gg_ttbarg_mc(), 17), (W.gauss(17), 17)):
+        e64 = torch.tensor(W.uniform_grid(nd, 10), dtype=torch.float64, device=dev)
+        hw2 = torch.zeros((nd, 10), dtype=torch.float64, device=dev)
+        hn = torch.zeros((nd, 10), dtype=torch.int32, device=dev)
+        sums = torch.zeros(8, dtype=torch.float64, device=dev)
+        with pytest.raises(M.McError) as e:
+            M.mc_vegas_iterate_noalloc(itg, gpdf, nd, 10, e64, e64.float(), M.MC_FP64, 0, 0, 0, 1000, 0, hw2, hn,
+                                       sums)
+        assert e.value.code == M.MC_EINVAL
+        assert ("MC_GG_TTBARG_MC" in str(e.value)) == (itg.proc == M.MC_GG_TTBARG_MC)
