@@ -135,38 +135,58 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(seconds=15.0, iteration=3):
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def golden(name):
+    """Stored oracle values (tests/golden/, written by tests/golden/make_golden.py)."""
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def cpu_baseline(seconds=15.0):
     """The FP64 oracle as it stands, timed on the host cores over a bounded
-    sample of the same workload (fresh uniform grid, one iteration)."""
+    sample of the same workload: the first events of the stored g g -> t tbar g
+    iteration (the oracle-adapted 50-bin grid, FP32-mode uniforms evaluated in
+    FP64).  Returns the baseline and the oracle's weights of the sample, which
+    the per-event check compares with the GPU's weights of the same events."""
     import oracle as O
+    g = golden("c3_ggttg_iteration.json")
+    p = g["params"]
     grid = W.synthetic_pdf_grid(0)
     pdf = O.Pdf(grid)
     itg = W.gg_ttbarg()
-    edges = W.uniform_grid(14, NBINS)
+    edges = np.array(g["edges"])
     cores = os.cpu_count() or 1
+
+    def run(first, n):
+        return O.weights(itg, pdf, edges, 1, p["seed"], p["iteration"], p["gid"], first, n, nthreads=cores)
+
     # calibrate on samples of at least a second (thread start-up dominates
     # smaller ones), then time a sample of about `seconds`
-    n0, dt = 200 * cores, 0.0
+    n0, dt, parts = 200 * cores, 0.0, []
     while True:
         t0 = time.perf_counter()
-        O.iterate(itg, pdf, edges, 1, 0, iteration, 0, 0, n0, nthreads=cores)
+        parts = [run(0, n0)]
         dt = time.perf_counter() - t0
         if dt >= 1.0 or n0 >= 1 << 30:
             break
         n0 *= 4
     n = max(n0, int(n0 * seconds / max(dt, 1e-3)))
     t0 = time.perf_counter()
-    O.iterate(itg, pdf, edges, 1, 0, iteration, 0, n0, n, nthreads=cores)
+    parts.append(run(n0, n))
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} gg->ttg events (one iteration on a uniform 50-bin grid, FP64 oracle, "
-                      f"{cores} threads, {dt:.1f} s)"}
+    return ({"value": n / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+             "sample": f"events {n0}..{n0 + n - 1} of one gg->ttg iteration (seed {p['seed']}, iteration "
+                       f"{p['iteration']}, the oracle-adapted 50-bin grid, FP32-mode uniforms, FP64 oracle), "
+                       f"{cores} threads, {dt:.1f} s"},
+            np.concatenate(parts))
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    base = cpu_baseline(seconds=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
+    base, _ = cpu_baseline(seconds=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
     # each step: a bounded sample of the same workload on all host cores
     import oracle as O
     grid = W.synthetic_pdf_grid(0)
@@ -573,6 +593,97 @@ def profile_case(case):
     print("profile case done:", case)
 
 
+def fma_peaks(M, stream, reps=5):
+    """FP32 and FP64 FMA throughput of this GPU (mc_fma_peak: a
+    full-occupancy grid of independent FMA chains), best of `reps` launches
+    timed with CUDA events: the measured denominators of the integrand
+    kernels' roofline."""
+    import torch
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    threads = props.multi_processor_count * props.max_threads_per_multi_processor
+    out = torch.empty(threads, dtype=torch.float32, device="cuda")
+    res = {}
+    for kind, name, iters in ((0, "fp32_fma", 1 << 16), (1, "fp32x2_fma", 1 << 15), (2, "fp64_fma", 1 << 11)):
+        M.mc_fma_peak(kind, iters, out, stream)  # warm-up
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flop = M.mc_fma_peak(kind, iters, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        res[name] = {"tflops": flop / (best / 1e3) / 1e12, "ms": best, "flop": flop}
+    res["fp32_tflops"] = max(res["fp32_fma"]["tflops"], res["fp32x2_fma"]["tflops"])
+    res["fp64_tflops"] = res["fp64_fma"]["tflops"]
+    res["how"] = ("mc_fma_peak: SMs x 2048 threads, 8 independent chains of dependent FMAs per thread, "
+                  "2 FLOP per lane operation, best of %d launches (CUDA events)" % reps)
+    return res
+
+
+def c2_pp_ttbar(M, pdf, stream):
+    """Config: plain FP64 VEGAS of p p -> t tbar (gg + q qbar) at 13 TeV, 4
+    dims, 50 bins, 10 iterations x 1e6 events, seed 0, from a uniform grid,
+    through mc_integrate (GPU time from its CUDA events); the combined
+    integral against the oracle's run of the same configuration and against
+    the closed-form cross section of the master formula (stored values)."""
+    g = golden("c2_pp_ttbar.json")
+    p = g["params"]
+    M.mc_integrate(W.pp_ttbar(), pdf, 1, p["nevents"], nbins=p["nbins"], seed=p["seed"], prec=M.MC_FP64,
+                   stream=stream)  # warm-up
+    res, _ = M.mc_integrate(W.pp_ttbar(), pdf, p["niter"], p["nevents"], nbins=p["nbins"], seed=p["seed"],
+                            gid=p["gid"], prec=M.MC_FP64, alpha=p["alpha"], stream=stream)
+    ref, cf = g["oracle"], g["closed_form"]["sigma_pb"]
+    n = p["niter"] * p["nevents"]
+    return {"workload": g["config"], "gpu_ms": res.gpu_ms, "events_per_s": n / (res.gpu_ms / 1e3),
+            "mean_pb": res.mean, "sigma_pb": res.sigma, "chi2_dof": res.chi2_dof,
+            "oracle_mean_pb": ref["mean_pb"], "rel_diff_vs_oracle": (res.mean - ref["mean_pb"]) / ref["mean_pb"],
+            "closed_form_pb": cf, "pull_vs_closed_form": (res.mean - cf) / res.sigma}
+
+
+def oracle_check(M, pdf, stream, keep=4_000_000):
+    """Config: one full FP32 iteration of the benchmark workload (g g -> t tbar
+    g, 1e7 events) on the grid the oracle adapted, against the FP64 oracle's
+    iteration at the identical 23-bit points (stored values): the relative
+    error of the integral, events in the cuts, w_max, and whether the bin
+    counts are bit-exact.  Returns the result and the GPU's weights of the
+    first `keep` events (host) for the per-event comparison with the
+    CPU-baseline sample."""
+    import torch
+    g = golden("c3_ggttg_iteration.json")
+    p = g["params"]
+    n = p["nevents"]
+    v = M.mc_vegas_init(14, p["nbins"], p["seed"], M.MC_FP32_KAHAN)
+    M.mc_vegas_set_grid(v, np.array(g["edges"]))
+    M.mc_vegas_set_iteration(v, p["iteration"])
+    M.mc_vegas_set_gid(v, p["gid"])
+    w = torch.empty(n, dtype=torch.float64, device="cuda")
+    r = M.mc_vegas_iterate_weights(v, W.gg_ttbarg(), pdf, n, w, stream)
+    _, cnt = M.mc_vegas_get_hist(v)
+    v.free()
+    ref = g["oracle"]
+    out = {"workload": g["config"], "events": n, "integral_pb": r.sum / n, "oracle_integral_pb": ref["sum"] / n,
+           "integral_rel_err": (r.sum - ref["sum"]) / ref["sum"], "in_cuts": r.n_nonzero,
+           "oracle_in_cuts": ref["n_nonzero"], "wmax_rel_err": (r.wmax - ref["wmax"]) / ref["wmax"],
+           "bin_counts_bit_exact": bool(np.array_equal(cnt, np.array(ref["hist_n"], dtype=np.uint32)))}
+    return out, w[:keep].cpu().numpy()
+
+
+def per_event_stats(w_gpu, w_oracle):
+    """Relative per-event errors of the FP32 weights against FP64 (events in
+    the cuts on both sides) and the events whose cut decision differs."""
+    k = min(len(w_gpu), len(w_oracle))
+    wg, wo = w_gpu[:k], w_oracle[:k]
+    both = (wg != 0) & (wo != 0)
+    e = np.abs(wg[both] - wo[both]) / np.abs(wo[both])
+    return {"events": int(k), "compared": int(both.sum()), "median": float(np.median(e)),
+            "p99": float(np.quantile(e, 0.99)), "max": float(e.max()),
+            "cut_flips": int(np.count_nonzero((wg != 0) != (wo != 0)))}
+
+
 def time_to_target(M, pdf, stream, seed=0):
     """GPU time (CUDA events around every launch of the arm) from the first
     launch to the end of the first iteration whose combined relative error is
@@ -731,6 +842,7 @@ def run_native(args, rank, world):
     if rank != 0:
         return
     value = job_rate(args.events, args.steps, world, total_ms)
+    measured = fma_peaks(M, stream)
     pk = peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = pk.get("sm_max_mhz", 2032.0)
@@ -739,9 +851,13 @@ def run_native(args, rank, world):
     mean_nnz = sum(nnz) / len(nnz)
     if FLOP_PER_EVENT:
         achieved = FLOP_PER_EVENT * mean_nnz / (mean_kernel_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": TRAFFIC_BYTES,
-                "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+        peak = measured["fp32_tflops"]
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": TRAFFIC_BYTES,
+                "peak_source": "measured (fma_peaks: the larger of the f32 and f32x2 FMA rates)",
+                "peak_nominal": fp32_peak,
+                "frac_of_nominal": achieved / fp32_peak,
+                "nominal_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                 "frac_of_mix_bound": achieved / (fp32_peak * FLOP_PER_LANE_OP / 2.0),
                 "mix_bound_note": "the same peak times the kernel's FLOP per FP32 lane operation / 2 "
                                   f"({FLOP_PER_LANE_OP:.3f} / 2): the rate if every lane slot issued its mix"}
@@ -764,10 +880,14 @@ def run_native(args, rank, world):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 3 * args.steps,
             "roofline": roof,
+            "fma_peaks": measured,
             "last_iteration": {"mean_pb": mean, "rel_err": (var ** 0.5) / abs(mean) if mean else None,
                                "n_nonzero": r_last.n_nonzero, "unweighting_eff": mean / r_last.wmax
                                if r_last.wmax > 0 else None}}
+    w_check = None
     if not args.no_time_to_target:
+        line["c2"] = c2_pp_ttbar(M, pdf, stream)
+        line["oracle_check"], w_check = oracle_check(M, pdf, stream)
         line["time_to_target"] = time_to_target(M, pdf, stream)
         line["batch16"] = batch16(M, pdf, stream)
         line["pdf_members"] = pdf_members(M, stream)
@@ -776,7 +896,9 @@ def run_native(args, rank, world):
         line["samplers"] = samplers(M, pdf, stream)
         line["pp_ttbarj"] = pp_ttbarj(M, pdf, stream)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"], w_oracle = cpu_baseline()
+        if w_check is not None:
+            line["oracle_check"]["per_event"] = per_event_stats(w_check, w_oracle)
     print(json.dumps(line), flush=True)
 
 

@@ -426,6 +426,18 @@ int mc_vegas_kernel_ms(mc_vegas v, float* ms);
  * library would use for a process (blocks, threads per block). */
 int mc_launch_shape(const mc_integrand* itg, int prec, int64_t nevents, int* blocks, int* threads);
 
+/* FMA throughput of the CUDA cores, the denominator of the integrand
+ * kernels' roofline (measured rather than derived from unit counts; the
+ * thesis has no counterpart).  Launches, asynchronously on `stream`, a
+ * full-occupancy grid (SMs x max threads per SM / 256 blocks of 256 threads)
+ * whose every thread runs 8 independent chains of `iters` dependent fused
+ * multiply-adds: kind 0 fma.rn.f32, kind 1 fma.rn.f32x2 (packed pairs),
+ * kind 2 fma.rn.f64.  *flop receives the launch's floating-point operations
+ * (2 per FMA lane operation); the caller times the launch with events on
+ * `stream`.  out (device, caller-owned) receives one float per thread:
+ * out_len must be at least the grid's thread count (EINVAL otherwise). */
+int mc_fma_peak(int kind, int iters, float* out, int64_t out_len, double* flop, void* stream);
+
 /* ---------------------------------------------------------------- batches
  * Many integrands of uneven dimension and event count in one persistent
  * launch per iteration.  The thesis evaluates one integrand at a time over

@@ -122,6 +122,9 @@ def lib():
         L.orc_event.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
                                 ctypes.POINTER(EventRecord)]
+        L.orc_weights.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
+                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_int, _dp]
         L.orc_iterate.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
                                   ctypes.c_int64, ctypes.c_int, ctypes.POINTER(IterResult), _dp, _u32p]
@@ -482,6 +485,16 @@ def iterate(itg, pdf, edges, prec, seed, iteration, gid, first, n, nthreads=0):
                       seed, iteration, gid, first, n, nthreads, ctypes.byref(res), _ptr(hist), _ptr(cnt, _u32p))
     return dict(sum=res.sum, sum2=res.sum2, n=res.n, n_nonzero=res.n_nonzero, wmax=res.wmax,
                 hist_w2=hist, hist_n=cnt)
+
+
+def weights(itg, pdf, edges, prec, seed, iteration, gid, first, n, nthreads=0):
+    """Per-event weights w = f J of events [first, first + n) of one iteration."""
+    c = _integrand_c(itg)
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    w = np.zeros(n)
+    lib().orc_weights(ctypes.byref(c), pdf.handle if pdf is not None else None, edges.shape[1] - 1, _ptr(edges),
+                      prec, seed, iteration, gid, first, n, nthreads, _ptr(w))
+    return w
 
 
 def integrate(itg, pdf, edges, prec, seed, gid, niter, nevents, alpha=1.5, nthreads=0):

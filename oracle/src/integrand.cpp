@@ -282,6 +282,29 @@ void orc_integrand_at(const orc_integrand* in, const void* pdf, int64_t n, const
   }
 }
 
+// The weight w = f J of each event of [first, first + n) of one VEGAS
+// iteration (thesis eq. mc_est_is: the terms of the estimate), in event order,
+// on nthreads threads (0: one per core).
+void orc_weights(const orc_integrand* in, const void* pdf_v, int nbins, const double* edges, int prec,
+                 uint64_t seed, uint32_t iteration, uint32_t gid, int64_t first, int64_t n, int nthreads,
+                 double* w) {
+  const auto* pdf = static_cast<const orc::Pdf*>(pdf_v);
+  if (nthreads <= 0) nthreads = int(std::max(1u, std::thread::hardware_concurrency()));
+  nthreads = int(std::min<int64_t>(nthreads, std::max<int64_t>(n, 1)));
+  auto work = [&](int tid) {
+    const int64_t lo = n * tid / nthreads, hi = n * (tid + 1) / nthreads;
+    orc_event_record rec;
+    for (int64_t i = lo; i < hi; ++i) {
+      orc::eval_event(*in, pdf, nbins, edges, prec, seed, iteration, gid, first + i, &rec);
+      w[i] = rec.weight;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthreads; ++t) th.emplace_back(work, t);
+  work(0);
+  for (auto& t : th) t.join();
+}
+
 // One VEGAS iteration over events [first, first + n): sums of w and w^2,
 // the count of non-zero weights, the largest weight, and the per-dimension
 // histograms of w^2 and of event counts (both accumulated into the outputs).

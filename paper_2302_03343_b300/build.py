@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmcint.so")
 SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "tc_gemm.cu", "flow.cu", "pdfset.cu", "unweight.cu",
-           "lhe.cu"]
+           "lhe.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -36,7 +36,7 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_pdfset_free", "mc_pdfset_xfxq2", "mc_alphas_load", "mc_alphas_free", "mc_alphas_q2",
            "mc_vegas_iterate_weights", "mc_unweight", "mc_unweight_ms", "mc_lhe_open", "mc_lhe_write",
            "mc_lhe_write_device", "mc_lhe_close", "mc_generate_lhe", "mc_vegas_set_channels", "mc_vegas_get_channels",
-           "mc_channel_update")
+           "mc_channel_update", "mc_fma_peak")
 
 # mc_event (include/mcint.h): one accepted event in the laboratory frame, 200 bytes
 EVENT_DTYPE = np.dtype([("event", "<i8"), ("weight", "<f8"), ("x1", "<f8"), ("x2", "<f8"), ("p", "<f8", (5, 4)),
@@ -123,6 +123,7 @@ def lib():
             "mc_launch_shape": [ctypes.POINTER(Integrand), i32, i64, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)],
             "mc_vegas_kernel_ms": [_vp, ctypes.POINTER(ctypes.c_float)],
+            "mc_fma_peak": [i32, i32, _vp, i64, _dp, _vp],
             "mc_batch_create": [i32, ctypes.POINTER(Integrand), ctypes.POINTER(ctypes.c_int64), _vp, i32, u64, i32,
                                 ctypes.POINTER(_vp)],
             "mc_batch_iterate": [_vp, d, _vp, ctypes.POINTER(IterResult)],
@@ -637,6 +638,15 @@ def mc_vegas_iterate_noalloc(itg, pdf, ndim, nbins, edges64_dev, edges32_dev, pr
     _check(lib().mc_vegas_iterate_noalloc(ctypes.byref(c), pdf.handle if pdf else None, ndim, nbins,
                                           _ptr(edges64_dev), e32, prec, seed, iteration, gid, nevents, blocks,
                                           _ptr(hist_w2_dev), _ptr(hist_n_dev), _ptr(sums_dev), _stream(stream)))
+
+
+def mc_fma_peak(kind, iters, out_dev, stream=None):
+    """Launch the FMA-throughput kernel (kind 0 f32, 1 f32x2, 2 f64) on
+    `stream`; returns the launch's FLOP.  out_dev: device float32, one per
+    thread of the grid (SMs x 2048)."""
+    flop = ctypes.c_double()
+    _check(lib().mc_fma_peak(kind, iters, _ptr(out_dev), out_dev.numel(), ctypes.byref(flop), _stream(stream)))
+    return flop.value
 
 
 def mc_launch_shape(itg, prec, nevents):

@@ -15,6 +15,7 @@ import pytest
 from scipy import integrate
 
 import oracle as O
+from oracle import hadronic as H
 
 AS, MT = 0.118, 173.0
 EW = dict(alpha=1 / 128, mz=91.1876, gz=2.4952, sw2=0.2312)
@@ -95,9 +96,9 @@ def test_ttbar_partonic_totals(rs):
         val, _ = integrate.quad(f, -1, 1, epsrel=1e-13)
         return val * 2 * math.pi * beta / (64 * math.pi ** 2 * s) * GEV2PB
 
-    qq_exact = 8 * math.pi * AS ** 2 / (27 * s) * beta * (1 + rho / 2) * GEV2PB
-    L = math.log((1 + beta) / (1 - beta))
-    gg_exact = math.pi * AS ** 2 / (3 * s) * ((1 + rho + rho * rho / 16) * L - beta * (7 / 4 + 31 * rho / 16)) * GEV2PB
+    # the textbook totals used by the closed-form hadronic cross section
+    qq_exact = H.sigma_hat_qqbar(AS, MT, s, GEV2PB)
+    gg_exact = H.sigma_hat_gg(AS, MT, s, GEV2PB)
     assert abs(sig(O.me2_qqbar_ttbar) - qq_exact) < 1e-10 * qq_exact
     assert abs(sig(O.me2_gg_ttbar) - gg_exact) < 1e-10 * gg_exact
 
