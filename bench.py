@@ -549,6 +549,11 @@ def profile_case(case):
         for _ in range(3):
             M.mc_vegas_iterate(v, W.gg_ttbarg(), pdf, 1 << 20)
             M.mc_vegas_refine(v, ALPHA)
+    elif case == "fp64_7d":  # plain FP64 VEGAS of gg -> ttg in 7 dims (the time-to-target arm): 2 x 2^20
+        v = M.mc_vegas_init(7, NBINS, 0, M.MC_FP64)
+        for _ in range(2):
+            M.mc_vegas_iterate(v, W.gg_ttbarg_7d(), pdf, 1 << 20)
+            M.mc_vegas_refine(v, ALPHA)
     elif case in ("mc", "ppttj"):  # three-channel gg -> ttg, or p p -> t tbar + parton: 3 iterations of 2^20
         itg = W.gg_ttbarg_mc() if case == "mc" else W.pp_ttbarj()
         v = M.mc_vegas_init(itg.ndim(), NBINS, 0, M.MC_FP32_KAHAN)
@@ -911,7 +916,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-target", action="store_true")
-    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdf", "pdfset", "unweight", "mc", "ppttj"], default=None,
+    ap.add_argument("--profile-case", choices=["integrand", "flow", "pdf", "pdfset", "unweight", "mc", "ppttj", "fp64_7d"], default=None,
                     help="run a small fixed workload for profiling and exit")
     args = ap.parse_args()
     if args.profile_case:
