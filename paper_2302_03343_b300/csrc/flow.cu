@@ -250,7 +250,24 @@ __global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* X
   __shared__ float red[8];
   const uint4* row = reinterpret_cast<const uint4*>(XT + size_t(blockIdx.x) * n);
   float acc = 0.0f;
-  for (long long c = threadIdx.x; c < n / 8; c += blockDim.x) {
+  const long long nv = n / 8;
+  long long c = threadIdx.x;
+  // eight independent 16-byte loads in flight per thread
+  for (; c + 7 * 256 < nv; c += 8 * 256) {
+    uint4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = row[c + u * 256];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v[u]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(h[q]);
+        acc += f.x + f.y;
+      }
+    }
+  }
+  for (; c < nv; c += 256) {
     const uint4 v = row[c];
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
@@ -382,15 +399,24 @@ __global__ void __launch_bounds__(256) loss_partials_kernel(const float* w, cons
     part[2 * blockIdx.x + 1] = sb;
   }
 }
+// One warp: lane j sums the partials j, j + 32, ... in order, then a fixed
+// shuffle tree adds the 32 lane sums (deterministic for a given nblocks).
 __global__ void loss_final_kernel(const double* part, int nblocks, double* sums) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
   double sa = 0.0, sb = 0.0;
-  for (int k = 0; k < nblocks; ++k) {
+  for (int k = lane; k < nblocks; k += 32) {
     sa += part[2 * k];
     sb += part[2 * k + 1];
   }
-  sums[0] = sa;
-  sums[1] = sb;
+  for (int off = 16; off > 0; off >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, off);
+    sb += __shfl_xor_sync(0xffffffffu, sb, off);
+  }
+  if (lane == 0) {
+    sums[0] = sa;
+    sums[1] = sb;
+  }
 }
 
 // Adam (thesis Sec. "Optimizers") on every master parameter; gradients of the

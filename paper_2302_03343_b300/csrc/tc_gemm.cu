@@ -452,11 +452,59 @@ __global__ void __launch_bounds__(kRsThreads, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * acc_cols));
 }
 
-__global__ void reduce_splits_kernel(const float* part, int splits, size_t n, float* out) {
-  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-    float acc = out[i];
-    for (int s = 0; s < splits; ++s) acc += part[size_t(s) * n + i];
-    out[i] = acc;
+// out[i] += sum over s of part[s][i], in a fixed order: the splits are cut
+// into kRedGroups contiguous ranges, each summed in order by its own thread
+// (so a thread has a short chain of independent loads in flight), and the
+// range sums are added in range order.  Blocks of kRedGroups x 32 threads
+// cover 32 groups of four consecutive elements (n % 4 == 0, 16-byte
+// aligned arrays); a thread that holds no full group reads nothing.
+constexpr int kRedGroups = 8;
+__global__ void __launch_bounds__(kRedGroups * 32) reduce_splits_kernel(const float* part, int splits, size_t n,
+                                                                      float* out) {
+  __shared__ float4 red[kRedGroups][32];
+  const int c = threadIdx.x & 31, gr = threadIdx.x >> 5;
+  const size_t q = size_t(blockIdx.x) * 32 + c;  // float4 index
+  const bool live = 4 * q + 4 <= n;
+  const int per = (splits + kRedGroups - 1) / kRedGroups;
+  const int s0 = gr * per, s1 = min(splits, s0 + per);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (live) {
+    const float4* p = reinterpret_cast<const float4*>(part) + q;
+    const size_t stride = n / 4;
+    int s = s0;
+#pragma unroll 1
+    for (; s + 4 <= s1; s += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = p[size_t(s + u) * stride];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc.x += v[u].x;
+        acc.y += v[u].y;
+        acc.z += v[u].z;
+        acc.w += v[u].w;
+      }
+    }
+    for (; s < s1; ++s) {
+      const float4 v = p[size_t(s) * stride];
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+  }
+  red[gr][c] = acc;
+  __syncthreads();
+  if (gr == 0 && live) {
+    float4 o = reinterpret_cast<float4*>(out)[q];
+#pragma unroll
+    for (int g = 0; g < kRedGroups; ++g) {
+      o.x += red[g][c].x;
+      o.y += red[g][c].y;
+      o.z += red[g][c].z;
+      o.w += red[g][c].w;
+    }
+    reinterpret_cast<float4*>(out)[q] = o;
   }
 }
 
@@ -580,8 +628,10 @@ cudaError_t tc_gemm_rs(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, con
 cudaError_t tc_reduce_splits(const float* part, int splits, size_t n, float* out, cudaStream_t st) {
   if (splits < 1 || !part || !out) return cudaErrorInvalidValue;
   if (n == 0) return cudaSuccess;
-  const unsigned grid = unsigned(std::min<size_t>((n + 255) / 256, size_t(num_sms_cached()) * 8));
-  reduce_splits_kernel<<<grid, 256, 0, st>>>(part, splits, n, out);
+  if (n % 4 != 0 || (reinterpret_cast<uintptr_t>(part) | reinterpret_cast<uintptr_t>(out)) % 16 != 0)
+    return cudaErrorInvalidValue;
+  const unsigned grid = unsigned((n / 4 + 31) / 32);
+  reduce_splits_kernel<<<grid, kRedGroups * 32, 0, st>>>(part, splits, n, out);
   return cudaGetLastError();
 }
 
