@@ -780,6 +780,41 @@ def time_to_target(M, pdf, stream, seed=0):
     return out
 
 
+def sharded_integration(M, pdf, itg, args, rank, world, stream, dev, l2):
+    """One integration of the benchmark workload split across the ranks (the
+    multi-GPU split of the path): every iteration, rank r evaluates its
+    contiguous share of the events (the same Philox counters as one device),
+    one all-reduce adds the sums and histograms, and every rank refines the
+    same grid.  Strong scaling: the events of an iteration are fixed as the
+    ranks grow.  Device time per step from CUDA events (the all-reduce and the
+    host round trips of the histograms included), slowest rank."""
+    import torch
+    from paper_2302_03343_b300 import shard
+    v = M.mc_vegas_init(14, NBINS, 0, M.MC_FP32_KAHAN)
+    for _ in range(args.warmup):
+        shard.iterate_sharded(v, itg, pdf, args.events, rank, world, stream, dev)
+        M.mc_vegas_refine(v, ALPHA, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ranks_barrier()
+    torch.cuda.synchronize()
+    last = None
+    for i in range(args.steps):
+        flush_l2(l2)
+        ev[i][0].record(stream)
+        last = shard.iterate_sharded(v, itg, pdf, args.events, rank, world, stream, dev)
+        M.mc_vegas_refine(v, ALPHA, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev)
+    v.free()
+    nh = 14 * NBINS
+    mean = last["sum"] / last["n"]
+    return {"value": args.events * args.steps / (ms / 1e3), "unit": "events/s", "parallelism": f"sharded x{world}",
+            "scaling": "strong", "ms_per_step": ms / args.steps, "events_per_step": args.events,
+            "allreduce_bytes_per_step": (2 + 1) * 8 + 3 * 8 + nh * 8 * 2 if world > 1 else 0,
+            "last_iteration_mean_pb": mean}
+
+
 def run_native(args, rank, world):
     import torch
     from paper_2302_03343_b300 import build
@@ -843,6 +878,7 @@ def run_native(args, rank, world):
     h2d = ngrid * 8 + ngrid * 4
     d2h = 64 + ngrid * 8
     e2e_ms = max_over_ranks(1e3 * sum(e2e_s), dev)
+    sharded = sharded_integration(M, pdf, itg, args, rank, world, stream, dev, l2)
 
     if rank != 0:
         return
@@ -879,11 +915,13 @@ def run_native(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (|M|^2) + f64 (sums, RAMBO boosts)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "events_per_step": args.events, "nbins": NBINS,
-                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
+                       "other_mode": "sharded (one integration split across the ranks): the 'sharded' object"},
             "clocks": clocks,
             "e2e": {"value": job_rate(args.events, args.steps, world, e2e_ms), "unit": "events/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 3 * args.steps,
+            "sharded": sharded,
             "roofline": roof,
             "fma_peaks": measured,
             "last_iteration": {"mean_pb": mean, "rel_err": (var ** 0.5) / abs(mean) if mean else None,

@@ -631,6 +631,32 @@ int mc_flow_adam_step(mc_flow f, double lr, void* stream);
  * check.  The flow's ndim must equal the process's. */
 int mc_flow_train(mc_flow f, const mc_integrand* itg, mc_pdf pdf, int steps, int64_t batch, double lr,
                   void* stream, double* losses);
+/* One training step of mc_flow_train split across devices (data parallel;
+ * the loss is a sum over the batch's events, so its gradient is a sum of
+ * per-device parts, thesis Sec. "Optimizers" applied to the importance-
+ * sampling loss).  Every rank holds a flow with the same parameters, seed
+ * and step count; rank r of W:
+ *   1. mc_flow_step_sample(f, itg, pdf, first, count, stream, &wsum):
+ *      samples events [first, first + count) of the step's batch (the same
+ *      Philox counters as mc_flow_train's single-device batch), keeps the
+ *      activations, evaluates f and w = |f| / q; *wsum (host) receives this
+ *      share's sum of w.  Synchronises.  count <= max_batch.
+ *   2. the ranks add their wsum (an all-reduce of one double);
+ *   3. mc_flow_step_grads(f, wsum_total, grads, stream): the gradient of
+ *      this share's part of L = -sum w log q / wsum_total into grads (device,
+ *      caller-owned, mc_flow_grad_count floats in the library's internal
+ *      parameter order; NULL keeps it in place).  Asynchronous.
+ *   4. the ranks add their grads (an all-reduce of mc_flow_grad_count floats);
+ *   5. mc_flow_step_apply(f, grads, lr, stream): installs the summed
+ *      gradient (NULL: the one in place) and takes the Adam step, advancing
+ *      the step counter.  Asynchronous.
+ * With one rank (first 0, count = batch, wsum_total = wsum, grads NULL) the
+ * three calls perform exactly the arithmetic of one mc_flow_train step. */
+int mc_flow_grad_count(mc_flow f, int64_t* n);
+int mc_flow_step_sample(mc_flow f, const mc_integrand* itg, mc_pdf pdf, int64_t first, int64_t count, void* stream,
+                        double* wsum);
+int mc_flow_step_grads(mc_flow f, double wsum_total, float* grads, void* stream);
+int mc_flow_step_apply(mc_flow f, const float* grads, double lr, void* stream);
 /* One sampling pass of nevents events from the flow (Philox counter
  * iteration 0x20000 + iteration), in chunks of max_batch: weights
  * w = f(x)/q(x) accumulated in compensated FP64 into *out (host); events

@@ -493,6 +493,8 @@ __global__ void zero_kernel(float* p, size_t n) {
   if (i < n) p[i] = 0.0f;
 }
 
+__global__ void set_double_kernel(double* p, double v) { *p = v; }
+
 // BF16 copy of W [rows x cols] and of its transpose.
 __global__ void to_bf16_kernel(const float* W, int rows, int cols, __nv_bfloat16* out, __nv_bfloat16* out_t) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1123,6 +1125,9 @@ struct mc_flow_s {
   float *Ps = nullptr, *lqs = nullptr;
   int* err = nullptr;
   int nout_pad_max = 0;
+  // data-parallel step: events of the batch sampled by mc_flow_step_sample
+  // and not yet differentiated (0: none)
+  long long step_n = 0;
   // fused layers (K = 32, nout_pad <= 512): tensor maps of W2, W3, W4, W1e per layer
   bool use_fused = true;      // fused forward layers
   bool use_fused_bwd = true;  // fused backward layers
@@ -1792,6 +1797,60 @@ int mc_flow_adam_step(mc_flow F, double lr, void* stream) {
                                                                    F->d_layers, F->L, A);  // refreshes the BF16 copies
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
+}
+
+// ---- one online training step split across devices (data parallel): each
+// rank samples its share of the step's batch, the ranks add their sums of w,
+// every rank differentiates its share with the loss normalised by the total,
+// the ranks add their gradients, and each takes the same Adam step.
+int mc_flow_grad_count(mc_flow F, int64_t* n) {
+  if (!F || !n) return ffail(MC_EINVAL, "mc_flow_grad_count: NULL argument");
+  *n = int64_t(F->nparam);
+  return MC_OK;
+}
+
+int mc_flow_step_sample(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int64_t first, int64_t count, void* stream,
+                        double* wsum) {
+  if (!F || !itg || !wsum || first < 0 || count < 1 || count > F->max_batch)
+    return ffail(MC_EINVAL, "mc_flow_step_sample: bad arguments");
+  if (mc::process_dim(itg) != F->D) return ffail(MC_EINVAL, "mc_flow_step_sample: flow dimension differs from the process");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long n = count, np = pad128(n);
+  F->step_n = 0;
+  FLOW_CUDA(cudaMemsetAsync(P_of(F, 0), 0, sizeof(float) * np * F->D, st));
+  mc::flow_uniforms_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(P_of(F, 0), n, F->D, F->seed,
+                                                                    0x10000u + uint32_t(F->step), first);
+  if (int rc = forward_pass(F, np, true, st)) return rc;
+  if (int rc = eval_points(F, itg, pdf, P_of(F, F->L), n, F->f, st)) return rc;
+  FLOW_CUDA(cudaMemsetAsync(F->w, 0, sizeof(float) * np, st));
+  mc::flow_weights_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->f, F->logq, F->w, n);
+  loss_sums(F, n, st);
+  FLOW_CUDA(cudaMemcpyAsync(F->h_sums, F->sums, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+  if (int rc = check_err(F, st)) return rc;
+  *wsum = F->h_sums[0];
+  F->step_n = n;
+  return MC_OK;
+}
+
+int mc_flow_step_grads(mc_flow F, double wsum_total, float* grads, void* stream) {
+  if (!F || !(wsum_total > 0.0)) return ffail(MC_EINVAL, "mc_flow_step_grads: bad arguments");
+  if (F->step_n < 1) return ffail(MC_EINVAL, "mc_flow_step_grads: no sampled batch (call mc_flow_step_sample)");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long n = F->step_n, np = pad128(n);
+  mc::set_double_kernel<<<1, 1, 0, st>>>(F->sums, wsum_total);
+  mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
+  if (int rc = backward_pass(F, np, n, st)) return rc;
+  if (grads) FLOW_CUDA(cudaMemcpyAsync(grads, F->d_grads, sizeof(float) * F->nparam, cudaMemcpyDeviceToDevice, st));
+  FLOW_CUDA(cudaGetLastError());
+  return MC_OK;
+}
+
+int mc_flow_step_apply(mc_flow F, const float* grads, double lr, void* stream) {
+  if (!F || !(lr > 0.0)) return ffail(MC_EINVAL, "mc_flow_step_apply: bad arguments");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (grads) FLOW_CUDA(cudaMemcpyAsync(F->d_grads, grads, sizeof(float) * F->nparam, cudaMemcpyDeviceToDevice, st));
+  F->step_n = 0;
+  return mc_flow_adam_step(F, lr, stream);
 }
 
 int mc_flow_train(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int steps, int64_t batch, double lr, void* stream,

@@ -36,7 +36,8 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_pdfset_free", "mc_pdfset_xfxq2", "mc_alphas_load", "mc_alphas_free", "mc_alphas_q2",
            "mc_vegas_iterate_weights", "mc_unweight", "mc_unweight_ms", "mc_lhe_open", "mc_lhe_write",
            "mc_lhe_write_device", "mc_lhe_close", "mc_generate_lhe", "mc_vegas_set_channels", "mc_vegas_get_channels",
-           "mc_channel_update", "mc_fma_peak")
+           "mc_channel_update", "mc_fma_peak", "mc_flow_grad_count", "mc_flow_step_sample", "mc_flow_step_grads",
+           "mc_flow_step_apply")
 
 # mc_event (include/mcint.h): one accepted event in the laboratory frame, 200 bytes
 EVENT_DTYPE = np.dtype([("event", "<i8"), ("weight", "<f8"), ("x1", "<f8"), ("x2", "<f8"), ("p", "<f8", (5, 4)),
@@ -137,6 +138,10 @@ def lib():
                                 _vp],
             "mc_vegas_iterate_noalloc": [ctypes.POINTER(Integrand), _vp, i32, i32, _vp, _vp, i32, u64, u32, u32,
                                          i64, i32, _vp, _vp, _vp, _vp],
+            "mc_flow_grad_count": [_vp, ctypes.POINTER(ctypes.c_int64)],
+            "mc_flow_step_sample": [_vp, ctypes.POINTER(Integrand), _vp, i64, i64, _vp, _dp],
+            "mc_flow_step_grads": [_vp, d, _vp, _vp],
+            "mc_flow_step_apply": [_vp, _vp, d, _vp],
             "mc_flow_param_count": [ctypes.POINTER(FlowCfg), ctypes.POINTER(ctypes.c_int64)],
             "mc_flow_create": [ctypes.POINTER(FlowCfg), _fp, i64, u64, ctypes.POINTER(_vp)],
             "mc_flow_free": [_vp],
@@ -761,6 +766,32 @@ def mc_flow_train(f, itg, pdf, steps, batch, lr=1e-3, stream=None, losses=True):
     _check(lib().mc_flow_train(f.handle, ctypes.byref(_integrand(itg)), pdf.handle if pdf else None, steps, batch, lr,
                                _stream(stream), out))
     return list(out)[:steps] if losses else None
+
+
+def mc_flow_grad_count(f):
+    n = ctypes.c_int64()
+    _check(lib().mc_flow_grad_count(f.handle, ctypes.byref(n)))
+    return n.value
+
+
+def mc_flow_step_sample(f, itg, pdf, first, count, stream=None):
+    """This rank's share of a training step's batch; returns its sum of w."""
+    w = ctypes.c_double()
+    _check(lib().mc_flow_step_sample(f.handle, ctypes.byref(_integrand(itg)), pdf.handle if pdf else None, first,
+                                     count, _stream(stream), ctypes.byref(w)))
+    return w.value
+
+
+def mc_flow_step_grads(f, wsum_total, grads_dev=None, stream=None):
+    """Gradient of this share with the loss normalised by wsum_total, into
+    grads_dev (device float32 [mc_flow_grad_count]) or kept in place."""
+    _check(lib().mc_flow_step_grads(f.handle, wsum_total, _ptr(grads_dev) if grads_dev is not None else None,
+                                    _stream(stream)))
+
+
+def mc_flow_step_apply(f, grads_dev=None, lr=1e-3, stream=None):
+    _check(lib().mc_flow_step_apply(f.handle, _ptr(grads_dev) if grads_dev is not None else None, lr,
+                                    _stream(stream)))
 
 
 def mc_flow_iterate(f, itg, pdf, nevents, iteration=0, stream=None):

@@ -59,3 +59,47 @@ def iterate_sharded(v, itg, pdf, n, rank, world, stream=None, device=None):
         sums, w2, cnt = allreduce_iteration(sums, w2, cnt, device)
         M.mc_vegas_set_hist(v, w2, cnt)
     return sums
+
+
+# ---- the flow's online training split across processes (data parallel).
+# The loss L = -sum_i w_i log q(x_i) / sum_i w_i is a sum over the batch's
+# events divided by the sum of their weights, so with every rank holding the
+# same parameters the step needs two all-reduces: one double (the sum of w,
+# before differentiating, so each rank's part is normalised by the total)
+# and the gradient (after); every rank then takes the same Adam step.
+
+def allreduce_sum(value, device=None):
+    """The sum over the default process group of one float (itself alone)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def allreduce_grads_(grads):
+    """In-place SUM of a gradient tensor over the default process group."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(grads, op=dist.ReduceOp.SUM)
+    return grads
+
+
+def train_flow_sharded(f, itg, pdf, steps, batch, lr, rank, world, stream=None, device=None):
+    """`steps` online training steps of the flow f with each batch split over
+    the ranks (rank r samples the events shard_range(batch, r, world) of the
+    step's batch).  Every rank calls it with the same arguments but its rank;
+    afterwards every rank's flow holds the same parameters."""
+    import torch
+    grads = torch.empty(M.mc_flow_grad_count(f), dtype=torch.float32, device=device or "cuda")
+    first, count = shard_range(batch, rank, world)
+    for _ in range(steps):
+        wsum = allreduce_sum(M.mc_flow_step_sample(f, itg, pdf, first, count, stream), device)
+        M.mc_flow_step_grads(f, wsum, grads, stream)
+        if world > 1:
+            if stream is not None:
+                stream.synchronize()
+            allreduce_grads_(grads)
+        M.mc_flow_step_apply(f, grads, lr, stream)

@@ -129,3 +129,88 @@ def test_shard_ranges_cover_the_iteration():
             assert max(c for _, c in parts) - min(c for _, c in parts) <= 1
     with pytest.raises(ValueError):
         shard.shard_range(10, 2, 2)
+
+
+# ---- the flow's data-parallel training step (paper_2302_03343_b300/shard.py):
+# the FP64 oracle flow stands in for each rank's device.  Two ranks holding
+# half a batch each, with the sum of w and the gradients all-reduced, give
+# the one-rank gradient and Adam step.
+N_FLOW, D_FLOW, L_FLOW, K_FLOW = 301, 4, 2, 8
+
+
+def _flow_setup():
+    import numpy as np
+    from oracle import flow as OF
+    arrays = W.flow_init_params(D_FLOW, L=L_FLOW, K=K_FLOW, seed=3)
+    rng = np.random.default_rng(11)
+    for layer in arrays:  # a non-zero last layer, so every parameter has a gradient
+        layer["W4"] = 0.05 * rng.standard_normal(layer["W4"].shape)
+        layer["b4"] = 0.05 * rng.standard_normal(layer["b4"].shape)
+    params = OF.params_from_arrays(arrays)
+    x = torch.tensor(rng.uniform(0.02, 0.98, size=(N_FLOW, D_FLOW)), dtype=torch.float64)
+    w = torch.tensor(rng.exponential(size=N_FLOW) + 0.1, dtype=torch.float64)
+    return params, x, w
+
+
+def _flat(grads):
+    return torch.cat([g[k].flatten() for g in grads for k in sorted(g)])
+
+
+def _flow_rank(rank, world, port, out):
+    from oracle import flow as OF
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        params, x, w = _flow_setup()
+        first, count = shard.shard_range(N_FLOW, rank, world)
+        xr, wr = x[first:first + count], w[first:first + count]
+        wtot = shard.allreduce_sum(float(wr.sum()))
+        _, g = OF.loss_and_grads(params, xr, wr, K_FLOW)  # normalised by this share's sum of w
+        flat = _flat(g) * (float(wr.sum()) / wtot)
+        shard.allreduce_grads_(flat)
+        out.put((rank, wtot, flat.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_flow_data_parallel_step_over_gloo():
+    import numpy as np
+    from oracle import flow as OF
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_flow_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((out.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    params, x, w = _flow_setup()
+    _, g_full = OF.loss_and_grads(params, x, w, K_FLOW)
+    ref = _flat(g_full).numpy()
+    assert np.count_nonzero(ref) > 0.5 * ref.size  # zero only through inactive ReLU units
+    scale = np.max(np.abs(ref))
+    for _, wtot, flat in res:
+        assert abs(wtot / float(w.sum()) - 1) < 1e-14
+        assert np.max(np.abs(flat - ref)) < 1e-12 * scale
+    # the same Adam step on every rank, equal to the one-rank step
+    def unflat(v):
+        out_, k = [], 0
+        for g in g_full:
+            d = {}
+            for key in sorted(g):
+                n = g[key].numel()
+                d[key] = torch.tensor(v[k:k + n], dtype=torch.float64).reshape(g[key].shape)
+                k += n
+            out_.append(d)
+        return out_
+    p_full = OF.adam_step(params, g_full, OF.adam_state(params), 1)
+    for _, _, flat in res:
+        p_rank = OF.adam_step(params, unflat(flat), OF.adam_state(params), 1)
+        # a gradient component within rounding of zero may take either sign of
+        # the first Adam step (+-lr); every other one takes the same step
+        d = np.abs(_flat(p_rank).numpy() - _flat(p_full).numpy())
+        assert np.max(d) <= 2e-3 + 1e-12
+        assert np.count_nonzero(d > 1e-12) <= np.count_nonzero(np.abs(ref) < 1e-10 * scale)
