@@ -108,7 +108,8 @@ def lib():
         for name, args in [("orc_me2_eemumu", [_d] * 6), ("orc_me2_eemumu_trace", [_d] * 4 + [_dp]),
                            ("orc_me2_qqbar_ttbar", [_d] * 4), ("orc_me2_qqbar_ttbar_trace", [_d, _d, _dp]),
                            ("orc_me2_gg_ttbar", [_d] * 4), ("orc_me2_gg_ttbar_colour_ordered", [_d, _d, _dp]),
-                           ("orc_me2_gg_ttbarg", [_d, _d, _dp]), ("orc_me2_gg_ttbarg_brute", [_d, _d, _dp])]:
+                           ("orc_me2_gg_ttbarg", [_d, _d, _dp]), ("orc_me2_gg_ttbarg_brute", [_d, _d, _dp]),
+                           ("orc_me2_gg_ttbarg_helicity", [_d, _d, _dp])]:
             getattr(L, name).argtypes = args
             getattr(L, name).restype = _d
         for name in ("orc_me2_qqbar_ttbarg", "orc_me2_qg_ttbarq"):
@@ -125,6 +126,9 @@ def lib():
         L.orc_weights.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
                                   ctypes.c_int64, ctypes.c_int, _dp]
+        L.orc_count_gg_ttbarg.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
+                                          ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
+                                          ctypes.c_int64, _dp]
         L.orc_iterate.argtypes = [ctypes.POINTER(IntegrandC), ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
                                   ctypes.c_int64, ctypes.c_int, ctypes.POINTER(IterResult), _dp, _u32p]
@@ -421,6 +425,29 @@ def me2_qqbar_ttbarg_eps(alpha_s, mt, p, eps):
     p = np.ascontiguousarray(p, dtype=np.float64)
     e = np.ascontiguousarray(np.stack([np.real(eps), np.imag(eps)], axis=1).reshape(-1), dtype=np.float64)
     return lib().orc_me2_qqbar_ttbarg_eps(alpha_s, mt, _ptr(p), _ptr(e))
+
+
+def me2_gg_ttbarg_helicity(alpha_s, mt, p):
+    """Formulation C: helicity amplitudes on spinors (oracle/src/helicity_t.h)."""
+    return lib().orc_me2_gg_ttbarg_helicity(alpha_s, mt, _ptr(np.ascontiguousarray(p, dtype=np.float64)))
+
+
+COUNT_STEPS = ("map", "rambo", "cuts", "pdf", "me2", "weight")
+COUNT_KINDS = ("add", "mul", "div", "sqrt", "fn")
+
+
+def count_gg_ttbarg(itg, pdf, edges, prec, seed, iteration, gid, first, n):
+    """Algorithmic operation counts of events [first, first + n) of one g g ->
+    t tbar g (RAMBO) iteration: {"events", "in_cuts", step: {kind: total}}."""
+    c = _integrand_c(itg)
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    out = np.zeros(3 + 5 * len(COUNT_STEPS))
+    lib().orc_count_gg_ttbarg(ctypes.byref(c), pdf.handle, edges.shape[1] - 1, _ptr(edges), prec, seed, iteration,
+                              gid, first, n, _ptr(out))
+    res = {"events": int(out[0]), "in_cuts": int(out[1]), "sum_w": float(out[-1])}
+    for k, st in enumerate(COUNT_STEPS):
+        res[st] = {kind: int(out[2 + 5 * k + j]) for j, kind in enumerate(COUNT_KINDS)}
+    return res
 
 
 def me2_gg_ttbarg_brute(alpha_s, mt, p):

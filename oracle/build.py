@@ -9,7 +9,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["philox.cpp", "vegas.cpp", "phasespace.cpp", "pdf.cpp", "pdfset.cpp", "unweight.cpp", "channels.cpp", "matrix_elements.cpp",
-           "integrand.cpp"]
+           "integrand.cpp", "opcount.cpp"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

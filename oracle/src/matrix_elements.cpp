@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "dirac.h"
+#include "helicity_t.h"
 
 namespace orc {
 
@@ -347,6 +348,19 @@ double me2_gg_ttbarg(double alpha_s, double mt, const P4* p) {
   return me2_colour_ordered(alpha_s, mt, p, 3);
 }
 
+const std::vector<std::array<int, 3>>& ggg_orderings() {
+  static const std::vector<std::array<int, 3>> o = orderings(3);
+  return o;
+}
+const std::vector<double>& ggg_colour_matrix() {
+  static const std::vector<double> c = colour_matrix(3, ggg_orderings());
+  return c;
+}
+// Formulation C: helicity amplitudes on spinors (helicity_t.h) at T = double.
+double me2_gg_ttbarg_helicity(double alpha_s, double mt, const P4* p) {
+  return me2_gg_ttbarg_helicity_t<double>(alpha_s, mt, p, ggg_colour_matrix(), ggg_orderings());
+}
+
 // Formulation B: the 16 Feynman diagrams of g g -> t tbar g at every explicit
 // colour assignment (a1, a2, a3, i, j), spins summed by Dirac traces.
 double me2_gg_ttbarg_brute(double alpha_s, double mt, const P4* p) {
@@ -623,6 +637,11 @@ double orc_me2_gg_ttbarg(double alpha_s, double mt, const double* p) {
   orc::P4 q[5];
   pack(p, 5, q);
   return orc::me2_gg_ttbarg(alpha_s, mt, q);
+}
+double orc_me2_gg_ttbarg_helicity(double alpha_s, double mt, const double* p) {
+  orc::P4 q[5];
+  pack(p, 5, q);
+  return orc::me2_gg_ttbarg_helicity(alpha_s, mt, q);
 }
 double orc_me2_gg_ttbarg_brute(double alpha_s, double mt, const double* p) {
   orc::P4 q[5];

@@ -11,6 +11,7 @@
 // tests/test_oracle_*.py against a closed form, an invariant, an external
 // library routine or brute force.  See the per-function comments.
 #pragma once
+#include <array>
 #include <complex>
 #include <cstdint>
 #include <vector>
@@ -32,13 +33,20 @@ void event_uniform_ints(uint64_t seed, uint32_t iteration, uint32_t gid, int pre
 int uniform_bits(int prec);
 
 // ---------------------------------------------------------------- Lorentz
-struct P4 {
-  double e = 0, x = 0, y = 0, z = 0;
+// Four-vectors over a scalar type T (double, or an operation-counting type).
+template <class T>
+struct P4T {
+  T e = 0, x = 0, y = 0, z = 0;
 };
-inline double dot(const P4& a, const P4& b) { return a.e * b.e - a.x * b.x - a.y * b.y - a.z * b.z; }
-inline P4 add(const P4& a, const P4& b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
-inline P4 sub(const P4& a, const P4& b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
-inline P4 scale(const P4& a, double s) { return {a.e * s, a.x * s, a.y * s, a.z * s}; }
+using P4 = P4T<double>;
+template <class T>
+inline T dot(const P4T<T>& a, const P4T<T>& b) { return a.e * b.e - a.x * b.x - a.y * b.y - a.z * b.z; }
+template <class T>
+inline P4T<T> add(const P4T<T>& a, const P4T<T>& b) { return {a.e + b.e, a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class T>
+inline P4T<T> sub(const P4T<T>& a, const P4T<T>& b) { return {a.e - b.e, a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class T>
+inline P4T<T> scale(const P4T<T>& a, T s) { return {a.e * s, a.x * s, a.y * s, a.z * s}; }
 
 // ---------------------------------------------------------------- phase space
 // Sec. "Phase space generation from particle collisions", eq. 2bodyps.
@@ -78,6 +86,11 @@ double me2_gg_ttbar_colour_ordered(double alpha_s, double mt, const P4* p);
 double me2_gg_ttbarg(double alpha_s, double mt, const P4* p);
 // Feynman diagrams with explicit SU(3) colour indices (formulation B).
 double me2_gg_ttbarg_brute(double alpha_s, double mt, const P4* p);
+// Helicity amplitudes on spinors (formulation C, helicity_t.h), and the
+// gluon orderings and colour matrix it shares with formulation A.
+double me2_gg_ttbarg_helicity(double alpha_s, double mt, const P4* p);
+const std::vector<std::array<int, 3>>& ggg_orderings();
+const std::vector<double>& ggg_colour_matrix();
 // q(p0) qbar(p1) -> t(p2) tbar(p3) g(p4) (five diagrams, explicit colours, Dirac
 // traces) and q(p0) g(p1) -> t(p2) tbar(p3) q(p4) by crossing; spin- and
 // colour-averaged.

@@ -12,6 +12,7 @@
 // from the hierarchical generator and from quadrature of the Dalitz area.
 #include <cmath>
 
+#include "kinematics_t.h"
 #include "oracle.h"
 
 namespace orc {
@@ -48,73 +49,7 @@ void two_body(double sqrt_s, double m1, double m2, double cos_theta, double phi,
 // restored, as the constraint on xi requires), and the first sum in w_m runs
 // over all n particles.
 int rambo(int n, const double* masses, double sqrt_s, const double* u, P4* p, double* w) {
-  const double pi = M_PI;
-  const double s = sqrt_s * sqrt_s;
-  std::vector<P4> q(n);
-  P4 qsum;
-  for (int i = 0; i < n; ++i) {
-    const double c = 2.0 * u[4 * i + 0] - 1.0;
-    const double phi = 2.0 * pi * u[4 * i + 1];
-    const double q0 = -std::log(u[4 * i + 2] * u[4 * i + 3]);
-    const double st = std::sqrt(std::fmax(0.0, 1.0 - c * c));
-    q[i] = {q0, q0 * st * std::cos(phi), q0 * st * std::sin(phi), q0 * c};
-    qsum = add(qsum, q[i]);
-  }
-  const double mq = std::sqrt(dot(qsum, qsum));
-  const double bx = -qsum.x / mq, by = -qsum.y / mq, bz = -qsum.z / mq;
-  const double gamma = qsum.e / mq;
-  const double a = 1.0 / (1.0 + gamma);
-  const double x = sqrt_s / mq;
-  for (int i = 0; i < n; ++i) {
-    const double bq = bx * q[i].x + by * q[i].y + bz * q[i].z;
-    p[i].e = x * (gamma * q[i].e + bq);
-    p[i].x = x * (q[i].x + bx * q[i].e + a * bq * bx);
-    p[i].y = x * (q[i].y + by * q[i].e + a * bq * by);
-    p[i].z = x * (q[i].z + bz * q[i].e + a * bq * bz);
-  }
-  const double w0 = std::pow(2.0 * pi, 4.0 - 3.0 * n) * std::pow(pi / 2.0, n - 1.0) *
-                    std::pow(s, n - 2.0) / (std::tgamma(double(n)) * std::tgamma(n - 1.0));
-  double msum = 0.0;
-  bool massive = false;
-  for (int i = 0; i < n; ++i) {
-    msum += masses[i];
-    if (masses[i] != 0.0) massive = true;
-  }
-  if (!massive) {
-    *w = w0;
-    return 0;
-  }
-  if (!(sqrt_s > msum)) return -1;
-  double xi = std::sqrt(1.0 - (msum / sqrt_s) * (msum / sqrt_s));
-  bool converged = false;
-  for (int it = 0; it < 100; ++it) {
-    double f = -sqrt_s, fp = 0.0;
-    for (int i = 0; i < n; ++i) {
-      const double e = std::sqrt(masses[i] * masses[i] + xi * xi * p[i].e * p[i].e);
-      f += e;
-      fp += xi * p[i].e * p[i].e / e;
-    }
-    const double step = f / fp;
-    xi -= step;
-    if (std::fabs(step) <= 1e-15 * xi) {
-      converged = true;
-      break;
-    }
-  }
-  if (!converged) return -5;
-  double sum_k = 0.0, prod = 1.0, sum_k2_e = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double e = std::sqrt(masses[i] * masses[i] + xi * xi * p[i].e * p[i].e);
-    P4 k = {e, xi * p[i].x, xi * p[i].y, xi * p[i].z};
-    const double kabs = std::sqrt(k.x * k.x + k.y * k.y + k.z * k.z);
-    sum_k += kabs;
-    prod *= kabs / k.e;
-    sum_k2_e += kabs * kabs / k.e;
-    p[i] = k;
-  }
-  const double wm = std::pow(s, 2.0 - n) * std::pow(sum_k, 2.0 * n - 3.0) * prod / sum_k2_e;
-  *w = w0 * wm;
-  return 0;
+  return rambo_t<double>(n, masses, sqrt_s, u, p, w);
 }
 
 // Boost v, given in the rest frame of q (mass mq), to the frame where q has

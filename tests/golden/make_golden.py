@@ -15,7 +15,14 @@ uniforms, seed 0), for the check of the FP32 path against FP64 at identical
 points (eq. mc_est_is): the grid, the sums, the count of events in the cuts,
 the largest weight and the bin counts.
 
-Run: python tests/golden/make_golden.py [c2] [c3]   (c3 takes several minutes)
+ggttg_opcount.json: the algorithmic operation counts of that workload's
+event (oracle/src/opcount.cpp: the oracle's VEGAS map, RAMBO, cuts, PDFs,
+|M|^2 from helicity amplitudes (formulation C) and weight, run with an
+operation-counting scalar) over the first 20 000 events of the stored
+iteration, per event and per event inside the cuts.
+
+Run: python tests/golden/make_golden.py [c2] [c3] [opcount]   (c3 takes several minutes;
+opcount reads c3's grid)
 """
 import json
 import os
@@ -79,9 +86,32 @@ def c3():
     print("c3", r["sum"] / r["n"], r["n_nonzero"], t_it)
 
 
+def opcount(n=20_000):
+    with open(os.path.join(HERE, "c3_ggttg_iteration.json")) as f:
+        g = json.load(f)
+    p = g["params"]
+    pdf = O.Pdf(W.synthetic_pdf_grid(0))
+    r = O.count_gg_ttbarg(W.gg_ttbarg(), pdf, np.array(g["edges"]), 1, p["seed"], p["iteration"], p["gid"], 0, n)
+    flop = {st: sum(r[st][k] for k in ("add", "mul", "div", "sqrt")) for st in O.COUNT_STEPS}
+    every = ("map", "rambo", "cuts")  # run for every event (cuts: every event above threshold)
+    out = {"config": "g g -> t tbar g, RAMBO 2 + 12 dims, the first %d events of the stored FP32-mode iteration" % n,
+           "events": r["events"], "in_cuts": r["in_cuts"], "counts": {st: r[st] for st in O.COUNT_STEPS},
+           "flop_per_event": {st: flop[st] / r["events"] for st in every},
+           "flop_per_event_in_cuts": {st: flop[st] / r["in_cuts"] for st in O.COUNT_STEPS if st not in every},
+           "convention": "additions, subtractions, multiplications, divisions and square roots count one FLOP each; "
+                         "special functions (log, exp, sin, cos, pow) are counted apart, not as FLOP",
+           "citation": "thesis Sec. \"The MadFlow event generator\" (|M|^2 from helicity amplitudes), Sec. \"RAMBO\", "
+                       "Sec. \"LHAPDF: the Les Houches Accord PDF\", eq. mc_est_is"}
+    with open(os.path.join(HERE, "ggttg_opcount.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print("opcount", out["flop_per_event"], out["flop_per_event_in_cuts"])
+
+
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["c2", "c3"]
+    which = sys.argv[1:] or ["c2", "c3", "opcount"]
     if "c2" in which:
         c2()
     if "c3" in which:
         c3()
+    if "opcount" in which:
+        opcount()

@@ -337,3 +337,51 @@ def test_qqbar_ttbarg_soft_gluon_scaling():
         assert np.allclose(Pl[2] + Pl[3] + Pl[4], [rs, 0, 0, 0], atol=1e-9 * rs)
         vals.append(O.me2_qqbar_ttbarg(AS, MT, Pl) * eg ** 2)
     assert abs(vals[2] / vals[1] - 1) < 1e-2 and abs(vals[1] / vals[0] - 1) < 1e-1
+
+
+# ------------------------------------------------- formulation C and op counts
+@pytest.mark.parametrize("rs,u", POINTS)
+def test_ggttg_helicity_formulation_agrees(rs, u):
+    """Formulation C (helicity amplitudes on spinors, one antitop spin doubled)
+    equals formulation A (Dirac traces, every spin) and B (Feynman diagrams at
+    explicit colours)."""
+    P = ggttg_point(rs, np.array(u))
+    a = O.me2_gg_ttbarg(AS, MT, P)
+    c = O.me2_gg_ttbarg_helicity(AS, MT, P)
+    b = O.me2_gg_ttbarg_brute(AS, MT, P)
+    assert abs(c - a) < 1e-12 * abs(a)
+    assert abs(c - b) < 1e-12 * abs(b)
+
+
+def test_ggttg_helicity_formulation_random_points():
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        rs = rng.uniform(400.0, 6000.0)
+        P = ggttg_point(rs, rng.uniform(0.02, 0.98, 12))
+        a = O.me2_gg_ttbarg(AS, MT, P)
+        assert abs(O.me2_gg_ttbarg_helicity(AS, MT, P) - a) < 1e-12 * abs(a)
+
+
+def test_operation_counts_of_the_event():
+    """The counting harness runs the oracle's own arithmetic (its weights sum
+    to orc_iterate's over the same events), the |M|^2 count is the same for
+    every event, and the VEGAS map costs what its formula says:
+    r = (2m + 1) 2^-(b+1) (1 multiplication), w = hi - lo, x = lo + r w,
+    J *= N_b w: 6 operations per dimension."""
+    from paper_2302_03343_b300 import workloads as W
+    pdf = O.Pdf(W.synthetic_pdf_grid(0))
+    itg = W.gg_ttbarg()
+    edges = O.vegas_refine(W.uniform_grid(14, 50), np.random.default_rng(3).exponential(size=(14, 50)) ** 2, 1.0)
+    per_event = []
+    for first in (0, 5000):
+        r = O.count_gg_ttbarg(itg, pdf, edges, 1, 4, 2, 0, first, 2000)
+        it = O.iterate(itg, pdf, edges, 1, 4, 2, 0, first, 2000, nthreads=1)
+        assert r["in_cuts"] == it["n_nonzero"] > 0
+        assert abs(r["sum_w"] - it["sum"]) <= 1e-12 * abs(it["sum"])
+        me = r["me2"]
+        flop = me["add"] + me["mul"] + me["div"] + me["sqrt"]
+        assert flop % r["in_cuts"] == 0
+        per_event.append(flop // r["in_cuts"])
+        m = r["map"]
+        assert (m["add"], m["mul"], m["div"], m["sqrt"], m["fn"]) == (2 * 14 * 2000, 4 * 14 * 2000, 0, 0, 0)
+    assert per_event[0] == per_event[1] > 0
