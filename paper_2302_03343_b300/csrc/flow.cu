@@ -206,6 +206,63 @@ __global__ void __launch_bounds__(128) spline_inv_bwd_kernel(const float* Pin, f
   }
 }
 
+constexpr int kFusedK = 32;   // bins of the fused kernels
+constexpr int kFusedLs = 80;  // their logit stride: 2K+1 rounded up to 16 columns
+
+// The same spline backward for K = 32 bins with one thread per (event,
+// coordinate j = blockIdx.y): the coordinates' independent work runs on
+// separate threads, and with the bin count fixed at compile time every value
+// stays in registers (no staging).  Writes exactly what spline_inv_bwd_kernel
+// writes (the same arithmetic and roundings per coordinate).
+__global__ void __launch_bounds__(128, 4) spline_bwd_k32_kernel(const float* Pin, float* dP, int D, const LayerDev L,
+                                                             const float* LT, const float* w, const double* wsum,
+                                                             __nv_bfloat16* G, __nv_bfloat16* GT, long long n,
+                                                             long long n_real) {
+  constexpr int K = kFusedK, K2 = 2 * K + 1;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  const bool real = i < n_real;
+  const size_t ldn = size_t(n);
+  const int d = L.b_idx[j];
+  float gw[kFlowMaxBins], gv[kFlowMaxBins + 1];
+  if (real) {
+    const float gl = float(-double(w[i]) / *wsum);
+    Spline s;
+    spline_load(LT + size_t(j) * L.ls * ldn + i, ldn, K, s);
+    dP[i * D + d] = spline_inv_bwd(s, K, Pin[i * D + d], dP[i * D + d], gl, gw, gv);
+  } else {
+    dP[i * D + d] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kFlowMaxBins; ++k) gw[k] = gv[k] = 0.0f;
+    gv[kFlowMaxBins] = 0.0f;
+  }
+  // logit k of the coordinate: k < K a width, K <= k <= 2K a height, then zeros
+  auto logit = [&](int k) -> float { return k < K ? gw[k < K ? k : 0] : (k < K2 ? gv[k < K2 ? k - K : 0] : 0.0f); };
+  __nv_bfloat16* gt = GT + size_t(j) * L.ls * ldn + i;
+#pragma unroll
+  for (int k = 0; k < K2; ++k) gt[size_t(k) * ldn] = __float2bfloat16_rn(logit(k));
+  uint4* gr = reinterpret_cast<uint4*>(G + size_t(i) * L.nout_pad + size_t(j) * L.ls);
+#pragma unroll
+  for (int c8 = 0; c8 < kFusedLs / 8; ++c8) {
+    uint4 pk;
+    uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(logit(c8 * 8 + 2 * e), logit(c8 * 8 + 2 * e + 1));
+      pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+    }
+    gr[c8] = pk;
+  }
+  if (j == 0) {  // the rows past the last coordinate (see spline_inv_bwd_kernel)
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+    for (int c = L.nb * L.ls; c < L.nout_pad; ++c) {
+      GT[size_t(c) * ldn + i] = z;
+      G[size_t(i) * L.nout_pad + c] = z;
+    }
+  }
+}
+
 // First dense layer backward, input side: dL/dx_A += 2 dU with dU = dA1 W1
 // computed on the tensor cores as [n][16] (u = 2 x_A - 1).
 __global__ void add_input_grad_kernel(float* dP, int D, const LayerDev L, const float* dU, long long n) {
@@ -246,6 +303,64 @@ __global__ void mask_bits_kernel(const __nv_bfloat16* hT, size_t slot_stride, lo
 
 // out[r] += sum_i XT[r][i] over a BF16 matrix XT [rows][n]: one block per
 // row, fixed-order reduction (bias gradients from transposed gradients).
+// Row sums of up to three transposed BF16 matrices in one launch: block b
+// sums row b of the first matrix, then of the second, then of the third
+// (rows[k] rows each), each exactly as rowsum_bf16_kernel would.
+struct RowSums3 {
+  const __nv_bfloat16* XT[3];
+  float* out[3];
+  int rows[3];
+};
+__global__ void __launch_bounds__(256) rowsum3_bf16_kernel(RowSums3 a, long long n) {
+  __shared__ float red[8];
+  int b = blockIdx.x, m = 0;
+  if (b >= a.rows[0]) {
+    b -= a.rows[0];
+    m = 1;
+    if (b >= a.rows[1]) {
+      b -= a.rows[1];
+      m = 2;
+    }
+  }
+  const __nv_bfloat16* X = m == 0 ? a.XT[0] : (m == 1 ? a.XT[1] : a.XT[2]);
+  float* out = m == 0 ? a.out[0] : (m == 1 ? a.out[1] : a.out[2]);
+  const uint4* row = reinterpret_cast<const uint4*>(X + size_t(b) * n);
+  float acc = 0.0f;
+  const long long nv = n / 8;
+  long long c = threadIdx.x;
+  for (; c + 7 * 256 < nv; c += 8 * 256) {
+    uint4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = row[c + u * 256];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v[u]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(h[q]);
+        acc += f.x + f.y;
+      }
+    }
+  }
+  for (; c < nv; c += 256) {
+    const uint4 v = row[c];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = __bfloat1622float2(h[q]);
+      acc += f.x + f.y;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.0f;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[w];
+    out[b] += v;
+  }
+}
+
 __global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* XT, long long n, float* out) {
   __shared__ float red[8];
   const uint4* row = reinterpret_cast<const uint4*>(XT + size_t(blockIdx.x) * n);
@@ -522,8 +637,6 @@ __global__ void to_bf16_kernel(const float* W, int rows, int cols, __nv_bfloat16
 // 6-9 are the two tiles' compute groups (warp w owns TMEM lanes
 // 32 (w % 4) .. 32 (w % 4) + 31: one event per thread, all of its columns).
 // KEEP (training) also writes the activations the backward needs.
-constexpr int kFusedK = 32;                       // bins
-constexpr int kFusedLs = 80;                      // logit stride: 2K+1 rounded up to 16 columns
 constexpr int kFusedThreads = 320;
 constexpr int kFusedCompute = 256;
 constexpr uint32_t kFusedABytes = 128 * kH * 2;   // one 128 x 256 BF16 operand (4 swizzled chunks)
@@ -1089,6 +1202,273 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
+// ---------------------------------------------------------------------------
+// Backward chain of a coupling layer for training, after the spline backward
+// (spline_inv_bwd_kernel has written the logit gradients G row-major, their
+// transpose G^T and the spline part of dP): per tile of 128 events the four
+// tcgen05 products dA3 = (G W4) * [h3 > 0], dA2 = (dA3 W3) * [h2 > 0],
+// dA1 = (dA2 W2) * [h1 > 0] and dU = dA1 W1, with two tiles in flight per SM,
+// one per half of the tensor memory (256 columns) and per operand buffer.
+// Warp 0 loads each tile's G by TMA into its operand buffer and streams the
+// transposed weights through a ring; warp 1 issues the MMAs, alternating
+// between the two tiles phase by phase, so that one tile's products overlap
+// the other tile's epilogues; warps 2-9 and 10-17 are the two tiles' compute
+// groups (warp w owns TMEM lanes 32 (w % 4) .. +31; warps 2-5 / 10-13 the
+// first 128 columns, 6-9 / 14-17 the other 128).  Each epilogue masks the
+// accumulator with the ReLU activity bits, rounds it to BF16 into the operand
+// buffer (the next product's A) and writes its transpose for the
+// weight-gradient products; the last adds 2 dU to the conditioning
+// coordinates of dP.  The arithmetic, and the order of every MMA, are those
+// of flow_layer_bwd_kernel, so the results are the same bit for bit.
+struct ChainBwdArgs {
+  float* dP;             // [n][D]: dL/dx_A += 2 dU
+  const uint32_t* bits;  // ReLU activity of h1, h2, h3: [3][n][8] words
+  __nv_bfloat16 *dA3T, *dA2T, *dA1T;
+  LayerDev L;
+  int D;
+  long long n;
+  int* error;
+};
+constexpr int kChainThreads = 576;
+constexpr size_t kChainSmemMax = 232448 - 1024;  // opt-in limit less the kernel's static shared memory
+constexpr int kChainCompute = 256;  // compute threads per tile slot
+
+__global__ void __launch_bounds__(kChainThreads, 1)
+    flow_chain_bwd_kernel(const __grid_constant__ CUtensorMap map_g, const __grid_constant__ CUtensorMap map_w4t,
+                          const __grid_constant__ CUtensorMap map_w3t, const __grid_constant__ CUtensorMap map_w2t,
+                          const __grid_constant__ CUtensorMap map_w1t, ChainBwdArgs g, int stages) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int kMaxStages = 4;
+  __shared__ __align__(8) uint64_t w_full[kMaxStages];
+  __shared__ __align__(8) uint64_t w_empty[kMaxStages];
+  __shared__ __align__(8) uint64_t g_full[2], abuf_free[2], a_ready[2], acc_full[2], acc_empty[2], fin_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int failed;
+
+  const LayerDev& L = g.L;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nout = L.nout_pad, kc0 = nout / 64;  // K chunks of the first product
+  const uint32_t stage_bytes = uint32_t(kH) * 128u;
+  const size_t abytes = size_t(max(kH, nout)) * 256;
+  unsigned char* ring = smem + 2 * abytes;
+  const int m_tiles = int(g.n / 128);
+  const int my_tiles = int(blockIdx.x) < m_tiles ? (m_tiles - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  auto tile_row = [&](int i) { return (int(blockIdx.x) + i * int(gridDim.x)) * 128; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&w_full[s], 1);
+      mbar_init(&w_empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&g_full[s], 1);
+      mbar_init(&abuf_free[s], 1);
+      mbar_init(&a_ready[s], kChainCompute);
+      mbar_init(&acc_full[s], 1);
+      mbar_init(&acc_empty[s], kChainCompute);
+    }
+    mbar_init(&fin_bar, 1);
+    failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0 && my_tiles > 0) {
+      int it = 0;
+      int loaded[2] = {0, 0};
+      bool ok = true;
+      for (int j = 0; 2 * j < my_tiles && ok; ++j) {
+        // this pair's G tiles, each once the slot's previous tile has left its operand buffer
+        for (int s = 0; s < 2 && ok; ++s) {
+          if (2 * j + s >= my_tiles) continue;
+          if (loaded[s] > 0 && !mbar_wait(&abuf_free[s], uint32_t(loaded[s] - 1) & 1u)) {
+            ok = false;
+            break;
+          }
+          unsigned char* dst = smem + size_t(s) * abytes;
+          mbar_expect_tx(&g_full[s], uint32_t(kc0) * 16384u);
+          for (int c = 0; c < kc0; ++c) tma_load_2d(dst + size_t(c) * 16384, &map_g, c * 64, tile_row(2 * j + s), &g_full[s]);
+          ++loaded[s];
+        }
+        // the weights in the MMA order: phase by phase, tile 0 then tile 1
+        for (int p = 0; p < 4 && ok; ++p)
+          for (int s = 0; s < 2 && ok; ++s) {
+            if (2 * j + s >= my_tiles) continue;
+            const int nk = p == 0 ? kc0 : 4;
+            for (int c = 0; c < nk; ++c, ++it) {
+              const int st = it % stages;
+              const uint32_t use = uint32_t(it / stages);
+              if (use > 0 && !mbar_wait(&w_empty[st], (use - 1) & 1u)) {
+                ok = false;
+                break;
+              }
+              unsigned char* dst = ring + size_t(st) * stage_bytes;
+              if (p < 3) {
+                mbar_expect_tx(&w_full[st], stage_bytes);
+                tma_load_2d(dst, p == 0 ? &map_w4t : (p == 1 ? &map_w3t : &map_w2t), c * 64, 0, &w_full[st]);
+              } else {
+                mbar_expect_tx(&w_full[st], uint32_t(kUPad) * 128u);
+                tma_load_2d(dst, &map_w1t, c * 64, 0, &w_full[st]);
+              }
+            }
+          }
+      }
+      if (!ok) {
+        failed = 1;
+        atomicExch(g.error, 41);
+      }
+      // every copy issued here lands before the kernel ends
+      for (int st = 0; st < stages && st < it; ++st) mbar_wait(&w_full[st], uint32_t((it - 1 - st) / stages) & 1u);
+      for (int s = 0; s < 2; ++s)
+        if (loaded[s] > 0) mbar_wait(&g_full[s], uint32_t(loaded[s] - 1) & 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && my_tiles > 0) {
+      const uint32_t idesc_h = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kH >> 3) << 17) | (8u << 24);
+      const uint32_t idesc_u = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kUPad >> 3) << 17) | (8u << 24);
+      int it = 0;
+      int use_a[2] = {0, 0}, done[2] = {0, 0};
+      bool ok = true;
+      for (int j = 0; 2 * j < my_tiles && ok; ++j)
+        for (int p = 0; p < 4 && ok; ++p)
+          for (int s = 0; s < 2 && ok; ++s) {
+            if (2 * j + s >= my_tiles) continue;
+            if (p == 0) {
+              // the slot's accumulator is free once its compute group has read
+              // the previous tile's dU, and its G tile has landed
+              if ((done[s] > 0 && !mbar_wait(&acc_empty[s], uint32_t(done[s] - 1) & 1u)) ||
+                  !mbar_wait(&g_full[s], uint32_t(done[s]) & 1u) || failed) {
+                ok = false;
+                break;
+              }
+            } else if (!mbar_wait(&a_ready[s], uint32_t(use_a[s]++) & 1u) || failed) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t d = tmem + uint32_t(s) * kH;
+            const unsigned char* ab = smem + size_t(s) * abytes;
+            const int nk = p == 0 ? kc0 : 4;
+            for (int c = 0; c < nk; ++c, ++it) {
+              const int st = it % stages;
+              if (!mbar_wait(&w_full[st], uint32_t(it / stages) & 1u)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+              const uint64_t ad = smem_desc(smem_u32(ab + size_t(c) * 16384));
+              const uint64_t bd = smem_desc(smem_u32(ring + size_t(st) * stage_bytes));
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                mma_bf16(d, ad + uint64_t(k * 2), bd + uint64_t(k * 2), p == 3 ? idesc_u : idesc_h,
+                         (c > 0 || k > 0) ? 1u : 0u);
+              mma_commit(&w_empty[st]);
+            }
+            if (!ok) break;
+            mma_commit(&acc_full[s]);
+            if (p == 3) {
+              mma_commit(&abuf_free[s]);  // the operand buffer may take the slot's next G tile
+              ++done[s];
+            }
+          }
+      if (!ok) {
+        failed = 1;
+        atomicExch(g.error, 42);
+      }
+      mma_commit(&fin_bar);  // every MMA issued here completes before the TMEM is released
+      mbar_wait(&fin_bar, 0);
+    }
+  } else {
+    const int slot = (warp - 2) >> 3, half = ((warp - 2) >> 2) & 1, q = warp & 3;
+    const int r = q * 32 + lane;  // event row in the tile (= TMEM lane)
+    const uint32_t trow = tmem + (uint32_t(q * 32) << 16) + uint32_t(slot) * kH;
+    unsigned char* abuf = smem + size_t(slot) * abytes;
+    const size_t n = size_t(g.n);
+    int use_acc = 0;
+    for (int i = slot; i < my_tiles; i += 2) {
+      const long long ev = (long long)tile_row(i) + r;
+      if (__any_sync(0xffffffffu, failed != 0)) break;
+      // the activity bits of this thread's 128 columns of h3, h2, h1
+      uint4 mbv[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) mbv[m] = reinterpret_cast<const uint4*>(g.bits + (size_t(2 - m) * n + ev) * 8)[half];
+      bool ok = true;
+      for (int m = 0; m < 3 && ok; ++m, ++use_acc) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[slot], uint32_t(use_acc) & 1u))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t mbw[4] = {mbv[m].x, mbv[m].y, mbv[m].z, mbv[m].w};
+        __nv_bfloat16* outT = m == 0 ? g.dA3T : (m == 1 ? g.dA2T : g.dA1T);
+        for (int cg = 0; cg < 2; ++cg) {
+          uint32_t v[4][16];
+          const int col0 = half * 128 + cg * 64;
+#pragma unroll
+          for (int x = 0; x < 4; ++x) tmem_ld16_nw(trow + uint32_t(col0 + 16 * x), v[x]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+#pragma unroll
+            for (int hlf = 0; hlf < 2; ++hlf) {
+              uint4 pk;
+              uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int cc = col0 + 16 * x + 8 * hlf + 2 * e;
+                const int jl = cc - half * 128;
+                const uint32_t word = mbw[cg * 2 + (x >> 1)];  // jl >> 5 = 2 cg + x / 2
+                const float o0 = (word >> (jl & 31)) & 1u ? __uint_as_float(v[x][8 * hlf + 2 * e]) : 0.0f;
+                const float o1 = (word >> ((jl + 1) & 31)) & 1u ? __uint_as_float(v[x][8 * hlf + 2 * e + 1]) : 0.0f;
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
+                pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                outT[size_t(cc) * n + ev] = hh.x;
+                outT[size_t(cc + 1) * n + ev] = hh.y;
+              }
+              *reinterpret_cast<uint4*>(abuf + swz_off(r, (col0 + 16 * x + 8 * hlf) >> 3)) = pk;
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        fence_async_smem();
+        mbar_arrive(&a_ready[slot]);
+      }
+      if (ok && !__all_sync(0xffffffffu, mbar_wait(&acc_full[slot], uint32_t(use_acc) & 1u))) ok = false;
+      ++use_acc;
+      if (!ok) {
+        failed = 1;
+        if (lane == 0) atomicExch(g.error, 43);
+        break;
+      }
+      // dU = dA1 W1 into the conditioning coordinates: dL/dx_A += 2 dU
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (half == 0) {
+        uint32_t v[16];
+        tmem_ld16_nw(trow, v);
+        tmem_wait_ld();
+        float* dPe = g.dP + ev * g.D;
+        for (int a = 0; a < L.na; ++a) dPe[L.a_idx[a]] += 2.0f * __uint_as_float(v[a < 16 ? a : 0]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      mbar_arrive(&acc_empty[slot]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 }  // namespace
 }  // namespace mc
 
@@ -1134,6 +1514,10 @@ struct mc_flow_s {
   std::vector<bool> fused_ok;
   std::vector<CUtensorMap> maps;
   std::vector<CUtensorMap> bwd_maps;  // W4^T, W3^T, W2^T, W1^T per layer (fused backward)
+  // two-tile backward chain (flow_chain_bwd_kernel): the row-major logit
+  // gradients G of each layer as a TMA source, and whether the layer fits
+  std::vector<CUtensorMap> g_maps;
+  std::vector<bool> chain_ok;
 };
 
 namespace {
@@ -1383,6 +1767,42 @@ int fused_bwd_layer(mc_flow F, int l, long long n, long long n_real, cudaStream_
   return MC_OK;
 }
 
+// Two-tile backward chain of layer l (flow_chain_bwd_kernel) after the spline
+// backward has written G, G^T and the spline part of dP.
+int chain_bwd_layer(mc_flow F, int l, long long n, cudaStream_t st) {
+  FLOW_CUDA(cudaGetLastError());
+  static int num_sms = 0;
+  if (num_sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms < 1)
+      num_sms = 1;
+  }
+  const LayerDev& L = F->layers[l];
+  mc::ChainBwdArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.dP = F->dP;
+  a.bits = MB_of(F, l);
+  a.dA3T = F->dAT;
+  a.dA2T = F->dAT + size_t(F->bp) * kH;
+  a.dA1T = F->dAT + 2 * size_t(F->bp) * kH;
+  a.L = L;
+  a.D = F->D;
+  a.n = n;
+  a.error = F->err;
+  const size_t abytes = size_t(std::max(kH, L.nout_pad)) * 256, stage = size_t(kH) * 128;
+  const int stages = int(std::min<size_t>(4, (mc::kChainSmemMax - 1024 - 2 * abytes) / stage));
+  if (stages < 2) return ffail(MC_EINVAL, "mc_flow: backward chain does not fit in shared memory");
+  const size_t smem = 1024 + 2 * abytes + stages * stage;
+  FLOW_CUDA(cudaFuncSetAttribute(mc::flow_chain_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const int grid = int(std::min<long long>(n / 128, num_sms));
+  mc::flow_chain_bwd_kernel<<<grid, mc::kChainThreads, smem, st>>>(F->g_maps[l], F->bwd_maps[4 * l],
+                                                                  F->bwd_maps[4 * l + 1], F->bwd_maps[4 * l + 2],
+                                                                  F->bwd_maps[4 * l + 3], a, stages);
+  FLOW_CUDA(cudaGetLastError());
+  return MC_OK;
+}
+
 // Backward of the density pass (weights F->w, sum w in F->sums[0]) over the
 // kept activations: accumulates every parameter gradient into F->d_grads
 // (zeroed beforehand).
@@ -1393,17 +1813,25 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& L = F->layers[l];
     if (F->use_fused_bwd && F->fused_ok[l]) {
-      // spline and activation gradients in one kernel, then the weight gradients
+      // spline and activation gradients (the spline backward at full
+      // occupancy, then the two-tile product chain; one fused kernel where the
+      // chain's buffers do not fit), then the weight gradients
       __nv_bfloat16* dA3T = F->dAT;
       __nv_bfloat16* dA2T = F->dAT + size_t(F->bp) * kH;
       __nv_bfloat16* dA1T = F->dAT + 2 * size_t(F->bp) * kH;
-      if (int rc = fused_bwd_layer(F, l, n, n_real, st)) return rc;
+      if (F->chain_ok[l]) {
+        mc::spline_bwd_k32_kernel<<<dim3(mc::blocks_for(n, 128), L.nb), 128, 0, st>>>(
+            P_of(F, l + 1), F->dP, D, L, LT_of(F, l), F->w, F->sums, F->G, F->GT, n, n_real);
+        if (int rc = chain_bwd_layer(F, l, n, st)) return rc;
+      } else if (int rc = fused_bwd_layer(F, l, n, n_real, st)) {
+        return rc;
+      }
       if (int rc = gemm_wgrad(F, n, L.nout_pad, hT_of(F, l, 2), F->GT, g + L.off_W4, st)) return rc;
-      mc::rowsum_bf16_kernel<<<L.nout_pad, 256, 0, st>>>(F->GT, n, g + L.off_b4);
       if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 1), dA3T, g + L.off_W3, st)) return rc;
-      mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(dA3T, n, g + L.off_b3);
       if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 0), dA2T, g + L.off_W2, st)) return rc;
-      mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(dA2T, n, g + L.off_b2);
+      // the bias gradients b4, b3, b2: row sums of G^T, dA3^T, dA2^T in one launch
+      mc::RowSums3 rs{{F->GT, dA3T, dA2T}, {g + L.off_b4, g + L.off_b3, g + L.off_b2}, {L.nout_pad, kH, kH}};
+      mc::rowsum3_bf16_kernel<<<L.nout_pad + 2 * kH, 256, 0, st>>>(rs, n);
       int splits = 0;
       if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, UT_of(F, l), nullptr, st, &splits)) return rc;
       mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
@@ -1670,6 +2098,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   // tensor maps of the fused layers
   F->maps.resize(4 * L);
   F->bwd_maps.resize(4 * L);
+  F->g_maps.resize(L);
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& Ld = F->layers[l];
     // fused layers: 32 bins (logit stride 80), at most 6 transformed
@@ -1684,6 +2113,11 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
          mc::tc_make_map(&F->bwd_maps[4 * l + 2], Ld.W2t, kH, kH, kH, kH) &&
          mc::tc_make_map(&F->bwd_maps[4 * l + 3], Ld.W1t, mc::kUPad, kH, kH, mc::kUPad);
     F->fused_ok.push_back(ok);
+    // two operand buffers of max(256, nout_pad) x 128 BF16 and at least two
+    // weight stages must fit in shared memory
+    const size_t abytes = size_t(std::max(kH, Ld.nout_pad)) * 256;
+    const bool fits = 2 * abytes + 2 * size_t(kH) * 128 + 1024 <= mc::kChainSmemMax;
+    F->chain_ok.push_back(ok && fits && mc::tc_make_map(&F->g_maps[l], F->G, int(bp), Ld.nout_pad, Ld.nout_pad, 128));
   }
   // the padding rows of the logit gradients and of U^T are never written: zero them once
   if (cudaMemcpy(F->d_layers, F->layers.data(), sizeof(LayerDev) * L, cudaMemcpyHostToDevice) != cudaSuccess ||
