@@ -255,12 +255,29 @@ MC_D int knot_cell_f(const float* t, int n, float v) {
 // out as one contiguous range.
 constexpr int kPdfTile = 512;
 constexpr size_t kPdfSmemMax = 224 * 1024;
-inline size_t pdf_smem_bytes(const PdfDev& p) {
-  return size_t(p.nq) * p.nx * p.nfp * 4 + size_t(kPdfTile) * p.nflav * 4 + 8 * size_t(p.nx + p.nq);
+// shared memory: the grid, the FP32 output staging, the knots and their
+// reciprocal spacings, then per point of a tile its setup (log x, log Q^2 and
+// the two cells) and the gather order
+__host__ __device__ inline size_t pdf_setup_offset(const PdfDev& p) {
+  return ((size_t(p.nq) * p.nx * p.nfp * 4 + size_t(kPdfTile) * p.nflav * 4 + 8 * size_t(p.nx + p.nq)) + 15) / 16 * 16;
 }
+inline size_t pdf_smem_bytes(const PdfDev& p) { return pdf_setup_offset(p) + size_t(kPdfTile) * (16 + 4); }
+
+// Points of a tile are gathered in an order that spreads the 16-byte bank
+// groups: the stencil of a point starts at float4 index base = (row of its
+// first Q knot x nx + its first x knot) x nfp / 4 and its sixteen loads sit at
+// offsets common to all interior points, so when the 8 lanes of a
+// quarter-warp hold points with distinct base mod 8 every load of the
+// quarter-warp is one wavefront.  Pass 1 finds each point's cells and key
+// (base mod 8) and ranks it within its key; the gather order interleaves the
+// keys rank by rank (position = sum over keys of min(count, rank) + the keys
+// below its own that still have a point of that rank).  Pass 2 evaluates the
+// point at its position, writing its outputs to the point's own staging row,
+// so results and output order do not depend on the order.
 __global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf, long long n, const double* x,
                                                                       const double* q2, double* out) {
   extern __shared__ __align__(16) unsigned char pdf_smem[];
+  __shared__ int cnt[8];
   float4* tab = reinterpret_cast<float4*>(pdf_smem);
   const int nx = pdf.nx, nq = pdf.nq, nfl = pdf.nflav, nf4 = pdf.nfp / 4;
   float* stage = reinterpret_cast<float*>(pdf_smem + size_t(nq) * nx * pdf.nfp * 4);
@@ -268,6 +285,8 @@ __global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf,
   float* rxf = lxf + nx;
   float* lqf = rxf + nx;  // [nq], [nq]
   float* rqf = lqf + nq;
+  float4* pset = reinterpret_cast<float4*>(pdf_smem + pdf_setup_offset(pdf));  // [kPdfTile]
+  int* perm = reinterpret_cast<int*>(pset + kPdfTile);                        // [kPdfTile]
   {
     const float4* g = reinterpret_cast<const float4*>(pdf.xf32t);
     const int n4 = nq * nx * nf4;
@@ -284,19 +303,47 @@ __global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf,
   __syncthreads();
   const long long ntiles = (n + kPdfTile - 1) / kPdfTile;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long i0 = tile * kPdfTile, i = i0 + threadIdx.x;
-    float* mine = stage + threadIdx.x * nfl;
-    if (i < n) {
+    const long long i0 = tile * kPdfTile;
+    const int npts = int(n - i0 < kPdfTile ? n - i0 : kPdfTile);
+    // pass 1: cells and key of this thread's point
+    if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int key = 0, rank = 0;
+    if (int(threadIdx.x) < npts) {
+      const long long i = i0 + threadIdx.x;
       const double xv = x[i], qv = q2[i];
       // x_lo, q2_lo > 0, so a NaN or a negative query fails one of the tests
       if (!(pos_f64_le(pdf.x_lo, xv) && pos_f64_le(xv, pdf.x_hi) && pos_f64_le(pdf.q2_lo, qv) &&
             pos_f64_le(qv, pdf.q2_hi))) {
-        for (int fl = 0; fl < nfl; ++fl) mine[fl] = __int_as_float(0x7fc00000);
+        pset[threadIdx.x] = make_float4(0.0f, 0.0f, __int_as_float(-1), __int_as_float(-1));
       } else {
         const float lx = fminf(fmaxf(log_f64_to_f32(xv), lxf[0]), lxf[nx - 1]);
         const float lq = fminf(fmaxf(log_f64_to_f32(qv), lqf[0]), lqf[nq - 1]);
+        const int iq = knot_cell_f(lqf, nq, lq), ix = knot_cell_f(lxf, nx, lx);
+        pset[threadIdx.x] = make_float4(lx, lq, __int_as_float(ix), __int_as_float(iq));
+        key = ((max(iq - 1, 0) * nx + max(ix - 1, 0)) * nf4) & 7;
+      }
+      rank = atomicAdd(&cnt[key], 1);
+    }
+    __syncthreads();
+    if (int(threadIdx.x) < npts) {
+      int pos = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) pos += min(cnt[k], rank) + (k < key && cnt[k] > rank ? 1 : 0);
+      perm[pos] = threadIdx.x;
+    }
+    __syncthreads();
+    // pass 2: the point at this thread's position in the gather order
+    if (int(threadIdx.x) < npts) {
+      const int pt = perm[threadIdx.x];
+      float* mine = stage + pt * nfl;
+      const float4 su = pset[pt];
+      const int ix = __float_as_int(su.z), iq = __float_as_int(su.w);
+      if (ix < 0) {
+        for (int fl = 0; fl < nfl; ++fl) mine[fl] = __int_as_float(0x7fc00000);
+      } else {
+        const float lx = su.x, lq = su.y;
         // Q weights of the knots j0 .. j0+3 (as q_weights)
-        const int iq = knot_cell_f(lqf, nq, lq);
         const int j0 = iq - 1;
         float w[4];
         {
@@ -324,7 +371,6 @@ __global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf,
           add_slope(iq, (q3 - 2.0f * q2_ + tq) * hq);
           add_slope(iq + 1, (q3 - q2_) * hq);
         }
-        const int ix = knot_cell_f(lxf, nx, lx);
         const float h = lxf[ix + 1] - lxf[ix];
         const float tau = (lx - lxf[ix]) * rxf[ix];
         int ii[4];
@@ -372,7 +418,6 @@ __global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf,
       }
     }
     __syncthreads();
-    const long long npts = n - i0 < kPdfTile ? n - i0 : kPdfTile;
     double* dst = out + i0 * nfl;
     for (int k = threadIdx.x; k < npts * nfl; k += kPdfTile) dst[k] = f32_to_f64(stage[k]);
     __syncthreads();
