@@ -24,7 +24,17 @@ pass, device-side acceptance-rejection and export of the accepted events,
 and the native LHE writer's throughput on them); and "samplers": RAMBO, the
 hierarchical generator and three-channel sampling side by side (time per
 iteration, variance per event, unweighting efficiency); and "pp_ttbarj": the
-higher-multiplicity process p p -> t tbar + parton (all partonic channels).
+higher-multiplicity process p p -> t tbar + parton (all partonic channels);
+"c2": plain FP64 VEGAS of p p -> t tbar at its configured size (10 x 1e6)
+against the oracle's run and the closed-form cross section; "oracle_check":
+one full 1e7-event FP32 iteration of the benchmark workload against the FP64
+oracle at identical points (integral, bin counts, and per-event errors over
+the CPU-baseline sample); "fma_peaks": the measured FP32 / FP64 FMA rates, the
+roofline's denominator; "sharded": one integration split across the ranks.
+
+The roofline's numerator is the algorithmic FLOP of the event counted by the
+oracle with an operation-counting scalar (tests/golden/ggttg_opcount.json);
+the kernel's executed FLOP (ncu) is reported beside it.
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (a
 bounded sample of events per step on the host cores).
