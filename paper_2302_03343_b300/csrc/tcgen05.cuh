@@ -11,6 +11,10 @@ namespace mc {
 namespace {
 
 constexpr uint32_t kSpinLimit = 1u << 20;  // about a second of try_wait polling
+// Longest time one try_wait may suspend the calling thread while the phase is
+// incomplete (ns): a waiting warp sleeps instead of taking issue slots from
+// the warps that do the work, and kSpinLimit tries stay about a second.
+constexpr uint32_t kTryWaitNs = 1000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -25,9 +29,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kTryWaitNs)
       : "memory");
   return ok != 0;
 }
