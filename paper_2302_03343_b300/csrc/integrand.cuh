@@ -185,6 +185,97 @@ MC_D double gg_weight(const KernelArgs& a, const GgKin<R>& kin, R me2) {
     return double(kin.lgg) * double(me2) / (2.0 * double(kin.shat)) * kin.psw * a.prm.gev2pb;
 }
 
+// p p -> t tbar + parton, split like gg -> t tbar g for the warp-specialised
+// kernel.  The kinematic part: every partonic channel at one point of the
+// hierarchical three-body phase space (the light parton massless), the
+// parton's cuts in the lab frame, and the seven channel luminosities summed
+// over the five light flavours, lum = {gg, q qbar, qbar q, q g, g q,
+// qbar g, g qbar}.  Returns 1 inside the cuts (kin and lum filled), else 0.
+template <class R>
+MC_D int ppj_kinematics(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, GgKin<R>* kin, R* lum, double* rec) {
+  const Params& p = a.prm;
+  const double s = p.sqrt_s * p.sqrt_s;
+  const R x1 = x[0], x2 = x[1];
+  const R m = R(p.m_top);
+  const R shat = sizeof(R) == 4 ? R(x1 * x2 * R(s)) : R(double(x1) * double(x2) * s);
+  rec_put(rec, 77, x1); rec_put(rec, 78, x2); rec_put(rec, 79, shat);
+  if (!(shat > R(4) * m * m)) return 0;
+  const R rs = m_sqrt(shat);
+  v4<double> kd[3];
+  double psw;
+  hierarchical3<R>(double(m), double(rs), x + 2, kd, &psw);
+  for (int i = 0; i < 3; ++i) kin->k[i] = vcast<R>(kd[i]);
+  kin->rs = rs;
+  kin->shat = shat;
+  kin->psw = psw;
+  if (rec) {
+    const v4<R> pa = {rs * R(0.5), R(0), R(0), rs * R(0.5)}, pb = {rs * R(0.5), R(0), R(0), -rs * R(0.5)};
+    rec_p4(rec, 0, pa); rec_p4(rec, 1, pb); rec_p4(rec, 2, kin->k[0]); rec_p4(rec, 3, kin->k[1]);
+    rec_p4(rec, 4, kin->k[2]);
+    rec_put(rec, 84, psw);
+  }
+  // cuts on the light parton in the lab frame
+  const v4<R>& pk = kin->k[2];
+  const R pt2 = pk.x * pk.x + pk.y * pk.y, ptc = R(p.ptcut_g);
+  const R pabs = m_sqrt(pt2 + pk.z * pk.z);
+  const R fwd = (pabs + pk.z) * x1, bwd = (pabs - pk.z) * x2, e2 = R(a.e2eta);
+  if (!(pt2 > ptc * ptc && fwd < e2 * bwd && bwd < e2 * fwd)) return 0;
+  const R lx1 = m_log(x1), lx2 = m_log(x2);
+  const R g1 = pdf_interp_1d(pdf.tab[0], lx1) / x1, g2x = pdf_interp_1d(pdf.tab[0], lx2) / x2;
+  R q1 = R(0), qb1 = R(0), q2 = R(0), qb2 = R(0), lqq = R(0), lqbq = R(0);
+#pragma unroll
+  for (int f = 1; f <= 5; ++f) {
+    const R a1 = pdf_interp_1d(pdf.tab[f], lx1) / x1, ab1 = pdf_interp_1d(pdf.tab[f + 5], lx1) / x1;
+    const R a2 = pdf_interp_1d(pdf.tab[f], lx2) / x2, ab2 = pdf_interp_1d(pdf.tab[f + 5], lx2) / x2;
+    q1 += a1; qb1 += ab1; q2 += a2; qb2 += ab2;
+    lqq += a1 * ab2;
+    lqbq += ab1 * a2;
+  }
+  lum[0] = g1 * g2x;
+  lum[1] = lqq;
+  lum[2] = lqbq;
+  lum[3] = q1 * g2x;
+  lum[4] = g1 * q2;
+  lum[5] = qb1 * g2x;
+  lum[6] = g1 * qb2;
+  return 1;
+}
+
+// The |M|^2 part: gg -> t tbar g and the six light-quark channels at the
+// event, weighted by the luminosities: f = sum_c lum_c <|M|^2>_c / (2 shat)
+// * w_PS * gev2pb (the VEGAS Jacobian is applied by the caller).  me (may be
+// null) receives the seven |M|^2 in the order of lum.
+template <class R>
+MC_D double ppj_weight(const KernelArgs& a, const GgKin<R>& kin, const R* lum, R* me) {
+  const Params& p = a.prm;
+  const R rs = kin.rs, m = R(p.m_top);
+  const v4<R> pa = {rs * R(0.5), R(0), R(0), rs * R(0.5)}, pb = {rs * R(0.5), R(0), R(0), -rs * R(0.5)};
+  const v4<R>& pt = kin.k[0];
+  const v4<R>& ptb = kin.k[1];
+  const v4<R>& pk = kin.k[2];
+  const R g2c = R(4.0 * kPi * p.alpha_s);
+  const R* cm;
+  if constexpr (sizeof(R) == 4) cm = a.cqqf; else cm = a.cqq;
+  const R me_gg = gg_me2<R>(a, kin);
+  // the light-quark channels: packed complex arithmetic in FP32
+  auto qline = [&](int kind, const v4<R>& x, const v4<R>& y) -> R {
+    if constexpr (sizeof(R) == 4)
+      return me2_qline_ttbarg_p(kind, x, y, pt, ptb, pk, m, g2c, cm);
+    else
+      return me2_qline_ttbarg<R>(kind, x, y, pt, ptb, pk, m, g2c, cm);
+  };
+  const R mq[6] = {qline(0, pa, pb), qline(0, pb, pa), qline(1, pa, pb),
+                   qline(1, pb, pa), qline(2, pa, pb), qline(2, pb, pa)};
+  const double sum = double(lum[0]) * double(me_gg) + double(lum[1]) * double(mq[0]) +
+                     double(lum[2]) * double(mq[1]) + double(lum[3]) * double(mq[2]) + double(lum[4]) * double(mq[3]) +
+                     double(lum[5]) * double(mq[4]) + double(lum[6]) * double(mq[5]);
+  if (me) {
+    me[0] = me_gg;
+    for (int c = 0; c < 6; ++c) me[c + 1] = mq[c];
+  }
+  return sum / (2.0 * double(kin.shat)) * kin.psw * p.gev2pb;
+}
+
 // Integrand at the point x of the unit hypercube; rec (may be null) receives
 // the intermediates in the MC_REC_* layout.
 template <int PROC, class R>
@@ -253,71 +344,17 @@ MC_D EventOut integrand(const KernelArgs& a, const SmPdf<R>& pdf, const R* x, do
       rec_put(rec, 82, me2);
     }
   } else if constexpr (PROC == P_PP_TTBARJ) {
-    // every partonic channel at one point of the hierarchical three-body
-    // phase space (the light parton massless): gg, q qbar, qbar q, q g, g q,
-    // qbar g, g qbar, luminosities summed over the five light flavours
-    const R x1 = x[0], x2 = x[1];
-    const R m = R(p.m_top);
-    const R shat = sizeof(R) == 4 ? R(x1 * x2 * R(s)) : R(double(x1) * double(x2) * s);
-    rec_put(rec, 77, x1); rec_put(rec, 78, x2); rec_put(rec, 79, shat);
-    if (!(shat > R(4) * m * m)) {
-      out.pass = 0;
-      return out;
-    }
-    const R rs = m_sqrt(shat);
-    v4<double> kd[3];
-    double psw;
-    hierarchical3<R>(double(m), double(rs), x + 2, kd, &psw);
     GgKin<R> kin;
-    for (int i = 0; i < 3; ++i) kin.k[i] = vcast<R>(kd[i]);
-    kin.rs = rs;
-    const v4<R> pa = {rs * R(0.5), R(0), R(0), rs * R(0.5)}, pb = {rs * R(0.5), R(0), R(0), -rs * R(0.5)};
-    const v4<R>& pt = kin.k[0];
-    const v4<R>& ptb = kin.k[1];
-    const v4<R>& pk = kin.k[2];
-    if (rec) {
-      rec_p4(rec, 0, pa); rec_p4(rec, 1, pb); rec_p4(rec, 2, pt); rec_p4(rec, 3, ptb); rec_p4(rec, 4, pk);
-      rec_put(rec, 84, psw);
-    }
-    // cuts on the light parton in the lab frame
-    const R pt2 = pk.x * pk.x + pk.y * pk.y, ptc = R(p.ptcut_g);
-    const R pabs = m_sqrt(pt2 + pk.z * pk.z);
-    const R fwd = (pabs + pk.z) * x1, bwd = (pabs - pk.z) * x2, e2 = R(a.e2eta);
-    if (!(pt2 > ptc * ptc && fwd < e2 * bwd && bwd < e2 * fwd)) {
+    R lum[7];
+    if (ppj_kinematics<R>(a, pdf, x, &kin, lum, rec) != 1) {
       out.pass = 0;
       return out;
     }
-    const R lx1 = m_log(x1), lx2 = m_log(x2);
-    const R g1 = pdf_interp_1d(pdf.tab[0], lx1) / x1, g2x = pdf_interp_1d(pdf.tab[0], lx2) / x2;
-    R q1 = R(0), qb1 = R(0), q2 = R(0), qb2 = R(0), lqq = R(0), lqbq = R(0);
-#pragma unroll
-    for (int f = 1; f <= 5; ++f) {
-      const R a1 = pdf_interp_1d(pdf.tab[f], lx1) / x1, ab1 = pdf_interp_1d(pdf.tab[f + 5], lx1) / x1;
-      const R a2 = pdf_interp_1d(pdf.tab[f], lx2) / x2, ab2 = pdf_interp_1d(pdf.tab[f + 5], lx2) / x2;
-      q1 += a1; qb1 += ab1; q2 += a2; qb2 += ab2;
-      lqq += a1 * ab2;
-      lqbq += ab1 * a2;
-    }
-    const R g2c = R(4.0 * kPi * p.alpha_s);
-    const R* cm;
-    if constexpr (sizeof(R) == 4) cm = a.cqqf; else cm = a.cqq;
-    const R me_gg = gg_me2<R>(a, kin);
-    // the light-quark channels: packed complex arithmetic in FP32
-    auto qline = [&](int kind, const v4<R>& x, const v4<R>& y) -> R {
-      if constexpr (sizeof(R) == 4)
-        return me2_qline_ttbarg_p(kind, x, y, pt, ptb, pk, m, g2c, cm);
-      else
-        return me2_qline_ttbarg<R>(kind, x, y, pt, ptb, pk, m, g2c, cm);
-    };
-    const R me[6] = {qline(0, pa, pb), qline(0, pb, pa), qline(1, pa, pb),
-                     qline(1, pb, pa), qline(2, pa, pb), qline(2, pb, pa)};
-    const double sum = double(g1 * g2x) * double(me_gg) + double(lqq) * double(me[0]) + double(lqbq) * double(me[1]) +
-                       double(q1 * g2x) * double(me[2]) + double(g1 * q2) * double(me[3]) +
-                       double(qb1 * g2x) * double(me[4]) + double(g1 * qb2) * double(me[5]);
-    out.f = sum / (2.0 * double(shat)) * psw * p.gev2pb;
+    R me[7];
+    out.f = ppj_weight<R>(a, kin, lum, rec ? me : nullptr);
     if (rec) {
-      rec_put(rec, 80, g1 * g2x); rec_put(rec, 81, lqq); rec_put(rec, 82, me_gg); rec_put(rec, 83, me[0]);
-      for (int c = 0; c < 5; ++c) rec_put(rec, 89 + c, me[c + 1]);
+      rec_put(rec, 80, lum[0]); rec_put(rec, 81, lum[1]); rec_put(rec, 82, me[0]); rec_put(rec, 83, me[1]);
+      for (int c = 0; c < 5; ++c) rec_put(rec, 89 + c, me[c + 2]);
     }
   } else {  // Gaussian
     const R sg = R(p.gauss_sigma);

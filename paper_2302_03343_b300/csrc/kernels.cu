@@ -451,7 +451,7 @@ static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
 }
 
 bool integrand_ws(int proc, bool fp64) {
-  return !fp64 && (proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_GG_TTBARG_MC);
+  return !fp64 && (proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_GG_TTBARG_MC || proc == P_PP_TTBARJ);
 }
 int integrand_threads(int proc, bool fp64) { return integrand_ws(proc, fp64) ? kWsThreads : kBlock; }
 // events one block takes per round of its grid-stride loop
@@ -462,6 +462,7 @@ static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, 
   if (!RECORD && integrand_ws(proc, fp64))
     return proc == P_GG_TTBARG      ? launch_ws<P_GG_TTBARG>(a, grid, st)
            : proc == P_GG_TTBARG_7D ? launch_ws<P_GG_TTBARG_7D>(a, grid, st)
+           : proc == P_PP_TTBARJ    ? launch_ws<P_PP_TTBARJ>(a, grid, st)
                                     : launch_ws<P_GG_TTBARG_MC>(a, grid, st);
   switch (proc) {
     case P_EE_MUMU:

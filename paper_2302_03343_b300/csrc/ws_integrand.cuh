@@ -63,15 +63,22 @@ constexpr int kWsMaxSlots = 4 * kWsProducerWarps;  // mbarrier arrays, sized for
 // record words of one event (structure of arrays inside a slot: word j of
 // lane e at [j][e]): k[3] (12), rs, lgg, flux, jac, psw (2 words), bins (4),
 // the event's index in the launch (weights pass only), and for the
-// three-channel process its channel and the ratios p_j / p (3)
+// three-channel process its channel and the ratios p_j / p (3); for
+// p p -> t tbar + parton kWLgg holds the gg luminosity, kWFlux the partonic
+// s and kWLum the other six channel luminosities
 enum : int {
   kWK = 0, kWRs = 12, kWLgg = 13, kWFlux = 14, kWJac = 15, kWPsw = 16, kWBin = 18, kWIdx = 22, kWCh = 23,
-  kWDens = 24
+  kWDens = 24, kWLum = 23
 };
-// words per record: 23, and 27 for the three-channel process (the ring of
-// the others stays at 23 words so their shared-memory carveout, and the L1
-// left for their register spills, does not change)
-MC_HD constexpr int ws_words(int proc) { return proc == P_GG_TTBARG_MC ? 27 : 23; }
+// words per record: 23, 27 for the three-channel process and 29 for
+// p p -> t tbar + parton (the ring of the others stays at 23 words so their
+// shared-memory carveout, and the L1 left for their register spills, does
+// not change)
+MC_HD constexpr int ws_words(int proc) {
+  return proc == P_GG_TTBARG_MC ? 27 : (proc == P_PP_TTBARJ ? 29 : 23);
+}
+// flavour tables of the process in shared memory (the gluon, or all eleven)
+MC_HD constexpr int ws_flavours(int proc) { return proc == P_PP_TTBARJ ? 11 : 1; }
 constexpr unsigned long long kWsWaitNs = 2000000000ull;
 // Registers per thread: the launch gets kWsRegs (65536 / threads, rounded
 // down to a multiple of 8); producers give up to kWsProducerRegs, consumers
@@ -123,7 +130,7 @@ inline size_t ws_smem_bytes(int proc, int ndim, int nbins, int nx, bool rows) {
   const size_t ring = size_t(ws_slots(proc)) * kWsProducerWarps * ws_words(proc) * 32 * 4 +
                       (rows ? size_t(kWsConsumerWarps) * 32 * kWsRowBytes : 0);
   const size_t hist = ((size_t(ndim) * nbins * 8 + 15) / 16) * 16;
-  return ring + hist + 4 * (size_t(ndim) * (nbins + 1) + size_t(nx) * 3);
+  return ring + hist + 4 * (size_t(ndim) * (nbins + 1) + size_t(nx) * (1 + 2 * ws_flavours(proc)));
 }
 inline bool ws_rows_in_smem(int proc, int ndim, int nbins, int nx) {
   return proc == P_GG_TTBARG_MC && ws_smem_bytes(proc, ndim, nbins, nx, true) <= kWsSmemRows;
@@ -182,6 +189,7 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
     float jac = 1.0f;
     int st = 0, ch = 0;
     float dr[kChannels] = {0.0f, 0.0f, 0.0f};
+    float lum[PROC == P_PP_TTBARJ ? 7 : 1];
     if constexpr (PROC == P_GG_TTBARG_MC) {
       if (i < hi) {
         McEvent<float> e;
@@ -216,7 +224,11 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
           atomicAdd(&sh_n[dd * nb + b], 1u);
         }
       }
-      st = gg_kinematics<PROC, float>(a, pdf, x, &kin, nullptr);
+      if constexpr (PROC == P_PP_TTBARJ) {
+        st = ppj_kinematics<float>(a, pdf, x, &kin, lum, nullptr);
+      } else {
+        st = gg_kinematics<PROC, float>(a, pdf, x, &kin, nullptr);
+      }
       if (st == -5) ++acc.nnoconv;
       if (WOUT && st != 1) a.wout[i] = 0.0;
     }
@@ -239,8 +251,15 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
         r[(kWK + 4 * j + 3) * 32] = __float_as_uint(kin.k[j].z);
       }
       r[kWRs * 32] = __float_as_uint(kin.rs);
-      r[kWLgg * 32] = __float_as_uint(kin.lgg);
-      r[kWFlux * 32] = __float_as_uint(kin.flux);
+      if constexpr (PROC == P_PP_TTBARJ) {
+        r[kWLgg * 32] = __float_as_uint(lum[0]);
+        r[kWFlux * 32] = __float_as_uint(kin.shat);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) r[(kWLum + j) * 32] = __float_as_uint(lum[1 + j]);
+      } else {
+        r[kWLgg * 32] = __float_as_uint(kin.lgg);
+        r[kWFlux * 32] = __float_as_uint(kin.flux);
+      }
       r[kWJac * 32] = __float_as_uint(jac);
       r[kWPsw * 32] = __double2loint(kin.psw);
       r[(kWPsw + 1) * 32] = __double2hiint(kin.psw);
@@ -322,15 +341,25 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
         kin.k[j] = {__uint_as_float(r[(kWK + 4 * j + 0) * 32]), __uint_as_float(r[(kWK + 4 * j + 1) * 32]),
                     __uint_as_float(r[(kWK + 4 * j + 2) * 32]), __uint_as_float(r[(kWK + 4 * j + 3) * 32])};
       kin.rs = __uint_as_float(r[kWRs * 32]);
-      kin.lgg = __uint_as_float(r[kWLgg * 32]);
-      kin.flux = __uint_as_float(r[kWFlux * 32]);
       const float jac = __uint_as_float(r[kWJac * 32]);
       kin.psw = __hiloint2double(int(r[(kWPsw + 1) * 32]), int(r[kWPsw * 32]));
       uint32_t binw[NW];
 #pragma unroll
       for (int j = 0; j < NW; ++j) binw[j] = r[(kWBin + j) * 32];
-      const float me2 = gg_me2<float>(a, kin, rows);
-      double w = gg_weight<float>(a, kin, me2) * double(jac);
+      double w;
+      if constexpr (PROC == P_PP_TTBARJ) {
+        kin.shat = __uint_as_float(r[kWFlux * 32]);
+        float lum[7];
+        lum[0] = __uint_as_float(r[kWLgg * 32]);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) lum[1 + j] = __uint_as_float(r[(kWLum + j) * 32]);
+        w = ppj_weight<float>(a, kin, lum, nullptr) * double(jac);
+      } else {
+        kin.lgg = __uint_as_float(r[kWLgg * 32]);
+        kin.flux = __uint_as_float(r[kWFlux * 32]);
+        const float me2 = gg_me2<float>(a, kin, rows);
+        w = gg_weight<float>(a, kin, me2) * double(jac);
+      }
       if (!isfinite(w)) {
         ++acc.nbad;
         w = 0.0;
@@ -372,7 +401,8 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
 // memory (ws_rows_in_smem).
 template <int PROC, bool WOUT, bool SMROWS>
 __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs a) {
-  static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D || PROC == P_GG_TTBARG_MC, "gg -> t tbar g only");
+  static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D || PROC == P_GG_TTBARG_MC || PROC == P_PP_TTBARJ,
+                "gg -> t tbar g and p p -> t tbar + parton only");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kWsMaxSlots], empty[kWsMaxSlots];
   __shared__ int count[kWsMaxSlots];
@@ -402,12 +432,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
   }
   SmPdf<float> pdf;
   {
+    constexpr int NFL = ws_flavours(PROC);
     const int nx = a.pdf.nx;
     float* t = sh_pdf;
     float* f = t + nx;
-    float* d = f + nx;
-    build_pdf_tables<float>(a.pdf, a.logq2_f, a.fl, 1, t, f, d);  // ends with __syncthreads
-    pdf.tab[0] = {t, f, d, nx};
+    float* d = f + NFL * nx;
+    build_pdf_tables<float>(a.pdf, a.logq2_f, a.fl, NFL, t, f, d);  // ends with __syncthreads
+    for (int k = 0; k < NFL; ++k) pdf.tab[k] = {t, f + k * nx, d + k * nx, nx};
   }
 
   Acc acc;
