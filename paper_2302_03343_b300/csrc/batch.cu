@@ -13,7 +13,7 @@
 // shapes on the batch itself (autotune()).
 //
 // In FP32 mode the batch runs batch_ws_kernel instead: one block of
-// kWsThreads per SM; a tile of gg -> t tbar g events goes through the
+// ws_threads(P_GG_TTBARG) per SM; a tile of gg -> t tbar g events goes through the
 // warp-specialised producer/consumer path of ws_integrand.cuh (each tile
 // ends every producer stream with end markers, so the ring is empty between
 // tiles), any other tile through all threads of the block one event each.
@@ -149,18 +149,25 @@ __global__ void __launch_bounds__(BLOCK) batch_kernel(BatchArgs b) {
 }
 
 // FP32 batch kernel with the warp-specialised path for gg -> t tbar g tiles
-// (both processes share the ring of P_GG_TTBARG: 23 words, ws_slots slots).
-__global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
+// (both processes share the launch shape and the ring of P_GG_TTBARG: 23
+// words, ws_slots slots).
+constexpr int kBwProducers = ws_producer_warps(P_GG_TTBARG), kBwThreads = ws_threads(P_GG_TTBARG);
+__global__ void __launch_bounds__(kBwThreads, 1) batch_ws_kernel(BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int kSlots = ws_slots(P_GG_TTBARG) * kWsProducerWarps;
-  static_assert(ws_slots(P_GG_TTBARG) == ws_slots(P_GG_TTBARG_7D) && ws_words(P_GG_TTBARG) == ws_words(P_GG_TTBARG_7D),
-                "the two processes share one ring");
+  constexpr int kSlots = ws_slots(P_GG_TTBARG) * kBwProducers;
+  static_assert(ws_slots(P_GG_TTBARG) == ws_slots(P_GG_TTBARG_7D) && ws_words(P_GG_TTBARG) == ws_words(P_GG_TTBARG_7D) &&
+                    ws_producer_warps(P_GG_TTBARG) == ws_producer_warps(P_GG_TTBARG_7D) &&
+                    ws_consumer_warps(P_GG_TTBARG) == ws_consumer_warps(P_GG_TTBARG_7D) &&
+                    ws_producer_regs(P_GG_TTBARG) == ws_producer_regs(P_GG_TTBARG_7D) &&
+                    ws_consumer_regs(P_GG_TTBARG) == ws_consumer_regs(P_GG_TTBARG_7D),
+                "the two processes share one ring and one launch shape");
+  static_assert(ws_shape_ok(P_GG_TTBARG), "launch shape");
   __shared__ __align__(8) uint64_t full[kSlots], empty[kSlots];
   __shared__ int count[kSlots];
   __shared__ int failed;
   __shared__ KernelArgs ka;
   __shared__ int sh_tile;
-  __shared__ BlockPartial warp_part[kWsThreads / 32];
+  __shared__ BlockPartial warp_part[kBwThreads / 32];
   const int nb = b.nbins;
   const int nhist = MC_MAX_DIM * nb, nedge = MC_MAX_DIM * (nb + 1);
   const WsRing ring = {reinterpret_cast<uint32_t*>(smem), full, empty, count};
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
   float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
   float* sh_pdf = sh_edges + nedge;
 
-  for (int i = threadIdx.x; i < nhist; i += kWsThreads) {
+  for (int i = threadIdx.x; i < nhist; i += kBwThreads) {
     sh_w2[i] = 0.0f;
     sh_n[i] = 0u;
   }
@@ -199,7 +206,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
   auto flush = [&](int item) {
     const BatchItem& it = b.items[item];
     const int n = it.args.ndim * nb;
-    for (int i = threadIdx.x; i < n; i += kWsThreads) {
+    for (int i = threadIdx.x; i < n; i += kBwThreads) {
       if (sh_n[i]) {
         atomicAdd(&it.args.hist_n[i], sh_n[i]);
         atomicAdd(&it.args.hist_w2[i], double(sh_w2[i]));
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
   };
   // slot sequence numbers, carried over from tile to tile
   int seq = 0;
-  int q0 = (warp - kWsProducerWarps) / kWsProducerWarps, q1 = q0;
+  int q0 = (warp - kBwProducers) / kBwProducers, q1 = q0;
   for (;;) {
     if (threadIdx.x == 0) sh_tile = int(atomicAdd(b.counter, 1u));
     __syncthreads();
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
         ka.iteration = iteration;
       }
       const int ne = it.args.ndim * (nb + 1);
-      for (int i = threadIdx.x; i < ne; i += kWsThreads) sh_edges[i] = it.args.edges32[i];
+      for (int i = threadIdx.x; i < ne; i += kBwThreads) sh_edges[i] = it.args.edges32[i];
       cur = item;
     }
     __syncthreads();
@@ -235,35 +242,35 @@ __global__ void __launch_bounds__(kWsThreads, 1) batch_ws_kernel(BatchArgs b) {
     Acc acc;
     bool ok = true;
     if (it.proc == P_GG_TTBARG || it.proc == P_GG_TTBARG_7D) {
-      if (warp < kWsProducerWarps) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
+      if (warp < kBwProducers) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(ws_producer_regs(P_GG_TTBARG)));
         ok = it.proc == P_GG_TTBARG
                  ? ws_produce<P_GG_TTBARG, false>(ka, pdf, sh_edges, sh_n, ring, warp, start, end, warp,
-                                                  kWsProducerWarps, seq, acc)
+                                                  kBwProducers, seq, acc)
                  : ws_produce<P_GG_TTBARG_7D, false>(ka, pdf, sh_edges, sh_n, ring, warp, start, end, warp,
-                                                     kWsProducerWarps, seq, acc);
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsRegs));
+                                                     kBwProducers, seq, acc);
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(ws_regs(P_GG_TTBARG)));
       } else {
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
-        const int c = warp - kWsProducerWarps;
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(ws_consumer_regs(P_GG_TTBARG)));
+        const int c = warp - kBwProducers;
         ok = it.proc == P_GG_TTBARG ? ws_consume<P_GG_TTBARG, false>(ka, sh_w2, ring, NoRows{}, c, q0, q1, acc)
                                     : ws_consume<P_GG_TTBARG_7D, false>(ka, sh_w2, ring, NoRows{}, c, q0, q1, acc);
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(ws_regs(P_GG_TTBARG)));
       }
     } else {
       switch (it.proc) {
         case P_EE_MUMU:
-          for (long long i = start + threadIdx.x; i < end; i += kWsThreads)
+          for (long long i = start + threadIdx.x; i < end; i += kBwThreads)
             process_event<P_EE_MUMU, false, false, float, float>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i), nullptr,
                                                                  acc);
           break;
         case P_PP_TTBAR:
-          for (long long i = start + threadIdx.x; i < end; i += kWsThreads)
+          for (long long i = start + threadIdx.x; i < end; i += kBwThreads)
             process_event<P_PP_TTBAR, false, false, float, float>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i),
                                                                   nullptr, acc);
           break;
         default:
-          for (long long i = start + threadIdx.x; i < end; i += kWsThreads)
+          for (long long i = start + threadIdx.x; i < end; i += kBwThreads)
             process_event<P_GAUSS, false, false, float, float>(ka, pdf, sh_edges, sh_w2, sh_n, uint64_t(i), nullptr,
                                                                acc);
       }
@@ -285,7 +292,7 @@ cudaError_t launch_batch_ws(const BatchArgs& b, int grid, size_t smem, cudaStrea
   (void)cudaGetLastError();
   const cudaError_t e = cudaFuncSetAttribute(batch_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  batch_ws_kernel<<<grid, kWsThreads, smem, st>>>(b);
+  batch_ws_kernel<<<grid, kBwThreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 
@@ -453,7 +460,7 @@ int build_tiles(mc_batch b) {
   b->smem = ((nhist * 12 + 15) / 16) * 16 + r * (size_t(MC_MAX_DIM) * (b->nbins + 1)) +
             (b->pdf ? r * size_t(b->pdf->nx) * 23 : 0);
   if (b->ws)
-    b->smem = size_t(mc::ws_slots(mc::P_GG_TTBARG)) * mc::kWsProducerWarps * mc::ws_words(mc::P_GG_TTBARG) * 32 * 4 +
+    b->smem = size_t(mc::ws_slots(mc::P_GG_TTBARG)) * mc::kBwProducers * mc::ws_words(mc::P_GG_TTBARG) * 32 * 4 +
               ((nhist * 8 + 15) / 16) * 16 + 4 * (size_t(MC_MAX_DIM) * (b->nbins + 1)) +
               (b->pdf ? 4 * size_t(b->pdf->nx) * 23 : 0);
   int sms = 1;
@@ -514,7 +521,7 @@ int autotune(mc_batch b, cudaStream_t st) {
   static const int kBlocks[] = {64, 128, 256};
   static const int kEpt[] = {2, 8, 32};
   float best = 1e30f;
-  int best_b = b->ws ? mc::kWsThreads : 128, best_e = b->ws ? 16 : 8;
+  int best_b = b->ws ? mc::kBwThreads : 128, best_e = b->ws ? 16 : 8;
   unsigned int it0 = 0;
   cudaMemcpy(&it0, b->d_iteration, sizeof(unsigned int), cudaMemcpyDeviceToHost);
   const size_t smem_r = sizeof(double) * MC_MAX_DIM * (3 * b->nbins + 2);
@@ -523,7 +530,7 @@ int autotune(mc_batch b, cudaStream_t st) {
           cudaSuccess)
     return bfail(MC_ECUDA, "mc_batch: refine kernel attribute");
   // warp-specialised kernel: one block shape, tiles of 4, 16 or 64 events per thread
-  static const int kBlocksWs[] = {mc::kWsThreads};
+  static const int kBlocksWs[] = {mc::kBwThreads};
   static const int kEptWs[] = {4, 16, 64};
   const int nbl = b->ws ? 1 : 3, nep = 3;
   const int* blocks = b->ws ? kBlocksWs : kBlocks;
@@ -601,7 +608,7 @@ int mc_batch_create(int n, const mc_integrand* itgs, const int64_t* nevents, mc_
   b->pdf = pdf;
   b->ws = prec == MC_FP32_KAHAN;
   if (b->ws) {
-    b->block = mc::kWsThreads;
+    b->block = mc::kBwThreads;
     b->events_per_thread = 16;
   }
   b->itg.assign(itgs, itgs + n);

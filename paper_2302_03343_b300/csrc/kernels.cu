@@ -446,16 +446,18 @@ static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
   (void)cudaGetLastError();
   const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  k<<<grid, kWsThreads, smem, st>>>(a);
+  k<<<grid, ws_threads(PROC), smem, st>>>(a);
   return cudaGetLastError();
 }
 
 bool integrand_ws(int proc, bool fp64) {
   return !fp64 && (proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_GG_TTBARG_MC || proc == P_PP_TTBARJ);
 }
-int integrand_threads(int proc, bool fp64) { return integrand_ws(proc, fp64) ? kWsThreads : kBlock; }
+int integrand_threads(int proc, bool fp64) { return integrand_ws(proc, fp64) ? ws_threads(proc) : kBlock; }
 // events one block takes per round of its grid-stride loop
-int integrand_block_events(int proc, bool fp64) { return integrand_ws(proc, fp64) ? 32 * kWsProducerWarps : kBlock; }
+int integrand_block_events(int proc, bool fp64) {
+  return integrand_ws(proc, fp64) ? 32 * ws_producer_warps(proc) : kBlock;
+}
 
 template <bool RECORD>
 static cudaError_t dispatch(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem, cudaStream_t st) {

@@ -1,4 +1,5 @@
-// Warp-specialised fused integrand kernel for gg -> t tbar g in FP32 mode.
+// Warp-specialised fused integrand kernel for gg -> t tbar g and
+// p p -> t tbar + parton in FP32 mode.
 //
 // The fused path of one event has two parts with very different hardware
 // profiles: the kinematics (Philox, VEGAS map, RAMBO with its FP64 conformal
@@ -9,7 +10,8 @@
 // every thread, a warp stalls for thousands of cycles in its FP64 section
 // and carries idle lanes through the |M|^2 for the events that were cut.
 //
-// Here each block (one per SM) splits its warps into two roles:
+// Here each block (one per SM) splits its warps into two roles (the shape
+// given for gg -> t tbar g; per process below):
 //  * 8 producer warps (two per SM sub-partition) walk the event range in
 //    chunks of 32, evaluate the kinematics, add every event to the bin-count
 //    histogram, and append the events that pass the cuts, compacted with a
@@ -27,8 +29,8 @@
 // slot and one end marker (count -1) for each consumer it feeds.  Sixteen
 // warps of 128 registers at launch, rebalanced to 88 (producers) and 168
 // (consumers) with setmaxnreg, measured fastest among the 4+8, 8+4 and 8+8
-// shapes on B300.  The compiled code of both roles is held to the launch's
-// 128 registers, so the consumers' |M|^2 runs on register spills, which
+// shapes on B300 for that process.  The compiled code of both roles is held
+// to the launch's 128 registers, so the consumers' |M|^2 runs on register spills, which
 // must stay in L1: the shared memory of a block is kept small for that
 // (see ws_rows_in_smem).
 //
@@ -39,27 +41,24 @@
 #include "event.cuh"
 #include "tcgen05.cuh"
 
-#ifndef WS_NP
-#define WS_NP 8
-#define WS_NC 8
-#define WS_PREGS 88
-#define WS_CREGS 168
-#endif
-
 namespace mc {
 
-// Launch shape: kWsProducerWarps producer warps and kWsConsumerWarps consumer
-// warps per block (each a multiple of 4, i.e. whole warpgroups, since the
-// register split below is per warpgroup), one block per SM.
-constexpr int kWsProducerWarps = WS_NP;
-constexpr int kWsConsumerWarps = WS_NC;
-constexpr int kWsThreads = 32 * (kWsProducerWarps + kWsConsumerWarps);
+// Launch shape, per process: ws_producer_warps producer warps and
+// ws_consumer_warps consumer warps per block (each a multiple of 4, i.e.
+// whole warpgroups, since the register split below is per warpgroup), one
+// block per SM.  gg -> t tbar g: 8 + 8 (the description above).
+// p p -> t tbar + parton: 4 + 8, so that the code of its seven-channel |M|^2
+// compiles to the 168 registers of a 12-warp launch instead of 128 (measured
+// on B300: 19.0 against 22.5 ms per 1e7 events with 8 + 8; the same 4 + 8
+// shape costs gg -> t tbar g 36 %).
+MC_HD constexpr int ws_producer_warps(int proc) { return proc == P_PP_TTBARJ ? 4 : 8; }
+MC_HD constexpr int ws_consumer_warps(int) { return 8; }
+MC_HD constexpr int ws_threads(int proc) { return 32 * (ws_producer_warps(proc) + ws_consumer_warps(proc)); }
 // Slots per producer warp (a producer holds up to two at once, so at least
 // three for the producer to work ahead of its consumer); 4 measured fastest
 // on B300 for every process (3 and 2 return 24 and 47 KB to L1 but starve
 // the three-channel consumers).
 MC_HD constexpr int ws_slots(int) { return 4; }
-constexpr int kWsMaxSlots = 4 * kWsProducerWarps;  // mbarrier arrays, sized for the deepest ring
 // record words of one event (structure of arrays inside a slot: word j of
 // lane e at [j][e]): k[3] (12), rs, lgg, flux, jac, psw (2 words), bins (4),
 // the event's index in the launch (weights pass only), and for the
@@ -80,25 +79,37 @@ MC_HD constexpr int ws_words(int proc) {
 // flavour tables of the process in shared memory (the gluon, or all eleven)
 MC_HD constexpr int ws_flavours(int proc) { return proc == P_PP_TTBARJ ? 11 : 1; }
 constexpr unsigned long long kWsWaitNs = 2000000000ull;
-// Registers per thread: the launch gets kWsRegs (65536 / threads, rounded
-// down to a multiple of 8); producers give up to kWsProducerRegs, consumers
-// take kWsConsumerRegs, and the two together stay within the launch's
-// registers, so the increase never waits on registers that are not there.
-constexpr int kWsRegs = (65536 / kWsThreads) / 8 * 8 > 248 ? 248 : (65536 / kWsThreads) / 8 * 8;
-constexpr int kWsProducerRegs = WS_PREGS, kWsConsumerRegs = WS_CREGS;
-static_assert(kWsProducerWarps % 4 == 0 && kWsConsumerWarps % 4 == 0, "roles must be whole warpgroups");
-static_assert(32 * kWsProducerWarps * kWsProducerRegs + 32 * kWsConsumerWarps * kWsConsumerRegs <=
-                  kWsThreads * kWsRegs,
-              "register split exceeds the launch's registers");
+// Registers per thread: the launch gets ws_regs (65536 / threads, rounded
+// down to a multiple of 8); producers give up to ws_producer_regs, consumers
+// take ws_consumer_regs, and the two together stay within the launch's
+// registers, so the increase never waits on registers that are not there
+// (ws_shape_ok, asserted in each kernel).
+MC_HD constexpr int ws_regs(int proc) {
+  return (65536 / ws_threads(proc)) / 8 * 8 > 248 ? 248 : (65536 / ws_threads(proc)) / 8 * 8;
+}
+MC_HD constexpr int ws_producer_regs(int) { return 88; }
+MC_HD constexpr int ws_consumer_regs(int proc) { return proc == P_PP_TTBARJ ? 208 : 168; }
 // Streams: producer p's slot sequence q = 0, 1, 2, ... goes to consumer
-// (p mod C) + P ((q mod kWsClasses)) when there are more consumers than
-// producers (C = kWsClasses P), and every consumer c serves the producers
-// c, c + C, ... (kWsStreams of them) when there are more producers.
-constexpr int kWsClasses = kWsConsumerWarps >= kWsProducerWarps ? kWsConsumerWarps / kWsProducerWarps : 1;
-constexpr int kWsStreams = kWsProducerWarps >= kWsConsumerWarps ? kWsProducerWarps / kWsConsumerWarps : 1;
-static_assert(kWsClasses * kWsProducerWarps == kWsConsumerWarps || kWsStreams * kWsConsumerWarps == kWsProducerWarps,
-              "warp counts must divide one another");
-static_assert(kWsStreams <= 2, "a consumer serves at most two producers");
+// (p mod C) + P ((q mod ws_classes)) when there are more consumers than
+// producers (C = ws_classes P), and every consumer c serves the producers
+// c, c + C, ... (ws_streams of them) when there are more producers.
+MC_HD constexpr int ws_classes(int proc) {
+  return ws_consumer_warps(proc) >= ws_producer_warps(proc) ? ws_consumer_warps(proc) / ws_producer_warps(proc) : 1;
+}
+MC_HD constexpr int ws_streams(int proc) {
+  return ws_producer_warps(proc) >= ws_consumer_warps(proc) ? ws_producer_warps(proc) / ws_consumer_warps(proc) : 1;
+}
+// whole warpgroups, a register split within the launch's registers, warp
+// counts that divide one another, at most two producers per consumer
+MC_HD constexpr bool ws_shape_ok(int proc) {
+  return ws_producer_warps(proc) % 4 == 0 && ws_consumer_warps(proc) % 4 == 0 &&
+         32 * ws_producer_warps(proc) * ws_producer_regs(proc) +
+                 32 * ws_consumer_warps(proc) * ws_consumer_regs(proc) <=
+             ws_threads(proc) * ws_regs(proc) &&
+         (ws_classes(proc) * ws_producer_warps(proc) == ws_consumer_warps(proc) ||
+          ws_streams(proc) * ws_consumer_warps(proc) == ws_producer_warps(proc)) &&
+         ws_streams(proc) <= 2;
+}
 
 MC_D unsigned long long ws_clock_ns() {
   unsigned long long t;
@@ -127,8 +138,8 @@ MC_D bool ws_wait(uint64_t* bar, uint32_t parity) {
 constexpr int kWsRowBytes = 12 * 32;
 constexpr size_t kWsSmemRows = 224 * 1024;  // 227 KB per block less the static shared memory
 inline size_t ws_smem_bytes(int proc, int ndim, int nbins, int nx, bool rows) {
-  const size_t ring = size_t(ws_slots(proc)) * kWsProducerWarps * ws_words(proc) * 32 * 4 +
-                      (rows ? size_t(kWsConsumerWarps) * 32 * kWsRowBytes : 0);
+  const size_t ring = size_t(ws_slots(proc)) * ws_producer_warps(proc) * ws_words(proc) * 32 * 4 +
+                      (rows ? size_t(ws_consumer_warps(proc)) * 32 * kWsRowBytes : 0);
   const size_t hist = ((size_t(ndim) * nbins * 8 + 15) / 16) * 16;
   return ring + hist + 4 * (size_t(ndim) * (nbins + 1) + size_t(nx) * (1 + 2 * ws_flavours(proc)));
 }
@@ -139,7 +150,7 @@ inline size_t ws_smem_bytes(int proc, int ndim, int nbins, int nx) {
   return ws_smem_bytes(proc, ndim, nbins, nx, ws_rows_in_smem(proc, ndim, nbins, nx));
 }
 
-// Shared-memory ring of one block: ws_slots(PROC) x kWsProducerWarps slots of 32 event records, their
+// Shared-memory ring of one block: ws_slots(PROC) x ws_producer_warps(PROC) slots of 32 event records, their
 // full/empty mbarriers and counts (-1 = end marker).
 struct WsRing {
   uint32_t* rec;   // [slots][ws_words(PROC)][32]
@@ -148,7 +159,7 @@ struct WsRing {
   int* count;      // [slots]
 };
 
-// Producer warp p (0 <= p < kWsProducerWarps): evaluates the kinematics of the
+// Producer warp p (0 <= p < ws_producer_warps(PROC)): evaluates the kinematics of the
 // events [lo, hi) of the integrand in chunks of 32 (chunk k = events
 // lo + 32 k .. lo + 32 k + 31; this warp takes chunks k0, k0 + dk, ...), adds
 // every event to the bin counts, appends the events that pass the cuts to its
@@ -283,24 +294,25 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
   }
   if (ok) {
     publish(seq, fill);  // the last, partial slot (possibly empty)
-    for (int e = 1; e <= kWsClasses && ok; ++e) {
+    for (int e = 1; e <= ws_classes(PROC) && ok; ++e) {
       ok = acquire(seq + e);
       if (ok) publish(seq + e, -1);
     }
-    seq += kWsClasses + 1;
+    seq += ws_classes(PROC) + 1;
   }
   return ok;
 }
 
-// This consumer thread's row store in the block's array of kWsConsumerWarps
-// x 32 x kWsRowBytes bytes (word j of consumer thread t at 16 (j C + t), C
-// the consumer threads).
+// This consumer thread's row store in the block's array of
+// ws_consumer_warps x 32 x kWsRowBytes bytes (word j of consumer thread t at
+// 16 (j C + t), C the consumer threads).
+template <int PROC>
 MC_D SmemRows ws_rows(const unsigned char* sh_rows) {
-  return {uint32_t(__cvta_generic_to_shared(sh_rows)) + 16u * uint32_t(threadIdx.x - 32 * kWsProducerWarps),
-          16u * 32u * kWsConsumerWarps};
+  return {uint32_t(__cvta_generic_to_shared(sh_rows)) + 16u * uint32_t(threadIdx.x - 32 * ws_producer_warps(PROC)),
+          16u * 32u * ws_consumer_warps(PROC)};
 }
 
-// Consumer warp c (0 <= c < kWsConsumerWarps): evaluates |M|^2 for the events
+// Consumer warp c (0 <= c < ws_consumer_warps(PROC)): evaluates |M|^2 for the events
 // of its producers' slots until every stream it serves has delivered an end
 // marker, and adds the weights w = f J to the Kahan sums, w_max and the
 // histogram of w^2.  q0, q1: the next slot sequence numbers of its (up to two)
@@ -313,16 +325,17 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
   constexpr int NW = (MAXD + 3) / 4;
   const int lane = threadIdx.x & 31;
   const int ndim = a.ndim, nb = a.nbins;
-  bool live0 = true, live1 = kWsStreams > 1;
-  for (int si = 0; live0 || live1; si ^= (kWsStreams > 1)) {
+  constexpr int NP = ws_producer_warps(PROC), NC = ws_consumer_warps(PROC), NS = ws_streams(PROC);
+  bool live0 = true, live1 = NS > 1;
+  for (int si = 0; live0 || live1; si ^= (NS > 1)) {
     if (si == 0 ? !live0 : !live1) si ^= 1;
-    const int p = (c % kWsProducerWarps) + si * kWsConsumerWarps;
+    const int p = (c % NP) + si * NC;
     int& q = si == 0 ? q0 : q1;
     constexpr int S = ws_slots(PROC);
     const int s = p * S + q % S;
     if (!ws_wait(&ring.full[s], uint32_t(q / S) & 1u)) return false;
     const int cnt = ring.count[s];
-    q += kWsClasses;
+    q += ws_classes(PROC);
     if (cnt < 0) {
       // release the marker's slot too: a later call (the next tile of a
       // batch) reuses it
@@ -400,19 +413,21 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
 // at most 2^32 - 1 events).  SMROWS: the consumers' row spinors in shared
 // memory (ws_rows_in_smem).
 template <int PROC, bool WOUT, bool SMROWS>
-__global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs a) {
+__global__ void __launch_bounds__(ws_threads(PROC), 1) ws_integrand_kernel(KernelArgs a) {
   static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D || PROC == P_GG_TTBARG_MC || PROC == P_PP_TTBARJ,
                 "gg -> t tbar g and p p -> t tbar + parton only");
+  static_assert(ws_shape_ok(PROC), "launch shape");
+  constexpr int NP = ws_producer_warps(PROC), NC = ws_consumer_warps(PROC), SLOTS = ws_slots(PROC) * NP;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kWsMaxSlots], empty[kWsMaxSlots];
-  __shared__ int count[kWsMaxSlots];
+  __shared__ __align__(8) uint64_t full[SLOTS], empty[SLOTS];
+  __shared__ int count[SLOTS];
   __shared__ int failed;
-  __shared__ BlockPartial warp_part[kWsThreads / 32];
+  __shared__ BlockPartial warp_part[NP + NC];
   const int ndim = a.ndim, nb = a.nbins;
   const int nedge = ndim * (nb + 1), nhist = ndim * nb;
   const WsRing ring = {reinterpret_cast<uint32_t*>(smem), full, empty, count};
-  unsigned char* sh_rows = smem + size_t(ws_slots(PROC)) * kWsProducerWarps * ws_words(PROC) * 32 * 4;
-  unsigned char* rest = sh_rows + (SMROWS ? size_t(kWsConsumerWarps) * 32 * kWsRowBytes : 0);
+  unsigned char* sh_rows = smem + size_t(SLOTS) * ws_words(PROC) * 32 * 4;
+  unsigned char* rest = sh_rows + (SMROWS ? size_t(NC) * 32 * kWsRowBytes : 0);
   float* sh_w2 = reinterpret_cast<float*>(rest);
   unsigned int* sh_n = reinterpret_cast<unsigned int*>(rest + size_t(nhist) * 4);
   float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
@@ -424,7 +439,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
     sh_n[i] = 0u;
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < ws_slots(PROC) * kWsProducerWarps; ++s) {
+    for (int s = 0; s < SLOTS; ++s) {
       mbar_init(&full[s], 32);
       mbar_init(&empty[s], 32);
     }
@@ -444,23 +459,23 @@ __global__ void __launch_bounds__(kWsThreads, 1) ws_integrand_kernel(KernelArgs 
   Acc acc;
   const int warp = threadIdx.x >> 5;
   bool ok = true;
-  if (warp < kWsProducerWarps) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
+  if (warp < NP) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(ws_producer_regs(PROC)));
     int seq = 0;
-    ok = ws_produce<PROC, WOUT>(a, pdf, sh_edges, sh_n, ring, warp, 0, a.n, (long long)blockIdx.x * kWsProducerWarps + warp,
-                          (long long)gridDim.x * kWsProducerWarps, seq, acc);
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsRegs));
+    ok = ws_produce<PROC, WOUT>(a, pdf, sh_edges, sh_n, ring, warp, 0, a.n, (long long)blockIdx.x * NP + warp,
+                                (long long)gridDim.x * NP, seq, acc);
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(ws_regs(PROC)));
   } else {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
-    const int c = warp - kWsProducerWarps;
-    int q0 = c / kWsProducerWarps, q1 = q0;
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(ws_consumer_regs(PROC)));
+    const int c = warp - NP;
+    int q0 = c / NP, q1 = q0;
     if constexpr (SMROWS) {
-      SmemRows rows = ws_rows(sh_rows);
+      SmemRows rows = ws_rows<PROC>(sh_rows);
       ok = ws_consume<PROC, WOUT>(a, sh_w2, ring, rows, c, q0, q1, acc);
     } else {
       ok = ws_consume<PROC, WOUT>(a, sh_w2, ring, NoRows{}, c, q0, q1, acc);
     }
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsRegs));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(ws_regs(PROC)));
   }
   if (!ok) atomicExch(&failed, 1);
   __syncthreads();
