@@ -29,10 +29,11 @@
 // slot and one end marker (count -1) for each consumer it feeds.  Sixteen
 // warps of 128 registers at launch, rebalanced to 88 (producers) and 168
 // (consumers) with setmaxnreg, measured fastest among the 4+8, 8+4 and 8+8
-// shapes on B300 for that process.  The compiled code of both roles is held
-// to the launch's 128 registers, so the consumers' |M|^2 runs on register spills, which
-// must stay in L1: the shared memory of a block is kept small for that
-// (see ws_rows_in_smem).
+// shapes on B300 for that process.  ptxas allocates the code after each
+// setmaxnreg within its count (the producers' within 88 registers, the
+// consumers' within 168), and the consumers' |M|^2 still spills at 168, so
+// the spills must stay in L1: the shared memory of a block is kept small for
+// that (see ws_rows_in_smem).
 //
 // Every wait is bounded (kWsWaitNs of %globaltimer); a warp that gives up
 // stops, the block poisons its partial sums with NaN and, when the launch
@@ -47,10 +48,11 @@ namespace mc {
 // ws_consumer_warps consumer warps per block (each a multiple of 4, i.e.
 // whole warpgroups, since the register split below is per warpgroup), one
 // block per SM.  gg -> t tbar g: 8 + 8 (the description above).
-// p p -> t tbar + parton: 4 + 8, so that the code of its seven-channel |M|^2
-// compiles to the 168 registers of a 12-warp launch instead of 128 (measured
-// on B300: 19.0 against 22.5 ms per 1e7 events with 8 + 8; the same 4 + 8
-// shape costs gg -> t tbar g 36 %).
+// p p -> t tbar + parton: 4 + 8, a 12-warp launch of 168 registers a
+// thread, so that the consumers' seven-channel |M|^2 compiles within 208
+// registers instead of 168 and spills half as much (measured on B300: 19.0
+// against 22.5 ms per 1e7 events with 8 + 8; the same 4 + 8 shape costs
+// gg -> t tbar g 36 %: four producers cannot keep its consumers fed).
 MC_HD constexpr int ws_producer_warps(int proc) { return proc == P_PP_TTBARJ ? 4 : 8; }
 MC_HD constexpr int ws_consumer_warps(int) { return 8; }
 MC_HD constexpr int ws_threads(int proc) { return 32 * (ws_producer_warps(proc) + ws_consumer_warps(proc)); }
