@@ -243,112 +243,158 @@ MC_D int knot_cell_f(const float* t, int n, float v) {
 }
 
 // FP32 batch interpolation with the whole grid in shared memory (when it
-// fits, 176 KB for 100 x 40 knots and 11 flavours): flavours innermost, so one
-// 16-byte load brings four flavours of a knot.  Per point the sixteen (Q, x)
-// stencil knots combine with coefficients formed once: the Q weights times
-// the x Hermite weights of the four x knots (the knot slopes written out as
-// differences, one-sided at the grid's ends), so each flavour costs sixteen
-// multiply-adds.  The knots and their reciprocal spacings are kept in FP32 in
-// shared memory too, and nothing in the loop runs on the FP64 pipe.  A
-// persistent grid of one block per SM walks the points in tiles of kPdfTile;
-// outputs are staged in FP32 and widened to FP64 as the block writes them
-// out as one contiguous range.
-constexpr int kPdfTile = 512;
+// fits, 188 KB for 100 x 40 knots and 11 flavours padded to 12): flavours
+// innermost, so one 16-byte load brings four flavours of a knot.  Per point
+// the sixteen (Q, x) stencil knots combine with coefficients formed once: the
+// Q weights times the x Hermite weights of the four x knots (the knot slopes
+// written out as differences, one-sided at the grid's ends), so each flavour
+// costs sixteen multiply-adds.  The knots and their reciprocal spacings are
+// kept in FP32 in shared memory too, and nothing in the loop runs on the FP64
+// pipe.  One block of kPdfThreads per SM; every warp walks its own chunks of
+// 32 points (chunk c = points 32 c .. 32 c + 31, warp w of the grid takes
+// chunks w, w + W, ...) with no block-wide barrier, loading the next chunk's
+// queries while it evaluates the current one; outputs are staged in FP32 per
+// warp and widened to FP64 as the warp writes its chunk out as one contiguous
+// range.
+constexpr int kPdfThreads = 512;
+constexpr int kPdfWarps = kPdfThreads / 32;
+constexpr int kPdfLut = 256;  // entries of each knot lookup table
 constexpr size_t kPdfSmemMax = 224 * 1024;
-// shared memory: the grid, the FP32 output staging, the knots and their
-// reciprocal spacings, then per point of a tile its setup (log x, log Q^2 and
-// the two cells) and the gather order
-__host__ __device__ inline size_t pdf_setup_offset(const PdfDev& p) {
-  return ((size_t(p.nq) * p.nx * p.nfp * 4 + size_t(kPdfTile) * p.nflav * 4 + 8 * size_t(p.nx + p.nq)) + 15) / 16 * 16;
+// shared memory: the grid, per warp its FP32 output staging (32 x nflav,
+// which holds the chunk's gather order before the outputs), the knots and
+// their reciprocal spacings, the two lookup tables
+inline size_t pdf_smem_bytes(const PdfDev& p) {
+  return size_t(p.nq) * p.nx * p.nfp * 4 + size_t(kPdfWarps) * 32 * p.nflav * 4 + 8 * size_t(p.nx + p.nq) +
+         2 * size_t(kPdfLut) * 4;
 }
-inline size_t pdf_smem_bytes(const PdfDev& p) { return pdf_setup_offset(p) + size_t(kPdfTile) * (16 + 4); }
 
-// Points of a tile are gathered in an order that spreads the 16-byte bank
+// The same cell as knot_cell_f (t strictly increasing, t[0] <= v <= t[n-1]):
+// lut[b] is the cell of t[0] + b (t[n-1] - t[0]) / kPdfLut, and from the
+// entry of v's step a walk (at most n steps, one or none on grids whose
+// spacing varies less than the steps) reaches the largest i in [0, n-2] with
+// t[i] <= v.
+MC_D int knot_cell_lut(const float* t, const int* lut, int n, float v, float inv_step) {
+  const int b = min(max(int((v - t[0]) * inv_step), 0), kPdfLut - 1);
+  int i = lut[b];
+  while (i < n - 2 && t[i + 1] <= v) ++i;
+  while (i > 0 && t[i] > v) --i;
+  return i;
+}
+
+// Points of a chunk are gathered in an order that spreads the 16-byte bank
 // groups: the stencil of a point starts at float4 index base = (row of its
 // first Q knot x nx + its first x knot) x nfp / 4 and its sixteen loads sit at
 // offsets common to all interior points, so when the 8 lanes of a
 // quarter-warp hold points with distinct base mod 8 every load of the
-// quarter-warp is one wavefront.  Pass 1 finds each point's cells and key
-// (base mod 8) and ranks it within its key; the gather order interleaves the
-// keys rank by rank (position = sum over keys of min(count, rank) + the keys
-// below its own that still have a point of that rank).  Pass 2 evaluates the
-// point at its position, writing its outputs to the point's own staging row,
-// so results and output order do not depend on the order.
-__global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf, long long n, const double* x,
-                                                                      const double* q2, double* out) {
+// quarter-warp is one wavefront.  Each lane finds its point's cells and key
+// (base mod 8) and its rank within its key (warp ballots); the gather order
+// interleaves the keys rank by rank (position = sum over keys of
+// min(count, rank) + the keys below its own that still have a point of that
+// rank).  The lane at a position evaluates that point and writes its outputs
+// to the point's own staging row, so results and output order do not depend
+// on the order.  (A quarter-warp pays the largest multiplicity of a key among
+// its 8 lanes; the most frequent of the 8 keys among 32 random points occurs
+// about 7.5 times, so a stencil load costs about 8 wavefronts per warp
+// instead of 4 whatever the order.  Chunks of 64 points on 12 warps, which
+// the shared memory allows, measured slower.)
+__global__ void __launch_bounds__(kPdfThreads, 1) pdf_xfxq2_smem_kernel(PdfDev pdf, long long n, const double* x,
+                                                                        const double* q2, double* out) {
   extern __shared__ __align__(16) unsigned char pdf_smem[];
-  __shared__ int cnt[8];
   float4* tab = reinterpret_cast<float4*>(pdf_smem);
   const int nx = pdf.nx, nq = pdf.nq, nfl = pdf.nflav, nf4 = pdf.nfp / 4;
-  float* stage = reinterpret_cast<float*>(pdf_smem + size_t(nq) * nx * pdf.nfp * 4);
-  float* lxf = stage + size_t(kPdfTile) * nfl;  // [nx] knots, [nx] 1/spacing
+  float* stage_all = reinterpret_cast<float*>(pdf_smem + size_t(nq) * nx * pdf.nfp * 4);  // [warps][32][nfl]
+  float* lxf = stage_all + size_t(kPdfWarps) * 32 * nfl;  // [nx] knots, [nx] 1/spacing
   float* rxf = lxf + nx;
   float* lqf = rxf + nx;  // [nq], [nq]
   float* rqf = lqf + nq;
-  float4* pset = reinterpret_cast<float4*>(pdf_smem + pdf_setup_offset(pdf));  // [kPdfTile]
-  int* perm = reinterpret_cast<int*>(pset + kPdfTile);                        // [kPdfTile]
+  int* lutx = reinterpret_cast<int*>(rqf + nq);  // [kPdfLut], [kPdfLut]
+  int* lutq = lutx + kPdfLut;
   {
     const float4* g = reinterpret_cast<const float4*>(pdf.xf32t);
     const int n4 = nq * nx * nf4;
-    for (int k = threadIdx.x; k < n4; k += kPdfTile) tab[k] = g[k];
-    for (int k = threadIdx.x; k < nx; k += kPdfTile) {
+    for (int k = threadIdx.x; k < n4; k += kPdfThreads) tab[k] = g[k];
+    for (int k = threadIdx.x; k < nx; k += kPdfThreads) {
       lxf[k] = float(pdf.logx[k]);
       rxf[k] = k + 1 < nx ? float(1.0 / (pdf.logx[k + 1] - pdf.logx[k])) : 0.0f;
     }
-    for (int k = threadIdx.x; k < nq; k += kPdfTile) {
+    for (int k = threadIdx.x; k < nq; k += kPdfThreads) {
       lqf[k] = float(pdf.logq2[k]);
       rqf[k] = k + 1 < nq ? float(1.0 / (pdf.logq2[k + 1] - pdf.logq2[k])) : 0.0f;
     }
   }
   __syncthreads();
-  const long long ntiles = (n + kPdfTile - 1) / kPdfTile;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long i0 = tile * kPdfTile;
-    const int npts = int(n - i0 < kPdfTile ? n - i0 : kPdfTile);
-    // pass 1: cells and key of this thread's point
-    if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
-    __syncthreads();
-    int key = 0, rank = 0;
-    if (int(threadIdx.x) < npts) {
-      const long long i = i0 + threadIdx.x;
-      const double xv = x[i], qv = q2[i];
-      // x_lo, q2_lo > 0, so a NaN or a negative query fails one of the tests
-      if (!(pos_f64_le(pdf.x_lo, xv) && pos_f64_le(xv, pdf.x_hi) && pos_f64_le(pdf.q2_lo, qv) &&
-            pos_f64_le(qv, pdf.q2_hi))) {
-        pset[threadIdx.x] = make_float4(0.0f, 0.0f, __int_as_float(-1), __int_as_float(-1));
-      } else {
-        const float lx = fminf(fmaxf(log_f64_to_f32(xv), lxf[0]), lxf[nx - 1]);
-        const float lq = fminf(fmaxf(log_f64_to_f32(qv), lqf[0]), lqf[nq - 1]);
-        const int iq = knot_cell_f(lqf, nq, lq), ix = knot_cell_f(lxf, nx, lx);
-        pset[threadIdx.x] = make_float4(lx, lq, __int_as_float(ix), __int_as_float(iq));
-        key = ((max(iq - 1, 0) * nx + max(ix - 1, 0)) * nf4) & 7;
-      }
-      rank = atomicAdd(&cnt[key], 1);
+  const float stx = (lxf[nx - 1] - lxf[0]) / float(kPdfLut), stq = (lqf[nq - 1] - lqf[0]) / float(kPdfLut);
+  for (int b = threadIdx.x; b < kPdfLut; b += kPdfThreads) {
+    lutx[b] = knot_cell_f(lxf, nx, lxf[0] + float(b) * stx);
+    lutq[b] = knot_cell_f(lqf, nq, lqf[0] + float(b) * stq);
+  }
+  __syncthreads();
+  const float inv_stx = 1.0f / stx, inv_stq = 1.0f / stq;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* stage = stage_all + size_t(warp) * 32 * nfl;
+  int* perm = reinterpret_cast<int*>(stage);  // [32], read before the outputs are staged
+  const long long nchunks = (n + 31) / 32;
+  const long long nw = (long long)gridDim.x * kPdfWarps;
+  long long c = (long long)blockIdx.x * kPdfWarps + warp;
+  double xv = 0.0, qv = 0.0;  // this lane's query of chunk c
+  if (c < nchunks && c * 32 + lane < n) {
+    xv = x[c * 32 + lane];
+    qv = q2[c * 32 + lane];
+  }
+  for (; c < nchunks; c += nw) {
+    const long long i0 = c * 32;
+    const int npts = int(n - i0 < 32 ? n - i0 : 32);
+    const bool act = lane < npts;
+    const double xc = xv, qc = qv;
+    if (c + nw < nchunks && (c + nw) * 32 + lane < n) {  // the next chunk's query, in flight meanwhile
+      xv = x[(c + nw) * 32 + lane];
+      qv = q2[(c + nw) * 32 + lane];
     }
-    __syncthreads();
-    if (int(threadIdx.x) < npts) {
+    // cells and key of this lane's point (ix = -1: outside the grid)
+    float lx = 0.0f, lq = 0.0f;
+    int ix = -1, iq = -1, key = 0;
+    // x_lo, q2_lo > 0, so a NaN or a negative query fails one of the tests
+    if (act && pos_f64_le(pdf.x_lo, xc) && pos_f64_le(xc, pdf.x_hi) && pos_f64_le(pdf.q2_lo, qc) &&
+        pos_f64_le(qc, pdf.q2_hi)) {
+      lx = fminf(fmaxf(log_f64_to_f32(xc), lxf[0]), lxf[nx - 1]);
+      lq = fminf(fmaxf(log_f64_to_f32(qc), lqf[0]), lqf[nq - 1]);
+      iq = knot_cell_lut(lqf, lutq, nq, lq, inv_stq);
+      ix = knot_cell_lut(lxf, lutx, nx, lx, inv_stx);
+      key = ((max(iq - 1, 0) * nx + max(ix - 1, 0)) * nf4) & 7;
+    }
+    // gather order
+    int cnt[8];
+    unsigned mine_keys = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, act && key == k);
+      cnt[k] = __popc(m);
+      if (key == k) mine_keys = m;
+    }
+    if (act) {
+      const int rank = __popc(mine_keys & ((1u << lane) - 1u));
       int pos = 0;
 #pragma unroll
       for (int k = 0; k < 8; ++k) pos += min(cnt[k], rank) + (k < key && cnt[k] > rank ? 1 : 0);
-      perm[pos] = threadIdx.x;
+      perm[pos] = lane;
     }
-    __syncthreads();
-    // pass 2: the point at this thread's position in the gather order
-    if (int(threadIdx.x) < npts) {
-      const int pt = perm[threadIdx.x];
+    __syncwarp();
+    // the point at this lane's position in the gather order
+    const int pt = act ? perm[lane] : lane;
+    __syncwarp();  // the gather order is read: the staging rows may be written
+    const float plx = __shfl_sync(0xffffffffu, lx, pt), plq = __shfl_sync(0xffffffffu, lq, pt);
+    const int pix = __shfl_sync(0xffffffffu, ix, pt), piq = __shfl_sync(0xffffffffu, iq, pt);
+    if (act) {
       float* mine = stage + pt * nfl;
-      const float4 su = pset[pt];
-      const int ix = __float_as_int(su.z), iq = __float_as_int(su.w);
-      if (ix < 0) {
+      if (pix < 0) {
         for (int fl = 0; fl < nfl; ++fl) mine[fl] = __int_as_float(0x7fc00000);
       } else {
-        const float lx = su.x, lq = su.y;
         // Q weights of the knots j0 .. j0+3 (as q_weights)
-        const int j0 = iq - 1;
+        const int j0 = piq - 1;
         float w[4];
         {
-          const float hq = lqf[iq + 1] - lqf[iq];
-          const float tq = (lq - lqf[iq]) * rqf[iq];
+          const float hq = lqf[piq + 1] - lqf[piq];
+          const float tq = (plq - lqf[piq]) * rqf[piq];
           const float q2_ = tq * tq, q3 = q2_ * tq;
           w[0] = 0.0f;
           w[1] = 2.0f * q3 - 3.0f * q2_ + 1.0f;
@@ -368,16 +414,16 @@ __global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf,
               w[b - 1] -= 0.5f * coef * rqf[k - 1];
             }
           };
-          add_slope(iq, (q3 - 2.0f * q2_ + tq) * hq);
-          add_slope(iq + 1, (q3 - q2_) * hq);
+          add_slope(piq, (q3 - 2.0f * q2_ + tq) * hq);
+          add_slope(piq + 1, (q3 - q2_) * hq);
         }
-        const float h = lxf[ix + 1] - lxf[ix];
-        const float tau = (lx - lxf[ix]) * rxf[ix];
+        const float h = lxf[pix + 1] - lxf[pix];
+        const float tau = (plx - lxf[pix]) * rxf[pix];
         int ii[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) ii[t] = min(max(ix - 1 + t, 0), nx - 1);
-        const float r[3] = {ix >= 1 ? rxf[ix - 1] : 0.0f, rxf[ix], ix + 2 <= nx - 1 ? rxf[ix + 1] : 0.0f};
-        const bool first = ix == 0, last = ix + 1 == nx - 1;
+        for (int t = 0; t < 4; ++t) ii[t] = min(max(pix - 1 + t, 0), nx - 1);
+        const float r[3] = {pix >= 1 ? rxf[pix - 1] : 0.0f, rxf[pix], pix + 2 <= nx - 1 ? rxf[pix + 1] : 0.0f};
+        const bool first = pix == 0, last = pix + 1 == nx - 1;
         const float t2 = tau * tau, t3 = t2 * tau;
         const float c0 = 2.0f * t3 - 3.0f * t2 + 1.0f, c1 = (t3 - 2.0f * t2 + tau) * h, c2 = -2.0f * t3 + 3.0f * t2,
                     c3 = (t3 - t2) * h;
@@ -417,10 +463,10 @@ __global__ void __launch_bounds__(kPdfTile, 1) pdf_xfxq2_smem_kernel(PdfDev pdf,
         }
       }
     }
-    __syncthreads();
+    __syncwarp();
     double* dst = out + i0 * nfl;
-    for (int k = threadIdx.x; k < npts * nfl; k += kPdfTile) dst[k] = f32_to_f64(stage[k]);
-    __syncthreads();
+    for (int k = lane; k < npts * nfl; k += 32) dst[k] = f32_to_f64(stage[k]);
+    __syncwarp();
   }
 }
 
@@ -554,13 +600,13 @@ cudaError_t launch_pdf_xfxq2(const PdfDev& pdf, bool fp64, long long n, const do
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long ntiles = (n + kPdfTile - 1) / kPdfTile;
-    const int grid = int(ntiles < sms ? ntiles : sms);
+    const long long blocks = ((n + 31) / 32 + kPdfWarps - 1) / kPdfWarps;
+    const int grid = int(blocks < sms ? blocks : sms);
     const size_t smem = pdf_smem_bytes(pdf);
     const cudaError_t e =
         cudaFuncSetAttribute(pdf_xfxq2_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    pdf_xfxq2_smem_kernel<<<grid, kPdfTile, smem, st>>>(pdf, n, x, q2, out);
+    pdf_xfxq2_smem_kernel<<<grid, kPdfThreads, smem, st>>>(pdf, n, x, q2, out);
     return cudaGetLastError();
   }
   const long long grid = (n + kPdfBlock - 1) / kPdfBlock;

@@ -296,6 +296,37 @@ def test_pdf_xfxq2_paths(gpu, prec, tol):
     big.free()
 
 
+def test_pdf_xfxq2_many_chunks(gpu, oracle_pdf, pdf_grid):
+    """A batch large enough that every warp of the FP32 shared-memory kernel
+    walks several chunks (the next chunk's queries loaded while the current
+    one is evaluated), with a ragged end: sampled points of every part of the
+    batch, including the last ones, against the oracle; and the batch split
+    into two launches at an odd offset gives the same bits (nothing in a
+    point's result depends on its chunk or gather position)."""
+    rng = np.random.default_rng(7)
+    n = 400_003
+    x = 10 ** rng.uniform(-7, math.log10(0.5), n)
+    q2 = (10 ** rng.uniform(math.log10(1.7), 3.95, n)) ** 2
+    xd = torch.tensor(x, device="cuda")
+    qd = torch.tensor(q2, device="cuda")
+    nfl = len(pdf_grid.pids)
+    out = torch.empty((n, nfl), dtype=torch.float64, device="cuda")
+    M.mc_pdf_xfxq2(gpu, M.MC_FP32_KAHAN, n, xd, qd, out)
+    got = out.cpu().numpy()
+    worst = 0.0
+    for i in list(range(0, n, 4001)) + [n - 2, n - 1]:
+        for fl, pid in enumerate(pdf_grid.pids):
+            ref = oracle_pdf.xfxq2(int(pid), x[i], q2[i])
+            worst = max(worst, abs(got[i, fl] - ref) / (abs(ref) + 1e-16))
+    assert worst < 1e-5, worst
+    k = 123_457
+    a = torch.empty((k, nfl), dtype=torch.float64, device="cuda")
+    b = torch.empty((n - k, nfl), dtype=torch.float64, device="cuda")
+    M.mc_pdf_xfxq2(gpu, M.MC_FP32_KAHAN, k, xd[:k].contiguous(), qd[:k].contiguous(), a)
+    M.mc_pdf_xfxq2(gpu, M.MC_FP32_KAHAN, n - k, xd[k:].contiguous(), qd[k:].contiguous(), b)
+    assert np.array_equal(np.concatenate([a.cpu().numpy(), b.cpu().numpy()]), got)
+
+
 # ------------------------------------------------------------------ edge cases
 def test_empty_single_and_ragged(gpu, oracle_pdf):
     itg = PROCS["gauss"]
