@@ -74,10 +74,14 @@ constexpr int kUPad = 16;  // rows of U^T: u_0 .. u_{na-1}, a row of ones (bias)
 unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
 
 // ------------------------------------------------------------------ kernels
-// z: FP32-mode Philox uniforms (2k + 1) / 2^24 of events first + i.
-__global__ void flow_uniforms_kernel(float* z, long long n, int D, uint64_t seed, uint32_t iteration, long long first) {
+// z: FP32-mode Philox uniforms (2k + 1) / 2^24 of events first + i; with
+// step, the iteration word is 0x10000 + *step (the training step count kept
+// on the device, so that a replayed graph of a step draws that step's batch).
+__global__ void flow_uniforms_kernel(float* z, long long n, int D, uint64_t seed, uint32_t iteration, long long first,
+                                     const long long* step = nullptr) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (step) iteration = 0x10000u + uint32_t(*step);
   uint64_t k[kMaxFlowDim];
   event_uniforms<kMaxFlowDim, false>(seed, iteration, 0u, uint64_t(first + i), D, k);
   for (int d = 0; d < D; ++d) z[i * D + d] = float(uint32_t(2 * k[d] + 1)) * 0x1p-24f;
@@ -537,12 +541,21 @@ __global__ void loss_final_kernel(const double* part, int nblocks, double* sums)
 // Adam (thesis Sec. "Optimizers") on every master parameter; gradients of the
 // 256-wide weights are read from their transposed layout.
 struct AdamArgs {
-  float lr, b1, b2, eps, c1, c2;  // c1 = 1/(1 - b1^t), c2 = 1/(1 - b2^t)
+  float lr, b1, b2, eps;
+  const float* c;  // [2] on the device: 1/(1 - b1^t), 1/(1 - b2^t) of step t
 };
+// Advances the device step count t and forms Adam's bias corrections of step
+// t (one thread; FP64 powers, rounded to FP32 as the update uses them).
+__global__ void adam_prep_kernel(long long* step, float* c, double b1, double b2) {
+  const long long t = ++*step;
+  c[0] = float(1.0 / (1.0 - pow(b1, double(t))));
+  c[1] = float(1.0 / (1.0 - pow(b2, double(t))));
+}
 __global__ void adam_kernel(float* params, const float* grads, float* m, float* v, size_t n, const LayerDev* layers,
                             int nl, AdamArgs A) {
   const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= n) return;
+  const float c1 = A.c[0], c2 = A.c[1];
   size_t gidx = idx;
   // the BF16 copies the tensor cores read: W2, W3, W4 and their transposes, W1^T
   __nv_bfloat16 *dst = nullptr, *dst_t = nullptr;
@@ -580,7 +593,7 @@ __global__ void adam_kernel(float* params, const float* grads, float* m, float* 
   const float vi = A.b2 * v[idx] + (1.0f - A.b2) * g * g;
   m[idx] = mi;
   v[idx] = vi;
-  const float p = params[idx] - A.lr * (mi * A.c1) / (sqrtf(vi * A.c2) + A.eps);
+  const float p = params[idx] - A.lr * (mi * c1) / (sqrtf(vi * c2) + A.eps);
   params[idx] = p;
   const __nv_bfloat16 h = __float2bfloat16_rn(p);
   if (dst) dst[di] = h;
@@ -1504,6 +1517,14 @@ struct mc_flow_s {
   long long sbp = 0;
   float *Ps = nullptr, *lqs = nullptr;
   int* err = nullptr;
+  // the training step count on the device (mirrors `step`) and Adam's bias
+  // corrections of the current step
+  long long* d_step = nullptr;
+  float* d_adam = nullptr;
+  // the stream a training step is captured on and replayed from as a CUDA
+  // graph, and the events that order it after and before the caller's stream
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int nout_pad_max = 0;
   // data-parallel step: events of the batch sampled by mc_flow_step_sample
   // and not yet differentiated (0: none)
@@ -1944,6 +1965,38 @@ int eval_points_sums(mc_flow F, const mc_integrand* itg, const mc::KernelArgs& a
   return MC_OK;
 }
 
+// Adam step of the parameters from F->d_grads (the step count advances on
+// the device; the caller advances F->step).
+int adam_launch(mc_flow F, double lr, cudaStream_t st) {
+  const double b1 = 0.9, b2 = 0.999;
+  mc::adam_prep_kernel<<<1, 1, 0, st>>>(F->d_step, F->d_adam, b1, b2);
+  mc::AdamArgs A{float(lr), float(b1), float(b2), 1e-8f, F->d_adam};
+  mc::adam_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_params, F->d_grads, F->d_m, F->d_v, F->nparam,
+                                                                   F->d_layers, F->L, A);  // refreshes the BF16 copies
+  FLOW_CUDA(cudaGetLastError());
+  return MC_OK;
+}
+
+// One online training step on a batch of n events (np padded): sample from
+// the current flow keeping every layer's activations, evaluate the
+// integrand, form the weights and the loss sums, differentiate, take the
+// Adam step.  Host-independent (the batch's Philox iteration and Adam's
+// corrections come from the device step count), so it can be captured once
+// and replayed.
+int train_step(mc_flow F, const mc_integrand* itg, mc_pdf pdf, long long n, long long np, double lr, cudaStream_t st) {
+  FLOW_CUDA(cudaMemsetAsync(P_of(F, 0), 0, sizeof(float) * np * F->D, st));
+  mc::flow_uniforms_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(P_of(F, 0), n, F->D, F->seed, 0u, 0, F->d_step);
+  if (int rc = forward_pass(F, np, true, st)) return rc;
+  if (int rc = eval_points(F, itg, pdf, P_of(F, F->L), n, F->f, st)) return rc;
+  FLOW_CUDA(cudaMemsetAsync(F->w, 0, sizeof(float) * np, st));
+  mc::flow_weights_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->f, F->logq, F->w, n);
+  loss_sums(F, n, st);
+  // the forward activations are those of the density pass at x: backward, Adam
+  mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
+  if (int rc = backward_pass(F, np, n, st)) return rc;
+  return adam_launch(F, lr, st);
+}
+
 // Packed host parameter layout -> padded device layout: W4 row j (2K+1) + k
 // of the packed matrix is device row j ls + k (and likewise for b4).
 void build_host_map(mc_flow F) {
@@ -1990,8 +2043,11 @@ int mc_flow_free(mc_flow F) {
                   (void*)F->LT, (void*)F->h, (void*)F->hT, (void*)F->G, (void*)F->GT, (void*)F->dA, (void*)F->dAT,
                   (void*)F->part, (void*)F->UT, (void*)F->MB, (void*)F->dU, (void*)F->U, (void*)F->Ps, (void*)F->lqs,
                   (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
-                  (void*)F->err})
+                  (void*)F->err, (void*)F->d_step, (void*)F->d_adam})
     cudaFree(p);
+  if (F->ev_in) cudaEventDestroy(F->ev_in);
+  if (F->ev_out) cudaEventDestroy(F->ev_out);
+  if (F->cap) cudaStreamDestroy(F->cap);
   if (F->h_sums) cudaFreeHost(F->h_sums);
   if (F->h_total) cudaFreeHost(F->h_total);
   delete F;
@@ -2074,11 +2130,16 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->parts, sizeof(BlockPartial) * kPartsGrid);
   alloc((void**)&F->total, sizeof(BlockPartial));
   alloc((void**)&F->err, sizeof(int));
+  alloc((void**)&F->d_step, sizeof(long long));
+  alloc((void**)&F->d_adam, sizeof(float) * 2);
   F->sbp = std::max<long long>(F->bp, 1 << 20);
   alloc((void**)&F->Ps, sizeof(float) * size_t(F->sbp) * D);
   alloc((void**)&F->lqs, sizeof(float) * size_t(F->sbp));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_sums, sizeof(double) * 2);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_total, sizeof(BlockPartial));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&F->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->ev_out, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     mc_flow_free(F);
     return ffail(MC_ENOMEM, std::string("mc_flow_create: allocation failed: ") + cudaGetErrorString(e));
@@ -2127,7 +2188,8 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
       cudaMemset(F->GT, 0, sizeof(__nv_bfloat16) * bp * np) != cudaSuccess ||
       cudaMemset(F->G, 0, sizeof(__nv_bfloat16) * bp * np) != cudaSuccess ||
       cudaMemset(F->UT, 0, sizeof(__nv_bfloat16) * L * mc::kUPad * bp) != cudaSuccess ||
-      cudaMemset(F->err, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(F->err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(F->d_step, 0, sizeof(long long)) != cudaSuccess) {
     mc_flow_free(F);
     return ffail(MC_ECUDA, "mc_flow_create: initialisation failed");
   }
@@ -2222,15 +2284,8 @@ int mc_flow_loss_grad(mc_flow F, int64_t n, const float* x, const float* w, doub
 
 int mc_flow_adam_step(mc_flow F, double lr, void* stream) {
   if (!F || !(lr > 0.0)) return ffail(MC_EINVAL, "mc_flow_adam_step: bad arguments");
-  const cudaStream_t st = static_cast<cudaStream_t>(stream);
   ++F->step;
-  const double b1 = 0.9, b2 = 0.999;
-  mc::AdamArgs A{float(lr), float(b1), float(b2), 1e-8f, float(1.0 / (1.0 - std::pow(b1, F->step))),
-                 float(1.0 / (1.0 - std::pow(b2, F->step)))};
-  mc::adam_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_params, F->d_grads, F->d_m, F->d_v, F->nparam,
-                                                                   F->d_layers, F->L, A);  // refreshes the BF16 copies
-  FLOW_CUDA(cudaGetLastError());
-  return MC_OK;
+  return adam_launch(F, lr, static_cast<cudaStream_t>(stream));
 }
 
 // ---- one online training step split across devices (data parallel): each
@@ -2294,20 +2349,36 @@ int mc_flow_train(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int steps, int
   if (mc::process_dim(itg) != F->D) return ffail(MC_EINVAL, "mc_flow_train: flow dimension differs from the process");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long n = batch, np = pad128(n);
+  if (!losses && steps >= 2) {
+    // the step captured once as a CUDA graph on F->cap and replayed `steps`
+    // times (its ~80 launches then cost one graph launch), ordered after the
+    // caller's stream and before its later work
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    FLOW_CUDA(cudaEventRecord(F->ev_in, st));
+    FLOW_CUDA(cudaStreamWaitEvent(F->cap, F->ev_in, 0));
+    FLOW_CUDA(cudaStreamBeginCapture(F->cap, cudaStreamCaptureModeRelaxed));
+    const int rc = train_step(F, itg, pdf, n, np, lr, F->cap);
+    const cudaError_t ec = cudaStreamEndCapture(F->cap, &graph);
+    if (rc != MC_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      (void)cudaGetLastError();
+      return rc != MC_OK ? rc : ffail(MC_ECUDA, std::string("mc_flow_train: graph capture failed: ") +
+                                                    cudaGetErrorString(ec));
+    }
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    for (int s = 0; s < steps && e == cudaSuccess; ++s) e = cudaGraphLaunch(exec, F->cap);
+    if (e == cudaSuccess) e = cudaEventRecord(F->ev_out, F->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, F->ev_out, 0);
+    if (exec) cudaGraphExecDestroy(exec);  // freed once the launches in flight complete
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return ffail(MC_ECUDA, std::string("mc_flow_train: ") + cudaGetErrorString(e));
+    F->step += steps;
+    return check_err(F, st);
+  }
   for (int s = 0; s < steps; ++s) {
-    // sample a batch from the current flow, keeping every layer's activations
-    FLOW_CUDA(cudaMemsetAsync(P_of(F, 0), 0, sizeof(float) * np * F->D, st));
-    mc::flow_uniforms_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(P_of(F, 0), n, F->D, F->seed,
-                                                                      0x10000u + uint32_t(F->step), 0);
-    if (int rc = forward_pass(F, np, true, st)) return rc;
-    if (int rc = eval_points(F, itg, pdf, P_of(F, F->L), n, F->f, st)) return rc;
-    FLOW_CUDA(cudaMemsetAsync(F->w, 0, sizeof(float) * np, st));
-    mc::flow_weights_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->f, F->logq, F->w, n);
-    loss_sums(F, n, st);
-    // the forward activations are those of the density pass at x: backward, Adam
-    mc::zero_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_grads, F->nparam);
-    if (int rc = backward_pass(F, np, n, st)) return rc;
-    if (int rc = mc_flow_adam_step(F, lr, stream)) return rc;
+    if (int rc = train_step(F, itg, pdf, n, np, lr, st)) return rc;
+    ++F->step;
     if (losses) {
       FLOW_CUDA(cudaMemcpyAsync(F->h_sums, F->sums, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
       FLOW_CUDA(cudaStreamSynchronize(st));
