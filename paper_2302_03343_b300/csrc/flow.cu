@@ -663,10 +663,14 @@ struct FusedLayerArgs {
   int D;
   long long n;     // multiple of 128
   int* error;
-  // training: the activations the backward needs, transposed [feature][n]
-  // (all null when sampling): h1, h2, h3 (BF16), the first-layer inputs
-  // U^T (BF16, rows u_a then a row of ones) and the logits (FP32, with bias)
-  __nv_bfloat16 *hT1, *hT2, *hT3, *UT;
+  // training (all null / unused when sampling): the activations the backward
+  // needs: h1, h2, h3 (BF16, row-major [n][256]) stored by TMA from the
+  // operand buffer through the map of the activation buffer, at rows
+  // h_row0 + m h_stride + event; the first-layer inputs U^T (BF16,
+  // transposed [16][n]: rows u_a then a row of ones) and the logits (FP32,
+  // with bias, transposed)
+  long long h_row0, h_stride;
+  __nv_bfloat16* UT;
   float* LT;
   uint32_t* bits;  // ReLU activity of h1, h2, h3: [3][n][8] words (bit c % 32 of word c / 32)
 };
@@ -686,13 +690,14 @@ template <bool KEEP>
 __global__ void __launch_bounds__(kFusedThreads, 1)
     flow_layer_fused_kernel(const __grid_constant__ CUtensorMap map_w1, const __grid_constant__ CUtensorMap map_w2,
                             const __grid_constant__ CUtensorMap map_w3, const __grid_constant__ CUtensorMap map_w4,
-                            FusedLayerArgs g, int stages) {
+                            const __grid_constant__ CUtensorMap map_h, FusedLayerArgs g, int stages) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int kMaxStages = 4;
   __shared__ __align__(8) uint64_t w_full[kMaxStages];
   __shared__ __align__(8) uint64_t w_empty[kMaxStages];
   __shared__ __align__(8) uint64_t a_ready[2], acc_full[2], fin_bar;
+  __shared__ __align__(8) uint64_t st_free[2];  // training: a stored activation's operand buffer may be rewritten
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int failed;
 
@@ -715,6 +720,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     for (int s = 0; s < 2; ++s) {
       mbar_init(&a_ready[s], kFusedCompute / 2);
       mbar_init(&acc_full[s], 1);
+      mbar_init(&st_free[s], 1);
     }
     mbar_init(&fin_bar, 1);
     failed = 0;
@@ -808,11 +814,57 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     unsigned char* abuf = smem + size_t(slot) * kFusedABytes;
     const float* prm = g.params;
     int use_acc = 0;
+    // training: thread 0 of warp q = 0 stores h1, h2, h3 of the tile from the
+    // operand buffer by TMA once every thread of the tile has written it (the
+    // a_ready phase); before the buffer is written again it waits until the
+    // store has read it and releases the buffer (st_free), which every thread
+    // waits for before it writes.
+    const bool issuer = KEEP && q == 0 && lane == 0;
+    int a_arrivals = 0, stores = 0, frees = 0;
+    bool pending = false;  // issuer: a store whose reads may be in flight
+    auto arrive_a = [&]() {
+      mbar_arrive(&a_ready[slot]);
+      ++a_arrivals;
+    };
+    // after arrive_a for activation m of the tile with first row row0
+    auto store_h = [&](int m, long long row0) -> bool {
+      bool ok = true;
+      if (issuer) {
+        ok = mbar_wait(&a_ready[slot], uint32_t(a_arrivals - 1) & 1u);
+        if (ok) {
+          const int y = int(g.h_row0 + m * g.h_stride + row0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) tma_store_2d(&map_h, 64 * c, y, abuf + c * 16384);
+          bulk_commit();
+          pending = true;
+        }
+      }
+      ++stores;
+      __syncwarp();
+      return __all_sync(0xffffffffu, ok);
+    };
+    // before this thread writes the operand buffer: every store of it has read it
+    auto buffer_free = [&]() -> bool {
+      if (issuer && pending) {
+        bulk_wait_read();
+        mbar_arrive(&st_free[slot]);
+        pending = false;
+      }
+      bool ok = true;
+      while (ok && frees < stores) ok = mbar_wait(&st_free[slot], uint32_t(frees++) & 1u);
+      return __all_sync(0xffffffffu, ok);
+    };
     for (int i = slot; i < my_tiles; i += 2) {
-      const long long ev = (long long)(int(blockIdx.x) + i * int(gridDim.x)) * 128 + r;
+      const long long row0 = (long long)(int(blockIdx.x) + i * int(gridDim.x)) * 128;
+      const long long ev = row0 + r;
       const float* Pe = g.P + ev * g.D;
       float* Po = g.Pout + ev * g.D;
       if (__any_sync(0xffffffffu, failed != 0)) break;
+      if (KEEP && !buffer_free()) {
+        failed = 1;
+        if (lane == 0) atomicExch(g.error, 24);
+        break;
+      }
       // the first-layer input (u_a, 1, zeros) as the A operand of the W1e product
       {
         __nv_bfloat16 v[16];
@@ -833,7 +885,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         for (int u16 = 2; u16 < kUK / 8; ++u16) *reinterpret_cast<uint4*>(abuf + swz_off(r, u16)) = make_uint4(0u, 0u, 0u, 0u);
       }
       fence_async_smem();
-      mbar_arrive(&a_ready[slot]);
+      arrive_a();
       // three hidden products: accumulator -> (bias), ReLU, BF16 -> operand buffer
       bool ok = true;
       for (int m = 0; m < 3 && ok; ++m, ++use_acc) {
@@ -842,8 +894,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
+        if (KEEP && !buffer_free()) {
+          ok = false;
+          break;
+        }
         const float* bias = m == 0 ? nullptr : prm + (m == 1 ? L.off_b2 : L.off_b3);  // b1 is inside W1e
-        __nv_bfloat16* hT = m == 0 ? g.hT1 : (m == 1 ? g.hT2 : g.hT3);
         uint32_t mb[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
         for (int cg = 0; cg < 4; ++cg) {  // 4 groups of 4 x 16 columns
           uint32_t v[4][16];
@@ -874,12 +929,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 const float o1 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e + 1]) + bv[2 * e + 1], 0.0f);
                 const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
                 pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
-                if (KEEP) {
+                if (KEEP)
                   mb[cc >> 5] |= (uint32_t(__bfloat162float(hh.x) > 0.0f) << (cc & 31)) |
                                  (uint32_t(__bfloat162float(hh.y) > 0.0f) << ((cc + 1) & 31));
-                  hT[size_t(cc) * g.n + ev] = hh.x;
-                  hT[size_t(cc + 1) * g.n + ev] = hh.y;
-                }
               }
               *reinterpret_cast<uint4*>(abuf + swz_off(r, (col0 + 16 * x + 8 * hlf) >> 3)) = pk;
             }
@@ -892,7 +944,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         fence_async_smem();
-        mbar_arrive(&a_ready[slot]);
+        arrive_a();
+        if (KEEP && !store_h(m, row0)) ok = false;
       }
       // W4 sub-products: the logits of two coordinates at a time, straight
       // from TMEM into the spline (coordinates in order, log c summed in order)
@@ -932,7 +985,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           ld += lc;
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
-        if (k + 1 < nsub) mbar_arrive(&a_ready[slot]);  // the accumulator is free for the next sub-product
+        if (k + 1 < nsub) arrive_a();  // the accumulator is free for the next sub-product
       }
       if (!ok) {
         failed = 1;
@@ -941,6 +994,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
       }
       g.logq[ev] -= ld;
     }
+    if (issuer) bulk_wait_all();  // the stores are complete before the kernel ends
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -1539,6 +1593,11 @@ struct mc_flow_s {
   // gradients G of each layer as a TMA source, and whether the layer fits
   std::vector<CUtensorMap> g_maps;
   std::vector<bool> chain_ok;
+  // the row-major activations h of every layer as one TMA map ([L x 3 x bp]
+  // rows of 256, boxes of 64 x 128): the fused training layer stores h1, h2,
+  // h3 through it
+  CUtensorMap h_map;
+  bool h_map_ok = false;
 };
 
 namespace {
@@ -1606,11 +1665,12 @@ int gemm_rs(mc_flow F, long long n, int N, int K, int epi, const __nv_bfloat16* 
   return MC_OK;
 }
 
-// Weight gradient gW^T [H x N] += XT [H x n] . YT [N x n]^T (both transposed
-// activations / gradients, K = n): split-K partial tiles, then a fixed-order
-// sum into the gradient.
-int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* XT, const __nv_bfloat16* YT, float* gWt,
-               cudaStream_t st, int* splits_out = nullptr) {
+// Weight gradient gW^T [H x N] += X^T . YT^T over the n events (K = n): X the
+// activations, row-major [n][H] (x_rows) or transposed [H][n], YT the
+// gradients transposed [N][n]; split-K partial tiles, then a fixed-order sum
+// into the gradient.
+int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* X, bool x_rows, const __nv_bfloat16* YT,
+               float* gWt, cudaStream_t st, int* splits_out = nullptr) {
   FLOW_CUDA(cudaGetLastError());
   const int bn = pick_bn(N);
   const int tiles = (kH / 128) * (N / bn);
@@ -1628,7 +1688,10 @@ int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* XT, const __n
   g.c_f32 = F->part;
   g.ldc = N;
   g.error = F->err;
-  FLOW_CUDA(mc::tc_gemm(g, XT, int(n), YT, int(n), splits, st));
+  if (x_rows)
+    FLOW_CUDA(mc::tc_gemm_xn(g, X, kH, YT, int(n), splits, st));
+  else
+    FLOW_CUDA(mc::tc_gemm(g, X, int(n), YT, int(n), splits, st));
   if (splits_out)
     *splits_out = splits;  // the caller sums the partials itself
   else
@@ -1676,9 +1739,8 @@ int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st, float
   a.Pout = keep ? P_of(F, l + 1) : (P0 ? P0 : P_of(F, 0));
   a.logq = lq ? lq : F->logq;
   if (keep) {
-    a.hT1 = hT_of(F, l, 0);
-    a.hT2 = hT_of(F, l, 1);
-    a.hT3 = hT_of(F, l, 2);
+    a.h_row0 = (long long)(h_of(F, l, 0) - F->h) / kH;
+    a.h_stride = F->bp;
     a.UT = UT_of(F, l);
     a.LT = LT_of(F, l);
     a.bits = MB_of(F, l);
@@ -1697,7 +1759,7 @@ int fused_layer(mc_flow F, int l, long long n, bool keep, cudaStream_t st, float
   FLOW_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const int grid = int(std::min<long long>(n / 128, num_sms));
   kern<<<grid, mc::kFusedThreads, smem, st>>>(F->maps[4 * l + 3], F->maps[4 * l], F->maps[4 * l + 1],
-                                              F->maps[4 * l + 2], a, stages);
+                                              F->maps[4 * l + 2], F->h_map, a, stages);
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
@@ -1847,14 +1909,14 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
       } else if (int rc = fused_bwd_layer(F, l, n, n_real, st)) {
         return rc;
       }
-      if (int rc = gemm_wgrad(F, n, L.nout_pad, hT_of(F, l, 2), F->GT, g + L.off_W4, st)) return rc;
-      if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 1), dA3T, g + L.off_W3, st)) return rc;
-      if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 0), dA2T, g + L.off_W2, st)) return rc;
+      if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, F->GT, g + L.off_W4, st)) return rc;
+      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, dA3T, g + L.off_W3, st)) return rc;
+      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, dA2T, g + L.off_W2, st)) return rc;
       // the bias gradients b4, b3, b2: row sums of G^T, dA3^T, dA2^T in one launch
       mc::RowSums3 rs{{F->GT, dA3T, dA2T}, {g + L.off_b4, g + L.off_b3, g + L.off_b2}, {L.nout_pad, kH, kH}};
       mc::rowsum3_bf16_kernel<<<L.nout_pad + 2 * kH, 256, 0, st>>>(rs, n);
       int splits = 0;
-      if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, UT_of(F, l), nullptr, st, &splits)) return rc;
+      if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, false, UT_of(F, l), nullptr, st, &splits)) return rc;
       mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
       FLOW_CUDA(cudaGetLastError());
       continue;
@@ -1864,18 +1926,18 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
     mc::spline_inv_bwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P_of(F, l + 1), F->dP, D, L, LT_of(F, l), F->K,
                                                                        F->w, F->sums, F->G, F->GT, n, n_real);
     // last dense layer: W4, b4, and the gradient of h3 (through its ReLU)
-    if (int rc = gemm_wgrad(F, n, L.nout_pad, hT_of(F, l, 2), F->GT, g + L.off_W4, st)) return rc;
+    if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, F->GT, g + L.off_W4, st)) return rc;
     mc::rowsum_bf16_kernel<<<L.nout_pad, 256, 0, st>>>(F->GT, n, g + L.off_b4);
     if (int rc = gemm_rs(F, n, kH, L.nout_pad, mc::kEpiReluMaskBf16, F->G, L.W4t, nullptr, dA, F->dAT,
                          hT_of(F, l, 2), st))
       return rc;
     // third dense layer
-    if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 1), F->dAT, g + L.off_W3, st)) return rc;
+    if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, F->dAT, g + L.off_W3, st)) return rc;
     mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b3);
     if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA, L.W3t, nullptr, dA_b, F->dAT, hT_of(F, l, 1), st))
       return rc;
     // second dense layer
-    if (int rc = gemm_wgrad(F, n, kH, hT_of(F, l, 0), F->dAT, g + L.off_W2, st)) return rc;
+    if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, F->dAT, g + L.off_W2, st)) return rc;
     mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b2);
     if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA_b, L.W2t, nullptr, dA, F->dAT, hT_of(F, l, 0), st))
       return rc;
@@ -1886,7 +1948,7 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
       return rc;
     mc::add_input_grad_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->dP, D, L, F->dU, n);
     int splits = 0;
-    if (int rc = gemm_wgrad(F, n, mc::kUPad, F->dAT, UT_of(F, l), nullptr, st, &splits)) return rc;
+    if (int rc = gemm_wgrad(F, n, mc::kUPad, F->dAT, false, UT_of(F, l), nullptr, st, &splits)) return rc;
     mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
     FLOW_CUDA(cudaGetLastError());
   }
@@ -2157,6 +2219,8 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   }
   build_host_map(F);
   // tensor maps of the fused layers
+  F->h_map_ok = size_t(L) * 3 * bp <= 0x7fffffffu &&
+                mc::tc_make_map(&F->h_map, F->h, int(size_t(L) * 3 * bp), kH, kH, 128);
   F->maps.resize(4 * L);
   F->bwd_maps.resize(4 * L);
   F->g_maps.resize(L);
@@ -2164,7 +2228,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
     const LayerDev& Ld = F->layers[l];
     // fused layers: 32 bins (logit stride 80), at most 6 transformed
     // coordinates (W4 sub-products of at most 256 rows)
-    bool ok = F->K == mc::kFusedK && ls == mc::kFusedLs && Ld.nb <= 6 && Ld.nout_pad <= 512;
+    bool ok = F->K == mc::kFusedK && ls == mc::kFusedLs && Ld.nb <= 6 && Ld.nout_pad <= 512 && F->h_map_ok;
     ok = ok && mc::tc_make_map(&F->maps[4 * l], Ld.W2h, kH, kH, kH, kH) &&
          mc::tc_make_map(&F->maps[4 * l + 1], Ld.W3h, kH, kH, kH, kH) &&
          mc::tc_make_map(&F->maps[4 * l + 2], Ld.W4h, Ld.nout_pad, kH, kH, 32) &&

@@ -32,11 +32,13 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;          // K elements per stage (one 128-byte swizzle atom)
 constexpr int kStages = 4;
 
-// TN: both operands MN-major, i.e. C = X^T Y with X [K x M] and Y [K x N]
-// row-major (the weight gradient of a dense layer from row-major activations
-// and gradients): each stage holds 64-wide MN blocks of 64 k rows (8 KiB each)
-// side by side, the descriptors step 2 KiB (16 k rows) per MMA.
-template <bool TN>
+// A_MN / B_MN: that operand is MN-major, i.e. it comes from a row-major
+// [K x M] (or [K x N]) array (C = X^T Y from row-major activations and
+// gradients: the weight gradient of a dense layer): its stage holds 64-wide
+// MN blocks of 64 k rows (8 KiB each) side by side and its descriptor steps
+// 2 KiB (16 k rows) per MMA; a K-major operand's stage is one box of 64 k
+// columns and its descriptor steps 32 bytes inside the swizzle atom.
+template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    TcGemmArgs g) {
@@ -94,13 +96,16 @@ __global__ void __launch_bounds__(128, 1)
       }
       unsigned char* st = smem + size_t(s) * stage_bytes;
       mbar_expect_tx(&full_bar[s], stage_bytes);
-      if (TN) {
+      if (A_MN) {
         for (int q = 0; q < kBM / 64; ++q)
           tma_load_2d(st + q * 8192, &map_a, tile_m * kBM + q * 64, (kb0 + i) * kBK, &full_bar[s]);
+      } else {
+        tma_load_2d(st, &map_a, (kb0 + i) * kBK, tile_m * kBM, &full_bar[s]);
+      }
+      if (B_MN) {
         for (int q = 0; q < bn / 64; ++q)
           tma_load_2d(st + a_bytes + q * 8192, &map_b, tile_n * bn + q * 64, (kb0 + i) * kBK, &full_bar[s]);
       } else {
-        tma_load_2d(st, &map_a, (kb0 + i) * kBK, tile_m * kBM, &full_bar[s]);
         tma_load_2d(st + a_bytes, &map_b, (kb0 + i) * kBK, tile_n * bn, &full_bar[s]);
       }
       ++issued;
@@ -109,8 +114,8 @@ __global__ void __launch_bounds__(128, 1)
     for (int s = 0; s < kStages && s < issued; ++s)
       mbar_wait(&full_bar[s], uint32_t((issued - 1 - s) / kStages) & 1u);
   } else if (warp == 1 && lane == 0 && nkb > 0) {
-    // MMA issuer: D = F32, A = B = BF16, K-major (or both MN-major: TN), N = bn, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (TN ? (1u << 15) | (1u << 16) : 0u) |
+    // MMA issuer: D = F32, A = B = BF16, each K-major or MN-major, N = bn, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (A_MN ? (1u << 15) : 0u) | (B_MN ? (1u << 16) : 0u) |
                            (uint32_t(bn >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % kStages;
@@ -121,17 +126,14 @@ __global__ void __launch_bounds__(128, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t a_addr = smem_u32(smem + size_t(s) * stage_bytes);
-      if (TN) {
-        const uint64_t ad = smem_desc_mn(a_addr, 8192), bd = smem_desc_mn(a_addr + a_bytes, 8192);
+      const uint64_t ad = A_MN ? smem_desc_mn(a_addr, 8192) : smem_desc(a_addr);
+      const uint64_t bd = B_MN ? smem_desc_mn(a_addr + a_bytes, 8192) : smem_desc(a_addr + a_bytes);
+      // per 16 k: an MN-major operand advances 16 k rows = 2 KiB, a K-major one
+      // 16 BF16 = 32 bytes along K inside the swizzle atom (descriptor units of 16 bytes)
+      constexpr uint64_t kStepA = A_MN ? 128 : 2, kStepB = B_MN ? 128 : 2;
 #pragma unroll
-        for (int k = 0; k < kBK / 16; ++k)  // advance 16 k rows = 2 KiB
-          mma_bf16(tmem, ad + uint64_t(k * 128), bd + uint64_t(k * 128), idesc, (i > 0 || k > 0) ? 1u : 0u);
-      } else {
-        const uint64_t ad = smem_desc(a_addr), bd = smem_desc(a_addr + a_bytes);
-#pragma unroll
-        for (int k = 0; k < kBK / 16; ++k)  // advance 16 BF16 = 32 bytes along K inside the swizzle atom
-          mma_bf16(tmem, ad + uint64_t(k * 2), bd + uint64_t(k * 2), idesc, (i > 0 || k > 0) ? 1u : 0u);
-      }
+      for (int k = 0; k < kBK / 16; ++k)
+        mma_bf16(tmem, ad + uint64_t(k) * kStepA, bd + uint64_t(k) * kStepB, idesc, (i > 0 || k > 0) ? 1u : 0u);
       mma_commit(&empty_bar[s]);
     }
     mma_commit(&done_bar);  // completes once every MMA issued above has
@@ -569,10 +571,11 @@ cudaError_t tc_gemm(const TcGemmArgs& g_in, const __nv_bfloat16* a, int lda, con
   if (!make_map(&ma, a, g.M, g.K, lda, kBM) || !make_map(&mb, b, g.N, g.K, ldb, g.bn)) return cudaErrorInvalidValue;
   const size_t smem = tc_gemm_smem(g.bn);
   (void)cudaGetLastError();
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e =
+      cudaFuncSetAttribute(tc_gemm_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const dim3 grid(g.M / kBM, g.N / g.bn, splits);
-  tc_gemm_kernel<false><<<grid, 128, smem, st>>>(ma, mb, g);
+  tc_gemm_kernel<false, false><<<grid, 128, smem, st>>>(ma, mb, g);
   return cudaGetLastError();
 }
 
@@ -587,10 +590,30 @@ cudaError_t tc_gemm_tn(const TcGemmArgs& g_in, const __nv_bfloat16* x, int ldx, 
   if (!tc_make_map(&ma, x, g.K, g.M, ldx, 64) || !tc_make_map(&mb, y, g.K, g.N, ldy, 64)) return cudaErrorInvalidValue;
   const size_t smem = tc_gemm_smem(g.bn);
   (void)cudaGetLastError();
-  cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e =
+      cudaFuncSetAttribute(tc_gemm_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const dim3 grid(g.M / kBM, g.N / g.bn, splits);
-  tc_gemm_kernel<true><<<grid, 128, smem, st>>>(ma, mb, g);
+  tc_gemm_kernel<true, true><<<grid, 128, smem, st>>>(ma, mb, g);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_xn(const TcGemmArgs& g_in, const __nv_bfloat16* x, int ldx, const __nv_bfloat16* b, int ldb,
+                       int splits, cudaStream_t st) {
+  TcGemmArgs g = g_in;
+  if (g.M % kBM || g.K % kBK || g.bn % 16 || g.bn < 16 || g.bn > 256 || g.N % g.bn || splits < 1 || !g.error ||
+      !aligned16(x) || !aligned16(b) || (ldx % 8) || (ldb % 8) || ldx < g.M || ldb < g.K ||
+      (g.epilogue != kEpiBiasF32 && g.epilogue != kEpiAtomicF32 && g.epilogue != kEpiPartialF32) || !g.c_f32)
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;  // x: [K rows x M], boxes of 64 x 64; b: [N rows x K], boxes of bn x 64
+  if (!tc_make_map(&ma, x, g.K, g.M, ldx, 64) || !make_map(&mb, b, g.N, g.K, ldb, g.bn)) return cudaErrorInvalidValue;
+  const size_t smem = tc_gemm_smem(g.bn);
+  (void)cudaGetLastError();
+  cudaError_t e =
+      cudaFuncSetAttribute(tc_gemm_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const dim3 grid(g.M / kBM, g.N / g.bn, splits);
+  tc_gemm_kernel<true, false><<<grid, 128, smem, st>>>(ma, mb, g);
   return cudaGetLastError();
 }
 

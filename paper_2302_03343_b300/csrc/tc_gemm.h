@@ -51,6 +51,13 @@ cudaError_t tc_gemm(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, const 
 cudaError_t tc_gemm_tn(const TcGemmArgs& g, const __nv_bfloat16* x, int ldx, const __nv_bfloat16* y, int ldy,
                        int splits, cudaStream_t st);
 
+// A MN-major, B K-major: C[M x N] (+)= X^T B^T with X [K x M] row-major
+// (ldx >= M) and B [N x K] row-major (ldb >= K), split-K over `splits`; bn a
+// multiple of 16, epilogues 1, 3 or 4.  The weight gradient of a dense layer
+// from row-major activations and transposed gradients.
+cudaError_t tc_gemm_xn(const TcGemmArgs& g, const __nv_bfloat16* x, int ldx, const __nv_bfloat16* b, int ldb,
+                       int splits, cudaStream_t st);
+
 // Persistent variant for a long A and a short B (the dense layers applied to
 // a batch): B [N x K] stays resident in shared memory (bn * K * 2 bytes <=
 // 160 KiB, K <= 320), A tiles stream through a TMA ring, two TMEM
