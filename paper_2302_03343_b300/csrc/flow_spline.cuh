@@ -3,7 +3,11 @@
 // vertex heights V = exp(e) / A with A = sum_k (exp e_k + exp e_{k+1})/2 W_k,
 // so that the piecewise-linear density c integrates to one and the CDF C is
 // piecewise quadratic.  Forward: y = C(x); inverse: x = C^-1(y) by the stable
-// root of the bin's quadratic; backward of the inverse for training.  FP32.
+// root of the bin's quadratic; backward of the inverse for training.  FP32;
+// the 2K+1 exponentials of a coordinate use the hardware exponential
+// (__expf: a few ulp for the logits' range, two instructions instead of the
+// range-reduced expf) in every path, so the fused and layer-by-layer kernels
+// agree bit for bit.
 //
 // Every loop runs over the compile-time maximum kFlowMaxBins with a K guard
 // and every array is indexed with compile-time indices only, so a Spline and
@@ -34,14 +38,14 @@ MC_D void spline_load(const float* lg, size_t ld, int K, Spline& s) {
   float sw = 0.0f;
 #pragma unroll
   for (int k = 0; k < kFlowMaxBins; ++k) {
-    s.W[k] = k < K ? expf(a[k] - mx) : 0.0f;
+    s.W[k] = k < K ? __expf(a[k] - mx) : 0.0f;
     sw += s.W[k];
   }
   const float isw = 1.0f / sw;
 #pragma unroll
   for (int k = 0; k < kFlowMaxBins; ++k) s.W[k] *= isw;
 #pragma unroll
-  for (int k = 0; k <= kFlowMaxBins; ++k) s.V[k] = k <= K ? expf(lg[size_t(K + k) * ld]) : 0.0f;
+  for (int k = 0; k <= kFlowMaxBins; ++k) s.V[k] = k <= K ? __expf(lg[size_t(K + k) * ld]) : 0.0f;
   float area = 0.0f;
 #pragma unroll
   for (int k = 0; k < kFlowMaxBins; ++k)
@@ -62,14 +66,14 @@ MC_D void spline_load_regs(const float (&lg)[NL], Spline& s) {
   float sw = 0.0f;
 #pragma unroll
   for (int k = 0; k < kFlowMaxBins; ++k) {
-    s.W[k] = k < K ? expf(lg[k < K ? k : 0] - mx) : 0.0f;
+    s.W[k] = k < K ? __expf(lg[k < K ? k : 0] - mx) : 0.0f;
     sw += s.W[k];
   }
   const float isw = 1.0f / sw;
 #pragma unroll
   for (int k = 0; k < kFlowMaxBins; ++k) s.W[k] *= isw;
 #pragma unroll
-  for (int k = 0; k <= kFlowMaxBins; ++k) s.V[k] = k <= K ? expf(lg[k <= K ? K + k : 0]) : 0.0f;
+  for (int k = 0; k <= kFlowMaxBins; ++k) s.V[k] = k <= K ? __expf(lg[k <= K ? K + k : 0]) : 0.0f;
   float area = 0.0f;
 #pragma unroll
   for (int k = 0; k < kFlowMaxBins; ++k)
