@@ -545,11 +545,16 @@ struct AdamArgs {
   const float* c;  // [2] on the device: 1/(1 - b1^t), 1/(1 - b2^t) of step t
 };
 // Advances the device step count t and forms Adam's bias corrections of step
-// t (one thread; FP64 powers, rounded to FP32 as the update uses them).
-__global__ void adam_prep_kernel(long long* step, float* c, double b1, double b2) {
-  const long long t = ++*step;
-  c[0] = float(1.0 / (1.0 - pow(b1, double(t))));
-  c[1] = float(1.0 / (1.0 - pow(b2, double(t))));
+// t (one thread): the powers b1^t, b2^t kept as running FP64 products in
+// pw[0..1] (one multiplication each per step instead of a pow), the
+// corrections rounded to FP32 as the update uses them.
+__global__ void adam_prep_kernel(long long* step, double* pw, float* c, double b1, double b2) {
+  ++*step;
+  const double p1 = pw[0] * b1, p2 = pw[1] * b2;
+  pw[0] = p1;
+  pw[1] = p2;
+  c[0] = float(1.0 / (1.0 - p1));
+  c[1] = float(1.0 / (1.0 - p2));
 }
 __global__ void adam_kernel(float* params, const float* grads, float* m, float* v, size_t n, const LayerDev* layers,
                             int nl, AdamArgs A) {
@@ -1574,11 +1579,20 @@ struct mc_flow_s {
   // the training step count on the device (mirrors `step`) and Adam's bias
   // corrections of the current step
   long long* d_step = nullptr;
+  double* d_adam_pow = nullptr;  // b1^t, b2^t
   float* d_adam = nullptr;
   // the stream a training step is captured on and replayed from as a CUDA
   // graph, and the events that order it after and before the caller's stream
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // the weight-gradient products of a fused backward layer run on `side`
+  // after the layer's chain (ev_chain), beside the next layers' spline
+  // backward and chain on the caller's stream; the logit gradients G, G^T and
+  // the activation gradients dA^T are double-buffered by layer parity, and a
+  // layer waits for the side work of the layer two before it (ev_side)
+  // before it rewrites that buffer set
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> ev_chain, ev_side;
   int nout_pad_max = 0;
   // data-parallel step: events of the batch sampled by mc_flow_step_sample
   // and not yet differentiated (0: none)
@@ -1623,6 +1637,11 @@ __nv_bfloat16* hT_of(mc_flow F, int l, int k) { return F->hT + (size_t(l) * 3 + 
 float* LT_of(mc_flow F, int l) { return F->LT + size_t(l) * F->bp * F->nout_pad_max; }
 __nv_bfloat16* UT_of(mc_flow F, int l) { return F->UT + size_t(l) * F->bp * mc::kUPad; }
 uint32_t* MB_of(mc_flow F, int l) { return F->MB + size_t(l) * 3 * F->bp * 8; }
+// buffer set `set` (0 or 1) of the logit gradients G [n][nout_pad] and G^T,
+// and of dA3^T, dA2^T, dA1^T (three slices of bp x 256)
+__nv_bfloat16* G_of(mc_flow F, int set) { return F->G + size_t(set) * F->bp * F->nout_pad_max; }
+__nv_bfloat16* GT_of(mc_flow F, int set) { return F->GT + size_t(set) * F->bp * F->nout_pad_max; }
+__nv_bfloat16* dAT_of(mc_flow F, int set, int k) { return F->dAT + (size_t(set) * 3 + k) * F->bp * kH; }
 
 // ReLU activity bits of layer slot l from its transposed activations (n rows).
 void make_mask_bits(mc_flow F, int l, long long n, cudaStream_t st) {
@@ -1809,7 +1828,7 @@ int inverse_pass(mc_flow F, long long n, cudaStream_t st) {
 // Fused backward of layer l (flow_layer_bwd_kernel): dP updated, the
 // transposed gradients G^T and dA3^T, dA2^T, dA1^T (three slices of F->dAT)
 // written for the weight-gradient products.
-int fused_bwd_layer(mc_flow F, int l, long long n, long long n_real, cudaStream_t st) {
+int fused_bwd_layer(mc_flow F, int l, long long n, long long n_real, int set, cudaStream_t st) {
   FLOW_CUDA(cudaGetLastError());
   static int num_sms = 0;
   if (num_sms == 0) {
@@ -1827,10 +1846,10 @@ int fused_bwd_layer(mc_flow F, int l, long long n, long long n_real, cudaStream_
   a.w = F->w;
   a.wsum = F->sums;
   a.bits = MB_of(F, l);
-  a.GT = F->GT;
-  a.dA3T = F->dAT;
-  a.dA2T = F->dAT + size_t(F->bp) * kH;
-  a.dA1T = F->dAT + 2 * size_t(F->bp) * kH;
+  a.GT = GT_of(F, set);
+  a.dA3T = dAT_of(F, set, 0);
+  a.dA2T = dAT_of(F, set, 1);
+  a.dA1T = dAT_of(F, set, 2);
   a.L = L;
   a.D = F->D;
   a.n = n;
@@ -1852,7 +1871,7 @@ int fused_bwd_layer(mc_flow F, int l, long long n, long long n_real, cudaStream_
 
 // Two-tile backward chain of layer l (flow_chain_bwd_kernel) after the spline
 // backward has written G, G^T and the spline part of dP.
-int chain_bwd_layer(mc_flow F, int l, long long n, cudaStream_t st) {
+int chain_bwd_layer(mc_flow F, int l, long long n, int set, cudaStream_t st) {
   FLOW_CUDA(cudaGetLastError());
   static int num_sms = 0;
   if (num_sms == 0) {
@@ -1866,9 +1885,9 @@ int chain_bwd_layer(mc_flow F, int l, long long n, cudaStream_t st) {
   std::memset(&a, 0, sizeof(a));
   a.dP = F->dP;
   a.bits = MB_of(F, l);
-  a.dA3T = F->dAT;
-  a.dA2T = F->dAT + size_t(F->bp) * kH;
-  a.dA1T = F->dAT + 2 * size_t(F->bp) * kH;
+  a.dA3T = dAT_of(F, set, 0);
+  a.dA2T = dAT_of(F, set, 1);
+  a.dA1T = dAT_of(F, set, 2);
   a.L = L;
   a.D = F->D;
   a.n = n;
@@ -1879,7 +1898,7 @@ int chain_bwd_layer(mc_flow F, int l, long long n, cudaStream_t st) {
   const size_t smem = 1024 + 2 * abytes + stages * stage;
   FLOW_CUDA(cudaFuncSetAttribute(mc::flow_chain_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const int grid = int(std::min<long long>(n / 128, num_sms));
-  mc::flow_chain_bwd_kernel<<<grid, mc::kChainThreads, smem, st>>>(F->g_maps[l], F->bwd_maps[4 * l],
+  mc::flow_chain_bwd_kernel<<<grid, mc::kChainThreads, smem, st>>>(F->g_maps[2 * l + set], F->bwd_maps[4 * l],
                                                                   F->bwd_maps[4 * l + 1], F->bwd_maps[4 * l + 2],
                                                                   F->bwd_maps[4 * l + 3], a, stages);
   FLOW_CUDA(cudaGetLastError());
@@ -1893,34 +1912,50 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
   const int D = F->D;
   float* g = F->d_grads;
   FLOW_CUDA(cudaMemsetAsync(F->dP, 0, sizeof(float) * n * D, st));
+  int side_last = -1;  // the last layer whose weight gradients went to F->side
+  auto join_side = [&]() -> int {
+    if (side_last >= 0) FLOW_CUDA(cudaStreamWaitEvent(st, F->ev_side[side_last], 0));
+    side_last = -1;
+    return MC_OK;
+  };
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& L = F->layers[l];
     if (F->use_fused_bwd && F->fused_ok[l]) {
       // spline and activation gradients (the spline backward at full
       // occupancy, then the two-tile product chain; one fused kernel where the
-      // chain's buffers do not fit), then the weight gradients
-      __nv_bfloat16* dA3T = F->dAT;
-      __nv_bfloat16* dA2T = F->dAT + size_t(F->bp) * kH;
-      __nv_bfloat16* dA1T = F->dAT + 2 * size_t(F->bp) * kH;
+      // chain's buffers do not fit), then the weight gradients on the side
+      // stream, beside the next layers' spline backward and chain
+      const int set = l & 1;
+      if (l >= 2 && side_last >= l - 2) FLOW_CUDA(cudaStreamWaitEvent(st, F->ev_side[l - 2], 0));
+      __nv_bfloat16 *G = G_of(F, set), *GT = GT_of(F, set);
+      __nv_bfloat16 *dA3T = dAT_of(F, set, 0), *dA2T = dAT_of(F, set, 1), *dA1T = dAT_of(F, set, 2);
       if (F->chain_ok[l]) {
         mc::spline_bwd_k32_kernel<<<dim3(mc::blocks_for(n, 128), L.nb), 128, 0, st>>>(
-            P_of(F, l + 1), F->dP, D, L, LT_of(F, l), F->w, F->sums, F->G, F->GT, n, n_real);
-        if (int rc = chain_bwd_layer(F, l, n, st)) return rc;
-      } else if (int rc = fused_bwd_layer(F, l, n, n_real, st)) {
+            P_of(F, l + 1), F->dP, D, L, LT_of(F, l), F->w, F->sums, G, GT, n, n_real);
+        if (int rc = chain_bwd_layer(F, l, n, set, st)) return rc;
+      } else if (int rc = fused_bwd_layer(F, l, n, n_real, set, st)) {
         return rc;
       }
-      if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, F->GT, g + L.off_W4, st)) return rc;
-      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, dA3T, g + L.off_W3, st)) return rc;
-      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, dA2T, g + L.off_W2, st)) return rc;
+      FLOW_CUDA(cudaEventRecord(F->ev_chain[l], st));
+      const cudaStream_t ss = F->side;
+      FLOW_CUDA(cudaStreamWaitEvent(ss, F->ev_chain[l], 0));
+      if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, GT, g + L.off_W4, ss)) return rc;
+      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, dA3T, g + L.off_W3, ss)) return rc;
+      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, dA2T, g + L.off_W2, ss)) return rc;
       // the bias gradients b4, b3, b2: row sums of G^T, dA3^T, dA2^T in one launch
-      mc::RowSums3 rs{{F->GT, dA3T, dA2T}, {g + L.off_b4, g + L.off_b3, g + L.off_b2}, {L.nout_pad, kH, kH}};
-      mc::rowsum3_bf16_kernel<<<L.nout_pad + 2 * kH, 256, 0, st>>>(rs, n);
+      mc::RowSums3 rs{{GT, dA3T, dA2T}, {g + L.off_b4, g + L.off_b3, g + L.off_b2}, {L.nout_pad, kH, kH}};
+      mc::rowsum3_bf16_kernel<<<L.nout_pad + 2 * kH, 256, 0, ss>>>(rs, n);
       int splits = 0;
-      if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, false, UT_of(F, l), nullptr, st, &splits)) return rc;
-      mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
+      if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, false, UT_of(F, l), nullptr, ss, &splits)) return rc;
+      mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, ss>>>(F->part, splits, L, g);
       FLOW_CUDA(cudaGetLastError());
+      FLOW_CUDA(cudaEventRecord(F->ev_side[l], ss));
+      side_last = l;
       continue;
     }
+    // the layer-by-layer path shares the split-K partials and buffer set 0
+    // with the side stream: wait for it
+    if (int rc = join_side()) return rc;
     __nv_bfloat16* dA = F->dA;
     __nv_bfloat16* dA_b = F->dA + size_t(F->bp) * kH;
     mc::spline_inv_bwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P_of(F, l + 1), F->dP, D, L, LT_of(F, l), F->K,
@@ -1952,7 +1987,7 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
     mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
     FLOW_CUDA(cudaGetLastError());
   }
-  return MC_OK;
+  return join_side();
 }
 
 int refresh_bf16(mc_flow F, cudaStream_t st) {
@@ -2031,7 +2066,7 @@ int eval_points_sums(mc_flow F, const mc_integrand* itg, const mc::KernelArgs& a
 // the device; the caller advances F->step).
 int adam_launch(mc_flow F, double lr, cudaStream_t st) {
   const double b1 = 0.9, b2 = 0.999;
-  mc::adam_prep_kernel<<<1, 1, 0, st>>>(F->d_step, F->d_adam, b1, b2);
+  mc::adam_prep_kernel<<<1, 1, 0, st>>>(F->d_step, F->d_adam_pow, F->d_adam, b1, b2);
   mc::AdamArgs A{float(lr), float(b1), float(b2), 1e-8f, F->d_adam};
   mc::adam_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_params, F->d_grads, F->d_m, F->d_v, F->nparam,
                                                                    F->d_layers, F->L, A);  // refreshes the BF16 copies
@@ -2105,8 +2140,13 @@ int mc_flow_free(mc_flow F) {
                   (void*)F->LT, (void*)F->h, (void*)F->hT, (void*)F->G, (void*)F->GT, (void*)F->dA, (void*)F->dAT,
                   (void*)F->part, (void*)F->UT, (void*)F->MB, (void*)F->dU, (void*)F->U, (void*)F->Ps, (void*)F->lqs,
                   (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
-                  (void*)F->err, (void*)F->d_step, (void*)F->d_adam})
+                  (void*)F->err, (void*)F->d_step, (void*)F->d_adam, (void*)F->d_adam_pow})
     cudaFree(p);
+  for (cudaEvent_t e : F->ev_chain)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : F->ev_side)
+    if (e) cudaEventDestroy(e);
+  if (F->side) cudaStreamDestroy(F->side);
   if (F->ev_in) cudaEventDestroy(F->ev_in);
   if (F->ev_out) cudaEventDestroy(F->ev_out);
   if (F->cap) cudaStreamDestroy(F->cap);
@@ -2179,10 +2219,10 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->LT, sizeof(float) * L * np * bp);
   alloc((void**)&F->h, sizeof(__nv_bfloat16) * L * 3 * bp * kH);
   alloc((void**)&F->hT, sizeof(__nv_bfloat16) * L * 3 * bp * kH);
-  alloc((void**)&F->G, sizeof(__nv_bfloat16) * bp * np);
-  alloc((void**)&F->GT, sizeof(__nv_bfloat16) * bp * np);
+  alloc((void**)&F->G, sizeof(__nv_bfloat16) * 2 * bp * np);
+  alloc((void**)&F->GT, sizeof(__nv_bfloat16) * 2 * bp * np);
   alloc((void**)&F->dA, sizeof(__nv_bfloat16) * 2 * bp * kH);
-  alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * 3 * bp * kH);
+  alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * 2 * 3 * bp * kH);
   alloc((void**)&F->part, sizeof(float) * size_t(F->max_splits) * kH * np);
   alloc((void**)&F->UT, sizeof(__nv_bfloat16) * L * mc::kUPad * bp);
   alloc((void**)&F->MB, sizeof(uint32_t) * L * 3 * bp * 8);
@@ -2194,12 +2234,20 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->err, sizeof(int));
   alloc((void**)&F->d_step, sizeof(long long));
   alloc((void**)&F->d_adam, sizeof(float) * 2);
+  alloc((void**)&F->d_adam_pow, sizeof(double) * 2);
   F->sbp = std::max<long long>(F->bp, 1 << 20);
   alloc((void**)&F->Ps, sizeof(float) * size_t(F->sbp) * D);
   alloc((void**)&F->lqs, sizeof(float) * size_t(F->sbp));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_sums, sizeof(double) * 2);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&F->h_total, sizeof(BlockPartial));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&F->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&F->side, cudaStreamNonBlocking);
+  F->ev_chain.assign(L, nullptr);
+  F->ev_side.assign(L, nullptr);
+  for (int l = 0; l < L && e == cudaSuccess; ++l) {
+    e = cudaEventCreateWithFlags(&F->ev_chain[l], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->ev_side[l], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->ev_out, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -2223,7 +2271,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
                 mc::tc_make_map(&F->h_map, F->h, int(size_t(L) * 3 * bp), kH, kH, 128);
   F->maps.resize(4 * L);
   F->bwd_maps.resize(4 * L);
-  F->g_maps.resize(L);
+  F->g_maps.resize(2 * L);
   for (int l = 0; l < F->L; ++l) {
     const LayerDev& Ld = F->layers[l];
     // fused layers: 32 bins (logit stride 80), at most 6 transformed
@@ -2242,18 +2290,22 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
     // weight stages must fit in shared memory
     const size_t abytes = size_t(std::max(kH, Ld.nout_pad)) * 256;
     const bool fits = 2 * abytes + 2 * size_t(kH) * 128 + 1024 <= mc::kChainSmemMax;
-    F->chain_ok.push_back(ok && fits && mc::tc_make_map(&F->g_maps[l], F->G, int(bp), Ld.nout_pad, Ld.nout_pad, 128));
+    F->chain_ok.push_back(ok && fits &&
+                          mc::tc_make_map(&F->g_maps[2 * l], G_of(F, 0), int(bp), Ld.nout_pad, Ld.nout_pad, 128) &&
+                          mc::tc_make_map(&F->g_maps[2 * l + 1], G_of(F, 1), int(bp), Ld.nout_pad, Ld.nout_pad, 128));
   }
+  const double kOnes[2] = {1.0, 1.0};  // b1^0, b2^0
   // the padding rows of the logit gradients and of U^T are never written: zero them once
   if (cudaMemcpy(F->d_layers, F->layers.data(), sizeof(LayerDev) * L, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(F->d_m, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(F->d_v, 0, sizeof(float) * off) != cudaSuccess ||
       cudaMemset(F->d_grads, 0, sizeof(float) * off) != cudaSuccess ||
-      cudaMemset(F->GT, 0, sizeof(__nv_bfloat16) * bp * np) != cudaSuccess ||
-      cudaMemset(F->G, 0, sizeof(__nv_bfloat16) * bp * np) != cudaSuccess ||
+      cudaMemset(F->GT, 0, sizeof(__nv_bfloat16) * 2 * bp * np) != cudaSuccess ||
+      cudaMemset(F->G, 0, sizeof(__nv_bfloat16) * 2 * bp * np) != cudaSuccess ||
       cudaMemset(F->UT, 0, sizeof(__nv_bfloat16) * L * mc::kUPad * bp) != cudaSuccess ||
       cudaMemset(F->err, 0, sizeof(int)) != cudaSuccess ||
-      cudaMemset(F->d_step, 0, sizeof(long long)) != cudaSuccess) {
+      cudaMemset(F->d_step, 0, sizeof(long long)) != cudaSuccess ||
+      cudaMemcpy(F->d_adam_pow, kOnes, sizeof(kOnes), cudaMemcpyHostToDevice) != cudaSuccess) {
     mc_flow_free(F);
     return ffail(MC_ECUDA, "mc_flow_create: initialisation failed");
   }
