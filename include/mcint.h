@@ -496,6 +496,15 @@ int mc_gemm_bf16(int M, int N, int K, int bn, int epilogue, const void* a, int l
  * Asynchronous on `stream`. */
 int mc_gemm_bf16_tn(int M, int N, int K, int bn, int epilogue, const void* x, int ldx, const void* y, int ldy,
                     float* c, int ldc, int splits, int* err, void* stream);
+/* mc_gemm_bf16_xn: C[M x N] (+)= X^T B^T with X [K x M] row-major (ldx >= M)
+ * and B [N x K] row-major (ldb >= K), BF16 on the device (leading dimensions
+ * multiples of 8, 16-byte aligned): the weight gradient of a dense layer from
+ * row-major activations X and transposed gradients B, X read MN-major and B
+ * K-major by the tensor cores.  Epilogues 1, 3, 4 as for mc_gemm_bf16_tn;
+ * M % 128 == 0, K % 64 == 0, bn a multiple of 16 <= 256 dividing N.
+ * Asynchronous on `stream`. */
+int mc_gemm_bf16_xn(int M, int N, int K, int bn, int epilogue, const void* x, int ldx, const void* b, int ldb,
+                    float* c, int ldc, int splits, int* err, void* stream);
 /* mc_gemm_bf16_rs: the same product for a long A and a short B (a dense
  * layer applied to a batch): a persistent kernel keeps B in shared memory
  * (bn * K * 2 bytes, K <= 320) and streams the 128-row tiles of A, with the

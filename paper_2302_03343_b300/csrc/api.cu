@@ -811,6 +811,28 @@ int mc_gemm_bf16_tn(int M, int N, int K, int bn, int epilogue, const void* x, in
   return MC_OK;
 }
 
+int mc_gemm_bf16_xn(int M, int N, int K, int bn, int epilogue, const void* x, int ldx, const void* b, int ldb,
+                    float* c, int ldc, int splits, int* err, void* stream) {
+  if (!x || !b || !c || !err || (epilogue != 1 && epilogue != 3 && epilogue != 4))
+    return fail(MC_EINVAL, "mc_gemm_bf16_xn: bad arguments");
+  mc::TcGemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.bn = bn;
+  g.epilogue = epilogue;
+  g.c_f32 = c;
+  g.ldc = ldc;
+  g.error = err;
+  const cudaError_t e = mc::tc_gemm_xn(g, static_cast<const __nv_bfloat16*>(x), ldx,
+                                       static_cast<const __nv_bfloat16*>(b), ldb, splits,
+                                       static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return fail(MC_EINVAL, "mc_gemm_bf16_xn: unsupported shape or alignment");
+  if (e != cudaSuccess) return fail(MC_ECUDA, "mc_gemm_bf16_xn: %s", cudaGetErrorString(e));
+  return MC_OK;
+}
+
 int mc_gemm_bf16_rs(int M, int N, int K, int bn, int epilogue, const void* a, int lda, const void* b, int ldb,
                     const float* bias, void* c, int ldc, void* c_t, int ldt, const void* mask, int ld_mask, int* err,
                     void* stream) {

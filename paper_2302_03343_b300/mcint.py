@@ -30,7 +30,7 @@ SYMBOLS = ("mc_last_error", "mc_pdf_load", "mc_pdf_free", "mc_pdf_xfxq2", "mc_ve
            "mc_vegas_get_iteration", "mc_vegas_set_gid", "mc_vegas_iterate", "mc_vegas_refine", "mc_integrate",
            "mc_debug_events", "mc_launch_shape", "mc_vegas_kernel_ms", "mc_vegas_iterate_noalloc",
            "mc_batch_create", "mc_batch_iterate", "mc_batch_get_grid", "mc_batch_shape", "mc_batch_kernel_ms",
-           "mc_batch_free", "mc_gemm_bf16", "mc_gemm_bf16_rs", "mc_gemm_bf16_tn", "mc_flow_param_count", "mc_flow_create", "mc_flow_free",
+           "mc_batch_free", "mc_gemm_bf16", "mc_gemm_bf16_rs", "mc_gemm_bf16_tn", "mc_gemm_bf16_xn", "mc_flow_param_count", "mc_flow_create", "mc_flow_free",
            "mc_flow_set_params", "mc_flow_get_params", "mc_flow_forward", "mc_flow_loss_grad", "mc_flow_adam_step",
            "mc_flow_train", "mc_flow_iterate", "mc_flow_set_fused", "mc_integrate_flow", "mc_pdfset_load",
            "mc_pdfset_free", "mc_pdfset_xfxq2", "mc_alphas_load", "mc_alphas_free", "mc_alphas_q2",
@@ -134,6 +134,7 @@ def lib():
             "mc_batch_free": [_vp],
             "mc_gemm_bf16": [i32, i32, i32, i32, i32, _vp, i32, _vp, i32, _vp, _vp, i32, _vp, i32, i32, _vp, _vp],
             "mc_gemm_bf16_tn": [i32, i32, i32, i32, i32, _vp, i32, _vp, i32, _vp, i32, i32, _vp, _vp],
+            "mc_gemm_bf16_xn": [i32, i32, i32, i32, i32, _vp, i32, _vp, i32, _vp, i32, i32, _vp, _vp],
             "mc_gemm_bf16_rs": [i32, i32, i32, i32, i32, _vp, i32, _vp, i32, _vp, _vp, i32, _vp, i32, _vp, i32, _vp,
                                 _vp],
             "mc_vegas_iterate_noalloc": [ctypes.POINTER(Integrand), _vp, i32, i32, _vp, _vp, i32, u64, u32, u32,
@@ -617,6 +618,12 @@ def mc_gemm_bf16(M, N, K, bn, epilogue, a, b, c, bias=None, mask=None, splits=1,
 def mc_gemm_bf16_tn(M, N, K, bn, epilogue, x, y, c, splits=1, err=None, stream=None):
     """C[M x N] (+)= X^T Y, X [K x M], Y [K x N] row-major BF16 (torch tensors on the device)."""
     _check(lib().mc_gemm_bf16_tn(M, N, K, bn, epilogue, _ptr(x), x.stride(0), _ptr(y), y.stride(0), _ptr(c),
+                                 c.stride(-2), splits, _ptr(err), _stream(stream)))
+
+
+def mc_gemm_bf16_xn(M, N, K, bn, epilogue, x, b, c, splits=1, err=None, stream=None):
+    """C[M x N] (+)= X^T B^T, X [K x M], B [N x K] row-major BF16 (torch tensors on the device)."""
+    _check(lib().mc_gemm_bf16_xn(M, N, K, bn, epilogue, _ptr(x), x.stride(0), _ptr(b), b.stride(0), _ptr(c),
                                  c.stride(-2), splits, _ptr(err), _stream(stream)))
 
 

@@ -156,3 +156,43 @@ def test_gemm_tn_weight_gradient(dev, M_, N, K, bn, splits):
     assert err.item() == 0
     ref = x.double().T @ y.double()
     assert ((c.double() - ref).abs().max() / ref.abs().max()).item() < 1e-5
+
+
+# A MN-major, B K-major: C = X^T B^T from row-major X [K x M] and B [N x K]
+# (the weight gradient from row-major activations and transposed gradients);
+# N = 240 and 320 are the logit widths of three and four transformed
+# coordinates, tiles of 16 to 256 columns
+@pytest.mark.parametrize("M_,N,K,bn,splits", [(128, 16, 64, 16, 1), (256, 256, 4096, 256, 4), (256, 240, 8192, 240, 8),
+                                              (256, 320, 65536, 160, 37), (128, 128, 65536, 128, 74)])
+def test_gemm_xn_weight_gradient(dev, M_, N, K, bn, splits):
+    g = torch.Generator(device="cpu").manual_seed(11)
+    x = torch.randn(K, M_, generator=g).to(torch.bfloat16).to(dev)
+    b = torch.randn(N, K, generator=g).to(torch.bfloat16).to(dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    c = torch.zeros((M_, N), device=dev)
+    M.mc_gemm_bf16_xn(M_, N, K, bn, M.EPI_ATOMIC_F32, x, b, c, splits=splits, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    ref = x.double().T @ b.double().T
+    assert ((c.double() - ref).abs().max() / ref.abs().max()).item() < 1e-5
+    # the per-split partials (epilogue 4) sum to the same product, and the
+    # K-major product of the transposed X gives the same bits split by split
+    parts = torch.empty((splits, M_, N), device=dev)
+    M.mc_gemm_bf16_xn(M_, N, K, bn, M.EPI_PARTIAL_F32, x, b, parts, splits=splits, err=err)
+    parts_k = torch.empty((splits, M_, N), device=dev)
+    M.mc_gemm_bf16(M_, N, K, bn, M.EPI_PARTIAL_F32, x.T.contiguous(), b, c=parts_k, splits=splits, err=err)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    assert ((parts.double().sum(0) - ref).abs().max() / ref.abs().max()).item() < 1e-5
+    assert torch.equal(parts, parts_k)
+
+
+def test_gemm_xn_rejects_bad_shapes(dev):
+    x = torch.zeros(64, 128, dtype=torch.bfloat16, device=dev)
+    b = torch.zeros(24, 64, dtype=torch.bfloat16, device=dev)
+    c = torch.zeros((128, 24), device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    with pytest.raises(M.McError):  # bn does not divide N
+        M.mc_gemm_bf16_xn(128, 24, 64, 16, M.EPI_ATOMIC_F32, x, b, c, err=err)
+    with pytest.raises(M.McError):  # an epilogue with a BF16 output
+        M.mc_gemm_bf16_xn(128, 16, 64, 16, 0, x, b[:16], c[:, :16], err=err)
