@@ -904,10 +904,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           break;
         }
         const float* bias = m == 0 ? nullptr : prm + (m == 1 ? L.off_b2 : L.off_b3);  // b1 is inside W1e
-        uint32_t mb[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
         for (int cg = 0; cg < 4; ++cg) {  // 4 groups of 4 x 16 columns
           uint32_t v[4][16];
           const int col0 = cg * 64;
+          uint32_t mb0 = 0u, mb1 = 0u;  // training: ReLU activity of columns col0 .. col0 + 63
 #pragma unroll
           for (int x = 0; x < 4; ++x) tmem_ld16_nw(trow + uint32_t(col0 + 16 * x), v[x]);
           tmem_wait_ld();
@@ -929,23 +929,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
               }
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                const int cc = col0 + 16 * x + 8 * hlf + 2 * e;
                 const float o0 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e]) + bv[2 * e], 0.0f);
                 const float o1 = fmaxf(__uint_as_float(v[x][8 * hlf + 2 * e + 1]) + bv[2 * e + 1], 0.0f);
                 const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
                 pw[e] = *reinterpret_cast<const uint32_t*>(&hh);
-                if (KEEP)
-                  mb[cc >> 5] |= (uint32_t(__bfloat162float(hh.x) > 0.0f) << (cc & 31)) |
-                                 (uint32_t(__bfloat162float(hh.y) > 0.0f) << ((cc + 1) & 31));
+                if (KEEP) {
+                  // bits c64, c64 + 1 of the group: the BF16 activation is
+                  // > 0, i.e. its magnitude bits are not all zero (after the
+                  // ReLU it is never negative); c64 is a constant once the
+                  // loops are unrolled, so the words stay in registers
+                  const int c64 = 16 * x + 8 * hlf + 2 * e;
+                  const uint32_t b2 = uint32_t((pw[e] & 0x7FFFu) != 0u) | (uint32_t((pw[e] & 0x7FFF0000u) != 0u) << 1);
+                  if (c64 < 32)
+                    mb0 |= b2 << c64;
+                  else
+                    mb1 |= b2 << (c64 - 32);
+                }
               }
               *reinterpret_cast<uint4*>(abuf + swz_off(r, (col0 + 16 * x + 8 * hlf) >> 3)) = pk;
             }
           }
-        }
-        if (KEEP) {
-          uint4* bp = reinterpret_cast<uint4*>(g.bits + (size_t(m) * g.n + ev) * 8);
-          bp[0] = make_uint4(mb[0], mb[1], mb[2], mb[3]);
-          bp[1] = make_uint4(mb[4], mb[5], mb[6], mb[7]);
+          if (KEEP) reinterpret_cast<uint2*>(g.bits + (size_t(m) * g.n + ev) * 8)[cg] = make_uint2(mb0, mb1);
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         fence_async_smem();
