@@ -1474,10 +1474,12 @@ __global__ void __launch_bounds__(kChainThreads, 1)
     for (int i = slot; i < my_tiles; i += 2) {
       const long long ev = (long long)tile_row(i) + r;
       if (__any_sync(0xffffffffu, failed != 0)) break;
-      // the activity bits of this thread's 128 columns of h3, h2, h1
-      uint4 mbv[3];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) mbv[m] = reinterpret_cast<const uint4*>(g.bits + (size_t(2 - m) * n + ev) * 8)[half];
+      // the activity bits of this thread's 128 columns of h3, h2, h1 (three
+      // named words, selected by the uniform m below: an array indexed at
+      // run time would live in local memory)
+      const uint4 mb_h3 = reinterpret_cast<const uint4*>(g.bits + (size_t(2) * n + ev) * 8)[half];
+      const uint4 mb_h2 = reinterpret_cast<const uint4*>(g.bits + (size_t(1) * n + ev) * 8)[half];
+      const uint4 mb_h1 = reinterpret_cast<const uint4*>(g.bits + ev * 8)[half];
       bool ok = true;
       for (int m = 0; m < 3 && ok; ++m, ++use_acc) {
         if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[slot], uint32_t(use_acc) & 1u))) {
@@ -1485,9 +1487,10 @@ __global__ void __launch_bounds__(kChainThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t mbw[4] = {mbv[m].x, mbv[m].y, mbv[m].z, mbv[m].w};
+        const uint4 mbm = m == 0 ? mb_h3 : (m == 1 ? mb_h2 : mb_h1);
         __nv_bfloat16* outT = m == 0 ? g.dA3T : (m == 1 ? g.dA2T : g.dA1T);
         for (int cg = 0; cg < 2; ++cg) {
+          const uint32_t wlo = cg == 0 ? mbm.x : mbm.z, whi = cg == 0 ? mbm.y : mbm.w;
           uint32_t v[4][16];
           const int col0 = half * 128 + cg * 64;
 #pragma unroll
@@ -1503,7 +1506,7 @@ __global__ void __launch_bounds__(kChainThreads, 1)
               for (int e = 0; e < 4; ++e) {
                 const int cc = col0 + 16 * x + 8 * hlf + 2 * e;
                 const int jl = cc - half * 128;
-                const uint32_t word = mbw[cg * 2 + (x >> 1)];  // jl >> 5 = 2 cg + x / 2
+                const uint32_t word = (x >> 1) == 0 ? wlo : whi;  // word jl >> 5 = 2 cg + x / 2
                 const float o0 = (word >> (jl & 31)) & 1u ? __uint_as_float(v[x][8 * hlf + 2 * e]) : 0.0f;
                 const float o1 = (word >> ((jl + 1) & 31)) & 1u ? __uint_as_float(v[x][8 * hlf + 2 * e + 1]) : 0.0f;
                 const __nv_bfloat162 hh = __floats2bfloat162_rn(o0, o1);
@@ -1533,7 +1536,9 @@ __global__ void __launch_bounds__(kChainThreads, 1)
         tmem_ld16_nw(trow, v);
         tmem_wait_ld();
         float* dPe = g.dP + ev * g.D;
-        for (int a = 0; a < L.na; ++a) dPe[L.a_idx[a]] += 2.0f * __uint_as_float(v[a < 16 ? a : 0]);
+#pragma unroll
+        for (int a = 0; a < kMaxA; ++a)
+          if (a < L.na) dPe[L.a_idx[a]] += 2.0f * __uint_as_float(v[a]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       mbar_arrive(&acc_empty[slot]);
