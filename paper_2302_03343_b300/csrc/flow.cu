@@ -2035,13 +2035,17 @@ int eval_points(mc_flow F, const mc_integrand* itg, mc_pdf pdf, const float* X, 
   mc::KernelArgs a;
   if (int rc = mc::fill_process_args(itg, pdf, &a)) return rc;
   const size_t smem = pdf_smem(itg, a);
-  const unsigned grid = std::min<unsigned>(mc::blocks_for(n, 128), 148u * 16u);
+  // one event per thread in blocks of 64: a training batch (65 536 points)
+  // is a single wave, and 1024 blocks spread over the SMs within one block
+  // of each other (512 blocks of 128 left some SMs a quarter more work)
+  constexpr int kPts = 64;
+  const unsigned grid = std::min<unsigned>(mc::blocks_for(n, kPts), 148u * 32u);
   switch (itg->proc) {
-    case MC_EE_MUMU: mc::points_kernel<mc::P_EE_MUMU><<<grid, 128, smem, st>>>(a, X, F->D, f, n); break;
-    case MC_PP_TTBAR: mc::points_kernel<mc::P_PP_TTBAR><<<grid, 128, smem, st>>>(a, X, F->D, f, n); break;
-    case MC_GG_TTBARG: mc::points_kernel<mc::P_GG_TTBARG><<<grid, 128, smem, st>>>(a, X, F->D, f, n); break;
-    case MC_GG_TTBARG_7D: mc::points_kernel<mc::P_GG_TTBARG_7D><<<grid, 128, smem, st>>>(a, X, F->D, f, n); break;
-    default: mc::points_kernel<mc::P_GAUSS><<<grid, 128, smem, st>>>(a, X, F->D, f, n);
+    case MC_EE_MUMU: mc::points_kernel<mc::P_EE_MUMU><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
+    case MC_PP_TTBAR: mc::points_kernel<mc::P_PP_TTBAR><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
+    case MC_GG_TTBARG: mc::points_kernel<mc::P_GG_TTBARG><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
+    case MC_GG_TTBARG_7D: mc::points_kernel<mc::P_GG_TTBARG_7D><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
+    default: mc::points_kernel<mc::P_GAUSS><<<grid, kPts, smem, st>>>(a, X, F->D, f, n);
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
