@@ -973,6 +973,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           for (int x = 0; x < kFusedLs / 16; ++x)
             tmem_ld16_nw(trow + uint32_t(jj * kFusedLs + 16 * x), reinterpret_cast<uint32_t*>(lg + 16 * x));
           tmem_wait_ld();
+          if (k + 1 < nsub && (jj == 1 || j + 1 >= L.nb)) {
+            // the sub-product's last logits are in registers: the accumulator
+            // is free, and the next sub-product's MMA runs beside this spline
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            arrive_a();
+          }
           const float4* b4 = reinterpret_cast<const float4*>(prm + L.off_b4 + j * kFusedLs);
 #pragma unroll
           for (int kk = 0; kk < kFusedLs / 4; ++kk) {
@@ -993,8 +999,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           Po[d] = spline_fwd(sp, kFusedK, Pe[d], &lc);
           ld += lc;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        if (k + 1 < nsub) arrive_a();  // the accumulator is free for the next sub-product
       }
       if (!ok) {
         failed = 1;
