@@ -24,12 +24,19 @@
 // fixed-order reduction, then Adam (thesis Sec. "Optimizers").
 //
 // Layouts (n = padded batch rows, H = 256): points P [n][D]; activations h
-// [n][H] BF16 row-major (A operands) plus their transposes [H][n] (operands of
-// the weight-gradient products, written by the producing epilogue); logits
+// [n][H] BF16 row-major (the fused forward stores them by TMA from its
+// operand buffer; the weight-gradient products read them as MN-major
+// operands), and in the layer-by-layer path also their transposes [H][n]
+// (ReLU masks of its products); ReLU activity bits [3][n][8] words; logits
 // transposed [row][n] FP32 with coordinate j's 2K+1 logits at rows
 // j * ls .. j * ls + 2K (ls = 2K+1 rounded up to 16, so that each coordinate
 // starts on a 16-byte boundary in the row-major gradient and on a 16-column
-// group of the tensor-memory accumulator).
+// group of the tensor-memory accumulator); logit and activation gradients
+// G [n][nout], G^T, dA^T in two buffer sets alternating by layer.
+//
+// A training step is captured once per mc_flow_train call as a CUDA graph
+// and replayed; the weight-gradient products of a layer run on a side stream
+// beside the next layer's spline backward and chain.
 #include <cuda_bf16.h>
 
 #include <algorithm>
