@@ -312,105 +312,6 @@ __global__ void mask_bits_kernel(const __nv_bfloat16* hT, size_t slot_stride, lo
   bits[(size_t(act) * n + ev) * 8 + w] = word;
 }
 
-// out[r] += sum_i XT[r][i] over a BF16 matrix XT [rows][n]: one block per
-// row, fixed-order reduction (bias gradients from transposed gradients).
-// Row sums of up to three transposed BF16 matrices in one launch: block b
-// sums row b of the first matrix, then of the second, then of the third
-// (rows[k] rows each), each exactly as rowsum_bf16_kernel would.
-struct RowSums3 {
-  const __nv_bfloat16* XT[3];
-  float* out[3];
-  int rows[3];
-};
-__global__ void __launch_bounds__(256) rowsum3_bf16_kernel(RowSums3 a, long long n) {
-  __shared__ float red[8];
-  int b = blockIdx.x, m = 0;
-  if (b >= a.rows[0]) {
-    b -= a.rows[0];
-    m = 1;
-    if (b >= a.rows[1]) {
-      b -= a.rows[1];
-      m = 2;
-    }
-  }
-  const __nv_bfloat16* X = m == 0 ? a.XT[0] : (m == 1 ? a.XT[1] : a.XT[2]);
-  float* out = m == 0 ? a.out[0] : (m == 1 ? a.out[1] : a.out[2]);
-  const uint4* row = reinterpret_cast<const uint4*>(X + size_t(b) * n);
-  float acc = 0.0f;
-  const long long nv = n / 8;
-  long long c = threadIdx.x;
-  for (; c + 7 * 256 < nv; c += 8 * 256) {
-    uint4 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = row[c + u * 256];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v[u]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 f = __bfloat1622float2(h[q]);
-        acc += f.x + f.y;
-      }
-    }
-  }
-  for (; c < nv; c += 256) {
-    const uint4 v = row[c];
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float2 f = __bfloat1622float2(h[q]);
-      acc += f.x + f.y;
-    }
-  }
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float v = 0.0f;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[w];
-    out[b] += v;
-  }
-}
-
-__global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* XT, long long n, float* out) {
-  __shared__ float red[8];
-  const uint4* row = reinterpret_cast<const uint4*>(XT + size_t(blockIdx.x) * n);
-  float acc = 0.0f;
-  const long long nv = n / 8;
-  long long c = threadIdx.x;
-  // eight independent 16-byte loads in flight per thread
-  for (; c + 7 * 256 < nv; c += 8 * 256) {
-    uint4 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = row[c + u * 256];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v[u]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 f = __bfloat1622float2(h[q]);
-        acc += f.x + f.y;
-      }
-    }
-  }
-  for (; c < nv; c += 256) {
-    const uint4 v = row[c];
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float2 f = __bfloat1622float2(h[q]);
-      acc += f.x + f.y;
-    }
-  }
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float v = 0.0f;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[w];
-    out[blockIdx.x] += v;
-  }
-}
 
 // Integrand at given points (no VEGAS map): f[i] = f(x_i) in FP32; a failed
 // event (non-finite, or unconverged phase space) is marked NaN.
@@ -1587,6 +1488,7 @@ struct mc_flow_s {
   float* dU = nullptr;          // [n][16] input gradient of the first layer
   __nv_bfloat16* U = nullptr;   // [n][64] first-layer inputs of the layer-by-layer path
   float* part = nullptr;  // split-K partial products of the weight gradients
+  float* bpart = nullptr;  // and the per-split row sums of their gradient operands (bias gradients)
   int max_splits = 0;
   double* sums = nullptr;
   double* h_sums = nullptr;  // pinned
@@ -1707,9 +1609,11 @@ int gemm_rs(mc_flow F, long long n, int N, int K, int epi, const __nv_bfloat16* 
 // Weight gradient gW^T [H x N] += X^T . YT^T over the n events (K = n): X the
 // activations, row-major [n][H] (x_rows) or transposed [H][n], YT the
 // gradients transposed [N][n]; split-K partial tiles, then a fixed-order sum
-// into the gradient.
+// into the gradient.  With gb, the bias gradient gb [N] += the row sums of
+// YT, formed by the product's CTAs from the YT tiles they stage anyway and
+// summed over the splits in the same fixed order.
 int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* X, bool x_rows, const __nv_bfloat16* YT,
-               float* gWt, cudaStream_t st, int* splits_out = nullptr) {
+               float* gWt, float* gb, cudaStream_t st, int* splits_out = nullptr) {
   FLOW_CUDA(cudaGetLastError());
   const int bn = pick_bn(N);
   const int tiles = (kH / 128) * (N / bn);
@@ -1727,6 +1631,7 @@ int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* X, bool x_row
   g.c_f32 = F->part;
   g.ldc = N;
   g.error = F->err;
+  g.rowsum_b = gb ? F->bpart : nullptr;
   if (x_rows)
     FLOW_CUDA(mc::tc_gemm_xn(g, X, kH, YT, int(n), splits, st));
   else
@@ -1735,6 +1640,7 @@ int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* X, bool x_row
     *splits_out = splits;  // the caller sums the partials itself
   else
     FLOW_CUDA(mc::tc_reduce_splits(F->part, splits, size_t(kH) * N, gWt, st));
+  if (gb) FLOW_CUDA(mc::tc_reduce_splits(F->bpart, splits, size_t(N), gb, st));
   return MC_OK;
 }
 
@@ -1959,14 +1865,13 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
       FLOW_CUDA(cudaEventRecord(F->ev_chain[l], st));
       const cudaStream_t ss = F->side;
       FLOW_CUDA(cudaStreamWaitEvent(ss, F->ev_chain[l], 0));
-      if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, GT, g + L.off_W4, ss)) return rc;
-      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, dA3T, g + L.off_W3, ss)) return rc;
-      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, dA2T, g + L.off_W2, ss)) return rc;
-      // the bias gradients b4, b3, b2: row sums of G^T, dA3^T, dA2^T in one launch
-      mc::RowSums3 rs{{GT, dA3T, dA2T}, {g + L.off_b4, g + L.off_b3, g + L.off_b2}, {L.nout_pad, kH, kH}};
-      mc::rowsum3_bf16_kernel<<<L.nout_pad + 2 * kH, 256, 0, ss>>>(rs, n);
+      // W4, W3, W2 and with them the bias gradients b4, b3, b2 (the row sums
+      // of G^T, dA3^T, dA2^T)
+      if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, GT, g + L.off_W4, g + L.off_b4, ss)) return rc;
+      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, dA3T, g + L.off_W3, g + L.off_b3, ss)) return rc;
+      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, dA2T, g + L.off_W2, g + L.off_b2, ss)) return rc;
       int splits = 0;
-      if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, false, UT_of(F, l), nullptr, ss, &splits)) return rc;
+      if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, false, UT_of(F, l), nullptr, nullptr, ss, &splits)) return rc;
       mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, ss>>>(F->part, splits, L, g);
       FLOW_CUDA(cudaGetLastError());
       FLOW_CUDA(cudaEventRecord(F->ev_side[l], ss));
@@ -1981,19 +1886,16 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
     mc::spline_inv_bwd_kernel<<<mc::blocks_for(n, 128), 128, 0, st>>>(P_of(F, l + 1), F->dP, D, L, LT_of(F, l), F->K,
                                                                        F->w, F->sums, F->G, F->GT, n, n_real);
     // last dense layer: W4, b4, and the gradient of h3 (through its ReLU)
-    if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, F->GT, g + L.off_W4, st)) return rc;
-    mc::rowsum_bf16_kernel<<<L.nout_pad, 256, 0, st>>>(F->GT, n, g + L.off_b4);
+    if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, F->GT, g + L.off_W4, g + L.off_b4, st)) return rc;
     if (int rc = gemm_rs(F, n, kH, L.nout_pad, mc::kEpiReluMaskBf16, F->G, L.W4t, nullptr, dA, F->dAT,
                          hT_of(F, l, 2), st))
       return rc;
     // third dense layer
-    if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, F->dAT, g + L.off_W3, st)) return rc;
-    mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b3);
+    if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, F->dAT, g + L.off_W3, g + L.off_b3, st)) return rc;
     if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA, L.W3t, nullptr, dA_b, F->dAT, hT_of(F, l, 1), st))
       return rc;
     // second dense layer
-    if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, F->dAT, g + L.off_W2, st)) return rc;
-    mc::rowsum_bf16_kernel<<<kH, 256, 0, st>>>(F->dAT, n, g + L.off_b2);
+    if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, F->dAT, g + L.off_W2, g + L.off_b2, st)) return rc;
     if (int rc = gemm_rs(F, n, kH, kH, mc::kEpiReluMaskBf16, dA_b, L.W2t, nullptr, dA, F->dAT, hT_of(F, l, 0), st))
       return rc;
     // first dense layer: dU = dA1 W1 (tensor cores, W1 zero-padded to 16
@@ -2003,7 +1905,7 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
       return rc;
     mc::add_input_grad_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->dP, D, L, F->dU, n);
     int splits = 0;
-    if (int rc = gemm_wgrad(F, n, mc::kUPad, F->dAT, false, UT_of(F, l), nullptr, st, &splits)) return rc;
+    if (int rc = gemm_wgrad(F, n, mc::kUPad, F->dAT, false, UT_of(F, l), nullptr, nullptr, st, &splits)) return rc;
     mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
     FLOW_CUDA(cudaGetLastError());
   }
@@ -2164,7 +2066,7 @@ int mc_flow_free(mc_flow F) {
                   (void*)F->LT, (void*)F->h, (void*)F->hT, (void*)F->G, (void*)F->GT, (void*)F->dA, (void*)F->dAT,
                   (void*)F->part, (void*)F->UT, (void*)F->MB, (void*)F->dU, (void*)F->U, (void*)F->Ps, (void*)F->lqs,
                   (void*)F->sums, (void*)F->parts, (void*)F->chunk_totals, (void*)F->total,
-                  (void*)F->err, (void*)F->d_step, (void*)F->d_adam, (void*)F->d_adam_pow})
+                  (void*)F->err, (void*)F->d_step, (void*)F->d_adam, (void*)F->d_adam_pow, (void*)F->bpart})
     cudaFree(p);
   for (cudaEvent_t e : F->ev_chain)
     if (e) cudaEventDestroy(e);
@@ -2248,6 +2150,7 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->dA, sizeof(__nv_bfloat16) * 2 * bp * kH);
   alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * 2 * 3 * bp * kH);
   alloc((void**)&F->part, sizeof(float) * size_t(F->max_splits) * kH * np);
+  alloc((void**)&F->bpart, sizeof(float) * size_t(F->max_splits) * np);
   alloc((void**)&F->UT, sizeof(__nv_bfloat16) * L * mc::kUPad * bp);
   alloc((void**)&F->MB, sizeof(uint32_t) * L * 3 * bp * 8);
   alloc((void**)&F->dU, sizeof(float) * bp * mc::kUPad);

@@ -62,11 +62,15 @@ __global__ void __launch_bounds__(128, 1)
   const int nkb = max(0, min(kblocks_total, kb0 + kb_per_split) - kb0);
   uint32_t ncols = 32;
   while (ncols < uint32_t(bn)) ncols <<= 1;
+  // warps 2 and 3 of the CTAs of m-tile 0 sum the rows of every B stage
+  // (kEpiPartialF32 with rowsum_b, B K-major): a stage returns to the
+  // producer after the MMA's commit and their 64 arrivals
+  const bool sum_b = !B_MN && g.rowsum_b != nullptr && g.epilogue == kEpiPartialF32 && tile_m == 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+      mbar_init(&empty_bar[s], sum_b ? 1 + 64 : 1);
     }
     mbar_init(&done_bar, 1);
     failed = 0;
@@ -138,6 +142,52 @@ __global__ void __launch_bounds__(128, 1)
     }
     mma_commit(&done_bar);  // completes once every MMA issued above has
   }
+  else if (sum_b && warp >= 2 && nkb > 0) {
+    // row r = t + 64 j of this n-tile's B: its 64 k values of a stage are
+    // eight 16-byte units in the 128-byte swizzled row (unit u at
+    // (u ^ (r % 8)) x 16); each unit's eight values are added as a tree
+    // into the unit's own accumulator, stage after stage, and the eight
+    // accumulators of a row in unit order at the end (a fixed order with
+    // short dependency chains)
+    const int t = threadIdx.x - 64;
+    float acc[4][8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[j][u] = 0.0f;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kStages;
+      if (!mbar_wait(&full_bar[s], uint32_t(i / kStages) & 1u)) {
+        failed = 1;
+        atomicExch(g.error, 5);
+        break;
+      }
+      const unsigned char* bst = smem + size_t(s) * stage_bytes + a_bytes;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = t + 64 * j;
+        if (r < bn) {
+          const unsigned char* row = bst + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const uint4 v = *reinterpret_cast<const uint4*>(row + ((u ^ (r & 7)) << 4));
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+            const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+            const float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+            acc[j][u] += ((f0.x + f0.y) + (f1.x + f1.y)) + ((f2.x + f2.y) + (f3.x + f3.y));
+          }
+        }
+      }
+      mbar_arrive(&empty_bar[s]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = t + 64 * j;
+      if (r < bn)
+        g.rowsum_b[size_t(blockIdx.z) * g.N + size_t(tile_n) * bn + r] =
+            ((acc[j][0] + acc[j][1]) + (acc[j][2] + acc[j][3])) + ((acc[j][4] + acc[j][5]) + (acc[j][6] + acc[j][7]));
+    }
+  }
   if (warp < 2) __syncwarp();
   if (nkb > 0) {
     // every thread waits for the accumulator (or the failure release)
@@ -204,6 +254,9 @@ __global__ void __launch_bounds__(128, 1)
     float4* out = reinterpret_cast<float4*>(g.c_f32 + size_t(blockIdx.z) * g.M * g.ldc + size_t(row) * g.ldc +
                                             tile_n * bn);
     for (int j = 0; j < bn / 4; ++j) out[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (sum_b)
+      for (int r = threadIdx.x; r < bn; r += blockDim.x)
+        g.rowsum_b[size_t(blockIdx.z) * g.N + size_t(tile_n) * bn + r] = 0.0f;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -564,6 +617,8 @@ size_t tc_gemm_smem(int bn) { return size_t(kStages) * (kBM * kBK * 2 + size_t(b
 cudaError_t tc_gemm(const TcGemmArgs& g_in, const __nv_bfloat16* a, int lda, const __nv_bfloat16* b, int ldb,
                     int splits, cudaStream_t st) {
   TcGemmArgs g = g_in;
+  if (g.rowsum_b && (g.epilogue != kEpiPartialF32 || (reinterpret_cast<uintptr_t>(g.rowsum_b) & 15)))
+    return cudaErrorInvalidValue;
   if (g.M % kBM || g.K % kBK || g.bn % 16 || g.bn < 16 || g.bn > 256 || g.N % g.bn || splits < 1 || !g.error ||
       (reinterpret_cast<uintptr_t>(a) & 15) || (reinterpret_cast<uintptr_t>(b) & 15) || (lda % 8) || (ldb % 8))
     return cudaErrorInvalidValue;
@@ -582,6 +637,7 @@ cudaError_t tc_gemm(const TcGemmArgs& g_in, const __nv_bfloat16* a, int lda, con
 cudaError_t tc_gemm_tn(const TcGemmArgs& g_in, const __nv_bfloat16* x, int ldx, const __nv_bfloat16* y, int ldy,
                        int splits, cudaStream_t st) {
   TcGemmArgs g = g_in;
+  if (g.rowsum_b) return cudaErrorInvalidValue;  // row sums of B need a K-major B
   if (g.M % kBM || g.K % kBK || g.bn % 64 || g.bn < 64 || g.bn > 256 || g.N % g.bn || splits < 1 || !g.error ||
       !aligned16(x) || !aligned16(y) || (ldx % 8) || (ldy % 8) || ldx < g.M || ldy < g.N ||
       (g.epilogue != kEpiBiasF32 && g.epilogue != kEpiAtomicF32 && g.epilogue != kEpiPartialF32) || !g.c_f32)
@@ -601,6 +657,8 @@ cudaError_t tc_gemm_tn(const TcGemmArgs& g_in, const __nv_bfloat16* x, int ldx, 
 cudaError_t tc_gemm_xn(const TcGemmArgs& g_in, const __nv_bfloat16* x, int ldx, const __nv_bfloat16* b, int ldb,
                        int splits, cudaStream_t st) {
   TcGemmArgs g = g_in;
+  if (g.rowsum_b && (g.epilogue != kEpiPartialF32 || (reinterpret_cast<uintptr_t>(g.rowsum_b) & 15)))
+    return cudaErrorInvalidValue;
   if (g.M % kBM || g.K % kBK || g.bn % 16 || g.bn < 16 || g.bn > 256 || g.N % g.bn || splits < 1 || !g.error ||
       !aligned16(x) || !aligned16(b) || (ldx % 8) || (ldb % 8) || ldx < g.M || ldb < g.K ||
       (g.epilogue != kEpiBiasF32 && g.epilogue != kEpiAtomicF32 && g.epilogue != kEpiPartialF32) || !g.c_f32)

@@ -32,6 +32,11 @@ struct TcGemmArgs {
   __nv_bfloat16* c_t_bf16;
   float* c_t_f32;
   int ldt;
+  // optional with kEpiPartialF32 and a K-major B (tc_gemm, tc_gemm_xn): per
+  // split the row sums of B over the split's K range, rowsum_b[split][N]
+  // (the bias gradient of a dense layer beside its weight gradient), summed
+  // by tc_reduce_splits like the partial tiles
+  float* rowsum_b;
 };
 
 size_t tc_gemm_smem(int bn);
