@@ -87,9 +87,11 @@ def cosine(a, b):
     return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
 
 
-@pytest.mark.parametrize("D,n", [(7, 2000), (4, 333)])
+@pytest.mark.parametrize("D,n", [(7, 2000), (4, 333), (7, 65536)])
 def test_loss_and_gradients_match_oracle(gpu, D, n):
-    f, arrays = make_flow(D, seed=21, last_scale=0.5, max_batch=2048)
+    # 65 536 events: the training batch, where the weight- and bias-gradient
+    # products split K (the events) 37 ways
+    f, arrays = make_flow(D, seed=21, last_scale=0.5, max_batch=max(n, 2048))
     rng = np.random.default_rng(8)
     x = rng.random((n, D)).astype(np.float32)
     w = rng.exponential(size=n).astype(np.float32)
