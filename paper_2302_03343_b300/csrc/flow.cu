@@ -36,7 +36,8 @@
 //
 // A training step is captured once per mc_flow_train call as a CUDA graph
 // and replayed; the weight-gradient products of a layer run on a side stream
-// beside the next layer's spline backward and chain.
+// beside the next layer's spline backward and chain, back to back (each into
+// its own split-K partial region), and their fixed-order sums in one launch.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -1489,6 +1490,7 @@ struct mc_flow_s {
   __nv_bfloat16* U = nullptr;   // [n][64] first-layer inputs of the layer-by-layer path
   float* part = nullptr;  // split-K partial products of the weight gradients
   float* bpart = nullptr;  // and the per-split row sums of their gradient operands (bias gradients)
+  size_t part_region = 0, bpart_region = 0;  // floats per partial / bias-partial region
   int max_splits = 0;
   double* sums = nullptr;
   double* h_sums = nullptr;  // pinned
@@ -1606,14 +1608,14 @@ int gemm_rs(mc_flow F, long long n, int N, int K, int epi, const __nv_bfloat16* 
   return MC_OK;
 }
 
-// Weight gradient gW^T [H x N] += X^T . YT^T over the n events (K = n): X the
-// activations, row-major [n][H] (x_rows) or transposed [H][n], YT the
-// gradients transposed [N][n]; split-K partial tiles, then a fixed-order sum
-// into the gradient.  With gb, the bias gradient gb [N] += the row sums of
-// YT, formed by the product's CTAs from the YT tiles they stage anyway and
-// summed over the splits in the same fixed order.
-int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* X, bool x_rows, const __nv_bfloat16* YT,
-               float* gWt, float* gb, cudaStream_t st, int* splits_out = nullptr) {
+// Split-K partial tiles of the weight gradient X^T . YT^T over the n events
+// (K = n): X the activations, row-major [n][H] (x_rows) or transposed
+// [H][n], YT the gradients transposed [N][n]; the partials go to part
+// [splits][H][N] and, with bpart, the row sums of YT (the bias gradient's
+// partials, formed by the product's CTAs from the YT tiles they stage
+// anyway) to bpart [splits][N].  The split count is returned in *splits.
+int wgrad_partials(mc_flow F, long long n, int N, const __nv_bfloat16* X, bool x_rows, const __nv_bfloat16* YT,
+                   float* part, float* bpart, cudaStream_t st, int* splits_out) {
   FLOW_CUDA(cudaGetLastError());
   const int bn = pick_bn(N);
   const int tiles = (kH / 128) * (N / bn);
@@ -1628,16 +1630,28 @@ int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* X, bool x_row
   g.K = int(n);
   g.bn = bn;
   g.epilogue = mc::kEpiPartialF32;
-  g.c_f32 = F->part;
+  g.c_f32 = part;
   g.ldc = N;
   g.error = F->err;
-  g.rowsum_b = gb ? F->bpart : nullptr;
+  g.rowsum_b = bpart;
   if (x_rows)
     FLOW_CUDA(mc::tc_gemm_xn(g, X, kH, YT, int(n), splits, st));
   else
     FLOW_CUDA(mc::tc_gemm(g, X, int(n), YT, int(n), splits, st));
+  *splits_out = splits;
+  return MC_OK;
+}
+
+// Weight gradient gW^T [H x N] += X^T . YT^T (wgrad_partials into the shared
+// partial buffer, then a fixed-order sum over the splits); with gb, the bias
+// gradient gb [N] += the row sums of YT, summed over the splits in the same
+// order.  With splits_out the caller sums the weight partials itself.
+int gemm_wgrad(mc_flow F, long long n, int N, const __nv_bfloat16* X, bool x_rows, const __nv_bfloat16* YT,
+               float* gWt, float* gb, cudaStream_t st, int* splits_out = nullptr) {
+  int splits = 0;
+  if (int rc = wgrad_partials(F, n, N, X, x_rows, YT, F->part, gb ? F->bpart : nullptr, st, &splits)) return rc;
   if (splits_out)
-    *splits_out = splits;  // the caller sums the partials itself
+    *splits_out = splits;
   else
     FLOW_CUDA(mc::tc_reduce_splits(F->part, splits, size_t(kH) * N, gWt, st));
   if (gb) FLOW_CUDA(mc::tc_reduce_splits(F->bpart, splits, size_t(N), gb, st));
@@ -1866,13 +1880,26 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
       const cudaStream_t ss = F->side;
       FLOW_CUDA(cudaStreamWaitEvent(ss, F->ev_chain[l], 0));
       // W4, W3, W2 and with them the bias gradients b4, b3, b2 (the row sums
-      // of G^T, dA3^T, dA2^T)
-      if (int rc = gemm_wgrad(F, n, L.nout_pad, h_of(F, l, 2), true, GT, g + L.off_W4, g + L.off_b4, ss)) return rc;
-      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 1), true, dA3T, g + L.off_W3, g + L.off_b3, ss)) return rc;
-      if (int rc = gemm_wgrad(F, n, kH, h_of(F, l, 0), true, dA2T, g + L.off_W2, g + L.off_b2, ss)) return rc;
-      int splits = 0;
-      if (int rc = gemm_wgrad(F, n, mc::kUPad, dA1T, false, UT_of(F, l), nullptr, nullptr, ss, &splits)) return rc;
-      mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, ss>>>(F->part, splits, L, g);
+      // of G^T, dA3^T, dA2^T), and W1, b1: four products back to back, each
+      // into its own partial region, then the six sums of W4..b2 in one
+      // launch (each summed as tc_reduce_splits sums it alone)
+      float* pw[4];
+      float* pb[3];
+      for (int k = 0; k < 4; ++k) pw[k] = F->part + size_t(k) * F->part_region;
+      for (int k = 0; k < 3; ++k) pb[k] = F->bpart + size_t(k) * F->bpart_region;
+      int s4 = 0, s3 = 0, s2 = 0, s1 = 0;
+      if (int rc = wgrad_partials(F, n, L.nout_pad, h_of(F, l, 2), true, GT, pw[0], pb[0], ss, &s4)) return rc;
+      if (int rc = wgrad_partials(F, n, kH, h_of(F, l, 1), true, dA3T, pw[1], pb[1], ss, &s3)) return rc;
+      if (int rc = wgrad_partials(F, n, kH, h_of(F, l, 0), true, dA2T, pw[2], pb[2], ss, &s2)) return rc;
+      if (int rc = wgrad_partials(F, n, mc::kUPad, dA1T, false, UT_of(F, l), pw[3], nullptr, ss, &s1)) return rc;
+      const mc::TcRedSeg segs[6] = {{pw[0], s4, size_t(kH) * L.nout_pad, g + L.off_W4},
+                                    {pb[0], s4, size_t(L.nout_pad), g + L.off_b4},
+                                    {pw[1], s3, size_t(kH) * kH, g + L.off_W3},
+                                    {pb[1], s3, size_t(kH), g + L.off_b3},
+                                    {pw[2], s2, size_t(kH) * kH, g + L.off_W2},
+                                    {pb[2], s2, size_t(kH), g + L.off_b2}};
+      FLOW_CUDA(mc::tc_reduce_splits_multi(segs, 6, ss));
+      mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, ss>>>(pw[3], s1, L, g);
       FLOW_CUDA(cudaGetLastError());
       FLOW_CUDA(cudaEventRecord(F->ev_side[l], ss));
       side_last = l;
@@ -2149,8 +2176,12 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->GT, sizeof(__nv_bfloat16) * 2 * bp * np);
   alloc((void**)&F->dA, sizeof(__nv_bfloat16) * 2 * bp * kH);
   alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * 2 * 3 * bp * kH);
-  alloc((void**)&F->part, sizeof(float) * size_t(F->max_splits) * kH * np);
-  alloc((void**)&F->bpart, sizeof(float) * size_t(F->max_splits) * np);
+  // four partial regions (the side stream's W4, W3, W2, W1 products of a
+  // layer) and three bias-partial regions
+  F->part_region = size_t(F->max_splits) * kH * np;
+  F->bpart_region = size_t(F->max_splits) * np;
+  alloc((void**)&F->part, sizeof(float) * 4 * F->part_region);
+  alloc((void**)&F->bpart, sizeof(float) * 3 * F->bpart_region);
   alloc((void**)&F->UT, sizeof(__nv_bfloat16) * L * mc::kUPad * bp);
   alloc((void**)&F->MB, sizeof(uint32_t) * L * 3 * bp * 8);
   alloc((void**)&F->dU, sizeof(float) * bp * mc::kUPad);

@@ -512,13 +512,14 @@ __global__ void __launch_bounds__(kRsThreads, 1)
 // (so a thread has a short chain of independent loads in flight), and the
 // range sums are added in range order.  Blocks of kRedGroups x 32 threads
 // cover 32 groups of four consecutive elements (n % 4 == 0, 16-byte
-// aligned arrays); a thread that holds no full group reads nothing.
+// aligned arrays); a thread that holds no full group reads nothing.  `blk`
+// is the block's index within its array.
 constexpr int kRedGroups = 8;
-__global__ void __launch_bounds__(kRedGroups * 32) reduce_splits_kernel(const float* part, int splits, size_t n,
-                                                                      float* out) {
+__device__ __forceinline__ void reduce_splits_block(const float* part, int splits, size_t n, float* out,
+                                                    unsigned blk) {
   __shared__ float4 red[kRedGroups][32];
   const int c = threadIdx.x & 31, gr = threadIdx.x >> 5;
-  const size_t q = size_t(blockIdx.x) * 32 + c;  // float4 index
+  const size_t q = size_t(blk) * 32 + c;  // float4 index
   const bool live = 4 * q + 4 <= n;
   const int per = (splits + kRedGroups - 1) / kRedGroups;
   const int s0 = gr * per, s1 = min(splits, s0 + per);
@@ -561,6 +562,25 @@ __global__ void __launch_bounds__(kRedGroups * 32) reduce_splits_kernel(const fl
     }
     reinterpret_cast<float4*>(out)[q] = o;
   }
+}
+
+__global__ void __launch_bounds__(kRedGroups * 32) reduce_splits_kernel(const float* part, int splits, size_t n,
+                                                                      float* out) {
+  reduce_splits_block(part, splits, n, out, blockIdx.x);
+}
+
+// Several reductions in one launch: segment k owns blocks [first[k],
+// first[k + 1]) and sums exactly as reduce_splits_kernel would alone.
+struct RedSegs {
+  TcRedSeg seg[kMaxRedSegs];
+  unsigned first[kMaxRedSegs + 1];
+  int nseg;
+};
+__global__ void __launch_bounds__(kRedGroups * 32) reduce_splits_multi_kernel(const RedSegs r) {
+  int k = 0;
+  while (k + 1 < r.nseg && blockIdx.x >= r.first[k + 1]) ++k;
+  const TcRedSeg& sg = r.seg[k];
+  reduce_splits_block(sg.part, sg.splits, sg.n, sg.out, blockIdx.x - r.first[k]);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -713,6 +733,27 @@ cudaError_t tc_reduce_splits(const float* part, int splits, size_t n, float* out
     return cudaErrorInvalidValue;
   const unsigned grid = unsigned((n / 4 + 31) / 32);
   reduce_splits_kernel<<<grid, kRedGroups * 32, 0, st>>>(part, splits, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_reduce_splits_multi(const TcRedSeg* segs, int nseg, cudaStream_t st) {
+  if (nseg < 1 || nseg > kMaxRedSegs || !segs) return cudaErrorInvalidValue;
+  RedSegs r;
+  std::memset(&r, 0, sizeof(r));
+  r.nseg = nseg;
+  unsigned blocks = 0;
+  for (int k = 0; k < nseg; ++k) {
+    const TcRedSeg& sg = segs[k];
+    if (sg.splits < 1 || !sg.part || !sg.out || sg.n % 4 != 0 ||
+        (reinterpret_cast<uintptr_t>(sg.part) | reinterpret_cast<uintptr_t>(sg.out)) % 16 != 0)
+      return cudaErrorInvalidValue;
+    r.seg[k] = sg;
+    r.first[k] = blocks;
+    blocks += unsigned((sg.n / 4 + 31) / 32);
+  }
+  r.first[nseg] = blocks;
+  if (blocks == 0) return cudaSuccess;
+  reduce_splits_multi_kernel<<<blocks, kRedGroups * 32, 0, st>>>(r);
   return cudaGetLastError();
 }
 

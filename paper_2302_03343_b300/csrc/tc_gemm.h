@@ -75,4 +75,15 @@ cudaError_t tc_gemm_rs(const TcGemmArgs& g, const __nv_bfloat16* a, int lda, con
 // out[i] += sum over s < splits of part[s * n + i] (fixed order), n floats.
 cudaError_t tc_reduce_splits(const float* part, int splits, size_t n, float* out, cudaStream_t st);
 
+// Up to kMaxRedSegs such sums in one launch, each segment summed exactly as
+// tc_reduce_splits sums it alone (the segments' outputs must not overlap).
+struct TcRedSeg {
+  const float* part;
+  int splits;
+  size_t n;
+  float* out;
+};
+constexpr int kMaxRedSegs = 8;
+cudaError_t tc_reduce_splits_multi(const TcRedSeg* segs, int nseg, cudaStream_t st);
+
 }  // namespace mc
