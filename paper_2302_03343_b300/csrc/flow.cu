@@ -225,7 +225,9 @@ constexpr int kFusedLs = 80;  // their logit stride: 2K+1 rounded up to 16 colum
 // coordinate j = blockIdx.y): the coordinates' independent work runs on
 // separate threads, and with the bin count fixed at compile time every value
 // stays in registers (no staging).  Writes exactly what spline_inv_bwd_kernel
-// writes (the same arithmetic and roundings per coordinate).
+// writes (the same arithmetic and roundings per coordinate).  The padded
+// rows past the last coordinate are cleared by the threads of every
+// coordinate in turn.
 __global__ void __launch_bounds__(128, 4) spline_bwd_k32_kernel(const float* Pin, float* dP, int D, const LayerDev L,
                                                              const float* LT, const float* w, const double* wsum,
                                                              __nv_bfloat16* G, __nv_bfloat16* GT, long long n,
@@ -266,13 +268,14 @@ __global__ void __launch_bounds__(128, 4) spline_bwd_k32_kernel(const float* Pin
     }
     gr[c8] = pk;
   }
-  if (j == 0) {  // the rows past the last coordinate (see spline_inv_bwd_kernel)
-    const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
-    for (int c = L.nb * L.ls; c < L.nout_pad; ++c) {
-      GT[size_t(c) * ldn + i] = z;
-      G[size_t(i) * L.nout_pad + c] = z;
-    }
-  }
+  // the rows past the last coordinate (see spline_inv_bwd_kernel), every
+  // nb-th one by this coordinate's threads (nb ls is a multiple of 16, so
+  // the row-major zeros are whole 16-byte units)
+  const int c0 = L.nb * L.ls;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+  for (int c = c0 + j; c < L.nout_pad; c += L.nb) GT[size_t(c) * ldn + i] = z;
+  uint4* gz = reinterpret_cast<uint4*>(G + size_t(i) * L.nout_pad + c0);
+  for (int u = j; u < (L.nout_pad - c0) / 8; u += L.nb) gz[u] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // First dense layer backward, input side: dL/dx_A += 2 dU with dU = dA1 W1
