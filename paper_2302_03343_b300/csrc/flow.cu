@@ -288,18 +288,36 @@ __global__ void add_input_grad_kernel(float* dP, int D, const LayerDev L, const 
 
 // First dense layer backward, weight side: the split-K partial products
 // part[s][j][c] of dA1^T U (c < na: W1 column, c = na: the bias row of ones)
-// summed in a fixed order into the gradients of W1 [H x na] and b1.
-__global__ void w1_grad_kernel(const float* part, int splits, const LayerDev L, float* grads) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= kH * kUPad) return;
+// summed in a fixed order into the gradients of W1 [H x na] and b1: blocks
+// of 8 x 32 threads cover 32 elements; each group of 32 sums a contiguous
+// range of the splits in order, and the eight range sums are added in range
+// order.
+constexpr int kW1Groups = 8;
+__global__ void __launch_bounds__(kW1Groups * 32) w1_grad_kernel(const float* part, int splits, const LayerDev L,
+                                                                 float* grads) {
+  __shared__ float red[kW1Groups][32];
+  const int c32 = threadIdx.x & 31, gr = threadIdx.x >> 5;
+  const int idx = blockIdx.x * 32 + c32;
+  const bool live = idx < kH * kUPad;
+  const int per = (splits + kW1Groups - 1) / kW1Groups;
+  const int s0 = gr * per, s1 = min(splits, s0 + per);
+  float acc = 0.0f;
+  if (live) {
+#pragma unroll 4
+    for (int s = s0; s < s1; ++s) acc += part[size_t(s) * kH * kUPad + idx];
+  }
+  red[gr][c32] = acc;
+  __syncthreads();
+  if (gr != 0 || !live) return;
   const int j = idx / kUPad, c = idx % kUPad;
   if (c > L.na) return;
-  float acc = 0.0f;
-  for (int s = 0; s < splits; ++s) acc += part[size_t(s) * kH * kUPad + idx];
+  float t = 0.0f;
+#pragma unroll
+  for (int g = 0; g < kW1Groups; ++g) t += red[g][c32];
   if (c == L.na)
-    grads[L.off_b1 + j] += acc;
+    grads[L.off_b1 + j] += t;
   else
-    grads[L.off_W1 + size_t(j) * L.na + c] += acc;
+    grads[L.off_W1 + size_t(j) * L.na + c] += t;
 }
 
 // ReLU activity bits of the three hidden activations of a layer from their
@@ -1902,7 +1920,7 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
                                     {pw[2], s2, size_t(kH) * kH, g + L.off_W2},
                                     {pb[2], s2, size_t(kH), g + L.off_b2}};
       FLOW_CUDA(mc::tc_reduce_splits_multi(segs, 6, ss));
-      mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, ss>>>(pw[3], s1, L, g);
+      mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 32), mc::kW1Groups * 32, 0, ss>>>(pw[3], s1, L, g);
       FLOW_CUDA(cudaGetLastError());
       FLOW_CUDA(cudaEventRecord(F->ev_side[l], ss));
       side_last = l;
@@ -1936,7 +1954,7 @@ int backward_pass(mc_flow F, long long n, long long n_real, cudaStream_t st) {
     mc::add_input_grad_kernel<<<mc::blocks_for(n, 256), 256, 0, st>>>(F->dP, D, L, F->dU, n);
     int splits = 0;
     if (int rc = gemm_wgrad(F, n, mc::kUPad, F->dAT, false, UT_of(F, l), nullptr, nullptr, st, &splits)) return rc;
-    mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 256), 256, 0, st>>>(F->part, splits, L, g);
+    mc::w1_grad_kernel<<<mc::blocks_for(kH * mc::kUPad, 32), mc::kW1Groups * 32, 0, st>>>(F->part, splits, L, g);
     FLOW_CUDA(cudaGetLastError());
   }
   return join_side();
