@@ -486,53 +486,91 @@ __global__ void adam_prep_kernel(long long* step, double* pw, float* c, double b
   c[0] = float(1.0 / (1.0 - p1));
   c[1] = float(1.0 / (1.0 - p2));
 }
-__global__ void adam_kernel(float* params, const float* grads, float* m, float* v, size_t n, const LayerDev* layers,
-                            int nl, AdamArgs A) {
-  const size_t idx = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= n) return;
+// One Adam update (thesis Sec. "Optimizers": beta1, beta2, eps; c1, c2 the
+// bias corrections of the step) of parameter p with gradient g and moments
+// m, v; returns the new parameter.
+__device__ __forceinline__ float adam_update(float& p, float& m, float& v, float g, const AdamArgs& A, float c1,
+                                             float c2) {
+  m = A.b1 * m + (1.0f - A.b1) * g;
+  v = A.b2 * v + (1.0f - A.b2) * g * g;
+  p = p - A.lr * (m * c1) / (sqrtf(v * c2) + A.eps);
+  return p;
+}
+
+// Adam on the dense matrices W2, W3, W4 of layer blockIdx.y / 3 (their
+// gradients kept transposed, gW^T [in x out]), one 32 x 32 tile per block
+// of 32 x 8 threads: the gradient tile and the transposed BF16 copy go
+// through shared memory, so that every array is read and written along its
+// own rows.  Also refreshes the row-major BF16 copy.
+__global__ void __launch_bounds__(256) adam_mat_kernel(float* params, const float* grads, float* m, float* v,
+                                                       const LayerDev* layers, AdamArgs A) {
+  __shared__ float tile[32][33];
+  const LayerDev& L = layers[blockIdx.y / 3];
+  const int which = blockIdx.y % 3;
+  const size_t off = which == 0 ? L.off_W2 : (which == 1 ? L.off_W3 : L.off_W4);
+  const int rows = which == 2 ? L.nout_pad : kH, cols = kH;  // W [rows x cols]
+  __nv_bfloat16* h = which == 0 ? L.W2h : (which == 1 ? L.W3h : L.W4h);
+  __nv_bfloat16* ht = which == 0 ? L.W2t : (which == 1 ? L.W3t : L.W4t);
+  const int tiles_c = cols / 32;
+  if (int(blockIdx.x) >= (rows / 32) * tiles_c) return;  // a smaller matrix than the grid's
+  const int r0 = int(blockIdx.x) / tiles_c * 32, c0 = int(blockIdx.x) % tiles_c * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
   const float c1 = A.c[0], c2 = A.c[1];
-  size_t gidx = idx;
-  // the BF16 copies the tensor cores read: W2, W3, W4 and their transposes, W1^T
-  __nv_bfloat16 *dst = nullptr, *dst_t = nullptr;
-  size_t di = 0, dti = 0;
-  for (int l = 0; l < nl; ++l) {
-    const LayerDev& L = layers[l];
-    auto tr = [&](size_t off, int rows, int cols, __nv_bfloat16* h, __nv_bfloat16* ht) {
-      // W [rows x cols], gradient stored [cols x rows]
-      if (idx >= off && idx < off + size_t(rows) * cols) {
-        const size_t e = idx - off, r = e / cols, c = e % cols;
-        gidx = off + c * rows + r;
-        dst = h;
-        di = e;
-        dst_t = ht;
-        dti = c * rows + r;
-      }
-    };
-    tr(L.off_W2, kH, kH, L.W2h, L.W2t);
-    tr(L.off_W3, kH, kH, L.W3h, L.W3t);
-    tr(L.off_W4, L.nout_pad, kH, L.W4h, L.W4t);
-    if (idx >= L.off_W1 && idx < L.off_W1 + size_t(kH) * L.na) {
-      const size_t e = idx - L.off_W1;
-      dst_t = L.W1t;
-      dti = (e % L.na) * kH + e / L.na;
-      dst = L.W1e;
-      di = (e / L.na) * kUK + e % L.na;
-    }
-    if (idx >= L.off_b1 && idx < L.off_b1 + kH) {
-      dst = L.W1e;
-      di = (idx - L.off_b1) * kUK + L.na;
-    }
+  // tile[c][r] = gradient of W[r0 + r][c0 + c], stored at (c0 + c) rows + r0 + r
+  for (int c = ty; c < 32; c += 8) tile[c][tx] = grads[off + size_t(c0 + c) * rows + r0 + tx];
+  __syncthreads();
+  float pv[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = ty + 8 * q;
+    const size_t e = size_t(r0 + r) * cols + c0 + tx, idx = off + e;
+    float p = params[idx], mi = m[idx], vi = v[idx];
+    pv[q] = adam_update(p, mi, vi, tile[tx][r], A, c1, c2);
+    m[idx] = mi;
+    v[idx] = vi;
+    params[idx] = p;
+    h[e] = __float2bfloat16_rn(p);
   }
-  const float g = grads[gidx];
-  const float mi = A.b1 * m[idx] + (1.0f - A.b1) * g;
-  const float vi = A.b2 * v[idx] + (1.0f - A.b2) * g * g;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) tile[tx][ty + 8 * q] = pv[q];  // tile[c][r] = new W[r0 + r][c0 + c]
+  __syncthreads();
+  for (int c = ty; c < 32; c += 8) ht[size_t(c0 + c) * rows + r0 + tx] = __float2bfloat16_rn(tile[c][tx]);
+}
+
+// Adam on the rest of layer blockIdx.y: W1 and b1 (they refresh W1e and
+// W1^T), b2, b3 and b4, taken as one index range of H na + 3 H + nout_pad
+// elements.
+__global__ void __launch_bounds__(256) adam_vec_kernel(float* params, const float* grads, float* m, float* v,
+                                                       const LayerDev* layers, AdamArgs A) {
+  const LayerDev& L = layers[blockIdx.y];
+  const size_t sw = size_t(kH) * L.na, s0 = sw + kH;
+  const size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  size_t idx;
+  if (t < sw)
+    idx = L.off_W1 + t;
+  else if (t < s0)
+    idx = L.off_b1 + (t - sw);
+  else if (t < s0 + kH)
+    idx = L.off_b2 + (t - s0);
+  else if (t < s0 + 2 * kH)
+    idx = L.off_b3 + (t - s0 - kH);
+  else if (t < s0 + 2 * kH + size_t(L.nout_pad))
+    idx = L.off_b4 + (t - s0 - 2 * kH);
+  else
+    return;
+  float p = params[idx], mi = m[idx], vi = v[idx];
+  adam_update(p, mi, vi, grads[idx], A, A.c[0], A.c[1]);
   m[idx] = mi;
   v[idx] = vi;
-  const float p = params[idx] - A.lr * (mi * c1) / (sqrtf(vi * c2) + A.eps);
   params[idx] = p;
-  const __nv_bfloat16 h = __float2bfloat16_rn(p);
-  if (dst) dst[di] = h;
-  if (dst_t) dst_t[dti] = h;
+  const __nv_bfloat16 hb = __float2bfloat16_rn(p);
+  if (t < sw) {  // W1 [H x na]: W1e [H][64] and W1^T [16][H]
+    L.W1e[(t / L.na) * kUK + t % L.na] = hb;
+    L.W1t[(t % L.na) * kH + t / L.na] = hb;
+  } else if (t < s0) {  // b1: column na of W1e
+    L.W1e[(t - sw) * kUK + L.na] = hb;
+  }
 }
 
 // W1e [H][64] = (W1 | b1 | 0) in BF16 (W1 [H x na], b1 [H], FP32).
@@ -2042,8 +2080,16 @@ int adam_launch(mc_flow F, double lr, cudaStream_t st) {
   const double b1 = 0.9, b2 = 0.999;
   mc::adam_prep_kernel<<<1, 1, 0, st>>>(F->d_step, F->d_adam_pow, F->d_adam, b1, b2);
   mc::AdamArgs A{float(lr), float(b1), float(b2), 1e-8f, F->d_adam};
-  mc::adam_kernel<<<mc::blocks_for(F->nparam, 256), 256, 0, st>>>(F->d_params, F->d_grads, F->d_m, F->d_v, F->nparam,
-                                                                   F->d_layers, F->L, A);  // refreshes the BF16 copies
+  // the dense matrices in 32 x 32 tiles, then the rest (both refresh the BF16 copies)
+  int mat_tiles = 0, vec_max = 0;
+  for (const LayerDev& L : F->layers) {
+    mat_tiles = std::max(mat_tiles, (std::max(L.nout_pad, kH) / 32) * (kH / 32));
+    vec_max = std::max(vec_max, kH * (L.na + 1) + 2 * kH + L.nout_pad);
+  }
+  mc::adam_mat_kernel<<<dim3(mat_tiles, 3 * F->L), dim3(32, 8), 0, st>>>(F->d_params, F->d_grads, F->d_m, F->d_v,
+                                                                       F->d_layers, A);
+  mc::adam_vec_kernel<<<dim3(mc::blocks_for(vec_max, 256), F->L), 256, 0, st>>>(F->d_params, F->d_grads, F->d_m,
+                                                                               F->d_v, F->d_layers, A);
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
