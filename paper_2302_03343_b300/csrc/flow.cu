@@ -49,6 +49,7 @@
 #include "event.cuh"
 #include "flow_spline.cuh"
 #include "handles.h"
+#include "launch.h"
 #include "tc_gemm.h"
 #include "tcgen05.cuh"
 
@@ -2026,10 +2027,25 @@ int check_err(mc_flow F, cudaStream_t st) {
 }
 
 size_t pdf_smem(const mc_integrand* itg, const mc::KernelArgs& a) {
-  const int nfl = itg->proc == MC_PP_TTBAR ? 11 : (a.pdf.nx ? 1 : 0);
+  const int nfl = (itg->proc == MC_PP_TTBAR || itg->proc == MC_PP_TTBARJ) ? 11 : (a.pdf.nx ? 1 : 0);
   return sizeof(float) * size_t(a.pdf.nx) * (1 + 2 * nfl);
 }
 
+int sm_count() {
+  static int num_sms = 0;
+  if (num_sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms < 1)
+      num_sms = 1;
+  }
+  return num_sms;
+}
+
+// The integrand at the n points X [n][D] of a training batch, one event per
+// thread (f = 0 outside the cuts, NaN where the integrand failed or is not
+// finite).  At 65 536 points the warp-specialised kernel with a points
+// input measured slower: the batch is too small for its pipeline.
 int eval_points(mc_flow F, const mc_integrand* itg, mc_pdf pdf, const float* X, long long n, float* f, cudaStream_t st) {
   mc::KernelArgs a;
   if (int rc = mc::fill_process_args(itg, pdf, &a)) return rc;
@@ -2044,17 +2060,38 @@ int eval_points(mc_flow F, const mc_integrand* itg, mc_pdf pdf, const float* X, 
     case MC_PP_TTBAR: mc::points_kernel<mc::P_PP_TTBAR><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
     case MC_GG_TTBARG: mc::points_kernel<mc::P_GG_TTBARG><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
     case MC_GG_TTBARG_7D: mc::points_kernel<mc::P_GG_TTBARG_7D><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
-    default: mc::points_kernel<mc::P_GAUSS><<<grid, kPts, smem, st>>>(a, X, F->D, f, n);
+    case MC_PP_TTBARJ: mc::points_kernel<mc::P_PP_TTBARJ><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
+    case MC_GAUSS: mc::points_kernel<mc::P_GAUSS><<<grid, kPts, smem, st>>>(a, X, F->D, f, n); break;
+    default: return ffail(MC_EINVAL, "mc_flow: the process has no flow integrand");
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
 }
 
+// The sampling pass's integrand at the n points X with log q: the block sums
+// of w = f exp(-log q) into F->parts, *nparts of them (g g -> t tbar g and
+// p p -> t tbar + parton on the warp-specialised kernel with a points input,
+// one block per SM; the other processes one event per thread).
 int eval_points_sums(mc_flow F, const mc_integrand* itg, const mc::KernelArgs& a, const float* X, const float* logq,
-                     long long n, cudaStream_t st) {
+                     long long n, cudaStream_t st, int* nparts) {
+  BlockPartial* parts = F->parts;
+  if (mc::points_ws(itg->proc)) {
+    mc::KernelArgs b = a;
+    b.ndim = F->D;
+    b.nbins = 0;
+    b.n = n;
+    b.pts = X;
+    b.pts_logq = logq;
+    b.wout = nullptr;
+    b.partials = parts;
+    b.status = F->err;
+    *nparts = std::min(sm_count(), kPartsGrid);
+    FLOW_CUDA(mc::launch_points_ws(itg->proc, b, *nparts, st));
+    return MC_OK;
+  }
   const size_t smem = pdf_smem(itg, a);
   const int grid = kPartsGrid;
-  BlockPartial* parts = F->parts;
+  *nparts = grid;
   switch (itg->proc) {
     case MC_EE_MUMU:
       mc::points_sums_kernel<mc::P_EE_MUMU><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
@@ -2062,13 +2099,8 @@ int eval_points_sums(mc_flow F, const mc_integrand* itg, const mc::KernelArgs& a
     case MC_PP_TTBAR:
       mc::points_sums_kernel<mc::P_PP_TTBAR><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
       break;
-    case MC_GG_TTBARG:
-      mc::points_sums_kernel<mc::P_GG_TTBARG><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
-      break;
-    case MC_GG_TTBARG_7D:
-      mc::points_sums_kernel<mc::P_GG_TTBARG_7D><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
-      break;
-    default: mc::points_sums_kernel<mc::P_GAUSS><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts);
+    case MC_GAUSS: mc::points_sums_kernel<mc::P_GAUSS><<<grid, 128, smem, st>>>(a, X, logq, F->D, n, parts); break;
+    default: return ffail(MC_EINVAL, "mc_flow: the process has no flow integrand");
   }
   FLOW_CUDA(cudaGetLastError());
   return MC_OK;
@@ -2563,8 +2595,9 @@ int mc_flow_iterate(mc_flow F, const mc_integrand* itg, mc_pdf pdf, int64_t neve
                                                                       first);
     FLOW_CUDA(cudaMemsetAsync(LQ, 0, sizeof(float) * np, st));
     if (int rc = all_fused ? forward_layers(F, np, false, st, Z, LQ) : forward_layers(F, np, false, st)) return rc;
-    if (int rc = eval_points_sums(F, itg, a, Z, LQ, n, st)) return rc;
-    FLOW_CUDA(mc::launch_finalize(F->parts, kPartsGrid, F->chunk_totals + c, st));
+    int nparts = 0;
+    if (int rc = eval_points_sums(F, itg, a, Z, LQ, n, st, &nparts)) return rc;
+    FLOW_CUDA(mc::launch_finalize(F->parts, nparts, F->chunk_totals + c, st));
   }
   FLOW_CUDA(mc::launch_finalize(F->chunk_totals, int(nchunks), F->total, st));
   FLOW_CUDA(cudaMemcpyAsync(F->h_total, F->total, sizeof(BlockPartial), cudaMemcpyDeviceToHost, st));

@@ -53,6 +53,11 @@ struct KernelArgs {
   double* record;          // [n][MC_REC_STRIDE] (debug launches only)
   int* status;             // optional: MC_ETIMEOUT when a bounded wait of the launch gave up
   double* wout;            // optional, [n]: weight of every event (0 outside the cuts), weights pass
+  // points input of the warp-specialised kernel (launch_points_ws): the
+  // points pts [n][ndim] in the unit cube replace Philox and the VEGAS map
+  // (nbins 0), and the weight is f exp(-pts_logq[i]) (pts_logq optional: f)
+  const float* pts;
+  const float* pts_logq;
   // three-channel process: cumulative channel probabilities (the channel of
   // an event is the first i with u < alpha_cum[i], u from Philox call 254),
   // the probabilities, and the alpha-update sums W_i (device, [3], added to)

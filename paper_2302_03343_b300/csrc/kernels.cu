@@ -496,6 +496,15 @@ static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+bool points_ws(int proc) { return proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_PP_TTBARJ; }
+cudaError_t launch_points_ws(int proc, const KernelArgs& a, int grid, cudaStream_t st) {
+  if (!points_ws(proc) || !a.pts || a.nbins != 0 || !a.partials || a.wout || grid < 1 || a.n < 0)
+    return cudaErrorInvalidValue;
+  return proc == P_GG_TTBARG      ? launch_ws<P_GG_TTBARG>(a, grid, st)
+         : proc == P_GG_TTBARG_7D ? launch_ws<P_GG_TTBARG_7D>(a, grid, st)
+                                  : launch_ws<P_PP_TTBARJ>(a, grid, st);
+}
+
 bool integrand_ws(int proc, bool fp64) {
   return !fp64 && (proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_GG_TTBARG_MC || proc == P_PP_TTBARJ);
 }

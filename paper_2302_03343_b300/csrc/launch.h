@@ -24,6 +24,12 @@ int integrand_max_blocks_per_sm(int proc, bool fp64, size_t smem);
 cudaError_t launch_integrand(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_integrand_record(int proc, bool fp64, const KernelArgs& a, int grid, size_t smem,
                                     cudaStream_t st);
+// The warp-specialised FP32 kernel at given points (KernelArgs::pts, nbins
+// 0, no wout): g g -> t tbar g (14 or 7 dims) and p p -> t tbar + parton;
+// the block sums of the weights f exp(-log q) into a.partials[grid] (one
+// block per SM).
+bool points_ws(int proc);
+cudaError_t launch_points_ws(int proc, const KernelArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_finalize(const BlockPartial* parts, int nblocks, BlockPartial* out, cudaStream_t st);
 cudaError_t launch_refine(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim, int nbins,
                           double alpha, cudaStream_t st);

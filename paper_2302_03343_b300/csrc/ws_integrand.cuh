@@ -223,18 +223,25 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
         if (WOUT && !e.pass) a.wout[i] = 0.0;
       }
     } else if (i < hi) {
-      uint64_t k[MAXD];
-      event_uniforms<MAXD, false>(a.seed, a.iteration, a.gid, a.first + uint64_t(i), ndim, k);
       float x[MAXD];
+      if (a.pts) {
+        // points input: x given; the record's Jacobian word carries log q(x)
 #pragma unroll
-      for (int dd = 0; dd < MAXD; ++dd) {
-        if (dd < ndim) {
-          int b;
-          float jd;
-          x[dd] = vegas_map_1d<float, false>(sh_edges + dd * (nb + 1), nb, k[dd], &b, &jd);
-          binw[dd / 4] |= uint32_t(b) << (8 * (dd % 4));
-          jac *= jd;
-          atomicAdd(&sh_n[dd * nb + b], 1u);
+        for (int dd = 0; dd < MAXD; ++dd) x[dd] = dd < ndim ? a.pts[size_t(i) * ndim + dd] : 0.5f;
+        jac = a.pts_logq ? a.pts_logq[i] : 0.0f;
+      } else {
+        uint64_t k[MAXD];
+        event_uniforms<MAXD, false>(a.seed, a.iteration, a.gid, a.first + uint64_t(i), ndim, k);
+#pragma unroll
+        for (int dd = 0; dd < MAXD; ++dd) {
+          if (dd < ndim) {
+            int b;
+            float jd;
+            x[dd] = vegas_map_1d<float, false>(sh_edges + dd * (nb + 1), nb, k[dd], &b, &jd);
+            binw[dd / 4] |= uint32_t(b) << (8 * (dd % 4));
+            jac *= jd;
+            atomicAdd(&sh_n[dd * nb + b], 1u);
+          }
         }
       }
       if constexpr (PROC == P_PP_TTBARJ) {
@@ -356,7 +363,7 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
         kin.k[j] = {__uint_as_float(r[(kWK + 4 * j + 0) * 32]), __uint_as_float(r[(kWK + 4 * j + 1) * 32]),
                     __uint_as_float(r[(kWK + 4 * j + 2) * 32]), __uint_as_float(r[(kWK + 4 * j + 3) * 32])};
       kin.rs = __uint_as_float(r[kWRs * 32]);
-      const float jac = __uint_as_float(r[kWJac * 32]);
+      const float jac = __uint_as_float(r[kWJac * 32]);  // log q(x) with a points input
       kin.psw = __hiloint2double(int(r[(kWPsw + 1) * 32]), int(r[kWPsw * 32]));
       uint32_t binw[NW];
 #pragma unroll
@@ -368,13 +375,14 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
         lum[0] = __uint_as_float(r[kWLgg * 32]);
 #pragma unroll
         for (int j = 0; j < 6; ++j) lum[1 + j] = __uint_as_float(r[(kWLum + j) * 32]);
-        w = ppj_weight<float>(a, kin, lum, nullptr) * double(jac);
+        w = ppj_weight<float>(a, kin, lum, nullptr);
       } else {
         kin.lgg = __uint_as_float(r[kWLgg * 32]);
         kin.flux = __uint_as_float(r[kWFlux * 32]);
         const float me2 = gg_me2<float>(a, kin, rows);
-        w = gg_weight<float>(a, kin, me2) * double(jac);
+        w = gg_weight<float>(a, kin, me2);
       }
+      w *= a.pts ? exp(-double(jac)) : double(jac);
       if (!isfinite(w)) {
         ++acc.nbad;
         w = 0.0;
@@ -400,7 +408,7 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
 #pragma unroll
         for (int d = 0; d < 7; ++d)
           atomicAdd(&sh_w2[ch_grid_dim(d, ch) * nb + int((binw[d / 4] >> (8 * (d % 4))) & 0xffu)], float(w2));
-      } else {
+      } else if (nb > 0) {
 #pragma unroll
         for (int dd = 0; dd < MAXD; ++dd)
           if (dd < ndim) atomicAdd(&sh_w2[dd * nb + int((binw[dd / 4] >> (8 * (dd % 4))) & 0xffu)], float(w2));
@@ -435,7 +443,8 @@ __global__ void __launch_bounds__(ws_threads(PROC), 1) ws_integrand_kernel(Kerne
   float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
   float* sh_pdf = sh_edges + nedge;
 
-  for (int i = threadIdx.x; i < nedge; i += blockDim.x) sh_edges[i] = a.edges32[i];
+  if (nb > 0)
+    for (int i = threadIdx.x; i < nedge; i += blockDim.x) sh_edges[i] = a.edges32[i];
   for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
     sh_w2[i] = 0.0f;
     sh_n[i] = 0u;

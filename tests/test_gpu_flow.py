@@ -156,20 +156,52 @@ def oracle_flow_sums(itg, pdf, arrays, D, seed, iteration, n):
     return w
 
 
-@pytest.mark.parametrize("name", ["gg7", "gauss"])
+@pytest.mark.parametrize("name", ["gg7", "ppj", "gauss"])
 def test_sampling_pass_matches_oracle(gpu, oracle_pdf, name):
-    itg = {"gg7": W.gg_ttbarg_7d(), "gauss": W.gauss(6, sigma=0.2)}[name]
+    itg = {"gg7": W.gg_ttbarg_7d(), "ppj": W.pp_ttbarj(), "gauss": W.gauss(6, sigma=0.2)}[name]
     D = itg.ndim()
     n = 3000
     f, arrays = make_flow(D, seed=17, last_scale=0.5, max_batch=1024, flow_seed=123)
-    r = M.mc_flow_iterate(f, itg, gpu if name == "gg7" else None, n, iteration=2)
-    w = oracle_flow_sums(itg, oracle_pdf if name == "gg7" else None, arrays, D, 123, 2, n)
+    r = M.mc_flow_iterate(f, itg, None if name == "gauss" else gpu, n, iteration=2)
+    w = oracle_flow_sums(itg, None if name == "gauss" else oracle_pdf, arrays, D, 123, 2, n)
     print(f"\n{name}: gpu sum {r.sum:.10e} oracle {w.sum():.10e} nnz {r.n_nonzero} vs {np.count_nonzero(w)} "
           f"bad {r.n_bad}")
     assert r.n == n and r.n_bad == 0
     assert abs(r.n_nonzero - np.count_nonzero(w)) <= 2
     assert abs(r.sum - w.sum()) <= 2e-3 * abs(w.sum())
     assert abs(r.sum2 - (w * w).sum()) <= 5e-3 * (w * w).sum()
+    f.free()
+
+
+@pytest.mark.parametrize("name", ["gg7", "ppj"])
+def test_training_batch_weights_match_oracle(gpu, oracle_pdf, name):
+    """The weights w = |f| / q of a training step's batch (Philox iteration
+    0x10000 + step, the integrand evaluated one event per thread) summed on
+    the device against the same batch written out with the oracle."""
+    itg = {"gg7": W.gg_ttbarg_7d(), "ppj": W.pp_ttbarj()}[name]
+    D = itg.ndim()
+    n = 2000
+    f, arrays = make_flow(D, seed=19, last_scale=0.5, max_batch=2048, flow_seed=77)
+    wsum = M.mc_flow_step_sample(f, itg, gpu, 0, n)
+    k = O.uniform_ints(77, 0x10000, 0, M.MC_FP32_KAHAN, D, 0, n).astype(np.float64)
+    x, lq = OF.flow_forward(OF.params_from_arrays(arrays), torch.tensor((2.0 * k + 1.0) / 2.0 ** 24, dtype=OF.DT),
+                            K, bf16=True)
+    fv, st = O.integrand_at(itg, oracle_pdf, x.numpy())
+    w = np.where(st == 0, np.abs(fv) * np.exp(-lq.numpy()), 0.0)
+    print(f"\n{name}: device sum of w {wsum:.10e} oracle {w.sum():.10e} in cuts {np.count_nonzero(w)} of {n}")
+    assert np.count_nonzero(w) > n // 4
+    assert abs(wsum - w.sum()) <= 2e-3 * abs(w.sum())
+    f.free()
+
+
+def test_flow_rejects_a_process_without_a_flow_integrand(gpu):
+    """The three-channel process has no flow integrand (its 17 grid
+    dimensions exceed the flow's 16 as well): training is refused."""
+    itg = W.gg_ttbarg_mc()
+    f, _ = make_flow(7, seed=2, last_scale=0.0, max_batch=256)
+    with pytest.raises(M.McError) as e:
+        M.mc_flow_train(f, itg, gpu, steps=1, batch=256, lr=1e-3, losses=False)
+    assert e.value.code == M.MC_EINVAL
     f.free()
 
 
