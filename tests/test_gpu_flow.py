@@ -135,6 +135,38 @@ def test_adam_first_step_moves_by_lr(gpu):
     f.free()
 
 
+def test_weight_copies_follow_the_adam_step(gpu):
+    """After an Adam step the BF16 copies the tensor cores read (W2..W4
+    row-major for the forward and transposed for the backward, W1 with its
+    bias column and transposed) are those of the updated FP32 parameters: the
+    loss and every gradient at a new batch agree with the oracle run from the
+    parameters read back.  The step (lr 1e-2) moves each weight by about a
+    tenth of its size, so a copy left behind or transposed wrongly fails."""
+    D, n = 7, 2000
+    f, _ = make_flow(D, seed=23, last_scale=0.5, max_batch=2048)
+    rng = np.random.default_rng(12)
+
+    def batch():
+        return (rng.random((n, D)).astype(np.float32), rng.exponential(size=n).astype(np.float32))
+
+    x0, w0 = batch()
+    M.mc_flow_loss_grad(f, torch.tensor(x0, device="cuda"), torch.tensor(w0, device="cuda"), grads=False)
+    M.mc_flow_adam_step(f, 1e-2)
+    new = M.mc_flow_get_params(f)
+    x, w = batch()
+    loss, grads = M.mc_flow_loss_grad(f, torch.tensor(x, device="cuda"), torch.tensor(w, device="cuda"))
+    lo, go = OF.loss_and_grads(OF.params_from_arrays(new), torch.tensor(x, dtype=OF.DT), torch.tensor(w, dtype=OF.DT),
+                               K, bf16=True)
+    print(f"\nloss after the step: gpu {loss:.8f} oracle {lo:.8f}")
+    assert abs(loss - lo) < 1e-4 * max(1.0, abs(lo))
+    for l in range(L):
+        for k in M.FLOW_KEYS:
+            c = cosine(grads[l][k], go[l][k].numpy())
+            nr = np.linalg.norm(grads[l][k]) / (np.linalg.norm(go[l][k].numpy()) + 1e-300)
+            assert c > 0.9995 and abs(nr - 1.0) < 0.005, (l, k, c, nr)
+    f.free()
+
+
 def test_params_round_trip(gpu):
     f, arrays = make_flow(7, seed=2, last_scale=0.7, max_batch=128)
     back = M.mc_flow_get_params(f)
