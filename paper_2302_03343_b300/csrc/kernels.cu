@@ -496,13 +496,25 @@ static cudaError_t launch_ws(const KernelArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// the points-input instance (no weights pass, no row store)
+template <int PROC>
+static cudaError_t launch_points(const KernelArgs& a, int grid, cudaStream_t st) {
+  auto k = ws_integrand_kernel<PROC, false, false, true>;
+  const size_t smem = ws_smem_bytes(PROC, a.ndim, 0, a.pdf.nx, false);
+  (void)cudaGetLastError();
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  k<<<grid, ws_threads(PROC), smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 bool points_ws(int proc) { return proc == P_GG_TTBARG || proc == P_GG_TTBARG_7D || proc == P_PP_TTBARJ; }
 cudaError_t launch_points_ws(int proc, const KernelArgs& a, int grid, cudaStream_t st) {
   if (!points_ws(proc) || !a.pts || a.nbins != 0 || !a.partials || a.wout || grid < 1 || a.n < 0)
     return cudaErrorInvalidValue;
-  return proc == P_GG_TTBARG      ? launch_ws<P_GG_TTBARG>(a, grid, st)
-         : proc == P_GG_TTBARG_7D ? launch_ws<P_GG_TTBARG_7D>(a, grid, st)
-                                  : launch_ws<P_PP_TTBARJ>(a, grid, st);
+  return proc == P_GG_TTBARG      ? launch_points<P_GG_TTBARG>(a, grid, st)
+         : proc == P_GG_TTBARG_7D ? launch_points<P_GG_TTBARG_7D>(a, grid, st)
+                                  : launch_points<P_PP_TTBARJ>(a, grid, st);
 }
 
 bool integrand_ws(int proc, bool fp64) {

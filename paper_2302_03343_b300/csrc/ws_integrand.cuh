@@ -171,7 +171,7 @@ struct WsRing {
 // (seq / S)-th time).  The Philox event index is a.first + i.  With WOUT the
 // weights pass writes a.wout[i] = 0 for the events that are cut and passes i
 // on in the record.  Returns false when a wait gave up.
-template <int PROC, bool WOUT>
+template <int PROC, bool WOUT, bool PTS = false>
 MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* sh_edges, unsigned int* sh_n,
                      const WsRing& ring, int p, long long lo, long long hi, long long k0, long long dk, int& seq,
                      Acc& acc) {
@@ -224,7 +224,7 @@ MC_D bool ws_produce(const KernelArgs& a, const SmPdf<float>& pdf, const float* 
       }
     } else if (i < hi) {
       float x[MAXD];
-      if (a.pts) {
+      if constexpr (PTS) {
         // points input: x given; the record's Jacobian word carries log q(x)
 #pragma unroll
         for (int dd = 0; dd < MAXD; ++dd) x[dd] = dd < ndim ? a.pts[size_t(i) * ndim + dd] : 0.5f;
@@ -327,7 +327,7 @@ MC_D SmemRows ws_rows(const unsigned char* sh_rows) {
 // histogram of w^2.  q0, q1: the next slot sequence numbers of its (up to two)
 // streams, carried over between calls.  With WOUT the weights pass writes
 // a.wout[i] = w.  Returns false when a wait gave up.
-template <int PROC, bool WOUT, class Rows>
+template <int PROC, bool WOUT, class Rows, bool PTS = false>
 MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows rows, int c, int& q0, int& q1,
                      Acc& acc) {
   constexpr int MAXD = ProcTraits<PROC>::MAXD;
@@ -382,7 +382,10 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
         const float me2 = gg_me2<float>(a, kin, rows);
         w = gg_weight<float>(a, kin, me2);
       }
-      w *= a.pts ? exp(-double(jac)) : double(jac);
+      if constexpr (PTS)
+        w *= exp(-double(jac));
+      else
+        w *= double(jac);
       if (!isfinite(w)) {
         ++acc.nbad;
         w = 0.0;
@@ -408,7 +411,7 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
 #pragma unroll
         for (int d = 0; d < 7; ++d)
           atomicAdd(&sh_w2[ch_grid_dim(d, ch) * nb + int((binw[d / 4] >> (8 * (d % 4))) & 0xffu)], float(w2));
-      } else if (nb > 0) {
+      } else if (!PTS) {
 #pragma unroll
         for (int dd = 0; dd < MAXD; ++dd)
           if (dd < ndim) atomicAdd(&sh_w2[dd * nb + int((binw[dd / 4] >> (8 * (dd % 4))) & 0xffu)], float(w2));
@@ -422,7 +425,7 @@ MC_D bool ws_consume(const KernelArgs& a, float* sh_w2, const WsRing& ring, Rows
 // WOUT: the weights pass (a.wout receives every event's weight; launches of
 // at most 2^32 - 1 events).  SMROWS: the consumers' row spinors in shared
 // memory (ws_rows_in_smem).
-template <int PROC, bool WOUT, bool SMROWS>
+template <int PROC, bool WOUT, bool SMROWS, bool PTS = false>
 __global__ void __launch_bounds__(ws_threads(PROC), 1) ws_integrand_kernel(KernelArgs a) {
   static_assert(PROC == P_GG_TTBARG || PROC == P_GG_TTBARG_7D || PROC == P_GG_TTBARG_MC || PROC == P_PP_TTBARJ,
                 "gg -> t tbar g and p p -> t tbar + parton only");
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(ws_threads(PROC), 1) ws_integrand_kernel(Kerne
   float* sh_edges = reinterpret_cast<float*>(rest + ((size_t(nhist) * 8 + 15) / 16) * 16);
   float* sh_pdf = sh_edges + nedge;
 
-  if (nb > 0)
+  if (!PTS)
     for (int i = threadIdx.x; i < nedge; i += blockDim.x) sh_edges[i] = a.edges32[i];
   for (int i = threadIdx.x; i < nhist; i += blockDim.x) {
     sh_w2[i] = 0.0f;
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(ws_threads(PROC), 1) ws_integrand_kernel(Kerne
   if (warp < NP) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(ws_producer_regs(PROC)));
     int seq = 0;
-    ok = ws_produce<PROC, WOUT>(a, pdf, sh_edges, sh_n, ring, warp, 0, a.n, (long long)blockIdx.x * NP + warp,
+    ok = ws_produce<PROC, WOUT, PTS>(a, pdf, sh_edges, sh_n, ring, warp, 0, a.n, (long long)blockIdx.x * NP + warp,
                                 (long long)gridDim.x * NP, seq, acc);
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(ws_regs(PROC)));
   } else {
@@ -482,9 +485,9 @@ __global__ void __launch_bounds__(ws_threads(PROC), 1) ws_integrand_kernel(Kerne
     int q0 = c / NP, q1 = q0;
     if constexpr (SMROWS) {
       SmemRows rows = ws_rows<PROC>(sh_rows);
-      ok = ws_consume<PROC, WOUT>(a, sh_w2, ring, rows, c, q0, q1, acc);
+      ok = ws_consume<PROC, WOUT, SmemRows, PTS>(a, sh_w2, ring, rows, c, q0, q1, acc);
     } else {
-      ok = ws_consume<PROC, WOUT>(a, sh_w2, ring, NoRows{}, c, q0, q1, acc);
+      ok = ws_consume<PROC, WOUT, NoRows, PTS>(a, sh_w2, ring, NoRows{}, c, q0, q1, acc);
     }
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(ws_regs(PROC)));
   }
