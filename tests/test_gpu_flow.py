@@ -205,6 +205,23 @@ def test_sampling_pass_matches_oracle(gpu, oracle_pdf, name):
     f.free()
 
 
+@pytest.mark.parametrize("n", [1, 31, 129, 4097])
+def test_sampling_pass_ragged_sizes(gpu, oracle_pdf, n):
+    """The sampling pass at event counts that leave most blocks of the
+    warp-specialised kernel without a point, or end in a partial chunk and a
+    partial 128-row tile: the same sums as the oracle's pass."""
+    itg = W.gg_ttbarg_7d()
+    D = itg.ndim()
+    f, arrays = make_flow(D, seed=29, last_scale=0.5, max_batch=1024, flow_seed=41)
+    r = M.mc_flow_iterate(f, itg, gpu, n, iteration=5)
+    w = oracle_flow_sums(itg, oracle_pdf, arrays, D, 41, 5, n)
+    print(f"\nn={n}: gpu sum {r.sum:.10e} oracle {w.sum():.10e} nnz {r.n_nonzero} vs {np.count_nonzero(w)}")
+    assert r.n == n and r.n_bad == 0
+    assert abs(r.n_nonzero - np.count_nonzero(w)) <= 1
+    assert abs(r.sum - w.sum()) <= 2e-3 * abs(w.sum()) + 1e-12
+    f.free()
+
+
 @pytest.mark.parametrize("name", ["gg7", "ppj"])
 def test_training_batch_weights_match_oracle(gpu, oracle_pdf, name):
     """The weights w = |f| / q of a training step's batch (Philox iteration
