@@ -71,10 +71,10 @@ METRIC = "events/sec and GPU time to 1e-3 rel. error: FP32+flow vs plain FP64 VE
 # how busy the pipes are.
 EXECUTED_FLOP_PER_EVENT = 20720.0
 # DRAM bytes (read + write) of one launch of that kernel, from an ncu capture
-# of this workload (0.46 MB read + 3.15 MB written; see profiles/).  Nothing
+# of this workload (0.46 MB read + 3.24 MB written; see profiles/).  Nothing
 # per event reaches DRAM: the kernel reads the grid and the PDF grid and
 # writes histograms and per-block partials.
-TRAFFIC_BYTES = 3608832
+TRAFFIC_BYTES = 3700480
 FP32_LANES_PER_SM = 128
 # FP32 FLOP per FP32 lane operation of that launch: its ncu counts give
 # 2 ffma + fmul + fadd + 4 ffma2 + 2 fmul2 + 2 fadd2 = 1.668e11 FLOP over
