@@ -2277,8 +2277,10 @@ int mc_flow_create(const mc_flow_cfg* cfg, const float* init, int64_t max_batch,
   alloc((void**)&F->dAT, sizeof(__nv_bfloat16) * 2 * 3 * bp * kH);
   // four partial regions (the side stream's W4, W3, W2, W1 products of a
   // layer) and three bias-partial regions
-  F->part_region = size_t(F->max_splits) * kH * np;
-  F->bpart_region = size_t(F->max_splits) * np;
+  // N of a product is nout_pad (W4), H (W3, W2) or 16 (W1)
+  const size_t nmax = std::max(np, size_t(kH));
+  F->part_region = size_t(F->max_splits) * kH * nmax;
+  F->bpart_region = size_t(F->max_splits) * nmax;
   alloc((void**)&F->part, sizeof(float) * 4 * F->part_region);
   alloc((void**)&F->bpart, sizeof(float) * 3 * F->bpart_region);
   alloc((void**)&F->UT, sizeof(__nv_bfloat16) * L * mc::kUPad * bp);
