@@ -8,7 +8,7 @@
 //    in FP32 mode with producer (kinematics) and consumer (|M|^2) warps.
 //  * finalize_kernel: fixed-order reduction of the per-block partials
 //    (deterministic sums for a given launch shape).
-//  * refine_kernel: VEGAS rebinning, one thread per dimension, FP64.
+//  * refine_kernel: VEGAS rebinning, one warp (block) per dimension, FP64.
 //  * pdf_xfxq2_kernel: batched log-bicubic PDF interpolation (all flavours).
 #include <cstdio>
 #include <type_traits>
@@ -95,15 +95,17 @@ __global__ void finalize_kernel(const BlockPartial* parts, int nblocks, BlockPar
   if (threadIdx.x == 0) *out = sh[0];
 }
 
-// Refinement kernel of one grid: one warp per dimension (refine_dimension in
-// refine.cuh); dynamic shared memory ndim * (3 nbins + 2) doubles.
+// Refinement kernel of one grid: one block of one warp per dimension
+// (refine_dimension in refine.cuh), so that the FP64 logarithms and powers of
+// the damping (B300's FP64 pipe runs at 1/64 of FP32) spread over ndim SMs;
+// dynamic shared memory 3 nbins + 2 doubles.
 __global__ void refine_kernel(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim,
                               int nbins, double alpha) {
   extern __shared__ double refine_smem[];
-  const int d = threadIdx.x >> 5;
+  const int d = blockIdx.x;
   if (d >= ndim) return;
   refine_dimension(edges + size_t(d) * (nbins + 1), edges32 + size_t(d) * (nbins + 1), hist_w2 + size_t(d) * nbins,
-                   hist_n + size_t(d) * nbins, nbins, alpha, refine_smem + size_t(d) * (3 * nbins + 2));
+                   hist_n + size_t(d) * nbins, nbins, alpha, refine_smem);
 }
 
 // Batched xf(x, Q^2) for all flavours, one thread per point: the range
@@ -604,13 +606,9 @@ cudaError_t launch_finalize(const BlockPartial* parts, int nblocks, BlockPartial
 }
 cudaError_t launch_refine(double* edges, float* edges32, double* hist_w2, unsigned int* hist_n, int ndim, int nbins,
                           double alpha, cudaStream_t st) {
-  const size_t smem = sizeof(double) * size_t(ndim) * (3 * nbins + 2);
+  const size_t smem = sizeof(double) * size_t(3 * nbins + 2);
   (void)cudaGetLastError();
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-  }
-  refine_kernel<<<1, 32 * ndim, smem, st>>>(edges, edges32, hist_w2, hist_n, ndim, nbins, alpha);
+  refine_kernel<<<ndim, 32, smem, st>>>(edges, edges32, hist_w2, hist_n, ndim, nbins, alpha);
   return cudaGetLastError();
 }
 cudaError_t launch_pdf_xfxq2(const PdfDev& pdf, bool fp64, long long n, const double* x, const double* q2,
